@@ -1,0 +1,224 @@
+/*
+ * ddeig.h -- C ABI of the GB300 two-level domain-decomposition eigensolver.
+ *
+ * Computes the ground state (lambda_1, phi) of the Schroedinger eigenproblem
+ *     -Laplace(phi) + V phi = lambda phi  on  (0,L)^p x (0,ell),  phi = 0 on the boundary
+ * (Theisen & Stamm, arXiv 2311.08757: the Schroedinger equation and box geometry of Sec. 1)
+ * discretised by Q1 finite elements on the uniform grid h = 1/n (Sec. 2, discrete weak
+ * form): A x = lambda B x with A = K + M_V, B = M.  The method is the shifted inverse
+ * iteration x_{k+1} = A_sigma^{-1} B x_k of Sec. 2, sigma the lowest eigenvalue of the
+ * x-periodic unit-cell problem (cell problem of Sec. 1, weak cell problem of Sec. 2).  Each
+ * shifted system A_sigma w = b (A_sigma = A - sigma M) is solved by conjugate gradients
+ * preconditioned with the two-level additive Schwarz operator M_AS2^{-1} (Sec. 2.2, Sec. 3.1)
+ * (one overlapping subdomain per unit cell, PerFact coarse space of Definition 2.1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Supported geometry: p in {1, 2} expanding directions, q = 1 fixed direction.
+ *  - Vectors over the box are FP64 arrays of length
+ *        ndof = (L n - 1)^p (ell n - 1)
+ *    holding the values at the interior nodes, y fastest, then x_p, ..., x_1 slowest:
+ *    node (a, j) (1 <= a <= Ln-1, 1 <= j <= ell n - 1) is entry (a-1)(ell n-1) + (j-1);
+ *    for p = 2, node (a1, a2, j) is ((a1-1)(Ln-1) + (a2-1))(ell n-1) + (j-1).
+ *  - Cell vectors (psi) have length n^p (ell n - 1): node (a, j), 0 <= a < n, is entry
+ *    a(ell n - 1) + (j-1) (p = 2: ((a1 n + a2)(ell n - 1) + j - 1)).
+ *  - V_cell_qp: the potential sampled on the unit cell at tensor Gauss-Legendre points,
+ *    quad_pts per direction.  Element-major: elements (ex, ey) (p = 2: (ex1, ex2, ey)),
+ *    ey fastest, element (ex, ey) = [ex h, (ex+1) h] x [ey h, (ey+1) h]; inside an element
+ *    the quad_pts^(p+1) points are ordered (qx, qy) (p = 2: (qx1, qx2, qy)), qy fastest.
+ *    Length n^p (ell n) quad_pts^(p+1).  V must be 1-periodic in x (assumption A1).
+ *  - Pointer arguments marked "host or device" may point to device memory or to host
+ *    memory (pageable or pinned); host buffers are staged through the context's device
+ *    buffers inside the call.  The caller owns every buffer it passes; the context owns
+ *    everything it allocates.
+ *  - Calls run on the CUDA stream given to dd_setup and return after the work has
+ *    completed (each call synchronises that stream before returning its scalars).
+ *  - Every call returns DD_OK (0) or a negative status; no exception crosses the ABI and
+ *    nothing aborts the process.  dd_status_string() names a status; dd_last_error()
+ *    gives a message for the last failure in the context.
+ */
+#ifndef DDEIG_H
+#define DDEIG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DD_OK           0
+#define DD_EINVAL      -1   /* bad argument or grid (L < 1, n < 3, delta < 1, 2 delta >= n, nV mismatch ...) */
+#define DD_ESTATE      -2   /* call out of order (e.g. pcg_solve before coarse_build) */
+#define DD_ENOMEM      -3   /* device allocation failed */
+#define DD_ECUDA       -4   /* CUDA runtime error */
+#define DD_ENAN        -5   /* non-finite input or iterate */
+#define DD_ENOTSPD     -6   /* non-positive pivot or p^T A p <= 0 (operator or shift not SPD) */
+#define DD_EMAXIT      -7   /* iteration limit reached; outputs hold the last iterate */
+#define DD_ETIMEOUT    -8   /* a bounded device-side wait gave up; the context must be destroyed */
+#define DD_EUNSUPPORTED -9  /* option combination not built (e.g. a precision for this size) */
+
+/* Local-inverse precision (the only place below FP64). */
+#define DD_PREC_FP64 0      /* local solves by FP64 banded Cholesky (plain method) */
+#define DD_PREC_TF32 1      /* dense local inverses, TF32 tensor-core GEMM, FP32 accumulate */
+#define DD_PREC_BF16 2      /* dense local inverses, BF16 tensor-core GEMM, FP32 accumulate */
+
+/* Partition of unity D_i (Sec. 2.2 equal weights; Sec. 4.1.2 distance based). */
+#define DD_PU_EQUAL    0
+#define DD_PU_DISTANCE 1
+
+typedef struct {
+    int    p;          /* expanding directions: 1 or 2                                     */
+    int    q;          /* fixed directions: must be 1                                      */
+    int    L;          /* domain length in unit cells, >= 1 (Sec. 1 box geometry, L in N)  */
+    double ell;        /* fixed-direction length; ell * n must be an integer >= 2         */
+    int    n;          /* elements per unit length, h = 1/n, n >= 3                        */
+    int    overlap;    /* delta >= 1 element layers added on each x side (Sec. 3.1), 2 delta < n */
+    int    quad_pts;   /* Gauss points per direction for int V phi v: 1..4 (default 2)   */
+    int    pu_kind;    /* DD_PU_EQUAL or DD_PU_DISTANCE                                   */
+    int    precision;  /* DD_PREC_*                                                        */
+    int    coarse;     /* 1: two-level M_AS2 (Sec. 2.2); 0: one-level M_AS1 ablation       */
+} dd_grid;
+
+typedef struct dd_ctx dd_ctx;    /* opaque; owns every device buffer it allocates */
+
+/* Sizes and state of a context (filled by dd_query). */
+typedef struct {
+    long long ndof;          /* interior unknowns of the box                               */
+    long long ncell;         /* unknowns of the periodic cell problem                       */
+    int       nsub;          /* subdomains N = L^p                                          */
+    int       ntypes;        /* distinct local matrices (left/interior/right per axis)      */
+    int       nloc_max;      /* largest local problem |N_i|                                 */
+    int       kpad;          /* local size padded for the tensor-core GEMM                  */
+    int       band_local;    /* half bandwidth of the local matrices                        */
+    double    sigma;         /* cell shift (valid after dd_cell_eigenpair)                  */
+    int       cell_iters;    /* inverse iterations used by the cell solve                   */
+    int       stage;         /* 1 set up, 2 cell eigenpair done, 3 coarse built             */
+    long long device_bytes;  /* device memory held by the context                           */
+} dd_info;
+
+/*
+ * dd_setup -- validate the grid, allocate the context, upload V and build the periodic
+ * stencil tables of A = K + M_V and M (Sec. 2: translated cell meshes make every box row
+ * a translated cell row, and V is periodic by assumption A1).
+ *   g          grid and options (copied)
+ *   V_cell_qp  host or device, nV doubles, layout above; non-finite values -> DD_ENAN
+ *   stream     cudaStream_t to run on (NULL = the legacy default stream)
+ *   out        receives the context; *out = NULL on failure
+ */
+int dd_setup(const dd_grid* g, const double* V_cell_qp, size_t nV, void* stream, dd_ctx** out);
+
+/*
+ * dd_cell_eigenpair -- lowest eigenpair (sigma, psi) of the x-periodic, y-Dirichlet cell
+ * problem (cell problem of Sec. 1, weak cell problem of Sec. 2), psi > 0, psi^T M_# psi = 1;
+ * then forms A_sigma = A - sigma M (Sec. 1.1) and the coarse weights D_i R_i E^# psi (Def. 2.1).
+ *   sigma_out     host, receives sigma (may be NULL)
+ *   psi_cell_out  host or device, n^p (ell n - 1) doubles, or NULL
+ */
+int dd_cell_eigenpair(dd_ctx* ctx, double* sigma_out, double* psi_cell_out);
+
+/*
+ * dd_coarse_build -- local matrices A_{sigma,i} = R_i A_sigma R_i^T per distinct subdomain
+ * type, factorised (FP64 banded Cholesky) and, for TF32/BF16, inverted and rounded; the
+ * coarse matrix A_{sigma,0} = R_0 A_sigma R_0^T (Sec. 3.1) assembled and factorised.
+ * DD_ENOTSPD if a local or coarse matrix is not positive definite.
+ */
+int dd_coarse_build(dd_ctx* ctx);
+
+/*
+ * dd_pcg_solve -- solve A_sigma x = b by CG preconditioned with M_AS2^{-1} (Sec. 3.1; the
+ * one-level M_AS1^{-1} when grid.coarse = 0); flexible CG (Polak-Ribiere beta) when the
+ * local inverses are rounded (TF32/BF16).  Stops when ||r_k||_2 <= rtol ||r_0||_2 (Sec. 4.1).
+ *   b          host or device, ndof doubles
+ *   x          host or device, ndof doubles; in: initial guess, out: solution
+ *   iters_out  host, iterations used (may be NULL);  relres_out host, ||r_k||/||r_0|| (may be NULL)
+ * DD_EMAXIT when maxit is reached (x holds the last iterate).
+ */
+int dd_pcg_solve(dd_ctx* ctx, const double* b, double* x, double rtol, int maxit,
+                 int* iters_out, double* relres_out);
+
+/*
+ * dd_inverse_iterate -- shifted inverse iteration (Sec. 2): b = M x_k, solve A_sigma w = b
+ * by dd_pcg_solve with zero initial guess and relative tolerance rtol_inner, x_{k+1} =
+ * w / ||w||_M (sign: sum x > 0); rho = x^T A x, eta = ||A x - rho M x||_2 / (|rho| ||M x||_2).
+ * Stops when eta <= tol_res and |rho_k - rho_{k-1}| <= tol_lam |rho_k|.
+ *   x                host or device, ndof doubles; in: x_0 (any nonzero vector; its M-norm is
+ *                    normalised), out: phi (M-normalised)
+ *   lambda_out       host, the Rayleigh quotient rho of the returned x (may be NULL)
+ *   outer_out, inner_total_out, inner_max_out  host iteration counts (may be NULL)
+ */
+int dd_inverse_iterate(dd_ctx* ctx, double* x, double tol_res, double tol_lam, int maxit_outer,
+                       double rtol_inner, double* lambda_out, int* outer_out,
+                       int* inner_total_out, int* inner_max_out);
+
+/*
+ * dd_eigenpair -- convenience: dd_setup, dd_cell_eigenpair, dd_coarse_build and
+ * dd_inverse_iterate from x_0 = 1 with tol_res = 1e-8, tol_lam = 1e-10, rtol_inner = 1e-8,
+ * maxit_outer = 100, then dd_destroy.
+ *   phi_out     host or device, ndof doubles (may be NULL)
+ *   lambda_out, sigma_out   host (may be NULL)
+ */
+int dd_eigenpair(const dd_grid* g, const double* V_cell_qp, size_t nV, void* stream,
+                 double* lambda_out, double* phi_out, double* sigma_out);
+
+/* dd_destroy -- free the context and everything it owns (NULL is ignored). */
+void dd_destroy(dd_ctx* ctx);
+
+/* dd_status_string -- static name of a status code. */
+const char* dd_status_string(int status);
+
+/* dd_last_error -- message of the last failure recorded in ctx ("" if none; ctx may be NULL
+ * for failures of dd_setup itself, which are kept per thread). */
+const char* dd_last_error(const dd_ctx* ctx);
+
+/* dd_query -- sizes and state of a context. */
+int dd_query(const dd_ctx* ctx, dd_info* info);
+
+/* ---------------------------------------------------------------------------------------
+ * Operator-level entry points (same layouts as above).  They expose the individual steps
+ * of the iteration so that each can be checked against an independent implementation.
+ * ------------------------------------------------------------------------------------- */
+
+#define DD_OP_ASIGMA 0   /* y = A_sigma x  (needs dd_cell_eigenpair)        */
+#define DD_OP_MASS   1   /* y = M x                                          */
+#define DD_OP_A      2   /* y = (K + M_V) x                                  */
+
+/* y = op x over the box (x, y host or device, ndof doubles). */
+int dd_apply_operator(dd_ctx* ctx, int op, const double* x, double* y);
+
+/* z = M_AS2^{-1} r (or M_AS1^{-1} r), Sec. 3.1 (r, z host or device, ndof doubles);
+ * needs dd_coarse_build. */
+int dd_apply_preconditioner(dd_ctx* ctx, const double* r, double* z);
+
+/* Coarse matrix A_{sigma,0} = R_0 A_sigma R_0^T copied to host as a dense nsub x nsub
+ * row-major array (needs dd_coarse_build; grid.coarse = 1). */
+int dd_coarse_matrix(dd_ctx* ctx, double* A0_host);
+
+/* Options of the iteration engine (defaults in brackets):
+ *   DD_OPT_CHECK_EVERY  iterations between host convergence checks [8]
+ *   DD_OPT_USE_GRAPH    replay the PCG iteration as a CUDA graph [1]
+ *   DD_OPT_FLEXIBLE     -1 automatic (flexible iff rounded local inverses) / 0 / 1 [-1]
+ *   DD_OPT_TIMING       1: time every kernel class with CUDA events (eager launches) [0] */
+#define DD_OPT_CHECK_EVERY 0
+#define DD_OPT_USE_GRAPH   1
+#define DD_OPT_FLEXIBLE    2
+#define DD_OPT_TIMING      3
+int dd_set_option(dd_ctx* ctx, int option, int value);
+
+/* Per-kernel-class timing collected while DD_OPT_TIMING = 1: for class k (0 <= k < count),
+ * names[k] (static string), launches[k] and total device milliseconds ms[k].  Pass NULL
+ * arrays to get only *count.  dd_reset_timings zeroes the counters. */
+int dd_kernel_timings(dd_ctx* ctx, int* count, const char** names, long long* launches, double* ms);
+int dd_reset_timings(dd_ctx* ctx);
+
+/* Self-test of the tensor-core contraction used for the local solves (no paper counterpart;
+ * it checks the kernel in isolation): D[n][m] = sum_k A[m][k] B[n][k] for host row-major
+ * A (M x K) and B (N x K), rounded to BF16 (precision = DD_PREC_BF16, nearest even) or
+ * read as TF32 (DD_PREC_TF32), FP32 accumulation; D is host N x M row-major.  Allocates and
+ * frees its own device buffers.  DD_ETIMEOUT if a bounded device wait expired. */
+int dd_tc_gemm_test(int precision, int M, int N, int K, const float* A_host, const float* B_host, float* D_host);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DDEIG_H */

@@ -1,0 +1,272 @@
+"""Python binding of ``libddeig`` (ctypes; argument marshalling only).
+
+Every function here has the name and argument order of the C entry point in
+``include/ddeig.h`` and forwards to it; all arithmetic runs in the library's CUDA
+kernels.  Vector arguments may be CUDA tensors (device pointers are passed through)
+or host arrays (numpy arrays or CPU tensors, staged by the library).  A failing call
+raises :class:`DDError` carrying the status code and the library's message.
+
+The library is built in-tree by ``__graft_entry__.build()`` (or
+``python -m paper_2311_08757_gb300._build``); importing this package does not load
+it, the first call does, and fails loudly if it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, byref, c_char_p, c_double, c_int, c_longlong, c_size_t, c_void_p
+
+from . import _build
+
+DD_OK, DD_EINVAL, DD_ESTATE, DD_ENOMEM, DD_ECUDA, DD_ENAN, DD_ENOTSPD, DD_EMAXIT, DD_ETIMEOUT, \
+    DD_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
+DD_PREC_FP64, DD_PREC_TF32, DD_PREC_BF16 = 0, 1, 2
+DD_PU_EQUAL, DD_PU_DISTANCE = 0, 1
+DD_OP_ASIGMA, DD_OP_MASS, DD_OP_A = 0, 1, 2
+DD_OPT_CHECK_EVERY, DD_OPT_USE_GRAPH, DD_OPT_FLEXIBLE, DD_OPT_TIMING = 0, 1, 2, 3
+PRECISIONS = {"fp64": DD_PREC_FP64, "tf32": DD_PREC_TF32, "bf16": DD_PREC_BF16}
+
+
+class dd_grid(ctypes.Structure):
+    _fields_ = [("p", c_int), ("q", c_int), ("L", c_int), ("ell", c_double), ("n", c_int),
+                ("overlap", c_int), ("quad_pts", c_int), ("pu_kind", c_int), ("precision", c_int),
+                ("coarse", c_int)]
+
+
+class dd_info(ctypes.Structure):
+    _fields_ = [("ndof", c_longlong), ("ncell", c_longlong), ("nsub", c_int), ("ntypes", c_int),
+                ("nloc_max", c_int), ("kpad", c_int), ("band_local", c_int), ("sigma", c_double),
+                ("cell_iters", c_int), ("stage", c_int), ("device_bytes", c_longlong)]
+
+
+class DDError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        self.code = code
+        super().__init__(f"{status_string(code)}: {message}")
+
+
+_lib = None
+
+_SIGS = {
+    "dd_setup": (c_int, [POINTER(dd_grid), c_void_p, c_size_t, c_void_p, POINTER(c_void_p)]),
+    "dd_cell_eigenpair": (c_int, [c_void_p, POINTER(c_double), c_void_p]),
+    "dd_coarse_build": (c_int, [c_void_p]),
+    "dd_pcg_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int, POINTER(c_int), POINTER(c_double)]),
+    "dd_inverse_iterate": (c_int, [c_void_p, c_void_p, c_double, c_double, c_int, c_double, POINTER(c_double),
+                                   POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
+    "dd_eigenpair": (c_int, [POINTER(dd_grid), c_void_p, c_size_t, c_void_p, POINTER(c_double), c_void_p,
+                             POINTER(c_double)]),
+    "dd_destroy": (None, [c_void_p]),
+    "dd_status_string": (c_char_p, [c_int]),
+    "dd_last_error": (c_char_p, [c_void_p]),
+    "dd_query": (c_int, [c_void_p, POINTER(dd_info)]),
+    "dd_apply_operator": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    "dd_apply_preconditioner": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "dd_coarse_matrix": (c_int, [c_void_p, c_void_p]),
+    "dd_set_option": (c_int, [c_void_p, c_int, c_int]),
+    "dd_kernel_timings": (c_int, [c_void_p, POINTER(c_int), POINTER(c_char_p), POINTER(c_longlong),
+                                  POINTER(c_double)]),
+    "dd_reset_timings": (c_int, [c_void_p]),
+    "dd_tc_gemm_test": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load ``libddeig.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def status_string(code: int) -> str:
+    return lib().dd_status_string(code).decode()
+
+
+def _check(code: int, ctx=None, allow=()):
+    if code != DD_OK and code not in allow:
+        msg = lib().dd_last_error(ctx).decode()
+        raise DDError(code, msg)
+    return code
+
+
+def _ptr(a):
+    """Raw pointer of a torch tensor or numpy array (contiguous float64), or None."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return c_void_p(a.data_ptr())
+    if hasattr(a, "ctypes"):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return c_void_p(a.ctypes.data)
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return c_void_p(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            pass
+        return None
+    if isinstance(stream, int):
+        return c_void_p(stream)
+    return c_void_p(stream.cuda_stream)
+
+
+def make_grid(p=1, L=1, n=16, ell=1.0, overlap=1, quad_pts=2, pu_kind=DD_PU_EQUAL, precision=DD_PREC_FP64,
+              coarse=1) -> dd_grid:
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    return dd_grid(p=p, q=1, L=L, ell=ell, n=n, overlap=overlap, quad_pts=quad_pts, pu_kind=pu_kind,
+                   precision=precision, coarse=coarse)
+
+
+def grid_from_workload(w, precision=DD_PREC_FP64, coarse=1, pu_kind=DD_PU_EQUAL) -> dd_grid:
+    return make_grid(p=w.p, L=w.L, n=w.n, ell=w.ell, overlap=w.overlap, quad_pts=w.quad_pts,
+                     pu_kind=pu_kind, precision=precision, coarse=coarse)
+
+
+# ---- entry points (names of include/ddeig.h) ------------------------------------------
+
+def dd_setup(grid: dd_grid, V_cell_qp, stream=None) -> c_void_p:
+    ctx = c_void_p()
+    n = V_cell_qp.numel() if hasattr(V_cell_qp, "numel") else V_cell_qp.size
+    _check(lib().dd_setup(byref(grid), _ptr(V_cell_qp), n, _stream_ptr(stream), byref(ctx)))
+    return ctx
+
+
+def dd_cell_eigenpair(ctx, psi_cell_out=None) -> float:
+    s = c_double()
+    _check(lib().dd_cell_eigenpair(ctx, byref(s), _ptr(psi_cell_out)), ctx)
+    return s.value
+
+
+def dd_coarse_build(ctx) -> None:
+    _check(lib().dd_coarse_build(ctx), ctx)
+
+
+def dd_pcg_solve(ctx, b, x, rtol=1e-8, maxit=10000, allow_maxit=False):
+    it, rel = c_int(), c_double()
+    _check(lib().dd_pcg_solve(ctx, _ptr(b), _ptr(x), rtol, maxit, byref(it), byref(rel)), ctx,
+           allow=(DD_EMAXIT,) if allow_maxit else ())
+    return it.value, rel.value
+
+
+def dd_inverse_iterate(ctx, x, tol_res=1e-8, tol_lam=1e-10, maxit_outer=100, rtol_inner=1e-8):
+    lam, outer, tot, mx = c_double(), c_int(), c_int(), c_int()
+    _check(lib().dd_inverse_iterate(ctx, _ptr(x), tol_res, tol_lam, maxit_outer, rtol_inner, byref(lam),
+                                    byref(outer), byref(tot), byref(mx)), ctx)
+    return lam.value, outer.value, tot.value, mx.value
+
+
+def dd_eigenpair(grid: dd_grid, V_cell_qp, stream=None, phi_out=None):
+    lam, sig = c_double(), c_double()
+    n = V_cell_qp.numel() if hasattr(V_cell_qp, "numel") else V_cell_qp.size
+    _check(lib().dd_eigenpair(byref(grid), _ptr(V_cell_qp), n, _stream_ptr(stream), byref(lam), _ptr(phi_out),
+                              byref(sig)))
+    return lam.value, sig.value
+
+
+def dd_destroy(ctx) -> None:
+    if ctx:
+        lib().dd_destroy(ctx)
+
+
+def dd_query(ctx) -> dict:
+    info = dd_info()
+    _check(lib().dd_query(ctx, byref(info)), ctx)
+    return {k: getattr(info, k) for k, _ in dd_info._fields_}
+
+
+def dd_apply_operator(ctx, op: int, x, y) -> None:
+    _check(lib().dd_apply_operator(ctx, op, _ptr(x), _ptr(y)), ctx)
+
+
+def dd_apply_preconditioner(ctx, r, z) -> None:
+    _check(lib().dd_apply_preconditioner(ctx, _ptr(r), _ptr(z)), ctx)
+
+
+def dd_coarse_matrix(ctx, A0_host) -> None:
+    _check(lib().dd_coarse_matrix(ctx, _ptr(A0_host)), ctx)
+
+
+def dd_set_option(ctx, option: int, value: int) -> None:
+    _check(lib().dd_set_option(ctx, option, value), ctx)
+
+
+def dd_kernel_timings(ctx) -> dict:
+    cnt = c_int()
+    _check(lib().dd_kernel_timings(ctx, byref(cnt), None, None, None), ctx)
+    n = cnt.value
+    names = (c_char_p * n)()
+    launches = (c_longlong * n)()
+    ms = (c_double * n)()
+    _check(lib().dd_kernel_timings(ctx, byref(cnt), names, launches, ms), ctx)
+    return {names[k].decode(): (launches[k], ms[k]) for k in range(n)}
+
+
+def dd_reset_timings(ctx) -> None:
+    _check(lib().dd_reset_timings(ctx), ctx)
+
+
+def dd_tc_gemm_test(precision: int, A, B, D) -> int:
+    """D[n][m] = sum_k A[m][k] B[n][k] (host float32 arrays) through the tensor-core kernel."""
+    M, K = A.shape
+    N = B.shape[0]
+    return _check(lib().dd_tc_gemm_test(precision, M, N, K, _ptr(A), _ptr(B), _ptr(D)))
+
+
+class Eigensolver:
+    """Owns a context: set-up, cell eigenpair, coarse build; ``ground_state`` runs
+    the inverse iteration.  Thin convenience over the entry points above."""
+
+    def __init__(self, grid: dd_grid, V_cell_qp, stream=None):
+        self.ctx = dd_setup(grid, V_cell_qp, stream)
+        self.grid = grid
+
+    def close(self):
+        if self.ctx:
+            dd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def info(self) -> dict:
+        return dd_query(self.ctx)
+
+    def prepare(self):
+        sigma = dd_cell_eigenpair(self.ctx)
+        dd_coarse_build(self.ctx)
+        return sigma
+
+    def ground_state(self, x, **kw):
+        return dd_inverse_iterate(self.ctx, x, **kw)

@@ -1,0 +1,740 @@
+// C ABI and host runtime: context set-up, the PCG engine (eager launches or a replayed
+// CUDA graph of a block of iterations), the shifted inverse iteration, staging of host
+// buffers, error reporting.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "dd_common.cuh"
+
+using dd::Error;
+
+namespace {
+
+thread_local std::string g_setup_err;
+
+bool is_device_ptr(const void* p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int fail(dd_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  else g_setup_err = msg;
+  return code;
+}
+
+template <typename F>
+int guarded(dd_ctx* c, F&& f) {
+  try {
+    return f();
+  } catch (const Error& e) {
+    return fail(c, e.code, e.msg);
+  } catch (const std::bad_alloc&) {
+    return fail(c, DD_ENOMEM, "host allocation failed");
+  } catch (...) {
+    return fail(c, DD_ECUDA, "unexpected exception");
+  }
+}
+
+}  // namespace
+
+namespace dd {
+
+void* dev_alloc(dd_ctx* c, size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Error(DD_ENOMEM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+  }
+  DD_CUDA(cudaMemsetAsync(p, 0, bytes, c->stream));
+  c->allocs.push_back(p);
+  c->bytes += (long long)bytes;
+  return p;
+}
+
+static const char* kClassNames[KC_COUNT] = {
+    "stencil_Asigma", "p_update", "xr_update", "local_solve_fp64", "pack_restrict", "local_gemm_tc",
+    "prolong_sum", "coarse_restrict", "coarse_solve", "outer_step", "misc"};
+
+void timer_begin(dd_ctx* c, int, cudaStream_t s, cudaEvent_t* e0) {
+  *e0 = nullptr;
+  if (!c->timing) return;
+  DD_CUDA(cudaEventCreate(e0));
+  DD_CUDA(cudaEventRecord(*e0, s));
+}
+
+void timer_end(dd_ctx* c, int kc, cudaStream_t s, cudaEvent_t e0) {
+  if (!c->timing || e0 == nullptr) return;
+  cudaEvent_t e1;
+  DD_CUDA(cudaEventCreate(&e1));
+  DD_CUDA(cudaEventRecord(e1, s));
+  c->timer.pending.push_back({kc, {e0, e1}});
+}
+
+void timer_collect(dd_ctx* c) {
+  for (auto& pe : c->timer.pending) {
+    float ms = 0.f;
+    DD_CUDA(cudaEventSynchronize(pe.second.second));
+    DD_CUDA(cudaEventElapsedTime(&ms, pe.second.first, pe.second.second));
+    c->timer.ms[pe.first] += ms;
+    c->timer.launches[pe.first] += 1;
+    cudaEventDestroy(pe.second.first);
+    cudaEventDestroy(pe.second.second);
+  }
+  c->timer.pending.clear();
+}
+
+}  // namespace dd
+
+#define TIMED(kc, stream, body)            \
+  do {                                     \
+    cudaEvent_t e0_;                       \
+    dd::timer_begin(c, kc, stream, &e0_);  \
+    body;                                  \
+    dd::timer_end(c, kc, stream, e0_);     \
+  } while (0)
+
+namespace {
+
+using namespace dd;
+
+void build_subdomains(dd_ctx* c) {
+  const Geo& g = c->g;
+  int id_of[16];
+  for (int k = 0; k < 16; ++k) id_of[k] = -1;
+  c->ntypes = 0;
+  c->subs_h.resize(g.nsub);
+  const int L2 = (g.p == 2) ? g.L : 1;
+  for (int s = 0; s < g.nsub; ++s) {
+    const int i1 = (g.p == 1) ? s : s / g.L, i2 = (g.p == 1) ? 0 : s % g.L;
+    const int t1 = ax_type(g, i1), t2 = (g.p == 2) ? ax_type(g, i2) : 0;
+    const int key = t1 * 4 + t2;
+    if (id_of[key] < 0) {
+      id_of[key] = c->ntypes;
+      c->type_ax[c->ntypes][0] = t1;
+      c->type_ax[c->ntypes][1] = t2;
+      ++c->ntypes;
+    }
+    Sub sb;
+    sb.type = id_of[key];
+    sb.lo1 = ax_lo(g, i1);
+    sb.w1 = ax_hi(g, i1) - sb.lo1 + 1;
+    if (g.p == 2) {
+      sb.lo2 = ax_lo(g, i2);
+      sb.w2 = ax_hi(g, i2) - sb.lo2 + 1;
+    } else {
+      sb.lo2 = 0;
+      sb.w2 = 1;
+    }
+    sb.nloc = sb.w1 * sb.w2 * g.nyi;
+    c->subs_h[s] = sb;
+    c->type_nloc[sb.type] = sb.nloc;
+    c->type_w1[sb.type] = sb.w1;
+    c->type_w2[sb.type] = sb.w2;
+  }
+  (void)L2;
+  c->type_count.assign(c->ntypes, 0);
+  for (const Sub& s : c->subs_h) c->type_count[s.type]++;
+  c->type_first.assign(c->ntypes, 0);
+  for (int t = 1; t < c->ntypes; ++t) c->type_first[t] = c->type_first[t - 1] + c->type_count[t - 1];
+  std::vector<int> next = c->type_first, slot(g.nsub);
+  for (int s = 0; s < g.nsub; ++s) slot[s] = next[c->subs_h[s].type]++;
+  c->nloc_max = 0;
+  int w2max = 1;
+  for (int t = 0; t < c->ntypes; ++t) {
+    c->nloc_max = std::max(c->nloc_max, c->type_nloc[t]);
+    w2max = std::max(w2max, c->type_w2[t]);
+  }
+  c->kpad = (c->nloc_max + 63) / 64 * 64;
+  c->band = (g.p == 1) ? g.nyi + 1 : w2max * g.nyi + g.nyi + 1;
+  c->subs = (Sub*)dev_alloc(c, sizeof(Sub) * g.nsub);
+  c->slot_of_sub = (int*)dev_alloc(c, sizeof(int) * g.nsub);
+  DD_CUDA(cudaMemcpyAsync(c->subs, c->subs_h.data(), sizeof(Sub) * g.nsub, cudaMemcpyHostToDevice, c->stream));
+  DD_CUDA(cudaMemcpyAsync(c->slot_of_sub, slot.data(), sizeof(int) * g.nsub, cudaMemcpyHostToDevice, c->stream));
+  DD_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+// user vector (ABI order, host or device) -> padded device vector
+void load_vec(dd_ctx* c, const double* u, double* padded) {
+  const Geo& g = c->g;
+  const double* src = u;
+  if (!is_device_ptr(u)) {
+    DD_CUDA(cudaMemcpyAsync(c->stage_a, u, sizeof(double) * g.ndof, cudaMemcpyHostToDevice, c->stream));
+    src = c->stage_a;
+  }
+  launch_pad(c, src, padded, c->stream);
+}
+
+void store_vec(dd_ctx* c, const double* padded, double* u) {
+  const Geo& g = c->g;
+  if (is_device_ptr(u)) {
+    launch_unpad(c, padded, u, c->stream);
+  } else {
+    launch_unpad(c, padded, c->stage_b, c->stream);
+    DD_CUDA(cudaMemcpyAsync(u, c->stage_b, sizeof(double) * g.ndof, cudaMemcpyDeviceToHost, c->stream));
+  }
+}
+
+// order the context's private stream after everything already queued on the caller's stream
+void enter(dd_ctx* c) {
+  DD_CUDA(cudaEventRecord(c->ev_enter, c->user_stream));
+  DD_CUDA(cudaStreamWaitEvent(c->stream, c->ev_enter, 0));
+}
+
+int stage_err(dd_ctx* c, int need) {
+  if (c == nullptr) return DD_EINVAL;
+  if (c->stage < need) return fail(c, DD_ESTATE, "call out of order");
+  return DD_OK;
+}
+
+bool use_gemm(const dd_ctx* c) { return c->grid.precision != DD_PREC_FP64; }
+
+// z = M^{-1} r on device padded vectors; mode 0 standalone, 1 PCG start, 2 PCG iteration
+void precond(dd_ctx* c, const double* r, int mode) {
+  cudaStream_t s = c->stream;
+  const bool coarse = c->grid.coarse != 0;
+  if (coarse) {
+    DD_CUDA(cudaEventRecord(c->ev_fork, s));
+    DD_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    TIMED(KC_CRESTRICT, c->side, launch_coarse_restrict(c, r, c->side));
+    TIMED(KC_CSOLVE, c->side, launch_coarse_solve(c, c->side));
+    DD_CUDA(cudaEventRecord(c->ev_join, c->side));
+  }
+  if (use_gemm(c)) {
+    TIMED(KC_PACK, s, launch_pack(c, r, s));
+    int rc;
+    TIMED(KC_GEMM, s, rc = launch_gemm(c, s));
+    if (rc != DD_OK) throw Error(rc, "local GEMM launch failed");
+  } else {
+    TIMED(KC_LOCAL_FP64, s, launch_band_solve_local(c, r, s));
+  }
+  if (coarse) DD_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
+  TIMED(KC_PROLONG, s, launch_prolong(c, mode, s));
+}
+
+void pcg_iteration(dd_ctx* c) {
+  cudaStream_t s = c->stream;
+  TIMED(KC_PUPDATE, s, launch_pupdate(c, s));
+  TIMED(KC_STENCIL, s, launch_matvec_pq(c, s));
+  TIMED(KC_XRUPDATE, s, launch_xr_update(c, s));
+  precond(c, c->r, 2);
+}
+
+void reset_graph(dd_ctx* c) {
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  c->graph_iters = 0;
+}
+
+void build_graph(dd_ctx* c) {
+  reset_graph(c);
+  cudaGraph_t gr;
+  DD_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  try {
+    for (int i = 0; i < c->check_every; ++i) pcg_iteration(c);
+  } catch (...) {
+    cudaStreamEndCapture(c->stream, &gr);
+    cudaGetLastError();
+    throw;
+  }
+  DD_CUDA(cudaStreamEndCapture(c->stream, &gr));
+  DD_CUDA(cudaGraphInstantiate(&c->graph, gr, 0));
+  DD_CUDA(cudaGraphDestroy(gr));
+  c->graph_iters = c->check_every;
+}
+
+// PCG on the context's padded vectors: b (device padded), x holds the initial guess.
+int pcg_run(dd_ctx* c, const double* b, double rtol, int maxit, int* iters, double* relres) {
+  cudaStream_t s = c->stream;
+  PcgState init;
+  std::memset(&init, 0, sizeof(init));
+  init.tol2 = rtol * rtol;
+  init.maxit = maxit;
+  init.flexible = (c->flexible_opt < 0) ? (use_gemm(c) ? 1 : 0) : c->flexible_opt;
+  DD_CUDA(cudaMemcpyAsync(c->st, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+  DD_CUDA(cudaMemsetAsync(c->p, 0, sizeof(double) * c->g.plen, s));
+  TIMED(KC_STENCIL, s, launch_pcg_init(c, b, s));
+  precond(c, c->r, 1);
+  const bool graph = c->use_graph && !c->timing;
+  if (graph && (c->graph == nullptr || c->graph_iters != c->check_every)) build_graph(c);
+  for (int done_iters = 0; done_iters < maxit + c->check_every; done_iters += c->check_every) {
+    if (graph) {
+      DD_CUDA(cudaGraphLaunch(c->graph, s));
+    } else {
+      for (int i = 0; i < c->check_every; ++i) pcg_iteration(c);
+    }
+    DD_CUDA(cudaMemcpyAsync(c->st_h, c->st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+    DD_CUDA(cudaStreamSynchronize(s));
+    if (c->timing) timer_collect(c);
+    if (c->st_h->done) break;
+  }
+  const PcgState& h = *c->st_h;
+  if (iters) *iters = h.iter;
+  if (relres) *relres = (h.rr0 > 0.0) ? std::sqrt(h.rr / h.rr0) : 0.0;
+  if (h.status != 0) {
+    if (h.status == DD_EMAXIT) return fail(c, DD_EMAXIT, "PCG reached maxit");
+    return fail(c, h.status, h.status == DD_ENOTSPD ? "p^T A_sigma p <= 0" : "non-finite PCG iterate");
+  }
+  if (!h.done) return fail(c, DD_EMAXIT, "PCG did not finish");
+  return DD_OK;
+}
+
+void read_outer(dd_ctx* c) {
+  DD_CUDA(cudaMemcpyAsync(c->ost_h, c->ost, sizeof(OuterState), cudaMemcpyDeviceToHost, c->stream));
+  DD_CUDA(cudaStreamSynchronize(c->stream));
+  if (c->timing) timer_collect(c);
+}
+
+}  // namespace
+
+// ==========================================================================================
+extern "C" {
+
+const char* dd_status_string(int s) {
+  switch (s) {
+    case DD_OK: return "DD_OK";
+    case DD_EINVAL: return "DD_EINVAL";
+    case DD_ESTATE: return "DD_ESTATE";
+    case DD_ENOMEM: return "DD_ENOMEM";
+    case DD_ECUDA: return "DD_ECUDA";
+    case DD_ENAN: return "DD_ENAN";
+    case DD_ENOTSPD: return "DD_ENOTSPD";
+    case DD_EMAXIT: return "DD_EMAXIT";
+    case DD_ETIMEOUT: return "DD_ETIMEOUT";
+    case DD_EUNSUPPORTED: return "DD_EUNSUPPORTED";
+    default: return "DD_UNKNOWN";
+  }
+}
+
+const char* dd_last_error(const dd_ctx* c) { return c ? c->err.c_str() : g_setup_err.c_str(); }
+
+void dd_destroy(dd_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  dd::gemm_free(c);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->st_h) cudaFreeHost(c->st_h);
+  if (c->ost_h) cudaFreeHost(c->ost_h);
+  if (c->side) cudaStreamDestroy(c->side);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_enter) cudaEventDestroy(c->ev_enter);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  for (auto& pe : c->timer.pending) {
+    cudaEventDestroy(pe.second.first);
+    cudaEventDestroy(pe.second.second);
+  }
+  delete c;
+}
+
+int dd_setup(const dd_grid* gr, const double* V, size_t nV, void* stream, dd_ctx** out) {
+  if (out) *out = nullptr;
+  if (!gr || !V || !out) return fail(nullptr, DD_EINVAL, "null argument");
+  const dd_grid G = *gr;
+  if (G.p < 1 || G.p > 2) return fail(nullptr, DD_EINVAL, "p must be 1 or 2");
+  if (G.q != 1) return fail(nullptr, DD_EINVAL, "q must be 1");
+  if (G.L < 1) return fail(nullptr, DD_EINVAL, "L must be >= 1");
+  if (G.n < 3) return fail(nullptr, DD_EINVAL, "n must be >= 3");
+  const double nyd = G.ell * G.n;
+  const int ny = (int)std::lround(nyd);
+  if (!(std::fabs(nyd - ny) < 1e-9) || ny < 2) return fail(nullptr, DD_EINVAL, "ell * n must be an integer >= 2");
+  if (G.overlap < 1 || 2 * G.overlap >= G.n) return fail(nullptr, DD_EINVAL, "need 1 <= overlap and 2 overlap < n");
+  if (G.quad_pts < 1 || G.quad_pts > dd::kMaxQ) return fail(nullptr, DD_EINVAL, "quad_pts must be 1..4");
+  if (G.pu_kind != DD_PU_EQUAL && G.pu_kind != DD_PU_DISTANCE) return fail(nullptr, DD_EINVAL, "bad pu_kind");
+  if (G.precision < DD_PREC_FP64 || G.precision > DD_PREC_BF16) return fail(nullptr, DD_EINVAL, "bad precision");
+  if (G.coarse != 0 && G.coarse != 1) return fail(nullptr, DD_EINVAL, "coarse must be 0 or 1");
+  size_t expect = (size_t)ny;
+  for (int k = 0; k < G.p; ++k) expect *= (size_t)G.n;
+  for (int k = 0; k <= G.p; ++k) expect *= (size_t)G.quad_pts;
+  if (nV != expect) return fail(nullptr, DD_EINVAL, "nV does not match n^p ny Q^(p+1)");
+  long long cols = 1;
+  for (int k = 0; k < G.p; ++k) cols *= (long long)G.L * G.n + 1;
+  if (cols * ((ny + 3) / 4 * 4) > (1LL << 31)) return fail(nullptr, DD_EINVAL, "grid too large");
+
+  dd_ctx* c = nullptr;
+  try {
+    c = new dd_ctx();
+  } catch (...) {
+    return fail(nullptr, DD_ENOMEM, "host allocation failed");
+  }
+  c->grid = G;
+  c->user_stream = (cudaStream_t)stream;
+  int rc = guarded(c, [&]() -> int {
+    DD_CUDA(cudaGetDevice(&c->device));
+    DD_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    DD_CUDA(cudaEventCreateWithFlags(&c->ev_enter, cudaEventDisableTiming));
+    enter(c);
+    Geo& g = c->g;
+    g.p = G.p; g.L = G.L; g.n = G.n; g.ny = ny; g.nyi = ny - 1;
+    g.delta = G.overlap; g.Q = G.quad_pts;
+    g.Ypad = (ny + 3) / 4 * 4;
+    g.ncx = G.L * G.n + 1;
+    g.nxi = G.L * G.n - 1;
+    g.ncol = (G.p == 1) ? g.ncx : (long long)g.ncx * g.ncx;
+    g.plen = g.ncol * g.Ypad;
+    g.ndof = (G.p == 1 ? (long long)g.nxi : (long long)g.nxi * g.nxi) * g.nyi;
+    g.nsub = (G.p == 1) ? G.L : G.L * G.L;
+    g.ntap = (G.p == 1) ? 9 : 27;
+    g.ncls = ((G.p == 1) ? G.n : G.n * G.n) * g.Ypad;
+    g.h = 1.0 / G.n;
+    DD_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    DD_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    DD_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    DD_CUDA(cudaMallocHost(&c->st_h, sizeof(PcgState)));
+    DD_CUDA(cudaMallocHost(&c->ost_h, sizeof(OuterState)));
+    c->dev_err = (int*)dev_alloc(c, sizeof(int) * 16);
+    c->red = (double*)dev_alloc(c, sizeof(double) * kMaxRedBlocks * 4);
+    c->cnt = (unsigned*)dev_alloc(c, sizeof(unsigned) * CNT_NUM);
+    c->st = (PcgState*)dev_alloc(c, sizeof(PcgState));
+    c->ost = (OuterState*)dev_alloc(c, sizeof(OuterState));
+    c->Vqp = (double*)dev_alloc(c, sizeof(double) * nV);
+    if (is_device_ptr(V)) DD_CUDA(cudaMemcpyAsync(c->Vqp, V, sizeof(double) * nV, cudaMemcpyDeviceToDevice, c->stream));
+    else DD_CUDA(cudaMemcpyAsync(c->Vqp, V, sizeof(double) * nV, cudaMemcpyHostToDevice, c->stream));
+    launch_check_finite(c->Vqp, (long long)nV, c->dev_err, c->stream);
+    int bad = 0;
+    DD_CUDA(cudaMemcpyAsync(&bad, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    DD_CUDA(cudaStreamSynchronize(c->stream));
+    if (bad) throw Error(DD_ENAN, "V contains non-finite values");
+    const size_t ntab = (size_t)g.ntap * g.ncls;
+    c->tabA = (double*)dev_alloc(c, sizeof(double) * ntab);
+    c->tabM = (double*)dev_alloc(c, sizeof(double) * ntab);
+    c->tabS = (double*)dev_alloc(c, sizeof(double) * ntab);
+    launch_build_tables(c);
+    build_subdomains(c);
+    const size_t vb = sizeof(double) * g.plen;
+    c->x = (double*)dev_alloc(c, vb);
+    c->r = (double*)dev_alloc(c, vb);
+    c->z = (double*)dev_alloc(c, vb);
+    c->p = (double*)dev_alloc(c, vb);
+    c->q = (double*)dev_alloc(c, vb);
+    c->w1 = (double*)dev_alloc(c, vb);
+    c->w2 = (double*)dev_alloc(c, vb);
+    c->w3 = (double*)dev_alloc(c, vb);
+    c->xe = (double*)dev_alloc(c, vb);
+    c->stage_a = (double*)dev_alloc(c, sizeof(double) * g.ndof);
+    c->stage_b = (double*)dev_alloc(c, sizeof(double) * g.ndof);
+    c->ncell = (long long)((G.p == 1) ? G.n : G.n * G.n) * g.nyi;
+    c->psi_cell = (double*)dev_alloc(c, sizeof(double) * c->ncell);
+    c->wT = (double*)dev_alloc(c, sizeof(double) * (size_t)c->ntypes * c->kpad);
+    c->c0 = (double*)dev_alloc(c, sizeof(double) * g.nsub);
+    c->u0 = (double*)dev_alloc(c, sizeof(double) * g.nsub);
+    c->A0band = (double*)dev_alloc(c, sizeof(double) * (size_t)g.nsub * (G.p == 1 ? 3 : 9));
+    DD_CUDA(cudaStreamSynchronize(c->stream));
+    c->stage = 1;
+    return DD_OK;
+  });
+  if (rc != DD_OK) {
+    g_setup_err = c->err;
+    dd_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return DD_OK;
+}
+
+int dd_cell_eigenpair(dd_ctx* c, double* sigma_out, double* psi_out) {
+  int rc = stage_err(c, 1);
+  if (rc) return rc;
+  return guarded(c, [&]() -> int {
+    enter(c);
+    int st = cell_eigenpair(c);
+    launch_tabS(c, c->sigma);
+    launch_coarse_weights(c);
+    reset_graph(c);
+    if (psi_out) {
+      if (is_device_ptr(psi_out))
+        DD_CUDA(cudaMemcpyAsync(psi_out, c->psi_cell, sizeof(double) * c->ncell, cudaMemcpyDeviceToDevice, c->stream));
+      else
+        DD_CUDA(cudaMemcpyAsync(psi_out, c->psi_cell, sizeof(double) * c->ncell, cudaMemcpyDeviceToHost, c->stream));
+    }
+    DD_CUDA(cudaStreamSynchronize(c->stream));
+    if (sigma_out) *sigma_out = c->sigma;
+    if (c->stage < 2) c->stage = 2;
+    if (st == DD_EMAXIT) return fail(c, DD_EMAXIT, "cell inverse iteration hit its limit");
+    return DD_OK;
+  });
+}
+
+int dd_coarse_build(dd_ctx* c) {
+  int rc = stage_err(c, 2);
+  if (rc) return rc;
+  return guarded(c, [&]() -> int {
+    enter(c);
+    const Geo& g = c->g;
+    reset_graph(c);
+    int* flag = c->dev_err + 3;
+    DD_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), c->stream));
+    const size_t bsz = (size_t)c->ntypes * c->nloc_max * (c->band + 1);
+    if (!c->bandCB) {
+      c->bandCB = (double*)dev_alloc(c, sizeof(double) * bsz);
+      c->bandRB = (double*)dev_alloc(c, sizeof(double) * bsz);
+      c->bandInv = (double*)dev_alloc(c, sizeof(double) * (size_t)c->ntypes * c->nloc_max);
+    }
+    launch_local_assemble(c);
+    launch_band_factor(c, c->bandCB, c->bandRB, c->bandInv, c->ntypes, c->nloc_max, c->band, flag);
+    int fl = 0;
+    DD_CUDA(cudaMemcpyAsync(&fl, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    DD_CUDA(cudaStreamSynchronize(c->stream));
+    if (fl) throw Error(DD_ENOTSPD, "local matrix not positive definite");
+    if (use_gemm(c)) {
+      int r2 = gemm_setup(c);
+      if (r2 != DD_OK) return r2;
+    } else if (!c->Y64) {
+      c->Y64 = (double*)dev_alloc(c, sizeof(double) * (size_t)g.nsub * c->kpad);
+    }
+    if (c->grid.coarse) {
+      coarse_assemble(c);
+      if (!c->cr && !c->A0inv) coarse_factor(c);
+      else {
+        // rebuild after a new cell eigenpair
+        c->cr = nullptr;
+        c->A0inv = nullptr;
+        coarse_factor(c);
+      }
+    }
+    DD_CUDA(cudaStreamSynchronize(c->stream));
+    c->stage = 3;
+    return DD_OK;
+  });
+}
+
+int dd_apply_operator(dd_ctx* c, int op, const double* x, double* y) {
+  if (op < 0 || op > 2 || !x || !y) return fail(c, DD_EINVAL, "bad operator or pointer");
+  int rc = stage_err(c, op == DD_OP_ASIGMA ? 2 : 1);
+  if (rc) return rc;
+  return guarded(c, [&]() -> int {
+    enter(c);
+    const double* tab = op == DD_OP_ASIGMA ? c->tabS : (op == DD_OP_MASS ? c->tabM : c->tabA);
+    load_vec(c, x, c->w1);
+    launch_stencil(c, tab, c->w1, c->w2, c->stream);
+    store_vec(c, c->w2, y);
+    DD_CUDA(cudaStreamSynchronize(c->stream));
+    return DD_OK;
+  });
+}
+
+int dd_apply_preconditioner(dd_ctx* c, const double* r, double* z) {
+  if (!r || !z) return fail(c, DD_EINVAL, "null pointer");
+  int rc = stage_err(c, 3);
+  if (rc) return rc;
+  return guarded(c, [&]() -> int {
+    enter(c);
+    PcgState init;
+    std::memset(&init, 0, sizeof(init));
+    DD_CUDA(cudaMemcpyAsync(c->st, &init, sizeof(init), cudaMemcpyHostToDevice, c->stream));
+    load_vec(c, r, c->r);
+    precond(c, c->r, 0);
+    store_vec(c, c->z, z);
+    DD_CUDA(cudaStreamSynchronize(c->stream));
+    if (c->timing) timer_collect(c);
+    return DD_OK;
+  });
+}
+
+int dd_coarse_matrix(dd_ctx* c, double* A0) {
+  if (!A0) return fail(c, DD_EINVAL, "null pointer");
+  int rc = stage_err(c, 3);
+  if (rc) return rc;
+  if (!c->grid.coarse) return fail(c, DD_ESTATE, "no coarse space (coarse = 0)");
+  return guarded(c, [&]() -> int {
+    enter(c);
+    const Geo& g = c->g;
+    const int N = g.nsub, nnb = (g.p == 1) ? 3 : 9;
+    std::vector<double> nb((size_t)N * nnb);
+    DD_CUDA(cudaMemcpyAsync(nb.data(), c->A0band, sizeof(double) * nb.size(), cudaMemcpyDeviceToHost, c->stream));
+    DD_CUDA(cudaStreamSynchronize(c->stream));
+    std::memset(A0, 0, sizeof(double) * (size_t)N * N);
+    for (int s = 0; s < N; ++s) {
+      const int s1 = (g.p == 1) ? s : s / g.L, s2 = (g.p == 1) ? 0 : s % g.L;
+      for (int k = 0; k < nnb; ++k) {
+        int t;
+        if (g.p == 1) {
+          t = s1 + k - 1;
+          if (t < 0 || t >= g.L) continue;
+        } else {
+          const int t1 = s1 + k / 3 - 1, t2 = s2 + k % 3 - 1;
+          if (t1 < 0 || t1 >= g.L || t2 < 0 || t2 >= g.L) continue;
+          t = t1 * g.L + t2;
+        }
+        A0[(size_t)s * N + t] = nb[(size_t)s * nnb + k];
+      }
+    }
+    return DD_OK;
+  });
+}
+
+int dd_pcg_solve(dd_ctx* c, const double* b, double* x, double rtol, int maxit, int* iters_out,
+                 double* relres_out) {
+  if (!b || !x || !(rtol > 0.0) || maxit < 1) return fail(c, DD_EINVAL, "bad argument");
+  int rc = stage_err(c, 3);
+  if (rc) return rc;
+  return guarded(c, [&]() -> int {
+    enter(c);
+    load_vec(c, b, c->w3);
+    load_vec(c, x, c->x);
+    int r2 = pcg_run(c, c->w3, rtol, maxit, iters_out, relres_out);
+    store_vec(c, c->x, x);
+    DD_CUDA(cudaStreamSynchronize(c->stream));
+    return r2;
+  });
+}
+
+int dd_inverse_iterate(dd_ctx* c, double* x, double tol_res, double tol_lam, int maxit_outer, double rtol_inner,
+                       double* lambda_out, int* outer_out, int* inner_total_out, int* inner_max_out) {
+  if (!x || maxit_outer < 1 || !(rtol_inner > 0.0)) return fail(c, DD_EINVAL, "bad argument");
+  int rc = stage_err(c, 3);
+  if (rc) return rc;
+  return guarded(c, [&]() -> int {
+    enter(c);
+    cudaStream_t s = c->stream;
+    const double sigma = c->sigma;
+    // x_0 -> M-normalised iterate xe, w2 = M xe
+    load_vec(c, x, c->w1);
+    TIMED(KC_OUTER, s, launch_stencil(c, c->tabM, c->w1, c->w2, s));
+    TIMED(KC_OUTER, s, launch_outer_normalize(c, c->w1, c->w2, c->xe, s));
+    TIMED(KC_OUTER, s, launch_outer_residual(c, c->xe, c->w2, c->w3, s));
+    read_outer(c);
+    if (c->ost_h->status != 0) throw Error(c->ost_h->status, "initial vector has zero M-norm");
+    double rho_prev = sigma + c->ost_h->xAx;
+    double rho = rho_prev;
+    int k = 0, inner_tot = 0, inner_max = 0, status = DD_EMAXIT;
+    for (k = 1; k <= maxit_outer; ++k) {
+      // b = M x_k (in w2); w = A_sigma^{-1} b by PCG from zero
+      DD_CUDA(cudaMemsetAsync(c->x, 0, sizeof(double) * c->g.plen, s));
+      int it = 0;
+      double rel = 0.0;
+      int prc = pcg_run(c, c->w2, rtol_inner, 10000, &it, &rel);
+      inner_tot += it;
+      inner_max = std::max(inner_max, it);
+      if (prc != DD_OK && prc != DD_EMAXIT) return prc;
+      // x_{k+1} = w / ||w||_M
+      TIMED(KC_OUTER, s, launch_stencil(c, c->tabM, c->x, c->w2, s));
+      TIMED(KC_OUTER, s, launch_outer_normalize(c, c->x, c->w2, c->xe, s));
+      TIMED(KC_OUTER, s, launch_outer_residual(c, c->xe, c->w2, c->w3, s));
+      read_outer(c);
+      if (c->ost_h->status != 0) throw Error(c->ost_h->status, "outer normalisation failed");
+      rho = sigma + c->ost_h->xAx;
+      const double eta = std::sqrt(c->ost_h->rr / c->ost_h->mm) / std::fabs(rho);
+      if (!std::isfinite(rho)) throw Error(DD_ENAN, "non-finite Rayleigh quotient");
+      if (eta <= tol_res && std::fabs(rho - rho_prev) <= tol_lam * std::fabs(rho)) {
+        status = DD_OK;
+        break;
+      }
+      rho_prev = rho;
+    }
+    store_vec(c, c->xe, x);
+    DD_CUDA(cudaStreamSynchronize(s));
+    if (lambda_out) *lambda_out = rho;
+    if (outer_out) *outer_out = std::min(k, maxit_outer);
+    if (inner_total_out) *inner_total_out = inner_tot;
+    if (inner_max_out) *inner_max_out = inner_max;
+    if (status != DD_OK) return fail(c, status, "outer iteration limit reached");
+    return DD_OK;
+  });
+}
+
+int dd_eigenpair(const dd_grid* g, const double* V, size_t nV, void* stream, double* lambda_out, double* phi_out,
+                 double* sigma_out) {
+  dd_ctx* c = nullptr;
+  int rc = dd_setup(g, V, nV, stream, &c);
+  if (rc) return rc;
+  rc = dd_cell_eigenpair(c, sigma_out, nullptr);
+  if (rc == DD_OK) rc = dd_coarse_build(c);
+  if (rc == DD_OK) {
+    rc = guarded(c, [&]() -> int {
+      // x_0 = 1 in the context's staging buffer (device), phi written to phi_out
+      const long long n = c->g.ndof;
+      std::vector<double> ones((size_t)n, 1.0);
+      DD_CUDA(cudaMemcpyAsync(c->stage_b, ones.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+      DD_CUDA(cudaStreamSynchronize(c->stream));
+      return DD_OK;
+    });
+  }
+  if (rc == DD_OK) {
+    double* xv = c->stage_b;
+    rc = dd_inverse_iterate(c, xv, 1e-8, 1e-10, 100, 1e-8, lambda_out, nullptr, nullptr, nullptr);
+    if ((rc == DD_OK || rc == DD_EMAXIT) && phi_out) {
+      int rc2 = guarded(c, [&]() -> int {
+        if (is_device_ptr(phi_out))
+          DD_CUDA(cudaMemcpyAsync(phi_out, xv, sizeof(double) * c->g.ndof, cudaMemcpyDeviceToDevice, c->stream));
+        else
+          DD_CUDA(cudaMemcpyAsync(phi_out, xv, sizeof(double) * c->g.ndof, cudaMemcpyDeviceToHost, c->stream));
+        DD_CUDA(cudaStreamSynchronize(c->stream));
+        return DD_OK;
+      });
+      if (rc == DD_OK) rc = rc2;
+    }
+  }
+  if (rc != DD_OK) g_setup_err = c->err;
+  dd_destroy(c);
+  return rc;
+}
+
+int dd_query(const dd_ctx* c, dd_info* info) {
+  if (!c || !info) return DD_EINVAL;
+  info->ndof = c->g.ndof;
+  info->ncell = c->ncell;
+  info->nsub = c->g.nsub;
+  info->ntypes = c->ntypes;
+  info->nloc_max = c->nloc_max;
+  info->kpad = c->kpad;
+  info->band_local = c->band;
+  info->sigma = c->sigma;
+  info->cell_iters = c->cell_iters;
+  info->stage = c->stage;
+  info->device_bytes = c->bytes;
+  return DD_OK;
+}
+
+int dd_set_option(dd_ctx* c, int option, int value) {
+  if (!c) return DD_EINVAL;
+  switch (option) {
+    case DD_OPT_CHECK_EVERY:
+      if (value < 1 || value > 1000) return fail(c, DD_EINVAL, "check_every out of range");
+      c->check_every = value;
+      break;
+    case DD_OPT_USE_GRAPH: c->use_graph = value ? 1 : 0; break;
+    case DD_OPT_FLEXIBLE:
+      if (value < -1 || value > 1) return fail(c, DD_EINVAL, "flexible must be -1, 0 or 1");
+      c->flexible_opt = value;
+      break;
+    case DD_OPT_TIMING: c->timing = value ? 1 : 0; break;
+    default: return fail(c, DD_EINVAL, "unknown option");
+  }
+  reset_graph(c);
+  return DD_OK;
+}
+
+int dd_kernel_timings(dd_ctx* c, int* count, const char** names, long long* launches, double* ms) {
+  if (!c || !count) return DD_EINVAL;
+  *count = dd::KC_COUNT;
+  for (int k = 0; k < dd::KC_COUNT; ++k) {
+    if (names) names[k] = dd::kClassNames[k];
+    if (launches) launches[k] = c->timer.launches[k];
+    if (ms) ms[k] = c->timer.ms[k];
+  }
+  return DD_OK;
+}
+
+int dd_reset_timings(dd_ctx* c) {
+  if (!c) return DD_EINVAL;
+  for (int k = 0; k < dd::KC_COUNT; ++k) {
+    c->timer.launches[k] = 0;
+    c->timer.ms[k] = 0.0;
+  }
+  return DD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,155 @@
+// Device helpers shared by the kernels: reductions, index maps, stencil evaluation.
+#pragma once
+
+#include "dd_internal.h"
+
+namespace dd {
+
+constexpr int kThreads = 256;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Last-block counters (one per reduction site so that concurrent kernels never share one).
+enum CounterId {
+  CNT_PQ = 0, CNT_RR, CNT_RZ, CNT_INIT, CNT_DOT0, CNT_DOT1, CNT_OUTER0, CNT_OUTER1, CNT_OUTER2,
+  CNT_NUM = 16
+};
+constexpr int kMaxRedBlocks = 4096;   // partial slots per value
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+  return v;
+}
+
+// Sums NV values over the block; the result is valid in thread 0 only.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV]) {
+  __shared__ double sm[32][NV];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sm[wid][k] = v[k];
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double t = lane < nw ? sm[lane][k] : 0.0;
+      v[k] = warp_sum(t);
+    }
+  }
+  __syncthreads();
+}
+
+// Deterministic grid-wide sum: every block stores its partial; the last block to finish
+// adds the partials in block order and returns true (result in tot[] of thread 0).
+template <int NV>
+__device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* partials, unsigned* counter,
+                                              double (&tot)[NV]) {
+  __shared__ int s_last;
+  block_sum<NV>(v);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) partials[(size_t)k * kMaxRedBlocks + blockIdx.x] = v[k];
+    __threadfence();
+    unsigned t = atomicAdd(counter, 1u);
+    s_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  double s[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    s[k] = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+      s[k] += __ldcg(partials + (size_t)k * kMaxRedBlocks + b);
+  }
+  block_sum<NV>(s);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) tot[k] = s[k];
+    *counter = 0u;
+  }
+  return true;
+}
+
+// Interior-element enumeration of a padded vector: t in [0, nxi^p * Ypad).
+struct Node {
+  long long idx;   // padded index
+  int slot;        // y slot (j - 1); >= nyi means pad
+  int a1, a2;      // node columns (a2 = 0 for p = 1)
+};
+
+template <int P>
+__device__ __forceinline__ Node node_of(const Geo& g, long long t) {
+  Node nd;
+  long long u = t / g.Ypad;
+  nd.slot = (int)(t - u * g.Ypad);
+  if (P == 1) {
+    nd.a1 = 1 + (int)u;
+    nd.a2 = 0;
+    nd.idx = t + g.Ypad;
+  } else {
+    int q1 = (int)(u / g.nxi);
+    nd.a1 = 1 + q1;
+    nd.a2 = 1 + (int)(u - (long long)q1 * g.nxi);
+    nd.idx = ((long long)nd.a1 * g.ncx + nd.a2) * g.Ypad + nd.slot;
+  }
+  return nd;
+}
+
+template <int P>
+__device__ __forceinline__ int cls_of(const Geo& g, const Node& nd) {
+  if (P == 1) return (nd.a1 % g.n) * g.Ypad + nd.slot;
+  return ((nd.a1 % g.n) * g.n + (nd.a2 % g.n)) * g.Ypad + nd.slot;
+}
+
+// y(node) = sum over the 3^d taps of tab[tap][cls] x(node + offset(tap)).
+template <int P>
+__device__ __forceinline__ double stencil_at(const Geo& g, const double* __restrict__ tab,
+                                             const double* __restrict__ x, long long idx, int cls) {
+  double acc = 0.0;
+  if (P == 1) {
+    const long long cs = g.Ypad;
+#pragma unroll
+    for (int dx = -1; dx <= 1; ++dx)
+#pragma unroll
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int tap = (dx + 1) * 3 + (dy + 1);
+        acc = fma(__ldg(tab + (size_t)tap * g.ncls + cls), x[idx + dx * cs + dy], acc);
+      }
+  } else {
+    const long long c1 = (long long)g.ncx * g.Ypad, c2 = g.Ypad;
+#pragma unroll
+    for (int d1 = -1; d1 <= 1; ++d1)
+#pragma unroll
+      for (int d2 = -1; d2 <= 1; ++d2)
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+          const int tap = ((d1 + 1) * 3 + (d2 + 1)) * 3 + (dy + 1);
+          acc = fma(__ldg(tab + (size_t)tap * g.ncls + cls), x[idx + d1 * c1 + d2 * c2 + dy], acc);
+        }
+  }
+  return acc;
+}
+
+// Owners of an interior node column along one axis: subdomains i with lo(i) <= a <= hi(i).
+__device__ __forceinline__ int axis_owners(const Geo& g, int a, int (&own)[2], int (&loc)[2]) {
+  int k = 0;
+  int i0 = a / g.n - 1;
+  for (int i = i0; i <= i0 + 2; ++i) {
+    if (i < 0 || i >= g.L) continue;
+    int lo = ax_lo(g, i), hi = ax_hi(g, i);
+    if (a >= lo && a <= hi && k < 2) {
+      own[k] = i;
+      loc[k] = a - lo;
+      ++k;
+    }
+  }
+  return k;
+}
+
+}  // namespace dd

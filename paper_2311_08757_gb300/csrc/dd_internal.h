@@ -1,0 +1,265 @@
+// Internal declarations of the ddeig library: geometry, context, kernel launchers.
+//
+// Device data layout ("padded layout"): a box vector is stored over ALL node columns,
+// boundary columns included, with Ypad >= ny slots per column:
+//     index(col, slot) = col * Ypad + slot,  col = a (p = 1) or a1 (Ln + 1) + a2 (p = 2),
+//     slot = j - 1 for the interior y-nodes j = 1..ny-1; slots ny-1..Ypad-1 are zero.
+// Boundary columns (a = 0, a = Ln) and pad slots are kept at zero by every kernel, so
+// the homogeneous Dirichlet condition (H^1_0, Sec. 1) needs no branch in the stencil:
+// the neighbours of a node next to the boundary read zeros.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <string>
+#include <vector>
+
+#include "../../include/ddeig.h"
+
+namespace dd {
+
+constexpr int kMaxQ = 4;
+constexpr int kMaxTypes = 16;
+
+// Geometry shared by host and device (passed by value to kernels).
+struct Geo {
+  int p;        // 1 or 2
+  int L, n, ny, nyi;   // nyi = ny - 1 interior y nodes
+  int delta, Q;
+  int Ypad;     // slots per column (>= ny, multiple of 4)
+  int ncx;      // node columns per x axis incl. boundary = L n + 1
+  int nxi;      // interior nodes per x axis = L n - 1
+  long long ncol;   // ncx^p
+  long long plen;   // ncol * Ypad  (padded vector length)
+  long long ndof;   // nxi^p * nyi
+  int nsub;     // L^p
+  int ntap;     // 9 or 27
+  int ncls;     // n^p * Ypad stencil classes
+  double h;
+};
+
+// Per-axis subdomain geometry: subdomain i (0-based) covers interior node columns
+// lo(i)..hi(i) along an x axis (Sec. 3.1: open overlapping boxes clipped at the box).
+__host__ __device__ inline int ax_lo(const Geo& g, int i) {
+  int v = i * g.n - g.delta + 1;
+  return v < 1 ? 1 : v;
+}
+__host__ __device__ inline int ax_hi(const Geo& g, int i) {
+  int v = (i + 1) * g.n + g.delta - 1;
+  int m = g.L * g.n - 1;
+  return v > m ? m : v;
+}
+// Per-axis type: 0 left-clipped, 1 interior, 2 right-clipped, 3 both (L = 1).
+__host__ __device__ inline int ax_type(const Geo& g, int i) {
+  if (g.L == 1) return 3;
+  if (i == 0) return 0;
+  if (i == g.L - 1) return 2;
+  return 1;
+}
+
+// Subdomain descriptor on the device.
+struct Sub {
+  int type;     // compact type id
+  int lo1, lo2; // first interior node column per axis (lo2 unused for p = 1)
+  int w1, w2;   // widths in columns (w2 = 1 for p = 1)
+  int nloc;     // w1 * w2 * nyi
+};
+
+// Scalars of the PCG iteration, resident on the device.
+struct PcgState {
+  double rho;      // (r, z) of the current z
+  double pq;       // (p, A p)
+  double alpha, beta;
+  double rr;       // (r, r)
+  double rr0;      // (r_0, r_0)
+  double tol2;     // rtol^2 rr0
+  double zq;       // (z_new, q) for the flexible variant
+  int iter, maxit, done, status;
+  int flexible;
+  int pad_[3];
+};
+
+// Scalars of the outer iteration.
+struct OuterState {
+  double wMw, wsum, scale;
+  double xAx;      // x^T A_sigma x
+  double rr, mm;   // ||A_sigma x - mu M x||^2, ||M x||^2
+  double lam_shift;
+  int status;
+  int pad_;
+};
+
+enum KernelClass {
+  KC_STENCIL = 0, KC_PUPDATE, KC_XRUPDATE, KC_LOCAL_FP64, KC_PACK, KC_GEMM, KC_PROLONG,
+  KC_CRESTRICT, KC_CSOLVE, KC_OUTER, KC_MISC, KC_COUNT
+};
+
+struct Timer {
+  long long launches[KC_COUNT] = {};
+  double ms[KC_COUNT] = {};
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+};
+
+}  // namespace dd
+
+struct dd_ctx {
+  dd_grid grid;
+  dd::Geo g;
+  cudaStream_t user_stream = nullptr;  // the caller's stream (may be the legacy NULL stream)
+  cudaStream_t stream = nullptr;       // private non-blocking stream ordered after user_stream
+  cudaStream_t side = nullptr;         // concurrent coarse branch
+  cudaEvent_t ev_enter = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int device = 0;
+  int stage = 0;
+  std::string err;
+  long long bytes = 0;
+  std::vector<void*> allocs;
+
+  // options
+  int check_every = 8;
+  int use_graph = 1;
+  int flexible_opt = -1;
+  int timing = 0;
+  dd::Timer timer;
+
+  // types and subdomains
+  int ntypes = 0;
+  int type_ax[dd::kMaxTypes][2];   // per-axis types of each compact type
+  int type_nloc[dd::kMaxTypes];
+  int type_w1[dd::kMaxTypes], type_w2[dd::kMaxTypes];
+  std::vector<dd::Sub> subs_h;
+  std::vector<int> type_count;      // subdomains per type
+  std::vector<int> type_first;      // first slot (subdomains sorted by type)
+  dd::Sub* subs = nullptr;          // device, indexed by subdomain id
+  int* slot_of_sub = nullptr;       // device: subdomain id -> packed row (type-sorted)
+  int nloc_max = 0, kpad = 0, band = 0;
+
+  // V and stencil tables [tap][cls]
+  double* Vqp = nullptr;
+  double* tabA = nullptr;   // K + M_V
+  double* tabM = nullptr;   // M
+  double* tabS = nullptr;   // K + M_V - sigma M
+
+  // cell problem
+  long long ncell = 0;
+  int cell_band = 0;
+  double sigma = 0.0;
+  int cell_iters = 0;
+  double* psi_cell = nullptr;      // natural cell order
+  double* wT = nullptr;            // coarse weights per type [type][kpad]: D_i R_i psi
+
+  // vectors (padded length plen)
+  double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+  double *w1 = nullptr, *w2 = nullptr, *w3 = nullptr;   // outer-iteration work vectors
+  double* xe = nullptr;                                  // eigenvector iterate
+  double *stage_a = nullptr, *stage_b = nullptr;         // unpadded staging (ndof)
+
+  // local solves
+  double* bandCB = nullptr;   // [type][nloc_max][band+1] column band of L
+  double* bandRB = nullptr;   // [type][nloc_max][band+1] row band of L
+  double* bandInv = nullptr;  // [type][nloc_max] 1/L_ii
+  double* Y64 = nullptr;      // [nsub][kpad] local solutions (FP64 path)
+  float* Y32 = nullptr;       // [nsub][kpad] local solutions (GEMM path)
+  void* Ainv = nullptr;       // [type][kpad][kpad] rounded local inverses
+  void* Rpack = nullptr;      // [nsub (type-sorted)][kpad] rounded restrictions
+  void* tmapA = nullptr;      // CUtensorMap (host copy, 128 B)
+  void* tmapB = nullptr;
+  int gemm_ok = 0;
+  int* dev_err = nullptr;     // device error word for bounded waits
+
+  // coarse
+  double* A0band = nullptr;   // p=1: [3][N] (sub, diag, super); p=2: [N][9]
+  double* cr = nullptr;       // p=1 cyclic-reduction coefficients
+  int cr_m = 0, cr_np = 0;
+  double* A0inv = nullptr;    // p=2 dense inverse [N][N]
+  double* c0 = nullptr;       // coarse rhs [N]
+  double* u0 = nullptr;       // coarse solution [N]
+
+  // reductions
+  double* red = nullptr;      // partials
+  unsigned* cnt = nullptr;    // last-block counters [16]
+  dd::PcgState* st = nullptr;
+  dd::OuterState* ost = nullptr;
+  dd::PcgState* st_h = nullptr;    // pinned mirror
+  dd::OuterState* ost_h = nullptr; // pinned mirror
+
+  // graph of one block of PCG iterations
+  cudaGraphExec_t graph = nullptr;
+  int graph_iters = 0;
+};
+
+namespace dd {
+
+// ----- launchers (kernels in k_*.cu) -----
+int grid_blocks(long long work, int threads, int max_per_sm = 8);
+
+void launch_build_tables(dd_ctx* c);
+void launch_tabS(dd_ctx* c, double sigma);
+void launch_stencil(dd_ctx* c, const double* tab, const double* x, double* y, cudaStream_t s);
+void launch_stencil_dot(dd_ctx* c, const double* tab, const double* x, double* y, double* out_dot,
+                        unsigned* counter, cudaStream_t s);
+void launch_pad(dd_ctx* c, const double* u, double* v, cudaStream_t s);     // unpadded -> padded
+void launch_unpad(dd_ctx* c, const double* v, double* u, cudaStream_t s);   // padded -> unpadded
+void launch_check_finite(const double* v, long long n, int* flag, cudaStream_t s);
+
+// PCG pieces
+void launch_pcg_init(dd_ctx* c, const double* b, cudaStream_t s);   // r = b - A x, rr0
+void launch_pupdate(dd_ctx* c, cudaStream_t s);                     // p = z + beta p
+void launch_matvec_pq(dd_ctx* c, cudaStream_t s);                   // q = A p, pq, alpha
+void launch_xr_update(dd_ctx* c, cudaStream_t s);                   // x, r, rr, done
+void launch_prolong(dd_ctx* c, int init, cudaStream_t s);           // z = ..., rz, beta
+void launch_precond(dd_ctx* c, const double* r, double* z, int pcg_mode, cudaStream_t s);
+
+// local solves
+void launch_local_assemble(dd_ctx* c);
+int launch_band_factor(dd_ctx* c, double* CB, double* RB, double* inv, int nmat, int n, int b, int* flag);
+void launch_band_solve_local(dd_ctx* c, const double* r, cudaStream_t s);
+void launch_band_inverse(dd_ctx* c, double* out, int ld);
+
+// cell problem
+int cell_eigenpair(dd_ctx* c);
+
+// coarse
+void launch_coarse_weights(dd_ctx* c);
+int coarse_assemble(dd_ctx* c);
+int coarse_factor(dd_ctx* c);
+void launch_coarse_restrict(dd_ctx* c, const double* r, cudaStream_t s);
+void launch_coarse_solve(dd_ctx* c, cudaStream_t s);
+
+// GEMM path
+int gemm_setup(dd_ctx* c);
+void launch_pack(dd_ctx* c, const double* r, cudaStream_t s);
+int launch_gemm(dd_ctx* c, cudaStream_t s);
+void gemm_free(dd_ctx* c);
+
+// outer iteration
+void launch_outer_normalize(dd_ctx* c, const double* w, double* Mw, double* xout, cudaStream_t s);
+void launch_outer_residual(dd_ctx* c, const double* xe, const double* Mx, double* Ax, cudaStream_t s);
+
+// timing helpers
+void timer_begin(dd_ctx* c, int kc, cudaStream_t s, cudaEvent_t* e0);
+void timer_end(dd_ctx* c, int kc, cudaStream_t s, cudaEvent_t e0);
+void timer_collect(dd_ctx* c);
+
+void* dev_alloc(dd_ctx* c, size_t bytes);
+
+}  // namespace dd
+
+#define DD_CUDA(call)                                                          \
+  do {                                                                         \
+    cudaError_t e_ = (call);                                                   \
+    if (e_ != cudaSuccess) {                                                   \
+      throw dd::Error(DD_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    }                                                                          \
+  } while (0)
+
+namespace dd {
+struct Error {
+  int code;
+  std::string msg;
+  Error(int c, std::string m) : code(c), msg(std::move(m)) {}
+};
+}  // namespace dd

@@ -1,0 +1,455 @@
+// Local subdomain matrices and their banded Cholesky factors; the FP64 local solves of
+// the plain method; the cell eigenpair.
+//
+// Local problems (Sec. 3.1): A_{sigma,i} = R_i A_sigma R_i^T on the interior nodes strictly
+// inside the open overlapping box Omega_i (homogeneous Dirichlet on its artificial
+// boundary).  All subdomains with the same clipping (left / interior / right per axis) have
+// identical matrices, because the cells are translated copies and V is periodic (A1); the
+// factors are stored once per type.  Local order: (c1, c2, j) with j fastest, so the
+// half bandwidth is nyi + 1 (p = 1) or w2 nyi + nyi + 1 (p = 2).
+#include "dd_band.cuh"
+
+namespace dd {
+
+// ----------------------------------------------------------------------------------------
+// Banded Cholesky A = L L^T, one CTA per matrix, right-looking, in place in CB.
+// A zero or negative pivot sets *flag (DD_ENOTSPD) and continues with pivot 1.
+// ----------------------------------------------------------------------------------------
+__global__ void k_band_factor(double* CB, double* inv, const int* __restrict__ nvec, int nmax, int b,
+                              int* flag) {
+  extern __shared__ double colk[];
+  const int m = blockIdx.x;
+  const int n = nvec[m];
+  const int bs = b + 1;
+  double* A = CB + (size_t)m * nmax * bs;
+  double* iv = inv + (size_t)m * nmax;
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) {
+      double piv = A[(size_t)k * bs];
+      if (!(piv > 0.0)) {
+        atomicOr(flag, 1);
+        piv = 1.0;
+      }
+      const double l = sqrt(piv);
+      A[(size_t)k * bs] = l;
+      iv[k] = 1.0 / l;
+      colk[0] = 1.0 / l;
+    }
+    __syncthreads();
+    const double il = colk[0];
+    const int dmax = min(b, n - 1 - k);
+    for (int d = 1 + threadIdx.x; d <= b; d += blockDim.x) {
+      double v = 0.0;
+      if (d <= dmax) {
+        v = A[(size_t)k * bs + d] * il;
+        A[(size_t)k * bs + d] = v;
+      }
+      colk[d] = v;
+    }
+    __syncthreads();
+    // A(k+d1, k+d2) -= L(k+d1,k) L(k+d2,k), 1 <= d2 <= d1 <= dmax; stored at CB[k+d2][d1-d2]
+    const int tot = dmax * dmax;
+    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+      const int d1 = t / dmax + 1, d2 = t % dmax + 1;
+      if (d2 <= d1) A[(size_t)(k + d2) * bs + (d1 - d2)] -= colk[d1] * colk[d2];
+    }
+    __syncthreads();
+  }
+}
+
+// RB[i][d] = L(i, i-d) = CB[i-d][d]
+__global__ void k_band_rows(const double* __restrict__ CB, double* RB, const int* __restrict__ nvec,
+                            int nmat, int nmax, int b) {
+  const int bs = b + 1;
+  const long long total = (long long)nmat * nmax * bs;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(t / ((long long)nmax * bs));
+    const long long rem = t - (long long)m * nmax * bs;
+    const int i = (int)(rem / bs), d = (int)(rem % bs);
+    const int n = nvec[m];
+    double v = 0.0;
+    if (i < n && i - d >= 0) v = CB[((size_t)m * nmax + (i - d)) * bs + d];
+    RB[t] = v;
+  }
+}
+
+int launch_band_factor(dd_ctx* c, double* CB, double* RB, double* inv, int nmat, int nmax, int b, int* flag) {
+  // nvec: sizes of the matrices, taken from ctx scratch (c->dev_err + 16 ...) -> use a temp
+  int* nvec = nullptr;
+  DD_CUDA(cudaMallocAsync(&nvec, sizeof(int) * nmat, c->stream));
+  std::vector<int> nh(nmat);
+  if (CB == c->bandCB) {
+    for (int t = 0; t < nmat; ++t) nh[t] = c->type_nloc[t];
+  } else {
+    for (int t = 0; t < nmat; ++t) nh[t] = nmax;
+  }
+  DD_CUDA(cudaMemcpyAsync(nvec, nh.data(), sizeof(int) * nmat, cudaMemcpyHostToDevice, c->stream));
+  const size_t smem = sizeof(double) * (b + 1);
+  int threads = 256;
+  if ((long long)b * b > 4096) threads = 1024;
+  k_band_factor<<<nmat, threads, smem, c->stream>>>(CB, inv, nvec, nmax, b, flag);
+  DD_CUDA(cudaGetLastError());
+  const long long total = (long long)nmat * nmax * (b + 1);
+  k_band_rows<<<grid_blocks(total, kThreads), kThreads, 0, c->stream>>>(CB, RB, nvec, nmat, nmax, b);
+  DD_CUDA(cudaGetLastError());
+  DD_CUDA(cudaFreeAsync(nvec, c->stream));
+  return DD_OK;
+}
+
+// ----------------------------------------------------------------------------------------
+// Local matrix assembly from the A_sigma stencil table: CB[t][k][k'-k] = A_sigma(k', k), k' >= k.
+// ----------------------------------------------------------------------------------------
+__global__ void k_local_assemble(Geo g, const double* __restrict__ tabS, const Sub* __restrict__ rep,
+                                 int ntypes, int nmax, int b, double* CB) {
+  const int bs = b + 1;
+  const long long total = (long long)ntypes * nmax;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int ty = (int)(t / nmax);
+    const int k = (int)(t - (long long)ty * nmax);
+    const Sub s = rep[ty];
+    if (k >= s.nloc) continue;
+    const int sj = k % g.nyi;
+    const int cc = k / g.nyi;
+    const int c1 = cc / s.w2, c2 = cc % s.w2;
+    const int a1 = s.lo1 + c1, a2 = s.lo2 + c2;
+    int cls;
+    if (g.p == 1) cls = (a1 % g.n) * g.Ypad + sj;
+    else cls = ((a1 % g.n) * g.n + (a2 % g.n)) * g.Ypad + sj;
+    double* row = CB + ((size_t)ty * nmax + k) * bs;
+    for (int tap = 0; tap < g.ntap; ++tap) {
+      int d1, d2 = 0, dy;
+      if (g.p == 1) { d1 = tap / 3 - 1; dy = tap % 3 - 1; }
+      else { d1 = tap / 9 - 1; d2 = (tap / 3) % 3 - 1; dy = tap % 3 - 1; }
+      const int n1 = c1 + d1, n2 = c2 + d2, nj = sj + dy;
+      if (n1 < 0 || n1 >= s.w1 || n2 < 0 || n2 >= s.w2 || nj < 0 || nj >= g.nyi) continue;
+      const int kk = (n1 * s.w2 + n2) * g.nyi + nj;
+      if (kk < k) continue;
+      row[kk - k] = tabS[(size_t)tap * g.ncls + cls];
+    }
+  }
+}
+
+void launch_local_assemble(dd_ctx* c) {
+  // representative subdomain of every type
+  std::vector<Sub> rep(c->ntypes);
+  for (int t = 0; t < c->ntypes; ++t) {
+    for (const Sub& s : c->subs_h)
+      if (s.type == t) { rep[t] = s; break; }
+  }
+  Sub* drep = nullptr;
+  DD_CUDA(cudaMallocAsync(&drep, sizeof(Sub) * c->ntypes, c->stream));
+  DD_CUDA(cudaMemcpyAsync(drep, rep.data(), sizeof(Sub) * c->ntypes, cudaMemcpyHostToDevice, c->stream));
+  const size_t nbytes = sizeof(double) * (size_t)c->ntypes * c->nloc_max * (c->band + 1);
+  DD_CUDA(cudaMemsetAsync(c->bandCB, 0, nbytes, c->stream));
+  const long long total = (long long)c->ntypes * c->nloc_max;
+  k_local_assemble<<<grid_blocks(total, 128), 128, 0, c->stream>>>(c->g, c->tabS, drep, c->ntypes,
+                                                                   c->nloc_max, c->band, c->bandCB);
+  DD_CUDA(cudaGetLastError());
+  DD_CUDA(cudaFreeAsync(drep, c->stream));
+}
+
+// ----------------------------------------------------------------------------------------
+// FP64 local solves y_i = A_{sigma,i}^{-1} R_i r for every subdomain (one warp each); the
+// result goes to Y[slot(i)][k]; the prolong-sum gathers it.
+// ----------------------------------------------------------------------------------------
+__global__ void k_local_solve(Geo g, const Sub* __restrict__ subs, const int* __restrict__ slot_of,
+                              const double* __restrict__ r, const double* __restrict__ CB,
+                              const double* __restrict__ RB, const double* __restrict__ inv, int nmax, int b,
+                              double* __restrict__ Y, int kpad, const PcgState* st) {
+  if (st != nullptr && st->done) return;
+  extern __shared__ double xs_all[];
+  const int wpb = blockDim.x >> 5;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.x * wpb + wid;
+  if (s >= g.nsub) return;
+  double* xs = xs_all + (size_t)wid * nmax;
+  const Sub sb = subs[s];
+  for (int k = lane; k < sb.nloc; k += 32) {
+    const int sj = k % g.nyi, cc = k / g.nyi;
+    const int c1 = cc / sb.w2, c2 = cc % sb.w2;
+    long long idx;
+    if (g.p == 1) idx = (long long)(sb.lo1 + c1) * g.Ypad + sj;
+    else idx = ((long long)(sb.lo1 + c1) * g.ncx + (sb.lo2 + c2)) * g.Ypad + sj;
+    xs[k] = r[idx];
+  }
+  const size_t off = (size_t)sb.type * nmax;
+  warp_band_solve(xs, sb.nloc, b, CB + off * (b + 1), RB + off * (b + 1), inv + off);
+  double* y = Y + (size_t)slot_of[s] * kpad;
+  for (int k = lane; k < sb.nloc; k += 32) y[k] = xs[k];
+}
+
+static int local_warps_per_block(int nmax) {
+  int w = (int)((200 * 1024) / ((size_t)nmax * sizeof(double)));
+  if (w > 4) w = 4;
+  if (w < 1) w = 1;
+  return w;
+}
+
+void launch_band_solve_local(dd_ctx* c, const double* r, cudaStream_t s) {
+  const int wpb = local_warps_per_block(c->nloc_max);
+  const size_t smem = sizeof(double) * (size_t)wpb * c->nloc_max;
+  static bool attr_set = false;
+  if (!attr_set) {
+    DD_CUDA(cudaFuncSetAttribute(k_local_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    attr_set = true;
+  }
+  const int nb = (c->g.nsub + wpb - 1) / wpb;
+  k_local_solve<<<nb, wpb * 32, smem, s>>>(c->g, c->subs, c->slot_of_sub, r, c->bandCB, c->bandRB, c->bandInv,
+                                          c->nloc_max, c->band, c->Y64, c->kpad, c->st);
+  DD_CUDA(cudaGetLastError());
+}
+
+// ----------------------------------------------------------------------------------------
+// Cell eigenpair (cell problem of Sec. 1 / weak cell problem of Sec. 2): lowest eigenpair of
+// A_# psi = sigma M_# psi with x-periodic, y-Dirichlet conditions, by shifted inverse
+// iteration with shift s = min V - 1 (A_# - s M_# is SPD because M_V >= min(V) M for a
+// quadrature with positive weights).  The factor uses an interleaved x order
+// (0, n-1, 1, n-2, ...) that keeps periodic neighbours within two positions, so the
+// periodic operator is banded.
+// ----------------------------------------------------------------------------------------
+__host__ __device__ inline int ipos(int a, int n) { return (2 * a < n) ? 2 * a : 2 * (n - 1 - a) + 1; }
+
+__global__ void k_cell_shift(const double* __restrict__ V, long long nV, double* shift) {
+  double m = 1e300;
+  for (long long t = threadIdx.x; t < nV; t += blockDim.x) m = fmin(m, V[t]);
+  __shared__ double sm[32];
+  for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_down_sync(kFull, m, o));
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = sm[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = fmin(v, sm[w]);
+    *shift = v - 1.0;
+  }
+}
+
+// cell DOF (natural) k = (a1 [n + a2]) nyi + sj; interleaved row ri = (ipos(a1) [n + ipos(a2)]) nyi + sj
+__global__ void k_cell_assemble(Geo g, const double* __restrict__ tabA, const double* __restrict__ tabM,
+                                const double* __restrict__ shift, int b, double* CB) {
+  const int bs = b + 1;
+  const int ncol = (g.p == 1) ? g.n : g.n * g.n;
+  const long long ncell = (long long)ncol * g.nyi;
+  const double s = *shift;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ncell;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int sj = (int)(t % g.nyi);
+    const int cc = (int)(t / g.nyi);
+    int a1, a2 = 0, cls, row;
+    if (g.p == 1) {
+      a1 = cc;
+      cls = a1 * g.Ypad + sj;
+      row = ipos(a1, g.n) * g.nyi + sj;
+    } else {
+      a1 = cc / g.n;
+      a2 = cc % g.n;
+      cls = (a1 * g.n + a2) * g.Ypad + sj;
+      row = (ipos(a1, g.n) * g.n + ipos(a2, g.n)) * g.nyi + sj;
+    }
+    for (int tap = 0; tap < g.ntap; ++tap) {
+      int d1, d2 = 0, dy;
+      if (g.p == 1) { d1 = tap / 3 - 1; dy = tap % 3 - 1; }
+      else { d1 = tap / 9 - 1; d2 = (tap / 3) % 3 - 1; dy = tap % 3 - 1; }
+      const int nj = sj + dy;
+      if (nj < 0 || nj >= g.nyi) continue;
+      const int b1 = (a1 + d1 + g.n) % g.n;
+      int col;
+      if (g.p == 1) col = ipos(b1, g.n) * g.nyi + nj;
+      else {
+        const int b2 = (a2 + d2 + g.n) % g.n;
+        col = (ipos(b1, g.n) * g.n + ipos(b2, g.n)) * g.nyi + nj;
+      }
+      if (col < row) continue;
+      const size_t ti = (size_t)tap * g.ncls + cls;
+      CB[(size_t)row * bs + (col - row)] += tabA[ti] - s * tabM[ti];
+    }
+  }
+}
+
+// periodic cell stencil y = T x (natural cell order), CTA-wide
+__device__ void cell_stencil(const Geo& g, const double* __restrict__ tab, const double* x, double* y, int ncell) {
+  for (int k = threadIdx.x; k < ncell; k += blockDim.x) {
+    const int sj = k % g.nyi, cc = k / g.nyi;
+    int a1, a2 = 0, cls;
+    if (g.p == 1) { a1 = cc; cls = a1 * g.Ypad + sj; }
+    else { a1 = cc / g.n; a2 = cc % g.n; cls = (a1 * g.n + a2) * g.Ypad + sj; }
+    double acc = 0.0;
+    for (int tap = 0; tap < g.ntap; ++tap) {
+      int d1, d2 = 0, dy;
+      if (g.p == 1) { d1 = tap / 3 - 1; dy = tap % 3 - 1; }
+      else { d1 = tap / 9 - 1; d2 = (tap / 3) % 3 - 1; dy = tap % 3 - 1; }
+      const int nj = sj + dy;
+      if (nj < 0 || nj >= g.nyi) continue;
+      const int b1 = (a1 + d1 + g.n) % g.n;
+      int kk;
+      if (g.p == 1) kk = b1 * g.nyi + nj;
+      else kk = (b1 * g.n + (a2 + d2 + g.n) % g.n) * g.nyi + nj;
+      acc = fma(__ldg(tab + (size_t)tap * g.ncls + cls), x[kk], acc);
+    }
+    y[k] = acc;
+  }
+}
+
+template <int NV>
+__device__ void cta_sum(double (&v)[NV]) {   // result broadcast to every thread
+  __shared__ double res[NV];
+  block_sum<NV>(v);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < NV; ++k) res[k] = v[k];
+  __syncthreads();
+  for (int k = 0; k < NV; ++k) v[k] = res[k];
+  __syncthreads();
+}
+
+struct CellOut {
+  double sigma, eta, drho;
+  int iters, status;
+};
+
+__global__ void k_cell_iterate(Geo g, const double* __restrict__ tabA, const double* __restrict__ tabM,
+                               const double* __restrict__ CB, const double* __restrict__ RB,
+                               const double* __restrict__ inv, int b, int maxit, double* psi_out,
+                               CellOut* out) {
+  extern __shared__ double sm[];
+  const int ncol = (g.p == 1) ? g.n : g.n * g.n;
+  const int ncell = ncol * g.nyi;
+  double* x = sm;
+  double* y = sm + ncell;
+  double* xs = sm + 2 * ncell;
+  // x0 = 1 / ||1||_M
+  for (int k = threadIdx.x; k < ncell; k += blockDim.x) x[k] = 1.0;
+  __syncthreads();
+  double rho_prev = 1e300;
+  int it = 0, stable = 0, status = 0;
+  double eta = 0.0, drho = 0.0, rho = 0.0;
+  for (it = 1; it <= maxit; ++it) {
+    // y = M x ; permute into interleaved order
+    cell_stencil(g, tabM, x, y, ncell);
+    __syncthreads();
+    for (int k = threadIdx.x; k < ncell; k += blockDim.x) {
+      const int sj = k % g.nyi, cc = k / g.nyi;
+      int ri;
+      if (g.p == 1) ri = ipos(cc, g.n) * g.nyi + sj;
+      else ri = (ipos(cc / g.n, g.n) * g.n + ipos(cc % g.n, g.n)) * g.nyi + sj;
+      xs[ri] = y[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) warp_band_solve(xs, ncell, b, CB, RB, inv);
+    __syncthreads();
+    // w (natural order) -> x
+    for (int k = threadIdx.x; k < ncell; k += blockDim.x) {
+      const int sj = k % g.nyi, cc = k / g.nyi;
+      int ri;
+      if (g.p == 1) ri = ipos(cc, g.n) * g.nyi + sj;
+      else ri = (ipos(cc / g.n, g.n) * g.n + ipos(cc % g.n, g.n)) * g.nyi + sj;
+      x[k] = xs[ri];
+    }
+    __syncthreads();
+    // normalise: x = w / ||w||_M, sign so that sum x > 0
+    cell_stencil(g, tabM, x, y, ncell);
+    __syncthreads();
+    double d2[2] = {0.0, 0.0};
+    for (int k = threadIdx.x; k < ncell; k += blockDim.x) {
+      d2[0] = fma(x[k], y[k], d2[0]);
+      d2[1] += x[k];
+    }
+    cta_sum<2>(d2);
+    if (!(d2[0] > 0.0)) { status = DD_ENAN; break; }
+    const double sc = (d2[1] < 0.0 ? -1.0 : 1.0) / sqrt(d2[0]);
+    for (int k = threadIdx.x; k < ncell; k += blockDim.x) {
+      x[k] *= sc;
+      y[k] *= sc;   // y = M x
+    }
+    __syncthreads();
+    // rho = x^T A x, residual A x - rho M x
+    cell_stencil(g, tabA, x, xs, ncell);
+    __syncthreads();
+    double d1[1] = {0.0};
+    for (int k = threadIdx.x; k < ncell; k += blockDim.x) d1[0] = fma(x[k], xs[k], d1[0]);
+    cta_sum<1>(d1);
+    rho = d1[0];
+    double d3[2] = {0.0, 0.0};
+    for (int k = threadIdx.x; k < ncell; k += blockDim.x) {
+      const double e = fma(-rho, y[k], xs[k]);
+      d3[0] = fma(e, e, d3[0]);
+      d3[1] = fma(y[k], y[k], d3[1]);
+    }
+    cta_sum<2>(d3);
+    eta = sqrt(d3[0] / d3[1]) / fabs(rho);
+    drho = fabs(rho - rho_prev);
+    if (!isfinite(rho)) { status = DD_ENAN; break; }
+    if (drho <= 1e-14 * fabs(rho) && eta <= 1e-11) {
+      if (++stable >= 2) break;
+    } else {
+      stable = 0;
+    }
+    rho_prev = rho;
+  }
+  for (int k = threadIdx.x; k < ncell; k += blockDim.x) psi_out[k] = x[k];
+  if (threadIdx.x == 0) {
+    out->sigma = rho;
+    out->eta = eta;
+    out->drho = drho;
+    out->iters = it > maxit ? maxit : it;
+    out->status = (status == 0 && it > maxit) ? DD_EMAXIT : status;
+  }
+}
+
+int cell_eigenpair(dd_ctx* c) {
+  const Geo& g = c->g;
+  const int ncol = (g.p == 1) ? g.n : g.n * g.n;
+  const int ncell = ncol * g.nyi;
+  const int b = (g.p == 1) ? 2 * g.nyi + 1 : 2 * g.n * g.nyi + 2 * g.nyi + 1;
+  c->ncell = ncell;
+  c->cell_band = b;
+  const size_t cbsz = sizeof(double) * (size_t)ncell * (b + 1);
+  double *CB = nullptr, *RB = nullptr, *inv = nullptr, *shift = nullptr;
+  CellOut* out = nullptr;
+  int* flag = c->dev_err + 1;
+  DD_CUDA(cudaMallocAsync(&CB, cbsz, c->stream));
+  DD_CUDA(cudaMallocAsync(&RB, cbsz, c->stream));
+  DD_CUDA(cudaMallocAsync(&inv, sizeof(double) * ncell, c->stream));
+  DD_CUDA(cudaMallocAsync(&shift, sizeof(double), c->stream));
+  DD_CUDA(cudaMallocAsync(&out, sizeof(CellOut), c->stream));
+  DD_CUDA(cudaMemsetAsync(CB, 0, cbsz, c->stream));
+  DD_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), c->stream));
+  long long nV = (long long)ncol * g.ny;
+  for (int k = 0; k <= g.p; ++k) nV *= g.Q;
+  k_cell_shift<<<1, 1024, 0, c->stream>>>(c->Vqp, nV, shift);
+  k_cell_assemble<<<grid_blocks(ncell, 128), 128, 0, c->stream>>>(g, c->tabA, c->tabM, shift, b, CB);
+  DD_CUDA(cudaGetLastError());
+  // factor (one matrix of size ncell)
+  {
+    int* nvec = nullptr;
+    DD_CUDA(cudaMallocAsync(&nvec, sizeof(int), c->stream));
+    DD_CUDA(cudaMemcpyAsync(nvec, &ncell, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    const int threads = ((long long)b * b > 4096) ? 1024 : 256;
+    k_band_factor<<<1, threads, sizeof(double) * (b + 1), c->stream>>>(CB, inv, nvec, ncell, b, flag);
+    k_band_rows<<<grid_blocks((long long)ncell * (b + 1), kThreads), kThreads, 0, c->stream>>>(CB, RB, nvec, 1,
+                                                                                              ncell, b);
+    DD_CUDA(cudaGetLastError());
+    DD_CUDA(cudaFreeAsync(nvec, c->stream));
+  }
+  const size_t smem = sizeof(double) * 3 * (size_t)ncell;
+  DD_CUDA(cudaFuncSetAttribute(k_cell_iterate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_cell_iterate<<<1, 1024, smem, c->stream>>>(g, c->tabA, c->tabM, CB, RB, inv, b, 20000, c->psi_cell, out);
+  DD_CUDA(cudaGetLastError());
+  CellOut h;
+  int fl = 0;
+  DD_CUDA(cudaMemcpyAsync(&h, out, sizeof(CellOut), cudaMemcpyDeviceToHost, c->stream));
+  DD_CUDA(cudaMemcpyAsync(&fl, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  DD_CUDA(cudaFreeAsync(CB, c->stream));
+  DD_CUDA(cudaFreeAsync(RB, c->stream));
+  DD_CUDA(cudaFreeAsync(inv, c->stream));
+  DD_CUDA(cudaFreeAsync(shift, c->stream));
+  DD_CUDA(cudaFreeAsync(out, c->stream));
+  DD_CUDA(cudaStreamSynchronize(c->stream));
+  if (fl) throw Error(DD_ENOTSPD, "cell matrix A_# - s M_# not positive definite");
+  if (h.status != 0 && h.status != DD_EMAXIT) throw Error(h.status, "cell inverse iteration failed");
+  c->sigma = h.sigma;
+  c->cell_iters = h.iters;
+  return h.status;
+}
+
+}  // namespace dd

@@ -1,0 +1,358 @@
+// PerFact coarse space (Definition 2.1): R_0^T = blockdiag(D_i R_i psi), one column per
+// subdomain; coarse matrix A_{sigma,0} = R_0 A_sigma R_0^T and its solve (Sec. 3.1).
+//
+// The weights D_i R_i psi of all subdomains of one type are the same table (the cells are
+// translated copies, psi and the partition of unity are periodic), stored per type.
+// A_0 couples only neighbouring subdomains (supports of D_i R_i psi overlap only for
+// |i - j| <= 1 per axis since 2 delta < n), so it is assembled with 3^p coloured
+// operator applications: v_c = sum of the columns of colour c, w_c = A_sigma v_c, and
+// A_0[i][j] = (D_i R_i psi)^T w_{c(j)} for the unique neighbour j of i of colour c.
+//   p = 1: A_0 is tridiagonal, solved by cyclic reduction in one CTA (coefficients
+//          precomputed once, so each solve is 2 log2 N synchronised sweeps).
+//   p = 2: A_0 is block tridiagonal (bandwidth L + 1); its dense inverse is formed once
+//          from a banded Cholesky factor and applied as an FP64 matrix-vector product.
+#include "dd_band.cuh"
+
+namespace dd {
+
+// Distance of a node coordinate to the artificial faces of subdomain i along one axis
+// (Sec. 4.1.2: d_i = dist(z, dOmega_i minus dOmega) inside Omega_i); +inf if no face.
+__device__ inline double axis_face_dist(const Geo& g, int i, int a) {
+  const double x = a * g.h;
+  const double lo = i - g.delta * g.h, hi = i + 1 + g.delta * g.h;
+  double d = 1e300;
+  if (lo > 1e-12) d = fmin(d, x - lo);
+  if (hi < g.L - 1e-12) d = fmin(d, hi - x);
+  return d;
+}
+
+// partition-of-unity weight of subdomain (i1, i2) at node (a1, a2)
+__device__ double pu_weight(const Geo& g, int pu, int i1, int i2, int a1, int a2) {
+  int o1[2], l1[2], o2[2] = {0, 0}, l2[2] = {0, 0};
+  const int n1 = axis_owners(g, a1, o1, l1);
+  const int n2 = (g.p == 2) ? axis_owners(g, a2, o2, l2) : 1;
+  if (pu == DD_PU_EQUAL) return 1.0 / (double)(n1 * n2);
+  if (g.nsub == 1) return 1.0;
+  double mine = 0.0, tot = 0.0;
+  for (int i = 0; i < n1; ++i)
+    for (int k = 0; k < n2; ++k) {
+      double d = axis_face_dist(g, o1[i], a1);
+      if (g.p == 2) d = fmin(d, axis_face_dist(g, o2[k], a2));
+      tot += d;
+      if (o1[i] == i1 && (g.p == 1 || o2[k] == i2)) mine = d;
+    }
+  return mine / tot;
+}
+
+__global__ void k_coarse_weights(Geo g, int pu, const Sub* __restrict__ rep, int ntypes, int kpad,
+                                 const double* __restrict__ psi, double* wT) {
+  const long long total = (long long)ntypes * kpad;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int ty = (int)(t / kpad), k = (int)(t % kpad);
+    const Sub s = rep[ty];
+    double v = 0.0;
+    if (k < s.nloc) {
+      const int sj = k % g.nyi, cc = k / g.nyi;
+      const int c1 = cc / s.w2, c2 = cc % s.w2;
+      const int a1 = s.lo1 + c1, a2 = s.lo2 + c2;
+      // subdomain index of the representative along each axis: from its first column
+      const int i1 = (s.lo1 + g.delta - 1) / g.n, i2 = (g.p == 2) ? (s.lo2 + g.delta - 1) / g.n : 0;
+      int pc;
+      if (g.p == 1) pc = (a1 % g.n) * g.nyi + sj;
+      else pc = ((a1 % g.n) * g.n + (a2 % g.n)) * g.nyi + sj;
+      v = pu_weight(g, pu, i1, i2, a1, a2) * psi[pc];
+    }
+    wT[t] = v;
+  }
+}
+
+static Sub* upload_reps(dd_ctx* c) {
+  std::vector<Sub> rep(c->ntypes);
+  for (int t = 0; t < c->ntypes; ++t)
+    for (const Sub& s : c->subs_h)
+      if (s.type == t) { rep[t] = s; break; }
+  Sub* d = nullptr;
+  DD_CUDA(cudaMallocAsync(&d, sizeof(Sub) * c->ntypes, c->stream));
+  DD_CUDA(cudaMemcpyAsync(d, rep.data(), sizeof(Sub) * c->ntypes, cudaMemcpyHostToDevice, c->stream));
+  return d;
+}
+
+void launch_coarse_weights(dd_ctx* c) {
+  Sub* rep = upload_reps(c);
+  const long long total = (long long)c->ntypes * c->kpad;
+  k_coarse_weights<<<grid_blocks(total, 128), 128, 0, c->stream>>>(c->g, c->grid.pu_kind, rep, c->ntypes,
+                                                                   c->kpad, c->psi_cell, c->wT);
+  DD_CUDA(cudaGetLastError());
+  DD_CUDA(cudaFreeAsync(rep, c->stream));
+}
+
+// local index k of subdomain s -> padded global index
+__device__ __forceinline__ long long sub_global(const Geo& g, const Sub& sb, int k) {
+  const int sj = k % g.nyi, cc = k / g.nyi;
+  const int c1 = cc / sb.w2, c2 = cc % sb.w2;
+  if (g.p == 1) return (long long)(sb.lo1 + c1) * g.Ypad + sj;
+  return ((long long)(sb.lo1 + c1) * g.ncx + (sb.lo2 + c2)) * g.Ypad + sj;
+}
+
+// v = sum of the coarse columns of colour (c1, c2)
+__global__ void k_colour_vector(Geo g, const Sub* __restrict__ subs, const double* __restrict__ wT, int kpad,
+                                int col1, int col2, double* v) {
+  const long long total = (long long)g.nxi * (g.p == 2 ? g.nxi : 1) * g.Ypad;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    Node nd = (g.p == 1) ? node_of<1>(g, t) : node_of<2>(g, t);
+    double val = 0.0;
+    if (nd.slot < g.nyi) {
+      int o1[2], l1[2], o2[2] = {0, 0}, l2[2] = {0, 0};
+      const int n1 = axis_owners(g, nd.a1, o1, l1);
+      const int n2 = (g.p == 2) ? axis_owners(g, nd.a2, o2, l2) : 1;
+      for (int i = 0; i < n1; ++i)
+        for (int k = 0; k < n2; ++k) {
+          if (o1[i] % 3 != col1) continue;
+          if (g.p == 2 && o2[k] % 3 != col2) continue;
+          const int s = (g.p == 1) ? o1[i] : o1[i] * g.L + o2[k];
+          const Sub sb = subs[s];
+          const int loc = ((g.p == 1) ? l1[i] : l1[i] * sb.w2 + l2[k]) * g.nyi + nd.slot;
+          val += wT[(size_t)sb.type * kpad + loc];
+        }
+    }
+    v[nd.idx] = val;
+  }
+}
+
+// A0nb[s][nb] for the neighbour of colour (col1, col2): block per subdomain
+__global__ void k_coarse_entries(Geo g, const Sub* __restrict__ subs, const double* __restrict__ wT, int kpad,
+                                 int col1, int col2, const double* __restrict__ w, double* A0nb) {
+  const int s = blockIdx.x;
+  const int s1 = (g.p == 1) ? s : s / g.L, s2 = (g.p == 1) ? 0 : s % g.L;
+  // the neighbour of colour col along each axis
+  int t1 = -10, t2 = 0;
+  for (int d = -1; d <= 1; ++d)
+    if (((s1 + d) % 3 + 3) % 3 == col1) t1 = s1 + d;
+  if (g.p == 2) {
+    t2 = -10;
+    for (int d = -1; d <= 1; ++d)
+      if (((s2 + d) % 3 + 3) % 3 == col2) t2 = s2 + d;
+  }
+  if (t1 < 0 || t1 >= g.L || (g.p == 2 && (t2 < 0 || t2 >= g.L))) return;
+  const Sub sb = subs[s];
+  double acc[1] = {0.0};
+  for (int k = threadIdx.x; k < sb.nloc; k += blockDim.x)
+    acc[0] = fma(wT[(size_t)sb.type * kpad + k], w[sub_global(g, sb, k)], acc[0]);
+  block_sum<1>(acc);
+  if (threadIdx.x == 0) {
+    const int nbk = (g.p == 1) ? (t1 - s1 + 1) : ((t1 - s1 + 1) * 3 + (t2 - s2 + 1));
+    A0nb[(size_t)s * (g.p == 1 ? 3 : 9) + nbk] = acc[0];
+  }
+}
+
+int coarse_assemble(dd_ctx* c) {
+  const Geo& g = c->g;
+  const int nnb = (g.p == 1) ? 3 : 9;
+  DD_CUDA(cudaMemsetAsync(c->A0band, 0, sizeof(double) * (size_t)g.nsub * nnb, c->stream));
+  const long long work = (long long)g.nxi * (g.p == 2 ? g.nxi : 1) * g.Ypad;
+  const int ncol2 = (g.p == 2) ? 3 : 1;
+  for (int c1 = 0; c1 < 3; ++c1)
+    for (int c2 = 0; c2 < ncol2; ++c2) {
+      k_colour_vector<<<grid_blocks(work, kThreads), kThreads, 0, c->stream>>>(g, c->subs, c->wT, c->kpad, c1, c2,
+                                                                               c->w1);
+      launch_stencil(c, c->tabS, c->w1, c->w2, c->stream);
+      k_coarse_entries<<<g.nsub, 256, 0, c->stream>>>(g, c->subs, c->wT, c->kpad, c1, c2, c->w2, c->A0band);
+      DD_CUDA(cudaGetLastError());
+    }
+  return DD_OK;
+}
+
+// ----------------------------------------------------------------------------------------
+// p = 1: cyclic reduction for the tridiagonal A_0 (symmetric positive definite, so the
+// odd-even elimination needs no pivoting).  Equations j = 1..N' (N' = 2^m - 1 >= N,
+// padded with identity rows): a_j x_{j-1} + b_j x_j + c_j x_{j+1} = f_j.
+// Layout of c->cr: alpha[m][N'+2], gamma[m][N'+2], a[N'+2], binv[N'+2], cc[N'+2].
+// ----------------------------------------------------------------------------------------
+__global__ void k_cr_setup(const double* __restrict__ A0nb, int N, int m, int Np, double* cr, int* flag) {
+  const int W = Np + 2;
+  double* alpha = cr;
+  double* gamma = cr + (size_t)m * W;
+  double* a = cr + (size_t)2 * m * W;
+  double* binv = a + W;
+  double* cc = binv + W;
+  double* b = cc + W;   // work: b values
+  for (int j = threadIdx.x; j < W; j += blockDim.x) {
+    double aj = 0.0, bj = 1.0, cj = 0.0;
+    if (j >= 1 && j <= N) {
+      bj = A0nb[(size_t)(j - 1) * 3 + 1];
+      aj = (j >= 2) ? A0nb[(size_t)(j - 1) * 3 + 0] : 0.0;
+      cj = (j <= N - 1) ? A0nb[(size_t)(j - 1) * 3 + 2] : 0.0;
+    }
+    if (j == 0 || j == W - 1) bj = 1.0;
+    a[j] = aj;
+    b[j] = bj;
+    cc[j] = cj;
+  }
+  __syncthreads();
+  for (int l = 0; l < m - 1; ++l) {
+    const int s = 1 << l;
+    for (int j = 2 * s + 2 * s * threadIdx.x; j <= Np; j += 2 * s * blockDim.x) {
+      const double al = -a[j] / b[j - s];
+      const double ga = -cc[j] / b[j + s];
+      alpha[(size_t)l * W + j] = al;
+      gamma[(size_t)l * W + j] = ga;
+      b[j] = b[j] + al * cc[j - s] + ga * a[j + s];
+      a[j] = al * a[j - s];
+      cc[j] = ga * cc[j + s];
+    }
+    __syncthreads();
+  }
+  for (int j = threadIdx.x; j < W; j += blockDim.x) {
+    if (!(b[j] > 0.0)) atomicOr(flag, 1);
+    binv[j] = 1.0 / b[j];
+  }
+}
+
+__global__ void k_cr_solve(const double* __restrict__ cr, int N, int m, int Np, const double* __restrict__ rhs,
+                           double* __restrict__ x, const PcgState* st) {
+  if (st != nullptr && st->done) return;
+  extern __shared__ double f[];
+  const int W = Np + 2;
+  const double* alpha = cr;
+  const double* gamma = cr + (size_t)m * W;
+  const double* a = cr + (size_t)2 * m * W;
+  const double* binv = a + W;
+  const double* cc = binv + W;
+  for (int j = threadIdx.x; j < W; j += blockDim.x) f[j] = (j >= 1 && j <= N) ? rhs[j - 1] : 0.0;
+  __syncthreads();
+  for (int l = 0; l < m - 1; ++l) {
+    const int s = 1 << l;
+    for (int j = 2 * s + 2 * s * threadIdx.x; j <= Np; j += 2 * s * blockDim.x)
+      f[j] = fma(alpha[(size_t)l * W + j], f[j - s], fma(gamma[(size_t)l * W + j], f[j + s], f[j]));
+    __syncthreads();
+  }
+  const int root = 1 << (m - 1);
+  if (threadIdx.x == 0) f[root] *= binv[root];
+  __syncthreads();
+  for (int l = m - 2; l >= 0; --l) {
+    const int s = 1 << l;
+    for (int j = s + 2 * s * threadIdx.x; j <= Np; j += 2 * s * blockDim.x) {
+      const double left = f[j - s];                       // j - s >= 0, f[0] = 0
+      const double right = (j + s <= Np) ? f[j + s] : 0.0;
+      f[j] = (f[j] - a[j] * left - cc[j] * right) * binv[j];
+    }
+    __syncthreads();
+  }
+  for (int j = threadIdx.x; j < N; j += blockDim.x) x[j] = f[j + 1];
+}
+
+// p = 2: dense inverse rows from the banded factor (identity right-hand sides)
+__global__ void k_band_inverse_rows(int n, int b, const double* __restrict__ CB, const double* __restrict__ RB,
+                                    const double* __restrict__ inv, double* out) {
+  extern __shared__ double xs_all[];
+  const int wpb = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int col = blockIdx.x * wpb + wid;
+  if (col >= n) return;
+  double* xs = xs_all + (size_t)wid * n;
+  for (int k = lane; k < n; k += 32) xs[k] = (k == col) ? 1.0 : 0.0;
+  warp_band_solve(xs, n, b, CB, RB, inv);
+  for (int k = lane; k < n; k += 32) out[(size_t)col * n + k] = xs[k];
+}
+
+__global__ void k_gemv_rows(int n, const double* __restrict__ A, const double* __restrict__ xin,
+                            double* __restrict__ y, const PcgState* st) {
+  if (st != nullptr && st->done) return;
+  const int wpb = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * wpb + wid;
+  if (row >= n) return;
+  const double* ar = A + (size_t)row * n;
+  double acc = 0.0;
+  for (int k = lane; k < n; k += 32) acc = fma(ar[k], __ldg(xin + k), acc);
+  acc = warp_sum(acc);
+  if (lane == 0) y[row] = acc;
+}
+
+int coarse_factor(dd_ctx* c) {
+  const Geo& g = c->g;
+  const int N = g.nsub;
+  int* flag = c->dev_err + 2;
+  DD_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), c->stream));
+  if (g.p == 1) {
+    int m = 1;
+    while ((1 << m) - 1 < N) ++m;
+    const int Np = (1 << m) - 1;
+    c->cr_m = m;
+    c->cr_np = Np;
+    const size_t W = (size_t)Np + 2;
+    c->cr = (double*)dev_alloc(c, sizeof(double) * W * (2 * m + 4));
+    k_cr_setup<<<1, 1024, 0, c->stream>>>(c->A0band, N, m, Np, c->cr, flag);
+    DD_CUDA(cudaGetLastError());
+  } else {
+    const int b = g.L + 1;
+    const size_t cb = sizeof(double) * (size_t)N * (b + 1);
+    double* CB = (double*)dev_alloc(c, cb);
+    double* RB = (double*)dev_alloc(c, cb);
+    double* inv = (double*)dev_alloc(c, sizeof(double) * N);
+    // scatter the 9-point coarse rows into lower band storage (order s = s1 L + s2)
+    std::vector<double> nb((size_t)N * 9), hcb((size_t)N * (b + 1), 0.0);
+    DD_CUDA(cudaMemcpyAsync(nb.data(), c->A0band, sizeof(double) * N * 9, cudaMemcpyDeviceToHost, c->stream));
+    DD_CUDA(cudaStreamSynchronize(c->stream));
+    for (int s = 0; s < N; ++s) {
+      const int s1 = s / g.L, s2 = s % g.L;
+      for (int k = 0; k < 9; ++k) {
+        const int t1 = s1 + k / 3 - 1, t2 = s2 + k % 3 - 1;
+        if (t1 < 0 || t1 >= g.L || t2 < 0 || t2 >= g.L) continue;
+        const int t = t1 * g.L + t2;
+        if (t < s) continue;
+        hcb[(size_t)s * (b + 1) + (t - s)] = nb[(size_t)s * 9 + k];
+      }
+    }
+    DD_CUDA(cudaMemcpyAsync(CB, hcb.data(), cb, cudaMemcpyHostToDevice, c->stream));
+    launch_band_factor(c, CB, RB, inv, 1, N, b, flag);
+    c->A0inv = (double*)dev_alloc(c, sizeof(double) * (size_t)N * N);
+    const int wpb = (N * 8 <= 48 * 1024) ? 4 : 1;
+    const size_t smem = sizeof(double) * (size_t)wpb * N;
+    DD_CUDA(cudaFuncSetAttribute(k_band_inverse_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    k_band_inverse_rows<<<(N + wpb - 1) / wpb, 32 * wpb, smem, c->stream>>>(N, b, CB, RB, inv, c->A0inv);
+    DD_CUDA(cudaGetLastError());
+  }
+  int fl = 0;
+  DD_CUDA(cudaMemcpyAsync(&fl, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  DD_CUDA(cudaStreamSynchronize(c->stream));
+  if (fl) throw Error(DD_ENOTSPD, "coarse matrix A_0 not positive definite");
+  return DD_OK;
+}
+
+// c_i = (D_i R_i psi)^T r, block per subdomain
+__global__ void k_coarse_restrict(Geo g, const Sub* __restrict__ subs, const double* __restrict__ wT, int kpad,
+                                  const double* __restrict__ r, double* __restrict__ c0, const PcgState* st) {
+  if (st != nullptr && st->done) return;
+  const int s = blockIdx.x;
+  const Sub sb = subs[s];
+  double acc[1] = {0.0};
+  for (int k = threadIdx.x; k < sb.nloc; k += blockDim.x)
+    acc[0] = fma(wT[(size_t)sb.type * kpad + k], r[sub_global(g, sb, k)], acc[0]);
+  block_sum<1>(acc);
+  if (threadIdx.x == 0) c0[s] = acc[0];
+}
+
+void launch_coarse_restrict(dd_ctx* c, const double* r, cudaStream_t s) {
+  k_coarse_restrict<<<c->g.nsub, 256, 0, s>>>(c->g, c->subs, c->wT, c->kpad, r, c->c0, c->st);
+  DD_CUDA(cudaGetLastError());
+}
+
+void launch_coarse_solve(dd_ctx* c, cudaStream_t s) {
+  const Geo& g = c->g;
+  if (g.p == 1) {
+    const size_t smem = sizeof(double) * ((size_t)c->cr_np + 2);
+    static bool attr = false;
+    if (!attr) {
+      DD_CUDA(cudaFuncSetAttribute(k_cr_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+      attr = true;
+    }
+    k_cr_solve<<<1, 1024, smem, s>>>(c->cr, g.nsub, c->cr_m, c->cr_np, c->c0, c->u0, c->st);
+  } else {
+    const int N = g.nsub;
+    k_gemv_rows<<<(N + 7) / 8, 256, 0, s>>>(N, c->A0inv, c->c0, c->u0, c->st);
+  }
+  DD_CUDA(cudaGetLastError());
+}
+
+}  // namespace dd

@@ -1,0 +1,516 @@
+// Local solves as a batched dense contraction on the tensor cores (tcgen05, sm_103a).
+//
+// Two-level additive Schwarz (Sec. 3.1) needs y_i = A_{sigma,i}^{-1} R_i r for every
+// subdomain.  Subdomains of one type share A_T = A_{sigma,i}, so with the rows
+// R_i r stacked (type-sorted) into B_T (N_T x K) the local solves of a type are one GEMM
+//     Y_T[n][m] = sum_k Ainv_T[m][k] B_T[n][k]           (Ainv_T symmetric, K-major)
+// with Ainv_T rounded to BF16 or TF32 and FP32 accumulation.  The rounding makes the
+// preconditioner inexact; the outer Krylov method is then flexible CG.
+//
+// Kernel: one CTA per 128 x 256 output tile; warp 0 lane 0 issues TMA loads into a
+// 4-stage ring of 128B-swizzled shared-memory tiles, warp 1 lane 0 issues tcgen05.mma
+// with the accumulator in tensor memory, all four warps read it back with tcgen05.ld and
+// store Y (FP32).  Every mbarrier wait is bounded; on expiry the CTA records an error in a
+// device word, stops issuing work and returns after freeing its tensor memory.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <cstring>
+
+#include "dd_band.cuh"
+
+namespace dd {
+
+struct Tile {
+  int type, m0, n0, nend;
+};
+
+template <typename T>
+struct TcCfg {
+  static constexpr int BM = 128, BN = 256;
+  static constexpr int BK = 128 / (int)sizeof(T);   // one 128-byte swizzle row
+  static constexpr int UK = 32 / (int)sizeof(T);    // K of one tcgen05.mma (32 bytes)
+  static constexpr int STAGES = 4;
+  static constexpr int A_BYTES = BM * 128;
+  static constexpr int B_BYTES = BN * 128;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait: about 4 s at most, then the error word gets `code`
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, int* err, int code) {
+  for (long long i = 0; i < (1LL << 26); ++i) {
+    if (mbar_try_wait(a, parity)) return true;
+    if (i > 256) __nanosleep(64);
+  }
+  atomicOr(err, code);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(tm), "r"(c0), "r"(c1), "r"(mbar)
+      : "memory");
+}
+
+// shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;              // leading byte offset (unused with 128B swizzle, K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset
+  d |= (uint64_t)1 << 46;              // descriptor version
+  d |= (uint64_t)2 << 61;              // 128-byte swizzle
+  return d;
+}
+
+// instruction descriptor: D = F32, A/B format fmt (1 = BF16, 2 = TF32), K-major both, M = 128, N = 256
+__host__ __device__ constexpr uint32_t mma_idesc(uint32_t fmt, int M, int N) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+template <typename T>
+__device__ __forceinline__ void mma_issue(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc);
+
+template <>
+__device__ __forceinline__ void mma_issue<__nv_bfloat16>(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                                         uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+template <>
+__device__ __forceinline__ void mma_issue<float>(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+constexpr int kTmemCols = 256;
+constexpr int ERR_TMA_WAIT = 1 << 4, ERR_MMA_WAIT = 1 << 5, ERR_ACC_WAIT = 1 << 6;
+
+template <typename T>
+__global__ void __launch_bounds__(128, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              const Tile* __restrict__ tiles, int K, int mlimit, int rows_per_type, float* __restrict__ Y,
+              int ldy, int* err, const PcgState* st) {
+  using C = TcCfg<T>;
+  if (st != nullptr && st->done) return;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* sm = smem_raw + (base - raw);
+  const uint32_t sA0 = base;
+  const uint32_t sB0 = base + C::STAGES * C::A_BYTES;
+  uint8_t* bar_ptr = sm + C::STAGES * C::STAGE_BYTES;
+  const uint32_t bar = base + C::STAGES * C::STAGE_BYTES;
+  // barriers: full[s] at bar + 8 s, empty[s] at bar + 64 + 8 s, accum at bar + 128, tmem slot at bar + 192
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_ptr + 192);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const Tile tl = tiles[blockIdx.x];
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(bar + 8 * s, 1);
+      mbar_init(bar + 64 + 8 * s, 1);
+    }
+    mbar_init(bar + 128, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const int nk = K / C::BK;
+  const int rowA = tl.type * rows_per_type + tl.m0;
+
+  if (warp == 0 && lane == 0) {
+    // producer
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % C::STAGES;
+      const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
+      if (!mbar_wait(bar + 64 + 8 * s, ph ^ 1u, err, ERR_TMA_WAIT)) break;
+      mbar_expect_tx(bar + 8 * s, C::STAGE_BYTES);
+      tma_load_2d(sA0 + s * C::A_BYTES, &tmA, kb * C::BK, rowA, bar + 8 * s);
+      tma_load_2d(sB0 + s * C::B_BYTES, &tmB, kb * C::BK, tl.n0, bar + 8 * s);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    constexpr uint32_t fmt = sizeof(T) == 2 ? 1u : 2u;
+    constexpr uint32_t idesc = mma_idesc(fmt, C::BM, C::BN);
+    bool ok = true;
+    for (int kb = 0; kb < nk && ok; ++kb) {
+      const int s = kb % C::STAGES;
+      const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
+      if (!mbar_wait(bar + 8 * s, ph, err, ERR_MMA_WAIT)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int kk = 0; kk < C::BK / C::UK; ++kk) {
+        const uint64_t ad = sw128_desc(sA0 + s * C::A_BYTES + kk * 32);
+        const uint64_t bd = sw128_desc(sB0 + s * C::B_BYTES + kk * 32);
+        mma_issue<T>(tmem, ad, bd, idesc, (kb | kk) != 0 ? 1u : 0u);
+      }
+      mma_commit(bar + 64 + 8 * s);
+    }
+    mma_commit(bar + 128);
+  }
+  __syncwarp();
+  // epilogue: warp w owns TMEM lanes 32w..32w+31 (output rows m)
+  const bool ready = mbar_wait(bar + 128, 0, err, ERR_ACC_WAIT);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ready) {
+    const int m = tl.m0 + warp * 32 + lane;
+    for (int c0 = 0; c0 < C::BN; c0 += 16) {
+      if (tl.n0 + c0 >= tl.nend) break;
+      uint32_t r[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+      if (m < mlimit) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int n = tl.n0 + c0 + j;
+          if (n < tl.nend) Y[(size_t)n * ldy + m] = __uint_as_float(r[j]);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+// ----------------------------------------------------------------------------------------
+// Host side: tensor maps through the driver entry point (no link-time libcuda dependency).
+// ----------------------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    DD_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !p) throw Error(DD_ECUDA, "cuTensorMapEncodeTiled unavailable");
+    fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+static void make_tmap(CUtensorMap* tm, void* base, bool bf16, int inner, long long rows, int box_inner, int box_rows) {
+  const int es = bf16 ? 2 : 4;
+  cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)inner * es};
+  cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode_fn()(tm, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base,
+                           dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error(DD_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+}
+
+template <typename T>
+static void launch_tc(const CUtensorMap* tA, const CUtensorMap* tB, const Tile* tiles, int ntiles, int K,
+                      int mlimit, int rows_per_type, float* Y, int ldy, int* err, const PcgState* st,
+                      cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    DD_CUDA(cudaFuncSetAttribute(k_tc_gemm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<T>::SMEM));
+    attr = true;
+  }
+  k_tc_gemm<T><<<ntiles, 128, TcCfg<T>::SMEM, s>>>(*tA, *tB, tiles, K, mlimit, rows_per_type, Y, ldy, err, st);
+  DD_CUDA(cudaGetLastError());
+}
+
+// ----------------------------------------------------------------------------------------
+// Rounded local inverses from the banded factors: column col of A_T^{-1} (identity
+// right-hand side) = row col (symmetric), rounded to BF16 or TF32.
+// ----------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T round_to(double v);
+template <>
+__device__ __forceinline__ __nv_bfloat16 round_to<__nv_bfloat16>(double v) {
+  return __double2bfloat16(v);
+}
+template <>
+__device__ __forceinline__ float round_to<float>(double v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"((float)v));
+  return __uint_as_float(r);
+}
+
+template <typename T>
+__global__ void k_local_inverse(const int* __restrict__ nloc, int nmax, int b, const double* __restrict__ CB,
+                                const double* __restrict__ RB, const double* __restrict__ inv, int ntypes, int kpad,
+                                T* __restrict__ out) {
+  extern __shared__ double xs_all[];
+  const int wpb = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long job = (long long)blockIdx.x * wpb + wid;
+  if (job >= (long long)ntypes * nmax) return;
+  const int ty = (int)(job / nmax), col = (int)(job % nmax);
+  const int n = nloc[ty];
+  if (col >= n) return;
+  double* xs = xs_all + (size_t)wid * nmax;
+  for (int k = lane; k < n; k += 32) xs[k] = (k == col) ? 1.0 : 0.0;
+  const size_t off = (size_t)ty * nmax;
+  warp_band_solve(xs, n, b, CB + off * (b + 1), RB + off * (b + 1), inv + off);
+  T* row = out + ((size_t)ty * kpad + col) * kpad;
+  for (int k = lane; k < n; k += 32) row[k] = round_to<T>(xs[k]);
+}
+
+// R_i r rounded, subdomain rows in type-sorted order, zero tail up to kpad
+template <typename T>
+__global__ void k_pack(Geo g, const Sub* __restrict__ subs, const int* __restrict__ slot_of,
+                       const double* __restrict__ r, int kpad, T* __restrict__ out, const PcgState* st) {
+  if (st != nullptr && st->done) return;
+  const int s = blockIdx.x;
+  const Sub sb = subs[s];
+  T* row = out + (size_t)slot_of[s] * kpad;
+  for (int k = threadIdx.x; k < kpad; k += blockDim.x) {
+    double v = 0.0;
+    if (k < sb.nloc) {
+      const int sj = k % g.nyi, cc = k / g.nyi;
+      const int c1 = cc / sb.w2, c2 = cc % sb.w2;
+      long long idx;
+      if (g.p == 1) idx = (long long)(sb.lo1 + c1) * g.Ypad + sj;
+      else idx = ((long long)(sb.lo1 + c1) * g.ncx + (sb.lo2 + c2)) * g.Ypad + sj;
+      v = r[idx];
+    }
+    row[k] = round_to<T>(v);
+  }
+}
+
+struct GemmPlan {
+  CUtensorMap tA, tB;
+  Tile* tiles = nullptr;
+  int ntiles = 0;
+  bool bf16 = true;
+};
+
+int gemm_setup(dd_ctx* c) {
+  const Geo& g = c->g;
+  const bool bf16 = c->grid.precision == DD_PREC_BF16;
+  const int es = bf16 ? 2 : 4;
+  const int kpad = c->kpad;
+  if (!c->Ainv) {
+    c->Ainv = dev_alloc(c, (size_t)es * c->ntypes * kpad * kpad);
+    c->Rpack = dev_alloc(c, (size_t)es * g.nsub * kpad);
+    c->Y32 = (float*)dev_alloc(c, sizeof(float) * (size_t)g.nsub * kpad);
+  } else {
+    DD_CUDA(cudaMemsetAsync(c->Ainv, 0, (size_t)es * c->ntypes * kpad * kpad, c->stream));
+  }
+  // local inverses
+  int* nloc = nullptr;
+  DD_CUDA(cudaMallocAsync(&nloc, sizeof(int) * c->ntypes, c->stream));
+  DD_CUDA(cudaMemcpyAsync(nloc, c->type_nloc, sizeof(int) * c->ntypes, cudaMemcpyHostToDevice, c->stream));
+  int wpb = (int)((200 * 1024) / ((size_t)c->nloc_max * sizeof(double)));
+  wpb = wpb > 8 ? 8 : (wpb < 1 ? 1 : wpb);
+  const size_t smem = sizeof(double) * (size_t)wpb * c->nloc_max;
+  const long long jobs = (long long)c->ntypes * c->nloc_max;
+  const int nb = (int)((jobs + wpb - 1) / wpb);
+  if (bf16) {
+    DD_CUDA(cudaFuncSetAttribute(k_local_inverse<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 220 * 1024));
+    k_local_inverse<__nv_bfloat16><<<nb, 32 * wpb, smem, c->stream>>>(
+        nloc, c->nloc_max, c->band, c->bandCB, c->bandRB, c->bandInv, c->ntypes, kpad, (__nv_bfloat16*)c->Ainv);
+  } else {
+    DD_CUDA(cudaFuncSetAttribute(k_local_inverse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    k_local_inverse<float><<<nb, 32 * wpb, smem, c->stream>>>(nloc, c->nloc_max, c->band, c->bandCB, c->bandRB,
+                                                              c->bandInv, c->ntypes, kpad, (float*)c->Ainv);
+  }
+  DD_CUDA(cudaGetLastError());
+  DD_CUDA(cudaFreeAsync(nloc, c->stream));
+  // plan: tensor maps and tile list
+  GemmPlan* plan = reinterpret_cast<GemmPlan*>(c->tmapA);
+  if (!plan) {
+    plan = new GemmPlan();
+    c->tmapA = plan;
+  }
+  plan->bf16 = bf16;
+  const int BK = bf16 ? TcCfg<__nv_bfloat16>::BK : TcCfg<float>::BK;
+  make_tmap(&plan->tA, c->Ainv, bf16, kpad, (long long)c->ntypes * kpad, BK, 128);
+  make_tmap(&plan->tB, c->Rpack, bf16, kpad, g.nsub, BK, 256);
+  std::vector<Tile> tl;
+  const int mt = (kpad + 127) / 128;
+  for (int t = 0; t < c->ntypes; ++t) {
+    const int first = c->type_first[t], cnt = c->type_count[t];
+    for (int n0 = 0; n0 < cnt; n0 += 256)
+      for (int m = 0; m < mt; ++m) tl.push_back(Tile{t, m * 128, first + n0, first + cnt});
+  }
+  if (!plan->tiles || plan->ntiles < (int)tl.size()) plan->tiles = (Tile*)dev_alloc(c, sizeof(Tile) * tl.size());
+  plan->ntiles = (int)tl.size();
+  DD_CUDA(cudaMemcpyAsync(plan->tiles, tl.data(), sizeof(Tile) * tl.size(), cudaMemcpyHostToDevice, c->stream));
+  DD_CUDA(cudaStreamSynchronize(c->stream));
+  c->gemm_ok = 1;
+  return DD_OK;
+}
+
+void launch_pack(dd_ctx* c, const double* r, cudaStream_t s) {
+  const Geo& g = c->g;
+  if (c->grid.precision == DD_PREC_BF16)
+    k_pack<__nv_bfloat16><<<g.nsub, 256, 0, s>>>(g, c->subs, c->slot_of_sub, r, c->kpad, (__nv_bfloat16*)c->Rpack,
+                                                 c->st);
+  else
+    k_pack<float><<<g.nsub, 256, 0, s>>>(g, c->subs, c->slot_of_sub, r, c->kpad, (float*)c->Rpack, c->st);
+  DD_CUDA(cudaGetLastError());
+}
+
+int launch_gemm(dd_ctx* c, cudaStream_t s) {
+  GemmPlan* plan = reinterpret_cast<GemmPlan*>(c->tmapA);
+  if (!c->gemm_ok || !plan) return DD_ESTATE;
+  if (plan->bf16)
+    launch_tc<__nv_bfloat16>(&plan->tA, &plan->tB, plan->tiles, plan->ntiles, c->kpad, c->kpad, c->kpad, c->Y32,
+                             c->kpad, c->dev_err + 8, c->st, s);
+  else
+    launch_tc<float>(&plan->tA, &plan->tB, plan->tiles, plan->ntiles, c->kpad, c->kpad, c->kpad, c->Y32, c->kpad,
+                     c->dev_err + 8, c->st, s);
+  return DD_OK;
+}
+
+void gemm_free(dd_ctx* c) {
+  delete reinterpret_cast<GemmPlan*>(c->tmapA);
+  c->tmapA = nullptr;
+}
+
+}  // namespace dd
+
+// ------------------------------------------------------------------------------------------
+// Diagnostic entry point: D[n][m] = sum_k A[m][k] B[n][k] through the same kernel.
+// ------------------------------------------------------------------------------------------
+extern "C" int dd_tc_gemm_test(int precision, int M, int N, int K, const float* A_host, const float* B_host,
+                               float* D_host) {
+  using namespace dd;
+  if (precision != DD_PREC_BF16 && precision != DD_PREC_TF32) return DD_EINVAL;
+  if (M < 1 || N < 1 || K < 1 || !A_host || !B_host || !D_host) return DD_EINVAL;
+  const bool bf16 = precision == DD_PREC_BF16;
+  const int es = bf16 ? 2 : 4;
+  const int kpad = (K + 63) / 64 * 64;
+  const int mpad = (M + 127) / 128 * 128;
+  void *dA = nullptr, *dB = nullptr;
+  float *dD = nullptr, *hA = nullptr;
+  int* derr = nullptr;
+  Tile* dt = nullptr;
+  cudaStream_t s = nullptr;
+  int rc = DD_OK;
+  try {
+    DD_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    DD_CUDA(cudaMalloc(&dA, (size_t)es * mpad * kpad));
+    DD_CUDA(cudaMalloc(&dB, (size_t)es * N * kpad));
+    DD_CUDA(cudaMalloc(&dD, sizeof(float) * (size_t)N * mpad));
+    DD_CUDA(cudaMalloc(&derr, sizeof(int)));
+    DD_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), s));
+    // BF16 operands rounded to nearest even on the host; TF32 operands passed as FP32
+    std::vector<uint16_t> a16, b16;
+    std::vector<float> a32, b32;
+    auto to_bf16 = [](float f) -> uint16_t {
+      uint32_t u;
+      std::memcpy(&u, &f, 4);
+      const uint32_t lsb = (u >> 16) & 1u;
+      u += 0x7FFFu + lsb;
+      return (uint16_t)(u >> 16);
+    };
+    if (bf16) {
+      a16.assign((size_t)mpad * kpad, 0);
+      b16.assign((size_t)N * kpad, 0);
+      for (int m = 0; m < M; ++m)
+        for (int k = 0; k < K; ++k) a16[(size_t)m * kpad + k] = to_bf16(A_host[(size_t)m * K + k]);
+      for (int n = 0; n < N; ++n)
+        for (int k = 0; k < K; ++k) b16[(size_t)n * kpad + k] = to_bf16(B_host[(size_t)n * K + k]);
+      DD_CUDA(cudaMemcpyAsync(dA, a16.data(), a16.size() * 2, cudaMemcpyHostToDevice, s));
+      DD_CUDA(cudaMemcpyAsync(dB, b16.data(), b16.size() * 2, cudaMemcpyHostToDevice, s));
+    } else {
+      a32.assign((size_t)mpad * kpad, 0.f);
+      b32.assign((size_t)N * kpad, 0.f);
+      for (int m = 0; m < M; ++m)
+        for (int k = 0; k < K; ++k) a32[(size_t)m * kpad + k] = A_host[(size_t)m * K + k];
+      for (int n = 0; n < N; ++n)
+        for (int k = 0; k < K; ++k) b32[(size_t)n * kpad + k] = B_host[(size_t)n * K + k];
+      DD_CUDA(cudaMemcpyAsync(dA, a32.data(), a32.size() * 4, cudaMemcpyHostToDevice, s));
+      DD_CUDA(cudaMemcpyAsync(dB, b32.data(), b32.size() * 4, cudaMemcpyHostToDevice, s));
+    }
+    CUtensorMap tA, tB;
+    const int BK = bf16 ? TcCfg<__nv_bfloat16>::BK : TcCfg<float>::BK;
+    make_tmap(&tA, dA, bf16, kpad, mpad, BK, 128);
+    make_tmap(&tB, dB, bf16, kpad, N, BK, 256);
+    std::vector<Tile> tl;
+    for (int n0 = 0; n0 < N; n0 += 256)
+      for (int m0 = 0; m0 < mpad; m0 += 128) tl.push_back(Tile{0, m0, n0, N});
+    DD_CUDA(cudaMalloc(&dt, sizeof(Tile) * tl.size()));
+    DD_CUDA(cudaMemcpyAsync(dt, tl.data(), sizeof(Tile) * tl.size(), cudaMemcpyHostToDevice, s));
+    if (bf16)
+      launch_tc<__nv_bfloat16>(&tA, &tB, dt, (int)tl.size(), kpad, mpad, 0, dD, mpad, derr, nullptr, s);
+    else
+      launch_tc<float>(&tA, &tB, dt, (int)tl.size(), kpad, mpad, 0, dD, mpad, derr, nullptr, s);
+    std::vector<float> hD((size_t)N * mpad);
+    int herr = 0;
+    DD_CUDA(cudaMemcpyAsync(hD.data(), dD, sizeof(float) * hD.size(), cudaMemcpyDeviceToHost, s));
+    DD_CUDA(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DD_CUDA(cudaStreamSynchronize(s));
+    for (int n = 0; n < N; ++n)
+      for (int m = 0; m < M; ++m) D_host[(size_t)n * M + m] = hD[(size_t)n * mpad + m];
+    if (herr) rc = DD_ETIMEOUT;
+  } catch (const Error& e) {
+    rc = e.code;
+  }
+  (void)hA;
+  if (dA) cudaFree(dA);
+  if (dB) cudaFree(dB);
+  if (dD) cudaFree(dD);
+  if (derr) cudaFree(derr);
+  if (dt) cudaFree(dt);
+  if (s) cudaStreamDestroy(s);
+  return rc;
+}

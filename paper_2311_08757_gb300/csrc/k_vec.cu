@@ -1,0 +1,564 @@
+// Stencil tables, the matrix-free Q1 operator, and the PCG vector kernels.
+//
+// A = K + M_V and M of the Q1 discretisation (Sec. 2, discrete weak form) are stored as
+// periodic stencil tables: because the box mesh is made of translated copies of the cell
+// mesh (Sec. 2) and V is 1-periodic in x (assumption A1), the row of node (a, j) depends
+// only on (a mod n, j).  tab[tap][cls] holds the coupling of class cls to its neighbour at
+// offset tap in {-1,0,1}^d; A_sigma = A - sigma M (Sec. 1.1) is a third table.
+#include "dd_common.cuh"
+
+namespace dd {
+
+__constant__ double c_gpt[kMaxQ];
+__constant__ double c_gwt[kMaxQ];
+
+int grid_blocks(long long work, int threads, int max_per_sm) {
+  long long b = (work + threads - 1) / threads;
+  long long cap = 152LL * max_per_sm;
+  if (b > cap) b = cap;
+  if (b > kMaxRedBlocks) b = kMaxRedBlocks;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+// ----------------------------------------------------------------------------------------
+// S4: stencil tables from V at the cell's Gauss points.
+// Element (ex, ey) with local node (bx, by) in {0,1}^d; Q1 basis N_b(xi) = prod N1_{b_k}(xi_k),
+// N1_0 = 1 - t, N1_1 = t.  Exact element matrices K^e = sum_k (x)_{ax} (ax == k ? K1 : M1),
+// M^e = (x) M1 with K1 = [[1,-1],[-1,1]]/h, M1 = [[2,1],[1,2]] h/6, and
+// M_V^e[a,b] = h^d sum_q W_q V_q N_a(xi_q) N_b(xi_q).
+// ----------------------------------------------------------------------------------------
+template <int P>
+__global__ void k_build_tables(Geo g, const double* __restrict__ V, double* tabA, double* tabM) {
+  constexpr int D = P + 1;
+  const long long total = (long long)g.ncls * g.ntap;
+  const double h = g.h;
+  const int Q = g.Q;
+  int nq = 1;
+  for (int k = 0; k < D; ++k) nq *= Q;
+  double hd = 1.0;
+  for (int k = 0; k < D; ++k) hd *= h;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int tap = (int)(t / g.ncls);
+    const int cls = (int)(t - (long long)tap * g.ncls);
+    const int slot = cls % g.Ypad;
+    const int cx = cls / g.Ypad;
+    if (slot >= g.nyi) {
+      tabA[t] = 0.0;
+      tabM[t] = 0.0;
+      continue;
+    }
+    const int j = slot + 1;
+    int c[2], dxs[2], dy;
+    if (P == 1) {
+      c[0] = cx;
+      dxs[0] = tap / 3 - 1;
+      dy = tap % 3 - 1;
+    } else {
+      c[0] = cx / g.n;
+      c[1] = cx % g.n;
+      dxs[0] = tap / 9 - 1;
+      dxs[1] = (tap / 3) % 3 - 1;
+      dy = tap % 3 - 1;
+    }
+    double sA = 0.0, sM = 0.0;
+    // elements around the node: local position l per axis (node = element origin + l)
+    for (int mask = 0; mask < (1 << D); ++mask) {
+      int la[3], lb[3];
+      bool ok = true;
+      for (int k = 0; k < P; ++k) {
+        la[k] = (mask >> (D - 1 - k)) & 1;
+        lb[k] = la[k] + dxs[k];
+        if (lb[k] < 0 || lb[k] > 1) ok = false;
+      }
+      la[P] = mask & 1;
+      lb[P] = la[P] + dy;
+      if (lb[P] < 0 || lb[P] > 1) ok = false;
+      if (!ok) continue;
+      const int ey = j - la[P];   // 0 <= ey <= ny-1
+      int e = 0;
+      for (int k = 0; k < P; ++k) {
+        int ex = c[k] - la[k];
+        ex = (ex % g.n + g.n) % g.n;
+        e = e * g.n + ex;
+      }
+      e = e * g.ny + ey;
+      // K^e and M^e
+      double me = 1.0, ke = 0.0;
+      for (int ax = 0; ax < D; ++ax) me *= (la[ax] == lb[ax] ? 2.0 : 1.0) * h / 6.0;
+      for (int kk = 0; kk < D; ++kk) {
+        double t2 = 1.0;
+        for (int ax = 0; ax < D; ++ax) {
+          if (ax == kk) t2 *= (la[ax] == lb[ax] ? 1.0 : -1.0) / h;
+          else t2 *= (la[ax] == lb[ax] ? 2.0 : 1.0) * h / 6.0;
+        }
+        ke += t2;
+      }
+      // M_V^e
+      double mv = 0.0;
+      for (int iq = 0; iq < nq; ++iq) {
+        int rem = iq;
+        double wq = 1.0, na = 1.0, nb = 1.0;
+        for (int ax = D - 1; ax >= 0; --ax) {
+          const int qa = rem % Q;
+          rem /= Q;
+          const double xi = c_gpt[qa];
+          wq *= c_gwt[qa];
+          na *= la[ax] ? xi : 1.0 - xi;
+          nb *= lb[ax] ? xi : 1.0 - xi;
+        }
+        mv = fma(wq * V[(size_t)e * nq + iq], na * nb, mv);
+      }
+      sA += ke + hd * mv;
+      sM += me;
+    }
+    tabA[t] = sA;
+    tabM[t] = sM;
+  }
+}
+
+void launch_build_tables(dd_ctx* c) {
+  const Geo& g = c->g;
+  // Gauss-Legendre points and weights on [0, 1] (closed forms).
+  double pt[kMaxQ] = {0}, wt[kMaxQ] = {0};
+  const int Q = g.Q;
+  if (Q == 1) {
+    pt[0] = 0.5; wt[0] = 1.0;
+  } else if (Q == 2) {
+    const double s = 0.5 / sqrt(3.0);
+    pt[0] = 0.5 - s; pt[1] = 0.5 + s; wt[0] = wt[1] = 0.5;
+  } else if (Q == 3) {
+    const double s = 0.5 * sqrt(0.6);
+    pt[0] = 0.5 - s; pt[1] = 0.5; pt[2] = 0.5 + s;
+    wt[0] = wt[2] = 5.0 / 18.0; wt[1] = 8.0 / 18.0;
+  } else {
+    const double a = sqrt(3.0 / 7.0 - 2.0 / 7.0 * sqrt(6.0 / 5.0));
+    const double b = sqrt(3.0 / 7.0 + 2.0 / 7.0 * sqrt(6.0 / 5.0));
+    const double wa = (18.0 + sqrt(30.0)) / 36.0, wb = (18.0 - sqrt(30.0)) / 36.0;
+    pt[0] = 0.5 - 0.5 * b; pt[1] = 0.5 - 0.5 * a; pt[2] = 0.5 + 0.5 * a; pt[3] = 0.5 + 0.5 * b;
+    wt[0] = wt[3] = 0.5 * wb; wt[1] = wt[2] = 0.5 * wa;
+  }
+  DD_CUDA(cudaMemcpyToSymbolAsync(c_gpt, pt, sizeof(pt), 0, cudaMemcpyHostToDevice, c->stream));
+  DD_CUDA(cudaMemcpyToSymbolAsync(c_gwt, wt, sizeof(wt), 0, cudaMemcpyHostToDevice, c->stream));
+  const long long total = (long long)g.ncls * g.ntap;
+  const int nb = grid_blocks(total, kThreads);
+  if (g.p == 1) k_build_tables<1><<<nb, kThreads, 0, c->stream>>>(g, c->Vqp, c->tabA, c->tabM);
+  else k_build_tables<2><<<nb, kThreads, 0, c->stream>>>(g, c->Vqp, c->tabA, c->tabM);
+  DD_CUDA(cudaGetLastError());
+}
+
+__global__ void k_tabS(long long n, const double* __restrict__ A, const double* __restrict__ M, double sigma,
+                       double* S) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    S[t] = A[t] - sigma * M[t];
+}
+
+void launch_tabS(dd_ctx* c, double sigma) {
+  const long long n = (long long)c->g.ncls * c->g.ntap;
+  k_tabS<<<grid_blocks(n, kThreads), kThreads, 0, c->stream>>>(n, c->tabA, c->tabM, sigma, c->tabS);
+  DD_CUDA(cudaGetLastError());
+}
+
+// ----------------------------------------------------------------------------------------
+// K1: matrix-free operator y = T x (T = A_sigma, A or M) over the interior columns.
+// ----------------------------------------------------------------------------------------
+template <int P, bool DOT>
+__global__ void __launch_bounds__(kThreads) k_stencil(Geo g, const double* __restrict__ tab,
+                                                      const double* __restrict__ x, double* __restrict__ y,
+                                                      double* partials, unsigned* counter, double* out) {
+  const long long total = (long long)g.nxi * (P == 2 ? g.nxi : 1) * g.Ypad;
+  double acc[1] = {0.0};
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    Node nd = node_of<P>(g, t);
+    const int cls = cls_of<P>(g, nd);
+    const double v = stencil_at<P>(g, tab, x, nd.idx, cls);
+    y[nd.idx] = v;
+    if (DOT) acc[0] = fma(x[nd.idx], v, acc[0]);
+  }
+  if (DOT) {
+    double tot[1];
+    if (grid_sum_last<1>(acc, partials, counter, tot) && threadIdx.x == 0) *out = tot[0];
+  }
+}
+
+static long long interior_work(const Geo& g) {
+  return (long long)g.nxi * (g.p == 2 ? g.nxi : 1) * g.Ypad;
+}
+
+void launch_stencil(dd_ctx* c, const double* tab, const double* x, double* y, cudaStream_t s) {
+  const Geo& g = c->g;
+  const int nb = grid_blocks(interior_work(g), kThreads);
+  if (g.p == 1) k_stencil<1, false><<<nb, kThreads, 0, s>>>(g, tab, x, y, nullptr, nullptr, nullptr);
+  else k_stencil<2, false><<<nb, kThreads, 0, s>>>(g, tab, x, y, nullptr, nullptr, nullptr);
+  DD_CUDA(cudaGetLastError());
+}
+
+void launch_stencil_dot(dd_ctx* c, const double* tab, const double* x, double* y, double* out,
+                        unsigned* counter, cudaStream_t s) {
+  const Geo& g = c->g;
+  const int nb = grid_blocks(interior_work(g), kThreads);
+  if (g.p == 1) k_stencil<1, true><<<nb, kThreads, 0, s>>>(g, tab, x, y, c->red, counter, out);
+  else k_stencil<2, true><<<nb, kThreads, 0, s>>>(g, tab, x, y, c->red, counter, out);
+  DD_CUDA(cudaGetLastError());
+}
+
+// ----------------------------------------------------------------------------------------
+// Layout conversion between the ABI order (interior nodes, y fastest) and the padded order.
+// ----------------------------------------------------------------------------------------
+template <int P, bool TO_PAD>
+__global__ void k_pad(Geo g, const double* __restrict__ src, double* __restrict__ dst) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < g.ndof;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long col = t / g.nyi;
+    const int j = (int)(t - col * g.nyi);
+    long long pidx;
+    if (P == 1) pidx = (col + 1) * g.Ypad + j;
+    else {
+      const long long a1 = col / g.nxi + 1, a2 = col % g.nxi + 1;
+      pidx = (a1 * g.ncx + a2) * g.Ypad + j;
+    }
+    if (TO_PAD) dst[pidx] = src[t];
+    else dst[t] = src[pidx];
+  }
+}
+
+void launch_pad(dd_ctx* c, const double* u, double* v, cudaStream_t s) {
+  const Geo& g = c->g;
+  const int nb = grid_blocks(g.ndof, kThreads);
+  if (g.p == 1) k_pad<1, true><<<nb, kThreads, 0, s>>>(g, u, v);
+  else k_pad<2, true><<<nb, kThreads, 0, s>>>(g, u, v);
+  DD_CUDA(cudaGetLastError());
+}
+
+void launch_unpad(dd_ctx* c, const double* v, double* u, cudaStream_t s) {
+  const Geo& g = c->g;
+  const int nb = grid_blocks(g.ndof, kThreads);
+  if (g.p == 1) k_pad<1, false><<<nb, kThreads, 0, s>>>(g, v, u);
+  else k_pad<2, false><<<nb, kThreads, 0, s>>>(g, v, u);
+  DD_CUDA(cudaGetLastError());
+}
+
+__global__ void k_check_finite(const double* __restrict__ v, long long n, int* flag) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    if (!isfinite(v[t])) atomicOr(flag, 1);
+}
+
+void launch_check_finite(const double* v, long long n, int* flag, cudaStream_t s) {
+  k_check_finite<<<grid_blocks(n, kThreads), kThreads, 0, s>>>(v, n, flag);
+  DD_CUDA(cudaGetLastError());
+}
+
+// ----------------------------------------------------------------------------------------
+// PCG (Hestenes-Stiefel; flexible Polak-Ribiere beta when the preconditioner is rounded).
+// The scalars live in PcgState on the device; every kernel returns at once when the
+// iteration is marked done, so a fixed block of iterations can be replayed as a graph.
+// ----------------------------------------------------------------------------------------
+
+// r = b - A_sigma x, rr0 = (r, r), tol2 = rtol^2 rr0 (rtol^2 preset in tol2 by the host).
+template <int P>
+__global__ void __launch_bounds__(kThreads) k_pcg_init(Geo g, const double* __restrict__ tab,
+                                                       const double* __restrict__ x,
+                                                       const double* __restrict__ b, double* __restrict__ r,
+                                                       PcgState* st, double* partials, unsigned* counter) {
+  const long long total = (long long)g.nxi * (P == 2 ? g.nxi : 1) * g.Ypad;
+  double acc[1] = {0.0};
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    Node nd = node_of<P>(g, t);
+    const int cls = cls_of<P>(g, nd);
+    const double v = b[nd.idx] - stencil_at<P>(g, tab, x, nd.idx, cls);
+    r[nd.idx] = v;
+    acc[0] = fma(v, v, acc[0]);
+  }
+  double tot[1];
+  if (grid_sum_last<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
+    st->rr0 = tot[0];
+    st->rr = tot[0];
+    st->tol2 = st->tol2 * tot[0];
+    st->iter = 0;
+    st->beta = 0.0;
+    st->status = 0;
+    st->done = 0;
+    if (!isfinite(tot[0])) { st->status = DD_ENAN; st->done = 1; }
+    else if (tot[0] == 0.0) st->done = 1;
+  }
+}
+
+void launch_pcg_init(dd_ctx* c, const double* b, cudaStream_t s) {
+  const Geo& g = c->g;
+  const int nb = grid_blocks(interior_work(g), kThreads);
+  if (g.p == 1)
+    k_pcg_init<1><<<nb, kThreads, 0, s>>>(g, c->tabS, c->x, b, c->r, c->st, c->red, c->cnt + CNT_INIT);
+  else
+    k_pcg_init<2><<<nb, kThreads, 0, s>>>(g, c->tabS, c->x, b, c->r, c->st, c->red, c->cnt + CNT_INIT);
+  DD_CUDA(cudaGetLastError());
+}
+
+// p = z + beta p (whole padded vector; boundary columns and pads stay zero).
+__global__ void __launch_bounds__(kThreads) k_pupdate(long long n, const double* __restrict__ z,
+                                                      double* __restrict__ p, const PcgState* st) {
+  if (st->done) return;
+  const double beta = st->beta;
+  const double2* z2 = reinterpret_cast<const double2*>(z);
+  double2* p2 = reinterpret_cast<double2*>(p);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n / 2;
+       t += (long long)gridDim.x * blockDim.x) {
+    double2 a = z2[t], b = p2[t];
+    b.x = fma(beta, b.x, a.x);
+    b.y = fma(beta, b.y, a.y);
+    p2[t] = b;
+  }
+}
+
+void launch_pupdate(dd_ctx* c, cudaStream_t s) {
+  const long long n = c->g.plen;
+  k_pupdate<<<grid_blocks(n / 2, kThreads), kThreads, 0, s>>>(n, c->z, c->p, c->st);
+  DD_CUDA(cudaGetLastError());
+}
+
+// q = A_sigma p, pq = (p, q), alpha = rho / pq.
+template <int P>
+__global__ void __launch_bounds__(kThreads) k_matvec_pq(Geo g, const double* __restrict__ tab,
+                                                        const double* __restrict__ p, double* __restrict__ q,
+                                                        PcgState* st, double* partials, unsigned* counter) {
+  if (st->done) return;
+  const long long total = (long long)g.nxi * (P == 2 ? g.nxi : 1) * g.Ypad;
+  double acc[1] = {0.0};
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    Node nd = node_of<P>(g, t);
+    const int cls = cls_of<P>(g, nd);
+    const double v = stencil_at<P>(g, tab, p, nd.idx, cls);
+    q[nd.idx] = v;
+    acc[0] = fma(p[nd.idx], v, acc[0]);
+  }
+  double tot[1];
+  if (grid_sum_last<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
+    const double pq = tot[0];
+    st->pq = pq;
+    if (!(pq > 0.0)) {
+      st->status = isfinite(pq) ? DD_ENOTSPD : DD_ENAN;
+      st->done = 1;
+    } else {
+      st->alpha = st->rho / pq;
+    }
+  }
+}
+
+void launch_matvec_pq(dd_ctx* c, cudaStream_t s) {
+  const Geo& g = c->g;
+  const int nb = grid_blocks(interior_work(g), kThreads);
+  if (g.p == 1) k_matvec_pq<1><<<nb, kThreads, 0, s>>>(g, c->tabS, c->p, c->q, c->st, c->red, c->cnt + CNT_PQ);
+  else k_matvec_pq<2><<<nb, kThreads, 0, s>>>(g, c->tabS, c->p, c->q, c->st, c->red, c->cnt + CNT_PQ);
+  DD_CUDA(cudaGetLastError());
+}
+
+// x += alpha p, r -= alpha q, rr = (r, r); stop test ||r|| <= rtol ||r0|| (Sec. 4.1).
+__global__ void __launch_bounds__(kThreads) k_xr_update(long long n, const double* __restrict__ p,
+                                                        const double* __restrict__ q, double* __restrict__ x,
+                                                        double* __restrict__ r, PcgState* st,
+                                                        double* partials, unsigned* counter) {
+  if (st->done) return;
+  const double alpha = st->alpha;
+  const double2* p2 = reinterpret_cast<const double2*>(p);
+  const double2* q2 = reinterpret_cast<const double2*>(q);
+  double2* x2 = reinterpret_cast<double2*>(x);
+  double2* r2 = reinterpret_cast<double2*>(r);
+  double acc[1] = {0.0};
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n / 2;
+       t += (long long)gridDim.x * blockDim.x) {
+    double2 pv = p2[t], qv = q2[t], xv = x2[t], rv = r2[t];
+    xv.x = fma(alpha, pv.x, xv.x);
+    xv.y = fma(alpha, pv.y, xv.y);
+    rv.x = fma(-alpha, qv.x, rv.x);
+    rv.y = fma(-alpha, qv.y, rv.y);
+    x2[t] = xv;
+    r2[t] = rv;
+    acc[0] = fma(rv.x, rv.x, acc[0]);
+    acc[0] = fma(rv.y, rv.y, acc[0]);
+  }
+  double tot[1];
+  if (grid_sum_last<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
+    const double rr = tot[0];
+    st->rr = rr;
+    st->iter += 1;
+    if (!isfinite(rr)) {
+      st->status = DD_ENAN;
+      st->done = 1;
+    } else if (rr <= st->tol2) {
+      st->done = 1;
+    } else if (st->iter >= st->maxit) {
+      st->status = DD_EMAXIT;
+      st->done = 1;
+    }
+  }
+}
+
+void launch_xr_update(dd_ctx* c, cudaStream_t s) {
+  const long long n = c->g.plen;
+  k_xr_update<<<grid_blocks(n / 2, kThreads), kThreads, 0, s>>>(n, c->p, c->q, c->x, c->r, c->st, c->red,
+                                                                 c->cnt + CNT_RR);
+  DD_CUDA(cudaGetLastError());
+}
+
+// ----------------------------------------------------------------------------------------
+// K5: prolong-sum of the preconditioner (Sec. 3.1):
+//   z = sum_i R_i^T y_i + sum_i (D_i R_i psi) u0_i
+// gathered per node from its (at most 2^p) owning subdomains, deterministic order;
+// fused with (r, z) and (q, z) and the beta update.
+//   mode 0: preconditioner only (no scalars); 1: PCG start (rho = (r,z), beta = 0);
+//   2: PCG iteration (beta standard or flexible).
+// ----------------------------------------------------------------------------------------
+template <int P, typename TY>
+__global__ void __launch_bounds__(kThreads) k_prolong(Geo g, const Sub* __restrict__ subs,
+                                                      const int* __restrict__ slot_of,
+                                                      const TY* __restrict__ Y, int kpad,
+                                                      const double* __restrict__ wT,
+                                                      const double* __restrict__ u0, int coarse,
+                                                      const double* __restrict__ r, const double* __restrict__ q,
+                                                      double* __restrict__ z, int mode, PcgState* st,
+                                                      double* partials, unsigned* counter) {
+  if (mode != 0 && st->done) return;
+  const long long total = (long long)g.nxi * (P == 2 ? g.nxi : 1) * g.Ypad;
+  double acc[2] = {0.0, 0.0};
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    Node nd = node_of<P>(g, t);
+    double v = 0.0;
+    if (nd.slot < g.nyi) {
+      int o1[2], l1[2], o2[2] = {0, 0}, l2[2] = {0, 0};
+      const int n1 = axis_owners(g, nd.a1, o1, l1);
+      int n2 = 1;
+      if (P == 2) n2 = axis_owners(g, nd.a2, o2, l2);
+      for (int i = 0; i < n1; ++i)
+        for (int k = 0; k < n2; ++k) {
+          const int s = (P == 1) ? o1[i] : o1[i] * g.L + o2[k];
+          const Sub sb = subs[s];
+          const int loc = ((P == 1) ? l1[i] : l1[i] * sb.w2 + l2[k]) * g.nyi + nd.slot;
+          v += (double)Y[(size_t)slot_of[s] * kpad + loc];
+          if (coarse) v = fma(wT[(size_t)sb.type * kpad + loc], u0[s], v);
+        }
+    }
+    z[nd.idx] = v;
+    if (mode != 0) {
+      acc[0] = fma(r[nd.idx], v, acc[0]);
+      acc[1] = fma(q[nd.idx], v, acc[1]);
+    }
+  }
+  if (mode == 0) return;
+  double tot[2];
+  if (grid_sum_last<2>(acc, partials, counter, tot) && threadIdx.x == 0) {
+    const double rz = tot[0];
+    if (!isfinite(rz)) {
+      st->status = DD_ENAN;
+      st->done = 1;
+      return;
+    }
+    if (mode == 1) {
+      st->beta = 0.0;
+    } else if (st->flexible) {
+      st->beta = -tot[1] / st->pq;   // (z_{k+1}, r_{k+1} - r_k)/(z_k, r_k) = -(z_{k+1}, q_k)/pq_k
+    } else {
+      st->beta = rz / st->rho;
+    }
+    st->rho = rz;
+    st->zq = tot[1];
+  }
+}
+
+void launch_prolong(dd_ctx* c, int mode, cudaStream_t s) {
+  const Geo& g = c->g;
+  const int nb = grid_blocks(interior_work(g), kThreads);
+  const int coarse = c->grid.coarse;
+  const bool f32 = (c->grid.precision != DD_PREC_FP64);
+#define DD_PROLONG(PP, TY, YP)                                                                          \
+  k_prolong<PP, TY><<<nb, kThreads, 0, s>>>(g, c->subs, c->slot_of_sub, YP, c->kpad, c->wT, c->u0,      \
+                                            coarse, c->r, c->q, c->z, mode, c->st, c->red, c->cnt + CNT_RZ)
+  if (g.p == 1) {
+    if (f32) DD_PROLONG(1, float, c->Y32); else DD_PROLONG(1, double, c->Y64);
+  } else {
+    if (f32) DD_PROLONG(2, float, c->Y32); else DD_PROLONG(2, double, c->Y64);
+  }
+#undef DD_PROLONG
+  DD_CUDA(cudaGetLastError());
+}
+
+// ----------------------------------------------------------------------------------------
+// K7: outer step of the inverse iteration (Sec. 2).
+//   normalize: given w (w1) and M w (w2): wMw = (w, Mw), s = sum w;
+//              x = w / sqrt(wMw) (sign so that sum x > 0), Mx = Mw / sqrt(wMw)
+//   residual : given A_sigma x (w3) and Mx (w2): mu = (x, A_sigma x);
+//              ||A_sigma x - mu M x||^2 and ||M x||^2
+// ----------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_outer_dots(long long n, const double* __restrict__ w,
+                                                         const double* __restrict__ Mw, OuterState* os,
+                                                         double* partials, unsigned* counter) {
+  double acc[2] = {0.0, 0.0};
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    acc[0] = fma(w[t], Mw[t], acc[0]);
+    acc[1] += w[t];
+  }
+  double tot[2];
+  if (grid_sum_last<2>(acc, partials, counter, tot) && threadIdx.x == 0) {
+    os->wMw = tot[0];
+    os->wsum = tot[1];
+    if (!(tot[0] > 0.0)) {
+      os->status = isfinite(tot[0]) ? DD_ENOTSPD : DD_ENAN;
+      os->scale = 0.0;
+    } else {
+      os->scale = (tot[1] < 0.0 ? -1.0 : 1.0) / sqrt(tot[0]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_outer_scale(long long n, double* __restrict__ x,
+                                                          const double* __restrict__ w, double* __restrict__ Mw,
+                                                          const OuterState* os) {
+  const double s = os->scale;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    x[t] = s * w[t];
+    Mw[t] *= s;
+  }
+}
+
+void launch_outer_normalize(dd_ctx* c, const double* w, double* Mw, double* xout, cudaStream_t s) {
+  const long long n = c->g.plen;
+  const int nb = grid_blocks(n, kThreads);
+  k_outer_dots<<<nb, kThreads, 0, s>>>(n, w, Mw, c->ost, c->red, c->cnt + CNT_OUTER0);
+  k_outer_scale<<<nb, kThreads, 0, s>>>(n, xout, w, Mw, c->ost);
+  DD_CUDA(cudaGetLastError());
+}
+
+__global__ void __launch_bounds__(kThreads) k_outer_res(long long n, const double* __restrict__ Ax,
+                                                        const double* __restrict__ Mx, OuterState* os,
+                                                        double* partials, unsigned* counter) {
+  const double mu = os->xAx;
+  double acc[2] = {0.0, 0.0};
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const double e = fma(-mu, Mx[t], Ax[t]);
+    acc[0] = fma(e, e, acc[0]);
+    acc[1] = fma(Mx[t], Mx[t], acc[1]);
+  }
+  double tot[2];
+  if (grid_sum_last<2>(acc, partials, counter, tot) && threadIdx.x == 0) {
+    os->rr = tot[0];
+    os->mm = tot[1];
+  }
+}
+
+void launch_outer_residual(dd_ctx* c, const double* xe, const double* Mx, double* Ax, cudaStream_t s) {
+  // Ax = A_sigma x and xAx = (x, A_sigma x); then the residual norms.
+  launch_stencil_dot(c, c->tabS, xe, Ax, &c->ost->xAx, c->cnt + CNT_OUTER1, s);
+  const long long n = c->g.plen;
+  k_outer_res<<<grid_blocks(n, kThreads), kThreads, 0, s>>>(n, Ax, Mx, c->ost, c->red, c->cnt + CNT_OUTER2);
+  DD_CUDA(cudaGetLastError());
+}
+
+}  // namespace dd

@@ -1,0 +1,84 @@
+"""Tensor-core local-solve contraction (tcgen05) and the mixed-precision path.
+
+The isolated kernel test uses small integers, which BF16/TF32 hold exactly and
+whose products and sums FP32 holds exactly, so the result must match a plain
+integer reference bit for bit, on shapes with ragged M, N and K tails.
+The mixed path is then checked against the FP64 oracle: the preconditioner to the
+rounding of its operands, the ground state to the 1e-10 eigenvalue target.
+"""
+import numpy as np
+import pytest
+
+import paper_2311_08757_gb300 as dd
+from ddinputs import WORKLOADS, Workload
+from oracle import solvers
+from tests.gpu_util import gpu_vec, host, make_solver, oracle_problem, rel_err
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(128, 256, 64), (200, 300, 130), (1209, 517, 1209), (96, 1000, 40), (1, 1, 1)]
+
+
+@pytest.mark.parametrize("prec", [dd.DD_PREC_BF16, dd.DD_PREC_TF32])
+@pytest.mark.parametrize("M,N,K", SHAPES)
+def test_tc_gemm_exact_on_integers(prec, M, N, K):
+    rng = np.random.default_rng(M * 7 + N * 3 + K)
+    A = rng.integers(-8, 9, size=(M, K)).astype(np.float32)
+    B = rng.integers(-8, 9, size=(N, K)).astype(np.float32)
+    D = np.zeros((N, M), dtype=np.float32)
+    dd.dd_tc_gemm_test(prec, A, B, D)
+    ref = (B.astype(np.int64) @ A.astype(np.int64).T).astype(np.float32)
+    assert np.array_equal(D, ref)
+
+
+@pytest.mark.parametrize("prec", [dd.DD_PREC_BF16, dd.DD_PREC_TF32])
+def test_tc_gemm_random_real(prec):
+    rng = np.random.default_rng(1)
+    M, N, K = 300, 700, 333
+    A = rng.standard_normal((M, K)).astype(np.float32)
+    B = rng.standard_normal((N, K)).astype(np.float32)
+    D = np.zeros((N, M), dtype=np.float32)
+    dd.dd_tc_gemm_test(prec, A, B, D)
+    ref = B.astype(np.float64) @ A.astype(np.float64).T
+    tol = 2e-2 if prec == dd.DD_PREC_BF16 else 4e-3
+    assert np.abs(D - ref).max() <= tol * np.abs(ref).max()
+
+
+MIXED = {
+    "cfg1": WORKLOADS["cfg1"],
+    "cfg2_small": WORKLOADS["cfg2_small"],
+    "p2_types": Workload("p2_types", p=2, L=3, n=6, overlap=2, kind="asym3"),
+    "ragged": Workload("ragged", p=1, L=5, n=10, ell=1.2, overlap=3, kind="cos4", seed=7),
+}
+
+
+@pytest.mark.parametrize("prec,tol", [("bf16", 2e-2), ("tf32", 4e-3)])
+@pytest.mark.parametrize("name", list(MIXED))
+def test_mixed_preconditioner(name, prec, tol):
+    w = MIXED[name]
+    P = oracle_problem(w)
+    with make_solver(w, precision=prec) as es:
+        es.prepare()
+        r = np.random.default_rng(3).standard_normal(w.dofs)
+        z = gpu_vec(np.zeros(w.dofs))
+        dd.dd_apply_preconditioner(es.ctx, gpu_vec(r), z)
+        assert rel_err(host(z), P.prec(r)) < tol
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+@pytest.mark.parametrize("name", list(MIXED))
+def test_mixed_ground_state(name, prec):
+    """Flexible CG with rounded local inverses reaches the FP64 ground state."""
+    w = MIXED[name]
+    P = oracle_problem(w, build_prec=False)
+    lam_ex, _ = solvers.exact_ground_state(P.A, P.M, sigma=P.sigma,
+                                           dense_limit=3000 if w.dofs <= 3000 else 0)
+    with make_solver(w, precision=prec) as es:
+        es.prepare()
+        x = gpu_vec(np.ones(w.dofs))
+        lam, outer, tot, mx = dd.dd_inverse_iterate(es.ctx, x)
+    assert abs(lam - lam_ex) <= 1e-10 * abs(lam_ex)
+    xh = host(x)
+    Mx = P.M @ xh
+    eta = np.linalg.norm(P.A @ xh - lam * Mx) / (abs(lam) * np.linalg.norm(Mx))
+    assert eta <= 1.5e-8
