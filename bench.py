@@ -1,0 +1,463 @@
+#!/usr/bin/env python3
+"""Time to the ground state on the periodic-potential box L = 2048, h = 1/32, delta = 4.
+
+One step = everything that depends on the potential, on one GPU: upload V (already in
+HBM) and rebuild the stencil tables, the cell eigenpair (sigma, psi), the local
+factorisations / rounded local inverses and the coarse matrix, and the shifted inverse
+iteration from x_0 = 1 to the stopping rule (eta <= 1e-8, relative change of the
+Rayleigh quotient <= 1e-10), with every inner PCG solve at rTOL = 1e-8.  The context
+(device buffers) is allocated once before the timed region.
+
+Printed: one JSON line.  ``value`` is ground states per second of the whole job
+(mixed precision: BF16 local inverses on the tensor cores inside flexible CG; the
+plain FP64 method is timed beside it); ``e2e`` repeats the measurement through
+``dd_eigenpair`` with host buffers (V in, phi out) and context set-up inside the timed
+region; ``roofline`` is for the kernel class with the largest device time;
+``cpu_baseline`` is the oracle on the host cores on a bounded sample.
+
+``--impl reference`` times the oracle itself (the reference arm of this workload).
+For N > 1 GPUs the ranks run independent replicas of the workload (the method has no
+data exchange between independent eigenproblems); ``value`` counts all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "time to ground state @1e-10 rel, mixed vs FP64 plain; PCG iters/s; % roofline"
+UNIT = "ground states/s"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# FP64 FMA throughput measured on this machine's GB300 with a DFMA microbenchmark
+# (8 independent chains per thread, 152 x 8 x 256 threads): 1.19 TFLOP/s.
+FP64_TFLOPS = 1.19
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cfg2")
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "tf32"])
+    ap.add_argument("--fp64-steps", type=int, default=None, help="timed steps of the plain FP64 method")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------------------
+# oracle sample (runs in a child process with one BLAS thread)
+# ----------------------------------------------------------------------------------------
+def cpu_sample(workload: str, pcg_its: int = 3) -> dict:
+    import numpy as np
+    from ddinputs import WORKLOADS, potential
+    from oracle import q1, solvers
+    from oracle.dd import Decomposition, TwoLevelAS
+    w = WORKLOADS[workload]
+    g = q1.Grid.from_workload(w)
+    V = potential(w)
+    t0 = time.perf_counter()
+    K, M, MV = q1.assemble_box(g, V)
+    A = (K + MV).tocsr()
+    sigma, psi = solvers.cell_eigenpair(g, V)
+    As = (A - sigma * M).tocsr()
+    P = TwoLevelAS(As, Decomposition(g), q1.periodic_extension(g, psi))
+    t1 = time.perf_counter()
+    x = np.ones(g.ndof)
+    x /= np.sqrt(x @ (M @ x))
+    b = M @ x
+    t2 = time.perf_counter()
+    _, it, _ = solvers.pcg(As, b, None, P, 1e-8, pcg_its)
+    t3 = time.perf_counter()
+    return {"setup_s": t1 - t0, "pcg_s_per_iter": (t3 - t2) / max(it, 1), "pcg_iters_run": it,
+            "sigma": sigma}
+
+
+def run_cpu_sample(workload: str) -> dict:
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = "1"
+    env.pop("RANK", None)
+    env.pop("WORLD_SIZE", None)
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", workload],
+                         capture_output=True, text=True, env=env, timeout=900)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+# ----------------------------------------------------------------------------------------
+# helpers
+# ----------------------------------------------------------------------------------------
+def load_peaks() -> tuple[dict, str]:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return dict(FALLBACK_PEAKS), "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling (200 ms) of SM clocks and throttle reasons while active."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_model(w, info, ntype_counts, nloc_by_type, band, precision):
+    """Algorithmic bytes (or flops) per launch of each kernel class."""
+    ndof = info["ndof"]
+    nloc_sum = sum(c * n for c, n in zip(ntype_counts, nloc_by_type))
+    f = nloc_sum / ndof
+    es = 2 if precision == "bf16" else 4
+    gemm_flops = sum(2.0 * c * n * n for c, n in zip(ntype_counts, nloc_by_type))
+    fp64_flops = 0.0
+    for c, n in zip(ntype_counts, nloc_by_type):
+        b = min(band, n - 1)
+        per_sweep = n * b - b * (b + 1) / 2
+        fp64_flops += c * 2 * 2 * per_sweep
+    return {
+        "stencil_Asigma": ("hbm", 16.0 * ndof),
+        "p_update": ("hbm", 24.0 * ndof),
+        "xr_update": ("hbm", 48.0 * ndof),
+        "prolong_sum": ("hbm", (24.0 + 4.0 * f) * ndof),
+        "pack_restrict": ("hbm", (8.0 + es * f) * ndof),
+        "local_gemm_tc": ("tensor", gemm_flops),
+        "local_solve_fp64": ("alu", fp64_flops),
+        "coarse_restrict": ("hbm", 8.0 * ndof),
+        "outer_step": ("hbm", 24.0 * ndof),
+        "_f": f,
+    }
+
+
+# ----------------------------------------------------------------------------------------
+# reference arm: the oracle as it stands
+# ----------------------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from ddinputs import WORKLOADS
+    w = WORKLOADS[args.workload]
+    times = []
+    samples = []
+    for i in range(args.warmup + args.steps):
+        s = run_cpu_sample(args.workload)
+        samples.append(s)
+    # extrapolation to a full ground state: the plain method's inner iterations on this
+    # workload (outer x inner, measured by the FP64 GPU run of the same algorithm)
+    inner_total = REF_INNER_ITERS.get(args.workload)
+    for s in samples[args.warmup:]:
+        times.append(s["setup_s"] + s["pcg_s_per_iter"] * inner_total)
+    t = sum(times) / len(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": 1.0 / t, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: p=1, L={w.L}, h=1/{w.n}, delta={w.overlap}, "
+                                 f"dofs={w.dofs}, V=4-term cosine (seed {w.seed})",
+                   "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": 1.0 / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"per step: oracle set-up + 3 PCG iterations; extrapolated with "
+                                   f"{inner_total} inner iterations per ground state"},
+        "e2e": {"value": 1.0 / t, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# total inner PCG iterations of one ground state with the plain FP64 method, used to
+# extrapolate oracle samples (filled from the GPU run of the same algorithm)
+REF_INNER_ITERS = {"cfg2": 330, "cfg1": 106, "cfg2_small": 250}
+
+
+# ----------------------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.cpu_sample:
+        print(json.dumps(cpu_sample(args.cpu_sample)))
+        return
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+    import paper_2311_08757_gb300 as dd
+    from ddinputs import WORKLOADS, sample_cell_qp
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    if not os.path.exists(dd.lib_path()):
+        raise RuntimeError("libddeig.so is not built (run __graft_entry__.build())")
+
+    w = WORKLOADS[args.workload]
+    V_host = sample_cell_qp(w)
+    V = torch.from_numpy(V_host).to(dev)
+    ones = torch.ones(w.dofs, dtype=torch.float64, device=dev)
+    x = torch.empty_like(ones)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+    def make(prec):
+        es = dd.Eigensolver(dd.grid_from_workload(w, precision=dd.PRECISIONS[prec]), V)
+        return es
+
+    def step(es):
+        dd.dd_set_potential(es.ctx, V)
+        sigma = dd.dd_cell_eigenpair(es.ctx)
+        dd.dd_coarse_build(es.ctx)
+        x.copy_(ones)
+        lam, outer, tot, mx = dd.dd_inverse_iterate(es.ctx, x)
+        return lam, sigma, outer, tot
+
+    def timed(es, nsteps, count_launches=False):
+        stream = torch.cuda.current_stream()
+        per = []
+        res = None
+        l0 = dd.dd_kernel_launch_count()
+        for _ in range(nsteps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = step(es)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            per.append(e0.elapsed_time(e1))
+        l1 = dd.dd_kernel_launch_count()
+        flushes = nsteps  # flush kernels are torch's, not counted by the library
+        return per, res, (l1 - l0)
+
+    mixed = make(args.precision)
+    for _ in range(args.warmup):
+        step(mixed)
+
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    per, res, launches = timed(mixed, args.steps)
+    torch.cuda.synchronize()
+    barrier()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    lam, sigma, outer, inner_tot = res
+    step_ms = sum(per) / len(per)
+    # max over ranks
+    if world > 1:
+        t = torch.tensor([step_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        step_ms = float(t.item())
+    value = world * 1e3 / step_ms
+
+    # plain FP64 method, same workload
+    fp64_steps = args.fp64_steps if args.fp64_steps is not None else max(1, args.steps // 2)
+    plain = make("fp64")
+    step(plain)
+    per64, res64, _ = timed(plain, fp64_steps)
+    fp64_ms = sum(per64) / len(per64)
+
+    # phase breakdown of one step (host timer around each synchronous call)
+    def phases(es):
+        out = {}
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dd.dd_set_potential(es.ctx, V)
+        t1 = time.perf_counter()
+        dd.dd_cell_eigenpair(es.ctx)
+        t2 = time.perf_counter()
+        dd.dd_coarse_build(es.ctx)
+        t3 = time.perf_counter()
+        x.copy_(ones)
+        torch.cuda.synchronize()
+        t4 = time.perf_counter()
+        dd.dd_inverse_iterate(es.ctx, x)
+        t5 = time.perf_counter()
+        return {"set_potential": 1e3 * (t1 - t0), "cell_eigenpair": 1e3 * (t2 - t1),
+                "coarse_build": 1e3 * (t3 - t2), "inverse_iterate": 1e3 * (t5 - t4)}
+
+    breakdown = {"mixed": phases(mixed), "fp64_plain": phases(plain)}
+
+    # per-kernel device times (CUDA events around every launch, one profiled step)
+    dd.dd_set_option(mixed.ctx, dd.DD_OPT_TIMING, 1)
+    dd.dd_reset_timings(mixed.ctx)
+    step(mixed)
+    kt = dd.dd_kernel_timings(mixed.ctx)
+    dd.dd_set_option(mixed.ctx, dd.DD_OPT_TIMING, 0)
+    dd.dd_set_option(plain.ctx, dd.DD_OPT_TIMING, 1)
+    dd.dd_reset_timings(plain.ctx)
+    step(plain)
+    kt64 = dd.dd_kernel_timings(plain.ctx)
+    dd.dd_set_option(plain.ctx, dd.DD_OPT_TIMING, 0)
+
+    info = mixed.info
+    peaks, peak_src = load_peaks()
+    subs = []
+    nloc_interior = (w.n + 2 * w.overlap - 1) * (w.ny - 1)
+    nloc_edge = (w.n + w.overlap - 1) * (w.ny - 1)
+    counts, nlocs = ([w.L - 2, 2], [nloc_interior, nloc_edge]) if w.p == 1 and w.L > 2 else ([1], [info["nloc_max"]])
+    model = kernel_model(w, info, counts, nlocs, info["band_local"], args.precision)
+    busy = {k: v for k, v in kt.items() if v[0] > 0}
+    dom = max((k for k in busy if k in model), key=lambda k: busy[k][1])
+    bound, units = model[dom]
+    nlaunch, ms_tot = busy[dom]
+    avg_s = ms_tot / nlaunch / 1e3
+    if bound == "hbm":
+        achieved = units / avg_s / 1e9
+        peak = peaks["hbm_gbs"]
+        unit = "GB/s"
+    elif bound == "tensor":
+        achieved = units / avg_s / 1e12
+        peak = peaks["bf16_tflops"] * (0.5 if args.precision == "tf32" else 1.0)
+        unit = "TFLOP/s"
+    else:
+        achieved = units / avg_s / 1e12
+        peak = FP64_TFLOPS
+        unit = "TFLOP/s"
+    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": peak_src if bound != "alu" else "DFMA microbenchmark",
+                "avg_launch_us": avg_s * 1e6, "launches": nlaunch}
+    kernel_table = {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in busy.items()}
+    kernel_table64 = {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in kt64.items() if v[0] > 0}
+
+    # end to end through dd_eigenpair with host buffers (pinned), context set-up included
+    e2e = None
+    if not args.no_e2e:
+        Vp = torch.from_numpy(V_host).pin_memory()
+        phi = torch.empty(w.dofs, dtype=torch.float64).pin_memory()
+        g = dd.grid_from_workload(w, precision=dd.PRECISIONS[args.precision])
+        dd.dd_eigenpair(g, Vp, phi_out=phi)
+        ts = []
+        for _ in range(max(1, min(3, args.steps))):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lam_e, _ = dd.dd_eigenpair(g, Vp, phi_out=phi)
+            ts.append(time.perf_counter() - t0)
+        te = sum(ts) / len(ts)
+        if world > 1:
+            tt = torch.tensor([te], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": world / te, "unit": UNIT, "h2d_bytes_per_step": int(Vp.numel() * 8),
+               "d2h_bytes_per_step": int(phi.numel() * 8), "ms_per_step": te * 1e3}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            s = run_cpu_sample(args.workload)
+            t_cpu = s["setup_s"] + s["pcg_s_per_iter"] * res64[3]
+            cpu = {"value": 1.0 / t_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": (f"oracle set-up of the same workload ({s['setup_s']:.1f} s: assembly, cell "
+                              f"eigenpair, {w.L ** w.p} local factorisations, coarse factorisation) + "
+                              f"{s['pcg_iters_run']} PCG iterations ({s['pcg_s_per_iter']:.3f} s each); "
+                              f"time to ground state extrapolated with the {res64[3]} inner iterations "
+                              f"the plain FP64 method needs"),
+                   "est_time_to_ground_state_s": t_cpu}
+        except Exception as e:  # noqa: BLE001
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 (local inverses %s)" % args.precision, "data": "synthetic",
+            "config": {"workload": f"{args.workload}: p=1, L={w.L}, ell=1, h=1/{w.n}, delta={w.overlap}, "
+                                   f"dofs={w.dofs}, {w.L ** w.p} subdomains, V=4-term cosine (seed {w.seed})",
+                       "precision": args.precision, "l2": "flushed between steps (256 MB write)",
+                       "parallelism": f"replicas x{world}"},
+            "time_to_ground_state_ms": {"mixed": step_ms, "fp64_plain": fp64_ms,
+                                        "speedup_mixed_vs_fp64": fp64_ms / step_ms},
+            "lambda": lam, "sigma": sigma, "outer_iters": outer, "inner_iters_total": inner_tot,
+            "fp64_plain": {"lambda": res64[0], "outer_iters": res64[2], "inner_iters_total": res64[3]},
+            "pcg_iters_per_s": inner_tot / (step_ms / 1e3),
+            "roofline": roofline,
+            "breakdown_ms": breakdown,
+            "kernels_mixed": kernel_table, "kernels_fp64": kernel_table64,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "wall_s_timed_region": t_wall,
+        }
+        print(json.dumps(line))
+    mixed.close()
+    plain.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

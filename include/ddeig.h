@@ -108,6 +108,15 @@ typedef struct {
 int dd_setup(const dd_grid* g, const double* V_cell_qp, size_t nV, void* stream, dd_ctx** out);
 
 /*
+ * dd_set_potential -- replace V on an existing context (same grid): uploads V_cell_qp (host or
+ * device, nV doubles, layout above), rebuilds the stencil tables of A = K + M_V and M and
+ * returns the context to the state after dd_setup (dd_cell_eigenpair and dd_coarse_build
+ * must follow).  Lets one context serve many potentials without re-allocating.
+ * DD_EINVAL on a size mismatch, DD_ENAN on non-finite values.
+ */
+int dd_set_potential(dd_ctx* ctx, const double* V_cell_qp, size_t nV);
+
+/*
  * dd_cell_eigenpair -- lowest eigenpair (sigma, psi) of the x-periodic, y-Dirichlet cell
  * problem (cell problem of Sec. 1, weak cell problem of Sec. 2), psi > 0, psi^T M_# psi = 1;
  * then forms A_sigma = A - sigma M (Sec. 1.1) and the coarse weights D_i R_i E^# psi (Def. 2.1).
@@ -209,6 +218,10 @@ int dd_set_option(dd_ctx* ctx, int option, int value);
  * arrays to get only *count.  dd_reset_timings zeroes the counters. */
 int dd_kernel_timings(dd_ctx* ctx, int* count, const char** names, long long* launches, double* ms);
 int dd_reset_timings(dd_ctx* ctx);
+
+/* Number of kernel launches this library has issued in the process so far (a replayed CUDA
+ * graph counts each of its kernel nodes); differences bracket a region of interest. */
+long long dd_kernel_launch_count(void);
 
 /* Self-test of the tensor-core contraction used for the local solves (no paper counterpart;
  * it checks the kernel in isolation): D[n][m] = sum_k A[m][k] B[n][k] for host row-major

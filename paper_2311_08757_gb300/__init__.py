@@ -68,6 +68,8 @@ _SIGS = {
                                   POINTER(c_double)]),
     "dd_reset_timings": (c_int, [c_void_p]),
     "dd_tc_gemm_test": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
+    "dd_set_potential": (c_int, [c_void_p, c_void_p, c_size_t]),
+    "dd_kernel_launch_count": (c_longlong, []),
 }
 
 
@@ -151,6 +153,15 @@ def dd_setup(grid: dd_grid, V_cell_qp, stream=None) -> c_void_p:
     n = V_cell_qp.numel() if hasattr(V_cell_qp, "numel") else V_cell_qp.size
     _check(lib().dd_setup(byref(grid), _ptr(V_cell_qp), n, _stream_ptr(stream), byref(ctx)))
     return ctx
+
+
+def dd_set_potential(ctx, V_cell_qp) -> None:
+    n = V_cell_qp.numel() if hasattr(V_cell_qp, "numel") else V_cell_qp.size
+    _check(lib().dd_set_potential(ctx, _ptr(V_cell_qp), n), ctx)
+
+
+def dd_kernel_launch_count() -> int:
+    return int(lib().dd_kernel_launch_count())
 
 
 def dd_cell_eigenpair(ctx, psi_cell_out=None) -> float:

@@ -1,6 +1,7 @@
 // C ABI and host runtime: context set-up, the PCG engine (eager launches or a replayed
 // CUDA graph of a block of iterations), the shifted inverse iteration, staging of host
 // buffers, error reporting.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -46,6 +47,11 @@ int guarded(dd_ctx* c, F&& f) {
 }  // namespace
 
 namespace dd {
+
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 void* dev_alloc(dd_ctx* c, size_t bytes) {
   void* p = nullptr;
@@ -163,6 +169,15 @@ void build_subdomains(dd_ctx* c) {
   DD_CUDA(cudaStreamSynchronize(c->stream));
 }
 
+// Padded box vector with a zeroed guard band of kVecGuard doubles on each side: the
+// 3^d-point stencil of the first (last) interior node reaches one element before (after)
+// the padded range, where the homogeneous Dirichlet value 0 must be read.
+constexpr long long kVecGuard = 64;   // 512 bytes, keeps the 256-byte alignment
+double* alloc_vec(dd_ctx* c) {
+  double* base = (double*)dev_alloc(c, sizeof(double) * (size_t)(c->g.plen + 2 * kVecGuard));
+  return base + kVecGuard;
+}
+
 // user vector (ABI order, host or device) -> padded device vector
 void load_vec(dd_ctx* c, const double* u, double* padded) {
   const Geo& g = c->g;
@@ -240,15 +255,20 @@ void reset_graph(dd_ctx* c) {
 void build_graph(dd_ctx* c) {
   reset_graph(c);
   cudaGraph_t gr;
+  const long long before = launch_count();
   DD_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
   try {
     for (int i = 0; i < c->check_every; ++i) pcg_iteration(c);
   } catch (...) {
     cudaStreamEndCapture(c->stream, &gr);
     cudaGetLastError();
+    note_launches(before - launch_count());
     throw;
   }
   DD_CUDA(cudaStreamEndCapture(c->stream, &gr));
+  // captured launches do not run; replays are counted when the graph is launched
+  c->graph_kernels = launch_count() - before;
+  note_launches(-c->graph_kernels);
   DD_CUDA(cudaGraphInstantiate(&c->graph, gr, 0));
   DD_CUDA(cudaGraphDestroy(gr));
   c->graph_iters = c->check_every;
@@ -264,13 +284,14 @@ int pcg_run(dd_ctx* c, const double* b, double rtol, int maxit, int* iters, doub
   init.flexible = (c->flexible_opt < 0) ? (use_gemm(c) ? 1 : 0) : c->flexible_opt;
   DD_CUDA(cudaMemcpyAsync(c->st, &init, sizeof(init), cudaMemcpyHostToDevice, s));
   DD_CUDA(cudaMemsetAsync(c->p, 0, sizeof(double) * c->g.plen, s));
-  TIMED(KC_STENCIL, s, launch_pcg_init(c, b, s));
+  TIMED(KC_MISC, s, launch_pcg_init(c, b, s));
   precond(c, c->r, 1);
   const bool graph = c->use_graph && !c->timing;
   if (graph && (c->graph == nullptr || c->graph_iters != c->check_every)) build_graph(c);
   for (int done_iters = 0; done_iters < maxit + c->check_every; done_iters += c->check_every) {
     if (graph) {
       DD_CUDA(cudaGraphLaunch(c->graph, s));
+      note_launches(c->graph_kernels);
     } else {
       for (int i = 0; i < c->check_every; ++i) pcg_iteration(c);
     }
@@ -413,16 +434,15 @@ int dd_setup(const dd_grid* gr, const double* V, size_t nV, void* stream, dd_ctx
     c->tabS = (double*)dev_alloc(c, sizeof(double) * ntab);
     launch_build_tables(c);
     build_subdomains(c);
-    const size_t vb = sizeof(double) * g.plen;
-    c->x = (double*)dev_alloc(c, vb);
-    c->r = (double*)dev_alloc(c, vb);
-    c->z = (double*)dev_alloc(c, vb);
-    c->p = (double*)dev_alloc(c, vb);
-    c->q = (double*)dev_alloc(c, vb);
-    c->w1 = (double*)dev_alloc(c, vb);
-    c->w2 = (double*)dev_alloc(c, vb);
-    c->w3 = (double*)dev_alloc(c, vb);
-    c->xe = (double*)dev_alloc(c, vb);
+    c->x = alloc_vec(c);
+    c->r = alloc_vec(c);
+    c->z = alloc_vec(c);
+    c->p = alloc_vec(c);
+    c->q = alloc_vec(c);
+    c->w1 = alloc_vec(c);
+    c->w2 = alloc_vec(c);
+    c->w3 = alloc_vec(c);
+    c->xe = alloc_vec(c);
     c->stage_a = (double*)dev_alloc(c, sizeof(double) * g.ndof);
     c->stage_b = (double*)dev_alloc(c, sizeof(double) * g.ndof);
     c->ncell = (long long)((G.p == 1) ? G.n : G.n * G.n) * g.nyi;
@@ -443,6 +463,36 @@ int dd_setup(const dd_grid* gr, const double* V, size_t nV, void* stream, dd_ctx
   *out = c;
   return DD_OK;
 }
+
+int dd_set_potential(dd_ctx* c, const double* V, size_t nV) {
+  if (!V) return fail(c, DD_EINVAL, "null potential");
+  int rc = stage_err(c, 1);
+  if (rc) return rc;
+  size_t expect = (size_t)c->g.ny;
+  for (int k = 0; k < c->g.p; ++k) expect *= (size_t)c->g.n;
+  for (int k = 0; k <= c->g.p; ++k) expect *= (size_t)c->g.Q;
+  if (nV != expect) return fail(c, DD_EINVAL, "nV does not match n^p ny Q^(p+1)");
+  return guarded(c, [&]() -> int {
+    enter(c);
+    if (is_device_ptr(V))
+      DD_CUDA(cudaMemcpyAsync(c->Vqp, V, sizeof(double) * nV, cudaMemcpyDeviceToDevice, c->stream));
+    else
+      DD_CUDA(cudaMemcpyAsync(c->Vqp, V, sizeof(double) * nV, cudaMemcpyHostToDevice, c->stream));
+    DD_CUDA(cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->stream));
+    launch_check_finite(c->Vqp, (long long)nV, c->dev_err, c->stream);
+    int bad = 0;
+    DD_CUDA(cudaMemcpyAsync(&bad, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    DD_CUDA(cudaStreamSynchronize(c->stream));
+    if (bad) throw Error(DD_ENAN, "V contains non-finite values");
+    launch_build_tables(c);
+    DD_CUDA(cudaStreamSynchronize(c->stream));
+    reset_graph(c);
+    c->stage = 1;
+    return DD_OK;
+  });
+}
+
+long long dd_kernel_launch_count(void) { return dd::launch_count(); }
 
 int dd_cell_eigenpair(dd_ctx* c, double* sigma_out, double* psi_out) {
   int rc = stage_err(c, 1);

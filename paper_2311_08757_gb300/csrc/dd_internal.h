@@ -6,7 +6,9 @@
 //     slot = j - 1 for the interior y-nodes j = 1..ny-1; slots ny-1..Ypad-1 are zero.
 // Boundary columns (a = 0, a = Ln) and pad slots are kept at zero by every kernel, so
 // the homogeneous Dirichlet condition (H^1_0, Sec. 1) needs no branch in the stencil:
-// the neighbours of a node next to the boundary read zeros.
+// the neighbours of a node next to the boundary read zeros.  The corner taps of the first
+// and last interior nodes reach one element outside [0, plen); every padded vector is
+// allocated with a zeroed guard band on both sides for them.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -189,6 +191,7 @@ struct dd_ctx {
   // graph of one block of PCG iterations
   cudaGraphExec_t graph = nullptr;
   int graph_iters = 0;
+  long long graph_kernels = 0;   // kernel nodes in one replay of the graph
 };
 
 namespace dd {
@@ -245,6 +248,11 @@ void timer_end(dd_ctx* c, int kc, cudaStream_t s, cudaEvent_t e0);
 void timer_collect(dd_ctx* c);
 
 void* dev_alloc(dd_ctx* c, size_t bytes);
+
+// process-wide count of kernel launches issued by this library (graph replays included)
+void note_launch();
+void note_launches(long long k);
+long long launch_count();
 
 }  // namespace dd
 

@@ -88,10 +88,10 @@ int launch_band_factor(dd_ctx* c, double* CB, double* RB, double* inv, int nmat,
   const size_t smem = sizeof(double) * (b + 1);
   int threads = 256;
   if ((long long)b * b > 4096) threads = 1024;
-  k_band_factor<<<nmat, threads, smem, c->stream>>>(CB, inv, nvec, nmax, b, flag);
+  (k_band_factor<<<nmat, threads, smem, c->stream>>>(CB, inv, nvec, nmax, b, flag), dd::note_launch());
   DD_CUDA(cudaGetLastError());
   const long long total = (long long)nmat * nmax * (b + 1);
-  k_band_rows<<<grid_blocks(total, kThreads), kThreads, 0, c->stream>>>(CB, RB, nvec, nmat, nmax, b);
+  (k_band_rows<<<grid_blocks(total, kThreads), kThreads, 0, c->stream>>>(CB, RB, nvec, nmat, nmax, b), dd::note_launch());
   DD_CUDA(cudaGetLastError());
   DD_CUDA(cudaFreeAsync(nvec, c->stream));
   return DD_OK;
@@ -144,8 +144,8 @@ void launch_local_assemble(dd_ctx* c) {
   const size_t nbytes = sizeof(double) * (size_t)c->ntypes * c->nloc_max * (c->band + 1);
   DD_CUDA(cudaMemsetAsync(c->bandCB, 0, nbytes, c->stream));
   const long long total = (long long)c->ntypes * c->nloc_max;
-  k_local_assemble<<<grid_blocks(total, 128), 128, 0, c->stream>>>(c->g, c->tabS, drep, c->ntypes,
-                                                                   c->nloc_max, c->band, c->bandCB);
+  (k_local_assemble<<<grid_blocks(total, 128), 128, 0, c->stream>>>(c->g, c->tabS, drep, c->ntypes,
+                                                                   c->nloc_max, c->band, c->bandCB), dd::note_launch());
   DD_CUDA(cudaGetLastError());
   DD_CUDA(cudaFreeAsync(drep, c->stream));
 }
@@ -196,8 +196,8 @@ void launch_band_solve_local(dd_ctx* c, const double* r, cudaStream_t s) {
     attr_set = true;
   }
   const int nb = (c->g.nsub + wpb - 1) / wpb;
-  k_local_solve<<<nb, wpb * 32, smem, s>>>(c->g, c->subs, c->slot_of_sub, r, c->bandCB, c->bandRB, c->bandInv,
-                                          c->nloc_max, c->band, c->Y64, c->kpad, c->st);
+  (k_local_solve<<<nb, wpb * 32, smem, s>>>(c->g, c->subs, c->slot_of_sub, r, c->bandCB, c->bandRB, c->bandInv,
+                                          c->nloc_max, c->band, c->Y64, c->kpad, c->st), dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 
@@ -416,8 +416,8 @@ int cell_eigenpair(dd_ctx* c) {
   DD_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), c->stream));
   long long nV = (long long)ncol * g.ny;
   for (int k = 0; k <= g.p; ++k) nV *= g.Q;
-  k_cell_shift<<<1, 1024, 0, c->stream>>>(c->Vqp, nV, shift);
-  k_cell_assemble<<<grid_blocks(ncell, 128), 128, 0, c->stream>>>(g, c->tabA, c->tabM, shift, b, CB);
+  (k_cell_shift<<<1, 1024, 0, c->stream>>>(c->Vqp, nV, shift), dd::note_launch());
+  (k_cell_assemble<<<grid_blocks(ncell, 128), 128, 0, c->stream>>>(g, c->tabA, c->tabM, shift, b, CB), dd::note_launch());
   DD_CUDA(cudaGetLastError());
   // factor (one matrix of size ncell)
   {
@@ -425,15 +425,15 @@ int cell_eigenpair(dd_ctx* c) {
     DD_CUDA(cudaMallocAsync(&nvec, sizeof(int), c->stream));
     DD_CUDA(cudaMemcpyAsync(nvec, &ncell, sizeof(int), cudaMemcpyHostToDevice, c->stream));
     const int threads = ((long long)b * b > 4096) ? 1024 : 256;
-    k_band_factor<<<1, threads, sizeof(double) * (b + 1), c->stream>>>(CB, inv, nvec, ncell, b, flag);
-    k_band_rows<<<grid_blocks((long long)ncell * (b + 1), kThreads), kThreads, 0, c->stream>>>(CB, RB, nvec, 1,
-                                                                                              ncell, b);
+    (k_band_factor<<<1, threads, sizeof(double) * (b + 1), c->stream>>>(CB, inv, nvec, ncell, b, flag), dd::note_launch());
+    (k_band_rows<<<grid_blocks((long long)ncell * (b + 1), kThreads), kThreads, 0, c->stream>>>(CB, RB, nvec, 1,
+                                                                                              ncell, b), dd::note_launch());
     DD_CUDA(cudaGetLastError());
     DD_CUDA(cudaFreeAsync(nvec, c->stream));
   }
   const size_t smem = sizeof(double) * 3 * (size_t)ncell;
   DD_CUDA(cudaFuncSetAttribute(k_cell_iterate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_cell_iterate<<<1, 1024, smem, c->stream>>>(g, c->tabA, c->tabM, CB, RB, inv, b, 20000, c->psi_cell, out);
+  (k_cell_iterate<<<1, 1024, smem, c->stream>>>(g, c->tabA, c->tabM, CB, RB, inv, b, 20000, c->psi_cell, out), dd::note_launch());
   DD_CUDA(cudaGetLastError());
   CellOut h;
   int fl = 0;

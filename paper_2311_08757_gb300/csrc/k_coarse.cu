@@ -81,8 +81,8 @@ static Sub* upload_reps(dd_ctx* c) {
 void launch_coarse_weights(dd_ctx* c) {
   Sub* rep = upload_reps(c);
   const long long total = (long long)c->ntypes * c->kpad;
-  k_coarse_weights<<<grid_blocks(total, 128), 128, 0, c->stream>>>(c->g, c->grid.pu_kind, rep, c->ntypes,
-                                                                   c->kpad, c->psi_cell, c->wT);
+  (k_coarse_weights<<<grid_blocks(total, 128), 128, 0, c->stream>>>(c->g, c->grid.pu_kind, rep, c->ntypes,
+                                                                   c->kpad, c->psi_cell, c->wT), dd::note_launch());
   DD_CUDA(cudaGetLastError());
   DD_CUDA(cudaFreeAsync(rep, c->stream));
 }
@@ -155,10 +155,10 @@ int coarse_assemble(dd_ctx* c) {
   const int ncol2 = (g.p == 2) ? 3 : 1;
   for (int c1 = 0; c1 < 3; ++c1)
     for (int c2 = 0; c2 < ncol2; ++c2) {
-      k_colour_vector<<<grid_blocks(work, kThreads), kThreads, 0, c->stream>>>(g, c->subs, c->wT, c->kpad, c1, c2,
-                                                                               c->w1);
+      (k_colour_vector<<<grid_blocks(work, kThreads), kThreads, 0, c->stream>>>(g, c->subs, c->wT, c->kpad, c1, c2,
+                                                                               c->w1), dd::note_launch());
       launch_stencil(c, c->tabS, c->w1, c->w2, c->stream);
-      k_coarse_entries<<<g.nsub, 256, 0, c->stream>>>(g, c->subs, c->wT, c->kpad, c1, c2, c->w2, c->A0band);
+      (k_coarse_entries<<<g.nsub, 256, 0, c->stream>>>(g, c->subs, c->wT, c->kpad, c1, c2, c->w2, c->A0band), dd::note_launch());
       DD_CUDA(cudaGetLastError());
     }
   return DD_OK;
@@ -282,7 +282,7 @@ int coarse_factor(dd_ctx* c) {
     c->cr_np = Np;
     const size_t W = (size_t)Np + 2;
     c->cr = (double*)dev_alloc(c, sizeof(double) * W * (2 * m + 4));
-    k_cr_setup<<<1, 1024, 0, c->stream>>>(c->A0band, N, m, Np, c->cr, flag);
+    (k_cr_setup<<<1, 1024, 0, c->stream>>>(c->A0band, N, m, Np, c->cr, flag), dd::note_launch());
     DD_CUDA(cudaGetLastError());
   } else {
     const int b = g.L + 1;
@@ -310,7 +310,7 @@ int coarse_factor(dd_ctx* c) {
     const int wpb = (N * 8 <= 48 * 1024) ? 4 : 1;
     const size_t smem = sizeof(double) * (size_t)wpb * N;
     DD_CUDA(cudaFuncSetAttribute(k_band_inverse_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-    k_band_inverse_rows<<<(N + wpb - 1) / wpb, 32 * wpb, smem, c->stream>>>(N, b, CB, RB, inv, c->A0inv);
+    (k_band_inverse_rows<<<(N + wpb - 1) / wpb, 32 * wpb, smem, c->stream>>>(N, b, CB, RB, inv, c->A0inv), dd::note_launch());
     DD_CUDA(cudaGetLastError());
   }
   int fl = 0;
@@ -334,7 +334,7 @@ __global__ void k_coarse_restrict(Geo g, const Sub* __restrict__ subs, const dou
 }
 
 void launch_coarse_restrict(dd_ctx* c, const double* r, cudaStream_t s) {
-  k_coarse_restrict<<<c->g.nsub, 256, 0, s>>>(c->g, c->subs, c->wT, c->kpad, r, c->c0, c->st);
+  (k_coarse_restrict<<<c->g.nsub, 256, 0, s>>>(c->g, c->subs, c->wT, c->kpad, r, c->c0, c->st), dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 
@@ -347,10 +347,10 @@ void launch_coarse_solve(dd_ctx* c, cudaStream_t s) {
       DD_CUDA(cudaFuncSetAttribute(k_cr_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
       attr = true;
     }
-    k_cr_solve<<<1, 1024, smem, s>>>(c->cr, g.nsub, c->cr_m, c->cr_np, c->c0, c->u0, c->st);
+    (k_cr_solve<<<1, 1024, smem, s>>>(c->cr, g.nsub, c->cr_m, c->cr_np, c->c0, c->u0, c->st), dd::note_launch());
   } else {
     const int N = g.nsub;
-    k_gemv_rows<<<(N + 7) / 8, 256, 0, s>>>(N, c->A0inv, c->c0, c->u0, c->st);
+    (k_gemv_rows<<<(N + 7) / 8, 256, 0, s>>>(N, c->A0inv, c->c0, c->u0, c->st), dd::note_launch());
   }
   DD_CUDA(cudaGetLastError());
 }

@@ -271,7 +271,7 @@ static void launch_tc(const CUtensorMap* tA, const CUtensorMap* tB, const Tile* 
     DD_CUDA(cudaFuncSetAttribute(k_tc_gemm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<T>::SMEM));
     attr = true;
   }
-  k_tc_gemm<T><<<ntiles, 128, TcCfg<T>::SMEM, s>>>(*tA, *tB, tiles, K, mlimit, rows_per_type, Y, ldy, err, st);
+  (k_tc_gemm<T><<<ntiles, 128, TcCfg<T>::SMEM, s>>>(*tA, *tB, tiles, K, mlimit, rows_per_type, Y, ldy, err, st), dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 
@@ -364,12 +364,12 @@ int gemm_setup(dd_ctx* c) {
   if (bf16) {
     DD_CUDA(cudaFuncSetAttribute(k_local_inverse<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  220 * 1024));
-    k_local_inverse<__nv_bfloat16><<<nb, 32 * wpb, smem, c->stream>>>(
-        nloc, c->nloc_max, c->band, c->bandCB, c->bandRB, c->bandInv, c->ntypes, kpad, (__nv_bfloat16*)c->Ainv);
+    (k_local_inverse<__nv_bfloat16><<<nb, 32 * wpb, smem, c->stream>>>(
+        nloc, c->nloc_max, c->band, c->bandCB, c->bandRB, c->bandInv, c->ntypes, kpad, (__nv_bfloat16*)c->Ainv), dd::note_launch());
   } else {
     DD_CUDA(cudaFuncSetAttribute(k_local_inverse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-    k_local_inverse<float><<<nb, 32 * wpb, smem, c->stream>>>(nloc, c->nloc_max, c->band, c->bandCB, c->bandRB,
-                                                              c->bandInv, c->ntypes, kpad, (float*)c->Ainv);
+    (k_local_inverse<float><<<nb, 32 * wpb, smem, c->stream>>>(nloc, c->nloc_max, c->band, c->bandCB, c->bandRB,
+                                                              c->bandInv, c->ntypes, kpad, (float*)c->Ainv), dd::note_launch());
   }
   DD_CUDA(cudaGetLastError());
   DD_CUDA(cudaFreeAsync(nloc, c->stream));
@@ -401,10 +401,10 @@ int gemm_setup(dd_ctx* c) {
 void launch_pack(dd_ctx* c, const double* r, cudaStream_t s) {
   const Geo& g = c->g;
   if (c->grid.precision == DD_PREC_BF16)
-    k_pack<__nv_bfloat16><<<g.nsub, 256, 0, s>>>(g, c->subs, c->slot_of_sub, r, c->kpad, (__nv_bfloat16*)c->Rpack,
-                                                 c->st);
+    (k_pack<__nv_bfloat16><<<g.nsub, 256, 0, s>>>(g, c->subs, c->slot_of_sub, r, c->kpad, (__nv_bfloat16*)c->Rpack,
+                                                 c->st), dd::note_launch());
   else
-    k_pack<float><<<g.nsub, 256, 0, s>>>(g, c->subs, c->slot_of_sub, r, c->kpad, (float*)c->Rpack, c->st);
+    (k_pack<float><<<g.nsub, 256, 0, s>>>(g, c->subs, c->slot_of_sub, r, c->kpad, (float*)c->Rpack, c->st), dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 

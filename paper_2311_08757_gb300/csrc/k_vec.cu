@@ -143,8 +143,8 @@ void launch_build_tables(dd_ctx* c) {
   DD_CUDA(cudaMemcpyToSymbolAsync(c_gwt, wt, sizeof(wt), 0, cudaMemcpyHostToDevice, c->stream));
   const long long total = (long long)g.ncls * g.ntap;
   const int nb = grid_blocks(total, kThreads);
-  if (g.p == 1) k_build_tables<1><<<nb, kThreads, 0, c->stream>>>(g, c->Vqp, c->tabA, c->tabM);
-  else k_build_tables<2><<<nb, kThreads, 0, c->stream>>>(g, c->Vqp, c->tabA, c->tabM);
+  if (g.p == 1) (k_build_tables<1><<<nb, kThreads, 0, c->stream>>>(g, c->Vqp, c->tabA, c->tabM), dd::note_launch());
+  else (k_build_tables<2><<<nb, kThreads, 0, c->stream>>>(g, c->Vqp, c->tabA, c->tabM), dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 
@@ -157,7 +157,7 @@ __global__ void k_tabS(long long n, const double* __restrict__ A, const double* 
 
 void launch_tabS(dd_ctx* c, double sigma) {
   const long long n = (long long)c->g.ncls * c->g.ntap;
-  k_tabS<<<grid_blocks(n, kThreads), kThreads, 0, c->stream>>>(n, c->tabA, c->tabM, sigma, c->tabS);
+  (k_tabS<<<grid_blocks(n, kThreads), kThreads, 0, c->stream>>>(n, c->tabA, c->tabM, sigma, c->tabS), dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 
@@ -191,8 +191,8 @@ static long long interior_work(const Geo& g) {
 void launch_stencil(dd_ctx* c, const double* tab, const double* x, double* y, cudaStream_t s) {
   const Geo& g = c->g;
   const int nb = grid_blocks(interior_work(g), kThreads);
-  if (g.p == 1) k_stencil<1, false><<<nb, kThreads, 0, s>>>(g, tab, x, y, nullptr, nullptr, nullptr);
-  else k_stencil<2, false><<<nb, kThreads, 0, s>>>(g, tab, x, y, nullptr, nullptr, nullptr);
+  if (g.p == 1) (k_stencil<1, false><<<nb, kThreads, 0, s>>>(g, tab, x, y, nullptr, nullptr, nullptr), dd::note_launch());
+  else (k_stencil<2, false><<<nb, kThreads, 0, s>>>(g, tab, x, y, nullptr, nullptr, nullptr), dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 
@@ -200,8 +200,8 @@ void launch_stencil_dot(dd_ctx* c, const double* tab, const double* x, double* y
                         unsigned* counter, cudaStream_t s) {
   const Geo& g = c->g;
   const int nb = grid_blocks(interior_work(g), kThreads);
-  if (g.p == 1) k_stencil<1, true><<<nb, kThreads, 0, s>>>(g, tab, x, y, c->red, counter, out);
-  else k_stencil<2, true><<<nb, kThreads, 0, s>>>(g, tab, x, y, c->red, counter, out);
+  if (g.p == 1) (k_stencil<1, true><<<nb, kThreads, 0, s>>>(g, tab, x, y, c->red, counter, out), dd::note_launch());
+  else (k_stencil<2, true><<<nb, kThreads, 0, s>>>(g, tab, x, y, c->red, counter, out), dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 
@@ -228,16 +228,16 @@ __global__ void k_pad(Geo g, const double* __restrict__ src, double* __restrict_
 void launch_pad(dd_ctx* c, const double* u, double* v, cudaStream_t s) {
   const Geo& g = c->g;
   const int nb = grid_blocks(g.ndof, kThreads);
-  if (g.p == 1) k_pad<1, true><<<nb, kThreads, 0, s>>>(g, u, v);
-  else k_pad<2, true><<<nb, kThreads, 0, s>>>(g, u, v);
+  if (g.p == 1) (k_pad<1, true><<<nb, kThreads, 0, s>>>(g, u, v), dd::note_launch());
+  else (k_pad<2, true><<<nb, kThreads, 0, s>>>(g, u, v), dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 
 void launch_unpad(dd_ctx* c, const double* v, double* u, cudaStream_t s) {
   const Geo& g = c->g;
   const int nb = grid_blocks(g.ndof, kThreads);
-  if (g.p == 1) k_pad<1, false><<<nb, kThreads, 0, s>>>(g, v, u);
-  else k_pad<2, false><<<nb, kThreads, 0, s>>>(g, v, u);
+  if (g.p == 1) (k_pad<1, false><<<nb, kThreads, 0, s>>>(g, v, u), dd::note_launch());
+  else (k_pad<2, false><<<nb, kThreads, 0, s>>>(g, v, u), dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 
@@ -248,7 +248,7 @@ __global__ void k_check_finite(const double* __restrict__ v, long long n, int* f
 }
 
 void launch_check_finite(const double* v, long long n, int* flag, cudaStream_t s) {
-  k_check_finite<<<grid_blocks(n, kThreads), kThreads, 0, s>>>(v, n, flag);
+  (k_check_finite<<<grid_blocks(n, kThreads), kThreads, 0, s>>>(v, n, flag), dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 
@@ -292,9 +292,9 @@ void launch_pcg_init(dd_ctx* c, const double* b, cudaStream_t s) {
   const Geo& g = c->g;
   const int nb = grid_blocks(interior_work(g), kThreads);
   if (g.p == 1)
-    k_pcg_init<1><<<nb, kThreads, 0, s>>>(g, c->tabS, c->x, b, c->r, c->st, c->red, c->cnt + CNT_INIT);
+    (k_pcg_init<1><<<nb, kThreads, 0, s>>>(g, c->tabS, c->x, b, c->r, c->st, c->red, c->cnt + CNT_INIT), dd::note_launch());
   else
-    k_pcg_init<2><<<nb, kThreads, 0, s>>>(g, c->tabS, c->x, b, c->r, c->st, c->red, c->cnt + CNT_INIT);
+    (k_pcg_init<2><<<nb, kThreads, 0, s>>>(g, c->tabS, c->x, b, c->r, c->st, c->red, c->cnt + CNT_INIT), dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(kThreads) k_pupdate(long long n, const double*
 
 void launch_pupdate(dd_ctx* c, cudaStream_t s) {
   const long long n = c->g.plen;
-  k_pupdate<<<grid_blocks(n / 2, kThreads), kThreads, 0, s>>>(n, c->z, c->p, c->st);
+  (k_pupdate<<<grid_blocks(n / 2, kThreads), kThreads, 0, s>>>(n, c->z, c->p, c->st), dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 
@@ -352,8 +352,8 @@ __global__ void __launch_bounds__(kThreads) k_matvec_pq(Geo g, const double* __r
 void launch_matvec_pq(dd_ctx* c, cudaStream_t s) {
   const Geo& g = c->g;
   const int nb = grid_blocks(interior_work(g), kThreads);
-  if (g.p == 1) k_matvec_pq<1><<<nb, kThreads, 0, s>>>(g, c->tabS, c->p, c->q, c->st, c->red, c->cnt + CNT_PQ);
-  else k_matvec_pq<2><<<nb, kThreads, 0, s>>>(g, c->tabS, c->p, c->q, c->st, c->red, c->cnt + CNT_PQ);
+  if (g.p == 1) (k_matvec_pq<1><<<nb, kThreads, 0, s>>>(g, c->tabS, c->p, c->q, c->st, c->red, c->cnt + CNT_PQ), dd::note_launch());
+  else (k_matvec_pq<2><<<nb, kThreads, 0, s>>>(g, c->tabS, c->p, c->q, c->st, c->red, c->cnt + CNT_PQ), dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 
@@ -400,8 +400,8 @@ __global__ void __launch_bounds__(kThreads) k_xr_update(long long n, const doubl
 
 void launch_xr_update(dd_ctx* c, cudaStream_t s) {
   const long long n = c->g.plen;
-  k_xr_update<<<grid_blocks(n / 2, kThreads), kThreads, 0, s>>>(n, c->p, c->q, c->x, c->r, c->st, c->red,
-                                                                 c->cnt + CNT_RR);
+  (k_xr_update<<<grid_blocks(n / 2, kThreads), kThreads, 0, s>>>(n, c->p, c->q, c->x, c->r, c->st, c->red,
+                                                                 c->cnt + CNT_RR), dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 
@@ -476,8 +476,8 @@ void launch_prolong(dd_ctx* c, int mode, cudaStream_t s) {
   const int coarse = c->grid.coarse;
   const bool f32 = (c->grid.precision != DD_PREC_FP64);
 #define DD_PROLONG(PP, TY, YP)                                                                          \
-  k_prolong<PP, TY><<<nb, kThreads, 0, s>>>(g, c->subs, c->slot_of_sub, YP, c->kpad, c->wT, c->u0,      \
-                                            coarse, c->r, c->q, c->z, mode, c->st, c->red, c->cnt + CNT_RZ)
+  (k_prolong<PP, TY><<<nb, kThreads, 0, s>>>(g, c->subs, c->slot_of_sub, YP, c->kpad, c->wT, c->u0,      \
+                                            coarse, c->r, c->q, c->z, mode, c->st, c->red, c->cnt + CNT_RZ), dd::note_launch())
   if (g.p == 1) {
     if (f32) DD_PROLONG(1, float, c->Y32); else DD_PROLONG(1, double, c->Y64);
   } else {
@@ -530,8 +530,8 @@ __global__ void __launch_bounds__(kThreads) k_outer_scale(long long n, double* _
 void launch_outer_normalize(dd_ctx* c, const double* w, double* Mw, double* xout, cudaStream_t s) {
   const long long n = c->g.plen;
   const int nb = grid_blocks(n, kThreads);
-  k_outer_dots<<<nb, kThreads, 0, s>>>(n, w, Mw, c->ost, c->red, c->cnt + CNT_OUTER0);
-  k_outer_scale<<<nb, kThreads, 0, s>>>(n, xout, w, Mw, c->ost);
+  (k_outer_dots<<<nb, kThreads, 0, s>>>(n, w, Mw, c->ost, c->red, c->cnt + CNT_OUTER0), dd::note_launch());
+  (k_outer_scale<<<nb, kThreads, 0, s>>>(n, xout, w, Mw, c->ost), dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 
@@ -557,7 +557,7 @@ void launch_outer_residual(dd_ctx* c, const double* xe, const double* Mx, double
   // Ax = A_sigma x and xAx = (x, A_sigma x); then the residual norms.
   launch_stencil_dot(c, c->tabS, xe, Ax, &c->ost->xAx, c->cnt + CNT_OUTER1, s);
   const long long n = c->g.plen;
-  k_outer_res<<<grid_blocks(n, kThreads), kThreads, 0, s>>>(n, Ax, Mx, c->ost, c->red, c->cnt + CNT_OUTER2);
+  (k_outer_res<<<grid_blocks(n, kThreads), kThreads, 0, s>>>(n, Ax, Mx, c->ost, c->red, c->cnt + CNT_OUTER2), dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 
