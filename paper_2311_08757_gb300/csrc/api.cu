@@ -164,6 +164,25 @@ void build_subdomains(dd_ctx* c) {
   c->band = (g.p == 1) ? g.nyi + 1 : w2max * g.nyi + g.nyi + 1;
   c->subs = (Sub*)dev_alloc(c, sizeof(Sub) * g.nsub);
   c->slot_of_sub = (int*)dev_alloc(c, sizeof(int) * g.nsub);
+  // index tables of the prolong-sum: owners of every x node column, row offsets per subdomain
+  std::vector<int4> ax(g.ncx), sr(g.nsub);
+  for (int a = 0; a < g.ncx; ++a) {
+    int4 v = make_int4(-1, 0, -1, 0);
+    int k = 0;
+    for (int i = 0; i < g.L && k < 2; ++i)
+      if (a >= ax_lo(g, i) && a <= ax_hi(g, i)) {
+        if (k == 0) { v.x = i; v.y = a - ax_lo(g, i); }
+        else { v.z = i; v.w = a - ax_lo(g, i); }
+        ++k;
+      }
+    ax[a] = v;
+  }
+  for (int s = 0; s < g.nsub; ++s)
+    sr[s] = make_int4(slot[s] * c->kpad, c->subs_h[s].type * c->kpad, c->subs_h[s].w2, c->subs_h[s].nloc);
+  c->axown = (int4*)dev_alloc(c, sizeof(int4) * g.ncx);
+  c->subrow = (int4*)dev_alloc(c, sizeof(int4) * g.nsub);
+  DD_CUDA(cudaMemcpyAsync(c->axown, ax.data(), sizeof(int4) * g.ncx, cudaMemcpyHostToDevice, c->stream));
+  DD_CUDA(cudaMemcpyAsync(c->subrow, sr.data(), sizeof(int4) * g.nsub, cudaMemcpyHostToDevice, c->stream));
   DD_CUDA(cudaMemcpyAsync(c->subs, c->subs_h.data(), sizeof(Sub) * g.nsub, cudaMemcpyHostToDevice, c->stream));
   DD_CUDA(cudaMemcpyAsync(c->slot_of_sub, slot.data(), sizeof(int) * g.nsub, cudaMemcpyHostToDevice, c->stream));
   DD_CUDA(cudaStreamSynchronize(c->stream));
@@ -213,33 +232,41 @@ int stage_err(dd_ctx* c, int need) {
 
 bool use_gemm(const dd_ctx* c) { return c->grid.precision != DD_PREC_FP64; }
 
-// z = M^{-1} r on device padded vectors; mode 0 standalone, 1 PCG start, 2 PCG iteration
+// z = M^{-1} r on device padded vectors; mode 0 standalone, 1 PCG start, 2 PCG iteration.
+// The coarse right-hand side is formed in the pass that gathers R_i r (local solve or pack);
+// with tensor-core local solves the coarse solve then runs on a second stream beside the
+// GEMM (the two-level operator is additive, so the branches are independent).
 void precond(dd_ctx* c, const double* r, int mode) {
   cudaStream_t s = c->stream;
   const bool coarse = c->grid.coarse != 0;
-  if (coarse) {
-    DD_CUDA(cudaEventRecord(c->ev_fork, s));
-    DD_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-    TIMED(KC_CRESTRICT, c->side, launch_coarse_restrict(c, r, c->side));
-    TIMED(KC_CSOLVE, c->side, launch_coarse_solve(c, c->side));
-    DD_CUDA(cudaEventRecord(c->ev_join, c->side));
-  }
+  double* c0 = coarse ? c->c0 : nullptr;
   if (use_gemm(c)) {
-    TIMED(KC_PACK, s, launch_pack(c, r, s));
+    TIMED(KC_PACK, s, launch_pack(c, r, c0, s));
+    if (coarse) {
+      DD_CUDA(cudaEventRecord(c->ev_fork, s));
+      DD_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+      TIMED(KC_CSOLVE, c->side, launch_coarse_solve(c, c->side));
+      DD_CUDA(cudaEventRecord(c->ev_join, c->side));
+    }
     int rc;
     TIMED(KC_GEMM, s, rc = launch_gemm(c, s));
     if (rc != DD_OK) throw Error(rc, "local GEMM launch failed");
+    if (coarse) DD_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
   } else {
-    TIMED(KC_LOCAL_FP64, s, launch_band_solve_local(c, r, s));
+    TIMED(KC_LOCAL_FP64, s, launch_band_solve_local(c, r, c0, s));
+    if (coarse) TIMED(KC_CSOLVE, s, launch_coarse_solve(c, s));
   }
-  if (coarse) DD_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
   TIMED(KC_PROLONG, s, launch_prolong(c, mode, s));
 }
 
 void pcg_iteration(dd_ctx* c) {
   cudaStream_t s = c->stream;
-  TIMED(KC_PUPDATE, s, launch_pupdate(c, s));
-  TIMED(KC_STENCIL, s, launch_matvec_pq(c, s));
+  if (c->g.p == 1) {
+    TIMED(KC_STENCIL, s, launch_fused_pq(c, s));
+  } else {
+    TIMED(KC_PUPDATE, s, launch_pupdate(c, s));
+    TIMED(KC_STENCIL, s, launch_matvec_pq(c, s));
+  }
   TIMED(KC_XRUPDATE, s, launch_xr_update(c, s));
   precond(c, c->r, 2);
 }
@@ -283,7 +310,8 @@ int pcg_run(dd_ctx* c, const double* b, double rtol, int maxit, int* iters, doub
   init.maxit = maxit;
   init.flexible = (c->flexible_opt < 0) ? (use_gemm(c) ? 1 : 0) : c->flexible_opt;
   DD_CUDA(cudaMemcpyAsync(c->st, &init, sizeof(init), cudaMemcpyHostToDevice, s));
-  DD_CUDA(cudaMemsetAsync(c->p, 0, sizeof(double) * c->g.plen, s));
+  DD_CUDA(cudaMemsetAsync(c->pb[0], 0, sizeof(double) * c->g.plen, s));
+  DD_CUDA(cudaMemsetAsync(c->pb[1], 0, sizeof(double) * c->g.plen, s));
   TIMED(KC_MISC, s, launch_pcg_init(c, b, s));
   precond(c, c->r, 1);
   const bool graph = c->use_graph && !c->timing;
@@ -382,7 +410,9 @@ int dd_setup(const dd_grid* gr, const double* V, size_t nV, void* stream, dd_ctx
   if (nV != expect) return fail(nullptr, DD_EINVAL, "nV does not match n^p ny Q^(p+1)");
   long long cols = 1;
   for (int k = 0; k < G.p; ++k) cols *= (long long)G.L * G.n + 1;
-  if (cols * ((ny + 3) / 4 * 4) > (1LL << 31)) return fail(nullptr, DD_EINVAL, "grid too large");
+  long long yp = 4;
+  while (yp < ny) yp *= 2;
+  if (cols * yp > (1LL << 31)) return fail(nullptr, DD_EINVAL, "grid too large");
 
   dd_ctx* c = nullptr;
   try {
@@ -400,7 +430,12 @@ int dd_setup(const dd_grid* gr, const double* V, size_t nV, void* stream, dd_ctx
     Geo& g = c->g;
     g.p = G.p; g.L = G.L; g.n = G.n; g.ny = ny; g.nyi = ny - 1;
     g.delta = G.overlap; g.Q = G.quad_pts;
-    g.Ypad = (ny + 3) / 4 * 4;
+    g.Ypad = 4;
+    g.ylog = 2;
+    while (g.Ypad < ny) {
+      g.Ypad *= 2;
+      g.ylog += 1;
+    }
     g.ncx = G.L * G.n + 1;
     g.nxi = G.L * G.n - 1;
     g.ncol = (G.p == 1) ? g.ncx : (long long)g.ncx * g.ncx;
@@ -437,7 +472,8 @@ int dd_setup(const dd_grid* gr, const double* V, size_t nV, void* stream, dd_ctx
     c->x = alloc_vec(c);
     c->r = alloc_vec(c);
     c->z = alloc_vec(c);
-    c->p = alloc_vec(c);
+    c->pb[0] = alloc_vec(c);
+    c->pb[1] = alloc_vec(c);
     c->q = alloc_vec(c);
     c->w1 = alloc_vec(c);
     c->w2 = alloc_vec(c);

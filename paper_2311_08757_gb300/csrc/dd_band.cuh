@@ -41,3 +41,114 @@ __device__ __forceinline__ void warp_band_solve(double* xs, int n, int b, const 
 }
 
 }  // namespace dd
+
+namespace dd {
+
+// Same solve with the band rows prefetched PF steps ahead into registers (a ring of PF
+// rows, NV = ceil(b/32) values per lane), so the global-memory latency of the factor is
+// off the sequential critical path.  The step loop is unrolled by PF so that the ring
+// index is a compile-time constant.
+template <int NV, int PF>
+__device__ __forceinline__ void warp_band_solve_pf(double* xs, int n, int b, const double* __restrict__ CB,
+                                                   const double* __restrict__ RB,
+                                                   const double* __restrict__ inv) {
+  const int lane = threadIdx.x & 31;
+  const int bs = b + 1;
+  double rb[PF][NV];
+  double iv[PF];
+  // ---- forward: L y = r, rows 0, 1, ...
+#pragma unroll
+  for (int u = 0; u < PF; ++u) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const int d = 1 + lane + 32 * v;
+      rb[u][v] = (u < n && d <= b) ? __ldg(CB + (size_t)u * bs + d) : 0.0;
+    }
+    iv[u] = (u < n) ? __ldg(inv + u) : 0.0;
+  }
+  __syncwarp();
+  for (int i0 = 0; i0 < n; i0 += PF) {
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+      const int i = i0 + u;
+      if (i < n) {
+        const double yi = xs[i] * iv[u];
+        const int dmax = min(b, n - 1 - i);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const int d = 1 + lane + 32 * v;
+          if (d <= dmax) xs[i + d] = fma(-rb[u][v], yi, xs[i + d]);
+        }
+        const int nx = i + PF;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const int d = 1 + lane + 32 * v;
+          rb[u][v] = (nx < n && d <= b) ? __ldg(CB + (size_t)nx * bs + d) : 0.0;
+        }
+        iv[u] = (nx < n) ? __ldg(inv + nx) : 0.0;
+        __syncwarp();
+        if (lane == 0) xs[i] = yi;
+      }
+    }
+  }
+  __syncwarp();
+  // ---- backward: L^T x = y, rows n-1, n-2, ...
+#pragma unroll
+  for (int u = 0; u < PF; ++u) {
+    const int i = n - 1 - u;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const int d = 1 + lane + 32 * v;
+      rb[u][v] = (i >= 0 && d <= b) ? __ldg(RB + (size_t)i * bs + d) : 0.0;
+    }
+    iv[u] = (i >= 0) ? __ldg(inv + i) : 0.0;
+  }
+  __syncwarp();
+  for (int i0 = 0; i0 < n; i0 += PF) {
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+      const int i = n - 1 - (i0 + u);
+      if (i >= 0) {
+        const double xi = xs[i] * iv[u];
+        const int dmax = min(b, i);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const int d = 1 + lane + 32 * v;
+          if (d <= dmax) xs[i - d] = fma(-rb[u][v], xi, xs[i - d]);
+        }
+        const int nx = i - PF;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const int d = 1 + lane + 32 * v;
+          rb[u][v] = (nx >= 0 && d <= b) ? __ldg(RB + (size_t)nx * bs + d) : 0.0;
+        }
+        iv[u] = (nx >= 0) ? __ldg(inv + nx) : 0.0;
+        __syncwarp();
+        if (lane == 0) xs[i] = xi;
+      }
+    }
+  }
+  __syncwarp();
+}
+
+// Host-side dispatch on the half bandwidth: BODY is compiled once per (NV, PF) pair.
+#define DD_BAND_DISPATCH(b, BODY)                                   \
+  do {                                                              \
+    if ((b) <= 32) { constexpr int NV = 1, PF = 8; BODY; }          \
+    else if ((b) <= 64) { constexpr int NV = 2, PF = 8; BODY; }     \
+    else if ((b) <= 128) { constexpr int NV = 4, PF = 6; BODY; }    \
+    else if ((b) <= 256) { constexpr int NV = 8, PF = 4; BODY; }    \
+    else if ((b) <= 320) { constexpr int NV = 10, PF = 4; BODY; }   \
+    else if ((b) <= 512) { constexpr int NV = 16, PF = 2; BODY; }   \
+    else { constexpr int NV = 0, PF = 0; BODY; }                    \
+  } while (0)
+
+// NV = 0 selects the plain solve (bandwidths beyond 512)
+template <int NV, int PF>
+__device__ __forceinline__ void band_solve(double* xs, int n, int b, const double* __restrict__ CB,
+                                           const double* __restrict__ RB, const double* __restrict__ inv) {
+  if constexpr (NV == 0) warp_band_solve(xs, n, b, CB, RB, inv);
+  else warp_band_solve_pf<NV, PF>(xs, n, b, CB, RB, inv);
+}
+
+}  // namespace dd

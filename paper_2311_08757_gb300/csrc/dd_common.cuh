@@ -86,8 +86,8 @@ struct Node {
 template <int P>
 __device__ __forceinline__ Node node_of(const Geo& g, long long t) {
   Node nd;
-  long long u = t / g.Ypad;
-  nd.slot = (int)(t - u * g.Ypad);
+  long long u = t >> g.ylog;
+  nd.slot = (int)(t & (g.Ypad - 1));
   if (P == 1) {
     nd.a1 = 1 + (int)u;
     nd.a2 = 0;

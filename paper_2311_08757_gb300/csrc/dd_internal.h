@@ -3,7 +3,8 @@
 // Device data layout ("padded layout"): a box vector is stored over ALL node columns,
 // boundary columns included, with Ypad >= ny slots per column:
 //     index(col, slot) = col * Ypad + slot,  col = a (p = 1) or a1 (Ln + 1) + a2 (p = 2),
-//     slot = j - 1 for the interior y-nodes j = 1..ny-1; slots ny-1..Ypad-1 are zero.
+//     slot = j - 1 for the interior y-nodes j = 1..ny-1; slots ny-1..Ypad-1 are zero
+//     (Ypad is the power of two >= ny, so index arithmetic is shifts and masks).
 // Boundary columns (a = 0, a = Ln) and pad slots are kept at zero by every kernel, so
 // the homogeneous Dirichlet condition (H^1_0, Sec. 1) needs no branch in the stencil:
 // the neighbours of a node next to the boundary read zeros.  The corner taps of the first
@@ -29,7 +30,8 @@ struct Geo {
   int p;        // 1 or 2
   int L, n, ny, nyi;   // nyi = ny - 1 interior y nodes
   int delta, Q;
-  int Ypad;     // slots per column (>= ny, multiple of 4)
+  int Ypad;     // slots per column: the power of two >= max(ny, 4)
+  int ylog;     // log2(Ypad)
   int ncx;      // node columns per x axis incl. boundary = L n + 1
   int nxi;      // interior nodes per x axis = L n - 1
   long long ncol;   // ncx^p
@@ -136,6 +138,8 @@ struct dd_ctx {
   std::vector<int> type_count;      // subdomains per type
   std::vector<int> type_first;      // first slot (subdomains sorted by type)
   dd::Sub* subs = nullptr;          // device, indexed by subdomain id
+  int4* axown = nullptr;            // device, per x node column a: {owner0, local col0, owner1 or -1, local col1}
+  int4* subrow = nullptr;           // device, per subdomain: {row offset in Y (slot kpad), type kpad, w2, nloc}
   int* slot_of_sub = nullptr;       // device: subdomain id -> packed row (type-sorted)
   int nloc_max = 0, kpad = 0, band = 0;
 
@@ -154,7 +158,8 @@ struct dd_ctx {
   double* wT = nullptr;            // coarse weights per type [type][kpad]: D_i R_i psi
 
   // vectors (padded length plen)
-  double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+  double *x = nullptr, *r = nullptr, *z = nullptr, *q = nullptr;
+  double* pb[2] = {nullptr, nullptr};  // search directions: iteration k reads pb[k & 1], writes pb[(k + 1) & 1]
   double *w1 = nullptr, *w2 = nullptr, *w3 = nullptr;   // outer-iteration work vectors
   double* xe = nullptr;                                  // eigenvector iterate
   double *stage_a = nullptr, *stage_b = nullptr;         // unpadded staging (ndof)
@@ -212,6 +217,7 @@ void launch_check_finite(const double* v, long long n, int* flag, cudaStream_t s
 void launch_pcg_init(dd_ctx* c, const double* b, cudaStream_t s);   // r = b - A x, rr0
 void launch_pupdate(dd_ctx* c, cudaStream_t s);                     // p = z + beta p
 void launch_matvec_pq(dd_ctx* c, cudaStream_t s);                   // q = A p, pq, alpha
+void launch_fused_pq(dd_ctx* c, cudaStream_t s);                    // p = z + beta p; q = A p; pq (p = 1)
 void launch_xr_update(dd_ctx* c, cudaStream_t s);                   // x, r, rr, done
 void launch_prolong(dd_ctx* c, int init, cudaStream_t s);           // z = ..., rz, beta
 void launch_precond(dd_ctx* c, const double* r, double* z, int pcg_mode, cudaStream_t s);
@@ -219,7 +225,7 @@ void launch_precond(dd_ctx* c, const double* r, double* z, int pcg_mode, cudaStr
 // local solves
 void launch_local_assemble(dd_ctx* c);
 int launch_band_factor(dd_ctx* c, double* CB, double* RB, double* inv, int nmat, int n, int b, int* flag);
-void launch_band_solve_local(dd_ctx* c, const double* r, cudaStream_t s);
+void launch_band_solve_local(dd_ctx* c, const double* r, double* c0, cudaStream_t s);
 void launch_band_inverse(dd_ctx* c, double* out, int ld);
 
 // cell problem
@@ -234,7 +240,7 @@ void launch_coarse_solve(dd_ctx* c, cudaStream_t s);
 
 // GEMM path
 int gemm_setup(dd_ctx* c);
-void launch_pack(dd_ctx* c, const double* r, cudaStream_t s);
+void launch_pack(dd_ctx* c, const double* r, double* c0, cudaStream_t s);
 int launch_gemm(dd_ctx* c, cudaStream_t s);
 void gemm_free(dd_ctx* c);
 

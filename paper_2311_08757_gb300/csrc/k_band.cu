@@ -15,7 +15,7 @@ namespace dd {
 // Banded Cholesky A = L L^T, one CTA per matrix, right-looking, in place in CB.
 // A zero or negative pivot sets *flag (DD_ENOTSPD) and continues with pivot 1.
 // ----------------------------------------------------------------------------------------
-__global__ void k_band_factor(double* CB, double* inv, const int* __restrict__ nvec, int nmax, int b,
+__global__ void __launch_bounds__(1024) k_band_factor(double* CB, double* inv, const int* __restrict__ nvec, int nmax, int b,
                               int* flag) {
   extern __shared__ double colk[];
   const int m = blockIdx.x;
@@ -154,10 +154,12 @@ void launch_local_assemble(dd_ctx* c) {
 // FP64 local solves y_i = A_{sigma,i}^{-1} R_i r for every subdomain (one warp each); the
 // result goes to Y[slot(i)][k]; the prolong-sum gathers it.
 // ----------------------------------------------------------------------------------------
+template <int NV, int PF>
 __global__ void k_local_solve(Geo g, const Sub* __restrict__ subs, const int* __restrict__ slot_of,
                               const double* __restrict__ r, const double* __restrict__ CB,
                               const double* __restrict__ RB, const double* __restrict__ inv, int nmax, int b,
-                              double* __restrict__ Y, int kpad, const PcgState* st) {
+                              double* __restrict__ Y, int kpad, const double* __restrict__ wT, double* c0,
+                              const PcgState* st) {
   if (st != nullptr && st->done) return;
   extern __shared__ double xs_all[];
   const int wpb = blockDim.x >> 5;
@@ -166,16 +168,25 @@ __global__ void k_local_solve(Geo g, const Sub* __restrict__ subs, const int* __
   if (s >= g.nsub) return;
   double* xs = xs_all + (size_t)wid * nmax;
   const Sub sb = subs[s];
+  // gather R_i r; the coarse right-hand side (D_i R_i psi)^T r rides along (Def. 2.1)
+  double cr = 0.0;
+  const double* wt = wT + (size_t)sb.type * kpad;
   for (int k = lane; k < sb.nloc; k += 32) {
     const int sj = k % g.nyi, cc = k / g.nyi;
     const int c1 = cc / sb.w2, c2 = cc % sb.w2;
     long long idx;
     if (g.p == 1) idx = (long long)(sb.lo1 + c1) * g.Ypad + sj;
     else idx = ((long long)(sb.lo1 + c1) * g.ncx + (sb.lo2 + c2)) * g.Ypad + sj;
-    xs[k] = r[idx];
+    const double v = r[idx];
+    xs[k] = v;
+    if (c0 != nullptr) cr = fma(wt[k], v, cr);
+  }
+  if (c0 != nullptr) {
+    cr = warp_sum(cr);
+    if (lane == 0) c0[s] = cr;
   }
   const size_t off = (size_t)sb.type * nmax;
-  warp_band_solve(xs, sb.nloc, b, CB + off * (b + 1), RB + off * (b + 1), inv + off);
+  band_solve<NV, PF>(xs, sb.nloc, b, CB + off * (b + 1), RB + off * (b + 1), inv + off);
   double* y = Y + (size_t)slot_of[s] * kpad;
   for (int k = lane; k < sb.nloc; k += 32) y[k] = xs[k];
 }
@@ -187,17 +198,20 @@ static int local_warps_per_block(int nmax) {
   return w;
 }
 
-void launch_band_solve_local(dd_ctx* c, const double* r, cudaStream_t s) {
+void launch_band_solve_local(dd_ctx* c, const double* r, double* c0, cudaStream_t s) {
   const int wpb = local_warps_per_block(c->nloc_max);
   const size_t smem = sizeof(double) * (size_t)wpb * c->nloc_max;
-  static bool attr_set = false;
-  if (!attr_set) {
-    DD_CUDA(cudaFuncSetAttribute(k_local_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-    attr_set = true;
-  }
   const int nb = (c->g.nsub + wpb - 1) / wpb;
-  (k_local_solve<<<nb, wpb * 32, smem, s>>>(c->g, c->subs, c->slot_of_sub, r, c->bandCB, c->bandRB, c->bandInv,
-                                          c->nloc_max, c->band, c->Y64, c->kpad, c->st), dd::note_launch());
+  DD_BAND_DISPATCH(c->band, {
+    static bool attr_set = false;
+    if (!attr_set) {
+      DD_CUDA(cudaFuncSetAttribute(k_local_solve<NV, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+      attr_set = true;
+    }
+    (k_local_solve<NV, PF><<<nb, wpb * 32, smem, s>>>(c->g, c->subs, c->slot_of_sub, r, c->bandCB, c->bandRB,
+                                                     c->bandInv, c->nloc_max, c->band, c->Y64, c->kpad, c->wT, c0,
+                                                     c->st), dd::note_launch());
+  });
   DD_CUDA(cudaGetLastError());
 }
 
@@ -211,7 +225,7 @@ void launch_band_solve_local(dd_ctx* c, const double* r, cudaStream_t s) {
 // ----------------------------------------------------------------------------------------
 __host__ __device__ inline int ipos(int a, int n) { return (2 * a < n) ? 2 * a : 2 * (n - 1 - a) + 1; }
 
-__global__ void k_cell_shift(const double* __restrict__ V, long long nV, double* shift) {
+__global__ void __launch_bounds__(1024) k_cell_shift(const double* __restrict__ V, long long nV, double* shift) {
   double m = 1e300;
   for (long long t = threadIdx.x; t < nV; t += blockDim.x) m = fmin(m, V[t]);
   __shared__ double sm[32];
@@ -303,24 +317,27 @@ __device__ void cta_sum(double (&v)[NV]) {   // result broadcast to every thread
 }
 
 struct CellOut {
-  double sigma, eta, drho;
+  double sigma, eta, drho, shift;
   int iters, status;
 };
 
-__global__ void k_cell_iterate(Geo g, const double* __restrict__ tabA, const double* __restrict__ tabM,
+constexpr int kCellThreads = 512;   // <= 128 registers per thread (prefetch ring of the band solve)
+
+template <int NV, int PF>
+__global__ void __launch_bounds__(kCellThreads, 1) k_cell_iterate(Geo g, const double* __restrict__ tabA, const double* __restrict__ tabM,
                                const double* __restrict__ CB, const double* __restrict__ RB,
-                               const double* __restrict__ inv, int b, int maxit, double* psi_out,
-                               CellOut* out) {
+                               const double* __restrict__ inv, int b, int maxit, double tol_drho, double tol_eta,
+                               int warm, double* psi_out, CellOut* out) {
   extern __shared__ double sm[];
   const int ncol = (g.p == 1) ? g.n : g.n * g.n;
   const int ncell = ncol * g.nyi;
   double* x = sm;
   double* y = sm + ncell;
   double* xs = sm + 2 * ncell;
-  // x0 = 1 / ||1||_M
-  for (int k = threadIdx.x; k < ncell; k += blockDim.x) x[k] = 1.0;
+  // start from 1, or from psi_out (warm start of the refined shift)
+  for (int k = threadIdx.x; k < ncell; k += blockDim.x) x[k] = warm ? psi_out[k] : 1.0;
   __syncthreads();
-  double rho_prev = 1e300;
+  double rho_prev = 1e300, eta_prev = 1e300;
   int it = 0, stable = 0, status = 0;
   double eta = 0.0, drho = 0.0, rho = 0.0;
   for (it = 1; it <= maxit; ++it) {
@@ -335,7 +352,7 @@ __global__ void k_cell_iterate(Geo g, const double* __restrict__ tabA, const dou
       xs[ri] = y[k];
     }
     __syncthreads();
-    if (threadIdx.x < 32) warp_band_solve(xs, ncell, b, CB, RB, inv);
+    if (threadIdx.x < 32) band_solve<NV, PF>(xs, ncell, b, CB, RB, inv);
     __syncthreads();
     // w (natural order) -> x
     for (int k = threadIdx.x; k < ncell; k += blockDim.x) {
@@ -379,11 +396,14 @@ __global__ void k_cell_iterate(Geo g, const double* __restrict__ tabA, const dou
     eta = sqrt(d3[0] / d3[1]) / fabs(rho);
     drho = fabs(rho - rho_prev);
     if (!isfinite(rho)) { status = DD_ENAN; break; }
-    if (drho <= 1e-14 * fabs(rho) && eta <= 1e-11) {
+    // at the residual target, stop once the Rayleigh quotient is stationary or the residual
+    // no longer improves (its rounding floor, which grows as the shift nears sigma_1)
+    if (eta <= tol_eta && (drho <= tol_drho * fabs(rho) || eta >= 0.5 * eta_prev)) {
       if (++stable >= 2) break;
     } else {
       stable = 0;
     }
+    eta_prev = eta;
     rho_prev = rho;
   }
   for (int k = threadIdx.x; k < ncell; k += blockDim.x) psi_out[k] = x[k];
@@ -396,59 +416,107 @@ __global__ void k_cell_iterate(Geo g, const double* __restrict__ tabA, const dou
   }
 }
 
-int cell_eigenpair(dd_ctx* c) {
+// one phase of the cell solve: assemble A_# - s M_#, factor, iterate; returns false if the
+// factorisation met a non-positive pivot (s not below sigma_1)
+static bool cell_phase(dd_ctx* c, double* shift, bool from_minV, double margin_frac, int warm, double tol_drho,
+                       double tol_eta, int maxit, CellOut* out_h) {
   const Geo& g = c->g;
-  const int ncol = (g.p == 1) ? g.n : g.n * g.n;
-  const int ncell = ncol * g.nyi;
-  const int b = (g.p == 1) ? 2 * g.nyi + 1 : 2 * g.n * g.nyi + 2 * g.nyi + 1;
-  c->ncell = ncell;
-  c->cell_band = b;
+  const int ncell = (int)c->ncell;
+  const int b = c->cell_band;
   const size_t cbsz = sizeof(double) * (size_t)ncell * (b + 1);
-  double *CB = nullptr, *RB = nullptr, *inv = nullptr, *shift = nullptr;
+  double *CB = nullptr, *RB = nullptr, *inv = nullptr;
   CellOut* out = nullptr;
   int* flag = c->dev_err + 1;
+  int* nvec = nullptr;
   DD_CUDA(cudaMallocAsync(&CB, cbsz, c->stream));
   DD_CUDA(cudaMallocAsync(&RB, cbsz, c->stream));
   DD_CUDA(cudaMallocAsync(&inv, sizeof(double) * ncell, c->stream));
-  DD_CUDA(cudaMallocAsync(&shift, sizeof(double), c->stream));
   DD_CUDA(cudaMallocAsync(&out, sizeof(CellOut), c->stream));
+  DD_CUDA(cudaMallocAsync(&nvec, sizeof(int), c->stream));
   DD_CUDA(cudaMemsetAsync(CB, 0, cbsz, c->stream));
   DD_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), c->stream));
-  long long nV = (long long)ncol * g.ny;
-  for (int k = 0; k <= g.p; ++k) nV *= g.Q;
-  (k_cell_shift<<<1, 1024, 0, c->stream>>>(c->Vqp, nV, shift), dd::note_launch());
-  (k_cell_assemble<<<grid_blocks(ncell, 128), 128, 0, c->stream>>>(g, c->tabA, c->tabM, shift, b, CB), dd::note_launch());
-  DD_CUDA(cudaGetLastError());
-  // factor (one matrix of size ncell)
-  {
-    int* nvec = nullptr;
-    DD_CUDA(cudaMallocAsync(&nvec, sizeof(int), c->stream));
-    DD_CUDA(cudaMemcpyAsync(nvec, &ncell, sizeof(int), cudaMemcpyHostToDevice, c->stream));
-    const int threads = ((long long)b * b > 4096) ? 1024 : 256;
-    (k_band_factor<<<1, threads, sizeof(double) * (b + 1), c->stream>>>(CB, inv, nvec, ncell, b, flag), dd::note_launch());
-    (k_band_rows<<<grid_blocks((long long)ncell * (b + 1), kThreads), kThreads, 0, c->stream>>>(CB, RB, nvec, 1,
-                                                                                              ncell, b), dd::note_launch());
-    DD_CUDA(cudaGetLastError());
-    DD_CUDA(cudaFreeAsync(nvec, c->stream));
+  DD_CUDA(cudaMemcpyAsync(nvec, &ncell, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  if (from_minV) {
+    long long nV = (long long)((g.p == 1) ? g.n : g.n * g.n) * g.ny;
+    for (int k = 0; k <= g.p; ++k) nV *= g.Q;
+    (k_cell_shift<<<1, 1024, 0, c->stream>>>(c->Vqp, nV, shift), dd::note_launch());
+  } else {
+    // shift = rho - margin_frac (rho - s_previous), from the previous phase's result
+    const double s_new = out_h->sigma - margin_frac * (out_h->sigma - out_h->shift);
+    DD_CUDA(cudaMemcpyAsync(shift, &s_new, sizeof(double), cudaMemcpyHostToDevice, c->stream));
   }
-  const size_t smem = sizeof(double) * 3 * (size_t)ncell;
-  DD_CUDA(cudaFuncSetAttribute(k_cell_iterate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  (k_cell_iterate<<<1, 1024, smem, c->stream>>>(g, c->tabA, c->tabM, CB, RB, inv, b, 20000, c->psi_cell, out), dd::note_launch());
+  (k_cell_assemble<<<grid_blocks(ncell, 128), 128, 0, c->stream>>>(g, c->tabA, c->tabM, shift, b, CB), dd::note_launch());
+  const int threads = ((long long)b * b > 4096) ? 1024 : 256;
+  (k_band_factor<<<1, threads, sizeof(double) * (b + 1), c->stream>>>(CB, inv, nvec, ncell, b, flag), dd::note_launch());
+  (k_band_rows<<<grid_blocks((long long)ncell * (b + 1), kThreads), kThreads, 0, c->stream>>>(CB, RB, nvec, 1, ncell,
+                                                                                            b), dd::note_launch());
   DD_CUDA(cudaGetLastError());
-  CellOut h;
   int fl = 0;
-  DD_CUDA(cudaMemcpyAsync(&h, out, sizeof(CellOut), cudaMemcpyDeviceToHost, c->stream));
   DD_CUDA(cudaMemcpyAsync(&fl, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  DD_CUDA(cudaStreamSynchronize(c->stream));
+  bool ok = (fl == 0);
+  if (ok) {
+    const size_t smem = sizeof(double) * 3 * (size_t)ncell;
+    DD_BAND_DISPATCH(b, {
+      DD_CUDA(cudaFuncSetAttribute(k_cell_iterate<NV, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      (k_cell_iterate<NV, PF><<<1, kCellThreads, smem, c->stream>>>(g, c->tabA, c->tabM, CB, RB, inv, b, maxit, tol_drho,
+                                                           tol_eta, warm, c->psi_cell, out), dd::note_launch());
+    });
+    DD_CUDA(cudaGetLastError());
+    DD_CUDA(cudaMemcpyAsync(out_h, out, sizeof(CellOut), cudaMemcpyDeviceToHost, c->stream));
+    double sh = 0.0;
+    DD_CUDA(cudaMemcpyAsync(&sh, shift, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    DD_CUDA(cudaStreamSynchronize(c->stream));
+    out_h->shift = sh;
+  }
   DD_CUDA(cudaFreeAsync(CB, c->stream));
   DD_CUDA(cudaFreeAsync(RB, c->stream));
   DD_CUDA(cudaFreeAsync(inv, c->stream));
-  DD_CUDA(cudaFreeAsync(shift, c->stream));
   DD_CUDA(cudaFreeAsync(out, c->stream));
+  DD_CUDA(cudaFreeAsync(nvec, c->stream));
   DD_CUDA(cudaStreamSynchronize(c->stream));
-  if (fl) throw Error(DD_ENOTSPD, "cell matrix A_# - s M_# not positive definite");
+  return ok;
+}
+
+// Two phases: shift s0 = min V - 1 (safe) until the Rayleigh quotient has settled to 1e-6,
+// then s1 = rho - 0.02 (rho - s0), warm-started, to full accuracy.  The refined shift is
+// below sigma_1 whenever the eigenvalue error is under 2% of rho - s0; if it is not, the
+// factorisation meets a non-positive pivot and the solve continues with the safe shift
+// (a larger margin is tried first).
+int cell_eigenpair(dd_ctx* c) {
+  const Geo& g = c->g;
+  const int ncol = (g.p == 1) ? g.n : g.n * g.n;
+  c->ncell = (long long)ncol * g.nyi;
+  c->cell_band = (g.p == 1) ? 2 * g.nyi + 1 : 2 * g.n * g.nyi + 2 * g.nyi + 1;
+  double* shift = nullptr;
+  DD_CUDA(cudaMallocAsync(&shift, sizeof(double), c->stream));
+  CellOut h{};
+  if (!cell_phase(c, shift, true, 0.0, 0, 1e-6, 1e-3, 20000, &h)) {
+    DD_CUDA(cudaFreeAsync(shift, c->stream));
+    throw Error(DD_ENOTSPD, "cell matrix A_# - s M_# not positive definite");
+  }
+  if (h.status != 0 && h.status != DD_EMAXIT) throw Error(h.status, "cell inverse iteration failed");
+  int iters = h.iters;
+  CellOut h1 = h;
+  bool refined = false;
+  for (double frac : {0.02, 0.2}) {
+    CellOut h2 = h1;
+    if (cell_phase(c, shift, false, frac, 1, 1e-14, 1e-10, 2000, &h2)) {
+      h = h2;
+      iters += h2.iters;
+      refined = true;
+      break;
+    }
+  }
+  if (!refined) {
+    if (!cell_phase(c, shift, true, 0.0, 1, 1e-14, 1e-10, 20000, &h)) throw Error(DD_ENOTSPD, "cell factorisation");
+    iters += h.iters;
+  }
+  DD_CUDA(cudaFreeAsync(shift, c->stream));
+  DD_CUDA(cudaStreamSynchronize(c->stream));
   if (h.status != 0 && h.status != DD_EMAXIT) throw Error(h.status, "cell inverse iteration failed");
   c->sigma = h.sigma;
-  c->cell_iters = h.iters;
+  c->cell_iters = iters;
   return h.status;
 }
 

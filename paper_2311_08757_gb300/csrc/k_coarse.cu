@@ -168,13 +168,17 @@ int coarse_assemble(dd_ctx* c) {
 // p = 1: cyclic reduction for the tridiagonal A_0 (symmetric positive definite, so the
 // odd-even elimination needs no pivoting).  Equations j = 1..N' (N' = 2^m - 1 >= N,
 // padded with identity rows): a_j x_{j-1} + b_j x_j + c_j x_{j+1} = f_j.
-// Layout of c->cr: alpha[m][N'+2], gamma[m][N'+2], a[N'+2], binv[N'+2], cc[N'+2].
+// Level l (stride s = 2^l) eliminates x_{j-s}, x_{j+s} from the equations j = 2s, 4s, ...
+// with multipliers alpha, gamma, stored packed per level (count floor(N'/2s) each).
+// Layout of c->cr: alpha[N'], gamma[N'], a[W], binv[W], cc[W], b[W] (W = N' + 2).
 // ----------------------------------------------------------------------------------------
-__global__ void k_cr_setup(const double* __restrict__ A0nb, int N, int m, int Np, double* cr, int* flag) {
+__device__ __forceinline__ int cr_count(int Np, int l) { return Np >> (l + 1); }
+
+__global__ void __launch_bounds__(1024) k_cr_setup(const double* __restrict__ A0nb, int N, int m, int Np, double* cr, int* flag) {
   const int W = Np + 2;
   double* alpha = cr;
-  double* gamma = cr + (size_t)m * W;
-  double* a = cr + (size_t)2 * m * W;
+  double* gamma = cr + Np;
+  double* a = cr + 2 * (size_t)Np;
   double* binv = a + W;
   double* cc = binv + W;
   double* b = cc + W;   // work: b values
@@ -185,23 +189,26 @@ __global__ void k_cr_setup(const double* __restrict__ A0nb, int N, int m, int Np
       aj = (j >= 2) ? A0nb[(size_t)(j - 1) * 3 + 0] : 0.0;
       cj = (j <= N - 1) ? A0nb[(size_t)(j - 1) * 3 + 2] : 0.0;
     }
-    if (j == 0 || j == W - 1) bj = 1.0;
     a[j] = aj;
     b[j] = bj;
     cc[j] = cj;
   }
   __syncthreads();
+  int off = 0;
   for (int l = 0; l < m - 1; ++l) {
     const int s = 1 << l;
-    for (int j = 2 * s + 2 * s * threadIdx.x; j <= Np; j += 2 * s * blockDim.x) {
+    const int cnt = cr_count(Np, l);
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+      const int j = 2 * s * (t + 1);
       const double al = -a[j] / b[j - s];
       const double ga = -cc[j] / b[j + s];
-      alpha[(size_t)l * W + j] = al;
-      gamma[(size_t)l * W + j] = ga;
+      alpha[off + t] = al;
+      gamma[off + t] = ga;
       b[j] = b[j] + al * cc[j - s] + ga * a[j + s];
       a[j] = al * a[j - s];
       cc[j] = ga * cc[j + s];
     }
+    off += cnt;
     __syncthreads();
   }
   for (int j = threadIdx.x; j < W; j += blockDim.x) {
@@ -210,22 +217,37 @@ __global__ void k_cr_setup(const double* __restrict__ A0nb, int N, int m, int Np
   }
 }
 
-__global__ void k_cr_solve(const double* __restrict__ cr, int N, int m, int Np, const double* __restrict__ rhs,
-                           double* __restrict__ x, const PcgState* st) {
+__global__ void __launch_bounds__(1024) k_cr_solve(const double* __restrict__ cr, int N, int m, int Np, const double* __restrict__ rhs,
+                           double* __restrict__ x, const PcgState* st, int staged) {
   if (st != nullptr && st->done) return;
-  extern __shared__ double f[];
+  extern __shared__ double sm_cr[];
   const int W = Np + 2;
-  const double* alpha = cr;
-  const double* gamma = cr + (size_t)m * W;
-  const double* a = cr + (size_t)2 * m * W;
+  double* f = sm_cr;
+  // the coefficients (2 N' + 3 W doubles) are staged into shared memory in one coalesced
+  // sweep when they fit, so that every level waits on shared memory only
+  const double* src = cr;
+  if (staged) {
+    double* dst = sm_cr + W;
+    const int tot = 2 * Np + 3 * W;
+    for (int t = threadIdx.x; t < tot; t += blockDim.x) dst[t] = __ldg(cr + t);
+    src = dst;
+  }
+  const double* alpha = src;
+  const double* gamma = src + Np;
+  const double* a = src + 2 * (size_t)Np;
   const double* binv = a + W;
   const double* cc = binv + W;
   for (int j = threadIdx.x; j < W; j += blockDim.x) f[j] = (j >= 1 && j <= N) ? rhs[j - 1] : 0.0;
   __syncthreads();
+  int off = 0;
   for (int l = 0; l < m - 1; ++l) {
     const int s = 1 << l;
-    for (int j = 2 * s + 2 * s * threadIdx.x; j <= Np; j += 2 * s * blockDim.x)
-      f[j] = fma(alpha[(size_t)l * W + j], f[j - s], fma(gamma[(size_t)l * W + j], f[j + s], f[j]));
+    const int cnt = cr_count(Np, l);
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+      const int j = 2 * s * (t + 1);
+      f[j] = fma(alpha[off + t], f[j - s], fma(gamma[off + t], f[j + s], f[j]));
+    }
+    off += cnt;
     __syncthreads();
   }
   const int root = 1 << (m - 1);
@@ -234,7 +256,7 @@ __global__ void k_cr_solve(const double* __restrict__ cr, int N, int m, int Np, 
   for (int l = m - 2; l >= 0; --l) {
     const int s = 1 << l;
     for (int j = s + 2 * s * threadIdx.x; j <= Np; j += 2 * s * blockDim.x) {
-      const double left = f[j - s];                       // j - s >= 0, f[0] = 0
+      const double left = f[j - s];
       const double right = (j + s <= Np) ? f[j + s] : 0.0;
       f[j] = (f[j] - a[j] * left - cc[j] * right) * binv[j];
     }
@@ -244,6 +266,7 @@ __global__ void k_cr_solve(const double* __restrict__ cr, int N, int m, int Np, 
 }
 
 // p = 2: dense inverse rows from the banded factor (identity right-hand sides)
+template <int NV, int PF>
 __global__ void k_band_inverse_rows(int n, int b, const double* __restrict__ CB, const double* __restrict__ RB,
                                     const double* __restrict__ inv, double* out) {
   extern __shared__ double xs_all[];
@@ -252,7 +275,7 @@ __global__ void k_band_inverse_rows(int n, int b, const double* __restrict__ CB,
   if (col >= n) return;
   double* xs = xs_all + (size_t)wid * n;
   for (int k = lane; k < n; k += 32) xs[k] = (k == col) ? 1.0 : 0.0;
-  warp_band_solve(xs, n, b, CB, RB, inv);
+  band_solve<NV, PF>(xs, n, b, CB, RB, inv);
   for (int k = lane; k < n; k += 32) out[(size_t)col * n + k] = xs[k];
 }
 
@@ -281,7 +304,7 @@ int coarse_factor(dd_ctx* c) {
     c->cr_m = m;
     c->cr_np = Np;
     const size_t W = (size_t)Np + 2;
-    c->cr = (double*)dev_alloc(c, sizeof(double) * W * (2 * m + 4));
+    c->cr = (double*)dev_alloc(c, sizeof(double) * (2 * (size_t)Np + 4 * W));
     (k_cr_setup<<<1, 1024, 0, c->stream>>>(c->A0band, N, m, Np, c->cr, flag), dd::note_launch());
     DD_CUDA(cudaGetLastError());
   } else {
@@ -309,8 +332,12 @@ int coarse_factor(dd_ctx* c) {
     c->A0inv = (double*)dev_alloc(c, sizeof(double) * (size_t)N * N);
     const int wpb = (N * 8 <= 48 * 1024) ? 4 : 1;
     const size_t smem = sizeof(double) * (size_t)wpb * N;
-    DD_CUDA(cudaFuncSetAttribute(k_band_inverse_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-    (k_band_inverse_rows<<<(N + wpb - 1) / wpb, 32 * wpb, smem, c->stream>>>(N, b, CB, RB, inv, c->A0inv), dd::note_launch());
+    DD_BAND_DISPATCH(b, {
+      DD_CUDA(cudaFuncSetAttribute(k_band_inverse_rows<NV, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   220 * 1024));
+      (k_band_inverse_rows<NV, PF><<<(N + wpb - 1) / wpb, 32 * wpb, smem, c->stream>>>(N, b, CB, RB, inv, c->A0inv),
+       dd::note_launch());
+    });
     DD_CUDA(cudaGetLastError());
   }
   int fl = 0;
@@ -341,13 +368,17 @@ void launch_coarse_restrict(dd_ctx* c, const double* r, cudaStream_t s) {
 void launch_coarse_solve(dd_ctx* c, cudaStream_t s) {
   const Geo& g = c->g;
   if (g.p == 1) {
-    const size_t smem = sizeof(double) * ((size_t)c->cr_np + 2);
+    const size_t W = (size_t)c->cr_np + 2;
+    const size_t full = sizeof(double) * (2 * (size_t)c->cr_np + 4 * W);   // f + coefficients
+    const int staged = full <= 210 * 1024 ? 1 : 0;
+    const size_t smem = staged ? full : sizeof(double) * W;
     static bool attr = false;
     if (!attr) {
       DD_CUDA(cudaFuncSetAttribute(k_cr_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
       attr = true;
     }
-    (k_cr_solve<<<1, 1024, smem, s>>>(c->cr, g.nsub, c->cr_m, c->cr_np, c->c0, c->u0, c->st), dd::note_launch());
+    (k_cr_solve<<<1, 1024, smem, s>>>(c->cr, g.nsub, c->cr_m, c->cr_np, c->c0, c->u0, c->st, staged),
+     dd::note_launch());
   } else {
     const int N = g.nsub;
     (k_gemv_rows<<<(N + 7) / 8, 256, 0, s>>>(N, c->A0inv, c->c0, c->u0, c->st), dd::note_launch());

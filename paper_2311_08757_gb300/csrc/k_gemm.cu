@@ -292,7 +292,7 @@ __device__ __forceinline__ float round_to<float>(double v) {
   return __uint_as_float(r);
 }
 
-template <typename T>
+template <typename T, int NV, int PF>
 __global__ void k_local_inverse(const int* __restrict__ nloc, int nmax, int b, const double* __restrict__ CB,
                                 const double* __restrict__ RB, const double* __restrict__ inv, int ntypes, int kpad,
                                 T* __restrict__ out) {
@@ -306,30 +306,41 @@ __global__ void k_local_inverse(const int* __restrict__ nloc, int nmax, int b, c
   double* xs = xs_all + (size_t)wid * nmax;
   for (int k = lane; k < n; k += 32) xs[k] = (k == col) ? 1.0 : 0.0;
   const size_t off = (size_t)ty * nmax;
-  warp_band_solve(xs, n, b, CB + off * (b + 1), RB + off * (b + 1), inv + off);
+  band_solve<NV, PF>(xs, n, b, CB + off * (b + 1), RB + off * (b + 1), inv + off);
   T* row = out + ((size_t)ty * kpad + col) * kpad;
   for (int k = lane; k < n; k += 32) row[k] = round_to<T>(xs[k]);
 }
 
-// R_i r rounded, subdomain rows in type-sorted order, zero tail up to kpad
+// R_i r rounded, subdomain rows in type-sorted order, zero tail up to kpad; the coarse
+// right-hand side c_i = (D_i R_i psi)^T r (Def. 2.1) is formed in FP64 in the same pass.
+// Block per subdomain, warp per local column (the y nodes of a column are contiguous in r).
 template <typename T>
 __global__ void k_pack(Geo g, const Sub* __restrict__ subs, const int* __restrict__ slot_of,
-                       const double* __restrict__ r, int kpad, T* __restrict__ out, const PcgState* st) {
+                       const double* __restrict__ r, int kpad, T* __restrict__ out, const double* __restrict__ wT,
+                       double* c0, const PcgState* st) {
   if (st != nullptr && st->done) return;
   const int s = blockIdx.x;
   const Sub sb = subs[s];
   T* row = out + (size_t)slot_of[s] * kpad;
-  for (int k = threadIdx.x; k < kpad; k += blockDim.x) {
-    double v = 0.0;
-    if (k < sb.nloc) {
-      const int sj = k % g.nyi, cc = k / g.nyi;
-      const int c1 = cc / sb.w2, c2 = cc % sb.w2;
-      long long idx;
-      if (g.p == 1) idx = (long long)(sb.lo1 + c1) * g.Ypad + sj;
-      else idx = ((long long)(sb.lo1 + c1) * g.ncx + (sb.lo2 + c2)) * g.Ypad + sj;
-      v = r[idx];
+  const double* wt = wT + (size_t)sb.type * kpad;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double acc[1] = {0.0};
+  const int ncols = sb.w1 * sb.w2;
+  for (int cc = warp; cc < ncols; cc += nw) {
+    const int c1 = cc / sb.w2, c2 = cc - c1 * sb.w2;
+    const long long base = (g.p == 1) ? (long long)(sb.lo1 + c1) * g.Ypad
+                                      : ((long long)(sb.lo1 + c1) * g.ncx + (sb.lo2 + c2)) * g.Ypad;
+    for (int sj = lane; sj < g.nyi; sj += 32) {
+      const int k = cc * g.nyi + sj;
+      const double v = r[base + sj];
+      acc[0] = fma(wt[k], v, acc[0]);
+      row[k] = round_to<T>(v);
     }
-    row[k] = round_to<T>(v);
+  }
+  for (int k = sb.nloc + threadIdx.x; k < kpad; k += blockDim.x) row[k] = round_to<T>(0.0);
+  if (c0 != nullptr) {
+    block_sum<1>(acc);
+    if (threadIdx.x == 0) c0[s] = acc[0];
   }
 }
 
@@ -361,16 +372,21 @@ int gemm_setup(dd_ctx* c) {
   const size_t smem = sizeof(double) * (size_t)wpb * c->nloc_max;
   const long long jobs = (long long)c->ntypes * c->nloc_max;
   const int nb = (int)((jobs + wpb - 1) / wpb);
-  if (bf16) {
-    DD_CUDA(cudaFuncSetAttribute(k_local_inverse<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 220 * 1024));
-    (k_local_inverse<__nv_bfloat16><<<nb, 32 * wpb, smem, c->stream>>>(
-        nloc, c->nloc_max, c->band, c->bandCB, c->bandRB, c->bandInv, c->ntypes, kpad, (__nv_bfloat16*)c->Ainv), dd::note_launch());
-  } else {
-    DD_CUDA(cudaFuncSetAttribute(k_local_inverse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-    (k_local_inverse<float><<<nb, 32 * wpb, smem, c->stream>>>(nloc, c->nloc_max, c->band, c->bandCB, c->bandRB,
-                                                              c->bandInv, c->ntypes, kpad, (float*)c->Ainv), dd::note_launch());
-  }
+  DD_BAND_DISPATCH(c->band, {
+    if (bf16) {
+      DD_CUDA(cudaFuncSetAttribute(k_local_inverse<__nv_bfloat16, NV, PF>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+      (k_local_inverse<__nv_bfloat16, NV, PF><<<nb, 32 * wpb, smem, c->stream>>>(
+           nloc, c->nloc_max, c->band, c->bandCB, c->bandRB, c->bandInv, c->ntypes, kpad, (__nv_bfloat16*)c->Ainv),
+       dd::note_launch());
+    } else {
+      DD_CUDA(cudaFuncSetAttribute(k_local_inverse<float, NV, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   220 * 1024));
+      (k_local_inverse<float, NV, PF><<<nb, 32 * wpb, smem, c->stream>>>(
+           nloc, c->nloc_max, c->band, c->bandCB, c->bandRB, c->bandInv, c->ntypes, kpad, (float*)c->Ainv),
+       dd::note_launch());
+    }
+  });
   DD_CUDA(cudaGetLastError());
   DD_CUDA(cudaFreeAsync(nloc, c->stream));
   // plan: tensor maps and tile list
@@ -398,13 +414,14 @@ int gemm_setup(dd_ctx* c) {
   return DD_OK;
 }
 
-void launch_pack(dd_ctx* c, const double* r, cudaStream_t s) {
+void launch_pack(dd_ctx* c, const double* r, double* c0, cudaStream_t s) {
   const Geo& g = c->g;
   if (c->grid.precision == DD_PREC_BF16)
     (k_pack<__nv_bfloat16><<<g.nsub, 256, 0, s>>>(g, c->subs, c->slot_of_sub, r, c->kpad, (__nv_bfloat16*)c->Rpack,
-                                                 c->st), dd::note_launch());
+                                                 c->wT, c0, c->st), dd::note_launch());
   else
-    (k_pack<float><<<g.nsub, 256, 0, s>>>(g, c->subs, c->slot_of_sub, r, c->kpad, (float*)c->Rpack, c->st), dd::note_launch());
+    (k_pack<float><<<g.nsub, 256, 0, s>>>(g, c->subs, c->slot_of_sub, r, c->kpad, (float*)c->Rpack, c->wT, c0,
+                                         c->st), dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 

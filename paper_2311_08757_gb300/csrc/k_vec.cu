@@ -298,34 +298,122 @@ void launch_pcg_init(dd_ctx* c, const double* b, cudaStream_t s) {
   DD_CUDA(cudaGetLastError());
 }
 
-// p = z + beta p (whole padded vector; boundary columns and pads stay zero).
-__global__ void __launch_bounds__(kThreads) k_pupdate(long long n, const double* __restrict__ z,
-                                                      double* __restrict__ p, const PcgState* st) {
+// p_k = z + beta p_{k-1} (whole padded vector; boundary columns and pads stay zero).
+// Iteration k reads pb[k & 1] and writes pb[(k + 1) & 1] (k = completed iterations).
+__device__ __forceinline__ const double* p_prev(const double* pb0, const double* pb1, int k) {
+  return (k & 1) ? pb1 : pb0;
+}
+__device__ __forceinline__ double* p_cur(double* pb0, double* pb1, int k) { return (k & 1) ? pb0 : pb1; }
+
+__global__ void __launch_bounds__(kThreads) k_pupdate(long long n, const double* __restrict__ z, double* pb0,
+                                                      double* pb1, const PcgState* st) {
   if (st->done) return;
   const double beta = st->beta;
+  const int k = st->iter;
   const double2* z2 = reinterpret_cast<const double2*>(z);
-  double2* p2 = reinterpret_cast<double2*>(p);
+  const double2* pp = reinterpret_cast<const double2*>(p_prev(pb0, pb1, k));
+  double2* pc = reinterpret_cast<double2*>(p_cur(pb0, pb1, k));
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n / 2;
        t += (long long)gridDim.x * blockDim.x) {
-    double2 a = z2[t], b = p2[t];
+    double2 a = z2[t], b = pp[t];
     b.x = fma(beta, b.x, a.x);
     b.y = fma(beta, b.y, a.y);
-    p2[t] = b;
+    pc[t] = b;
   }
 }
 
 void launch_pupdate(dd_ctx* c, cudaStream_t s) {
   const long long n = c->g.plen;
-  (k_pupdate<<<grid_blocks(n / 2, kThreads), kThreads, 0, s>>>(n, c->z, c->p, c->st), dd::note_launch());
+  (k_pupdate<<<grid_blocks(n / 2, kThreads), kThreads, 0, s>>>(n, c->z, c->pb[0], c->pb[1], c->st), dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+}
+
+// p = 1 fused K1: tiles of TC node columns plus one halo column per side are staged in
+// shared memory as p_k = z + beta p_{k-1} (each value computed once per tile), written
+// back for the tile's own columns, and the 9-point stencil q = A_sigma p_k and (p_k, q)
+// are evaluated from shared memory.
+constexpr int kFusedCols = 32;
+
+__global__ void __launch_bounds__(kThreads) k_fused_pq(Geo g, const double* __restrict__ tab,
+                                                       const double* __restrict__ z, double* pb0, double* pb1,
+                                                       double* __restrict__ q, PcgState* st, double* partials,
+                                                       unsigned* counter) {
+  if (st->done) return;
+  extern __shared__ double sp_raw[];
+  double* sp = sp_raw + 1;   // one zero guard element on each side
+  const int k = st->iter;
+  const double beta = st->beta;
+  const double* __restrict__ pp = p_prev(pb0, pb1, k);
+  double* __restrict__ pc = p_cur(pb0, pb1, k);
+  const int Y = g.Ypad, yl = g.ylog;
+  const int ntiles = (g.nxi + kFusedCols - 1) / kFusedCols;
+  if (threadIdx.x == 0) {
+    sp_raw[0] = 0.0;
+    sp_raw[(kFusedCols + 2) * Y + 1] = 0.0;
+  }
+  double acc[1] = {0.0};
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int a0 = 1 + tile * kFusedCols;
+    const int own = min(kFusedCols, g.nxi - (a0 - 1));
+    const int nload = (own + 2) << yl;
+    const long long gbase = (long long)(a0 - 1) << yl;
+    __syncthreads();
+    for (int e = threadIdx.x; e < nload; e += blockDim.x) sp[e] = fma(beta, pp[gbase + e], z[gbase + e]);
+    if (threadIdx.x == 0) sp[nload] = 0.0;   // corner tap of the last (pad) slot of a partial tile
+    __syncthreads();
+    const int nown = own << yl;
+    for (int e = threadIdx.x; e < nown; e += blockDim.x) {
+      const int se = e + Y;
+      const long long gi = gbase + se;
+      const double pv = sp[se];
+      pc[gi] = pv;
+      const int col = a0 + (e >> yl), slot = e & (Y - 1);
+      const int cls = (col % g.n) * Y + slot;
+      double qv = 0.0;
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx)
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+          qv = fma(__ldg(tab + (size_t)((dx + 1) * 3 + (dy + 1)) * g.ncls + cls), sp[se + dx * Y + dy], qv);
+      q[gi] = qv;
+      acc[0] = fma(pv, qv, acc[0]);
+    }
+  }
+  double tot[1];
+  if (grid_sum_last<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
+    const double pq = tot[0];
+    st->pq = pq;
+    if (!(pq > 0.0)) {
+      st->status = isfinite(pq) ? DD_ENOTSPD : DD_ENAN;
+      st->done = 1;
+    } else {
+      st->alpha = st->rho / pq;
+    }
+  }
+}
+
+void launch_fused_pq(dd_ctx* c, cudaStream_t s) {
+  const Geo& g = c->g;
+  const int ntiles = (g.nxi + kFusedCols - 1) / kFusedCols;
+  const int nb = ntiles < 152 * 6 ? ntiles : 152 * 6;
+  const size_t smem = sizeof(double) * ((size_t)(kFusedCols + 2) * g.Ypad + 2);
+  static bool attr = false;
+  if (!attr) {
+    DD_CUDA(cudaFuncSetAttribute(k_fused_pq, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr = true;
+  }
+  (k_fused_pq<<<nb, kThreads, smem, s>>>(g, c->tabS, c->z, c->pb[0], c->pb[1], c->q, c->st, c->red,
+                                         c->cnt + CNT_PQ), dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 
 // q = A_sigma p, pq = (p, q), alpha = rho / pq.
 template <int P>
-__global__ void __launch_bounds__(kThreads) k_matvec_pq(Geo g, const double* __restrict__ tab,
-                                                        const double* __restrict__ p, double* __restrict__ q,
-                                                        PcgState* st, double* partials, unsigned* counter) {
+__global__ void __launch_bounds__(kThreads) k_matvec_pq(Geo g, const double* __restrict__ tab, double* pb0,
+                                                        double* pb1, double* __restrict__ q, PcgState* st,
+                                                        double* partials, unsigned* counter) {
   if (st->done) return;
+  const double* __restrict__ p = p_cur(pb0, pb1, st->iter);
   const long long total = (long long)g.nxi * (P == 2 ? g.nxi : 1) * g.Ypad;
   double acc[1] = {0.0};
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
@@ -352,18 +440,23 @@ __global__ void __launch_bounds__(kThreads) k_matvec_pq(Geo g, const double* __r
 void launch_matvec_pq(dd_ctx* c, cudaStream_t s) {
   const Geo& g = c->g;
   const int nb = grid_blocks(interior_work(g), kThreads);
-  if (g.p == 1) (k_matvec_pq<1><<<nb, kThreads, 0, s>>>(g, c->tabS, c->p, c->q, c->st, c->red, c->cnt + CNT_PQ), dd::note_launch());
-  else (k_matvec_pq<2><<<nb, kThreads, 0, s>>>(g, c->tabS, c->p, c->q, c->st, c->red, c->cnt + CNT_PQ), dd::note_launch());
+  if (g.p == 1)
+    (k_matvec_pq<1><<<nb, kThreads, 0, s>>>(g, c->tabS, c->pb[0], c->pb[1], c->q, c->st, c->red, c->cnt + CNT_PQ),
+     dd::note_launch());
+  else
+    (k_matvec_pq<2><<<nb, kThreads, 0, s>>>(g, c->tabS, c->pb[0], c->pb[1], c->q, c->st, c->red, c->cnt + CNT_PQ),
+     dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 
 // x += alpha p, r -= alpha q, rr = (r, r); stop test ||r|| <= rtol ||r0|| (Sec. 4.1).
-__global__ void __launch_bounds__(kThreads) k_xr_update(long long n, const double* __restrict__ p,
+__global__ void __launch_bounds__(kThreads) k_xr_update(long long n, double* pb0, double* pb1,
                                                         const double* __restrict__ q, double* __restrict__ x,
                                                         double* __restrict__ r, PcgState* st,
                                                         double* partials, unsigned* counter) {
   if (st->done) return;
   const double alpha = st->alpha;
+  const double* __restrict__ p = p_cur(pb0, pb1, st->iter);
   const double2* p2 = reinterpret_cast<const double2*>(p);
   const double2* q2 = reinterpret_cast<const double2*>(q);
   double2* x2 = reinterpret_cast<double2*>(x);
@@ -400,29 +493,31 @@ __global__ void __launch_bounds__(kThreads) k_xr_update(long long n, const doubl
 
 void launch_xr_update(dd_ctx* c, cudaStream_t s) {
   const long long n = c->g.plen;
-  (k_xr_update<<<grid_blocks(n / 2, kThreads), kThreads, 0, s>>>(n, c->p, c->q, c->x, c->r, c->st, c->red,
-                                                                 c->cnt + CNT_RR), dd::note_launch());
+  (k_xr_update<<<grid_blocks(n / 2, kThreads), kThreads, 0, s>>>(n, c->pb[0], c->pb[1], c->q, c->x, c->r, c->st,
+                                                                 c->red, c->cnt + CNT_RR), dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 
 // ----------------------------------------------------------------------------------------
 // K5: prolong-sum of the preconditioner (Sec. 3.1):
 //   z = sum_i R_i^T y_i + sum_i (D_i R_i psi) u0_i
-// gathered per node from its (at most 2^p) owning subdomains, deterministic order;
-// fused with (r, z) and (q, z) and the beta update.
+// gathered per node from its (at most 2^p) owning subdomains in a fixed order, with the
+// owners read from per-column tables; fused with (r, z) (and (q, z) for the flexible
+// variant) and the beta update.  With rounded local inverses y is FP32 and the owners'
+// contributions are summed in FP32 before the FP64 coarse term is added.
 //   mode 0: preconditioner only (no scalars); 1: PCG start (rho = (r,z), beta = 0);
 //   2: PCG iteration (beta standard or flexible).
 // ----------------------------------------------------------------------------------------
 template <int P, typename TY>
-__global__ void __launch_bounds__(kThreads) k_prolong(Geo g, const Sub* __restrict__ subs,
-                                                      const int* __restrict__ slot_of,
-                                                      const TY* __restrict__ Y, int kpad,
+__global__ void __launch_bounds__(kThreads) k_prolong(Geo g, const int4* __restrict__ axown,
+                                                      const int4* __restrict__ subrow, const TY* __restrict__ Y,
                                                       const double* __restrict__ wT,
                                                       const double* __restrict__ u0, int coarse,
                                                       const double* __restrict__ r, const double* __restrict__ q,
                                                       double* __restrict__ z, int mode, PcgState* st,
                                                       double* partials, unsigned* counter) {
   if (mode != 0 && st->done) return;
+  const bool flex = (mode == 2) && st->flexible;
   const long long total = (long long)g.nxi * (P == 2 ? g.nxi : 1) * g.Ypad;
   double acc[2] = {0.0, 0.0};
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
@@ -430,23 +525,33 @@ __global__ void __launch_bounds__(kThreads) k_prolong(Geo g, const Sub* __restri
     Node nd = node_of<P>(g, t);
     double v = 0.0;
     if (nd.slot < g.nyi) {
-      int o1[2], l1[2], o2[2] = {0, 0}, l2[2] = {0, 0};
-      const int n1 = axis_owners(g, nd.a1, o1, l1);
-      int n2 = 1;
-      if (P == 2) n2 = axis_owners(g, nd.a2, o2, l2);
-      for (int i = 0; i < n1; ++i)
-        for (int k = 0; k < n2; ++k) {
-          const int s = (P == 1) ? o1[i] : o1[i] * g.L + o2[k];
-          const Sub sb = subs[s];
-          const int loc = ((P == 1) ? l1[i] : l1[i] * sb.w2 + l2[k]) * g.nyi + nd.slot;
-          v += (double)Y[(size_t)slot_of[s] * kpad + loc];
-          if (coarse) v = fma(wT[(size_t)sb.type * kpad + loc], u0[s], v);
+      const int4 A1 = __ldg(axown + nd.a1);
+      const int4 A2 = (P == 2) ? __ldg(axown + nd.a2) : make_int4(0, 0, -1, 0);
+      TY ys = (TY)0;
+      double cz = 0.0;
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int o1 = i ? A1.z : A1.x;
+        if (o1 < 0) continue;
+        const int l1 = i ? A1.w : A1.y;
+#pragma unroll
+        for (int k = 0; k < (P == 2 ? 2 : 1); ++k) {
+          const int o2 = k ? A2.z : A2.x;
+          if (o2 < 0) continue;
+          const int l2 = k ? A2.w : A2.y;
+          const int s = (P == 1) ? o1 : o1 * g.L + o2;
+          const int4 sr = __ldg(subrow + s);
+          const int loc = ((P == 1) ? l1 : l1 * sr.z + l2) * g.nyi + nd.slot;
+          ys += Y[(size_t)sr.x + loc];
+          if (coarse) cz = fma(__ldg(wT + (size_t)sr.y + loc), __ldg(u0 + s), cz);
         }
+      }
+      v = (double)ys + cz;
     }
     z[nd.idx] = v;
     if (mode != 0) {
       acc[0] = fma(r[nd.idx], v, acc[0]);
-      acc[1] = fma(q[nd.idx], v, acc[1]);
+      if (flex) acc[1] = fma(q[nd.idx], v, acc[1]);
     }
   }
   if (mode == 0) return;
@@ -475,9 +580,10 @@ void launch_prolong(dd_ctx* c, int mode, cudaStream_t s) {
   const int nb = grid_blocks(interior_work(g), kThreads);
   const int coarse = c->grid.coarse;
   const bool f32 = (c->grid.precision != DD_PREC_FP64);
-#define DD_PROLONG(PP, TY, YP)                                                                          \
-  (k_prolong<PP, TY><<<nb, kThreads, 0, s>>>(g, c->subs, c->slot_of_sub, YP, c->kpad, c->wT, c->u0,      \
-                                            coarse, c->r, c->q, c->z, mode, c->st, c->red, c->cnt + CNT_RZ), dd::note_launch())
+#define DD_PROLONG(PP, TY, YP)                                                                             \
+  (k_prolong<PP, TY><<<nb, kThreads, 0, s>>>(g, c->axown, c->subrow, YP, c->wT, c->u0, coarse, c->r, c->q, \
+                                             c->z, mode, c->st, c->red, c->cnt + CNT_RZ),                  \
+   dd::note_launch())
   if (g.p == 1) {
     if (f32) DD_PROLONG(1, float, c->Y32); else DD_PROLONG(1, double, c->Y64);
   } else {
