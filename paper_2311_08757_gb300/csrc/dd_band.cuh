@@ -1,11 +1,13 @@
 // Banded Cholesky solves, one warp per right-hand side, vector held in shared memory.
 //
-// Band storage of the lower factor L (half bandwidth b):
-//   CB[i*(b+1) + d] = L(i+d, i)   (column band, used by the forward solve L y = r)
-//   RB[i*(b+1) + d] = L(i, i-d)   (row band,    used by the backward solve L^T x = y)
-//   inv[i]          = 1 / L(i, i)
-// Both sweeps are written in "axpy" form: once x_i is known the lanes update the b
-// entries it couples to, so each step costs one broadcast and b/32 FMAs per lane.
+// Storage of the factor A = L L^T (half bandwidth b), pre-scaled by the pivots:
+//   CB[i*(b+1) + d] = L(i+d, i) / L(i, i)       (column band; d = 0 unused)
+//   RB[i*(b+1) + d] = L(i, i-d) / L(i-d, i-d)   (row band; RB[i][d] = CB[i-d][d])
+//   inv[i]          = 1 / L(i, i)^2
+// Forward sweep on w = L diag(L)^{-1}-scaled unknowns: w_{i+d} -= CB[i][d] w_i, then
+// x_i = w_i inv_i, then the backward sweep x_{i-d} -= RB[i][d] x_i.  Every step is one
+// broadcast of the pivot unknown and b/32 FMAs per lane, with no division or multiply on
+// the sequential path.
 #pragma once
 
 #include "dd_common.cuh"
@@ -13,7 +15,7 @@
 namespace dd {
 
 // Solves (L L^T) x = r in place in xs[0..n).  Caller: all 32 lanes of a warp, xs visible to
-// the warp (shared memory), followed by __syncwarp() before xs is read elsewhere.
+// the warp (shared memory).
 __device__ __forceinline__ void warp_band_solve(double* xs, int n, int b, const double* __restrict__ CB,
                                                 const double* __restrict__ RB,
                                                 const double* __restrict__ inv) {
@@ -21,23 +23,21 @@ __device__ __forceinline__ void warp_band_solve(double* xs, int n, int b, const 
   const int bs = b + 1;
   __syncwarp();
   for (int i = 0; i < n; ++i) {
-    const double yi = xs[i] * __ldg(inv + i);
+    const double wi = xs[i];
     const double* col = CB + (size_t)i * bs;
     const int dmax = min(b, n - 1 - i);
-    for (int d = 1 + lane; d <= dmax; d += 32) xs[i + d] = fma(-__ldg(col + d), yi, xs[i + d]);
+    for (int d = 1 + lane; d <= dmax; d += 32) xs[i + d] = fma(-__ldg(col + d), wi, xs[i + d]);
     __syncwarp();
-    if (lane == 0) xs[i] = yi;
   }
+  for (int i = lane; i < n; i += 32) xs[i] *= __ldg(inv + i);
   __syncwarp();
   for (int i = n - 1; i >= 0; --i) {
-    const double xi = xs[i] * __ldg(inv + i);
+    const double xi = xs[i];
     const double* row = RB + (size_t)i * bs;
     const int dmax = min(b, i);
     for (int d = 1 + lane; d <= dmax; d += 32) xs[i - d] = fma(-__ldg(row + d), xi, xs[i - d]);
     __syncwarp();
-    if (lane == 0) xs[i] = xi;
   }
-  __syncwarp();
 }
 
 }  // namespace dd
@@ -55,8 +55,7 @@ __device__ __forceinline__ void warp_band_solve_pf(double* xs, int n, int b, con
   const int lane = threadIdx.x & 31;
   const int bs = b + 1;
   double rb[PF][NV];
-  double iv[PF];
-  // ---- forward: L y = r, rows 0, 1, ...
+  // ---- forward sweep, rows 0, 1, ...
 #pragma unroll
   for (int u = 0; u < PF; ++u) {
 #pragma unroll
@@ -64,7 +63,6 @@ __device__ __forceinline__ void warp_band_solve_pf(double* xs, int n, int b, con
       const int d = 1 + lane + 32 * v;
       rb[u][v] = (u < n && d <= b) ? __ldg(CB + (size_t)u * bs + d) : 0.0;
     }
-    iv[u] = (u < n) ? __ldg(inv + u) : 0.0;
   }
   __syncwarp();
   for (int i0 = 0; i0 < n; i0 += PF) {
@@ -72,12 +70,12 @@ __device__ __forceinline__ void warp_band_solve_pf(double* xs, int n, int b, con
     for (int u = 0; u < PF; ++u) {
       const int i = i0 + u;
       if (i < n) {
-        const double yi = xs[i] * iv[u];
+        const double wi = xs[i];
         const int dmax = min(b, n - 1 - i);
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           const int d = 1 + lane + 32 * v;
-          if (d <= dmax) xs[i + d] = fma(-rb[u][v], yi, xs[i + d]);
+          if (d <= dmax) xs[i + d] = fma(-rb[u][v], wi, xs[i + d]);
         }
         const int nx = i + PF;
 #pragma unroll
@@ -85,14 +83,12 @@ __device__ __forceinline__ void warp_band_solve_pf(double* xs, int n, int b, con
           const int d = 1 + lane + 32 * v;
           rb[u][v] = (nx < n && d <= b) ? __ldg(CB + (size_t)nx * bs + d) : 0.0;
         }
-        iv[u] = (nx < n) ? __ldg(inv + nx) : 0.0;
         __syncwarp();
-        if (lane == 0) xs[i] = yi;
       }
     }
   }
-  __syncwarp();
-  // ---- backward: L^T x = y, rows n-1, n-2, ...
+  for (int i = lane; i < n; i += 32) xs[i] *= __ldg(inv + i);
+  // ---- backward sweep, rows n-1, n-2, ...
 #pragma unroll
   for (int u = 0; u < PF; ++u) {
     const int i = n - 1 - u;
@@ -101,7 +97,6 @@ __device__ __forceinline__ void warp_band_solve_pf(double* xs, int n, int b, con
       const int d = 1 + lane + 32 * v;
       rb[u][v] = (i >= 0 && d <= b) ? __ldg(RB + (size_t)i * bs + d) : 0.0;
     }
-    iv[u] = (i >= 0) ? __ldg(inv + i) : 0.0;
   }
   __syncwarp();
   for (int i0 = 0; i0 < n; i0 += PF) {
@@ -109,7 +104,7 @@ __device__ __forceinline__ void warp_band_solve_pf(double* xs, int n, int b, con
     for (int u = 0; u < PF; ++u) {
       const int i = n - 1 - (i0 + u);
       if (i >= 0) {
-        const double xi = xs[i] * iv[u];
+        const double xi = xs[i];
         const int dmax = min(b, i);
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
@@ -122,13 +117,10 @@ __device__ __forceinline__ void warp_band_solve_pf(double* xs, int n, int b, con
           const int d = 1 + lane + 32 * v;
           rb[u][v] = (nx >= 0 && d <= b) ? __ldg(RB + (size_t)nx * bs + d) : 0.0;
         }
-        iv[u] = (nx >= 0) ? __ldg(inv + nx) : 0.0;
         __syncwarp();
-        if (lane == 0) xs[i] = xi;
       }
     }
   }
-  __syncwarp();
 }
 
 // Host-side dispatch on the half bandwidth: BODY is compiled once per (NV, PF) pair.

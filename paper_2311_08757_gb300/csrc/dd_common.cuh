@@ -1,6 +1,8 @@
 // Device helpers shared by the kernels: reductions, index maps, stencil evaluation.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "dd_internal.h"
 
 namespace dd {
@@ -74,6 +76,63 @@ __device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* partials,
     *counter = 0u;
   }
   return true;
+}
+
+// ---- precision conversions on the integer pipe ------------------------------------------
+// GB300 retires FP64 instructions (conversions included) at 2 per clock per SM; these
+// conversions do the same rounding with integer operations for normal-range values.
+
+// IEEE round-to-nearest-even of a double to bfloat16 (bits); non-normal results fall back to
+// the hardware conversion.
+__device__ __forceinline__ unsigned short f64_to_bf16_bits(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(u >> 63);
+  const int e = (int)((u >> 52) & 0x7FF);
+  const int eb = e - 1023 + 127;
+  if (e == 0 && (u << 1) == 0) return (unsigned short)(sign << 15);   // +-0
+  if (eb < 1 || eb > 254) {
+    const __nv_bfloat16 h = __double2bfloat16(x);
+    return *reinterpret_cast<const unsigned short*>(&h);
+  }
+  const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
+  const unsigned long long keep = m >> 45, rem = m & ((1ull << 45) - 1), half = 1ull << 44;
+  unsigned r = ((unsigned)eb << 7) | (unsigned)keep;
+  if (rem > half || (rem == half && (keep & 1))) r += 1;   // a carry rounds into the exponent
+  return (unsigned short)((sign << 15) | r);
+}
+
+// Round-to-nearest, ties away from zero, of a double to TF32 (an FP32 bit pattern whose low
+// 13 mantissa bits are zero), as cvt.rna.tf32.f32 would round the exact value.
+__device__ __forceinline__ float f64_to_tf32(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(u >> 63);
+  const int e = (int)((u >> 52) & 0x7FF);
+  const int ef = e - 1023 + 127;
+  if (e == 0 && (u << 1) == 0) return __uint_as_float(sign << 31);
+  if (ef < 1 || ef > 254) {
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"((float)x));
+    return __uint_as_float(r);
+  }
+  const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
+  const unsigned long long keep = m >> 42, rem = m & ((1ull << 42) - 1), half = 1ull << 41;
+  unsigned r = ((unsigned)ef << 10) | (unsigned)keep;
+  if (rem >= half) r += 1;
+  return __uint_as_float((sign << 31) | (r << 13));
+}
+
+// Exact float -> double for normal floats and zeros.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFF;
+  if (e == 0 || e == 255) {
+    if ((u << 1) == 0) return __longlong_as_double((long long)((unsigned long long)(u >> 31) << 63));
+    return (double)f;
+  }
+  const unsigned long long bits = ((unsigned long long)(u >> 31) << 63) |
+                                  ((unsigned long long)(e + 896) << 52) |
+                                  ((unsigned long long)(u & 0x7FFFFF) << 29);
+  return __longlong_as_double((long long)bits);
 }
 
 // Interior-element enumeration of a padded vector: t in [0, nxi^p * Ypad).

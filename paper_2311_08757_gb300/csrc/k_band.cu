@@ -12,11 +12,70 @@
 namespace dd {
 
 // ----------------------------------------------------------------------------------------
-// Banded Cholesky A = L L^T, one CTA per matrix, right-looking, in place in CB.
+// Banded Cholesky A = L L^T, one CTA per matrix, right-looking.  Input: the lower band of A
+// in CB (CB[i][d] = A(i+d, i)).  Output in place: CB[i][d] = L(i+d, i)/L(i, i) (d >= 1),
+// CB[i][0] = L(i, i), inv[i] = 1/L(i, i)^2 (the storage the band solves expect).
 // A zero or negative pivot sets *flag (DD_ENOTSPD) and continues with pivot 1.
+//
+// k_band_factor_win keeps the active (b+1) x (b+1) window in shared memory as a ring of
+// columns: every column is read from global memory once and written back once when it is
+// final, so each step waits on shared memory only.  k_band_factor (global window) serves
+// bandwidths whose window does not fit.
 // ----------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_band_factor(double* CB, double* inv, const int* __restrict__ nvec, int nmax, int b,
-                              int* flag) {
+constexpr int kBandWinMax = 160;
+
+__global__ void __launch_bounds__(1024) k_band_factor_win(double* CB, double* inv, const int* __restrict__ nvec,
+                                                          int nmax, int b, int* flag) {
+  extern __shared__ double fsm[];
+  const int m = blockIdx.x;
+  const int n = nvec[m];
+  const int bs = b + 1, W = b + 1;
+  double* win = fsm;               // W columns x bs entries
+  double* colk = fsm + W * bs;     // L(k+d, k), d = 0..b
+  double* A = CB + (size_t)m * nmax * bs;
+  double* iv = inv + (size_t)m * nmax;
+  const int first = min(W, n);
+  for (int t = threadIdx.x; t < first * bs; t += blockDim.x) win[t] = A[t];
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    const int sk = k % W;
+    if (threadIdx.x == 0) {
+      double piv = win[sk * bs];
+      if (!(piv > 0.0)) {
+        atomicOr(flag, 1);
+        piv = 1.0;
+      }
+      const double l = sqrt(piv);
+      A[(size_t)k * bs] = l;
+      iv[k] = 1.0 / piv;
+      colk[0] = 1.0 / l;
+    }
+    __syncthreads();
+    const double il = colk[0];
+    const int dmax = min(b, n - 1 - k);
+    for (int d = 1 + threadIdx.x; d <= b; d += blockDim.x) {
+      double v = 0.0;
+      if (d <= dmax) {
+        v = win[sk * bs + d] * il;             // L(k+d, k)
+        A[(size_t)k * bs + d] = v * il;        // pre-scaled by 1/L(k,k)
+      }
+      colk[d] = v;
+    }
+    __syncthreads();
+    const int tot = dmax * dmax;
+    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+      const int d1 = t / dmax + 1, d2 = t % dmax + 1;
+      if (d2 <= d1) win[((k + d2) % W) * bs + (d1 - d2)] -= colk[d1] * colk[d2];
+    }
+    __syncthreads();
+    // the slot of column k is free: bring in column k + W (untouched so far)
+    if (k + W < n)
+      for (int d = threadIdx.x; d < bs; d += blockDim.x) win[sk * bs + d] = A[(size_t)(k + W) * bs + d];
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_band_factor(double* CB, double* inv, const int* __restrict__ nvec,
+                                                      int nmax, int b, int* flag) {
   extern __shared__ double colk[];
   const int m = blockIdx.x;
   const int n = nvec[m];
@@ -32,7 +91,7 @@ __global__ void __launch_bounds__(1024) k_band_factor(double* CB, double* inv, c
       }
       const double l = sqrt(piv);
       A[(size_t)k * bs] = l;
-      iv[k] = 1.0 / l;
+      iv[k] = 1.0 / piv;
       colk[0] = 1.0 / l;
     }
     __syncthreads();
@@ -40,10 +99,7 @@ __global__ void __launch_bounds__(1024) k_band_factor(double* CB, double* inv, c
     const int dmax = min(b, n - 1 - k);
     for (int d = 1 + threadIdx.x; d <= b; d += blockDim.x) {
       double v = 0.0;
-      if (d <= dmax) {
-        v = A[(size_t)k * bs + d] * il;
-        A[(size_t)k * bs + d] = v;
-      }
+      if (d <= dmax) v = A[(size_t)k * bs + d] * il;
       colk[d] = v;
     }
     __syncthreads();
@@ -53,9 +109,14 @@ __global__ void __launch_bounds__(1024) k_band_factor(double* CB, double* inv, c
       const int d1 = t / dmax + 1, d2 = t % dmax + 1;
       if (d2 <= d1) A[(size_t)(k + d2) * bs + (d1 - d2)] -= colk[d1] * colk[d2];
     }
+    for (int d = 1 + threadIdx.x; d <= dmax; d += blockDim.x) A[(size_t)k * bs + d] = colk[d] * il;
     __syncthreads();
   }
 }
+
+// launch the factorisation of nmat band matrices (sizes in nvec) and build the row band
+static void factor_launch(const Geo&, double* CB, double* RB, double* inv, const int* nvec, int nmat, int nmax, int b,
+                          int* flag, cudaStream_t s);
 
 // RB[i][d] = L(i, i-d) = CB[i-d][d]
 __global__ void k_band_rows(const double* __restrict__ CB, double* RB, const int* __restrict__ nvec,
@@ -85,16 +146,29 @@ int launch_band_factor(dd_ctx* c, double* CB, double* RB, double* inv, int nmat,
     for (int t = 0; t < nmat; ++t) nh[t] = nmax;
   }
   DD_CUDA(cudaMemcpyAsync(nvec, nh.data(), sizeof(int) * nmat, cudaMemcpyHostToDevice, c->stream));
-  const size_t smem = sizeof(double) * (b + 1);
-  int threads = 256;
-  if ((long long)b * b > 4096) threads = 1024;
-  (k_band_factor<<<nmat, threads, smem, c->stream>>>(CB, inv, nvec, nmax, b, flag), dd::note_launch());
-  DD_CUDA(cudaGetLastError());
-  const long long total = (long long)nmat * nmax * (b + 1);
-  (k_band_rows<<<grid_blocks(total, kThreads), kThreads, 0, c->stream>>>(CB, RB, nvec, nmat, nmax, b), dd::note_launch());
-  DD_CUDA(cudaGetLastError());
+  factor_launch(c->g, CB, RB, inv, nvec, nmat, nmax, b, flag, c->stream);
   DD_CUDA(cudaFreeAsync(nvec, c->stream));
   return DD_OK;
+}
+
+static void factor_launch(const Geo&, double* CB, double* RB, double* inv, const int* nvec, int nmat, int nmax, int b,
+                          int* flag, cudaStream_t s) {
+  if (b <= kBandWinMax) {
+    const size_t smem = sizeof(double) * ((size_t)(b + 1) * (b + 1) + (b + 1));
+    const int threads = (b * b > 2048) ? 512 : 256;
+    static bool attr = false;
+    if (!attr) {
+      DD_CUDA(cudaFuncSetAttribute(k_band_factor_win, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+      attr = true;
+    }
+    (k_band_factor_win<<<nmat, threads, smem, s>>>(CB, inv, nvec, nmax, b, flag), dd::note_launch());
+  } else {
+    (k_band_factor<<<nmat, 1024, sizeof(double) * (b + 1), s>>>(CB, inv, nvec, nmax, b, flag), dd::note_launch());
+  }
+  DD_CUDA(cudaGetLastError());
+  const long long total = (long long)nmat * nmax * (b + 1);
+  (k_band_rows<<<grid_blocks(total, kThreads), kThreads, 0, s>>>(CB, RB, nvec, nmat, nmax, b), dd::note_launch());
+  DD_CUDA(cudaGetLastError());
 }
 
 // ----------------------------------------------------------------------------------------
@@ -446,11 +520,7 @@ static bool cell_phase(dd_ctx* c, double* shift, bool from_minV, double margin_f
     DD_CUDA(cudaMemcpyAsync(shift, &s_new, sizeof(double), cudaMemcpyHostToDevice, c->stream));
   }
   (k_cell_assemble<<<grid_blocks(ncell, 128), 128, 0, c->stream>>>(g, c->tabA, c->tabM, shift, b, CB), dd::note_launch());
-  const int threads = ((long long)b * b > 4096) ? 1024 : 256;
-  (k_band_factor<<<1, threads, sizeof(double) * (b + 1), c->stream>>>(CB, inv, nvec, ncell, b, flag), dd::note_launch());
-  (k_band_rows<<<grid_blocks((long long)ncell * (b + 1), kThreads), kThreads, 0, c->stream>>>(CB, RB, nvec, 1, ncell,
-                                                                                            b), dd::note_launch());
-  DD_CUDA(cudaGetLastError());
+  factor_launch(g, CB, RB, inv, nvec, 1, ncell, b, flag, c->stream);
   int fl = 0;
   DD_CUDA(cudaMemcpyAsync(&fl, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   DD_CUDA(cudaStreamSynchronize(c->stream));

@@ -279,17 +279,17 @@ static void launch_tc(const CUtensorMap* tA, const CUtensorMap* tB, const Tile* 
 // Rounded local inverses from the banded factors: column col of A_T^{-1} (identity
 // right-hand side) = row col (symmetric), rounded to BF16 or TF32.
 // ----------------------------------------------------------------------------------------
+// rounding of FP64 values to the operand type, on the integer pipe (see dd_common.cuh)
 template <typename T>
-__device__ __forceinline__ T round_to(double v);
+__device__ __forceinline__ T round_fast(double v);
 template <>
-__device__ __forceinline__ __nv_bfloat16 round_to<__nv_bfloat16>(double v) {
-  return __double2bfloat16(v);
+__device__ __forceinline__ __nv_bfloat16 round_fast<__nv_bfloat16>(double v) {
+  const unsigned short b = f64_to_bf16_bits(v);
+  return *reinterpret_cast<const __nv_bfloat16*>(&b);
 }
 template <>
-__device__ __forceinline__ float round_to<float>(double v) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"((float)v));
-  return __uint_as_float(r);
+__device__ __forceinline__ float round_fast<float>(double v) {
+  return f64_to_tf32(v);
 }
 
 template <typename T, int NV, int PF>
@@ -308,7 +308,7 @@ __global__ void k_local_inverse(const int* __restrict__ nloc, int nmax, int b, c
   const size_t off = (size_t)ty * nmax;
   band_solve<NV, PF>(xs, n, b, CB + off * (b + 1), RB + off * (b + 1), inv + off);
   T* row = out + ((size_t)ty * kpad + col) * kpad;
-  for (int k = lane; k < n; k += 32) row[k] = round_to<T>(xs[k]);
+  for (int k = lane; k < n; k += 32) row[k] = round_fast<T>(xs[k]);
 }
 
 // R_i r rounded, subdomain rows in type-sorted order, zero tail up to kpad; the coarse
@@ -334,10 +334,10 @@ __global__ void k_pack(Geo g, const Sub* __restrict__ subs, const int* __restric
       const int k = cc * g.nyi + sj;
       const double v = r[base + sj];
       acc[0] = fma(wt[k], v, acc[0]);
-      row[k] = round_to<T>(v);
+      row[k] = round_fast<T>(v);
     }
   }
-  for (int k = sb.nloc + threadIdx.x; k < kpad; k += blockDim.x) row[k] = round_to<T>(0.0);
+  for (int k = sb.nloc + threadIdx.x; k < kpad; k += blockDim.x) row[k] = round_fast<T>(0.0);
   if (c0 != nullptr) {
     block_sum<1>(acc);
     if (threadIdx.x == 0) c0[s] = acc[0];

@@ -508,6 +508,9 @@ void launch_xr_update(dd_ctx* c, cudaStream_t s) {
 //   mode 0: preconditioner only (no scalars); 1: PCG start (rho = (r,z), beta = 0);
 //   2: PCG iteration (beta standard or flexible).
 // ----------------------------------------------------------------------------------------
+__device__ __forceinline__ double to_f64(float f) { return f32_to_f64(f); }
+__device__ __forceinline__ double to_f64(double d) { return d; }
+
 template <int P, typename TY>
 __global__ void __launch_bounds__(kThreads) k_prolong(Geo g, const int4* __restrict__ axown,
                                                       const int4* __restrict__ subrow, const TY* __restrict__ Y,
@@ -546,7 +549,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong(Geo g, const int4* __restr
           if (coarse) cz = fma(__ldg(wT + (size_t)sr.y + loc), __ldg(u0 + s), cz);
         }
       }
-      v = (double)ys + cz;
+      v = to_f64(ys) + cz;
     }
     z[nd.idx] = v;
     if (mode != 0) {
