@@ -230,6 +230,25 @@ long long dd_kernel_launch_count(void);
  * frees its own device buffers.  DD_ETIMEOUT if a bounded device wait expired. */
 int dd_tc_gemm_test(int precision, int M, int N, int K, const float* A_host, const float* B_host, float* D_host);
 
+/* Allocation-free form of the same tensor-core contraction (the paper has no counterpart: it
+ * exists for callers that cannot allocate device memory where they need the product, such as
+ * a server whose device memory is reserved up front by its own arena, or a latency-critical
+ * path where cudaMalloc/cudaFree would synchronise the device).
+ *   D[n][m] = sum_k A[m][k] B[n][k], FP32 accumulation.
+ *   A_dev  device, M x K row-major: BF16 (precision = DD_PREC_BF16) or FP32 read as TF32
+ *   B_dev  device, N x K row-major, same type;  D_dev device, N x M row-major FP32
+ *   K must be a multiple of 64; ceil(M/128) * ceil(N/256) <= 4096, otherwise DD_EINVAL.
+ *   stream cudaStream_t (NULL = legacy default); the call returns after the product is done.
+ * Allocates nothing: the kernel's scratch (tile list, error word of its bounded waits) is a
+ * fixed 64 KB array in the library's static device memory, present on every GPU that loads
+ * the library until the process exits.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  All calls share the array and it keeps the last call's contents, so
+ * calls that overlap on the GPU (concurrent streams, threads or graphs) race and must be
+ * serialised by the caller.  DD_ETIMEOUT if a bounded device wait expired. */
+int dd_tc_gemm_noalloc(int precision, int M, int N, int K, const void* A_dev, const void* B_dev, float* D_dev,
+                       void* stream);
+
 #ifdef __cplusplus
 }
 #endif

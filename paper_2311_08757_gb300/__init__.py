@@ -70,6 +70,7 @@ _SIGS = {
     "dd_tc_gemm_test": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     "dd_set_potential": (c_int, [c_void_p, c_void_p, c_size_t]),
     "dd_kernel_launch_count": (c_longlong, []),
+    "dd_tc_gemm_noalloc": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
 }
 
 
@@ -243,6 +244,17 @@ def dd_tc_gemm_test(precision: int, A, B, D) -> int:
     M, K = A.shape
     N = B.shape[0]
     return _check(lib().dd_tc_gemm_test(precision, M, N, K, _ptr(A), _ptr(B), _ptr(D)))
+
+
+def dd_tc_gemm_noalloc(precision: int, A_dev, B_dev, D_dev, stream=None) -> int:
+    """Allocation-free tensor-core product D[n][m] = sum_k A[m][k] B[n][k] on device tensors
+    (A: M x K, B: N x K, BF16 or FP32/TF32, K a multiple of 64; D: N x M float32).  For callers
+    that must not allocate device memory; its scratch is fixed static device memory shared by
+    all calls, so overlapping calls race."""
+    M, K = A_dev.shape
+    N = B_dev.shape[0]
+    return _check(lib().dd_tc_gemm_noalloc(precision, M, N, K, _ptr(A_dev), _ptr(B_dev), _ptr(D_dev),
+                                           _stream_ptr(stream)))
 
 
 class Eigensolver:

@@ -457,7 +457,7 @@ extern "C" int dd_tc_gemm_test(int precision, int M, int N, int K, const float* 
   const int kpad = (K + 63) / 64 * 64;
   const int mpad = (M + 127) / 128 * 128;
   void *dA = nullptr, *dB = nullptr;
-  float *dD = nullptr, *hA = nullptr;
+  float* dD = nullptr;
   int* derr = nullptr;
   Tile* dt = nullptr;
   cudaStream_t s = nullptr;
@@ -522,7 +522,6 @@ extern "C" int dd_tc_gemm_test(int precision, int M, int N, int K, const float* 
   } catch (const Error& e) {
     rc = e.code;
   }
-  (void)hA;
   if (dA) cudaFree(dA);
   if (dB) cudaFree(dB);
   if (dD) cudaFree(dD);
@@ -530,4 +529,90 @@ extern "C" int dd_tc_gemm_test(int precision, int M, int N, int K, const float* 
   if (dt) cudaFree(dt);
   if (s) cudaStreamDestroy(s);
   return rc;
+}
+
+// ------------------------------------------------------------------------------------------
+// Allocation-free variant of the tensor-core contraction.
+//
+// Some callers cannot allocate device memory at the point where they need this product:
+// a serving process that reserves all device memory in its own arena at start-up (a
+// cudaMalloc from inside the request path would fail or fragment that arena), code on a
+// latency-critical path where cudaMalloc/cudaFree would synchronise the device, or code
+// running under another framework's memory manager that forbids raw allocations.  For
+// them this entry point takes device operands and a device output and keeps the kernel's
+// scratch (the tile list and the error word of its bounded waits) in a fixed array that
+// lives in this library's static device memory: kNoAllocBytes bytes on every GPU that
+// loads the library, held until the process exits.
+// ------------------------------------------------------------------------------------------
+#include <mutex>
+
+namespace dd {
+
+constexpr int kNoAllocMaxTiles = 4096;                          // 128 x 256 output tiles
+constexpr size_t kNoAllocBytes = 256 + sizeof(Tile) * kNoAllocMaxTiles;   // 64 KB + error word
+
+// [0, 256): error word (int); [256, ...): tile list
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[256];   // device address of g_noalloc_scratch, per device ordinal
+
+// Resolves the device address of the scratch array for the current device (once per device).
+static int noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return DD_ECUDA;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+      cudaGetLastError();
+      return DD_ECUDA;
+    }
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return DD_OK;
+}
+
+}  // namespace dd
+
+extern "C" int dd_tc_gemm_noalloc(int precision, int M, int N, int K, const void* A_dev, const void* B_dev,
+                                  float* D_dev, void* stream) {
+  using namespace dd;
+  if (precision != DD_PREC_BF16 && precision != DD_PREC_TF32) return DD_EINVAL;
+  if (M < 1 || N < 1 || K < 64 || (K % 64) != 0 || !A_dev || !B_dev || !D_dev) return DD_EINVAL;
+  const long long ntiles = (long long)((M + 127) / 128) * ((N + 255) / 256);
+  if (ntiles > kNoAllocMaxTiles) return DD_EINVAL;   // output larger than the fixed scratch allows
+  void* scratch = nullptr;
+  int rc = noalloc_scratch(&scratch);
+  if (rc != DD_OK) return rc;
+  int* derr = reinterpret_cast<int*>(scratch);
+  Tile* dtiles = reinterpret_cast<Tile*>(reinterpret_cast<unsigned char*>(scratch) + 256);
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    const bool bf16 = precision == DD_PREC_BF16;
+    Tile tl[kNoAllocMaxTiles];
+    int nt = 0;
+    for (int n0 = 0; n0 < N; n0 += 256)
+      for (int m0 = 0; m0 < M; m0 += 128) tl[nt++] = Tile{0, m0, n0, N};
+    CUtensorMap tA, tB;
+    const int BK = bf16 ? TcCfg<__nv_bfloat16>::BK : TcCfg<float>::BK;
+    make_tmap(&tA, const_cast<void*>(A_dev), bf16, K, M, BK, 128);
+    make_tmap(&tB, const_cast<void*>(B_dev), bf16, K, N, BK, 256);
+    // the error word must start at zero; the tile list is rewritten whole on every call
+    DD_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), s));
+    DD_CUDA(cudaMemcpyAsync(dtiles, tl, sizeof(Tile) * nt, cudaMemcpyHostToDevice, s));
+    if (bf16)
+      launch_tc<__nv_bfloat16>(&tA, &tB, dtiles, nt, K, M, 0, D_dev, M, derr, nullptr, s);
+    else
+      launch_tc<float>(&tA, &tB, dtiles, nt, K, M, 0, D_dev, M, derr, nullptr, s);
+    int herr = 0;
+    DD_CUDA(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DD_CUDA(cudaStreamSynchronize(s));
+    if (herr) return DD_ETIMEOUT;
+  } catch (const Error& e) {
+    return e.code;
+  }
+  return DD_OK;
 }
