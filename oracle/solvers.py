@@ -9,6 +9,11 @@
   r = A x - R(x) B x (Sec. 2).  Stop when
   eta = ||A x - rho B x||_2 / (|rho| ||B x||_2) <= tol_res and
   |rho_k - rho_{k-1}| <= tol_lam |rho_k|.
+* ``si_lopcg``: the inexact shift-and-invert preconditioned LOPCG of Algorithm 1:
+  outer residual r_o = A x_k - R(x_k) B x_k, inner solve A_sigma w_k = r_o by PCG
+  (relative tolerance fixed, or min{0.1, ||r_o||_2} as in Sec. 4.3), or w_k = M^{-1} r_o
+  with the Schwarz preconditioner alone (the fused variant of Sec. 4.3); orthogonalised
+  Rayleigh-Ritz on span{w_k, x_k, x_{k-1}}; start x_0 = e_1, x_1 = 1/||1||_B (Sec. 4.2).
 * ``cell_eigenpair``: lowest eigenpair of the x-periodic cell GEVP (weak cell
   problem, Sec. 2), by a dense generalised symmetric eigensolver; psi > 0,
   psi^T M_# psi = 1.
@@ -90,6 +95,96 @@ def inverse_iteration(Asig, M, sigma, prec=None, x0=None, tol_res=1e-8, tol_lam=
     return rho, x, maxit_outer, inner, info
 
 
+def rayleigh_ritz3(GA, GB, sums, drop=1e-10):
+    """Orthogonalised Rayleigh-Ritz (Algorithm 1) on span{s_0, s_1, s_2} from the Gram
+    matrices GA = S^T A_sigma S and GB = S^T B S, S = [x_k, w_k, x_{k-1}].
+
+    The basis is B-orthonormalised by Gram-Schmidt (two passes) in the order x_k, w_k,
+    x_{k-1}, on coefficient vectors; a direction whose B-norm after orthogonalisation is
+    at most ``drop`` times its norm before is dropped.  Returns (theta, c): the lowest
+    eigenvalue of the projected pencil (shifted: theta = R(y) - sigma) and the
+    coefficients c of its B-normalised Ritz vector y = S c, signed so that sum(y) > 0
+    (``sums`` = [sum s_0, sum s_1, sum s_2]).
+    """
+    GA = np.asarray(GA, dtype=float)
+    GB = np.asarray(GB, dtype=float)
+    cols = []
+    for i in range(3):
+        v = np.zeros(3)
+        v[i] = 1.0
+        n0 = GB[i, i]
+        for _ in range(2):
+            for t in cols:
+                v = v - (t @ GB @ v) * t
+        nrm2 = v @ GB @ v
+        if n0 > 0.0 and nrm2 > (drop * drop) * n0:
+            cols.append(v / np.sqrt(nrm2))
+    T = np.column_stack(cols)
+    H = T.T @ GA @ T
+    H = 0.5 * (H + H.T)
+    w, V = np.linalg.eigh(H)
+    c = T @ V[:, 0]
+    if np.dot(np.asarray(sums, dtype=float), c) < 0.0:
+        c = -c
+    return float(w[0]), c
+
+
+def si_lopcg(A, M, sigma, prec=None, x0=None, x1=None, tol_res=1e-8, tol_lam=1e-10,
+             maxit_outer=1000, inner="fixed", rtol_inner=1e-8, maxit_inner=10000):
+    """Inexact SI-preconditioned LOPCG (Algorithm 1).
+
+    inner = "fixed": PCG on A_sigma w = r_o to relative residual rtol_inner;
+    "adaptive": to min{0.1, ||r_o||_2} (Sec. 4.3); "fused": w = M^{-1} r_o, one
+    application of the Schwarz preconditioner and no inner Krylov loop (Sec. 4.3).
+    Stops like ``inverse_iteration``: eta <= tol_res and |rho_k - rho_{k-1}| <= tol_lam |rho_k|.
+    Returns (rho, x, outer steps, inner iterations per step, info).
+    """
+    n = A.shape[0]
+    Asig = (A - sigma * M).tocsr()
+    if x0 is None:
+        x0 = np.zeros(n)
+        x0[0] = 1.0
+    xp = x0 / np.sqrt(dot(x0, M @ x0))
+    x = np.ones(n) if x1 is None else x1.astype(float).copy()
+    x /= np.sqrt(dot(x, M @ x))
+    Ax, Mx = Asig @ x, M @ x
+    lam = dot(x, Ax)                         # rho - sigma, x^T B x = 1
+    rho_prev = np.inf
+    inner_its = []
+    info = {}
+    for k in range(0, maxit_outer + 1):
+        rho = sigma + lam
+        ro = Ax - lam * Mx                   # = A x - rho B x
+        nro = np.sqrt(dot(ro, ro))
+        eta = nro / (abs(rho) * np.sqrt(dot(Mx, Mx)))
+        info = dict(eta=eta, drho=abs(rho - rho_prev))
+        if eta <= tol_res and abs(rho - rho_prev) <= tol_lam * abs(rho):
+            return rho, x, k, inner_its, info
+        if k == maxit_outer:
+            break
+        if inner == "fused":
+            w, it = prec(ro), 1
+        else:
+            rt = rtol_inner if inner == "fixed" else min(0.1, nro)
+            w, it, _ = pcg(Asig, ro, None, prec, rt, maxit_inner)
+        inner_its.append(it)
+        S = [x, w, xp]
+        AS = [Ax, Asig @ w, Asig @ xp]
+        MS = [Mx, M @ w, M @ xp]
+        GA = np.array([[dot(S[i], AS[j]) for j in range(3)] for i in range(3)])
+        GB = np.array([[dot(S[i], MS[j]) for j in range(3)] for i in range(3)])
+        GA = 0.5 * (GA + GA.T)
+        GB = 0.5 * (GB + GB.T)
+        _, c = rayleigh_ritz3(GA, GB, [v.sum() for v in S])
+        xn = c[0] * x + c[1] * w + c[2] * xp
+        xp = x
+        x = xn / np.sqrt(dot(xn, M @ xn))
+        Ax, Mx = Asig @ x, M @ x
+        rho_prev = rho
+        lam = dot(x, Ax)
+    return sigma + lam, x, maxit_outer, inner_its, info
+
+
 def cell_eigenpair(g: q1.Grid, V):
     """(sigma, psi) of the x-periodic cell problem; psi > 0, psi^T M_# psi = 1."""
     K, M, MV = q1.assemble_cell(g, V)
@@ -160,3 +255,6 @@ class Problem:
 
     def ground_state(self, **kw):
         return inverse_iteration(self.Asig, self.M, self.sigma, self.prec, **kw)
+
+    def ground_state_lopcg(self, **kw):
+        return si_lopcg(self.A, self.M, self.sigma, self.prec, **kw)

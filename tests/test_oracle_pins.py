@@ -337,3 +337,92 @@ def test_printed_cell_shift_is_recorded_unpinned():
     s4, _ = solvers.cell_eigenpair(g4, potential(w))
     assert abs(s2 - s4) / s4 < 1e-5
     assert abs(s2 - gold["sigma_printed"]) > 1.0
+
+
+# --- SI-LOPCG (Algorithm 1) and the inner-tolerance strategies of Sec. 4.3 ------------
+
+def test_rayleigh_ritz3_brute_force():
+    """The orthogonalised Rayleigh-Ritz step returns the minimum of the Rayleigh quotient
+    over the span (brute force: the lowest eigenvalue of the projected pencil from an
+    explicit B-orthonormal basis), a B-normalised Ritz vector with that quotient and
+    positive sum; an exactly dependent third vector is dropped."""
+    rng = np.random.default_rng(41)
+    n = 30
+    Q = rng.standard_normal((n, n))
+    A = Q @ Q.T + n * np.eye(n)
+    R = rng.standard_normal((n, n))
+    B = R @ R.T + n * np.eye(n)
+    S = rng.standard_normal((n, 3))
+    GA, GB = S.T @ A @ S, S.T @ B @ S
+    theta, c = solvers.rayleigh_ritz3(GA, GB, S.sum(axis=0))
+    Lb = np.linalg.cholesky(B)
+    Qs, _ = np.linalg.qr(Lb.T @ S)                  # B-orthonormal basis: S' = Lb^-T Qs
+    Sb = np.linalg.solve(Lb.T, Qs)
+    ref = np.linalg.eigvalsh(Sb.T @ A @ Sb)[0]
+    assert theta == pytest.approx(ref, rel=1e-12)
+    y = S @ c
+    assert y @ B @ y == pytest.approx(1.0, rel=1e-12)
+    assert y @ A @ y == pytest.approx(theta, rel=1e-12)
+    assert y.sum() > 0
+    # dependent third vector: same as the two-vector problem
+    S2 = np.column_stack([S[:, 0], S[:, 1], 2.0 * S[:, 0] - 3.0 * S[:, 1]])
+    t2, c2 = solvers.rayleigh_ritz3(S2.T @ A @ S2, S2.T @ B @ S2, S2.sum(axis=0))
+    ref2 = sla.eigh(S[:, :2].T @ A @ S[:, :2], S[:, :2].T @ B @ S[:, :2], eigvals_only=True)[0]
+    assert t2 == pytest.approx(ref2, rel=1e-10)
+    assert c2[2] == 0.0
+
+
+@pytest.mark.parametrize("inner", ["fixed", "adaptive", "fused"])
+def test_si_lopcg_reaches_ground_state(inner):
+    """All three inner strategies of Sec. 4.3 reach the exact ground state (dense
+    generalised eigensolver) to 1e-10 with residual eta <= 1e-8, and the Ritz values
+    never increase (x_k lies in the next search space)."""
+    w = Workload("t", p=1, L=6, n=8, overlap=2, kind="cos1")
+    P = solvers.Problem(q1.Grid.from_workload(w), potential(w))
+    le, _ = solvers.exact_ground_state(P.A, P.M, dense_limit=5000)
+    rhos = []
+    orig = solvers.rayleigh_ritz3
+
+    def spy(GA, GB, sums, drop=1e-10):
+        t, c = orig(GA, GB, sums, drop)
+        rhos.append(P.sigma + t)
+        return t, c
+
+    solvers.rayleigh_ritz3 = spy
+    try:
+        lam, x, k, inner_its, info = P.ground_state_lopcg(inner=inner)
+    finally:
+        solvers.rayleigh_ritz3 = orig
+    assert lam == pytest.approx(le, rel=1e-10)
+    assert info["eta"] <= 1e-8
+    assert x @ (P.M @ x) == pytest.approx(1.0, rel=1e-12) and x.sum() > 0
+    assert all(b <= a + 1e-12 * abs(a) for a, b in zip(rhos, rhos[1:]))
+
+
+def test_si_lopcg_v0_closed_form():
+    """V = 0: SI-LOPCG with the fused strategy reaches the closed-form lambda_1."""
+    L, n, ny = 12, 8, 8
+    g = grid(1, L, n, ny, delta=2)
+    P = solvers.Problem(g, zeroV(1))
+    h = g.h
+    lam1 = mu(np.pi * h / L, h) + mu(np.pi * h, h)
+    lam, x, k, inner, info = P.ground_state_lopcg(inner="fused")
+    assert lam == pytest.approx(lam1, rel=1e-10)
+
+
+def test_inner_tolerance_strategies_order():
+    """Sec. 4.3: the adaptive inner tolerance min{0.1, ||r_o||} needs fewer inner
+    iterations in total than the fixed 1e-8, and the fused variant (the Schwarz
+    preconditioner in place of the inner solve) fewer still; all reach the same
+    eigenvalue."""
+    w = Workload("t", p=1, L=16, n=16, overlap=2, kind="cos1")
+    P = solvers.Problem(q1.Grid.from_workload(w), potential(w))
+    tot, lams = {}, {}
+    for inner in ("fixed", "adaptive", "fused"):
+        lam, x, k, its, info = P.ground_state_lopcg(inner=inner)
+        tot[inner] = sum(its)
+        lams[inner] = lam
+    assert tot["adaptive"] < tot["fixed"]
+    assert tot["fused"] < tot["adaptive"]
+    assert lams["adaptive"] == pytest.approx(lams["fixed"], rel=1e-10)
+    assert lams["fused"] == pytest.approx(lams["fixed"], rel=1e-10)
