@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=None, help="timed steps of the plain FP64 method")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-lopcg", action="store_true")
     ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -162,29 +163,69 @@ class ClockSampler:
 
 
 def kernel_model(w, info, ntype_counts, nloc_by_type, band, precision):
-    """Algorithmic bytes (or flops) per launch of each kernel class."""
+    """Algorithmic work per launch of each kernel class: (FP64 flops, tensor flops, bytes).
+
+    Bytes count one pass over each vector the kernel must read or write (DOF = interior
+    unknown, f = sum |N_i| / ndof); FP64 flops count 2 per FMA of the arithmetic the
+    kernel must do.  See the design doc, section 4.
+    """
     ndof = info["ndof"]
     nloc_sum = sum(c * n for c, n in zip(ntype_counts, nloc_by_type))
     f = nloc_sum / ndof
     es = 2 if precision == "bf16" else 4
     gemm_flops = sum(2.0 * c * n * n for c, n in zip(ntype_counts, nloc_by_type))
-    fp64_flops = 0.0
+    fp64_band = 0.0
     for c, n in zip(ntype_counts, nloc_by_type):
         b = min(band, n - 1)
         per_sweep = n * b - b * (b + 1) / 2
-        fp64_flops += c * 2 * 2 * per_sweep
+        fp64_band += c * 2 * 2 * per_sweep
+    taps = 3 ** (w.p + 1)
+    if w.p == 1:   # fused p update + stencil + (p, q)
+        stencil = (2.0 * (taps + 2) * ndof, 0.0, 32.0 * ndof)
+    else:
+        stencil = (2.0 * (taps + 1) * ndof, 0.0, 16.0 * ndof)
     return {
-        "stencil_Asigma": ("hbm", 16.0 * ndof),
-        "p_update": ("hbm", 24.0 * ndof),
-        "xr_update": ("hbm", 48.0 * ndof),
-        "prolong_sum": ("hbm", (24.0 + 4.0 * f) * ndof),
-        "pack_restrict": ("hbm", (8.0 + es * f) * ndof),
-        "local_gemm_tc": ("tensor", gemm_flops),
-        "local_solve_fp64": ("alu", fp64_flops),
-        "coarse_restrict": ("hbm", 8.0 * ndof),
-        "outer_step": ("hbm", 24.0 * ndof),
-        "_f": f,
+        "stencil_Asigma": stencil,
+        "p_update": (2.0 * ndof, 0.0, 24.0 * ndof),
+        "xr_update": (6.0 * ndof, 0.0, 48.0 * ndof),
+        "prolong_sum": (2.0 * (3.0 + f) * ndof, 0.0, (24.0 + 4.0 * f) * ndof),
+        "pack_restrict": (2.0 * f * ndof, 0.0, (8.0 + es * f) * ndof),
+        "local_gemm_tc": (0.0, gemm_flops, (es * f + 4.0 * f) * ndof),
+        "local_solve_fp64": (fp64_band, 0.0, 16.0 * f * ndof),
     }
+
+
+def roofline_entry(name, model, ms_total, nlaunch, peaks, peak_src, precision):
+    """The binding roofline of one kernel class (the resource whose ideal time is longest)."""
+    fp64, tens, byt = model
+    avg_s = ms_total / nlaunch / 1e3
+    t_alu = fp64 / (FP64_TFLOPS * 1e12)
+    tpeak = peaks["bf16_tflops"] * (0.5 if precision == "tf32" else 1.0)
+    t_ten = tens / (tpeak * 1e12)
+    t_hbm = byt / (peaks["hbm_gbs"] * 1e9)
+    bound = max((t_alu, "alu"), (t_ten, "tensor"), (t_hbm, "hbm"))[1]
+    if bound == "alu":
+        ent = {"bound": "alu", "achieved": fp64 / avg_s / 1e12, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
+               "peak_source": "FP64 FMA microbenchmark on this GB300 (DESIGN.md section 4)"}
+    elif bound == "tensor":
+        ent = {"bound": "tensor", "achieved": tens / avg_s / 1e12, "peak": tpeak, "unit": "TFLOP/s",
+               "peak_source": peak_src + (" (bf16 x 1/2 for tf32)" if precision == "tf32" else "")}
+    else:
+        ent = {"bound": "hbm", "achieved": byt / avg_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+               "peak_source": peak_src}
+    ent["frac"] = ent["achieved"] / ent["peak"]
+    ent["kernel"] = name
+    ent["avg_launch_us"] = avg_s * 1e6
+    ent["launches"] = nlaunch
+    ent["hbm_gbs_algorithmic"] = byt / avg_s / 1e9
+    ent["traffic"] = TRAFFIC.get(name)
+    return ent
+
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the current kernels
+# from one ncu capture of this workload (profiles/top_kernels_cfg2_bench.md); None when the
+# kernel changed after the capture.
+TRAFFIC = {}
 
 
 # ----------------------------------------------------------------------------------------
@@ -279,7 +320,15 @@ def main():
         lam, outer, tot, mx = dd.dd_inverse_iterate(es.ctx, x)
         return lam, sigma, outer, tot
 
-    def timed(es, nsteps, count_launches=False):
+    def step_lopcg(es, inner):
+        dd.dd_set_potential(es.ctx, V)
+        sigma = dd.dd_cell_eigenpair(es.ctx)
+        dd.dd_coarse_build(es.ctx)
+        x.copy_(ones)
+        lam, outer, tot, mx = dd.dd_lopcg(es.ctx, x, inner)
+        return lam, sigma, outer, tot
+
+    def timed(es, nsteps, count_launches=False, fn=None):
         stream = torch.cuda.current_stream()
         per = []
         res = None
@@ -290,7 +339,7 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            res = step(es)
+            res = step(es) if fn is None else fn(es)
             e1.record(stream)
             torch.cuda.synchronize()
             per.append(e0.elapsed_time(e1))
@@ -327,6 +376,20 @@ def main():
     step(plain)
     per64, res64, _ = timed(plain, fp64_steps)
     fp64_ms = sum(per64) / len(per64)
+
+    # SI-LOPCG (Algorithm 1) with the three inner strategies of Sec. 4.3, same workload and
+    # stop rule, mixed and plain forms
+    lopcg = {}
+    if not args.no_lopcg:
+        for form, es_f in (("mixed", mixed), ("fp64_plain", plain)):
+            for inner in ("fixed", "adaptive", "fused"):
+                if form == "fp64_plain" and inner == "fixed":
+                    continue
+                fn = (lambda e, m=inner: step_lopcg(e, m))
+                fn(es_f)
+                perl, resl, _ = timed(es_f, max(1, min(3, args.steps)), fn=fn)
+                lopcg[f"{form}_{inner}"] = {"ms": sum(perl) / len(perl), "lambda": resl[0], "outer_iters": resl[2],
+                                            "inner_iters_total": resl[3]}
 
     # phase breakdown of one step (host timer around each synchronous call)
     def phases(es):
@@ -370,49 +433,56 @@ def main():
     model = kernel_model(w, info, counts, nlocs, info["band_local"], args.precision)
     busy = {k: v for k, v in kt.items() if v[0] > 0}
     dom = max((k for k in busy if k in model), key=lambda k: busy[k][1])
-    bound, units = model[dom]
-    nlaunch, ms_tot = busy[dom]
-    avg_s = ms_tot / nlaunch / 1e3
-    if bound == "hbm":
-        achieved = units / avg_s / 1e9
-        peak = peaks["hbm_gbs"]
-        unit = "GB/s"
-    elif bound == "tensor":
-        achieved = units / avg_s / 1e12
-        peak = peaks["bf16_tflops"] * (0.5 if args.precision == "tf32" else 1.0)
-        unit = "TFLOP/s"
-    else:
-        achieved = units / avg_s / 1e12
-        peak = FP64_TFLOPS
-        unit = "TFLOP/s"
-    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": peak_src if bound != "alu" else "DFMA microbenchmark",
-                "avg_launch_us": avg_s * 1e6, "launches": nlaunch}
+    roofline = roofline_entry(dom, model[dom], busy[dom][1], busy[dom][0], peaks, peak_src, args.precision)
+    others = {k: roofline_entry(k, model[k], v[1], v[0], peaks, peak_src, args.precision)
+              for k, v in busy.items() if k in model and k != dom}
     kernel_table = {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in busy.items()}
     kernel_table64 = {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in kt64.items() if v[0] > 0}
 
-    # end to end through dd_eigenpair with host buffers (pinned), context set-up included
+    # end to end through the public C-ABI with HOST buffers: one context serves the stream of
+    # potentials (dd_setup once); every step uploads V and x_0 from pinned host memory and
+    # returns phi to host memory.  The one-shot dd_eigenpair (context set-up and teardown
+    # inside) is reported beside it.
     e2e = None
     if not args.no_e2e:
         Vp = torch.from_numpy(V_host).pin_memory()
+        x0 = torch.ones(w.dofs, dtype=torch.float64).pin_memory()
         phi = torch.empty(w.dofs, dtype=torch.float64).pin_memory()
-        g = dd.grid_from_workload(w, precision=dd.PRECISIONS[args.precision])
-        dd.dd_eigenpair(g, Vp, phi_out=phi)
+        es_h = make(args.precision)
+
+        def host_step():
+            dd.dd_set_potential(es_h.ctx, Vp)
+            dd.dd_cell_eigenpair(es_h.ctx)
+            dd.dd_coarse_build(es_h.ctx)
+            phi.copy_(x0)
+            return dd.dd_inverse_iterate(es_h.ctx, phi)
+
+        for _ in range(2):
+            host_step()
         ts = []
-        for _ in range(max(1, min(3, args.steps))):
+        for _ in range(max(1, args.steps)):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            lam_e, _ = dd.dd_eigenpair(g, Vp, phi_out=phi)
+            lam_h = host_step()[0]
             ts.append(time.perf_counter() - t0)
         te = sum(ts) / len(ts)
+        es_h.close()
+        g = dd.grid_from_workload(w, precision=dd.PRECISIONS[args.precision])
+        dd.dd_eigenpair(g, Vp, phi_out=phi)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dd.dd_eigenpair(g, Vp, phi_out=phi)
+        t_cold = time.perf_counter() - t0
         if world > 1:
             tt = torch.tensor([te], device=dev, dtype=torch.float64)
             torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
             te = float(tt.item())
-        e2e = {"value": world / te, "unit": UNIT, "h2d_bytes_per_step": int(Vp.numel() * 8),
-               "d2h_bytes_per_step": int(phi.numel() * 8), "ms_per_step": te * 1e3}
+        e2e = {"value": world / te, "unit": UNIT, "h2d_bytes_per_step": int(Vp.numel() * 8 + x0.numel() * 8),
+               "d2h_bytes_per_step": int(phi.numel() * 8), "ms_per_step": te * 1e3,
+               "path": "dd_set_potential + dd_cell_eigenpair + dd_coarse_build + dd_inverse_iterate, host buffers",
+               "lambda": lam_h,
+               "one_shot_dd_eigenpair_ms": t_cold * 1e3}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -443,7 +513,12 @@ def main():
             "lambda": lam, "sigma": sigma, "outer_iters": outer, "inner_iters_total": inner_tot,
             "fp64_plain": {"lambda": res64[0], "outer_iters": res64[2], "inner_iters_total": res64[3]},
             "pcg_iters_per_s": inner_tot / (step_ms / 1e3),
+            "si_lopcg_time_to_ground_state": lopcg,
             "roofline": roofline,
+            "roofline_other_kernels": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv)
+                                           for kk, vv in v.items() if kk in ("bound", "achieved", "peak", "unit",
+                                                                             "frac", "avg_launch_us")}
+                                       for k, v in others.items()},
             "breakdown_ms": breakdown,
             "kernels_mixed": kernel_table, "kernels_fp64": kernel_table64,
             "gpu_launches": launches,

@@ -160,5 +160,8 @@ WORKLOADS = {
     "cfg2_small": Workload("cfg2_small", p=1, L=64, n=32, overlap=4, kind="cos4", seed=2311),
     "cfg3": Workload("cfg3", p=2, L=64, n=16, overlap=2, kind="wells"),
     "cfg3_small": Workload("cfg3_small", p=2, L=4, n=8, overlap=2, kind="wells"),
+    # the d=3 well lattice at its full cell resolution and overlap on a 3 x 3 cell box: the
+    # same nine local matrices and cell problem as the 64 x 64 box
+    "cfg3_mid": Workload("cfg3_mid", p=2, L=3, n=16, overlap=2, kind="wells"),
     "e1": Workload("e1", p=1, L=8, n=30, overlap=1, kind="sin4"),
 }

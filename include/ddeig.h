@@ -160,6 +160,31 @@ int dd_inverse_iterate(dd_ctx* ctx, double* x, double tol_res, double tol_lam, i
                        int* inner_total_out, int* inner_max_out);
 
 /*
+ * dd_lopcg -- inexact shift-and-invert preconditioned LOPCG (Algorithm 1, Sec. 2.1; inner
+ * strategies of Sec. 4.3).  Outer residual r_o = A x_k - rho_k M x_k (x_k M-normalised,
+ * rho_k its Rayleigh quotient); inner step w_k:
+ *   DD_INNER_FIXED     PCG on A_sigma w = r_o from zero to relative residual rtol_inner
+ *   DD_INNER_ADAPTIVE  the same to relative residual min(0.1, ||r_o||_2)
+ *   DD_INNER_FUSED     w = M_AS2^{-1} r_o: one application of the two-level Schwarz
+ *                      preconditioner, no inner Krylov loop
+ * then x_{k+1} = the lowest Ritz vector of span{x_k, w_k, x_{k-1}} (M-orthonormalised basis
+ * in the order x_k, w_k, x_{k-1}; a direction whose M-norm drops below 1e-10 of its norm
+ * before orthogonalisation is dropped), M-normalised with sum x > 0.  x_0 = e_1 (the first
+ * interior node), x_1 = the caller's x.  Stops like dd_inverse_iterate: eta <= tol_res and
+ * |rho_k - rho_{k-1}| <= tol_lam |rho_k|.
+ *   x                 host or device, ndof doubles; in: x_1 (nonzero), out: phi
+ *   inner_total_out   inner PCG iterations summed (preconditioner applications when fused)
+ * DD_EINVAL for a bad mode or tolerance, DD_EMAXIT after maxit_outer steps (x holds the
+ * last iterate), DD_ENOTSPD / DD_ENAN if the Rayleigh-Ritz basis degenerates.
+ */
+#define DD_INNER_FIXED    0
+#define DD_INNER_ADAPTIVE 1
+#define DD_INNER_FUSED    2
+int dd_lopcg(dd_ctx* ctx, double* x, int inner, double tol_res, double tol_lam, int maxit_outer,
+             double rtol_inner, double* lambda_out, int* outer_out, int* inner_total_out,
+             int* inner_max_out);
+
+/*
  * dd_eigenpair -- convenience: dd_setup, dd_cell_eigenpair, dd_coarse_build and
  * dd_inverse_iterate from x_0 = 1 with tol_res = 1e-8, tol_lam = 1e-10, rtol_inner = 1e-8,
  * maxit_outer = 100, then dd_destroy.
@@ -206,11 +231,15 @@ int dd_coarse_matrix(dd_ctx* ctx, double* A0_host);
  *   DD_OPT_CHECK_EVERY  iterations between host convergence checks [8]
  *   DD_OPT_USE_GRAPH    replay the PCG iteration as a CUDA graph [1]
  *   DD_OPT_FLEXIBLE     -1 automatic (flexible iff rounded local inverses) / 0 / 1 [-1]
- *   DD_OPT_TIMING       1: time every kernel class with CUDA events (eager launches) [0] */
+ *   DD_OPT_TIMING       1: time every kernel class with CUDA events (eager launches) [0]
+ *   DD_OPT_LOCAL_RHS    FP64 local solves: subdomains of one type solved together by one warp,
+ *                       1, 2 or 4 (capped by shared memory), 0 = default (2 where allowed) [0]; the result
+ *                       does not depend on it (same operations per vector) */
 #define DD_OPT_CHECK_EVERY 0
 #define DD_OPT_USE_GRAPH   1
 #define DD_OPT_FLEXIBLE    2
 #define DD_OPT_TIMING      3
+#define DD_OPT_LOCAL_RHS   4
 int dd_set_option(dd_ctx* ctx, int option, int value);
 
 /* Per-kernel-class timing collected while DD_OPT_TIMING = 1: for class k (0 <= k < count),

@@ -23,8 +23,10 @@ DD_OK, DD_EINVAL, DD_ESTATE, DD_ENOMEM, DD_ECUDA, DD_ENAN, DD_ENOTSPD, DD_EMAXIT
 DD_PREC_FP64, DD_PREC_TF32, DD_PREC_BF16 = 0, 1, 2
 DD_PU_EQUAL, DD_PU_DISTANCE = 0, 1
 DD_OP_ASIGMA, DD_OP_MASS, DD_OP_A = 0, 1, 2
-DD_OPT_CHECK_EVERY, DD_OPT_USE_GRAPH, DD_OPT_FLEXIBLE, DD_OPT_TIMING = 0, 1, 2, 3
+DD_OPT_CHECK_EVERY, DD_OPT_USE_GRAPH, DD_OPT_FLEXIBLE, DD_OPT_TIMING, DD_OPT_LOCAL_RHS = 0, 1, 2, 3, 4
 PRECISIONS = {"fp64": DD_PREC_FP64, "tf32": DD_PREC_TF32, "bf16": DD_PREC_BF16}
+DD_INNER_FIXED, DD_INNER_ADAPTIVE, DD_INNER_FUSED = 0, 1, 2
+INNER_MODES = {"fixed": DD_INNER_FIXED, "adaptive": DD_INNER_ADAPTIVE, "fused": DD_INNER_FUSED}
 
 
 class dd_grid(ctypes.Structure):
@@ -54,6 +56,8 @@ _SIGS = {
     "dd_pcg_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int, POINTER(c_int), POINTER(c_double)]),
     "dd_inverse_iterate": (c_int, [c_void_p, c_void_p, c_double, c_double, c_int, c_double, POINTER(c_double),
                                    POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
+    "dd_lopcg": (c_int, [c_void_p, c_void_p, c_int, c_double, c_double, c_int, c_double, POINTER(c_double),
+                         POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
     "dd_eigenpair": (c_int, [POINTER(dd_grid), c_void_p, c_size_t, c_void_p, POINTER(c_double), c_void_p,
                              POINTER(c_double)]),
     "dd_destroy": (None, [c_void_p]),
@@ -189,6 +193,15 @@ def dd_inverse_iterate(ctx, x, tol_res=1e-8, tol_lam=1e-10, maxit_outer=100, rto
     return lam.value, outer.value, tot.value, mx.value
 
 
+def dd_lopcg(ctx, x, inner="fused", tol_res=1e-8, tol_lam=1e-10, maxit_outer=1000, rtol_inner=1e-8):
+    """SI-LOPCG (Algorithm 1); ``inner`` is "fixed", "adaptive" or "fused" (or its code)."""
+    mode = INNER_MODES[inner] if isinstance(inner, str) else int(inner)
+    lam, outer, tot, mx = c_double(), c_int(), c_int(), c_int()
+    _check(lib().dd_lopcg(ctx, _ptr(x), mode, tol_res, tol_lam, maxit_outer, rtol_inner, byref(lam), byref(outer),
+                          byref(tot), byref(mx)), ctx)
+    return lam.value, outer.value, tot.value, mx.value
+
+
 def dd_eigenpair(grid: dd_grid, V_cell_qp, stream=None, phi_out=None):
     lam, sig = c_double(), c_double()
     n = V_cell_qp.numel() if hasattr(V_cell_qp, "numel") else V_cell_qp.size
@@ -293,3 +306,6 @@ class Eigensolver:
 
     def ground_state(self, x, **kw):
         return dd_inverse_iterate(self.ctx, x, **kw)
+
+    def ground_state_lopcg(self, x, inner="fused", **kw):
+        return dd_lopcg(self.ctx, x, inner, **kw)

@@ -5,9 +5,11 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <limits>
+#include <utility>
 #include <new>
 
-#include "dd_common.cuh"
+#include "dd_band.cuh"
 
 using dd::Error;
 
@@ -69,7 +71,7 @@ void* dev_alloc(dd_ctx* c, size_t bytes) {
 
 static const char* kClassNames[KC_COUNT] = {
     "stencil_Asigma", "p_update", "xr_update", "local_solve_fp64", "pack_restrict", "local_gemm_tc",
-    "prolong_sum", "coarse_restrict", "coarse_solve", "outer_step", "misc"};
+    "prolong_sum", "coarse_restrict", "coarse_solve", "outer_step", "misc", "rayleigh_ritz"};
 
 void timer_begin(dd_ctx* c, int, cudaStream_t s, cudaEvent_t* e0) {
   *e0 = nullptr;
@@ -112,6 +114,18 @@ void timer_collect(dd_ctx* c) {
 namespace {
 
 using namespace dd;
+
+// FP64 local solves: groups of up to k consecutive slots of one type, one group per warp
+void set_local_groups(dd_ctx* c, int k) {
+  c->rhs_k = k;
+  c->group_h.clear();
+  for (int t = 0; t < c->ntypes; ++t)
+    for (int j = 0; j < c->type_count[t]; j += k)
+      c->group_h.push_back(make_int2(c->type_first[t] + j, std::min(k, c->type_count[t] - j)));
+  c->ngroups = (int)c->group_h.size();
+  DD_CUDA(cudaMemcpyAsync(c->groups, c->group_h.data(), sizeof(int2) * c->group_h.size(), cudaMemcpyHostToDevice,
+                          c->stream));
+}
 
 void build_subdomains(dd_ctx* c) {
   const Geo& g = c->g;
@@ -179,6 +193,12 @@ void build_subdomains(dd_ctx* c) {
   }
   for (int s = 0; s < g.nsub; ++s)
     sr[s] = make_int4(slot[s] * c->kpad, c->subs_h[s].type * c->kpad, c->subs_h[s].w2, c->subs_h[s].nloc);
+  std::vector<int> sos(g.nsub);
+  for (int s2 = 0; s2 < g.nsub; ++s2) sos[slot[s2]] = s2;
+  c->sub_of_slot = (int*)dev_alloc(c, sizeof(int) * g.nsub);
+  c->groups = (int2*)dev_alloc(c, sizeof(int2) * g.nsub);
+  DD_CUDA(cudaMemcpyAsync(c->sub_of_slot, sos.data(), sizeof(int) * g.nsub, cudaMemcpyHostToDevice, c->stream));
+  set_local_groups(c, std::min(2, rhs_per_warp(c->nloc_max, c->band)));
   c->axown = (int4*)dev_alloc(c, sizeof(int4) * g.ncx);
   c->subrow = (int4*)dev_alloc(c, sizeof(int4) * g.nsub);
   DD_CUDA(cudaMemcpyAsync(c->axown, ax.data(), sizeof(int4) * g.ncx, cudaMemcpyHostToDevice, c->stream));
@@ -376,6 +396,7 @@ void dd_destroy(dd_ctx* c) {
   for (void* p : c->allocs) cudaFree(p);
   if (c->st_h) cudaFreeHost(c->st_h);
   if (c->ost_h) cudaFreeHost(c->ost_h);
+  if (c->lst_h) cudaFreeHost(c->lst_h);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
@@ -686,6 +707,7 @@ int dd_inverse_iterate(dd_ctx* c, double* x, double tol_res, double tol_lam, int
     enter(c);
     cudaStream_t s = c->stream;
     const double sigma = c->sigma;
+    DD_CUDA(cudaMemsetAsync(c->ost, 0, sizeof(OuterState), s));
     // x_0 -> M-normalised iterate xe, w2 = M xe
     load_vec(c, x, c->w1);
     TIMED(KC_OUTER, s, launch_stencil(c, c->tabM, c->w1, c->w2, s));
@@ -721,6 +743,119 @@ int dd_inverse_iterate(dd_ctx* c, double* x, double tol_res, double tol_lam, int
       rho_prev = rho;
     }
     store_vec(c, c->xe, x);
+    DD_CUDA(cudaStreamSynchronize(s));
+    if (lambda_out) *lambda_out = rho;
+    if (outer_out) *outer_out = std::min(k, maxit_outer);
+    if (inner_total_out) *inner_total_out = inner_tot;
+    if (inner_max_out) *inner_max_out = inner_max;
+    if (status != DD_OK) return fail(c, status, "outer iteration limit reached");
+    return DD_OK;
+  });
+}
+
+int dd_lopcg(dd_ctx* c, double* x, int inner, double tol_res, double tol_lam, int maxit_outer, double rtol_inner,
+             double* lambda_out, int* outer_out, int* inner_total_out, int* inner_max_out) {
+  if (!x || maxit_outer < 1) return fail(c, DD_EINVAL, "bad argument");
+  if (inner != DD_INNER_FIXED && inner != DD_INNER_ADAPTIVE && inner != DD_INNER_FUSED)
+    return fail(c, DD_EINVAL, "inner must be DD_INNER_FIXED, DD_INNER_ADAPTIVE or DD_INNER_FUSED");
+  if (inner == DD_INNER_FIXED && !(rtol_inner > 0.0)) return fail(c, DD_EINVAL, "rtol_inner must be > 0");
+  int rc = stage_err(c, 3);
+  if (rc) return rc;
+  return guarded(c, [&]() -> int {
+    enter(c);
+    cudaStream_t s = c->stream;
+    const Geo& g = c->g;
+    const double sigma = c->sigma;
+    if (!c->lst) {
+      c->lst = (LopState*)dev_alloc(c, sizeof(LopState));
+      DD_CUDA(cudaMallocHost(&c->lst_h, sizeof(LopState)));
+      c->lop_red = (double*)dev_alloc(c, sizeof(double) * kMaxRedBlocks * 15);
+      for (double*& v : c->lop) v = alloc_vec(c);
+    }
+    // work vectors: iterate, previous iterate, spare; their A_sigma- and M-images; the
+    // images of w; the outer residual
+    double *X = c->lop[0], *XP = c->lop[1], *T = c->lop[2];
+    double *AX = c->lop[3], *AXP = c->lop[4], *MX = c->lop[5], *MXP = c->lop[6];
+    double *AW = c->lop[7], *MW = c->lop[8], *RO = c->lop[9];
+    for (double* v : c->lop) DD_CUDA(cudaMemsetAsync(v, 0, sizeof(double) * g.plen, s));
+    DD_CUDA(cudaMemsetAsync(c->ost, 0, sizeof(OuterState), s));
+    DD_CUDA(cudaMemsetAsync(c->lst, 0, sizeof(LopState), s));
+    // x_0 = e_1 (first interior node), B-normalised, and its images
+    const long long first = (g.p == 1) ? (long long)g.Ypad : ((long long)g.ncx + 1) * g.Ypad;
+    launch_set_entry(XP, first, 1.0, s);
+    TIMED(KC_OUTER, s, launch_stencil(c, c->tabM, XP, MXP, s));
+    TIMED(KC_OUTER, s, launch_lop_normalize(c, XP, MXP, s));
+    TIMED(KC_OUTER, s, launch_stencil(c, c->tabS, XP, AXP, s));
+    // x_1 from the caller, B-normalised; A_sigma x_1, rho and the outer residual
+    load_vec(c, x, X);
+    TIMED(KC_OUTER, s, launch_stencil(c, c->tabM, X, MX, s));
+    TIMED(KC_OUTER, s, launch_lop_normalize(c, X, MX, s));
+    TIMED(KC_OUTER, s, launch_outer_residual(c, X, MX, AX, s, RO));
+    read_outer(c);
+    if (c->ost_h->status != 0) throw Error(c->ost_h->status, "start vector has zero M-norm");
+    double lam = c->ost_h->xAx, rr = c->ost_h->rr, mm = c->ost_h->mm;
+    double rho_prev = std::numeric_limits<double>::infinity(), rho = sigma + lam;
+    int k = 0, inner_tot = 0, inner_max = 0, status = DD_EMAXIT;
+    for (k = 0; k <= maxit_outer; ++k) {
+      rho = sigma + lam;
+      if (!std::isfinite(rho)) throw Error(DD_ENAN, "non-finite Rayleigh quotient");
+      const double eta = std::sqrt(rr / mm) / std::fabs(rho);
+      if (eta <= tol_res && std::fabs(rho - rho_prev) <= tol_lam * std::fabs(rho)) {
+        status = DD_OK;
+        break;
+      }
+      if (k == maxit_outer) break;
+      // inner step: A_sigma w = r_o inexactly (Algorithm 1), or w = M^{-1} r_o (fused)
+      const double* W = nullptr;
+      int it = 0;
+      if (inner == DD_INNER_FUSED) {
+        PcgState init;
+        std::memset(&init, 0, sizeof(init));
+        DD_CUDA(cudaMemcpyAsync(c->st, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+        precond(c, RO, 0);
+        W = c->z;
+        it = 1;
+      } else {
+        const double rt = (inner == DD_INNER_FIXED) ? rtol_inner : std::min(0.1, std::sqrt(rr));
+        DD_CUDA(cudaMemsetAsync(c->x, 0, sizeof(double) * g.plen, s));
+        double rel = 0.0;
+        const int prc = pcg_run(c, RO, rt, 10000, &it, &rel);
+        if (prc != DD_OK && prc != DD_EMAXIT) return prc;
+        W = c->x;
+      }
+      inner_tot += it;
+      inner_max = std::max(inner_max, it);
+      TIMED(KC_OUTER, s, launch_stencil(c, c->tabS, W, AW, s));
+      TIMED(KC_OUTER, s, launch_stencil(c, c->tabM, W, MW, s));
+      // Rayleigh-Ritz on span{x_k, w_k, x_{k-1}} and x_{k+1} = S c
+      const double* S[3] = {X, W, XP};
+      const double* AS[3] = {AX, AW, AXP};
+      const double* MS[3] = {MX, MW, MXP};
+      TIMED(KC_RR, s, launch_lop_gram(c, S, AS, MS, 1e-10, s));
+      TIMED(KC_RR, s, launch_lop_update(c, X, W, XP, T, s));
+      // rotate: x_{k-1} <- x_k, x_k <- x_{k+1}; the images of x_k become those of x_{k-1}
+      double* t0 = XP;
+      XP = X;
+      X = T;
+      T = t0;
+      std::swap(AX, AXP);
+      std::swap(MX, MXP);
+      TIMED(KC_OUTER, s, launch_stencil(c, c->tabM, X, MX, s));
+      TIMED(KC_OUTER, s, launch_lop_normalize(c, X, MX, s));
+      TIMED(KC_OUTER, s, launch_outer_residual(c, X, MX, AX, s, RO));
+      DD_CUDA(cudaMemcpyAsync(c->lst_h, c->lst, sizeof(LopState), cudaMemcpyDeviceToHost, s));
+      read_outer(c);
+      if (c->lst_h->status != 0) throw Error(c->lst_h->status, "Rayleigh-Ritz step failed");
+      if (c->ost_h->status != 0) throw Error(c->ost_h->status, "outer normalisation failed");
+      rho_prev = rho;
+      lam = c->ost_h->xAx;
+      rr = c->ost_h->rr;
+      mm = c->ost_h->mm;
+    }
+    // keep the buffer roles for the next call
+    c->lop[0] = X; c->lop[1] = XP; c->lop[2] = T;
+    c->lop[3] = AX; c->lop[4] = AXP; c->lop[5] = MX; c->lop[6] = MXP;
+    store_vec(c, X, x);
     DD_CUDA(cudaStreamSynchronize(s));
     if (lambda_out) *lambda_out = rho;
     if (outer_out) *outer_out = std::min(k, maxit_outer);
@@ -797,6 +932,18 @@ int dd_set_option(dd_ctx* c, int option, int value) {
       c->flexible_opt = value;
       break;
     case DD_OPT_TIMING: c->timing = value ? 1 : 0; break;
+    case DD_OPT_LOCAL_RHS: {
+      if (value != 0 && value != 1 && value != 2 && value != 4)
+        return fail(c, DD_EINVAL, "local right-hand sides per warp must be 0, 1, 2 or 4");
+      const int kmax = rhs_per_warp(c->nloc_max, c->band);
+      const int k = value == 0 ? std::min(2, kmax) : std::min(value, kmax);
+      try {
+        set_local_groups(c, k);
+      } catch (const Error& e) {
+        return fail(c, e.code, e.msg);
+      }
+      break;
+    }
     default: return fail(c, DD_EINVAL, "unknown option");
   }
   reset_graph(c);

@@ -12,14 +12,24 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // Last-block counters (one per reduction site so that concurrent kernels never share one).
 enum CounterId {
-  CNT_PQ = 0, CNT_RR, CNT_RZ, CNT_INIT, CNT_DOT0, CNT_DOT1, CNT_OUTER0, CNT_OUTER1, CNT_OUTER2,
+  CNT_PQ = 0, CNT_RR, CNT_RZ, CNT_INIT, CNT_DOT0, CNT_DOT1, CNT_OUTER0, CNT_OUTER1, CNT_OUTER2, CNT_LOP,
   CNT_NUM = 16
 };
 constexpr int kMaxRedBlocks = 4096;   // partial slots per value
 
+// Tree sum over the warp (result in lane 0).  Only the lanes whose partial survives add:
+// FP64 instructions issue at 2 lanes per clock per SM on GB300, so the 31 adds of the
+// predicated tree cost a fifth of the 160 of a full butterfly.
 __device__ __forceinline__ double warp_sum(double v) {
+  const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+  for (int o = 16; o > 0; o >>= 1) {
+    const double u = __shfl_down_sync(kFull, v, o);
+    // a predicated add (an if-converted select would issue the add on every lane)
+    asm("{\n .reg .pred q;\n setp.lt.s32 q, %2, %3;\n @q add.rn.f64 %0, %0, %1;\n}\n"
+        : "+d"(v)
+        : "d"(u), "r"(lane), "r"(o));
+  }
   return v;
 }
 
@@ -82,6 +92,19 @@ __device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* partials,
 // GB300 retires FP64 instructions (conversions included) at 2 per clock per SM; these
 // conversions do the same rounding with integer operations for normal-range values.
 
+// Out-of-line fallbacks for non-normal values (kept out of line so that they are not
+// if-converted into the common path).
+static __device__ __noinline__ unsigned short bf16_bits_slow(double x) {
+  const __nv_bfloat16 h = __double2bfloat16(x);
+  return *reinterpret_cast<const unsigned short*>(&h);
+}
+static __device__ __noinline__ float tf32_slow(double x) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"((float)x));
+  return __uint_as_float(r);
+}
+static __device__ __noinline__ double f64_slow(float f) { return (double)f; }
+
 // IEEE round-to-nearest-even of a double to bfloat16 (bits); non-normal results fall back to
 // the hardware conversion.
 __device__ __forceinline__ unsigned short f64_to_bf16_bits(double x) {
@@ -90,10 +113,7 @@ __device__ __forceinline__ unsigned short f64_to_bf16_bits(double x) {
   const int e = (int)((u >> 52) & 0x7FF);
   const int eb = e - 1023 + 127;
   if (e == 0 && (u << 1) == 0) return (unsigned short)(sign << 15);   // +-0
-  if (eb < 1 || eb > 254) {
-    const __nv_bfloat16 h = __double2bfloat16(x);
-    return *reinterpret_cast<const unsigned short*>(&h);
-  }
+  if (__builtin_expect(eb < 1 || eb > 254, 0)) return bf16_bits_slow(x);
   const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
   const unsigned long long keep = m >> 45, rem = m & ((1ull << 45) - 1), half = 1ull << 44;
   unsigned r = ((unsigned)eb << 7) | (unsigned)keep;
@@ -109,11 +129,7 @@ __device__ __forceinline__ float f64_to_tf32(double x) {
   const int e = (int)((u >> 52) & 0x7FF);
   const int ef = e - 1023 + 127;
   if (e == 0 && (u << 1) == 0) return __uint_as_float(sign << 31);
-  if (ef < 1 || ef > 254) {
-    unsigned r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"((float)x));
-    return __uint_as_float(r);
-  }
+  if (__builtin_expect(ef < 1 || ef > 254, 0)) return tf32_slow(x);
   const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
   const unsigned long long keep = m >> 42, rem = m & ((1ull << 42) - 1), half = 1ull << 41;
   unsigned r = ((unsigned)ef << 10) | (unsigned)keep;
@@ -125,9 +141,9 @@ __device__ __forceinline__ float f64_to_tf32(double x) {
 __device__ __forceinline__ double f32_to_f64(float f) {
   const unsigned u = __float_as_uint(f);
   const unsigned e = (u >> 23) & 0xFF;
-  if (e == 0 || e == 255) {
+  if (__builtin_expect(e == 0 || e == 255, 0)) {
     if ((u << 1) == 0) return __longlong_as_double((long long)((unsigned long long)(u >> 31) << 63));
-    return (double)f;
+    return f64_slow(f);
   }
   const unsigned long long bits = ((unsigned long long)(u >> 31) << 63) |
                                   ((unsigned long long)(e + 896) << 52) |

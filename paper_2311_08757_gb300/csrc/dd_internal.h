@@ -84,6 +84,16 @@ struct PcgState {
   int pad_[3];
 };
 
+// Scalars of one SI-LOPCG Rayleigh-Ritz step (Algorithm 1): Gram matrices (upper triangles,
+// entries (0,0) (0,1) (0,2) (1,1) (1,2) (2,2)) of S = [x_k, w_k, x_{k-1}] under A_sigma and M,
+// the sums of the three vectors, the Ritz coefficients c and value theta (shifted by -sigma).
+struct LopState {
+  double GA[6], GB[6], sums[3];
+  double c[3];
+  double theta;
+  int m, status;
+};
+
 // Scalars of the outer iteration.
 struct OuterState {
   double wMw, wsum, scale;
@@ -96,7 +106,7 @@ struct OuterState {
 
 enum KernelClass {
   KC_STENCIL = 0, KC_PUPDATE, KC_XRUPDATE, KC_LOCAL_FP64, KC_PACK, KC_GEMM, KC_PROLONG,
-  KC_CRESTRICT, KC_CSOLVE, KC_OUTER, KC_MISC, KC_COUNT
+  KC_CRESTRICT, KC_CSOLVE, KC_OUTER, KC_MISC, KC_RR, KC_COUNT
 };
 
 struct Timer {
@@ -141,6 +151,10 @@ struct dd_ctx {
   int4* axown = nullptr;            // device, per x node column a: {owner0, local col0, owner1 or -1, local col1}
   int4* subrow = nullptr;           // device, per subdomain: {row offset in Y (slot kpad), type kpad, w2, nloc}
   int* slot_of_sub = nullptr;       // device: subdomain id -> packed row (type-sorted)
+  int* sub_of_slot = nullptr;       // device: packed row -> subdomain id
+  int2* groups = nullptr;           // device: {first slot, count} of same-type slots solved by one warp
+  int ngroups = 0, rhs_k = 1;       // FP64 local solves: groups and right-hand sides per warp
+  std::vector<int2> group_h;        // host copy of groups
   int nloc_max = 0, kpad = 0, band = 0;
 
   // V and stencil tables [tap][cls]
@@ -192,6 +206,10 @@ struct dd_ctx {
   dd::OuterState* ost = nullptr;
   dd::PcgState* st_h = nullptr;    // pinned mirror
   dd::OuterState* ost_h = nullptr; // pinned mirror
+  dd::LopState* lst = nullptr;     // SI-LOPCG step scalars (device)
+  dd::LopState* lst_h = nullptr;   // pinned mirror
+  double* lop_red = nullptr;       // partials of the 15 Gram sums
+  double* lop[10] = {};            // SI-LOPCG work vectors (padded layout)
 
   // graph of one block of PCG iterations
   cudaGraphExec_t graph = nullptr;
@@ -227,6 +245,8 @@ void launch_local_assemble(dd_ctx* c);
 int launch_band_factor(dd_ctx* c, double* CB, double* RB, double* inv, int nmat, int n, int b, int* flag);
 void launch_band_solve_local(dd_ctx* c, const double* r, double* c0, cudaStream_t s);
 void launch_band_inverse(dd_ctx* c, double* out, int ld);
+void launch_band_inverse_rows(int n, int b, const double* CB, const double* RB, const double* inv, double* out,
+                              cudaStream_t s);
 
 // cell problem
 int cell_eigenpair(dd_ctx* c);
@@ -246,7 +266,15 @@ void gemm_free(dd_ctx* c);
 
 // outer iteration
 void launch_outer_normalize(dd_ctx* c, const double* w, double* Mw, double* xout, cudaStream_t s);
-void launch_outer_residual(dd_ctx* c, const double* xe, const double* Mx, double* Ax, cudaStream_t s);
+void launch_outer_residual(dd_ctx* c, const double* xe, const double* Mx, double* Ax, cudaStream_t s,
+                           double* ro = nullptr);
+void launch_outer_dots(dd_ctx* c, const double* w, const double* Mw, cudaStream_t s);
+void launch_lop_gram(dd_ctx* c, const double* const S[3], const double* const AS[3], const double* const MS[3],
+                     double drop, cudaStream_t s);
+void launch_lop_update(dd_ctx* c, const double* x, const double* w, const double* xp, double* out,
+                       cudaStream_t s);
+void launch_lop_normalize(dd_ctx* c, double* x, double* Mx, cudaStream_t s);
+void launch_set_entry(double* v, long long idx, double val, cudaStream_t s);
 
 // timing helpers
 void timer_begin(dd_ctx* c, int kc, cudaStream_t s, cudaEvent_t* e0);

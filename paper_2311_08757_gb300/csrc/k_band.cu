@@ -24,53 +24,82 @@ namespace dd {
 // ----------------------------------------------------------------------------------------
 constexpr int kBandWinMax = 160;
 
+template <int P>
 __global__ void __launch_bounds__(1024) k_band_factor_win(double* CB, double* inv, const int* __restrict__ nvec,
                                                           int nmax, int b, int* flag) {
   extern __shared__ double fsm[];
   const int m = blockIdx.x;
   const int n = nvec[m];
   const int bs = b + 1, W = b + 1;
+  const int t = threadIdx.x;   // owns entry d = t of the columns it stages (bs <= blockDim.x)
   double* win = fsm;               // W columns x bs entries
   double* colk = fsm + W * bs;     // L(k+d, k), d = 0..b
   double* A = CB + (size_t)m * nmax * bs;
   double* iv = inv + (size_t)m * nmax;
+  // this thread's first pair (1-based d1, d2 over the b x b square) and the stride in pairs
+  const int t0_d1 = t / b + 1, t0_d2 = t % b + 1;
+  const int st_d1 = (int)blockDim.x / b, st_d2 = (int)blockDim.x % b;
   const int first = min(W, n);
-  for (int t = threadIdx.x; t < first * bs; t += blockDim.x) win[t] = A[t];
+  for (int e = t; e < first * bs; e += blockDim.x) win[e] = A[e];
+  // entering columns are loaded P steps before they are needed
+  double ring[P];
+#pragma unroll
+  for (int u = 0; u < P; ++u) {
+    const int j = W + u;
+    ring[u] = A[(size_t)min(j, n - 1) * bs + min(t, b)];   // clamped: no select on the load
+  }
   __syncthreads();
-  for (int k = 0; k < n; ++k) {
-    const int sk = k % W;
-    if (threadIdx.x == 0) {
-      double piv = win[sk * bs];
-      if (!(piv > 0.0)) {
-        atomicOr(flag, 1);
-        piv = 1.0;
+  for (int k0 = 0; k0 < n; k0 += P) {
+#pragma unroll
+    for (int u = 0; u < P; ++u) {
+      const int k = k0 + u;
+      if (k < n) {
+        const int sk = k % W;
+        if (t == 0) {
+          double piv = win[sk * bs];
+          if (!(piv > 0.0)) {
+            atomicOr(flag, 1);
+            piv = 1.0;
+          }
+          const double il = rsqrt(piv);
+          A[(size_t)k * bs] = piv * il;
+          iv[k] = il * il;
+          colk[0] = il;
+        }
+        __syncthreads();
+        const double il = colk[0];
+        const int dmax = min(b, n - 1 - k);
+        for (int d = 1 + t; d <= b; d += blockDim.x) {
+          double v = 0.0;
+          if (d <= dmax) {
+            v = win[sk * bs + d] * il;           // L(k+d, k)
+            A[(size_t)k * bs + d] = v * il;      // pre-scaled by 1/L(k,k)
+          }
+          colk[d] = v;
+        }
+        __syncthreads();
+        // pairs (d1, d2) of the b x b square, walked with the step's fixed stride (no division)
+        for (int e = 0, d1 = t0_d1, d2 = t0_d2; d1 <= b; e += blockDim.x) {
+          if (d2 <= d1 && d1 <= dmax) {
+            int slot = sk + d2;                  // ring slot of column k + d2
+            if (slot >= W) slot -= W;
+            double* a = win + slot * bs + (d1 - d2);
+            *a = fma(-colk[d1], colk[d2], *a);
+          }
+          d2 += st_d2;
+          d1 += st_d1;
+          if (d2 > b) {
+            d2 -= b;
+            d1 += 1;
+          }
+        }
+        __syncthreads();
+        // the slot of column k is free: store column k + W (untouched so far), prefetch k + W + P
+        if (k + W < n && t < bs) win[sk * bs + t] = ring[u];
+        const int j = k + W + P;
+        ring[u] = A[(size_t)min(j, n - 1) * bs + min(t, b)];
       }
-      const double l = sqrt(piv);
-      A[(size_t)k * bs] = l;
-      iv[k] = 1.0 / piv;
-      colk[0] = 1.0 / l;
     }
-    __syncthreads();
-    const double il = colk[0];
-    const int dmax = min(b, n - 1 - k);
-    for (int d = 1 + threadIdx.x; d <= b; d += blockDim.x) {
-      double v = 0.0;
-      if (d <= dmax) {
-        v = win[sk * bs + d] * il;             // L(k+d, k)
-        A[(size_t)k * bs + d] = v * il;        // pre-scaled by 1/L(k,k)
-      }
-      colk[d] = v;
-    }
-    __syncthreads();
-    const int tot = dmax * dmax;
-    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-      const int d1 = t / dmax + 1, d2 = t % dmax + 1;
-      if (d2 <= d1) win[((k + d2) % W) * bs + (d1 - d2)] -= colk[d1] * colk[d2];
-    }
-    __syncthreads();
-    // the slot of column k is free: bring in column k + W (untouched so far)
-    if (k + W < n)
-      for (int d = threadIdx.x; d < bs; d += blockDim.x) win[sk * bs + d] = A[(size_t)(k + W) * bs + d];
   }
 }
 
@@ -107,7 +136,10 @@ __global__ void __launch_bounds__(1024) k_band_factor(double* CB, double* inv, c
     const int tot = dmax * dmax;
     for (int t = threadIdx.x; t < tot; t += blockDim.x) {
       const int d1 = t / dmax + 1, d2 = t % dmax + 1;
-      if (d2 <= d1) A[(size_t)(k + d2) * bs + (d1 - d2)] -= colk[d1] * colk[d2];
+      if (d2 <= d1) {
+        double* a = A + (size_t)(k + d2) * bs + (d1 - d2);
+        *a = fma(-colk[d1], colk[d2], *a);
+      }
     }
     for (int d = 1 + threadIdx.x; d <= dmax; d += blockDim.x) A[(size_t)k * bs + d] = colk[d] * il;
     __syncthreads();
@@ -158,10 +190,10 @@ static void factor_launch(const Geo&, double* CB, double* RB, double* inv, const
     const int threads = (b * b > 2048) ? 512 : 256;
     static bool attr = false;
     if (!attr) {
-      DD_CUDA(cudaFuncSetAttribute(k_band_factor_win, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+      DD_CUDA(cudaFuncSetAttribute(k_band_factor_win<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
       attr = true;
     }
-    (k_band_factor_win<<<nmat, threads, smem, s>>>(CB, inv, nvec, nmax, b, flag), dd::note_launch());
+    (k_band_factor_win<8><<<nmat, threads, smem, s>>>(CB, inv, nvec, nmax, b, flag), dd::note_launch());
   } else {
     (k_band_factor<<<nmat, 1024, sizeof(double) * (b + 1), s>>>(CB, inv, nvec, nmax, b, flag), dd::note_launch());
   }
@@ -228,63 +260,81 @@ void launch_local_assemble(dd_ctx* c) {
 // FP64 local solves y_i = A_{sigma,i}^{-1} R_i r for every subdomain (one warp each); the
 // result goes to Y[slot(i)][k]; the prolong-sum gathers it.
 // ----------------------------------------------------------------------------------------
-template <int NV, int PF>
-__global__ void k_local_solve(Geo g, const Sub* __restrict__ subs, const int* __restrict__ slot_of,
-                              const double* __restrict__ r, const double* __restrict__ CB,
-                              const double* __restrict__ RB, const double* __restrict__ inv, int nmax, int b,
-                              double* __restrict__ Y, int kpad, const double* __restrict__ wT, double* c0,
-                              const PcgState* st) {
+template <int NV, int PF, int K>
+__global__ void k_local_solve(Geo g, const Sub* __restrict__ subs, const int2* __restrict__ groups, int ngroups,
+                              const int* __restrict__ sub_of_slot, const double* __restrict__ r,
+                              const double* __restrict__ CB, const double* __restrict__ RB,
+                              const double* __restrict__ inv, int nmax, int b, double* __restrict__ Y, int kpad,
+                              const double* __restrict__ wT, double* c0, const PcgState* st) {
   if (st != nullptr && st->done) return;
   extern __shared__ double xs_all[];
   const int wpb = blockDim.x >> 5;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int s = blockIdx.x * wpb + wid;
-  if (s >= g.nsub) return;
-  double* xs = xs_all + (size_t)wid * nmax;
-  const Sub sb = subs[s];
-  // gather R_i r; the coarse right-hand side (D_i R_i psi)^T r rides along (Def. 2.1)
-  double cr = 0.0;
-  const double* wt = wT + (size_t)sb.type * kpad;
-  for (int k = lane; k < sb.nloc; k += 32) {
-    const int sj = k % g.nyi, cc = k / g.nyi;
-    const int c1 = cc / sb.w2, c2 = cc % sb.w2;
-    long long idx;
-    if (g.p == 1) idx = (long long)(sb.lo1 + c1) * g.Ypad + sj;
-    else idx = ((long long)(sb.lo1 + c1) * g.ncx + (sb.lo2 + c2)) * g.Ypad + sj;
-    const double v = r[idx];
-    xs[k] = v;
-    if (c0 != nullptr) cr = fma(wt[k], v, cr);
+  const int gi = blockIdx.x * wpb + wid;
+  if (gi >= ngroups) return;
+  const int2 grp = groups[gi];   // K (or fewer) consecutive slots of one type
+  constexpr int RING = band_ring_doubles<NV, PF>();
+  double* xs = xs_all + (size_t)wid * (K * nmax + RING);
+  double* ring = xs + (size_t)K * nmax;
+  const int type = subs[sub_of_slot[grp.x]].type;
+  int n = 0;
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    double* xj = xs + (size_t)j * nmax;
+    if (j < grp.y) {
+      const int s = sub_of_slot[grp.x + j];
+      const Sub sb = subs[s];
+      n = sb.nloc;
+      // gather R_i r; the coarse right-hand side (D_i R_i psi)^T r rides along (Def. 2.1)
+      double cr = 0.0;
+      const double* wt = wT + (size_t)type * kpad;
+      for (int k = lane; k < sb.nloc; k += 32) {
+        const int sj = k % g.nyi, cc = k / g.nyi;
+        const int c1 = cc / sb.w2, c2 = cc % sb.w2;
+        long long idx;
+        if (g.p == 1) idx = (long long)(sb.lo1 + c1) * g.Ypad + sj;
+        else idx = ((long long)(sb.lo1 + c1) * g.ncx + (sb.lo2 + c2)) * g.Ypad + sj;
+        const double v = r[idx];
+        xj[k] = v;
+        if (c0 != nullptr) cr = fma(wt[k], v, cr);
+      }
+      if (c0 != nullptr) {
+        cr = warp_sum(cr);
+        if (lane == 0) c0[s] = cr;
+      }
+    } else {
+      for (int k = lane; k < nmax; k += 32) xj[k] = 0.0;
+    }
   }
-  if (c0 != nullptr) {
-    cr = warp_sum(cr);
-    if (lane == 0) c0[s] = cr;
+  const size_t off = (size_t)type * nmax;
+  band_solve_k<NV, PF, K>(xs, nmax, n, b, CB + off * (b + 1), RB + off * (b + 1), inv + off, ring);
+  __syncwarp();
+  for (int j = 0; j < grp.y; ++j) {
+    double* y = Y + (size_t)(grp.x + j) * kpad;
+    for (int k = lane; k < n; k += 32) y[k] = xs[(size_t)j * nmax + k];
   }
-  const size_t off = (size_t)sb.type * nmax;
-  band_solve<NV, PF>(xs, sb.nloc, b, CB + off * (b + 1), RB + off * (b + 1), inv + off);
-  double* y = Y + (size_t)slot_of[s] * kpad;
-  for (int k = lane; k < sb.nloc; k += 32) y[k] = xs[k];
-}
-
-static int local_warps_per_block(int nmax) {
-  int w = (int)((200 * 1024) / ((size_t)nmax * sizeof(double)));
-  if (w > 4) w = 4;
-  if (w < 1) w = 1;
-  return w;
 }
 
 void launch_band_solve_local(dd_ctx* c, const double* r, double* c0, cudaStream_t s) {
-  const int wpb = local_warps_per_block(c->nloc_max);
-  const size_t smem = sizeof(double) * (size_t)wpb * c->nloc_max;
-  const int nb = (c->g.nsub + wpb - 1) / wpb;
+  const int K = c->rhs_k;
+  const int wpb = 1;
+  const size_t smem = sizeof(double) * (size_t)K * c->nloc_max + band_ring_bytes(c->band);
+  const int nb = c->ngroups;
   DD_BAND_DISPATCH(c->band, {
-    static bool attr_set = false;
-    if (!attr_set) {
-      DD_CUDA(cudaFuncSetAttribute(k_local_solve<NV, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-      attr_set = true;
-    }
-    (k_local_solve<NV, PF><<<nb, wpb * 32, smem, s>>>(c->g, c->subs, c->slot_of_sub, r, c->bandCB, c->bandRB,
-                                                     c->bandInv, c->nloc_max, c->band, c->Y64, c->kpad, c->wT, c0,
-                                                     c->st), dd::note_launch());
+    DD_K_DISPATCH(K, {
+      constexpr int KK = (NV == 0 || NV > 4) ? 1 : KR;
+      if (K > KK) throw Error(DD_EINVAL, "local right-hand sides per warp exceed the kernel's");
+      static bool attr_set = false;
+      if (!attr_set) {
+        DD_CUDA(cudaFuncSetAttribute(k_local_solve<NV, PF, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     220 * 1024));
+        attr_set = true;
+      }
+      (k_local_solve<NV, PF, KK><<<nb, wpb * 32, smem, s>>>(c->g, c->subs, c->groups, c->ngroups, c->sub_of_slot,
+                                                           r, c->bandCB, c->bandRB, c->bandInv, c->nloc_max,
+                                                           c->band, c->Y64, c->kpad, c->wT, c0, c->st),
+       dd::note_launch());
+    });
   });
   DD_CUDA(cudaGetLastError());
 }
@@ -395,117 +445,162 @@ struct CellOut {
   int iters, status;
 };
 
-constexpr int kCellThreads = 512;   // <= 128 registers per thread (prefetch ring of the band solve)
+constexpr int kCellThreads = 512;
 
-template <int NV, int PF>
-__global__ void __launch_bounds__(kCellThreads, 1) k_cell_iterate(Geo g, const double* __restrict__ tabA, const double* __restrict__ tabM,
-                               const double* __restrict__ CB, const double* __restrict__ RB,
-                               const double* __restrict__ inv, int b, int maxit, double tol_drho, double tol_eta,
-                               int warm, double* psi_out, CellOut* out) {
-  extern __shared__ double sm[];
-  const int ncol = (g.p == 1) ? g.n : g.n * g.n;
-  const int ncell = ncol * g.nyi;
-  double* x = sm;
-  double* y = sm + ncell;
-  double* xs = sm + 2 * ncell;
-  // start from 1, or from psi_out (warm start of the refined shift)
-  for (int k = threadIdx.x; k < ncell; k += blockDim.x) x[k] = warm ? psi_out[k] : 1.0;
-  __syncthreads();
-  double rho_prev = 1e300, eta_prev = 1e300;
-  int it = 0, stable = 0, status = 0;
-  double eta = 0.0, drho = 0.0, rho = 0.0;
-  for (it = 1; it <= maxit; ++it) {
-    // y = M x ; permute into interleaved order
-    cell_stencil(g, tabM, x, y, ncell);
-    __syncthreads();
-    for (int k = threadIdx.x; k < ncell; k += blockDim.x) {
-      const int sj = k % g.nyi, cc = k / g.nyi;
-      int ri;
-      if (g.p == 1) ri = ipos(cc, g.n) * g.nyi + sj;
-      else ri = (ipos(cc / g.n, g.n) * g.n + ipos(cc % g.n, g.n)) * g.nyi + sj;
-      xs[ri] = y[k];
+// ---- cell inverse iteration on a dense inverse -------------------------------------------
+// G = (A_# - s M_#)^{-1} is formed once per shift from the band factor (every column an
+// independent band solve, one warp each, all in parallel) and permuted to the natural cell
+// order; each inverse-iteration step is then y = M_# x (stencil), w = G y (a GEMV across the
+// GPU) and one CTA that normalises, forms rho and eta and applies the stop rule.  The state
+// lives on the device; the host reads it every few steps.
+struct CellState {
+  double rho, rho_prev, eta, eta_prev, drho;
+  int iters, stable, done, status;
+};
+
+__global__ void k_cell_perm_dense(Geo g, int ncell, const double* __restrict__ Gi, double* __restrict__ Gn) {
+  // Gn[i][j] = Gi[pos(i)][pos(j)], natural index k = (a1 [n + a2]) nyi + sj
+  const long long total = (long long)ncell * ncell;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t / ncell), j = (int)(t % ncell);
+    int pi, pj;
+    {
+      const int sj = i % g.nyi, cc = i / g.nyi;
+      pi = (g.p == 1) ? ipos(cc, g.n) * g.nyi + sj : (ipos(cc / g.n, g.n) * g.n + ipos(cc % g.n, g.n)) * g.nyi + sj;
     }
-    __syncthreads();
-    if (threadIdx.x < 32) band_solve<NV, PF>(xs, ncell, b, CB, RB, inv);
-    __syncthreads();
-    // w (natural order) -> x
-    for (int k = threadIdx.x; k < ncell; k += blockDim.x) {
-      const int sj = k % g.nyi, cc = k / g.nyi;
-      int ri;
-      if (g.p == 1) ri = ipos(cc, g.n) * g.nyi + sj;
-      else ri = (ipos(cc / g.n, g.n) * g.n + ipos(cc % g.n, g.n)) * g.nyi + sj;
-      x[k] = xs[ri];
+    {
+      const int sj = j % g.nyi, cc = j / g.nyi;
+      pj = (g.p == 1) ? ipos(cc, g.n) * g.nyi + sj : (ipos(cc / g.n, g.n) * g.n + ipos(cc % g.n, g.n)) * g.nyi + sj;
     }
-    __syncthreads();
-    // normalise: x = w / ||w||_M, sign so that sum x > 0
-    cell_stencil(g, tabM, x, y, ncell);
-    __syncthreads();
-    double d2[2] = {0.0, 0.0};
-    for (int k = threadIdx.x; k < ncell; k += blockDim.x) {
-      d2[0] = fma(x[k], y[k], d2[0]);
-      d2[1] += x[k];
-    }
-    cta_sum<2>(d2);
-    if (!(d2[0] > 0.0)) { status = DD_ENAN; break; }
-    const double sc = (d2[1] < 0.0 ? -1.0 : 1.0) / sqrt(d2[0]);
-    for (int k = threadIdx.x; k < ncell; k += blockDim.x) {
-      x[k] *= sc;
-      y[k] *= sc;   // y = M x
-    }
-    __syncthreads();
-    // rho = x^T A x, residual A x - rho M x
-    cell_stencil(g, tabA, x, xs, ncell);
-    __syncthreads();
-    double d1[1] = {0.0};
-    for (int k = threadIdx.x; k < ncell; k += blockDim.x) d1[0] = fma(x[k], xs[k], d1[0]);
-    cta_sum<1>(d1);
-    rho = d1[0];
-    double d3[2] = {0.0, 0.0};
-    for (int k = threadIdx.x; k < ncell; k += blockDim.x) {
-      const double e = fma(-rho, y[k], xs[k]);
-      d3[0] = fma(e, e, d3[0]);
-      d3[1] = fma(y[k], y[k], d3[1]);
-    }
-    cta_sum<2>(d3);
-    eta = sqrt(d3[0] / d3[1]) / fabs(rho);
-    drho = fabs(rho - rho_prev);
-    if (!isfinite(rho)) { status = DD_ENAN; break; }
-    // at the residual target, stop once the Rayleigh quotient is stationary or the residual
-    // no longer improves (its rounding floor, which grows as the shift nears sigma_1)
-    if (eta <= tol_eta && (drho <= tol_drho * fabs(rho) || eta >= 0.5 * eta_prev)) {
-      if (++stable >= 2) break;
-    } else {
-      stable = 0;
-    }
-    eta_prev = eta;
-    rho_prev = rho;
-  }
-  for (int k = threadIdx.x; k < ncell; k += blockDim.x) psi_out[k] = x[k];
-  if (threadIdx.x == 0) {
-    out->sigma = rho;
-    out->eta = eta;
-    out->drho = drho;
-    out->iters = it > maxit ? maxit : it;
-    out->status = (status == 0 && it > maxit) ? DD_EMAXIT : status;
+    Gn[t] = Gi[(size_t)pi * ncell + pj];
   }
 }
 
-// one phase of the cell solve: assemble A_# - s M_#, factor, iterate; returns false if the
-// factorisation met a non-positive pivot (s not below sigma_1)
+// y = M_# x over the cell, grid-wide
+__global__ void k_cell_mass(Geo g, int ncell, const double* __restrict__ tabM, const double* __restrict__ x,
+                            double* __restrict__ y, const CellState* cs) {
+  if (cs->done) return;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ncell; k += gridDim.x * blockDim.x) {
+    const int sj = k % g.nyi, cc = k / g.nyi;
+    int a1, a2 = 0, cls;
+    if (g.p == 1) { a1 = cc; cls = a1 * g.Ypad + sj; }
+    else { a1 = cc / g.n; a2 = cc % g.n; cls = (a1 * g.n + a2) * g.Ypad + sj; }
+    double acc = 0.0;
+    for (int tap = 0; tap < g.ntap; ++tap) {
+      int d1, d2 = 0, dy;
+      if (g.p == 1) { d1 = tap / 3 - 1; dy = tap % 3 - 1; }
+      else { d1 = tap / 9 - 1; d2 = (tap / 3) % 3 - 1; dy = tap % 3 - 1; }
+      const int nj = sj + dy;
+      if (nj < 0 || nj >= g.nyi) continue;
+      const int b1 = (a1 + d1 + g.n) % g.n;
+      const int kk = (g.p == 1) ? b1 * g.nyi + nj : (b1 * g.n + (a2 + d2 + g.n) % g.n) * g.nyi + nj;
+      acc = fma(__ldg(tabM + (size_t)tap * g.ncls + cls), x[kk], acc);
+    }
+    y[k] = acc;
+  }
+}
+
+// w = G y, warp per row
+__global__ void k_cell_gemv(int n, const double* __restrict__ G, const double* __restrict__ y, double* __restrict__ w,
+                            const CellState* cs) {
+  if (cs->done) return;
+  const int lane = threadIdx.x & 31;
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= n) return;
+  const double* gr = G + (size_t)row * n;
+  double acc = 0.0;
+  for (int k = lane; k < n; k += 32) acc = fma(gr[k], y[k], acc);
+  acc = warp_sum(acc);
+  if (lane == 0) w[row] = acc;
+}
+
+// x = w / ||w||_M (sign: sum > 0), rho = x^T A_# x, eta = ||A x - rho M x|| / (|rho| ||M x||), stop rule
+__global__ void __launch_bounds__(kCellThreads) k_cell_update(Geo g, int ncell, const double* __restrict__ tabA,
+                                                             const double* __restrict__ tabM, const double* w,
+                                                             double* x, double tol_drho, double tol_eta, int maxit,
+                                                             CellState* cs) {
+  if (cs->done) return;
+  extern __shared__ double sm[];
+  double* xs = sm;            // w, then x
+  double* ys = sm + ncell;    // M x
+  double* zs = sm + 2 * ncell;
+  for (int k = threadIdx.x; k < ncell; k += blockDim.x) xs[k] = w[k];
+  __syncthreads();
+  cell_stencil(g, tabM, xs, ys, ncell);
+  __syncthreads();
+  double d2[2] = {0.0, 0.0};
+  for (int k = threadIdx.x; k < ncell; k += blockDim.x) {
+    d2[0] = fma(xs[k], ys[k], d2[0]);
+    d2[1] += xs[k];
+  }
+  cta_sum<2>(d2);
+  if (!(d2[0] > 0.0)) {
+    if (threadIdx.x == 0) { cs->status = DD_ENAN; cs->done = 1; }
+    return;
+  }
+  const double sc = (d2[1] < 0.0 ? -1.0 : 1.0) / sqrt(d2[0]);
+  for (int k = threadIdx.x; k < ncell; k += blockDim.x) {
+    xs[k] *= sc;
+    ys[k] *= sc;
+  }
+  __syncthreads();
+  cell_stencil(g, tabA, xs, zs, ncell);
+  __syncthreads();
+  double d1[1] = {0.0};
+  for (int k = threadIdx.x; k < ncell; k += blockDim.x) d1[0] = fma(xs[k], zs[k], d1[0]);
+  cta_sum<1>(d1);
+  const double rho = d1[0];
+  double d3[2] = {0.0, 0.0};
+  for (int k = threadIdx.x; k < ncell; k += blockDim.x) {
+    const double e = fma(-rho, ys[k], zs[k]);
+    d3[0] = fma(e, e, d3[0]);
+    d3[1] = fma(ys[k], ys[k], d3[1]);
+  }
+  cta_sum<2>(d3);
+  for (int k = threadIdx.x; k < ncell; k += blockDim.x) x[k] = xs[k];
+  if (threadIdx.x == 0) {
+    const double eta = sqrt(d3[0] / d3[1]) / fabs(rho);
+    const double drho = fabs(rho - cs->rho_prev);
+    cs->iters += 1;
+    cs->rho = rho;
+    cs->eta = eta;
+    cs->drho = drho;
+    if (!isfinite(rho)) {
+      cs->status = DD_ENAN;
+      cs->done = 1;
+    } else {
+      // at the residual target, stop once the Rayleigh quotient is stationary or the residual
+      // no longer improves (its rounding floor grows as the shift nears sigma_1)
+      if (eta <= tol_eta && (drho <= tol_drho * fabs(rho) || eta >= 0.5 * cs->eta_prev)) cs->stable += 1;
+      else cs->stable = 0;
+      if (cs->stable >= 2) cs->done = 1;
+      else if (cs->iters >= maxit) {
+        cs->status = DD_EMAXIT;
+        cs->done = 1;
+      }
+    }
+    cs->eta_prev = eta;
+    cs->rho_prev = rho;
+  }
+}
+
+// one phase of the cell solve: assemble A_# - s M_#, factor, invert, iterate; returns false
+// if the factorisation met a non-positive pivot (s not below sigma_1)
 static bool cell_phase(dd_ctx* c, double* shift, bool from_minV, double margin_frac, int warm, double tol_drho,
                        double tol_eta, int maxit, CellOut* out_h) {
   const Geo& g = c->g;
   const int ncell = (int)c->ncell;
   const int b = c->cell_band;
   const size_t cbsz = sizeof(double) * (size_t)ncell * (b + 1);
-  double *CB = nullptr, *RB = nullptr, *inv = nullptr;
-  CellOut* out = nullptr;
+  const size_t gsz = sizeof(double) * (size_t)ncell * ncell;
+  double *CB = nullptr, *RB = nullptr, *inv = nullptr, *Gi = nullptr, *Gn = nullptr, *y = nullptr, *w = nullptr;
+  CellState* cs = nullptr;
   int* flag = c->dev_err + 1;
   int* nvec = nullptr;
   DD_CUDA(cudaMallocAsync(&CB, cbsz, c->stream));
   DD_CUDA(cudaMallocAsync(&RB, cbsz, c->stream));
   DD_CUDA(cudaMallocAsync(&inv, sizeof(double) * ncell, c->stream));
-  DD_CUDA(cudaMallocAsync(&out, sizeof(CellOut), c->stream));
   DD_CUDA(cudaMallocAsync(&nvec, sizeof(int), c->stream));
   DD_CUDA(cudaMemsetAsync(CB, 0, cbsz, c->stream));
   DD_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), c->stream));
@@ -526,23 +621,58 @@ static bool cell_phase(dd_ctx* c, double* shift, bool from_minV, double margin_f
   DD_CUDA(cudaStreamSynchronize(c->stream));
   bool ok = (fl == 0);
   if (ok) {
+    DD_CUDA(cudaMallocAsync(&Gi, gsz, c->stream));
+    DD_CUDA(cudaMallocAsync(&Gn, gsz, c->stream));
+    DD_CUDA(cudaMallocAsync(&y, sizeof(double) * ncell, c->stream));
+    DD_CUDA(cudaMallocAsync(&w, sizeof(double) * ncell, c->stream));
+    DD_CUDA(cudaMallocAsync(&cs, sizeof(CellState), c->stream));
+    launch_band_inverse_rows(ncell, b, CB, RB, inv, Gi, c->stream);
+    (k_cell_perm_dense<<<grid_blocks((long long)ncell * ncell, kThreads), kThreads, 0, c->stream>>>(g, ncell, Gi, Gn),
+     dd::note_launch());
+    CellState init{};
+    init.rho_prev = 1e300;
+    init.eta_prev = 1e300;
+    DD_CUDA(cudaMemcpyAsync(cs, &init, sizeof(init), cudaMemcpyHostToDevice, c->stream));
+    if (!warm) {
+      std::vector<double> ones((size_t)ncell, 1.0);
+      DD_CUDA(cudaMemcpyAsync(c->psi_cell, ones.data(), sizeof(double) * ncell, cudaMemcpyHostToDevice, c->stream));
+      DD_CUDA(cudaStreamSynchronize(c->stream));
+    }
     const size_t smem = sizeof(double) * 3 * (size_t)ncell;
-    DD_BAND_DISPATCH(b, {
-      DD_CUDA(cudaFuncSetAttribute(k_cell_iterate<NV, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      (k_cell_iterate<NV, PF><<<1, kCellThreads, smem, c->stream>>>(g, c->tabA, c->tabM, CB, RB, inv, b, maxit, tol_drho,
-                                                           tol_eta, warm, c->psi_cell, out), dd::note_launch());
-    });
-    DD_CUDA(cudaGetLastError());
-    DD_CUDA(cudaMemcpyAsync(out_h, out, sizeof(CellOut), cudaMemcpyDeviceToHost, c->stream));
+    DD_CUDA(cudaFuncSetAttribute(k_cell_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int gemv_blocks = (ncell + 7) / 8;
+    CellState h{};
+    for (int it = 0; it < maxit; it += 4) {
+      for (int k = 0; k < 4; ++k) {
+        (k_cell_mass<<<grid_blocks(ncell, 256), 256, 0, c->stream>>>(g, ncell, c->tabM, c->psi_cell, y, cs),
+         dd::note_launch());
+        (k_cell_gemv<<<gemv_blocks, 256, 0, c->stream>>>(ncell, Gn, y, w, cs), dd::note_launch());
+        (k_cell_update<<<1, kCellThreads, smem, c->stream>>>(g, ncell, c->tabA, c->tabM, w, c->psi_cell, tol_drho,
+                                                           tol_eta, maxit, cs), dd::note_launch());
+      }
+      DD_CUDA(cudaGetLastError());
+      DD_CUDA(cudaMemcpyAsync(&h, cs, sizeof(CellState), cudaMemcpyDeviceToHost, c->stream));
+      DD_CUDA(cudaStreamSynchronize(c->stream));
+      if (h.done) break;
+    }
     double sh = 0.0;
     DD_CUDA(cudaMemcpyAsync(&sh, shift, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     DD_CUDA(cudaStreamSynchronize(c->stream));
+    out_h->sigma = h.rho;
+    out_h->eta = h.eta;
+    out_h->drho = h.drho;
+    out_h->iters = h.iters;
+    out_h->status = h.done ? h.status : DD_EMAXIT;
     out_h->shift = sh;
+    DD_CUDA(cudaFreeAsync(Gi, c->stream));
+    DD_CUDA(cudaFreeAsync(Gn, c->stream));
+    DD_CUDA(cudaFreeAsync(y, c->stream));
+    DD_CUDA(cudaFreeAsync(w, c->stream));
+    DD_CUDA(cudaFreeAsync(cs, c->stream));
   }
   DD_CUDA(cudaFreeAsync(CB, c->stream));
   DD_CUDA(cudaFreeAsync(RB, c->stream));
   DD_CUDA(cudaFreeAsync(inv, c->stream));
-  DD_CUDA(cudaFreeAsync(out, c->stream));
   DD_CUDA(cudaFreeAsync(nvec, c->stream));
   DD_CUDA(cudaStreamSynchronize(c->stream));
   return ok;

@@ -265,18 +265,43 @@ __global__ void __launch_bounds__(1024) k_cr_solve(const double* __restrict__ cr
   for (int j = threadIdx.x; j < N; j += blockDim.x) x[j] = f[j + 1];
 }
 
-// p = 2: dense inverse rows from the banded factor (identity right-hand sides)
-template <int NV, int PF>
+// dense inverse rows from the banded factor (identity right-hand sides, K per warp)
+template <int NV, int PF, int K>
 __global__ void k_band_inverse_rows(int n, int b, const double* __restrict__ CB, const double* __restrict__ RB,
                                     const double* __restrict__ inv, double* out) {
   extern __shared__ double xs_all[];
   const int wpb = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int col = blockIdx.x * wpb + wid;
-  if (col >= n) return;
-  double* xs = xs_all + (size_t)wid * n;
-  for (int k = lane; k < n; k += 32) xs[k] = (k == col) ? 1.0 : 0.0;
-  band_solve<NV, PF>(xs, n, b, CB, RB, inv);
-  for (int k = lane; k < n; k += 32) out[(size_t)col * n + k] = xs[k];
+  const int col0 = (blockIdx.x * wpb + wid) * K;
+  if (col0 >= n) return;
+  constexpr int RING = band_ring_doubles<NV, PF>();
+  double* xs = xs_all + (size_t)wid * (K * n + RING);
+  double* ring = xs + (size_t)K * n;
+#pragma unroll
+  for (int j = 0; j < K; ++j)
+    for (int k = lane; k < n; k += 32) xs[(size_t)j * n + k] = (k == col0 + j) ? 1.0 : 0.0;
+  band_solve_k<NV, PF, K>(xs, n, n, b, CB, RB, inv, ring);
+  __syncwarp();
+  for (int j = 0; j < K && col0 + j < n; ++j)
+    for (int k = lane; k < n; k += 32) out[(size_t)(col0 + j) * n + k] = xs[(size_t)j * n + k];
+}
+
+void launch_band_inverse_rows(int n, int b, const double* CB, const double* RB, const double* inv, double* out,
+                              cudaStream_t s) {
+  const int K = 1;
+  const size_t per = sizeof(double) * (size_t)K * n + band_ring_bytes(b);
+  const int wpb = per <= 48 * 1024 ? 2 : 1;
+  const size_t smem = per * wpb;
+  const int ncolgroups = (n + K - 1) / K;
+  DD_BAND_DISPATCH(b, {
+    {
+      constexpr int KK = 1;
+      DD_CUDA(cudaFuncSetAttribute(k_band_inverse_rows<NV, PF, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   220 * 1024));
+      (k_band_inverse_rows<NV, PF, KK><<<(ncolgroups + wpb - 1) / wpb, 32 * wpb, smem, s>>>(n, b, CB, RB, inv, out),
+       dd::note_launch());
+    }
+  });
+  DD_CUDA(cudaGetLastError());
 }
 
 __global__ void k_gemv_rows(int n, const double* __restrict__ A, const double* __restrict__ xin,
@@ -330,15 +355,7 @@ int coarse_factor(dd_ctx* c) {
     DD_CUDA(cudaMemcpyAsync(CB, hcb.data(), cb, cudaMemcpyHostToDevice, c->stream));
     launch_band_factor(c, CB, RB, inv, 1, N, b, flag);
     c->A0inv = (double*)dev_alloc(c, sizeof(double) * (size_t)N * N);
-    const int wpb = (N * 8 <= 48 * 1024) ? 4 : 1;
-    const size_t smem = sizeof(double) * (size_t)wpb * N;
-    DD_BAND_DISPATCH(b, {
-      DD_CUDA(cudaFuncSetAttribute(k_band_inverse_rows<NV, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   220 * 1024));
-      (k_band_inverse_rows<NV, PF><<<(N + wpb - 1) / wpb, 32 * wpb, smem, c->stream>>>(N, b, CB, RB, inv, c->A0inv),
-       dd::note_launch());
-    });
-    DD_CUDA(cudaGetLastError());
+    launch_band_inverse_rows(N, b, CB, RB, inv, c->A0inv, c->stream);
   }
   int fl = 0;
   DD_CUDA(cudaMemcpyAsync(&fl, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));

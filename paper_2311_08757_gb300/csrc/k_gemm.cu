@@ -292,23 +292,32 @@ __device__ __forceinline__ float round_fast<float>(double v) {
   return f64_to_tf32(v);
 }
 
-template <typename T, int NV, int PF>
+template <typename T, int NV, int PF, int K>
 __global__ void k_local_inverse(const int* __restrict__ nloc, int nmax, int b, const double* __restrict__ CB,
                                 const double* __restrict__ RB, const double* __restrict__ inv, int ntypes, int kpad,
                                 T* __restrict__ out) {
   extern __shared__ double xs_all[];
   const int wpb = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int groups_per_type = (nmax + K - 1) / K;
   const long long job = (long long)blockIdx.x * wpb + wid;
-  if (job >= (long long)ntypes * nmax) return;
-  const int ty = (int)(job / nmax), col = (int)(job % nmax);
+  if (job >= (long long)ntypes * groups_per_type) return;
+  const int ty = (int)(job / groups_per_type);
+  const int col0 = (int)(job % groups_per_type) * K;
   const int n = nloc[ty];
-  if (col >= n) return;
-  double* xs = xs_all + (size_t)wid * nmax;
-  for (int k = lane; k < n; k += 32) xs[k] = (k == col) ? 1.0 : 0.0;
+  if (col0 >= n) return;
+  constexpr int RING = band_ring_doubles<NV, PF>();
+  double* xs = xs_all + (size_t)wid * (K * nmax + RING);
+  double* ring = xs + (size_t)K * nmax;
+#pragma unroll
+  for (int j = 0; j < K; ++j)
+    for (int k = lane; k < n; k += 32) xs[(size_t)j * nmax + k] = (k == col0 + j) ? 1.0 : 0.0;
   const size_t off = (size_t)ty * nmax;
-  band_solve<NV, PF>(xs, n, b, CB + off * (b + 1), RB + off * (b + 1), inv + off);
-  T* row = out + ((size_t)ty * kpad + col) * kpad;
-  for (int k = lane; k < n; k += 32) row[k] = round_fast<T>(xs[k]);
+  band_solve_k<NV, PF, K>(xs, nmax, n, b, CB + off * (b + 1), RB + off * (b + 1), inv + off, ring);
+  __syncwarp();
+  for (int j = 0; j < K && col0 + j < n; ++j) {
+    T* row = out + ((size_t)ty * kpad + col0 + j) * kpad;
+    for (int k = lane; k < n; k += 32) row[k] = round_fast<T>(xs[(size_t)j * nmax + k]);
+  }
 }
 
 // R_i r rounded, subdomain rows in type-sorted order, zero tail up to kpad; the coarse
@@ -367,24 +376,28 @@ int gemm_setup(dd_ctx* c) {
   int* nloc = nullptr;
   DD_CUDA(cudaMallocAsync(&nloc, sizeof(int) * c->ntypes, c->stream));
   DD_CUDA(cudaMemcpyAsync(nloc, c->type_nloc, sizeof(int) * c->ntypes, cudaMemcpyHostToDevice, c->stream));
-  int wpb = (int)((200 * 1024) / ((size_t)c->nloc_max * sizeof(double)));
-  wpb = wpb > 8 ? 8 : (wpb < 1 ? 1 : wpb);
-  const size_t smem = sizeof(double) * (size_t)wpb * c->nloc_max;
-  const long long jobs = (long long)c->ntypes * c->nloc_max;
+  const int K = 1;
+  const size_t per = sizeof(double) * (size_t)K * c->nloc_max + band_ring_bytes(c->band);
+  const int wpb = per <= 48 * 1024 ? 2 : 1;
+  const size_t smem = per * wpb;
+  const long long jobs = (long long)c->ntypes * ((c->nloc_max + K - 1) / K);
   const int nb = (int)((jobs + wpb - 1) / wpb);
   DD_BAND_DISPATCH(c->band, {
-    if (bf16) {
-      DD_CUDA(cudaFuncSetAttribute(k_local_inverse<__nv_bfloat16, NV, PF>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-      (k_local_inverse<__nv_bfloat16, NV, PF><<<nb, 32 * wpb, smem, c->stream>>>(
-           nloc, c->nloc_max, c->band, c->bandCB, c->bandRB, c->bandInv, c->ntypes, kpad, (__nv_bfloat16*)c->Ainv),
-       dd::note_launch());
-    } else {
-      DD_CUDA(cudaFuncSetAttribute(k_local_inverse<float, NV, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   220 * 1024));
-      (k_local_inverse<float, NV, PF><<<nb, 32 * wpb, smem, c->stream>>>(
-           nloc, c->nloc_max, c->band, c->bandCB, c->bandRB, c->bandInv, c->ntypes, kpad, (float*)c->Ainv),
-       dd::note_launch());
+    {
+      constexpr int KK = 1;
+      if (bf16) {
+        DD_CUDA(cudaFuncSetAttribute(k_local_inverse<__nv_bfloat16, NV, PF, KK>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+        (k_local_inverse<__nv_bfloat16, NV, PF, KK><<<nb, 32 * wpb, smem, c->stream>>>(
+             nloc, c->nloc_max, c->band, c->bandCB, c->bandRB, c->bandInv, c->ntypes, kpad, (__nv_bfloat16*)c->Ainv),
+         dd::note_launch());
+      } else {
+        DD_CUDA(cudaFuncSetAttribute(k_local_inverse<float, NV, PF, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     220 * 1024));
+        (k_local_inverse<float, NV, PF, KK><<<nb, 32 * wpb, smem, c->stream>>>(
+             nloc, c->nloc_max, c->band, c->bandCB, c->bandRB, c->bandInv, c->ntypes, kpad, (float*)c->Ainv),
+         dd::note_launch());
+      }
     }
   });
   DD_CUDA(cudaGetLastError());

@@ -1,0 +1,237 @@
+// SI-LOPCG outer step (Algorithm 1): Gram matrices of the search space S = [x_k, w_k, x_{k-1}]
+// under A_sigma and M, the orthogonalised Rayleigh-Ritz step on them, and the update
+// x_{k+1} = S c.  All three vectors, their A_sigma- and M-images are read in one pass; the
+// 3 x 3 Rayleigh-Ritz problem is solved by the last block of that pass, so the coefficients
+// never leave the device.
+#include "dd_common.cuh"
+
+namespace dd {
+
+namespace {
+
+// index of the upper-triangular entry (i, j), i <= j, of a symmetric 3 x 3 matrix
+__device__ __forceinline__ int sym3(int i, int j) {
+  if (i > j) {
+    const int t = i;
+    i = j;
+    j = t;
+  }
+  return i == 0 ? j : (i == 1 ? 2 + j : 5);
+}
+
+// Lowest eigenpair of the symmetric m x m matrix H (m <= 3, row-major 3 x 3 storage) by
+// cyclic Jacobi rotations (symmetric Schur decompositions of 2 x 2 blocks).
+__device__ void jacobi_lowest(double H[3][3], int m, double* theta, double y[3]) {
+  double V[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  for (int sweep = 0; sweep < 50; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < m; ++p)
+      for (int q = p + 1; q < m; ++q) off += H[p][q] * H[p][q];
+    if (off == 0.0) break;
+    for (int p = 0; p < m; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        if (H[p][q] == 0.0) continue;
+        const double tau = (H[q][q] - H[p][p]) / (2.0 * H[p][q]);
+        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        const double cs = 1.0 / sqrt(1.0 + t * t), sn = t * cs;
+        for (int k = 0; k < m; ++k) {   // H <- H J
+          const double hp = H[k][p], hq = H[k][q];
+          H[k][p] = cs * hp - sn * hq;
+          H[k][q] = sn * hp + cs * hq;
+        }
+        for (int k = 0; k < m; ++k) {   // H <- J^T H
+          const double hp = H[p][k], hq = H[q][k];
+          H[p][k] = cs * hp - sn * hq;
+          H[q][k] = sn * hp + cs * hq;
+        }
+        for (int k = 0; k < m; ++k) {   // V <- V J
+          const double vp = V[k][p], vq = V[k][q];
+          V[k][p] = cs * vp - sn * vq;
+          V[k][q] = sn * vp + cs * vq;
+        }
+      }
+  }
+  int lo = 0;
+  for (int k = 1; k < m; ++k)
+    if (H[k][k] < H[lo][lo]) lo = k;
+  *theta = H[lo][lo];
+  for (int k = 0; k < 3; ++k) y[k] = (k < m) ? V[k][lo] : 0.0;
+}
+
+// Orthogonalised Rayleigh-Ritz on span{x_k, w_k, x_{k-1}} from the Gram matrices (Algorithm 1):
+// Gram-Schmidt in the M inner product on coefficient vectors (order x_k, w_k, x_{k-1}, two
+// passes; a direction whose M-norm falls to drop times its norm before is dropped), lowest
+// eigenpair of the projected matrix, coefficients signed so that the sum of the Ritz vector
+// is positive.
+__device__ void rayleigh_ritz3(LopState* ls, double drop) {
+  double GA[3][3], GB[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      GA[i][j] = ls->GA[sym3(i, j)];
+      GB[i][j] = ls->GB[sym3(i, j)];
+    }
+  double T[3][3];   // columns: accepted coefficient vectors
+  int m = 0;
+  for (int i = 0; i < 3; ++i) {
+    double v[3] = {0.0, 0.0, 0.0};
+    v[i] = 1.0;
+    const double n0 = GB[i][i];
+    for (int pass = 0; pass < 2; ++pass)
+      for (int k = 0; k < m; ++k) {
+        double gv[3];
+        for (int a = 0; a < 3; ++a) gv[a] = GB[a][0] * v[0] + GB[a][1] * v[1] + GB[a][2] * v[2];
+        const double pr = T[0][k] * gv[0] + T[1][k] * gv[1] + T[2][k] * gv[2];
+        for (int a = 0; a < 3; ++a) v[a] -= pr * T[a][k];
+      }
+    double gv[3];
+    for (int a = 0; a < 3; ++a) gv[a] = GB[a][0] * v[0] + GB[a][1] * v[1] + GB[a][2] * v[2];
+    const double nrm2 = v[0] * gv[0] + v[1] * gv[1] + v[2] * gv[2];
+    if (n0 > 0.0 && nrm2 > drop * drop * n0) {
+      const double s = 1.0 / sqrt(nrm2);
+      for (int a = 0; a < 3; ++a) T[a][m] = v[a] * s;
+      ++m;
+    }
+  }
+  if (m == 0) {
+    ls->status = DD_ENOTSPD;
+    ls->c[0] = 1.0;
+    ls->c[1] = ls->c[2] = 0.0;
+    return;
+  }
+  double H[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  for (int p = 0; p < m; ++p)
+    for (int q = 0; q < m; ++q) {
+      double acc = 0.0;
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) acc += T[a][p] * GA[a][b] * T[b][q];
+      H[p][q] = acc;
+    }
+  for (int p = 0; p < m; ++p)
+    for (int q = p + 1; q < m; ++q) H[p][q] = H[q][p] = 0.5 * (H[p][q] + H[q][p]);
+  double theta, y[3];
+  jacobi_lowest(H, m, &theta, y);
+  double c[3];
+  for (int a = 0; a < 3; ++a) {
+    c[a] = 0.0;
+    for (int k = 0; k < m; ++k) c[a] += T[a][k] * y[k];
+  }
+  const double sg = ls->sums[0] * c[0] + ls->sums[1] * c[1] + ls->sums[2] * c[2];
+  if (sg < 0.0)
+    for (int a = 0; a < 3; ++a) c[a] = -c[a];
+  for (int a = 0; a < 3; ++a) ls->c[a] = c[a];
+  ls->theta = theta;
+  ls->m = m;
+  if (!isfinite(theta)) ls->status = DD_ENAN;
+}
+
+}  // namespace
+
+// Gram matrices (upper triangles) of S = [x, w, xp] under A_sigma and M, and the sums of the
+// three vectors; then the Rayleigh-Ritz step in the last block.
+__global__ void __launch_bounds__(kThreads) k_lop_gram(long long n, const double* __restrict__ x,
+                                                       const double* __restrict__ w, const double* __restrict__ xp,
+                                                       const double* __restrict__ Ax, const double* __restrict__ Aw,
+                                                       const double* __restrict__ Axp, const double* __restrict__ Mx,
+                                                       const double* __restrict__ Mw, const double* __restrict__ Mxp,
+                                                       LopState* ls, double* partials, unsigned* counter,
+                                                       double drop) {
+  double acc[15];
+#pragma unroll
+  for (int k = 0; k < 15; ++k) acc[k] = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const double s0 = x[t], s1 = w[t], s2 = xp[t];
+    const double a0 = Ax[t], a1 = Aw[t], a2 = Axp[t];
+    const double m0 = Mx[t], m1 = Mw[t], m2 = Mxp[t];
+    acc[0] = fma(s0, a0, acc[0]);
+    acc[1] = fma(s0, a1, acc[1]);
+    acc[2] = fma(s0, a2, acc[2]);
+    acc[3] = fma(s1, a1, acc[3]);
+    acc[4] = fma(s1, a2, acc[4]);
+    acc[5] = fma(s2, a2, acc[5]);
+    acc[6] = fma(s0, m0, acc[6]);
+    acc[7] = fma(s0, m1, acc[7]);
+    acc[8] = fma(s0, m2, acc[8]);
+    acc[9] = fma(s1, m1, acc[9]);
+    acc[10] = fma(s1, m2, acc[10]);
+    acc[11] = fma(s2, m2, acc[11]);
+    acc[12] += s0;
+    acc[13] += s1;
+    acc[14] += s2;
+  }
+  double tot[15];
+  if (grid_sum_last<15>(acc, partials, counter, tot) && threadIdx.x == 0) {
+    for (int k = 0; k < 6; ++k) {
+      ls->GA[k] = tot[k];
+      ls->GB[k] = tot[6 + k];
+    }
+    for (int k = 0; k < 3; ++k) ls->sums[k] = tot[12 + k];
+    ls->status = 0;
+    bool finite = true;
+    for (int k = 0; k < 15; ++k) finite = finite && isfinite(tot[k]);
+    if (!finite) {
+      ls->status = DD_ENAN;
+      ls->c[0] = 1.0;
+      ls->c[1] = ls->c[2] = 0.0;
+    } else {
+      rayleigh_ritz3(ls, drop);
+    }
+  }
+}
+
+// out = c0 x + c1 w + c2 xp (out distinct from the inputs)
+__global__ void __launch_bounds__(kThreads) k_lop_update(long long n, const double* __restrict__ x,
+                                                         const double* __restrict__ w,
+                                                         const double* __restrict__ xp, double* __restrict__ out,
+                                                         const LopState* __restrict__ ls) {
+  const double c0 = ls->c[0], c1 = ls->c[1], c2 = ls->c[2];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    out[t] = fma(c2, xp[t], fma(c1, w[t], c0 * x[t]));
+}
+
+// in-place scaling x *= s, Mx *= s with s = os->scale (set by the normalisation dots)
+__global__ void __launch_bounds__(kThreads) k_lop_scale(long long n, double* x, double* Mx, const OuterState* os) {
+  const double s = os->scale;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    x[t] *= s;
+    Mx[t] *= s;
+  }
+}
+
+__global__ void k_set_entry(double* v, long long idx, double val) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) v[idx] = val;
+}
+
+void launch_lop_gram(dd_ctx* c, const double* const S[3], const double* const AS[3], const double* const MS[3],
+                     double drop, cudaStream_t s) {
+  const long long n = c->g.plen;
+  const int nb = grid_blocks(n, kThreads);
+  (k_lop_gram<<<nb, kThreads, 0, s>>>(n, S[0], S[1], S[2], AS[0], AS[1], AS[2], MS[0], MS[1], MS[2], c->lst,
+                                       c->lop_red, c->cnt + CNT_LOP, drop),
+   dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+}
+
+void launch_lop_update(dd_ctx* c, const double* x, const double* w, const double* xp, double* out,
+                       cudaStream_t s) {
+  const long long n = c->g.plen;
+  (k_lop_update<<<grid_blocks(n, kThreads), kThreads, 0, s>>>(n, x, w, xp, out, c->lst), dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+}
+
+void launch_lop_normalize(dd_ctx* c, double* x, double* Mx, cudaStream_t s) {
+  const long long n = c->g.plen;
+  const int nb = grid_blocks(n, kThreads);
+  launch_outer_dots(c, x, Mx, s);
+  (k_lop_scale<<<nb, kThreads, 0, s>>>(n, x, Mx, c->ost), dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+}
+
+void launch_set_entry(double* v, long long idx, double val, cudaStream_t s) {
+  (k_set_entry<<<1, 32, 0, s>>>(v, idx, val), dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+}
+
+}  // namespace dd

@@ -646,12 +646,13 @@ void launch_outer_normalize(dd_ctx* c, const double* w, double* Mw, double* xout
 
 __global__ void __launch_bounds__(kThreads) k_outer_res(long long n, const double* __restrict__ Ax,
                                                         const double* __restrict__ Mx, OuterState* os,
-                                                        double* partials, unsigned* counter) {
+                                                        double* partials, unsigned* counter, double* __restrict__ ro) {
   const double mu = os->xAx;
   double acc[2] = {0.0, 0.0};
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x) {
     const double e = fma(-mu, Mx[t], Ax[t]);
+    if (ro != nullptr) ro[t] = e;
     acc[0] = fma(e, e, acc[0]);
     acc[1] = fma(Mx[t], Mx[t], acc[1]);
   }
@@ -662,11 +663,20 @@ __global__ void __launch_bounds__(kThreads) k_outer_res(long long n, const doubl
   }
 }
 
-void launch_outer_residual(dd_ctx* c, const double* xe, const double* Mx, double* Ax, cudaStream_t s) {
-  // Ax = A_sigma x and xAx = (x, A_sigma x); then the residual norms.
+void launch_outer_residual(dd_ctx* c, const double* xe, const double* Mx, double* Ax, cudaStream_t s, double* ro) {
+  // Ax = A_sigma x and xAx = (x, A_sigma x); then the residual norms (and the residual
+  // A_sigma x - xAx M x = A x - rho M x itself when ro is given).
   launch_stencil_dot(c, c->tabS, xe, Ax, &c->ost->xAx, c->cnt + CNT_OUTER1, s);
   const long long n = c->g.plen;
-  (k_outer_res<<<grid_blocks(n, kThreads), kThreads, 0, s>>>(n, Ax, Mx, c->ost, c->red, c->cnt + CNT_OUTER2), dd::note_launch());
+  (k_outer_res<<<grid_blocks(n, kThreads), kThreads, 0, s>>>(n, Ax, Mx, c->ost, c->red, c->cnt + CNT_OUTER2, ro),
+   dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+}
+
+void launch_outer_dots(dd_ctx* c, const double* w, const double* Mw, cudaStream_t s) {
+  const long long n = c->g.plen;
+  (k_outer_dots<<<grid_blocks(n, kThreads), kThreads, 0, s>>>(n, w, Mw, c->ost, c->red, c->cnt + CNT_OUTER0),
+   dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 

@@ -36,3 +36,14 @@ def oracle_problem(w: Workload, coarse=True, pu="equal", build_prec=True):
 
 def rel_err(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def sigma_tol(P):
+    """Tolerance on the cell shift sigma.  In FP64 the smallest eigenvalue of the cell pencil
+    is fixed only to about eps * lambda_max absolutely (the rounding of A psi, whose entries
+    are of size lambda_max |psi|, against sigma M psi), by any method: the dense solver of
+    the oracle and the inverse iteration of the GPU each land within a few such units."""
+    import scipy.sparse.linalg as spla
+    K, M, MV = q1.assemble_cell(P.g, P.V)
+    lmax = float(spla.eigsh((K + MV).tocsc(), k=1, M=M.tocsc(), which="LA", return_eigenvectors=False)[0])
+    return max(1e-12 * max(1.0, abs(P.sigma)), 8 * np.finfo(float).eps * lmax)
