@@ -12,5 +12,6 @@ paper's examples (Sec. 4.1 uses V = 100 sin^4(pi x) sin^4(pi y)); the paper
 uses no dataset.
 """
 from .potentials import (  # noqa: F401
-    Workload, WORKLOADS, potential, sample_cell_qp, gauss_legendre_01,
+    Workload, WORKLOADS, potential, sample_cell_qp, gauss_legendre_01, theta_seed, theta8_basis,
+    theta8_qp_basis,
 )

@@ -64,6 +64,8 @@ def potential(w: Workload):
                 c over the lattice (Z + 1/2)^2 within max-norm distance 3
       asym3     V = 10 (4 + sin 2pi x1 + sin 4pi x1 + 2 sin 2pi x2 + 2 sin 4pi x2 + y)
                 (the unsymmetric potential of Sec. 4.3)
+      theta8    V = sum_{j=1..8} theta_j cos(2 pi j x)(1 + 0.3 y), theta from
+                w.params["theta"], else theta_seed(w.seed) (the differentiable workload)
     """
     k = w.kind
     if k == "zero":
@@ -116,7 +118,38 @@ def potential(w: Workload):
         assert w.p == 2
         return lambda x1, x2, y: 10.0 * (4 + np.sin(2 * np.pi * x1) + np.sin(4 * np.pi * x1)
                                          + 2 * np.sin(2 * np.pi * x2) + 2 * np.sin(4 * np.pi * x2) + y)
+    if k == "theta8":
+        assert w.p == 1
+        th = np.asarray(w.params.get("theta", theta_seed(w.seed)[0]), dtype=float)
+
+        def Vt(x, y):
+            x = np.asarray(x, dtype=float)
+            out = np.zeros_like(x)
+            for j in range(len(th)):
+                out += th[j] * theta8_basis(j, x, y)
+            return out
+        return Vt
     raise ValueError(f"unknown potential kind {k!r}")
+
+
+def theta8_basis(j: int, x, y):
+    """g_j(x, y) = cos(2 pi (j+1) x)(1 + 0.3 y), the j-th basis potential of theta8 (0-based)."""
+    return np.cos(2 * np.pi * (j + 1) * np.asarray(x, dtype=float)) * (1.0 + 0.3 * np.asarray(y, dtype=float))
+
+
+def theta_seed(seed: int, terms: int = 8):
+    """(theta, theta_target) of the differentiable workload: theta ~ N(0, 25) and
+    theta_target = theta + N(0, 1), drawn from default_rng(seed) in that order."""
+    rng = np.random.default_rng(seed)
+    th = rng.normal(0.0, 5.0, terms)
+    tt = th + rng.normal(0.0, 1.0, terms)
+    return th, tt
+
+
+def theta8_qp_basis(w: Workload) -> np.ndarray:
+    """[8, n_qp] values of the basis potentials g_j at the cell quadrature points, in the
+    layout of sample_cell_qp (so that V_cell_qp = theta @ basis)."""
+    return np.stack([sample_cell_qp(w, lambda x, y, j=j: theta8_basis(j, x, y)) for j in range(8)])
 
 
 def gauss_legendre_01(Q: int):
@@ -164,4 +197,7 @@ WORKLOADS = {
     # same nine local matrices and cell problem as the 64 x 64 box
     "cfg3_mid": Workload("cfg3_mid", p=2, L=3, n=16, overlap=2, kind="wells"),
     "e1": Workload("e1", p=1, L=8, n=30, overlap=1, kind="sin4"),
+    # differentiable workload: theta ~ N(0, 25), 8 cosine modes times (1 + 0.3 y)
+    "cfg5": Workload("cfg5", p=1, L=256, n=32, overlap=4, kind="theta8", seed=5),
+    "cfg5_small": Workload("cfg5_small", p=1, L=8, n=16, overlap=2, kind="theta8", seed=5),
 }
