@@ -173,16 +173,20 @@ def _band_lower(A: sp.spmatrix):
 
 
 class TwoLevelAS:
-    """z = M_AS2^{-1} r (or M_AS1^{-1} r with coarse=False), Sec. 3.1.
+    """z = M_AS2^{-1} r (or M_AS1^{-1} r with coarse=False), Sec. 3.1; with restricted=True
+    the restricted variant M_RAS2^{-1} (M_RAS1^{-1}): the local solutions are weighted by the
+    partition of unity before the extension, sum_i R_i^T D_i A_i^{-1} R_i r (eq. of the
+    one-level preconditioners), the coarse correction added the same way.
 
     Every subdomain gets its own local matrix and its own banded Cholesky
     factor (no sharing between equal subdomains); A_0 is factorised densely.
     """
 
     def __init__(self, Asig: sp.csr_matrix, dec: Decomposition, psi_ext: np.ndarray,
-                 coarse: bool = True):
+                 coarse: bool = True, restricted: bool = False):
         self.dec = dec
         self.coarse = coarse
+        self.restricted = restricted
         self.local = []
         for ids in dec.idx:
             Ai = Asig[ids][:, ids]
@@ -196,8 +200,11 @@ class TwoLevelAS:
 
     def local_part(self, r: np.ndarray) -> np.ndarray:
         z = np.zeros_like(r)
-        for ids, cb in self.local:
-            z[ids] += sla.cho_solve_banded((cb, True), r[ids])
+        for i, (ids, cb) in enumerate(self.local):
+            yi = sla.cho_solve_banded((cb, True), r[ids])
+            if self.restricted:
+                yi = self.dec.weights[i] * yi
+            z[ids] += yi
         return z
 
     def coarse_part(self, r: np.ndarray) -> np.ndarray:

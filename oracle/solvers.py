@@ -9,6 +9,9 @@
   r = A x - R(x) B x (Sec. 2).  Stop when
   eta = ||A x - rho B x||_2 / (|rho| ||B x||_2) <= tol_res and
   |rho_k - rho_{k-1}| <= tol_lam |rho_k|.
+* ``gmres``: right-preconditioned restarted GMRES (Arnoldi with modified Gram-Schmidt,
+  Givens rotations), the Krylov method for the unsymmetric M_RAS2^{-1} (Sec. 2.2); stopped
+  on the true residual ||r_k||_2 <= rtol ||r_0||_2 like ``pcg``.
 * ``si_lopcg``: the inexact shift-and-invert preconditioned LOPCG of Algorithm 1:
   outer residual r_o = A x_k - R(x_k) B x_k, inner solve A_sigma w_k = r_o by PCG
   (relative tolerance fixed, or min{0.1, ||r_o||_2} as in Sec. 4.3), or w_k = M^{-1} r_o
@@ -67,9 +70,70 @@ def pcg(A, b, x0=None, prec=None, rtol=1e-8, maxit=10000, history=False):
     return x, maxit, hist
 
 
+def gmres(A, b, x0=None, prec=None, rtol=1e-8, restart=30, maxit=10000):
+    """Right-preconditioned restarted GMRES: x = x0 + M^{-1} V y minimising ||b - A x||_2 over
+    the Krylov space of A M^{-1}.  Returns (x, iterations, list of ||r_k||/||r_0||)."""
+    n = b.size
+    x = np.zeros(n) if x0 is None else x0.astype(float).copy()
+    P = (lambda v: v) if prec is None else prec
+    r = b - A @ x
+    r0 = np.sqrt(dot(r, r))
+    hist = [1.0]
+    if r0 == 0.0:
+        return x, 0, hist
+    its = 0
+    while its < maxit:
+        beta = np.sqrt(dot(r, r))
+        V = [r / beta]
+        Z = []
+        H = np.zeros((restart + 1, restart))
+        cs, sn = np.zeros(restart), np.zeros(restart)
+        g = np.zeros(restart + 1)
+        g[0] = beta
+        j_done = 0
+        for j in range(restart):
+            z = P(V[j])
+            Z.append(z)
+            w = A @ z
+            for i in range(j + 1):                 # modified Gram-Schmidt
+                H[i, j] = dot(w, V[i])
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.sqrt(dot(w, w))
+            V.append(w / H[j + 1, j] if H[j + 1, j] > 0 else w)
+            for i in range(j):                     # earlier rotations
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            den = np.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / den, H[j + 1, j] / den
+            H[j, j] = den
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            its += 1
+            j_done = j + 1
+            hist.append(abs(g[j + 1]) / r0)
+            if abs(g[j + 1]) <= rtol * r0 or its >= maxit:
+                break
+        y = sla.solve_triangular(H[:j_done, :j_done], g[:j_done])
+        for i in range(j_done):
+            x = x + y[i] * Z[i]
+        r = b - A @ x
+        if np.sqrt(dot(r, r)) <= rtol * r0:
+            return x, its, hist
+    return x, its, hist
+
+
+def _inner_solve(Asig, b, prec, rtol, maxit, krylov, restart):
+    if krylov == "gmres":
+        return gmres(Asig, b, None, prec, rtol, restart, maxit)
+    return pcg(Asig, b, None, prec, rtol, maxit)
+
+
 def inverse_iteration(Asig, M, sigma, prec=None, x0=None, tol_res=1e-8, tol_lam=1e-10,
-                      maxit_outer=100, rtol_inner=1e-8, maxit_inner=10000):
-    """Shifted inverse iteration with inexact PCG inner solves (Sec. 2)."""
+                      maxit_outer=100, rtol_inner=1e-8, maxit_inner=10000, krylov="cg", restart=30):
+    """Shifted inverse iteration with inexact inner solves (Sec. 2): PCG (krylov="cg", with
+    M_AS2^{-1}) or right-preconditioned GMRES (krylov="gmres", with M_RAS2^{-1})."""
     n = Asig.shape[0]
     x = np.ones(n) if x0 is None else x0.astype(float).copy()
     x /= np.sqrt(dot(x, M @ x))
@@ -78,7 +142,7 @@ def inverse_iteration(Asig, M, sigma, prec=None, x0=None, tol_res=1e-8, tol_lam=
     info = {}
     for k in range(1, maxit_outer + 1):
         b = M @ x
-        w, it, _ = pcg(Asig, b, None, prec, rtol_inner, maxit_inner)
+        w, it, _ = _inner_solve(Asig, b, prec, rtol_inner, maxit_inner, krylov, restart)
         inner.append(it)
         x = w / np.sqrt(dot(w, M @ w))
         if x.sum() < 0:
@@ -130,7 +194,7 @@ def rayleigh_ritz3(GA, GB, sums, drop=1e-10):
 
 
 def si_lopcg(A, M, sigma, prec=None, x0=None, x1=None, tol_res=1e-8, tol_lam=1e-10,
-             maxit_outer=1000, inner="fixed", rtol_inner=1e-8, maxit_inner=10000):
+             maxit_outer=1000, inner="fixed", rtol_inner=1e-8, maxit_inner=10000, krylov="cg", restart=30):
     """Inexact SI-preconditioned LOPCG (Algorithm 1).
 
     inner = "fixed": PCG on A_sigma w = r_o to relative residual rtol_inner;
@@ -166,7 +230,7 @@ def si_lopcg(A, M, sigma, prec=None, x0=None, x1=None, tol_res=1e-8, tol_lam=1e-
             w, it = prec(ro), 1
         else:
             rt = rtol_inner if inner == "fixed" else min(0.1, nro)
-            w, it, _ = pcg(Asig, ro, None, prec, rt, maxit_inner)
+            w, it, _ = _inner_solve(Asig, ro, prec, rt, maxit_inner, krylov, restart)
         inner_its.append(it)
         S = [x, w, xp]
         AS = [Ax, Asig @ w, Asig @ xp]
@@ -239,7 +303,8 @@ def exact_ground_state(A, M, sigma=None, dense_limit=2500, band=True, tol=1e-15,
 class Problem:
     """Everything the method builds for one workload, in oracle form."""
 
-    def __init__(self, g: q1.Grid, V, pu: str = "equal", coarse: bool = True, build_prec=True):
+    def __init__(self, g: q1.Grid, V, pu: str = "equal", coarse: bool = True, build_prec=True,
+                 restricted: bool = False):
         self.g = g
         self.V = V
         self.K, self.M, self.MV = q1.assemble_box(g, V)
@@ -248,10 +313,14 @@ class Problem:
         self.psi = q1.periodic_extension(g, self.psi_cell)
         self.Asig = (self.A - self.sigma * self.M).tocsr()
         self.dec = Decomposition(g, pu)
-        self.prec = TwoLevelAS(self.Asig, self.dec, self.psi, coarse=coarse) if build_prec else None
+        self.prec = TwoLevelAS(self.Asig, self.dec, self.psi, coarse=coarse,
+                               restricted=restricted) if build_prec else None
 
     def solve(self, b, rtol=1e-8, maxit=10000, x0=None, history=False):
         return pcg(self.Asig, b, x0, self.prec, rtol, maxit, history)
+
+    def solve_gmres(self, b, rtol=1e-8, restart=30, maxit=10000, x0=None):
+        return gmres(self.Asig, b, x0, self.prec, rtol, restart, maxit)
 
     def ground_state(self, **kw):
         return inverse_iteration(self.Asig, self.M, self.sigma, self.prec, **kw)
