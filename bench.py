@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-lopcg", action="store_true")
+    ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -391,6 +392,49 @@ def main():
                 lopcg[f"{form}_{inner}"] = {"ms": sum(perl) / len(perl), "lambda": resl[0], "outer_iters": resl[2],
                                             "inner_iters_total": resl[3]}
 
+    # differentiable workload (L = 256, 8-mode cosine potential): forward ground state and the
+    # backward pass (Hellmann-Feynman reduction + adjoint PCG) of lambda and of the
+    # eigenvector loss ||phi - phi_target||_M^2
+    grad_line = None
+    if not args.no_grad:
+        from ddinputs import theta_seed, theta8_qp_basis
+        w5 = WORKLOADS["cfg5"]
+        th5, tt5 = theta_seed(w5.seed)
+        B5 = torch.from_numpy(theta8_qp_basis(w5)).to(dev)
+        es5 = dd.Eigensolver(dd.grid_from_workload(w5, precision=dd.PRECISIONS[args.precision]),
+                             torch.from_numpy(tt5).to(dev) @ B5)
+        es5.prepare()
+        phi5t = torch.ones(w5.dofs, dtype=torch.float64, device=dev)
+        dd.dd_inverse_iterate(es5.ctx, phi5t)
+        V5 = (torch.from_numpy(th5).to(dev) @ B5).contiguous()
+        x5 = torch.empty(w5.dofs, dtype=torch.float64, device=dev)
+        g5 = torch.empty(w5.dofs, dtype=torch.float64, device=dev)
+        dV5 = torch.empty_like(V5)
+        fw, bw, its = [], [], 0
+        for rep in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dd.dd_set_potential(es5.ctx, V5)
+            dd.dd_cell_eigenpair(es5.ctx)
+            dd.dd_coarse_build(es5.ctx)
+            x5.fill_(1.0)
+            lam5 = dd.dd_inverse_iterate(es5.ctx, x5)[0]
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            dd.dd_apply_operator(es5.ctx, dd.DD_OP_MASS, (x5 - phi5t).contiguous(), g5)
+            g5.mul_(2.0)
+            its = dd.dd_potential_gradient(es5.ctx, x5, lam5, 1.0, g5, dV5)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            if rep > 0:
+                fw.append(t1 - t0)
+                bw.append(t2 - t1)
+        es5.close()
+        grad_line = {"workload": "cfg5: p=1, L=256, h=1/32, delta=4, V = sum_j theta_j cos(2 pi j x)(1+0.3y), "
+                                 f"theta ~ N(0,25) seed {w5.seed}",
+                     "forward_ms": 1e3 * sum(fw) / len(fw), "backward_ms": 1e3 * sum(bw) / len(bw),
+                     "adjoint_pcg_iters": its, "lambda": lam5}
+
     # phase breakdown of one step (host timer around each synchronous call)
     def phases(es):
         out = {}
@@ -514,6 +558,7 @@ def main():
             "fp64_plain": {"lambda": res64[0], "outer_iters": res64[2], "inner_iters_total": res64[3]},
             "pcg_iters_per_s": inner_tot / (step_ms / 1e3),
             "si_lopcg_time_to_ground_state": lopcg,
+            "differentiable": grad_line,
             "roofline": roofline,
             "roofline_other_kernels": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv)
                                            for kk, vv in v.items() if kk in ("bound", "achieved", "peak", "unit",

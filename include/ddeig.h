@@ -146,6 +146,20 @@ int dd_pcg_solve(dd_ctx* ctx, const double* b, double* x, double rtol, int maxit
                  int* iters_out, double* relres_out);
 
 /*
+ * dd_gmres_solve -- A_sigma x = b by right-preconditioned restarted GMRES (flexible form, so
+ * a rounded preconditioner is allowed) with the context's two-level Schwarz preconditioner,
+ * M_RAS2^{-1} or M_AS2^{-1} (DD_OPT_PRECOND; Sec. 2.2 pairs the restricted one with GMRES),
+ * restart length DD_OPT_RESTART.  Arnoldi by classical Gram-Schmidt applied twice.
+ *   b        host or device, ndof doubles
+ *   x        host or device, ndof doubles; in: initial guess, out: solution
+ *   stops when ||b - A_sigma x||_2 <= rtol ||b - A_sigma x_0||_2 (true residual)
+ * DD_EMAXIT after maxit iterations (x holds the last iterate).  dd_pcg_solve returns
+ * DD_EINVAL while the restricted preconditioner is selected.
+ */
+int dd_gmres_solve(dd_ctx* ctx, const double* b, double* x, double rtol, int maxit, int* iters_out,
+                   double* relres_out);
+
+/*
  * dd_inverse_iterate -- shifted inverse iteration (Sec. 2): b = M x_k, solve A_sigma w = b
  * by dd_pcg_solve with zero initial guess and relative tolerance rtol_inner, x_{k+1} =
  * w / ||w||_M (sign: sum x > 0); rho = x^T A x, eta = ||A x - rho M x||_2 / (|rho| ||M x||_2).
@@ -183,6 +197,32 @@ int dd_inverse_iterate(dd_ctx* ctx, double* x, double tol_res, double tol_lam, i
 int dd_lopcg(dd_ctx* ctx, double* x, int inner, double tol_res, double tol_lam, int maxit_outer,
              double rtol_inner, double* lambda_out, int* outer_out, int* inner_total_out,
              int* inner_max_out);
+
+/*
+ * dd_potential_gradient -- gradient of a function of the ground state with respect to the
+ * potential values V_cell_qp (the layout of dd_setup's V).  The potential enters only through
+ * M_V (Sec. 1: (V phi, v) by tensor Gauss quadrature), so for the M-normalised ground state
+ * (lambda, phi):
+ *   d lambda / dV_cell_qp[e, q] = sum over the copies of cell element e of h^d W_q phi_h(z_q)^2
+ *     (Hellmann-Feynman: d lambda = phi^T dA phi),
+ * and for a loss l(phi) with g = dl/dphi, with w the solution of the projected singular
+ * system (A - lambda M) w = g - M phi (phi^T g), phi^T M w = 0, solved by projected PCG with
+ * the two-level Schwarz preconditioner of the context (preconditioned residuals projected
+ * M-orthogonally to phi, so A - lambda M is positive definite on every search direction even
+ * with lambda, phi only as accurate as the eigen-solve):
+ *   dl / dV_cell_qp[e, q] = - sum over the copies of h^d W_q w_h(z_q) phi_h(z_q).
+ * Writes dV = g_lambda * d lambda/dV + dl/dV (the second term only when g_phi != NULL).
+ *   phi        host or device, ndof doubles: the M-normalised ground state (dd_inverse_iterate
+ *              or dd_lopcg output) of the context's potential; lambda its eigenvalue
+ *   g_phi      host or device, ndof doubles, or NULL
+ *   rtol       relative residual of the adjoint PCG (e.g. 1e-10)
+ *   dV         host or device, nV = n^p ny Q^(p+1) doubles (output)
+ *   iters_out  adjoint PCG iterations (0 without g_phi; may be NULL)
+ * Needs dd_coarse_build.  DD_EINVAL on a size mismatch, DD_EMAXIT if the adjoint PCG does not
+ * converge in 10000 iterations.
+ */
+int dd_potential_gradient(dd_ctx* ctx, const double* phi, double lambda, double g_lambda,
+                          const double* g_phi, double rtol, double* dV, size_t nV, int* iters_out);
 
 /*
  * dd_eigenpair -- convenience: dd_setup, dd_cell_eigenpair, dd_coarse_build and
@@ -232,6 +272,10 @@ int dd_coarse_matrix(dd_ctx* ctx, double* A0_host);
  *   DD_OPT_USE_GRAPH    replay the PCG iteration as a CUDA graph [1]
  *   DD_OPT_FLEXIBLE     -1 automatic (flexible iff rounded local inverses) / 0 / 1 [-1]
  *   DD_OPT_TIMING       1: time every kernel class with CUDA events (eager launches) [0]
+ *   DD_OPT_KRYLOV       inner solver of dd_inverse_iterate / dd_lopcg: 0 PCG, 1 GMRES [0]
+ *   DD_OPT_PRECOND      0 M_AS2^{-1} (symmetric, for CG), 1 M_RAS2^{-1} (restricted: local
+ *                       solutions weighted by the partition of unity D_i; GMRES only) [0]
+ *   DD_OPT_RESTART      GMRES restart length, 1..200, fixed by the first GMRES solve [30]
  *   DD_OPT_LOCAL_RHS    FP64 local solves: subdomains of one type solved together by one warp,
  *                       1, 2 or 4 (capped by shared memory), 0 = default (2 where allowed) [0]; the result
  *                       does not depend on it (same operations per vector) */
@@ -240,6 +284,9 @@ int dd_coarse_matrix(dd_ctx* ctx, double* A0_host);
 #define DD_OPT_FLEXIBLE    2
 #define DD_OPT_TIMING      3
 #define DD_OPT_LOCAL_RHS   4
+#define DD_OPT_KRYLOV      5
+#define DD_OPT_PRECOND     6
+#define DD_OPT_RESTART     7
 int dd_set_option(dd_ctx* ctx, int option, int value);
 
 /* Per-kernel-class timing collected while DD_OPT_TIMING = 1: for class k (0 <= k < count),

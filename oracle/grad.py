@@ -16,7 +16,11 @@ so every copy of a cell element uses the same V_cell_qp[e, q]):
   with phi^T M dphi = 0.  With w the solution of (A - lambda M) w = g - M phi (phi^T g) in the
   M-orthogonal complement of phi (the projected singular system), dl = -w^T dA phi, so
   dl / d V_cell_qp = -qp_product(w, phi).  The oracle solves the singular system exactly
-  through the bordered matrix [[A - lambda M, M phi], [phi^T M, 0]] (sparse LU).
+  through the bordered matrix [[A - lambda M, M phi], [phi^T M, 0]] (sparse LU) on small
+  grids; on large ones (where the dense border makes sparse LU slow) by CG on the consistent
+  singular system preconditioned with the exact banded Cholesky factor of A - sigma M (sigma
+  below lambda), to a relative residual of 1e-14, followed by the projection
+  w <- w - phi (phi^T M w).
 """
 from __future__ import annotations
 
@@ -70,18 +74,43 @@ def eigenvalue_gradient(g: q1.Grid, phi: np.ndarray) -> np.ndarray:
     return qp_product(g, phi, phi)
 
 
-def adjoint_solve(A, M, lam: float, phi: np.ndarray, gphi: np.ndarray) -> np.ndarray:
-    """w with (A - lam M) w = gphi - M phi (phi^T gphi) and phi^T M w = 0 (bordered system)."""
+def adjoint_solve(A, M, lam: float, phi: np.ndarray, gphi: np.ndarray, sigma=None,
+                  direct_limit: int = 20000, rtol: float = 1e-14) -> np.ndarray:
+    """w with (A - lam M) w = gphi - M phi (phi^T gphi) and phi^T M w = 0."""
     Mphi = M @ phi
     r = gphi - Mphi * float(phi @ gphi)
     n = A.shape[0]
     Al = (A - lam * M).tocsr()
-    K = sp.bmat([[Al, sp.csr_matrix(Mphi[:, None])], [sp.csr_matrix(Mphi[None, :]), None]], format="csc")
-    sol = spla.spsolve(K, np.concatenate([r, [0.0]]))
-    return sol[:n]
+    if n <= direct_limit:
+        K = sp.bmat([[Al, sp.csr_matrix(Mphi[:, None])], [sp.csr_matrix(Mphi[None, :]), None]], format="csc")
+        sol = spla.spsolve(K, np.concatenate([r, [0.0]]))
+        return sol[:n]
+    if sigma is None:
+        raise ValueError("the iterative adjoint needs a shift sigma below lambda")
+    from .dd import _band_lower
+    import scipy.linalg as sla
+    cb = sla.cholesky_banded(_band_lower((A - sigma * M).tocsr()), lower=True)
+    w = np.zeros(n)
+    res = r.copy()
+    r0 = np.sqrt(res @ res)
+    z = sla.cho_solve_banded((cb, True), res)
+    p = z.copy()
+    rz = res @ z
+    for _ in range(1000):
+        q = Al @ p
+        alpha = rz / (p @ q)
+        w += alpha * p
+        res -= alpha * q
+        if np.sqrt(res @ res) <= rtol * r0:
+            break
+        z = sla.cho_solve_banded((cb, True), res)
+        rz_new = res @ z
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return w - phi * float(phi @ (M @ w))
 
 
-def loss_gradient(g: q1.Grid, A, M, lam: float, phi: np.ndarray, gphi: np.ndarray) -> np.ndarray:
+def loss_gradient(g: q1.Grid, A, M, lam: float, phi: np.ndarray, gphi: np.ndarray, sigma=None) -> np.ndarray:
     """dl / d V_cell_qp for a loss l(phi) with gradient gphi = dl/dphi."""
-    w = adjoint_solve(A, M, lam, phi, gphi)
+    w = adjoint_solve(A, M, lam, phi, gphi, sigma=sigma)
     return -qp_product(g, w, phi)

@@ -24,6 +24,7 @@ DD_PREC_FP64, DD_PREC_TF32, DD_PREC_BF16 = 0, 1, 2
 DD_PU_EQUAL, DD_PU_DISTANCE = 0, 1
 DD_OP_ASIGMA, DD_OP_MASS, DD_OP_A = 0, 1, 2
 DD_OPT_CHECK_EVERY, DD_OPT_USE_GRAPH, DD_OPT_FLEXIBLE, DD_OPT_TIMING, DD_OPT_LOCAL_RHS = 0, 1, 2, 3, 4
+DD_OPT_KRYLOV, DD_OPT_PRECOND, DD_OPT_RESTART = 5, 6, 7
 PRECISIONS = {"fp64": DD_PREC_FP64, "tf32": DD_PREC_TF32, "bf16": DD_PREC_BF16}
 DD_INNER_FIXED, DD_INNER_ADAPTIVE, DD_INNER_FUSED = 0, 1, 2
 INNER_MODES = {"fixed": DD_INNER_FIXED, "adaptive": DD_INNER_ADAPTIVE, "fused": DD_INNER_FUSED}
@@ -56,6 +57,9 @@ _SIGS = {
     "dd_pcg_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int, POINTER(c_int), POINTER(c_double)]),
     "dd_inverse_iterate": (c_int, [c_void_p, c_void_p, c_double, c_double, c_int, c_double, POINTER(c_double),
                                    POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
+    "dd_potential_gradient": (c_int, [c_void_p, c_void_p, c_double, c_double, c_void_p, c_double, c_void_p,
+                                      c_size_t, POINTER(c_int)]),
+    "dd_gmres_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int, POINTER(c_int), POINTER(c_double)]),
     "dd_lopcg": (c_int, [c_void_p, c_void_p, c_int, c_double, c_double, c_int, c_double, POINTER(c_double),
                          POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
     "dd_eigenpair": (c_int, [POINTER(dd_grid), c_void_p, c_size_t, c_void_p, POINTER(c_double), c_void_p,
@@ -186,6 +190,12 @@ def dd_pcg_solve(ctx, b, x, rtol=1e-8, maxit=10000, allow_maxit=False):
     return it.value, rel.value
 
 
+def dd_gmres_solve(ctx, b, x, rtol=1e-8, maxit=10000):
+    it, rel = c_int(), c_double()
+    _check(lib().dd_gmres_solve(ctx, _ptr(b), _ptr(x), rtol, maxit, byref(it), byref(rel)), ctx)
+    return it.value, rel.value
+
+
 def dd_inverse_iterate(ctx, x, tol_res=1e-8, tol_lam=1e-10, maxit_outer=100, rtol_inner=1e-8):
     lam, outer, tot, mx = c_double(), c_int(), c_int(), c_int()
     _check(lib().dd_inverse_iterate(ctx, _ptr(x), tol_res, tol_lam, maxit_outer, rtol_inner, byref(lam),
@@ -200,6 +210,16 @@ def dd_lopcg(ctx, x, inner="fused", tol_res=1e-8, tol_lam=1e-10, maxit_outer=100
     _check(lib().dd_lopcg(ctx, _ptr(x), mode, tol_res, tol_lam, maxit_outer, rtol_inner, byref(lam), byref(outer),
                           byref(tot), byref(mx)), ctx)
     return lam.value, outer.value, tot.value, mx.value
+
+
+def dd_potential_gradient(ctx, phi, lam, g_lambda, g_phi, dV, rtol=1e-10) -> int:
+    """dV = g_lambda d(lambda)/dV_cell_qp + dl/dV_cell_qp (adjoint term when g_phi is given);
+    returns the adjoint PCG iteration count."""
+    it = c_int()
+    n = dV.numel() if hasattr(dV, "numel") else dV.size
+    _check(lib().dd_potential_gradient(ctx, _ptr(phi), float(lam), float(g_lambda), _ptr(g_phi), rtol, _ptr(dV), n,
+                                       byref(it)), ctx)
+    return it.value
 
 
 def dd_eigenpair(grid: dd_grid, V_cell_qp, stream=None, phi_out=None):

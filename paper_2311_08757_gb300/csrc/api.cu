@@ -256,7 +256,7 @@ bool use_gemm(const dd_ctx* c) { return c->grid.precision != DD_PREC_FP64; }
 // The coarse right-hand side is formed in the pass that gathers R_i r (local solve or pack);
 // with tensor-core local solves the coarse solve then runs on a second stream beside the
 // GEMM (the two-level operator is additive, so the branches are independent).
-void precond(dd_ctx* c, const double* r, int mode) {
+void precond(dd_ctx* c, const double* r, int mode, double* zout = nullptr) {
   cudaStream_t s = c->stream;
   const bool coarse = c->grid.coarse != 0;
   double* c0 = coarse ? c->c0 : nullptr;
@@ -276,7 +276,7 @@ void precond(dd_ctx* c, const double* r, int mode) {
     TIMED(KC_LOCAL_FP64, s, launch_band_solve_local(c, r, c0, s));
     if (coarse) TIMED(KC_CSOLVE, s, launch_coarse_solve(c, s));
   }
-  TIMED(KC_PROLONG, s, launch_prolong(c, mode, s));
+  TIMED(KC_PROLONG, s, launch_prolong(c, mode, s, zout));
 }
 
 void pcg_iteration(dd_ctx* c) {
@@ -359,6 +359,113 @@ int pcg_run(dd_ctx* c, const double* b, double rtol, int maxit, int* iters, doub
   return DD_OK;
 }
 
+// Right-preconditioned restarted (flexible) GMRES on A_sigma x = b, x in c->x (initial guess
+// in, solution out); stop when the true residual is <= rtol ||b - A x_0||.
+int gmres_run(dd_ctx* c, const double* b, double rtol, int maxit, int* iters, double* relres) {
+  cudaStream_t s = c->stream;
+  const Geo& g = c->g;
+  const int m = c->gm_restart;
+  const int ld = m + 1;
+  if (c->gm_alloc != m) {
+    if (c->gm_alloc != 0) throw Error(DD_ESTATE, "GMRES restart length cannot change after the first solve");
+    c->gm_V.resize(m + 1);
+    c->gm_Z.resize(m);
+    for (auto& v : c->gm_V) v = alloc_vec(c);
+    for (auto& v : c->gm_Z) v = alloc_vec(c);
+    c->gm_W = alloc_vec(c);
+    c->gm_Vptr = (double**)dev_alloc(c, sizeof(double*) * (m + 1));
+    c->gm_Zptr = (double**)dev_alloc(c, sizeof(double*) * m);
+    DD_CUDA(cudaMemcpyAsync(c->gm_Vptr, c->gm_V.data(), sizeof(double*) * (m + 1), cudaMemcpyHostToDevice, s));
+    DD_CUDA(cudaMemcpyAsync(c->gm_Zptr, c->gm_Z.data(), sizeof(double*) * m, cudaMemcpyHostToDevice, s));
+    c->gm_part = (double*)dev_alloc(c, sizeof(double) * (size_t)(m + 1) * 304);
+    c->gm_h = (double*)dev_alloc(c, sizeof(double) * 2 * ld + 1);
+    c->gm_H = (double*)dev_alloc(c, sizeof(double) * (size_t)ld * m);
+    c->gm_cs = (double*)dev_alloc(c, sizeof(double) * m);
+    c->gm_sn = (double*)dev_alloc(c, sizeof(double) * m);
+    c->gm_g = (double*)dev_alloc(c, sizeof(double) * ld);
+    c->gm_y = (double*)dev_alloc(c, sizeof(double) * m);
+    c->gm_res = (double*)dev_alloc(c, sizeof(double) * 2);
+    DD_CUDA(cudaMallocHost(&c->gm_res_h, sizeof(double) * 2));
+    c->gm_alloc = m;
+  }
+  double* W = c->gm_W;
+  double* h2 = c->gm_h + ld;        // second Gram-Schmidt pass
+  double* nrm2 = c->gm_h + 2 * ld;  // ||w||^2
+  const double* const* Vp = c->gm_Vptr;
+  auto read_scalar = [&](const double* d) -> double {
+    DD_CUDA(cudaMemcpyAsync(c->gm_res_h, d, sizeof(double), cudaMemcpyDeviceToHost, s));
+    DD_CUDA(cudaStreamSynchronize(s));
+    if (c->timing) timer_collect(c);
+    return c->gm_res_h[0];
+  };
+  PcgState init;
+  std::memset(&init, 0, sizeof(init));
+  DD_CUDA(cudaMemcpyAsync(c->st, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+  // r_0 = b - A x_0
+  TIMED(KC_STENCIL, s, launch_stencil(c, c->tabS, c->x, W, s));
+  TIMED(KC_XRUPDATE, s, launch_axpby(c, -1.0, W, 1.0, nullptr, b, W, s));
+  TIMED(KC_XRUPDATE, s, launch_dot(c, W, W, nrm2, s));
+  const double r0 = std::sqrt(read_scalar(nrm2));
+  int its = 0;
+  double rel = 0.0;
+  if (!std::isfinite(r0)) return fail(c, DD_ENAN, "non-finite GMRES residual");
+  if (r0 == 0.0) {
+    if (iters) *iters = 0;
+    if (relres) *relres = 0.0;
+    return DD_OK;
+  }
+  while (true) {
+    TIMED(KC_XRUPDATE, s, launch_scale_by_norm(c, W, nrm2, c->gm_V[0], s));
+    TIMED(KC_MISC, s, launch_gmres_start(c, nrm2, s));
+    int j = 0, done = 0;
+    for (j = 0; j < m; ++j) {
+      precond(c, c->gm_V[j], 0, c->gm_Z[j]);
+      TIMED(KC_STENCIL, s, launch_stencil(c, c->tabS, c->gm_Z[j], W, s));
+      TIMED(KC_XRUPDATE, s, launch_multidot(c, j + 1, Vp, W, c->gm_h, 0, s));
+      TIMED(KC_XRUPDATE, s, launch_multiaxpy(c, j + 1, Vp, c->gm_h, -1.0, W, s));
+      TIMED(KC_XRUPDATE, s, launch_multidot(c, j + 1, Vp, W, h2, 0, s));
+      TIMED(KC_XRUPDATE, s, launch_multiaxpy(c, j + 1, Vp, h2, -1.0, W, s));
+      TIMED(KC_XRUPDATE, s, launch_add_inplace(c, j + 1, c->gm_h, h2, s));
+      TIMED(KC_XRUPDATE, s, launch_dot(c, W, W, nrm2, s));
+      TIMED(KC_XRUPDATE, s, launch_scale_by_norm(c, W, nrm2, c->gm_V[j + 1], s));
+      TIMED(KC_MISC, s, launch_givens(c, j, s));
+      const double est = read_scalar(c->gm_res);
+      ++its;
+      if (!std::isfinite(est)) return fail(c, DD_ENAN, "non-finite GMRES residual");
+      if (est <= rtol * r0 || its >= maxit) {
+        done = 1;
+        ++j;
+        break;
+      }
+    }
+    const int mm = std::min(j, m);
+    TIMED(KC_MISC, s, launch_backsolve(c, mm, s));
+    TIMED(KC_XRUPDATE, s, launch_multiaxpy(c, mm, c->gm_Zptr, c->gm_y, 1.0, c->x, s));
+    // true residual
+    TIMED(KC_STENCIL, s, launch_stencil(c, c->tabS, c->x, W, s));
+    TIMED(KC_XRUPDATE, s, launch_axpby(c, -1.0, W, 1.0, nullptr, b, W, s));
+    TIMED(KC_XRUPDATE, s, launch_dot(c, W, W, nrm2, s));
+    rel = std::sqrt(read_scalar(nrm2)) / r0;
+    if (rel <= rtol) break;
+    if (its >= maxit) {
+      if (iters) *iters = its;
+      if (relres) *relres = rel;
+      return fail(c, DD_EMAXIT, "GMRES reached maxit");
+    }
+    (void)done;
+  }
+  if (iters) *iters = its;
+  if (relres) *relres = rel;
+  return DD_OK;
+}
+
+// the inner solve of the outer eigen-iterations: PCG (AS2) or GMRES (either preconditioner)
+int inner_solve(dd_ctx* c, const double* b, double rtol, int maxit, int* iters, double* relres) {
+  if (c->krylov == 1) return gmres_run(c, b, rtol, maxit, iters, relres);
+  if (c->ras) throw Error(DD_EINVAL, "the restricted Schwarz preconditioner is not symmetric: use GMRES");
+  return pcg_run(c, b, rtol, maxit, iters, relres);
+}
+
 void read_outer(dd_ctx* c) {
   DD_CUDA(cudaMemcpyAsync(c->ost_h, c->ost, sizeof(OuterState), cudaMemcpyDeviceToHost, c->stream));
   DD_CUDA(cudaStreamSynchronize(c->stream));
@@ -395,6 +502,7 @@ void dd_destroy(dd_ctx* c) {
   dd::gemm_free(c);
   for (void* p : c->allocs) cudaFree(p);
   if (c->st_h) cudaFreeHost(c->st_h);
+  if (c->gm_res_h) cudaFreeHost(c->gm_res_h);
   if (c->ost_h) cudaFreeHost(c->ost_h);
   if (c->lst_h) cudaFreeHost(c->lst_h);
   if (c->side) cudaStreamDestroy(c->side);
@@ -505,6 +613,7 @@ int dd_setup(const dd_grid* gr, const double* V, size_t nV, void* stream, dd_ctx
     c->ncell = (long long)((G.p == 1) ? G.n : G.n * G.n) * g.nyi;
     c->psi_cell = (double*)dev_alloc(c, sizeof(double) * c->ncell);
     c->wT = (double*)dev_alloc(c, sizeof(double) * (size_t)c->ntypes * c->kpad);
+    c->puT = (double*)dev_alloc(c, sizeof(double) * (size_t)c->ntypes * c->kpad);
     c->c0 = (double*)dev_alloc(c, sizeof(double) * g.nsub);
     c->u0 = (double*)dev_alloc(c, sizeof(double) * g.nsub);
     c->A0band = (double*)dev_alloc(c, sizeof(double) * (size_t)g.nsub * (G.p == 1 ? 3 : 9));
@@ -689,9 +798,26 @@ int dd_pcg_solve(dd_ctx* c, const double* b, double* x, double rtol, int maxit, 
   if (rc) return rc;
   return guarded(c, [&]() -> int {
     enter(c);
+    if (c->ras) throw Error(DD_EINVAL, "the restricted Schwarz preconditioner is not symmetric: use dd_gmres_solve");
     load_vec(c, b, c->w3);
     load_vec(c, x, c->x);
     int r2 = pcg_run(c, c->w3, rtol, maxit, iters_out, relres_out);
+    store_vec(c, c->x, x);
+    DD_CUDA(cudaStreamSynchronize(c->stream));
+    return r2;
+  });
+}
+
+int dd_gmres_solve(dd_ctx* c, const double* b, double* x, double rtol, int maxit, int* iters_out,
+                   double* relres_out) {
+  if (!b || !x || !(rtol > 0.0) || maxit < 1) return fail(c, DD_EINVAL, "bad argument");
+  int rc = stage_err(c, 3);
+  if (rc) return rc;
+  return guarded(c, [&]() -> int {
+    enter(c);
+    load_vec(c, b, c->w3);
+    load_vec(c, x, c->x);
+    int r2 = gmres_run(c, c->w3, rtol, maxit, iters_out, relres_out);
     store_vec(c, c->x, x);
     DD_CUDA(cudaStreamSynchronize(c->stream));
     return r2;
@@ -723,7 +849,7 @@ int dd_inverse_iterate(dd_ctx* c, double* x, double tol_res, double tol_lam, int
       DD_CUDA(cudaMemsetAsync(c->x, 0, sizeof(double) * c->g.plen, s));
       int it = 0;
       double rel = 0.0;
-      int prc = pcg_run(c, c->w2, rtol_inner, 10000, &it, &rel);
+      int prc = inner_solve(c, c->w2, rtol_inner, 10000, &it, &rel);
       inner_tot += it;
       inner_max = std::max(inner_max, it);
       if (prc != DD_OK && prc != DD_EMAXIT) return prc;
@@ -819,7 +945,7 @@ int dd_lopcg(dd_ctx* c, double* x, int inner, double tol_res, double tol_lam, in
         const double rt = (inner == DD_INNER_FIXED) ? rtol_inner : std::min(0.1, std::sqrt(rr));
         DD_CUDA(cudaMemsetAsync(c->x, 0, sizeof(double) * g.plen, s));
         double rel = 0.0;
-        const int prc = pcg_run(c, RO, rt, 10000, &it, &rel);
+        const int prc = inner_solve(c, RO, rt, 10000, &it, &rel);
         if (prc != DD_OK && prc != DD_EMAXIT) return prc;
         W = c->x;
       }
@@ -862,6 +988,119 @@ int dd_lopcg(dd_ctx* c, double* x, int inner, double tol_res, double tol_lam, in
     if (inner_total_out) *inner_total_out = inner_tot;
     if (inner_max_out) *inner_max_out = inner_max;
     if (status != DD_OK) return fail(c, status, "outer iteration limit reached");
+    return DD_OK;
+  });
+}
+
+namespace {
+
+// Projected PCG for the adjoint (A - lambda M) w = r, r orthogonal to phi, w M-orthogonal to
+// phi: the preconditioned residual is projected, z = Pi M^{-1} Pi^T r with
+// Pi = I - phi (M phi)^T, so every search direction stays in the M-orthogonal complement
+// of phi, where A - lambda M is positive definite even when lambda and phi carry the error
+// of the eigen-solve (there A - lambda M has a tiny negative eigenvalue along phi).
+// Polak-Ribiere beta (exact for the FP64 preconditioner, flexible for the rounded one).
+// Vectors: b (in, overwritten as the residual), x (out), u = M phi, phi; scratch p, q, rp.
+int adjoint_pcg(dd_ctx* c, double* r, double* x, const double* u, const double* phi, double* p, double* q,
+                double* zs, double rtol, int maxit, int* iters) {
+  cudaStream_t s = c->stream;
+  const Geo& g = c->g;
+  double* d = c->gscal;   // device scalars
+  auto dot = [&](const double* a, const double* b2) -> double {
+    launch_dot(c, a, b2, d, s);
+    double h = 0.0;
+    DD_CUDA(cudaMemcpyAsync(&h, d, sizeof(double), cudaMemcpyDeviceToHost, s));
+    DD_CUDA(cudaStreamSynchronize(s));
+    return h;
+  };
+  auto axpby = [&](double a, const double* xv, double bcoef, const double* yv, double* out) {
+    launch_axpby(c, a, xv, bcoef, nullptr, yv, out, s);
+  };
+  auto apply_prec = [&]() {   // zs = Pi M^{-1} Pi^T r  (r is kept orthogonal to phi)
+    PcgState init;
+    std::memset(&init, 0, sizeof(init));
+    DD_CUDA(cudaMemcpyAsync(c->st, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+    precond(c, r, 0);
+    const double t = dot(u, c->z);
+    axpby(1.0, c->z, -t, phi, zs);
+  };
+  DD_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * g.plen, s));
+  const double rr0 = dot(r, r);
+  *iters = 0;
+  if (rr0 == 0.0) return DD_OK;
+  apply_prec();
+  DD_CUDA(cudaMemcpyAsync(p, zs, sizeof(double) * g.plen, cudaMemcpyDeviceToDevice, s));
+  double rz = dot(r, zs);
+  for (int k = 1; k <= maxit; ++k) {
+    TIMED(KC_STENCIL, s, launch_stencil(c, c->tabL, p, q, s));
+    const double pq = dot(p, q);
+    if (!(pq > 0.0)) return fail(c, std::isfinite(pq) ? DD_ENOTSPD : DD_ENAN, "adjoint: p^T (A - lambda M) p <= 0");
+    const double alpha = rz / pq;
+    axpby(1.0, x, alpha, p, x);
+    axpby(1.0, r, -alpha, q, r);
+    // keep r orthogonal to phi against drift
+    const double tp = dot(phi, r);
+    axpby(1.0, r, -tp, u, r);
+    const double rr = dot(r, r);
+    *iters = k;
+    if (rr <= rtol * rtol * rr0) return DD_OK;
+    apply_prec();
+    const double zq = dot(zs, q);
+    const double rz_new = dot(r, zs);
+    const double beta = -zq / pq;   // (z_{k+1}, r_{k+1} - r_k) / (z_k, r_k)
+    axpby(1.0, zs, beta, p, p);
+    rz = rz_new;
+  }
+  return fail(c, DD_EMAXIT, "adjoint PCG reached maxit");
+}
+
+}  // namespace
+
+int dd_potential_gradient(dd_ctx* c, const double* phi, double lambda, double g_lambda, const double* g_phi,
+                          double rtol, double* dV, size_t nV, int* iters_out) {
+  if (!phi || !dV || !(rtol > 0.0)) return fail(c, DD_EINVAL, "bad argument");
+  int rc = stage_err(c, 3);
+  if (rc) return rc;
+  const Geo& g = c->g;
+  size_t expect = (size_t)(g.p == 2 ? g.n * g.n : g.n) * (size_t)(g.nyi + 1);
+  for (int k = 0; k < g.p + 1; ++k) expect *= (size_t)g.Q;
+  if (nV != expect) return fail(c, DD_EINVAL, "nV does not match n^p ny Q^(p+1)");
+  return guarded(c, [&]() -> int {
+    enter(c);
+    cudaStream_t s = c->stream;
+    if (!c->gv[0]) {
+      for (double*& v : c->gv) v = alloc_vec(c);
+      c->tabL = (double*)dev_alloc(c, sizeof(double) * (size_t)g.ncls * g.ntap);
+      c->gscal = (double*)dev_alloc(c, sizeof(double) * 2);
+      c->gout = (double*)dev_alloc(c, sizeof(double) * nV);
+    }
+    double *PHI = c->gv[0], *G = c->gv[1], *U = c->gv[2], *VV = c->gv[3];
+    double *W = c->gv[4], *P = c->gv[5], *Q = c->gv[6], *Z = c->gv[7];
+    load_vec(c, phi, PHI);
+    int iters = 0;
+    if (g_phi) {
+      // r = g - M phi (phi^T g): orthogonal to phi, the right-hand side of the adjoint
+      load_vec(c, g_phi, G);
+      TIMED(KC_OUTER, s, launch_stencil(c, c->tabM, PHI, U, s));
+      TIMED(KC_OUTER, s, launch_dot(c, PHI, G, c->gscal, s));
+      TIMED(KC_OUTER, s, launch_axpby(c, 1.0, G, -1.0, c->gscal, U, G, s));
+      launch_tab_shift(c, lambda, c->tabL);
+      const int prc = adjoint_pcg(c, G, W, U, PHI, P, Q, Z, rtol, 10000, &iters);
+      if (prc != DD_OK) return prc;
+      // w <- w - phi (M phi)^T w (the iterates stay there up to rounding)
+      TIMED(KC_OUTER, s, launch_dot(c, U, W, c->gscal, s));
+      TIMED(KC_OUTER, s, launch_axpby(c, 1.0, W, -1.0, c->gscal, PHI, W, s));
+      // v = g_lambda phi - w
+      TIMED(KC_OUTER, s, launch_axpby(c, g_lambda, PHI, -1.0, nullptr, W, VV, s));
+    } else {
+      TIMED(KC_OUTER, s, launch_axpby(c, g_lambda, PHI, 0.0, nullptr, PHI, VV, s));
+    }
+    // dV[e, q] = sum over copies of h^d W_q phi_h (g_lambda phi_h - w_h)
+    double* out = is_device_ptr(dV) ? dV : c->gout;
+    TIMED(KC_OUTER, s, launch_qp_product(c, PHI, VV, out, s));
+    if (out != dV) DD_CUDA(cudaMemcpyAsync(dV, out, sizeof(double) * nV, cudaMemcpyDeviceToHost, s));
+    DD_CUDA(cudaStreamSynchronize(s));
+    if (iters_out) *iters_out = iters;
     return DD_OK;
   });
 }
@@ -932,6 +1171,19 @@ int dd_set_option(dd_ctx* c, int option, int value) {
       c->flexible_opt = value;
       break;
     case DD_OPT_TIMING: c->timing = value ? 1 : 0; break;
+    case DD_OPT_KRYLOV:
+      if (value != 0 && value != 1) return fail(c, DD_EINVAL, "krylov must be 0 (PCG) or 1 (GMRES)");
+      c->krylov = value;
+      break;
+    case DD_OPT_PRECOND:
+      if (value != 0 && value != 1) return fail(c, DD_EINVAL, "precond must be 0 (AS2) or 1 (RAS2)");
+      c->ras = value;
+      break;
+    case DD_OPT_RESTART:
+      if (value < 1 || value > 200) return fail(c, DD_EINVAL, "restart must be in 1..200");
+      if (c->gm_alloc != 0 && c->gm_alloc != value) return fail(c, DD_ESTATE, "restart fixed after the first GMRES solve");
+      c->gm_restart = value;
+      break;
     case DD_OPT_LOCAL_RHS: {
       if (value != 0 && value != 1 && value != 2 && value != 4)
         return fail(c, DD_EINVAL, "local right-hand sides per warp must be 0, 1, 2 or 4");

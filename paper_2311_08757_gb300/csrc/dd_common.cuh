@@ -12,7 +12,7 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // Last-block counters (one per reduction site so that concurrent kernels never share one).
 enum CounterId {
-  CNT_PQ = 0, CNT_RR, CNT_RZ, CNT_INIT, CNT_DOT0, CNT_DOT1, CNT_OUTER0, CNT_OUTER1, CNT_OUTER2, CNT_LOP,
+  CNT_PQ = 0, CNT_RR, CNT_RZ, CNT_INIT, CNT_DOT0, CNT_DOT1, CNT_OUTER0, CNT_OUTER1, CNT_OUTER2, CNT_LOP, CNT_GRAD,
   CNT_NUM = 16
 };
 constexpr int kMaxRedBlocks = 4096;   // partial slots per value

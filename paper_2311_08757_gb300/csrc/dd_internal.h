@@ -162,6 +162,21 @@ struct dd_ctx {
   double* tabA = nullptr;   // K + M_V
   double* tabM = nullptr;   // M
   double* tabS = nullptr;   // K + M_V - sigma M
+  double* tabL = nullptr;   // K + M_V - lambda M (adjoint of the eigenvector)
+  double* qp_part = nullptr;      // quadrature-point reduction partials
+  long long qp_part_len = 0;
+  double* gv[8] = {};             // gradient work vectors
+  double* gscal = nullptr;        // device scalars of the gradient projections
+  // GMRES (restart gm_restart): basis V[0..m], preconditioned directions Z[0..m-1]
+  int krylov = 0;                 // inner solver of the eigen-iterations: 0 PCG, 1 GMRES
+  int gm_restart = 30, gm_alloc = 0;
+  std::vector<double*> gm_V, gm_Z;
+  double* gm_W = nullptr;
+  double** gm_Vptr = nullptr;
+  double** gm_Zptr = nullptr;
+  double *gm_part = nullptr, *gm_h = nullptr, *gm_H = nullptr, *gm_cs = nullptr, *gm_sn = nullptr;
+  double *gm_g = nullptr, *gm_y = nullptr, *gm_res = nullptr, *gm_res_h = nullptr;
+  double* gout = nullptr;         // gradient staging (n_V doubles)
 
   // cell problem
   long long ncell = 0;
@@ -170,6 +185,8 @@ struct dd_ctx {
   int cell_iters = 0;
   double* psi_cell = nullptr;      // natural cell order
   double* wT = nullptr;            // coarse weights per type [type][kpad]: D_i R_i psi
+  double* puT = nullptr;           // partition of unity per type [type][kpad]: D_i
+  int ras = 0;                     // 1: restricted local prolongation (M_RAS2^{-1})
 
   // vectors (padded length plen)
   double *x = nullptr, *r = nullptr, *z = nullptr, *q = nullptr;
@@ -237,7 +254,7 @@ void launch_pupdate(dd_ctx* c, cudaStream_t s);                     // p = z + b
 void launch_matvec_pq(dd_ctx* c, cudaStream_t s);                   // q = A p, pq, alpha
 void launch_fused_pq(dd_ctx* c, cudaStream_t s);                    // p = z + beta p; q = A p; pq (p = 1)
 void launch_xr_update(dd_ctx* c, cudaStream_t s);                   // x, r, rr, done
-void launch_prolong(dd_ctx* c, int init, cudaStream_t s);           // z = ..., rz, beta
+void launch_prolong(dd_ctx* c, int init, cudaStream_t s, double* zout = nullptr);   // z = ..., rz, beta
 void launch_precond(dd_ctx* c, const double* r, double* z, int pcg_mode, cudaStream_t s);
 
 // local solves
@@ -275,6 +292,21 @@ void launch_lop_update(dd_ctx* c, const double* x, const double* w, const double
                        cudaStream_t s);
 void launch_lop_normalize(dd_ctx* c, double* x, double* Mx, cudaStream_t s);
 void launch_set_entry(double* v, long long idx, double val, cudaStream_t s);
+void launch_qp_product(dd_ctx* c, const double* u, const double* v, double* out, cudaStream_t s);
+void launch_dot(dd_ctx* c, const double* a, const double* b, double* out, cudaStream_t s);
+void launch_axpby(dd_ctx* c, double ca, const double* x, double cb_scale, const double* cb, const double* y,
+                  double* out, cudaStream_t s);
+void launch_tab_shift(dd_ctx* c, double shift, double* dst);
+void launch_multidot(dd_ctx* c, int nv, const double* const* V, const double* w, double* h, int accumulate,
+                     cudaStream_t s);
+void launch_multiaxpy(dd_ctx* c, int nv, const double* const* V, const double* coef, double sign, double* w,
+                      cudaStream_t s);
+void launch_scale_by_norm(dd_ctx* c, const double* w, const double* nrm2, double* v, cudaStream_t s);
+void launch_givens(dd_ctx* c, int j, cudaStream_t s);
+void launch_backsolve(dd_ctx* c, int m, cudaStream_t s);
+void launch_gmres_start(dd_ctx* c, const double* nrm2, cudaStream_t s);
+void launch_add_inplace(dd_ctx* c, int n, double* a, const double* b, cudaStream_t s);
+
 
 // timing helpers
 void timer_begin(dd_ctx* c, int kc, cudaStream_t s, cudaEvent_t* e0);

@@ -45,13 +45,13 @@ __device__ double pu_weight(const Geo& g, int pu, int i1, int i2, int a1, int a2
 }
 
 __global__ void k_coarse_weights(Geo g, int pu, const Sub* __restrict__ rep, int ntypes, int kpad,
-                                 const double* __restrict__ psi, double* wT) {
+                                 const double* __restrict__ psi, double* wT, double* puT) {
   const long long total = (long long)ntypes * kpad;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     const int ty = (int)(t / kpad), k = (int)(t % kpad);
     const Sub s = rep[ty];
-    double v = 0.0;
+    double v = 0.0, d = 0.0;
     if (k < s.nloc) {
       const int sj = k % g.nyi, cc = k / g.nyi;
       const int c1 = cc / s.w2, c2 = cc % s.w2;
@@ -61,9 +61,11 @@ __global__ void k_coarse_weights(Geo g, int pu, const Sub* __restrict__ rep, int
       int pc;
       if (g.p == 1) pc = (a1 % g.n) * g.nyi + sj;
       else pc = ((a1 % g.n) * g.n + (a2 % g.n)) * g.nyi + sj;
-      v = pu_weight(g, pu, i1, i2, a1, a2) * psi[pc];
+      d = pu_weight(g, pu, i1, i2, a1, a2);
+      v = d * psi[pc];
     }
-    wT[t] = v;
+    wT[t] = v;     // D_i R_i psi: the coarse basis function of the type
+    puT[t] = d;    // D_i: the partition-of-unity weights (restricted local prolongation)
   }
 }
 
@@ -82,7 +84,7 @@ void launch_coarse_weights(dd_ctx* c) {
   Sub* rep = upload_reps(c);
   const long long total = (long long)c->ntypes * c->kpad;
   (k_coarse_weights<<<grid_blocks(total, 128), 128, 0, c->stream>>>(c->g, c->grid.pu_kind, rep, c->ntypes,
-                                                                   c->kpad, c->psi_cell, c->wT), dd::note_launch());
+                                                                   c->kpad, c->psi_cell, c->wT, c->puT), dd::note_launch());
   DD_CUDA(cudaGetLastError());
   DD_CUDA(cudaFreeAsync(rep, c->stream));
 }

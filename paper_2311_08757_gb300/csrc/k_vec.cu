@@ -5,6 +5,8 @@
 // mesh (Sec. 2) and V is 1-periodic in x (assumption A1), the row of node (a, j) depends
 // only on (a mod n, j).  tab[tap][cls] holds the coupling of class cls to its neighbour at
 // offset tap in {-1,0,1}^d; A_sigma = A - sigma M (Sec. 1.1) is a third table.
+#include <algorithm>
+
 #include "dd_common.cuh"
 
 namespace dd {
@@ -511,10 +513,10 @@ void launch_xr_update(dd_ctx* c, cudaStream_t s) {
 __device__ __forceinline__ double to_f64(float f) { return f32_to_f64(f); }
 __device__ __forceinline__ double to_f64(double d) { return d; }
 
-template <int P, typename TY>
+template <int P, typename TY, bool RAS>
 __global__ void __launch_bounds__(kThreads) k_prolong(Geo g, const int4* __restrict__ axown,
                                                       const int4* __restrict__ subrow, const TY* __restrict__ Y,
-                                                      const double* __restrict__ wT,
+                                                      const double* __restrict__ wT, const double* __restrict__ puT,
                                                       const double* __restrict__ u0, int coarse,
                                                       const double* __restrict__ r, const double* __restrict__ q,
                                                       double* __restrict__ z, int mode, PcgState* st,
@@ -545,7 +547,8 @@ __global__ void __launch_bounds__(kThreads) k_prolong(Geo g, const int4* __restr
           const int s = (P == 1) ? o1 : o1 * g.L + o2;
           const int4 sr = __ldg(subrow + s);
           const int loc = ((P == 1) ? l1 : l1 * sr.z + l2) * g.nyi + nd.slot;
-          ys += Y[(size_t)sr.x + loc];
+          if (RAS) ys += (TY)__ldg(puT + (size_t)sr.y + loc) * Y[(size_t)sr.x + loc];   // R_i^T D_i y_i
+          else ys += Y[(size_t)sr.x + loc];
           if (coarse) cz = fma(__ldg(wT + (size_t)sr.y + loc), __ldg(u0 + s), cz);
         }
       }
@@ -578,19 +581,28 @@ __global__ void __launch_bounds__(kThreads) k_prolong(Geo g, const int4* __restr
   }
 }
 
-void launch_prolong(dd_ctx* c, int mode, cudaStream_t s) {
+void launch_prolong(dd_ctx* c, int mode, cudaStream_t s, double* zout) {
   const Geo& g = c->g;
   const int nb = grid_blocks(interior_work(g), kThreads);
   const int coarse = c->grid.coarse;
   const bool f32 = (c->grid.precision != DD_PREC_FP64);
-#define DD_PROLONG(PP, TY, YP)                                                                             \
-  (k_prolong<PP, TY><<<nb, kThreads, 0, s>>>(g, c->axown, c->subrow, YP, c->wT, c->u0, coarse, c->r, c->q, \
-                                             c->z, mode, c->st, c->red, c->cnt + CNT_RZ),                  \
+  double* z = zout != nullptr ? zout : c->z;
+#define DD_PROLONG(PP, TY, YP, RS)                                                                          \
+  (k_prolong<PP, TY, RS><<<nb, kThreads, 0, s>>>(g, c->axown, c->subrow, YP, c->wT, c->puT, c->u0, coarse, \
+                                                 c->r, c->q, z, mode, c->st, c->red, c->cnt + CNT_RZ),    \
    dd::note_launch())
-  if (g.p == 1) {
-    if (f32) DD_PROLONG(1, float, c->Y32); else DD_PROLONG(1, double, c->Y64);
+  if (c->ras) {
+    if (g.p == 1) {
+      if (f32) DD_PROLONG(1, float, c->Y32, true); else DD_PROLONG(1, double, c->Y64, true);
+    } else {
+      if (f32) DD_PROLONG(2, float, c->Y32, true); else DD_PROLONG(2, double, c->Y64, true);
+    }
   } else {
-    if (f32) DD_PROLONG(2, float, c->Y32); else DD_PROLONG(2, double, c->Y64);
+    if (g.p == 1) {
+      if (f32) DD_PROLONG(1, float, c->Y32, false); else DD_PROLONG(1, double, c->Y64, false);
+    } else {
+      if (f32) DD_PROLONG(2, float, c->Y32, false); else DD_PROLONG(2, double, c->Y64, false);
+    }
   }
 #undef DD_PROLONG
   DD_CUDA(cudaGetLastError());
@@ -677,6 +689,159 @@ void launch_outer_dots(dd_ctx* c, const double* w, const double* Mw, cudaStream_
   const long long n = c->g.plen;
   (k_outer_dots<<<grid_blocks(n, kThreads), kThreads, 0, s>>>(n, w, Mw, c->ost, c->red, c->cnt + CNT_OUTER0),
    dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+}
+
+// ----------------------------------------------------------------------------------------
+// Gradients with respect to V at the cell quadrature points.  M_V is assembled from
+// h^d W_q V_q N(z_q) N(z_q)^T on every box element, with V_q = V_cell_qp[e, q] on every copy
+// of cell element e; so d(u^T M_V v)/dV_cell_qp[e, q] = sum over the copies of e of
+// h^d W_q u_h(z_q) v_h(z_q).  Stage 1: partial sums over chunks of cells (cells in order);
+// stage 2: the chunks in order (deterministic).
+// ----------------------------------------------------------------------------------------
+template <int P>
+__global__ void __launch_bounds__(kThreads) k_qp_partial(Geo g, const double* __restrict__ u,
+                                                         const double* __restrict__ v, int ny, int nq,
+                                                         int cells_per_chunk, int nchunk, double* part) {
+  constexpr int D = P + 1;
+  const long long ncell_el = (long long)(P == 2 ? g.n * g.n : g.n) * ny;
+  const long long per_chunk = ncell_el * nq;
+  const long long total = per_chunk * nchunk;
+  const int Q = g.Q;
+  const long long ncells = (P == 2) ? (long long)g.L * g.L : g.L;
+  double hd = 1.0;
+  for (int k = 0; k < D; ++k) hd *= g.h;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int ch = (int)(t / per_chunk);
+    const long long r = t - (long long)ch * per_chunk;
+    const long long e = r / nq;
+    const int q = (int)(r - e * nq);
+    // quadrature point (qx[, qx2], qy), qy fastest; element (ex[, ex2], ey), ey fastest
+    int qa[3], ea[3];
+    {
+      int rq = q;
+      for (int k = D - 1; k >= 0; --k) {
+        qa[k] = rq % Q;
+        rq /= Q;
+      }
+      long long re = e;
+      ea[D - 1] = (int)(re % ny);
+      re /= ny;
+      for (int k = D - 2; k >= 0; --k) {
+        ea[k] = (int)(re % g.n);
+        re /= g.n;
+      }
+    }
+    double wq = hd, nb[3][2];
+    for (int k = 0; k < D; ++k) {
+      const double xi = c_gpt[qa[k]];
+      wq *= c_gwt[qa[k]];
+      nb[k][0] = 1.0 - xi;
+      nb[k][1] = xi;
+    }
+    const long long c0 = (long long)ch * cells_per_chunk;
+    const long long c1 = min(ncells, c0 + cells_per_chunk);
+    double acc = 0.0;
+    for (long long cc = c0; cc < c1; ++cc) {
+      const int cx1 = (P == 2) ? (int)(cc / g.L) : (int)cc;
+      const int cx2 = (P == 2) ? (int)(cc % g.L) : 0;
+      const int ex1 = cx1 * g.n + ea[0];
+      const int ex2 = (P == 2) ? cx2 * g.n + ea[1] : 0;
+      const int ey = ea[D - 1];
+      double uh = 0.0, vh = 0.0;
+#pragma unroll
+      for (int b = 0; b < (1 << D); ++b) {
+        // local node bits: x1 slowest, y fastest
+        const int by = b & 1;
+        const int b1 = (b >> (D - 1)) & 1;
+        const int b2 = (P == 2) ? (b >> 1) & 1 : 0;
+        const long long col = (P == 2) ? (long long)(ex1 + b1) * g.ncx + (ex2 + b2) : (long long)(ex1 + b1);
+        const long long idx = col * g.Ypad + (ey + by - 1);   // slot -1 / nyi: zero pad or guard
+        double nv = nb[0][b1] * nb[D - 1][by];
+        if (P == 2) nv *= nb[1][b2];
+        uh = fma(nv, u[idx], uh);
+        vh = fma(nv, v[idx], vh);
+      }
+      acc = fma(uh, vh, acc);
+    }
+    part[t] = wq * acc;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_qp_sum(long long n, int nchunk, const double* __restrict__ part,
+                                                     double* out) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int ch = 0; ch < nchunk; ++ch) s += part[(size_t)ch * n + t];
+    out[t] = s;
+  }
+}
+
+void launch_qp_product(dd_ctx* c, const double* u, const double* v, double* out, cudaStream_t s) {
+  const Geo& g = c->g;
+  const int ny = g.nyi + 1;
+  int nq = 1;
+  for (int k = 0; k < g.p + 1; ++k) nq *= g.Q;
+  const long long ncell_el = (long long)(g.p == 2 ? g.n * g.n : g.n) * ny;
+  const long long ncells = (g.p == 2) ? (long long)g.L * g.L : g.L;
+  const long long per = ncell_el * nq;
+  long long nchunk = (152LL * 2048 + per - 1) / per;
+  nchunk = std::max(1LL, std::min(nchunk, ncells));
+  const int cpc = (int)((ncells + nchunk - 1) / nchunk);
+  nchunk = (ncells + cpc - 1) / cpc;
+  if (c->qp_part_len < per * nchunk) {
+    c->qp_part = (double*)dev_alloc(c, sizeof(double) * per * nchunk);
+    c->qp_part_len = per * nchunk;
+  }
+  const long long total = per * nchunk;
+  const int nb = (int)std::min<long long>((total + kThreads - 1) / kThreads, 152LL * 64);
+  if (g.p == 1)
+    (k_qp_partial<1><<<nb, kThreads, 0, s>>>(g, u, v, ny, nq, cpc, (int)nchunk, c->qp_part), dd::note_launch());
+  else
+    (k_qp_partial<2><<<nb, kThreads, 0, s>>>(g, u, v, ny, nq, cpc, (int)nchunk, c->qp_part), dd::note_launch());
+  (k_qp_sum<<<grid_blocks(per, kThreads), kThreads, 0, s>>>(per, (int)nchunk, c->qp_part, out), dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+}
+
+// (a, b) over the padded vectors, deterministic; result in *out (device)
+__global__ void __launch_bounds__(kThreads) k_dot(long long n, const double* __restrict__ a,
+                                                  const double* __restrict__ b, double* out, double* partials,
+                                                  unsigned* counter) {
+  double acc[1] = {0.0};
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    acc[0] = fma(a[t], b[t], acc[0]);
+  double tot[1];
+  if (grid_sum_last<1>(acc, partials, counter, tot) && threadIdx.x == 0) *out = tot[0];
+}
+
+// out = ca x + cb_scale * (*cb) y  (cb read on the device; out may alias x)
+__global__ void __launch_bounds__(kThreads) k_axpby(long long n, double ca, const double* x, double cb_scale,
+                                                    const double* cb, const double* y, double* out) {
+  const double b = cb_scale * (cb != nullptr ? *cb : 1.0);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    out[t] = fma(b, y[t], ca * x[t]);
+}
+
+void launch_dot(dd_ctx* c, const double* a, const double* b, double* out, cudaStream_t s) {
+  const long long n = c->g.plen;
+  (k_dot<<<grid_blocks(n, kThreads), kThreads, 0, s>>>(n, a, b, out, c->red, c->cnt + CNT_GRAD), dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+}
+
+void launch_axpby(dd_ctx* c, double ca, const double* x, double cb_scale, const double* cb, const double* y,
+                  double* out, cudaStream_t s) {
+  const long long n = c->g.plen;
+  (k_axpby<<<grid_blocks(n, kThreads), kThreads, 0, s>>>(n, ca, x, cb_scale, cb, y, out), dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+}
+
+void launch_tab_shift(dd_ctx* c, double shift, double* dst) {
+  const long long n = (long long)c->g.ncls * c->g.ntap;
+  (k_tabS<<<grid_blocks(n, kThreads), kThreads, 0, c->stream>>>(n, c->tabA, c->tabM, shift, dst), dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 

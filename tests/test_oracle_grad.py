@@ -63,6 +63,18 @@ def test_adjoint_solution_defining_equations():
     assert abs(phi @ (M @ wv)) <= 1e-12 * np.linalg.norm(wv)
 
 
+def test_adjoint_iterative_matches_direct():
+    """The iterative adjoint (CG preconditioned by the exact factor of A - sigma M) equals
+    the direct bordered solve."""
+    w = Workload("t", p=1, L=6, n=8, overlap=1, kind="cos1")
+    P = solvers.Problem(q1.Grid.from_workload(w), potential(w), build_prec=False)
+    lam, phi = _exact(P.A, P.M)
+    gphi = np.random.default_rng(5).standard_normal(P.g.ndof)
+    wd = grad.adjoint_solve(P.A, P.M, lam, phi, gphi)
+    wi = grad.adjoint_solve(P.A, P.M, lam, phi, gphi, sigma=P.sigma, direct_limit=0)
+    assert np.abs(wi - wd).max() <= 1e-11 * np.abs(wd).max()
+
+
 def _solve_theta(w, theta):
     wt = w.with_(params={"theta": theta})
     g = q1.Grid.from_workload(wt)
