@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-lopcg", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -435,6 +436,33 @@ def main():
                      "forward_ms": 1e3 * sum(fw) / len(fw), "backward_ms": 1e3 * sum(bw) / len(bw),
                      "adjoint_pcg_iters": its, "lambda": lam5}
 
+    # batched workload: 64 instances, L log-uniform in [16, 2048], own potentials; all
+    # pipelines (cell eigenpair, coarse build, inverse iteration) concurrent on the GPU
+    batch_line = None
+    if not args.no_batch:
+        from ddinputs import batch_workloads
+        wb = batch_workloads()
+        grids_b = [dd.grid_from_workload(wi, precision=dd.PRECISIONS[args.precision]) for wi in wb]
+        Vb = [torch.from_numpy(sample_cell_qp(wi)).to(dev) for wi in wb]
+        with dd.Batch(grids_b, Vb) as bt:
+            runs = {}
+            for label, method, threads in (("concurrent_ipm", "ipm", 0), ("concurrent_lopcg_fused", "lopcg_fused", 0),
+                                           ("one_thread_ipm", "ipm", 1)):
+                bt.ground_states(method, threads=threads)          # warm-up (graphs, workspaces)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rb = bt.ground_states(method, threads=threads)
+                torch.cuda.synchronize()
+                tb = time.perf_counter() - t0
+                runs[label] = {"seconds": tb, "eigenpairs_per_s": len(wb) / tb,
+                               "instance_seconds_min_median_max": [float(rb["seconds"].min()),
+                                                                   float(np.median(rb["seconds"])),
+                                                                   float(rb["seconds"].max())],
+                               "inner_iters_total": int(rb["inner"].sum())}
+        batch_line = {"workload": f"cfg4: {len(wb)} instances, p=1, h=1/32, delta=4, L log-uniform in [16, 2048] "
+                                  f"(sum of unknowns {sum(wi.dofs for wi in wb)}), own 4-term cosine potentials "
+                                  "(seed 4242)", **runs}
+
     # phase breakdown of one step (host timer around each synchronous call)
     def phases(es):
         out = {}
@@ -559,6 +587,7 @@ def main():
             "pcg_iters_per_s": inner_tot / (step_ms / 1e3),
             "si_lopcg_time_to_ground_state": lopcg,
             "differentiable": grad_line,
+            "batched": batch_line,
             "roofline": roofline,
             "roofline_other_kernels": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv)
                                            for kk, vv in v.items() if kk in ("bound", "achieved", "peak", "unit",

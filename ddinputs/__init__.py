@@ -13,5 +13,5 @@ uses no dataset.
 """
 from .potentials import (  # noqa: F401
     Workload, WORKLOADS, potential, sample_cell_qp, gauss_legendre_01, theta_seed, theta8_basis,
-    theta8_qp_basis,
+    theta8_qp_basis, batch_workloads,
 )

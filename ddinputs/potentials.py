@@ -79,7 +79,10 @@ def potential(w: Workload):
         assert w.p == 1
         return lambda x, y: 10.0 * (1.0 + np.cos(2 * np.pi * x)) * (1.0 + 0.5 * np.sin(np.pi * y))
     if k == "cos4":
-        a, b = _cos_series_coeffs(w.seed)
+        if "a" in w.params:
+            a, b = np.asarray(w.params["a"], dtype=float), np.asarray(w.params["b"], dtype=float)
+        else:
+            a, b = _cos_series_coeffs(w.seed)
         if w.p == 1:
             def V(x, y):
                 x = np.asarray(x, dtype=float)
@@ -130,6 +133,23 @@ def potential(w: Workload):
             return out
         return Vt
     raise ValueError(f"unknown potential kind {k!r}")
+
+
+def batch_workloads(seed: int = 4242, count: int = 64, L_min: int = 16, L_max: int = 2048, n: int = 32,
+                    overlap: int = 4):
+    """The batched workload: ``count`` independent 2D instances (h = 1/n, ell = 1) with
+    L_i = round(exp(U(ln L_min, ln L_max))) and each its own 4-term cosine potential
+    (a ~ U(0, 20), b ~ U(-1/2, 1/2) as in cfg2), all drawn from default_rng(seed): the L_i
+    first, then (a_i, b_i) instance by instance."""
+    rng = np.random.default_rng(seed)
+    Ls = np.rint(np.exp(rng.uniform(np.log(L_min), np.log(L_max), count))).astype(int)
+    out = []
+    for i, L in enumerate(Ls):
+        a = rng.uniform(0.0, 20.0, 4)
+        b = rng.uniform(-0.5, 0.5, 4)
+        out.append(Workload(f"cfg4_{i}", p=1, L=int(L), n=n, overlap=overlap, kind="cos4",
+                            params={"a": a.tolist(), "b": b.tolist()}))
+    return out
 
 
 def theta8_basis(j: int, x, y):

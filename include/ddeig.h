@@ -234,6 +234,35 @@ int dd_potential_gradient(dd_ctx* ctx, const double* phi, double lambda, double 
 int dd_eigenpair(const dd_grid* g, const double* V_cell_qp, size_t nV, void* stream,
                  double* lambda_out, double* phi_out, double* sigma_out);
 
+/*
+ * Batched ground states (many independent instances: uneven L, own potential and shift).
+ * dd_batch_create sets up one context per instance (grids[i], V[i] of nV[i] doubles, host or
+ * device, as for dd_setup; all on the caller's stream).  dd_batch_ground_states runs every
+ * instance's whole pipeline -- dd_cell_eigenpair, dd_coarse_build and, from x_0 = 1,
+ *   DD_BATCH_IPM             dd_inverse_iterate (tol_res 1e-8, tol_lam 1e-10, rtol_inner 1e-8)
+ *   DD_BATCH_LOPCG_FUSED     dd_lopcg with DD_INNER_FUSED
+ *   DD_BATCH_LOPCG_ADAPTIVE  dd_lopcg with DD_INNER_ADAPTIVE
+ * -- on a pool of `threads` host threads (<= 0: min(count, 16)), largest instance first, each
+ * instance on its own context stream, so that the instances' kernels overlap on the GPU.
+ * Outputs per instance (arrays of count entries, each may be NULL): lambda, outer and inner
+ * iteration counts, wall seconds from the start of its cell eigenpair to its eigenpair;
+ * phi_out[i] (host or device, ndof_i doubles; phi_out or an entry may be NULL).
+ * Returns the first failing instance's status (the others still run).  Results equal those
+ * of the single-instance calls bit for bit (same kernels, deterministic reductions).
+ * dd_batch_context gives instance i's context (owned by the batch) for options and queries.
+ */
+typedef struct dd_batch dd_batch;
+#define DD_BATCH_IPM            0
+#define DD_BATCH_LOPCG_FUSED    1
+#define DD_BATCH_LOPCG_ADAPTIVE 2
+int dd_batch_create(const dd_grid* grids, const double* const* V, const size_t* nV, int count, void* stream,
+                    dd_batch** out);
+int dd_batch_ground_states(dd_batch* b, int method, int threads, double* lambda_out, double* const* phi_out,
+                           int* outer_out, int* inner_out, double* seconds_out);
+int dd_batch_size(const dd_batch* b);
+dd_ctx* dd_batch_context(dd_batch* b, int i);
+void dd_batch_destroy(dd_batch* b);
+
 /* dd_destroy -- free the context and everything it owns (NULL is ignored). */
 void dd_destroy(dd_ctx* ctx);
 
@@ -276,6 +305,9 @@ int dd_coarse_matrix(dd_ctx* ctx, double* A0_host);
  *   DD_OPT_PRECOND      0 M_AS2^{-1} (symmetric, for CG), 1 M_RAS2^{-1} (restricted: local
  *                       solutions weighted by the partition of unity D_i; GMRES only) [0]
  *   DD_OPT_RESTART      GMRES restart length, 1..200, fixed by the first GMRES solve [30]
+ *   DD_OPT_GEMM_TILE_N  N tile of the mixed local-solve contraction: 128 or 256, 0 = chosen by
+ *                       timing both on the context's operands at dd_coarse_build (cached per
+ *                       problem shape); the result does not depend on it [0]
  *   DD_OPT_LOCAL_RHS    FP64 local solves: subdomains of one type solved together by one warp,
  *                       1, 2 or 4 (capped by shared memory), 0 = default (2 where allowed) [0]; the result
  *                       does not depend on it (same operations per vector) */
@@ -287,6 +319,7 @@ int dd_coarse_matrix(dd_ctx* ctx, double* A0_host);
 #define DD_OPT_KRYLOV      5
 #define DD_OPT_PRECOND     6
 #define DD_OPT_RESTART     7
+#define DD_OPT_GEMM_TILE_N 8
 int dd_set_option(dd_ctx* ctx, int option, int value);
 
 /* Per-kernel-class timing collected while DD_OPT_TIMING = 1: for class k (0 <= k < count),

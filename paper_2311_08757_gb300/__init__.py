@@ -24,7 +24,7 @@ DD_PREC_FP64, DD_PREC_TF32, DD_PREC_BF16 = 0, 1, 2
 DD_PU_EQUAL, DD_PU_DISTANCE = 0, 1
 DD_OP_ASIGMA, DD_OP_MASS, DD_OP_A = 0, 1, 2
 DD_OPT_CHECK_EVERY, DD_OPT_USE_GRAPH, DD_OPT_FLEXIBLE, DD_OPT_TIMING, DD_OPT_LOCAL_RHS = 0, 1, 2, 3, 4
-DD_OPT_KRYLOV, DD_OPT_PRECOND, DD_OPT_RESTART = 5, 6, 7
+DD_OPT_KRYLOV, DD_OPT_PRECOND, DD_OPT_RESTART, DD_OPT_GEMM_TILE_N = 5, 6, 7, 8
 PRECISIONS = {"fp64": DD_PREC_FP64, "tf32": DD_PREC_TF32, "bf16": DD_PREC_BF16}
 DD_INNER_FIXED, DD_INNER_ADAPTIVE, DD_INNER_FUSED = 0, 1, 2
 INNER_MODES = {"fixed": DD_INNER_FIXED, "adaptive": DD_INNER_ADAPTIVE, "fused": DD_INNER_FUSED}
@@ -60,6 +60,12 @@ _SIGS = {
     "dd_potential_gradient": (c_int, [c_void_p, c_void_p, c_double, c_double, c_void_p, c_double, c_void_p,
                                       c_size_t, POINTER(c_int)]),
     "dd_gmres_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int, POINTER(c_int), POINTER(c_double)]),
+    "dd_batch_create": (c_int, [POINTER(dd_grid), POINTER(c_void_p), POINTER(c_size_t), c_int, c_void_p,
+                                POINTER(c_void_p)]),
+    "dd_batch_ground_states": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "dd_batch_size": (c_int, [c_void_p]),
+    "dd_batch_context": (c_void_p, [c_void_p, c_int]),
+    "dd_batch_destroy": (None, [c_void_p]),
     "dd_lopcg": (c_int, [c_void_p, c_void_p, c_int, c_double, c_double, c_int, c_double, POINTER(c_double),
                          POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
     "dd_eigenpair": (c_int, [POINTER(dd_grid), c_void_p, c_size_t, c_void_p, POINTER(c_double), c_void_p,
@@ -329,3 +335,58 @@ class Eigensolver:
 
     def ground_state_lopcg(self, x, inner="fused", **kw):
         return dd_lopcg(self.ctx, x, inner, **kw)
+
+
+DD_BATCH_IPM, DD_BATCH_LOPCG_FUSED, DD_BATCH_LOPCG_ADAPTIVE = 0, 1, 2
+BATCH_METHODS = {"ipm": DD_BATCH_IPM, "lopcg_fused": DD_BATCH_LOPCG_FUSED, "lopcg_adaptive": DD_BATCH_LOPCG_ADAPTIVE}
+
+
+class Batch:
+    """Many independent ground-state problems solved concurrently (dd_batch_*)."""
+
+    def __init__(self, grids, potentials, stream=None):
+        import numpy as np
+        n = len(grids)
+        self._grids = (dd_grid * n)(*grids)
+        self._V = list(potentials)               # keep the buffers alive during set-up
+        ptrs = (c_void_p * n)(*[_ptr(v).value for v in self._V])
+        sizes = (c_size_t * n)(*[(v.numel() if hasattr(v, "numel") else v.size) for v in self._V])
+        h = c_void_p()
+        code = lib().dd_batch_create(self._grids, ptrs, sizes, n, _stream_ptr(stream), byref(h))
+        if code != DD_OK:
+            raise DDError(code, lib().dd_last_error(None).decode())
+        self.handle = h
+        self.count = n
+        self._np = np
+
+    def context(self, i):
+        return c_void_p(lib().dd_batch_context(self.handle, i))
+
+    def ground_states(self, method="ipm", threads=0, phi=None):
+        """Returns dict of per-instance arrays (lambda, outer, inner, seconds); phi: optional list
+        of output buffers (host or device), one per instance."""
+        np = self._np
+        n = self.count
+        lam = np.zeros(n)
+        outer = np.zeros(n, dtype=np.int32)
+        inner = np.zeros(n, dtype=np.int32)
+        sec = np.zeros(n)
+        phis = (c_void_p * n)(*[(_ptr(p).value if p is not None else None) for p in phi]) if phi is not None else None
+        code = lib().dd_batch_ground_states(self.handle, BATCH_METHODS[method] if isinstance(method, str) else method,
+                                            threads, c_void_p(lam.ctypes.data), phis,
+                                            c_void_p(outer.ctypes.data), c_void_p(inner.ctypes.data),
+                                            c_void_p(sec.ctypes.data))
+        if code != DD_OK:
+            raise DDError(code, "batched ground states failed")
+        return {"lambda": lam, "outer": outer, "inner": inner, "seconds": sec}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().dd_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -378,7 +378,7 @@ int gmres_run(dd_ctx* c, const double* b, double rtol, int maxit, int* iters, do
     DD_CUDA(cudaMemcpyAsync(c->gm_Vptr, c->gm_V.data(), sizeof(double*) * (m + 1), cudaMemcpyHostToDevice, s));
     DD_CUDA(cudaMemcpyAsync(c->gm_Zptr, c->gm_Z.data(), sizeof(double*) * m, cudaMemcpyHostToDevice, s));
     c->gm_part = (double*)dev_alloc(c, sizeof(double) * (size_t)(m + 1) * 304);
-    c->gm_h = (double*)dev_alloc(c, sizeof(double) * 2 * ld + 1);
+    c->gm_h = (double*)dev_alloc(c, sizeof(double) * (2 * ld + 1));
     c->gm_H = (double*)dev_alloc(c, sizeof(double) * (size_t)ld * m);
     c->gm_cs = (double*)dev_alloc(c, sizeof(double) * m);
     c->gm_sn = (double*)dev_alloc(c, sizeof(double) * m);
@@ -1183,6 +1183,10 @@ int dd_set_option(dd_ctx* c, int option, int value) {
       if (value < 1 || value > 200) return fail(c, DD_EINVAL, "restart must be in 1..200");
       if (c->gm_alloc != 0 && c->gm_alloc != value) return fail(c, DD_ESTATE, "restart fixed after the first GMRES solve");
       c->gm_restart = value;
+      break;
+    case DD_OPT_GEMM_TILE_N:
+      if (value != 0 && value != 128 && value != 256) return fail(c, DD_EINVAL, "GEMM tile N must be 0, 128 or 256");
+      c->gemm_bn_opt = value;
       break;
     case DD_OPT_LOCAL_RHS: {
       if (value != 0 && value != 1 && value != 2 && value != 4)

@@ -187,6 +187,8 @@ struct dd_ctx {
   double* wT = nullptr;            // coarse weights per type [type][kpad]: D_i R_i psi
   double* puT = nullptr;           // partition of unity per type [type][kpad]: D_i
   int ras = 0;                     // 1: restricted local prolongation (M_RAS2^{-1})
+  int gemm_bn_opt = 0;             // local-solve GEMM N tile: 0 autotuned, 128 or 256
+  int gemm_bn = 0;                 // the N tile chosen by the autotuner (or forced) at set-up
 
   // vectors (padded length plen)
   double *x = nullptr, *r = nullptr, *z = nullptr, *q = nullptr;

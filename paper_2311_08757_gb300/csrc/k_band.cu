@@ -7,6 +7,8 @@
 // identical matrices, because the cells are translated copies and V is periodic (A1); the
 // factors are stored once per type.  Local order: (c1, c2, j) with j fastest, so the
 // half bandwidth is nyi + 1 (p = 1) or w2 nyi + nyi + 1 (p = 2).
+#include <atomic>
+
 #include "dd_band.cuh"
 
 namespace dd {
@@ -188,7 +190,7 @@ static void factor_launch(const Geo&, double* CB, double* RB, double* inv, const
   if (b <= kBandWinMax) {
     const size_t smem = sizeof(double) * ((size_t)(b + 1) * (b + 1) + (b + 1));
     const int threads = (b * b > 2048) ? 512 : 256;
-    static bool attr = false;
+    static std::atomic<bool> attr{false};   // set once per process (idempotent if two threads race)
     if (!attr) {
       DD_CUDA(cudaFuncSetAttribute(k_band_factor_win<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
       attr = true;
@@ -324,7 +326,7 @@ void launch_band_solve_local(dd_ctx* c, const double* r, double* c0, cudaStream_
     DD_K_DISPATCH(K, {
       constexpr int KK = (NV == 0 || NV > 4) ? 1 : KR;
       if (K > KK) throw Error(DD_EINVAL, "local right-hand sides per warp exceed the kernel's");
-      static bool attr_set = false;
+      static std::atomic<bool> attr_set{false};
       if (!attr_set) {
         DD_CUDA(cudaFuncSetAttribute(k_local_solve<NV, PF, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      220 * 1024));

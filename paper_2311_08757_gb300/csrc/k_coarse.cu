@@ -11,6 +11,8 @@
 //          precomputed once, so each solve is 2 log2 N synchronised sweeps).
 //   p = 2: A_0 is block tridiagonal (bandwidth L + 1); its dense inverse is formed once
 //          from a banded Cholesky factor and applied as an FP64 matrix-vector product.
+#include <atomic>
+
 #include "dd_band.cuh"
 
 namespace dd {
@@ -391,7 +393,7 @@ void launch_coarse_solve(dd_ctx* c, cudaStream_t s) {
     const size_t full = sizeof(double) * (2 * (size_t)c->cr_np + 4 * W);   // f + coefficients
     const int staged = full <= 210 * 1024 ? 1 : 0;
     const size_t smem = staged ? full : sizeof(double) * W;
-    static bool attr = false;
+    static std::atomic<bool> attr{false};   // set once per process (idempotent if two threads race)
     if (!attr) {
       DD_CUDA(cudaFuncSetAttribute(k_cr_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
       attr = true;

@@ -16,6 +16,11 @@
 #include <cuda_bf16.h>
 
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+
+#include <atomic>
 
 #include "dd_band.cuh"
 
@@ -25,9 +30,9 @@ struct Tile {
   int type, m0, n0, nend;
 };
 
-template <typename T>
+template <typename T, int BN_ = 256>
 struct TcCfg {
-  static constexpr int BM = 128, BN = 256;
+  static constexpr int BM = 128, BN = BN_;
   static constexpr int BK = 128 / (int)sizeof(T);   // one 128-byte swizzle row
   static constexpr int UK = 32 / (int)sizeof(T);    // K of one tcgen05.mma (32 bytes)
   static constexpr int STAGES = 4;
@@ -126,15 +131,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-constexpr int kTmemCols = 256;
 constexpr int ERR_TMA_WAIT = 1 << 4, ERR_MMA_WAIT = 1 << 5, ERR_ACC_WAIT = 1 << 6;
 
-template <typename T>
+template <typename T, int BN>
 __global__ void __launch_bounds__(128, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const Tile* __restrict__ tiles, int K, int mlimit, int rows_per_type, float* __restrict__ Y,
               int ldy, int* err, const PcgState* st) {
-  using C = TcCfg<T>;
+  using C = TcCfg<T, BN>;
+  constexpr int kTmemCols = BN;   // FP32 accumulator: one column per output column
   if (st != nullptr && st->done) return;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -239,14 +244,18 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 static EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
+  // resolved once (thread-safe initialisation of a function-local static)
+  static const EncodeTiledFn fn = []() -> EncodeTiledFn {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
-    DD_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
-    if (q != cudaDriverEntryPointSuccess || !p) throw Error(DD_ECUDA, "cuTensorMapEncodeTiled unavailable");
-    fn = (EncodeTiledFn)p;
-  }
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return (EncodeTiledFn)p;
+  }();
+  if (!fn) throw Error(DD_ECUDA, "cuTensorMapEncodeTiled unavailable");
   return fn;
 }
 
@@ -262,16 +271,19 @@ static void make_tmap(CUtensorMap* tm, void* base, bool bf16, int inner, long lo
   if (r != CUDA_SUCCESS) throw Error(DD_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
 }
 
-template <typename T>
+template <typename T, int BN = 256>
 static void launch_tc(const CUtensorMap* tA, const CUtensorMap* tB, const Tile* tiles, int ntiles, int K,
                       int mlimit, int rows_per_type, float* Y, int ldy, int* err, const PcgState* st,
                       cudaStream_t s) {
-  static bool attr = false;
+  static std::atomic<bool> attr{false};   // set once per process (idempotent if two threads race)
   if (!attr) {
-    DD_CUDA(cudaFuncSetAttribute(k_tc_gemm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<T>::SMEM));
+    DD_CUDA(cudaFuncSetAttribute(k_tc_gemm<T, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 TcCfg<T, BN>::SMEM));
     attr = true;
   }
-  (k_tc_gemm<T><<<ntiles, 128, TcCfg<T>::SMEM, s>>>(*tA, *tB, tiles, K, mlimit, rows_per_type, Y, ldy, err, st), dd::note_launch());
+  (k_tc_gemm<T, BN><<<ntiles, 128, TcCfg<T, BN>::SMEM, s>>>(*tA, *tB, tiles, K, mlimit, rows_per_type, Y, ldy, err,
+                                                             st),
+   dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 
@@ -353,12 +365,74 @@ __global__ void k_pack(Geo g, const Sub* __restrict__ subs, const int* __restric
   }
 }
 
+// Two output-tile shapes, 128 x 256 and 128 x 128: per output element the K order of the
+// accumulation is the same in both, so the choice changes the speed, not the result.
 struct GemmPlan {
-  CUtensorMap tA, tB;
-  Tile* tiles = nullptr;
-  int ntiles = 0;
+  CUtensorMap tA, tB256, tB128;
+  Tile* tiles[2] = {nullptr, nullptr};   // [0]: 128 x 256 tiles, [1]: 128 x 128 tiles
+  int ntiles[2] = {0, 0};
+  int cap[2] = {0, 0};
   bool bf16 = true;
 };
+
+// Autotuner cache: the faster N tile per problem shape (precision, K, rows per type, subdomain
+// counts per type), measured once per process.
+static std::mutex g_tune_mu;
+static std::map<std::string, int> g_tune_bn;
+
+static void run_gemm(dd_ctx* c, GemmPlan* plan, int bn, const PcgState* st, cudaStream_t s) {
+  const int i = bn == 256 ? 0 : 1;
+  const CUtensorMap* tB = bn == 256 ? &plan->tB256 : &plan->tB128;
+  if (plan->bf16) {
+    if (bn == 256)
+      launch_tc<__nv_bfloat16, 256>(&plan->tA, tB, plan->tiles[i], plan->ntiles[i], c->kpad, c->kpad, c->kpad, c->Y32,
+                                    c->kpad, c->dev_err + 8, st, s);
+    else
+      launch_tc<__nv_bfloat16, 128>(&plan->tA, tB, plan->tiles[i], plan->ntiles[i], c->kpad, c->kpad, c->kpad, c->Y32,
+                                    c->kpad, c->dev_err + 8, st, s);
+  } else {
+    if (bn == 256)
+      launch_tc<float, 256>(&plan->tA, tB, plan->tiles[i], plan->ntiles[i], c->kpad, c->kpad, c->kpad, c->Y32, c->kpad,
+                            c->dev_err + 8, st, s);
+    else
+      launch_tc<float, 128>(&plan->tA, tB, plan->tiles[i], plan->ntiles[i], c->kpad, c->kpad, c->kpad, c->Y32, c->kpad,
+                            c->dev_err + 8, st, s);
+  }
+}
+
+// time both tile shapes on the context's operands (3 launches each after one warm-up)
+static int tune_bn(dd_ctx* c, GemmPlan* plan) {
+  std::string key = std::to_string((int)plan->bf16) + ":" + std::to_string(c->kpad);
+  for (int t = 0; t < c->ntypes; ++t) key += ":" + std::to_string(c->type_count[t]);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_bn.find(key);
+    if (it != g_tune_bn.end()) return it->second;
+  }
+  cudaEvent_t e0, e1;
+  DD_CUDA(cudaEventCreate(&e0));
+  DD_CUDA(cudaEventCreate(&e1));
+  float best = 0.0f;
+  int best_bn = 256;
+  for (int bn : {256, 128}) {
+    run_gemm(c, plan, bn, nullptr, c->stream);
+    DD_CUDA(cudaEventRecord(e0, c->stream));
+    for (int r = 0; r < 3; ++r) run_gemm(c, plan, bn, nullptr, c->stream);
+    DD_CUDA(cudaEventRecord(e1, c->stream));
+    DD_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    DD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (bn == 256 || ms < best) {
+      best = ms;
+      best_bn = bn;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_bn.emplace(key, best_bn);
+  return best_bn;
+}
 
 int gemm_setup(dd_ctx* c) {
   const Geo& g = c->g;
@@ -411,18 +485,26 @@ int gemm_setup(dd_ctx* c) {
   plan->bf16 = bf16;
   const int BK = bf16 ? TcCfg<__nv_bfloat16>::BK : TcCfg<float>::BK;
   make_tmap(&plan->tA, c->Ainv, bf16, kpad, (long long)c->ntypes * kpad, BK, 128);
-  make_tmap(&plan->tB, c->Rpack, bf16, kpad, g.nsub, BK, 256);
-  std::vector<Tile> tl;
+  make_tmap(&plan->tB256, c->Rpack, bf16, kpad, g.nsub, BK, 256);
+  make_tmap(&plan->tB128, c->Rpack, bf16, kpad, g.nsub, BK, 128);
   const int mt = (kpad + 127) / 128;
-  for (int t = 0; t < c->ntypes; ++t) {
-    const int first = c->type_first[t], cnt = c->type_count[t];
-    for (int n0 = 0; n0 < cnt; n0 += 256)
-      for (int m = 0; m < mt; ++m) tl.push_back(Tile{t, m * 128, first + n0, first + cnt});
+  for (int i = 0; i < 2; ++i) {
+    const int bn = i == 0 ? 256 : 128;
+    std::vector<Tile> tl;
+    for (int t = 0; t < c->ntypes; ++t) {
+      const int first = c->type_first[t], cnt = c->type_count[t];
+      for (int n0 = 0; n0 < cnt; n0 += bn)
+        for (int m = 0; m < mt; ++m) tl.push_back(Tile{t, m * 128, first + n0, first + cnt});
+    }
+    if (!plan->tiles[i] || plan->cap[i] < (int)tl.size()) {
+      plan->tiles[i] = (Tile*)dev_alloc(c, sizeof(Tile) * tl.size());
+      plan->cap[i] = (int)tl.size();
+    }
+    plan->ntiles[i] = (int)tl.size();
+    DD_CUDA(cudaMemcpyAsync(plan->tiles[i], tl.data(), sizeof(Tile) * tl.size(), cudaMemcpyHostToDevice, c->stream));
   }
-  if (!plan->tiles || plan->ntiles < (int)tl.size()) plan->tiles = (Tile*)dev_alloc(c, sizeof(Tile) * tl.size());
-  plan->ntiles = (int)tl.size();
-  DD_CUDA(cudaMemcpyAsync(plan->tiles, tl.data(), sizeof(Tile) * tl.size(), cudaMemcpyHostToDevice, c->stream));
   DD_CUDA(cudaStreamSynchronize(c->stream));
+  if (c->gemm_bn == 0) c->gemm_bn = c->gemm_bn_opt != 0 ? c->gemm_bn_opt : tune_bn(c, plan);
   c->gemm_ok = 1;
   return DD_OK;
 }
@@ -441,12 +523,7 @@ void launch_pack(dd_ctx* c, const double* r, double* c0, cudaStream_t s) {
 int launch_gemm(dd_ctx* c, cudaStream_t s) {
   GemmPlan* plan = reinterpret_cast<GemmPlan*>(c->tmapA);
   if (!c->gemm_ok || !plan) return DD_ESTATE;
-  if (plan->bf16)
-    launch_tc<__nv_bfloat16>(&plan->tA, &plan->tB, plan->tiles, plan->ntiles, c->kpad, c->kpad, c->kpad, c->Y32,
-                             c->kpad, c->dev_err + 8, c->st, s);
-  else
-    launch_tc<float>(&plan->tA, &plan->tB, plan->tiles, plan->ntiles, c->kpad, c->kpad, c->kpad, c->Y32, c->kpad,
-                     c->dev_err + 8, c->st, s);
+  run_gemm(c, plan, c->gemm_bn_opt != 0 ? c->gemm_bn_opt : c->gemm_bn, c->st, s);
   return DD_OK;
 }
 

@@ -7,6 +7,8 @@
 // offset tap in {-1,0,1}^d; A_sigma = A - sigma M (Sec. 1.1) is a third table.
 #include <algorithm>
 
+#include <atomic>
+
 #include "dd_common.cuh"
 
 namespace dd {
@@ -399,7 +401,7 @@ void launch_fused_pq(dd_ctx* c, cudaStream_t s) {
   const int ntiles = (g.nxi + kFusedCols - 1) / kFusedCols;
   const int nb = ntiles < 152 * 6 ? ntiles : 152 * 6;
   const size_t smem = sizeof(double) * ((size_t)(kFusedCols + 2) * g.Ypad + 2);
-  static bool attr = false;
+  static std::atomic<bool> attr{false};   // set once per process (idempotent if two threads race)
   if (!attr) {
     DD_CUDA(cudaFuncSetAttribute(k_fused_pq, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr = true;

@@ -1,0 +1,80 @@
+"""Batched ground states (dd_batch_*): many instances with uneven L and their own potentials
+solved concurrently give, instance by instance, the exact ground state (oracle) and the very
+same bits as the single-instance calls."""
+import numpy as np
+import pytest
+
+import paper_2311_08757_gb300 as dd
+from ddinputs import batch_workloads, sample_cell_qp
+from oracle import solvers
+from tests.gpu_util import gpu_vec, host, make_solver, oracle_problem
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch(ws, precision="bf16"):
+    import torch
+    grids = [dd.grid_from_workload(w, precision=dd.PRECISIONS[precision]) for w in ws]
+    Vs = [torch.from_numpy(sample_cell_qp(w)).cuda() for w in ws]
+    return dd.Batch(grids, Vs)
+
+
+@pytest.mark.parametrize("method", ["ipm", "lopcg_fused", "lopcg_adaptive"])
+@pytest.mark.parametrize("precision", ["fp64", "bf16"])
+def test_small_batch_matches_oracle_and_single_calls(method, precision):
+    ws = batch_workloads(seed=11, count=8, L_min=2, L_max=40, n=16, overlap=2)
+    phis = [gpu_vec(np.zeros(w.dofs)) for w in ws]
+    with _batch(ws, precision) as b:
+        res = b.ground_states(method, threads=4, phi=phis)
+    for i, w in enumerate(ws):
+        P = oracle_problem(w, build_prec=False)
+        lam_ex, _ = solvers.exact_ground_state(P.A, P.M, sigma=P.sigma, dense_limit=3000 if w.dofs <= 3000 else 0)
+        assert abs(res["lambda"][i] - lam_ex) <= 1e-10 * abs(lam_ex), (i, w.L)
+        xh = host(phis[i])
+        Mx = P.M @ xh
+        assert np.linalg.norm(P.A @ xh - res["lambda"][i] * Mx) / (abs(lam_ex) * np.linalg.norm(Mx)) <= 1.5e-8
+        # the single-instance path gives the same bits
+        with make_solver(w, precision=precision) as es:
+            es.prepare()
+            x = gpu_vec(np.ones(w.dofs))
+            if method == "ipm":
+                lam, outer, tot, mx = dd.dd_inverse_iterate(es.ctx, x)
+            else:
+                lam, outer, tot, mx = dd.dd_lopcg(es.ctx, x, method.split("_")[1])
+        assert lam == res["lambda"][i] and outer == res["outer"][i] and tot == res["inner"][i]
+        assert np.array_equal(host(x), xh)
+
+
+def test_full_batched_workload():
+    """The 64-instance workload (L log-uniform in [16, 2048], h = 1/32, delta = 4): every
+    instance converges with residual eta <= 1e-8, the smallest ones match the oracle, and the
+    largest ones match their single-instance solves bit for bit."""
+    import torch
+    ws = batch_workloads()
+    order = np.argsort([w.L for w in ws])
+    with _batch(ws) as b:
+        res = b.ground_states("ipm")
+        for i, w in enumerate(ws):
+            ctx = b.context(i)
+            x = torch.ones(w.dofs, dtype=torch.float64, device="cuda")
+            # eta of the returned pair from the instance's own operators
+            lam, *_ = dd.dd_inverse_iterate(ctx, x)
+            assert lam == res["lambda"][i]
+            Ax = torch.empty_like(x)
+            Mx = torch.empty_like(x)
+            dd.dd_apply_operator(ctx, dd.DD_OP_A, x, Ax)
+            dd.dd_apply_operator(ctx, dd.DD_OP_MASS, x, Mx)
+            eta = float(torch.linalg.norm(Ax - lam * Mx) / (abs(lam) * torch.linalg.norm(Mx)))
+            assert eta <= 1.5e-8, (i, w.L)
+    for i in order[:3]:
+        w = ws[i]
+        P = oracle_problem(w, build_prec=False)
+        lam_ex, _ = solvers.exact_ground_state(P.A, P.M, sigma=P.sigma, dense_limit=0)
+        assert abs(res["lambda"][i] - lam_ex) <= 1e-10 * abs(lam_ex)
+    for i in order[-2:]:
+        w = ws[i]
+        with make_solver(w, precision="bf16") as es:
+            es.prepare()
+            x = gpu_vec(np.ones(w.dofs))
+            lam, outer, tot, mx = dd.dd_inverse_iterate(es.ctx, x)
+        assert lam == res["lambda"][i] and tot == res["inner"][i]

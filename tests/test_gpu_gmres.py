@@ -1,0 +1,114 @@
+"""The restricted two-level Schwarz preconditioner M_RAS2^{-1} and right-preconditioned GMRES
+through the C ABI against the oracle: the preconditioner element by element, GMRES iteration
+counts and true residuals, and the ground state with GMRES + RAS2 inner solves (inverse
+iteration, SI-LOPCG) and with M_RAS2^{-1} as the fused LOPCG preconditioner (Sec. 4.3)."""
+import numpy as np
+import pytest
+
+import paper_2311_08757_gb300 as dd
+from ddinputs import Workload, WORKLOADS
+from oracle import solvers
+from tests.gpu_util import gpu_vec, host, make_solver, oracle_problem, rel_err
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "cfg1": WORKLOADS["cfg1"],
+    "cfg2_small": WORKLOADS["cfg2_small"],
+    "p2_types": Workload("p2_types", p=2, L=3, n=6, overlap=2, kind="asym3"),
+    "L2": Workload("L2", p=1, L=2, n=8, overlap=3, kind="cos1"),
+}
+
+
+def _ras_solver(w, precision="fp64", pu="equal"):
+    es = make_solver(w, precision=precision, pu=pu)
+    es.prepare()
+    dd.dd_set_option(es.ctx, dd.DD_OPT_PRECOND, 1)
+    return es
+
+
+@pytest.mark.parametrize("pu", ["equal", "distance"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_ras2_preconditioner(name, pu):
+    w = CASES[name]
+    P = oracle_problem(w, pu=pu)
+    P.prec.restricted = True
+    r = np.random.default_rng(8).standard_normal(w.dofs)
+    with _ras_solver(w, pu=pu) as es:
+        z = gpu_vec(np.zeros(w.dofs))
+        dd.dd_apply_preconditioner(es.ctx, gpu_vec(r), z)
+        assert rel_err(host(z), P.prec(r)) < 1e-10
+        # back to the additive form
+        dd.dd_set_option(es.ctx, dd.DD_OPT_PRECOND, 0)
+        dd.dd_apply_preconditioner(es.ctx, gpu_vec(r), z)
+        P.prec.restricted = False
+        assert rel_err(host(z), P.prec(r)) < 1e-10
+
+
+@pytest.mark.parametrize("precond", [1, 0])
+@pytest.mark.parametrize("name", list(CASES))
+def test_gmres_solve_matches_oracle(name, precond):
+    w = CASES[name]
+    P = oracle_problem(w)
+    P.prec.restricted = bool(precond)
+    b = np.random.default_rng(12).standard_normal(w.dofs)
+    _, it_o, _ = solvers.gmres(P.Asig, b, None, P.prec, 1e-8, 30)
+    with make_solver(w) as es:
+        es.prepare()
+        dd.dd_set_option(es.ctx, dd.DD_OPT_PRECOND, precond)
+        x = gpu_vec(np.zeros(w.dofs))
+        it, rel = dd.dd_gmres_solve(es.ctx, gpu_vec(b), x, rtol=1e-8)
+    assert abs(it - it_o) <= 1
+    xh = host(x)
+    assert np.linalg.norm(b - P.Asig @ xh) <= 1.01e-8 * np.linalg.norm(b)
+    assert rel <= 1e-8
+
+
+def test_gmres_restart_initial_guess_and_errors():
+    w = CASES["cfg2_small"]
+    P = oracle_problem(w)
+    P.prec.restricted = True
+    b = np.random.default_rng(13).standard_normal(w.dofs)
+    with make_solver(w) as es:
+        es.prepare()
+        dd.dd_set_option(es.ctx, dd.DD_OPT_PRECOND, 1)
+        dd.dd_set_option(es.ctx, dd.DD_OPT_RESTART, 5)
+        x = gpu_vec(np.zeros(w.dofs))
+        it, rel = dd.dd_gmres_solve(es.ctx, gpu_vec(b), x, rtol=1e-8)
+        _, it_o, _ = solvers.gmres(P.Asig, b, None, P.prec, 1e-8, 5)
+        assert abs(it - it_o) <= 1 and rel <= 1e-8
+        with pytest.raises(dd.DDError) as e:          # restart fixed after the first solve
+            dd.dd_set_option(es.ctx, dd.DD_OPT_RESTART, 10)
+        assert e.value.code == dd.DD_ESTATE
+        # an initial guess: the residual is measured from it
+        x0 = gpu_vec(0.5 * host(x))
+        it2, rel2 = dd.dd_gmres_solve(es.ctx, gpu_vec(b), x0, rtol=1e-8)
+        xh = host(x0)
+        assert rel2 <= 1e-8
+        assert np.linalg.norm(b - P.Asig @ xh) <= 1e-8 * np.linalg.norm(b - 0.5 * (P.Asig @ host(x)))
+        with pytest.raises(dd.DDError) as e:          # CG with the unsymmetric preconditioner
+            dd.dd_pcg_solve(es.ctx, gpu_vec(b), gpu_vec(np.zeros(w.dofs)))
+        assert e.value.code == dd.DD_EINVAL
+        with pytest.raises(dd.DDError) as e:
+            dd.dd_gmres_solve(es.ctx, gpu_vec(b), gpu_vec(np.zeros(w.dofs)), rtol=1e-12, maxit=3)
+        assert e.value.code == dd.DD_EMAXIT
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16"])
+@pytest.mark.parametrize("name", ["cfg1", "cfg2_small", "p2_types"])
+def test_ground_state_with_gmres_ras2(name, prec):
+    w = CASES[name]
+    P = oracle_problem(w, build_prec=False)
+    lam_ex, _ = solvers.exact_ground_state(P.A, P.M, sigma=P.sigma, dense_limit=3000 if w.dofs <= 3000 else 0)
+    with _ras_solver(w, precision=prec) as es:
+        dd.dd_set_option(es.ctx, dd.DD_OPT_KRYLOV, 1)
+        for run in ("ipm", "lopcg_adaptive", "lopcg_fused"):
+            x = gpu_vec(np.ones(w.dofs))
+            if run == "ipm":
+                lam, *_ = dd.dd_inverse_iterate(es.ctx, x)
+            else:
+                lam, *_ = dd.dd_lopcg(es.ctx, x, run.split("_")[1])
+            assert abs(lam - lam_ex) <= 1e-10 * abs(lam_ex), run
+            xh = host(x)
+            Mx = P.M @ xh
+            assert np.linalg.norm(P.A @ xh - lam * Mx) / (abs(lam) * np.linalg.norm(Mx)) <= 1.5e-8, run
