@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-lopcg", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -225,9 +226,15 @@ def roofline_entry(name, model, ms_total, nlaunch, peaks, peak_src, precision):
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the current kernels
-# from one ncu capture of this workload (profiles/top_kernels_cfg2_bench.md); None when the
-# kernel changed after the capture.
-TRAFFIC = {}
+# from one ncu capture of this workload (profiles/top_kernels_cfg2_bench.md,
+# profiles/local_solve_fp64_cfg2.md); a kernel changed since its capture is left out.
+TRAFFIC = {
+    "stencil_Asigma": (33.65 + 0.52) * 1e6,
+    "prolong_sum": (44.66 + 0.13) * 1e6,
+    "xr_update": (67.13 + 0.64) * 1e6,
+    "pack_restrict": (16.88 + 0.00) * 1e6,
+    "local_solve_fp64": (18.77 + 0.00) * 1e6,
+}
 
 
 # ----------------------------------------------------------------------------------------
@@ -463,6 +470,40 @@ def main():
                                   f"(sum of unknowns {sum(wi.dofs for wi in wb)}), own 4-term cosine potentials "
                                   "(seed 4242)", **runs}
 
+    # the d = 3 workload (p = 2, L = 64, h = 1/16, delta = 2, Gaussian wells; 15.7M unknowns,
+    # 4096 subdomains of 9 types): mixed form, same step as the headline
+    d3_line = None
+    if not args.no_3d:
+        w3 = WORKLOADS["cfg3"]
+        V3 = torch.from_numpy(sample_cell_qp(w3)).to(dev)
+        es3 = dd.Eigensolver(dd.grid_from_workload(w3, precision=dd.PRECISIONS[args.precision]), V3)
+        x3 = torch.empty(w3.dofs, dtype=torch.float64, device=dev)
+
+        def step3():
+            dd.dd_set_potential(es3.ctx, V3)
+            dd.dd_cell_eigenpair(es3.ctx)
+            dd.dd_coarse_build(es3.ctx)
+            x3.fill_(1.0)
+            return dd.dd_inverse_iterate(es3.ctx, x3)
+
+        step3()
+        torch.cuda.synchronize()
+        ts3 = []
+        for _ in range(2):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r3 = step3()
+            e1.record()
+            torch.cuda.synchronize()
+            ts3.append(e0.elapsed_time(e1))
+        d3_line = {"workload": f"cfg3: p=2, L=64, h=1/16, delta=2, dofs={w3.dofs}, 4096 subdomains, Gaussian-well "
+                               "lattice", "precision": args.precision, "ms_per_ground_state": sum(ts3) / len(ts3),
+                   "lambda": r3[0], "outer_iters": r3[1], "inner_iters_total": r3[2]}
+        es3.close()
+
     # phase breakdown of one step (host timer around each synchronous call)
     def phases(es):
         out = {}
@@ -588,6 +629,7 @@ def main():
             "si_lopcg_time_to_ground_state": lopcg,
             "differentiable": grad_line,
             "batched": batch_line,
+            "d3": d3_line,
             "roofline": roofline,
             "roofline_other_kernels": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv)
                                            for kk, vv in v.items() if kk in ("bound", "achieved", "peak", "unit",

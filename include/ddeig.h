@@ -61,6 +61,9 @@ extern "C" {
 #define DD_PREC_FP64 0      /* local solves by FP64 banded Cholesky (plain method) */
 #define DD_PREC_TF32 1      /* dense local inverses, TF32 tensor-core GEMM, FP32 accumulate */
 #define DD_PREC_BF16 2      /* dense local inverses, BF16 tensor-core GEMM, FP32 accumulate */
+#define DD_PREC_FP8  3      /* dense local inverses, FP8 (E4M3) tensor-core GEMM, FP32 accumulate;
+                               A_T^{-1} scaled per type and R_i r per subdomain to the E4M3 range
+                               before rounding, the product scaled back in the GEMM's epilogue */
 
 /* Partition of unity D_i (Sec. 2.2 equal weights; Sec. 4.1.2 distance based). */
 #define DD_PU_EQUAL    0
@@ -334,8 +337,9 @@ long long dd_kernel_launch_count(void);
 
 /* Self-test of the tensor-core contraction used for the local solves (no paper counterpart;
  * it checks the kernel in isolation): D[n][m] = sum_k A[m][k] B[n][k] for host row-major
- * A (M x K) and B (N x K), rounded to BF16 (precision = DD_PREC_BF16, nearest even) or
- * read as TF32 (DD_PREC_TF32), FP32 accumulation; D is host N x M row-major.  Allocates and
+ * A (M x K) and B (N x K), rounded to BF16 (precision = DD_PREC_BF16, nearest even), to
+ * E4M3 (DD_PREC_FP8, nearest even, saturating; unscaled) or read as TF32 (DD_PREC_TF32),
+ * FP32 accumulation; D is host N x M row-major.  Allocates and
  * frees its own device buffers.  DD_ETIMEOUT if a bounded device wait expired. */
 int dd_tc_gemm_test(int precision, int M, int N, int K, const float* A_host, const float* B_host, float* D_host);
 

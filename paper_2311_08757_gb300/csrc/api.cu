@@ -174,7 +174,10 @@ void build_subdomains(dd_ctx* c) {
     c->nloc_max = std::max(c->nloc_max, c->type_nloc[t]);
     w2max = std::max(w2max, c->type_w2[t]);
   }
-  c->kpad = (c->nloc_max + 63) / 64 * 64;
+  // K of the local contraction: whole 128-byte swizzle rows of the operand type (64 BF16,
+  // 32 TF32, 128 E4M3 values)
+  const int kq = c->grid.precision == DD_PREC_FP8 ? 128 : 64;
+  c->kpad = (c->nloc_max + kq - 1) / kq * kq;
   c->band = (g.p == 1) ? g.nyi + 1 : w2max * g.nyi + g.nyi + 1;
   c->subs = (Sub*)dev_alloc(c, sizeof(Sub) * g.nsub);
   c->slot_of_sub = (int*)dev_alloc(c, sizeof(int) * g.nsub);
@@ -531,7 +534,7 @@ int dd_setup(const dd_grid* gr, const double* V, size_t nV, void* stream, dd_ctx
   if (G.overlap < 1 || 2 * G.overlap >= G.n) return fail(nullptr, DD_EINVAL, "need 1 <= overlap and 2 overlap < n");
   if (G.quad_pts < 1 || G.quad_pts > dd::kMaxQ) return fail(nullptr, DD_EINVAL, "quad_pts must be 1..4");
   if (G.pu_kind != DD_PU_EQUAL && G.pu_kind != DD_PU_DISTANCE) return fail(nullptr, DD_EINVAL, "bad pu_kind");
-  if (G.precision < DD_PREC_FP64 || G.precision > DD_PREC_BF16) return fail(nullptr, DD_EINVAL, "bad precision");
+  if (G.precision < DD_PREC_FP64 || G.precision > DD_PREC_FP8) return fail(nullptr, DD_EINVAL, "bad precision");
   if (G.coarse != 0 && G.coarse != 1) return fail(nullptr, DD_EINVAL, "coarse must be 0 or 1");
   size_t expect = (size_t)ny;
   for (int k = 0; k < G.p; ++k) expect *= (size_t)G.n;
@@ -898,11 +901,11 @@ int dd_lopcg(dd_ctx* c, double* x, int inner, double tol_res, double tol_lam, in
       c->lop_red = (double*)dev_alloc(c, sizeof(double) * kMaxRedBlocks * 15);
       for (double*& v : c->lop) v = alloc_vec(c);
     }
-    // work vectors: iterate, previous iterate, spare; their A_sigma- and M-images; the
-    // images of w; the outer residual
+    // work vectors: iterate, previous iterate, spare; their A_sigma- and M-images (and two
+    // spares for the next images); the images of w; the outer residual
     double *X = c->lop[0], *XP = c->lop[1], *T = c->lop[2];
     double *AX = c->lop[3], *AXP = c->lop[4], *MX = c->lop[5], *MXP = c->lop[6];
-    double *AW = c->lop[7], *MW = c->lop[8], *RO = c->lop[9];
+    double *AW = c->lop[7], *MW = c->lop[8], *RO = c->lop[9], *AT = c->lop[10], *MT = c->lop[11];
     for (double* v : c->lop) DD_CUDA(cudaMemsetAsync(v, 0, sizeof(double) * g.plen, s));
     DD_CUDA(cudaMemsetAsync(c->ost, 0, sizeof(OuterState), s));
     DD_CUDA(cudaMemsetAsync(c->lst, 0, sizeof(LopState), s));
@@ -912,14 +915,18 @@ int dd_lopcg(dd_ctx* c, double* x, int inner, double tol_res, double tol_lam, in
     TIMED(KC_OUTER, s, launch_stencil(c, c->tabM, XP, MXP, s));
     TIMED(KC_OUTER, s, launch_lop_normalize(c, XP, MXP, s));
     TIMED(KC_OUTER, s, launch_stencil(c, c->tabS, XP, AXP, s));
-    // x_1 from the caller, B-normalised; A_sigma x_1, rho and the outer residual
+    // x_1 from the caller, B-normalised; A_sigma x_1, rho and the outer residual (explicit)
+    auto explicit_images = [&]() {
+      TIMED(KC_OUTER, s, launch_stencil(c, c->tabM, X, MX, s));
+      TIMED(KC_OUTER, s, launch_lop_normalize(c, X, MX, s));
+      TIMED(KC_OUTER, s, launch_outer_residual(c, X, MX, AX, s, RO));
+      read_outer(c);
+      if (c->ost_h->status != 0) throw Error(c->ost_h->status, "iterate has zero M-norm");
+    };
     load_vec(c, x, X);
-    TIMED(KC_OUTER, s, launch_stencil(c, c->tabM, X, MX, s));
-    TIMED(KC_OUTER, s, launch_lop_normalize(c, X, MX, s));
-    TIMED(KC_OUTER, s, launch_outer_residual(c, X, MX, AX, s, RO));
-    read_outer(c);
-    if (c->ost_h->status != 0) throw Error(c->ost_h->status, "start vector has zero M-norm");
+    explicit_images();
     double lam = c->ost_h->xAx, rr = c->ost_h->rr, mm = c->ost_h->mm;
+    bool exact = true;   // images computed by stencils (not carried as combinations)
     double rho_prev = std::numeric_limits<double>::infinity(), rho = sigma + lam;
     int k = 0, inner_tot = 0, inner_max = 0, status = DD_EMAXIT;
     for (k = 0; k <= maxit_outer; ++k) {
@@ -927,8 +934,23 @@ int dd_lopcg(dd_ctx* c, double* x, int inner, double tol_res, double tol_lam, in
       if (!std::isfinite(rho)) throw Error(DD_ENAN, "non-finite Rayleigh quotient");
       const double eta = std::sqrt(rr / mm) / std::fabs(rho);
       if (eta <= tol_res && std::fabs(rho - rho_prev) <= tol_lam * std::fabs(rho)) {
-        status = DD_OK;
-        break;
+        if (exact) {
+          status = DD_OK;
+          break;
+        }
+        // confirm on images recomputed from x (the carried ones hold rounding of k steps)
+        explicit_images();
+        exact = true;
+        lam = c->ost_h->xAx;
+        rr = c->ost_h->rr;
+        mm = c->ost_h->mm;
+        const double rho_e = sigma + lam;
+        const double eta_e = std::sqrt(rr / mm) / std::fabs(rho_e);
+        if (eta_e <= tol_res && std::fabs(rho_e - rho_prev) <= tol_lam * std::fabs(rho_e)) {
+          rho = rho_e;
+          status = DD_OK;
+          break;
+        }
       }
       if (k == maxit_outer) break;
       // inner step: A_sigma w = r_o inexactly (Algorithm 1), or w = M^{-1} r_o (fused)
@@ -951,36 +973,40 @@ int dd_lopcg(dd_ctx* c, double* x, int inner, double tol_res, double tol_lam, in
       }
       inner_tot += it;
       inner_max = std::max(inner_max, it);
-      TIMED(KC_OUTER, s, launch_stencil(c, c->tabS, W, AW, s));
-      TIMED(KC_OUTER, s, launch_stencil(c, c->tabM, W, MW, s));
-      // Rayleigh-Ritz on span{x_k, w_k, x_{k-1}} and x_{k+1} = S c
+      TIMED(KC_OUTER, s, launch_stencil2(c, c->tabS, c->tabM, W, AW, MW, s));
+      // Rayleigh-Ritz on span{x_k, w_k, x_{k-1}}; x_{k+1} = S c with its images and r_o
       const double* S[3] = {X, W, XP};
       const double* AS[3] = {AX, AW, AXP};
       const double* MS[3] = {MX, MW, MXP};
       TIMED(KC_RR, s, launch_lop_gram(c, S, AS, MS, 1e-10, s));
-      TIMED(KC_RR, s, launch_lop_update(c, X, W, XP, T, s));
-      // rotate: x_{k-1} <- x_k, x_k <- x_{k+1}; the images of x_k become those of x_{k-1}
+      TIMED(KC_RR, s, launch_lop_update3(c, S, AS, MS, T, AT, MT, RO, s));
+      // rotate: x_{k-1} <- x_k, x_k <- x_{k+1}, and the same for the images
       double* t0 = XP;
       XP = X;
       X = T;
       T = t0;
-      std::swap(AX, AXP);
-      std::swap(MX, MXP);
-      TIMED(KC_OUTER, s, launch_stencil(c, c->tabM, X, MX, s));
-      TIMED(KC_OUTER, s, launch_lop_normalize(c, X, MX, s));
-      TIMED(KC_OUTER, s, launch_outer_residual(c, X, MX, AX, s, RO));
+      t0 = AXP;
+      AXP = AX;
+      AX = AT;
+      AT = t0;
+      t0 = MXP;
+      MXP = MX;
+      MX = MT;
+      MT = t0;
       DD_CUDA(cudaMemcpyAsync(c->lst_h, c->lst, sizeof(LopState), cudaMemcpyDeviceToHost, s));
-      read_outer(c);
+      DD_CUDA(cudaStreamSynchronize(s));
+      if (c->timing) timer_collect(c);
       if (c->lst_h->status != 0) throw Error(c->lst_h->status, "Rayleigh-Ritz step failed");
-      if (c->ost_h->status != 0) throw Error(c->ost_h->status, "outer normalisation failed");
       rho_prev = rho;
-      lam = c->ost_h->xAx;
-      rr = c->ost_h->rr;
-      mm = c->ost_h->mm;
+      lam = c->lst_h->theta;
+      rr = c->lst_h->rr;
+      mm = c->lst_h->mm;
+      exact = false;
     }
     // keep the buffer roles for the next call
     c->lop[0] = X; c->lop[1] = XP; c->lop[2] = T;
     c->lop[3] = AX; c->lop[4] = AXP; c->lop[5] = MX; c->lop[6] = MXP;
+    c->lop[10] = AT; c->lop[11] = MT;
     store_vec(c, X, x);
     DD_CUDA(cudaStreamSynchronize(s));
     if (lambda_out) *lambda_out = rho;

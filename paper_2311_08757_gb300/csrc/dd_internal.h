@@ -91,6 +91,7 @@ struct LopState {
   double GA[6], GB[6], sums[3];
   double c[3];
   double theta;
+  double rr, mm, xmx;   // after the update: ||A_sigma x - theta M x||^2, ||M x||^2, x^T M x
   int m, status;
 };
 
@@ -188,6 +189,9 @@ struct dd_ctx {
   double* puT = nullptr;           // partition of unity per type [type][kpad]: D_i
   int ras = 0;                     // 1: restricted local prolongation (M_RAS2^{-1})
   int gemm_bn_opt = 0;             // local-solve GEMM N tile: 0 autotuned, 128 or 256
+  float* ysc = nullptr;            // FP8: per packed row 1 / (s_i s_T) (undoes the operand scales)
+  float* ascale = nullptr;         // FP8: per type 1 / s_T
+  double* ascale64 = nullptr;      // FP8: per type s_T = 448 / max|A_T^{-1}|
   int gemm_bn = 0;                 // the N tile chosen by the autotuner (or forced) at set-up
 
   // vectors (padded length plen)
@@ -228,7 +232,7 @@ struct dd_ctx {
   dd::LopState* lst = nullptr;     // SI-LOPCG step scalars (device)
   dd::LopState* lst_h = nullptr;   // pinned mirror
   double* lop_red = nullptr;       // partials of the 15 Gram sums
-  double* lop[10] = {};            // SI-LOPCG work vectors (padded layout)
+  double* lop[12] = {};            // SI-LOPCG work vectors (padded layout)
 
   // graph of one block of PCG iterations
   cudaGraphExec_t graph = nullptr;
@@ -293,6 +297,10 @@ void launch_lop_gram(dd_ctx* c, const double* const S[3], const double* const AS
 void launch_lop_update(dd_ctx* c, const double* x, const double* w, const double* xp, double* out,
                        cudaStream_t s);
 void launch_lop_normalize(dd_ctx* c, double* x, double* Mx, cudaStream_t s);
+void launch_lop_update3(dd_ctx* c, const double* const S[3], const double* const AS[3], const double* const MS[3],
+                        double* x, double* Ax, double* Mx, double* ro, cudaStream_t s);
+void launch_stencil2(dd_ctx* c, const double* tab1, const double* tab2, const double* x, double* y1, double* y2,
+                     cudaStream_t s);
 void launch_set_entry(double* v, long long idx, double val, cudaStream_t s);
 void launch_qp_product(dd_ctx* c, const double* u, const double* v, double* out, cudaStream_t s);
 void launch_dot(dd_ctx* c, const double* a, const double* b, double* out, cudaStream_t s);

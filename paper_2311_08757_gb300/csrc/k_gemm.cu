@@ -14,7 +14,9 @@
 // device word, stops issuing work and returns after freeing its tensor memory.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -93,7 +95,7 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
-// instruction descriptor: D = F32, A/B format fmt (1 = BF16, 2 = TF32), K-major both, M = 128, N = 256
+// instruction descriptor: D = F32, A/B format fmt (1 = BF16, 2 = TF32, 0 = E4M3), K-major both, M = 128, N = BN
 __host__ __device__ constexpr uint32_t mma_idesc(uint32_t fmt, int M, int N) {
   return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
@@ -118,6 +120,22 @@ __device__ __forceinline__ void mma_issue<float>(uint32_t tmem, uint64_t a, uint
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
+template <>
+__device__ __forceinline__ void mma_issue<__nv_fp8_e4m3>(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                                         uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+// operand format field of the instruction descriptor: BF16 1 (kind::f16), TF32 2 (kind::tf32),
+// E4M3 0 (kind::f8f6f4)
+template <typename T>
+constexpr uint32_t mma_fmt() {
+  return sizeof(T) == 2 ? 1u : (sizeof(T) == 4 ? 2u : 0u);
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
 }
@@ -137,7 +155,7 @@ template <typename T, int BN>
 __global__ void __launch_bounds__(128, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const Tile* __restrict__ tiles, int K, int mlimit, int rows_per_type, float* __restrict__ Y,
-              int ldy, int* err, const PcgState* st) {
+              int ldy, int* err, const PcgState* st, const float* __restrict__ ysc) {
   using C = TcCfg<T, BN>;
   constexpr int kTmemCols = BN;   // FP32 accumulator: one column per output column
   if (st != nullptr && st->done) return;
@@ -188,7 +206,7 @@ __global__ void __launch_bounds__(128, 1)
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
-    constexpr uint32_t fmt = sizeof(T) == 2 ? 1u : 2u;
+    constexpr uint32_t fmt = mma_fmt<T>();
     constexpr uint32_t idesc = mma_idesc(fmt, C::BM, C::BN);
     bool ok = true;
     for (int kb = 0; kb < nk && ok; ++kb) {
@@ -223,7 +241,8 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int n = tl.n0 + c0 + j;
-          if (n < tl.nend) Y[(size_t)n * ldy + m] = __uint_as_float(r[j]);
+          // scaled operands (FP8): undo the row scales of A and B
+          if (n < tl.nend) Y[(size_t)n * ldy + m] = ysc != nullptr ? __uint_as_float(r[j]) * ysc[n] : __uint_as_float(r[j]);
         }
       }
     }
@@ -259,13 +278,14 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
-static void make_tmap(CUtensorMap* tm, void* base, bool bf16, int inner, long long rows, int box_inner, int box_rows) {
-  const int es = bf16 ? 2 : 4;
+static void make_tmap(CUtensorMap* tm, void* base, int es, int inner, long long rows, int box_inner, int box_rows) {
   cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)inner * es};
   cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = encode_fn()(tm, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base,
+  const CUtensorMapDataType dt = es == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                : (es == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32);
+  CUresult r = encode_fn()(tm, dt, 2, base,
                            dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) throw Error(DD_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
@@ -274,7 +294,7 @@ static void make_tmap(CUtensorMap* tm, void* base, bool bf16, int inner, long lo
 template <typename T, int BN = 256>
 static void launch_tc(const CUtensorMap* tA, const CUtensorMap* tB, const Tile* tiles, int ntiles, int K,
                       int mlimit, int rows_per_type, float* Y, int ldy, int* err, const PcgState* st,
-                      cudaStream_t s) {
+                      cudaStream_t s, const float* ysc = nullptr) {
   static std::atomic<bool> attr{false};   // set once per process (idempotent if two threads race)
   if (!attr) {
     DD_CUDA(cudaFuncSetAttribute(k_tc_gemm<T, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -282,7 +302,7 @@ static void launch_tc(const CUtensorMap* tA, const CUtensorMap* tB, const Tile* 
     attr = true;
   }
   (k_tc_gemm<T, BN><<<ntiles, 128, TcCfg<T, BN>::SMEM, s>>>(*tA, *tB, tiles, K, mlimit, rows_per_type, Y, ldy, err,
-                                                             st),
+                                                             st, ysc),
    dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
@@ -303,6 +323,18 @@ template <>
 __device__ __forceinline__ float round_fast<float>(double v) {
   return f64_to_tf32(v);
 }
+template <>
+__device__ __forceinline__ double round_fast<double>(double v) {
+  return v;
+}
+
+// E4M3 (saturating, nearest even) of a scaled value
+__device__ __forceinline__ __nv_fp8_e4m3 to_e4m3(double v) {
+  __nv_fp8_e4m3 q;
+  q.__x = __nv_cvt_double_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+  return q;
+}
+constexpr double kE4M3Max = 448.0;   // largest finite E4M3 value
 
 template <typename T, int NV, int PF, int K>
 __global__ void k_local_inverse(const int* __restrict__ nloc, int nmax, int b, const double* __restrict__ CB,
@@ -335,18 +367,40 @@ __global__ void k_local_inverse(const int* __restrict__ nloc, int nmax, int b, c
 // R_i r rounded, subdomain rows in type-sorted order, zero tail up to kpad; the coarse
 // right-hand side c_i = (D_i R_i psi)^T r (Def. 2.1) is formed in FP64 in the same pass.
 // Block per subdomain, warp per local column (the y nodes of a column are contiguous in r).
+// FP8: the row is scaled by s_i = 448 / max|R_i r| before rounding, and 1 / (s_i s_T) (with
+// s_T the scale of the type's inverse) is recorded for the GEMM's epilogue.
 template <typename T>
 __global__ void k_pack(Geo g, const Sub* __restrict__ subs, const int* __restrict__ slot_of,
                        const double* __restrict__ r, int kpad, T* __restrict__ out, const double* __restrict__ wT,
-                       double* c0, const PcgState* st) {
+                       double* c0, const PcgState* st, const float* __restrict__ ascale, float* __restrict__ ysc) {
   if (st != nullptr && st->done) return;
+  constexpr bool FP8 = sizeof(T) == 1;
   const int s = blockIdx.x;
   const Sub sb = subs[s];
-  T* row = out + (size_t)slot_of[s] * kpad;
+  const int slot = slot_of[s];
+  T* row = out + (size_t)slot * kpad;
   const double* wt = wT + (size_t)sb.type * kpad;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  double acc[1] = {0.0};
   const int ncols = sb.w1 * sb.w2;
+  double scale = 1.0;
+  if (FP8) {
+    double mx[1] = {0.0};
+    for (int cc = warp; cc < ncols; cc += nw) {
+      const int c1 = cc / sb.w2, c2 = cc - c1 * sb.w2;
+      const long long base = (g.p == 1) ? (long long)(sb.lo1 + c1) * g.Ypad
+                                        : ((long long)(sb.lo1 + c1) * g.ncx + (sb.lo2 + c2)) * g.Ypad;
+      for (int sj = lane; sj < g.nyi; sj += 32) mx[0] = fmax(mx[0], fabs(r[base + sj]));
+    }
+    __shared__ double s_mx[32];
+    for (int o = 16; o > 0; o >>= 1) mx[0] = fmax(mx[0], __shfl_xor_sync(kFull, mx[0], o));
+    if (lane == 0) s_mx[warp] = mx[0];
+    __syncthreads();
+    double m = 0.0;
+    for (int w = 0; w < nw; ++w) m = fmax(m, s_mx[w]);
+    scale = m > 0.0 ? kE4M3Max / m : 1.0;
+    if (threadIdx.x == 0) ysc[slot] = (float)(ascale[sb.type] / scale);
+  }
+  double acc[1] = {0.0};
   for (int cc = warp; cc < ncols; cc += nw) {
     const int c1 = cc / sb.w2, c2 = cc - c1 * sb.w2;
     const long long base = (g.p == 1) ? (long long)(sb.lo1 + c1) * g.Ypad
@@ -355,14 +409,56 @@ __global__ void k_pack(Geo g, const Sub* __restrict__ subs, const int* __restric
       const int k = cc * g.nyi + sj;
       const double v = r[base + sj];
       acc[0] = fma(wt[k], v, acc[0]);
-      row[k] = round_fast<T>(v);
+      if constexpr (FP8) row[k] = to_e4m3(v * scale);
+      else row[k] = round_fast<T>(v);
     }
   }
-  for (int k = sb.nloc + threadIdx.x; k < kpad; k += blockDim.x) row[k] = round_fast<T>(0.0);
+  for (int k = sb.nloc + threadIdx.x; k < kpad; k += blockDim.x) {
+    if constexpr (FP8) row[k] = to_e4m3(0.0);
+    else row[k] = round_fast<T>(0.0);
+  }
   if (c0 != nullptr) {
     block_sum<1>(acc);
     if (threadIdx.x == 0) c0[s] = acc[0];
   }
+}
+
+// FP8 local inverses: per-type max |A_T^{-1}| (grid = blocks x types), then the scaled rounding
+__global__ void k_type_absmax(const double* __restrict__ a, long long per_type, double* partial) {
+  const int ty = blockIdx.y;
+  const double* at = a + (size_t)ty * per_type;
+  double m = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < per_type;
+       t += (long long)gridDim.x * blockDim.x)
+    m = fmax(m, fabs(at[t]));
+  __shared__ double sm[32];
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(kFull, m, o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sm[wid] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, sm[w]);
+    partial[(size_t)ty * gridDim.x + blockIdx.x] = fmax(sm[0], m);
+  }
+}
+
+__global__ void k_type_scale(const double* __restrict__ partial, int nblk, int ntypes, double* scale,
+                             float* ascale) {
+  const int ty = threadIdx.x;
+  if (ty >= ntypes) return;
+  double m = 0.0;
+  for (int b = 0; b < nblk; ++b) m = fmax(m, partial[(size_t)ty * nblk + b]);
+  const double sc = m > 0.0 ? kE4M3Max / m : 1.0;
+  scale[ty] = sc;
+  ascale[ty] = (float)(1.0 / sc);
+}
+
+__global__ void k_quantize_e4m3(const double* __restrict__ a, long long per_type, int ntypes,
+                                const double* __restrict__ scale, __nv_fp8_e4m3* out) {
+  const long long total = per_type * ntypes;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x)
+    out[t] = to_e4m3(a[t] * scale[t / per_type]);
 }
 
 // Two output-tile shapes, 128 x 256 and 128 x 128: per output element the K order of the
@@ -372,7 +468,7 @@ struct GemmPlan {
   Tile* tiles[2] = {nullptr, nullptr};   // [0]: 128 x 256 tiles, [1]: 128 x 128 tiles
   int ntiles[2] = {0, 0};
   int cap[2] = {0, 0};
-  bool bf16 = true;
+  int es = 2;                            // operand bytes: 1 E4M3, 2 BF16, 4 TF32
 };
 
 // Autotuner cache: the faster N tile per problem shape (precision, K, rows per type, subdomain
@@ -380,29 +476,27 @@ struct GemmPlan {
 static std::mutex g_tune_mu;
 static std::map<std::string, int> g_tune_bn;
 
-static void run_gemm(dd_ctx* c, GemmPlan* plan, int bn, const PcgState* st, cudaStream_t s) {
+template <typename T>
+static void run_gemm_t(dd_ctx* c, GemmPlan* plan, int bn, const PcgState* st, cudaStream_t s, const float* ysc) {
   const int i = bn == 256 ? 0 : 1;
   const CUtensorMap* tB = bn == 256 ? &plan->tB256 : &plan->tB128;
-  if (plan->bf16) {
-    if (bn == 256)
-      launch_tc<__nv_bfloat16, 256>(&plan->tA, tB, plan->tiles[i], plan->ntiles[i], c->kpad, c->kpad, c->kpad, c->Y32,
-                                    c->kpad, c->dev_err + 8, st, s);
-    else
-      launch_tc<__nv_bfloat16, 128>(&plan->tA, tB, plan->tiles[i], plan->ntiles[i], c->kpad, c->kpad, c->kpad, c->Y32,
-                                    c->kpad, c->dev_err + 8, st, s);
-  } else {
-    if (bn == 256)
-      launch_tc<float, 256>(&plan->tA, tB, plan->tiles[i], plan->ntiles[i], c->kpad, c->kpad, c->kpad, c->Y32, c->kpad,
-                            c->dev_err + 8, st, s);
-    else
-      launch_tc<float, 128>(&plan->tA, tB, plan->tiles[i], plan->ntiles[i], c->kpad, c->kpad, c->kpad, c->Y32, c->kpad,
-                            c->dev_err + 8, st, s);
-  }
+  if (bn == 256)
+    launch_tc<T, 256>(&plan->tA, tB, plan->tiles[i], plan->ntiles[i], c->kpad, c->kpad, c->kpad, c->Y32, c->kpad,
+                      c->dev_err + 8, st, s, ysc);
+  else
+    launch_tc<T, 128>(&plan->tA, tB, plan->tiles[i], plan->ntiles[i], c->kpad, c->kpad, c->kpad, c->Y32, c->kpad,
+                      c->dev_err + 8, st, s, ysc);
+}
+
+static void run_gemm(dd_ctx* c, GemmPlan* plan, int bn, const PcgState* st, cudaStream_t s) {
+  if (plan->es == 2) run_gemm_t<__nv_bfloat16>(c, plan, bn, st, s, nullptr);
+  else if (plan->es == 4) run_gemm_t<float>(c, plan, bn, st, s, nullptr);
+  else run_gemm_t<__nv_fp8_e4m3>(c, plan, bn, st, s, c->ysc);
 }
 
 // time both tile shapes on the context's operands (3 launches each after one warm-up)
 static int tune_bn(dd_ctx* c, GemmPlan* plan) {
-  std::string key = std::to_string((int)plan->bf16) + ":" + std::to_string(c->kpad);
+  std::string key = std::to_string(plan->es) + ":" + std::to_string(c->kpad);
   for (int t = 0; t < c->ntypes; ++t) key += ":" + std::to_string(c->type_count[t]);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -434,22 +528,13 @@ static int tune_bn(dd_ctx* c, GemmPlan* plan) {
   return best_bn;
 }
 
-int gemm_setup(dd_ctx* c) {
-  const Geo& g = c->g;
-  const bool bf16 = c->grid.precision == DD_PREC_BF16;
-  const int es = bf16 ? 2 : 4;
+static int prec_bytes(int precision) {
+  return precision == DD_PREC_BF16 ? 2 : (precision == DD_PREC_TF32 ? 4 : 1);
+}
+
+template <typename T>
+static void launch_local_inverse_t(dd_ctx* c, const int* nloc, T* out) {
   const int kpad = c->kpad;
-  if (!c->Ainv) {
-    c->Ainv = dev_alloc(c, (size_t)es * c->ntypes * kpad * kpad);
-    c->Rpack = dev_alloc(c, (size_t)es * g.nsub * kpad);
-    c->Y32 = (float*)dev_alloc(c, sizeof(float) * (size_t)g.nsub * kpad);
-  } else {
-    DD_CUDA(cudaMemsetAsync(c->Ainv, 0, (size_t)es * c->ntypes * kpad * kpad, c->stream));
-  }
-  // local inverses
-  int* nloc = nullptr;
-  DD_CUDA(cudaMallocAsync(&nloc, sizeof(int) * c->ntypes, c->stream));
-  DD_CUDA(cudaMemcpyAsync(nloc, c->type_nloc, sizeof(int) * c->ntypes, cudaMemcpyHostToDevice, c->stream));
   const int K = 1;
   const size_t per = sizeof(double) * (size_t)K * c->nloc_max + band_ring_bytes(c->band);
   const int wpb = per <= 48 * 1024 ? 2 : 1;
@@ -457,24 +542,59 @@ int gemm_setup(dd_ctx* c) {
   const long long jobs = (long long)c->ntypes * ((c->nloc_max + K - 1) / K);
   const int nb = (int)((jobs + wpb - 1) / wpb);
   DD_BAND_DISPATCH(c->band, {
-    {
-      constexpr int KK = 1;
-      if (bf16) {
-        DD_CUDA(cudaFuncSetAttribute(k_local_inverse<__nv_bfloat16, NV, PF, KK>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-        (k_local_inverse<__nv_bfloat16, NV, PF, KK><<<nb, 32 * wpb, smem, c->stream>>>(
-             nloc, c->nloc_max, c->band, c->bandCB, c->bandRB, c->bandInv, c->ntypes, kpad, (__nv_bfloat16*)c->Ainv),
-         dd::note_launch());
-      } else {
-        DD_CUDA(cudaFuncSetAttribute(k_local_inverse<float, NV, PF, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     220 * 1024));
-        (k_local_inverse<float, NV, PF, KK><<<nb, 32 * wpb, smem, c->stream>>>(
-             nloc, c->nloc_max, c->band, c->bandCB, c->bandRB, c->bandInv, c->ntypes, kpad, (float*)c->Ainv),
-         dd::note_launch());
-      }
-    }
+    constexpr int KK = 1;
+    DD_CUDA(cudaFuncSetAttribute(k_local_inverse<T, NV, PF, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 220 * 1024));
+    (k_local_inverse<T, NV, PF, KK><<<nb, 32 * wpb, smem, c->stream>>>(nloc, c->nloc_max, c->band, c->bandCB,
+                                                                       c->bandRB, c->bandInv, c->ntypes, kpad, out),
+     dd::note_launch());
   });
   DD_CUDA(cudaGetLastError());
+}
+
+int gemm_setup(dd_ctx* c) {
+  const Geo& g = c->g;
+  const int es = prec_bytes(c->grid.precision);
+  const int kpad = c->kpad;
+  const long long per_type = (long long)kpad * kpad;
+  if (!c->Ainv) {
+    c->Ainv = dev_alloc(c, (size_t)es * c->ntypes * per_type);
+    c->Rpack = dev_alloc(c, (size_t)es * g.nsub * kpad);
+    c->Y32 = (float*)dev_alloc(c, sizeof(float) * (size_t)g.nsub * kpad);
+    if (es == 1) {
+      c->ysc = (float*)dev_alloc(c, sizeof(float) * g.nsub);
+      c->ascale = (float*)dev_alloc(c, sizeof(float) * c->ntypes);
+      c->ascale64 = (double*)dev_alloc(c, sizeof(double) * c->ntypes);
+    }
+  } else {
+    DD_CUDA(cudaMemsetAsync(c->Ainv, 0, (size_t)es * c->ntypes * per_type, c->stream));
+  }
+  // local inverses
+  int* nloc = nullptr;
+  DD_CUDA(cudaMallocAsync(&nloc, sizeof(int) * c->ntypes, c->stream));
+  DD_CUDA(cudaMemcpyAsync(nloc, c->type_nloc, sizeof(int) * c->ntypes, cudaMemcpyHostToDevice, c->stream));
+  if (es == 2) {
+    launch_local_inverse_t<__nv_bfloat16>(c, nloc, (__nv_bfloat16*)c->Ainv);
+  } else if (es == 4) {
+    launch_local_inverse_t<float>(c, nloc, (float*)c->Ainv);
+  } else {
+    // FP64 inverse in a scratch, per-type scale 448 / max|A_T^{-1}|, scaled E4M3 rounding
+    double* a64 = nullptr;
+    DD_CUDA(cudaMallocAsync(&a64, sizeof(double) * (size_t)c->ntypes * per_type, c->stream));
+    DD_CUDA(cudaMemsetAsync(a64, 0, sizeof(double) * (size_t)c->ntypes * per_type, c->stream));
+    launch_local_inverse_t<double>(c, nloc, a64);
+    const int nblk = 64;
+    double* part = nullptr;
+    DD_CUDA(cudaMallocAsync(&part, sizeof(double) * nblk * c->ntypes, c->stream));
+    (k_type_absmax<<<dim3(nblk, c->ntypes), 256, 0, c->stream>>>(a64, per_type, part), dd::note_launch());
+    (k_type_scale<<<1, 32, 0, c->stream>>>(part, nblk, c->ntypes, c->ascale64, c->ascale), dd::note_launch());
+    (k_quantize_e4m3<<<grid_blocks(per_type * c->ntypes, 256), 256, 0, c->stream>>>(
+         a64, per_type, c->ntypes, c->ascale64, (__nv_fp8_e4m3*)c->Ainv),
+     dd::note_launch());
+    DD_CUDA(cudaGetLastError());
+    DD_CUDA(cudaFreeAsync(part, c->stream));
+    DD_CUDA(cudaFreeAsync(a64, c->stream));
+  }
   DD_CUDA(cudaFreeAsync(nloc, c->stream));
   // plan: tensor maps and tile list
   GemmPlan* plan = reinterpret_cast<GemmPlan*>(c->tmapA);
@@ -482,11 +602,11 @@ int gemm_setup(dd_ctx* c) {
     plan = new GemmPlan();
     c->tmapA = plan;
   }
-  plan->bf16 = bf16;
-  const int BK = bf16 ? TcCfg<__nv_bfloat16>::BK : TcCfg<float>::BK;
-  make_tmap(&plan->tA, c->Ainv, bf16, kpad, (long long)c->ntypes * kpad, BK, 128);
-  make_tmap(&plan->tB256, c->Rpack, bf16, kpad, g.nsub, BK, 256);
-  make_tmap(&plan->tB128, c->Rpack, bf16, kpad, g.nsub, BK, 128);
+  plan->es = es;
+  const int BK = 128 / es;   // one 128-byte swizzle row of K
+  make_tmap(&plan->tA, c->Ainv, es, kpad, (long long)c->ntypes * kpad, BK, 128);
+  make_tmap(&plan->tB256, c->Rpack, es, kpad, g.nsub, BK, 256);
+  make_tmap(&plan->tB128, c->Rpack, es, kpad, g.nsub, BK, 128);
   const int mt = (kpad + 127) / 128;
   for (int i = 0; i < 2; ++i) {
     const int bn = i == 0 ? 256 : 128;
@@ -513,10 +633,13 @@ void launch_pack(dd_ctx* c, const double* r, double* c0, cudaStream_t s) {
   const Geo& g = c->g;
   if (c->grid.precision == DD_PREC_BF16)
     (k_pack<__nv_bfloat16><<<g.nsub, 256, 0, s>>>(g, c->subs, c->slot_of_sub, r, c->kpad, (__nv_bfloat16*)c->Rpack,
-                                                 c->wT, c0, c->st), dd::note_launch());
-  else
+                                                 c->wT, c0, c->st, nullptr, nullptr), dd::note_launch());
+  else if (c->grid.precision == DD_PREC_TF32)
     (k_pack<float><<<g.nsub, 256, 0, s>>>(g, c->subs, c->slot_of_sub, r, c->kpad, (float*)c->Rpack, c->wT, c0,
-                                         c->st), dd::note_launch());
+                                         c->st, nullptr, nullptr), dd::note_launch());
+  else
+    (k_pack<__nv_fp8_e4m3><<<g.nsub, 256, 0, s>>>(g, c->subs, c->slot_of_sub, r, c->kpad, (__nv_fp8_e4m3*)c->Rpack,
+                                                 c->wT, c0, c->st, c->ascale, c->ysc), dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 
@@ -537,14 +660,43 @@ void gemm_free(dd_ctx* c) {
 // ------------------------------------------------------------------------------------------
 // Diagnostic entry point: D[n][m] = sum_k A[m][k] B[n][k] through the same kernel.
 // ------------------------------------------------------------------------------------------
+namespace dd {
+
+// E4M3 bits of a float (1 sign, 4 exponent bits with bias 7, 3 mantissa bits, subnormals below
+// 2^-6, no infinities; nearest even, saturating at 448), from the format's definition
+static uint8_t host_e4m3(float f) {
+  const uint8_t sign = std::signbit(f) ? 0x80 : 0x00;
+  double a = std::fabs((double)f);
+  if (a == 0.0) return sign;
+  if (a >= 448.0) return sign | 0x7E;
+  int e;
+  std::frexp(a, &e);   // a = fr 2^e, fr in [0.5, 1): exponent of the leading bit is e - 1
+  int E = e - 1;
+  if (E < -6) {        // subnormal: units of 2^-9
+    const double q = a * 512.0;
+    double m = std::nearbyint(q);
+    if (m >= 8.0) return sign | (1u << 3);   // rounds up to the smallest normal
+    return sign | (uint8_t)m;
+  }
+  double mant = a / std::ldexp(1.0, E) - 1.0;   // in [0, 1)
+  double m = std::nearbyint(mant * 8.0);
+  if (m >= 8.0) {
+    m = 0.0;
+    ++E;
+  }
+  if (E > 8 || (E == 8 && m > 6.0)) return sign | 0x7E;
+  return sign | (uint8_t)(((E + 7) << 3) | (int)m);
+}
+
+}  // namespace dd
+
 extern "C" int dd_tc_gemm_test(int precision, int M, int N, int K, const float* A_host, const float* B_host,
                                float* D_host) {
   using namespace dd;
-  if (precision != DD_PREC_BF16 && precision != DD_PREC_TF32) return DD_EINVAL;
+  if (precision != DD_PREC_BF16 && precision != DD_PREC_TF32 && precision != DD_PREC_FP8) return DD_EINVAL;
   if (M < 1 || N < 1 || K < 1 || !A_host || !B_host || !D_host) return DD_EINVAL;
-  const bool bf16 = precision == DD_PREC_BF16;
-  const int es = bf16 ? 2 : 4;
-  const int kpad = (K + 63) / 64 * 64;
+  const int es = precision == DD_PREC_BF16 ? 2 : (precision == DD_PREC_TF32 ? 4 : 1);
+  const int kpad = (K + 127) / 128 * 128;
   const int mpad = (M + 127) / 128 * 128;
   void *dA = nullptr, *dB = nullptr;
   float* dD = nullptr;
@@ -559,7 +711,8 @@ extern "C" int dd_tc_gemm_test(int precision, int M, int N, int K, const float* 
     DD_CUDA(cudaMalloc(&dD, sizeof(float) * (size_t)N * mpad));
     DD_CUDA(cudaMalloc(&derr, sizeof(int)));
     DD_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), s));
-    // BF16 operands rounded to nearest even on the host; TF32 operands passed as FP32
+    // operands rounded on the host: BF16 and E4M3 to nearest even, TF32 passed as FP32
+    std::vector<uint8_t> a8, b8;
     std::vector<uint16_t> a16, b16;
     std::vector<float> a32, b32;
     auto to_bf16 = [](float f) -> uint16_t {
@@ -569,7 +722,7 @@ extern "C" int dd_tc_gemm_test(int precision, int M, int N, int K, const float* 
       u += 0x7FFFu + lsb;
       return (uint16_t)(u >> 16);
     };
-    if (bf16) {
+    if (es == 2) {
       a16.assign((size_t)mpad * kpad, 0);
       b16.assign((size_t)N * kpad, 0);
       for (int m = 0; m < M; ++m)
@@ -578,6 +731,15 @@ extern "C" int dd_tc_gemm_test(int precision, int M, int N, int K, const float* 
         for (int k = 0; k < K; ++k) b16[(size_t)n * kpad + k] = to_bf16(B_host[(size_t)n * K + k]);
       DD_CUDA(cudaMemcpyAsync(dA, a16.data(), a16.size() * 2, cudaMemcpyHostToDevice, s));
       DD_CUDA(cudaMemcpyAsync(dB, b16.data(), b16.size() * 2, cudaMemcpyHostToDevice, s));
+    } else if (es == 1) {
+      a8.assign((size_t)mpad * kpad, 0);
+      b8.assign((size_t)N * kpad, 0);
+      for (int m = 0; m < M; ++m)
+        for (int k = 0; k < K; ++k) a8[(size_t)m * kpad + k] = host_e4m3(A_host[(size_t)m * K + k]);
+      for (int n = 0; n < N; ++n)
+        for (int k = 0; k < K; ++k) b8[(size_t)n * kpad + k] = host_e4m3(B_host[(size_t)n * K + k]);
+      DD_CUDA(cudaMemcpyAsync(dA, a8.data(), a8.size(), cudaMemcpyHostToDevice, s));
+      DD_CUDA(cudaMemcpyAsync(dB, b8.data(), b8.size(), cudaMemcpyHostToDevice, s));
     } else {
       a32.assign((size_t)mpad * kpad, 0.f);
       b32.assign((size_t)N * kpad, 0.f);
@@ -589,18 +751,20 @@ extern "C" int dd_tc_gemm_test(int precision, int M, int N, int K, const float* 
       DD_CUDA(cudaMemcpyAsync(dB, b32.data(), b32.size() * 4, cudaMemcpyHostToDevice, s));
     }
     CUtensorMap tA, tB;
-    const int BK = bf16 ? TcCfg<__nv_bfloat16>::BK : TcCfg<float>::BK;
-    make_tmap(&tA, dA, bf16, kpad, mpad, BK, 128);
-    make_tmap(&tB, dB, bf16, kpad, N, BK, 256);
+    const int BK = 128 / es;
+    make_tmap(&tA, dA, es, kpad, mpad, BK, 128);
+    make_tmap(&tB, dB, es, kpad, N, BK, 256);
     std::vector<Tile> tl;
     for (int n0 = 0; n0 < N; n0 += 256)
       for (int m0 = 0; m0 < mpad; m0 += 128) tl.push_back(Tile{0, m0, n0, N});
     DD_CUDA(cudaMalloc(&dt, sizeof(Tile) * tl.size()));
     DD_CUDA(cudaMemcpyAsync(dt, tl.data(), sizeof(Tile) * tl.size(), cudaMemcpyHostToDevice, s));
-    if (bf16)
+    if (es == 2)
       launch_tc<__nv_bfloat16>(&tA, &tB, dt, (int)tl.size(), kpad, mpad, 0, dD, mpad, derr, nullptr, s);
-    else
+    else if (es == 4)
       launch_tc<float>(&tA, &tB, dt, (int)tl.size(), kpad, mpad, 0, dD, mpad, derr, nullptr, s);
+    else
+      launch_tc<__nv_fp8_e4m3>(&tA, &tB, dt, (int)tl.size(), kpad, mpad, 0, dD, mpad, derr, nullptr, s);
     std::vector<float> hD((size_t)N * mpad);
     int herr = 0;
     DD_CUDA(cudaMemcpyAsync(hD.data(), dD, sizeof(float) * hD.size(), cudaMemcpyDeviceToHost, s));
@@ -688,8 +852,8 @@ extern "C" int dd_tc_gemm_noalloc(int precision, int M, int N, int K, const void
       for (int m0 = 0; m0 < M; m0 += 128) tl[nt++] = Tile{0, m0, n0, N};
     CUtensorMap tA, tB;
     const int BK = bf16 ? TcCfg<__nv_bfloat16>::BK : TcCfg<float>::BK;
-    make_tmap(&tA, const_cast<void*>(A_dev), bf16, K, M, BK, 128);
-    make_tmap(&tB, const_cast<void*>(B_dev), bf16, K, N, BK, 256);
+    make_tmap(&tA, const_cast<void*>(A_dev), bf16 ? 2 : 4, K, M, BK, 128);
+    make_tmap(&tB, const_cast<void*>(B_dev), bf16 ? 2 : 4, K, N, BK, 256);
     // the error word must start at zero; the tile list is rewritten whole on every call
     DD_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), s));
     DD_CUDA(cudaMemcpyAsync(dtiles, tl, sizeof(Tile) * nt, cudaMemcpyHostToDevice, s));

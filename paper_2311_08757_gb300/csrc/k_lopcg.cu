@@ -190,6 +190,42 @@ __global__ void __launch_bounds__(kThreads) k_lop_update(long long n, const doub
     out[t] = fma(c2, xp[t], fma(c1, w[t], c0 * x[t]));
 }
 
+// x_{k+1} = S c together with its images A_sigma x_{k+1} = (A_sigma S) c and M x_{k+1} = (M S) c
+// (linear combinations instead of two more stencil passes), the outer residual
+// r_o = A_sigma x - theta M x and the norms of the stop test.  c is M-normalised by the
+// Rayleigh-Ritz step, so x^T M x = 1 up to rounding (its value is returned as a check).
+__global__ void __launch_bounds__(kThreads) k_lop_update3(long long n, const double* __restrict__ s0,
+                                                          const double* __restrict__ s1, const double* __restrict__ s2,
+                                                          const double* __restrict__ a0, const double* __restrict__ a1,
+                                                          const double* __restrict__ a2, const double* __restrict__ m0,
+                                                          const double* __restrict__ m1, const double* __restrict__ m2,
+                                                          double* __restrict__ x, double* __restrict__ ax,
+                                                          double* __restrict__ mx, double* __restrict__ ro, LopState* ls,
+                                                          double* partials, unsigned* counter) {
+  const double c0 = ls->c[0], c1 = ls->c[1], c2 = ls->c[2], th = ls->theta;
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const double xv = fma(c2, s2[t], fma(c1, s1[t], c0 * s0[t]));
+    const double av = fma(c2, a2[t], fma(c1, a1[t], c0 * a0[t]));
+    const double mv = fma(c2, m2[t], fma(c1, m1[t], c0 * m0[t]));
+    const double e = fma(-th, mv, av);
+    x[t] = xv;
+    ax[t] = av;
+    mx[t] = mv;
+    ro[t] = e;
+    acc[0] = fma(e, e, acc[0]);
+    acc[1] = fma(mv, mv, acc[1]);
+    acc[2] = fma(xv, mv, acc[2]);
+  }
+  double tot[3];
+  if (grid_sum_last<3>(acc, partials, counter, tot) && threadIdx.x == 0) {
+    ls->rr = tot[0];
+    ls->mm = tot[1];
+    ls->xmx = tot[2];
+  }
+}
+
 // in-place scaling x *= s, Mx *= s with s = os->scale (set by the normalisation dots)
 __global__ void __launch_bounds__(kThreads) k_lop_scale(long long n, double* x, double* Mx, const OuterState* os) {
   const double s = os->scale;
@@ -218,6 +254,16 @@ void launch_lop_update(dd_ctx* c, const double* x, const double* w, const double
                        cudaStream_t s) {
   const long long n = c->g.plen;
   (k_lop_update<<<grid_blocks(n, kThreads), kThreads, 0, s>>>(n, x, w, xp, out, c->lst), dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+}
+
+void launch_lop_update3(dd_ctx* c, const double* const S[3], const double* const AS[3], const double* const MS[3],
+                        double* x, double* Ax, double* Mx, double* ro, cudaStream_t s) {
+  const long long n = c->g.plen;
+  (k_lop_update3<<<grid_blocks(n, kThreads), kThreads, 0, s>>>(n, S[0], S[1], S[2], AS[0], AS[1], AS[2], MS[0], MS[1],
+                                                                MS[2], x, Ax, Mx, ro, c->lst, c->lop_red,
+                                                                c->cnt + CNT_LOP),
+   dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 

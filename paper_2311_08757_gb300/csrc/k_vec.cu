@@ -188,6 +188,21 @@ __global__ void __launch_bounds__(kThreads) k_stencil(Geo g, const double* __res
   }
 }
 
+// two operators on one vector in one pass: y1 = T1 x, y2 = T2 x
+template <int P>
+__global__ void __launch_bounds__(kThreads) k_stencil2(Geo g, const double* __restrict__ tab1,
+                                                       const double* __restrict__ tab2, const double* __restrict__ x,
+                                                       double* __restrict__ y1, double* __restrict__ y2) {
+  const long long total = (long long)g.nxi * (P == 2 ? g.nxi : 1) * g.Ypad;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    Node nd = node_of<P>(g, t);
+    const int cls = cls_of<P>(g, nd);
+    y1[nd.idx] = stencil_at<P>(g, tab1, x, nd.idx, cls);
+    y2[nd.idx] = stencil_at<P>(g, tab2, x, nd.idx, cls);
+  }
+}
+
 static long long interior_work(const Geo& g) {
   return (long long)g.nxi * (g.p == 2 ? g.nxi : 1) * g.Ypad;
 }
@@ -197,6 +212,15 @@ void launch_stencil(dd_ctx* c, const double* tab, const double* x, double* y, cu
   const int nb = grid_blocks(interior_work(g), kThreads);
   if (g.p == 1) (k_stencil<1, false><<<nb, kThreads, 0, s>>>(g, tab, x, y, nullptr, nullptr, nullptr), dd::note_launch());
   else (k_stencil<2, false><<<nb, kThreads, 0, s>>>(g, tab, x, y, nullptr, nullptr, nullptr), dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+}
+
+void launch_stencil2(dd_ctx* c, const double* tab1, const double* tab2, const double* x, double* y1, double* y2,
+                     cudaStream_t s) {
+  const Geo& g = c->g;
+  const int nb = grid_blocks(interior_work(g), kThreads);
+  if (g.p == 1) (k_stencil2<1><<<nb, kThreads, 0, s>>>(g, tab1, tab2, x, y1, y2), dd::note_launch());
+  else (k_stencil2<2><<<nb, kThreads, 0, s>>>(g, tab1, tab2, x, y1, y2), dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 

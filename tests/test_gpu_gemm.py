@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 SHAPES = [(128, 256, 64), (200, 300, 130), (1209, 517, 1209), (96, 1000, 40), (1, 1, 1)]
 
 
-@pytest.mark.parametrize("prec", [dd.DD_PREC_BF16, dd.DD_PREC_TF32])
+@pytest.mark.parametrize("prec", [dd.DD_PREC_BF16, dd.DD_PREC_TF32, dd.DD_PREC_FP8])
 @pytest.mark.parametrize("M,N,K", SHAPES)
 def test_tc_gemm_exact_on_integers(prec, M, N, K):
     rng = np.random.default_rng(M * 7 + N * 3 + K)
@@ -31,7 +31,7 @@ def test_tc_gemm_exact_on_integers(prec, M, N, K):
     assert np.array_equal(D, ref)
 
 
-@pytest.mark.parametrize("prec", [dd.DD_PREC_BF16, dd.DD_PREC_TF32])
+@pytest.mark.parametrize("prec", [dd.DD_PREC_BF16, dd.DD_PREC_TF32, dd.DD_PREC_FP8])
 def test_tc_gemm_random_real(prec):
     rng = np.random.default_rng(1)
     M, N, K = 300, 700, 333
@@ -40,7 +40,7 @@ def test_tc_gemm_random_real(prec):
     D = np.zeros((N, M), dtype=np.float32)
     dd.dd_tc_gemm_test(prec, A, B, D)
     ref = B.astype(np.float64) @ A.astype(np.float64).T
-    tol = 2e-2 if prec == dd.DD_PREC_BF16 else 4e-3
+    tol = {dd.DD_PREC_BF16: 2e-2, dd.DD_PREC_TF32: 4e-3, dd.DD_PREC_FP8: 1e-1}[prec]
     assert np.abs(D - ref).max() <= tol * np.abs(ref).max()
 
 
@@ -52,7 +52,10 @@ MIXED = {
 }
 
 
-@pytest.mark.parametrize("prec,tol", [("bf16", 2e-2), ("tf32", 4e-3)])
+# FP8 (E4M3, 3 mantissa bits, operands scaled per type and per subdomain to the E4M3 range):
+# a CPU emulation of the same scaled rounding gives relative errors of 2.2e-2 (cfg1) and
+# 4.5e-3 (cfg2_small), hence the 1e-1 bound
+@pytest.mark.parametrize("prec,tol", [("bf16", 2e-2), ("tf32", 4e-3), ("fp8", 1e-1)])
 @pytest.mark.parametrize("name", list(MIXED))
 def test_mixed_preconditioner(name, prec, tol):
     w = MIXED[name]
@@ -65,7 +68,7 @@ def test_mixed_preconditioner(name, prec, tol):
         assert rel_err(host(z), P.prec(r)) < tol
 
 
-@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+@pytest.mark.parametrize("prec", ["bf16", "tf32", "fp8"])
 @pytest.mark.parametrize("name", list(MIXED))
 def test_mixed_ground_state(name, prec):
     """Flexible CG with rounded local inverses reaches the FP64 ground state."""
@@ -84,7 +87,7 @@ def test_mixed_ground_state(name, prec):
     assert eta <= 1.5e-8
 
 
-@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+@pytest.mark.parametrize("prec", ["bf16", "tf32", "fp8"])
 @pytest.mark.parametrize("name", ["cfg2_small", "p2_small"])
 def test_gemm_tile_shapes_give_identical_preconditioner(name, prec):
     """The 128 x 128 and 128 x 256 output tiles accumulate every element over K in the same
