@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-3d", action="store_true")
+    ap.add_argument("--coarse-solve", default="auto", choices=["auto", "cr", "dense"])
     ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -319,6 +320,7 @@ def main():
 
     def make(prec):
         es = dd.Eigensolver(dd.grid_from_workload(w, precision=dd.PRECISIONS[prec]), V)
+        dd.dd_set_option(es.ctx, dd.DD_OPT_COARSE_SOLVE, {"auto": 0, "cr": 1, "dense": 2}[args.coarse_solve])
         return es
 
     def step(es):

@@ -63,7 +63,11 @@ extern "C" {
 #define DD_PREC_BF16 2      /* dense local inverses, BF16 tensor-core GEMM, FP32 accumulate */
 #define DD_PREC_FP8  3      /* dense local inverses, FP8 (E4M3) tensor-core GEMM, FP32 accumulate;
                                A_T^{-1} scaled per type and R_i r per subdomain to the E4M3 range
-                               before rounding, the product scaled back in the GEMM's epilogue */
+                               before rounding, the product scaled back in the GEMM's epilogue.
+                               The preconditioner is within a few percent of M_AS2^{-1}, but for
+                               the shifted local problems of this method that is not close
+                               enough: the flexible CG stagnates or diverges (the eigen-solves
+                               then end with DD_EMAXIT).  Use BF16 or TF32 for solves. */
 
 /* Partition of unity D_i (Sec. 2.2 equal weights; Sec. 4.1.2 distance based). */
 #define DD_PU_EQUAL    0
@@ -308,6 +312,11 @@ int dd_coarse_matrix(dd_ctx* ctx, double* A0_host);
  *   DD_OPT_PRECOND      0 M_AS2^{-1} (symmetric, for CG), 1 M_RAS2^{-1} (restricted: local
  *                       solutions weighted by the partition of unity D_i; GMRES only) [0]
  *   DD_OPT_RESTART      GMRES restart length, 1..200, fixed by the first GMRES solve [30]
+ *   DD_OPT_COARSE_SOLVE coarse solve u_0 = A_0^{-1} c: 1 cyclic reduction of the tridiagonal A_0
+ *                       (p = 1 only), 2 dense A_0^{-1} from its banded Cholesky factor applied
+ *                       as a GEMV, 0 = automatic (cyclic reduction for p = 1: measured faster
+ *                       beside the local GEMM at 2048 subdomains, and no N^2 set-up; dense for
+ *                       p = 2); read by dd_coarse_build [0]
  *   DD_OPT_GEMM_TILE_N  N tile of the mixed local-solve contraction: 128 or 256, 0 = chosen by
  *                       timing both on the context's operands at dd_coarse_build (cached per
  *                       problem shape); the result does not depend on it [0]
@@ -323,6 +332,7 @@ int dd_coarse_matrix(dd_ctx* ctx, double* A0_host);
 #define DD_OPT_PRECOND     6
 #define DD_OPT_RESTART     7
 #define DD_OPT_GEMM_TILE_N 8
+#define DD_OPT_COARSE_SOLVE 9
 int dd_set_option(dd_ctx* ctx, int option, int value);
 
 /* Per-kernel-class timing collected while DD_OPT_TIMING = 1: for class k (0 <= k < count),

@@ -1210,6 +1210,11 @@ int dd_set_option(dd_ctx* c, int option, int value) {
       if (c->gm_alloc != 0 && c->gm_alloc != value) return fail(c, DD_ESTATE, "restart fixed after the first GMRES solve");
       c->gm_restart = value;
       break;
+    case DD_OPT_COARSE_SOLVE:
+      if (value < 0 || value > 2) return fail(c, DD_EINVAL, "coarse solve must be 0, 1 or 2");
+      if (value == 1 && c->g.p == 2) return fail(c, DD_EINVAL, "cyclic reduction needs p = 1");
+      c->coarse_mode = value;
+      break;
     case DD_OPT_GEMM_TILE_N:
       if (value != 0 && value != 128 && value != 256) return fail(c, DD_EINVAL, "GEMM tile N must be 0, 128 or 256");
       c->gemm_bn_opt = value;

@@ -218,7 +218,10 @@ struct dd_ctx {
   double* A0band = nullptr;   // p=1: [3][N] (sub, diag, super); p=2: [N][9]
   double* cr = nullptr;       // p=1 cyclic-reduction coefficients
   int cr_m = 0, cr_np = 0;
-  double* A0inv = nullptr;    // p=2 dense inverse [N][N]
+  double* A0inv = nullptr;    // dense inverse [N][N] (p = 2; p = 1 on request)
+  int coarse_mode = 0;        // 0 automatic, 1 cyclic reduction (p = 1), 2 dense inverse
+  double *cf_CB = nullptr, *cf_RB = nullptr, *cf_inv = nullptr;   // banded factor of A_0
+  int coarse_dense = 0;       // the form in use
   double* c0 = nullptr;       // coarse rhs [N]
   double* u0 = nullptr;       // coarse solution [N]
 

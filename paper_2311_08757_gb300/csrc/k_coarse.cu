@@ -326,39 +326,45 @@ int coarse_factor(dd_ctx* c) {
   const int N = g.nsub;
   int* flag = c->dev_err + 2;
   DD_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), c->stream));
-  if (g.p == 1) {
+  c->coarse_dense = (g.p == 2) || c->coarse_mode == 2;
+  if (!c->coarse_dense) {
     int m = 1;
     while ((1 << m) - 1 < N) ++m;
     const int Np = (1 << m) - 1;
     c->cr_m = m;
     c->cr_np = Np;
     const size_t W = (size_t)Np + 2;
-    c->cr = (double*)dev_alloc(c, sizeof(double) * (2 * (size_t)Np + 4 * W));
+    if (!c->cr) c->cr = (double*)dev_alloc(c, sizeof(double) * (2 * (size_t)Np + 4 * W));   // kept across builds
     (k_cr_setup<<<1, 1024, 0, c->stream>>>(c->A0band, N, m, Np, c->cr, flag), dd::note_launch());
     DD_CUDA(cudaGetLastError());
   } else {
-    const int b = g.L + 1;
+    // dense A_0^{-1} (rows from the banded Cholesky factor), applied as a GEMV in the solve
+    const int b = (g.p == 2) ? g.L + 1 : 1;
+    const int nn = (g.p == 2) ? 9 : 3;   // couplings per coarse row
     const size_t cb = sizeof(double) * (size_t)N * (b + 1);
-    double* CB = (double*)dev_alloc(c, cb);
-    double* RB = (double*)dev_alloc(c, cb);
-    double* inv = (double*)dev_alloc(c, sizeof(double) * N);
-    // scatter the 9-point coarse rows into lower band storage (order s = s1 L + s2)
-    std::vector<double> nb((size_t)N * 9), hcb((size_t)N * (b + 1), 0.0);
-    DD_CUDA(cudaMemcpyAsync(nb.data(), c->A0band, sizeof(double) * N * 9, cudaMemcpyDeviceToHost, c->stream));
+    if (!c->cf_CB) {   // kept across builds (same grid)
+      c->cf_CB = (double*)dev_alloc(c, cb);
+      c->cf_RB = (double*)dev_alloc(c, cb);
+      c->cf_inv = (double*)dev_alloc(c, sizeof(double) * N);
+    }
+    double *CB = c->cf_CB, *RB = c->cf_RB, *inv = c->cf_inv;
+    // scatter the 3- or 9-point coarse rows into lower band storage (order s = s1 L + s2)
+    std::vector<double> nb((size_t)N * nn), hcb((size_t)N * (b + 1), 0.0);
+    DD_CUDA(cudaMemcpyAsync(nb.data(), c->A0band, sizeof(double) * N * nn, cudaMemcpyDeviceToHost, c->stream));
     DD_CUDA(cudaStreamSynchronize(c->stream));
     for (int s = 0; s < N; ++s) {
-      const int s1 = s / g.L, s2 = s % g.L;
-      for (int k = 0; k < 9; ++k) {
-        const int t1 = s1 + k / 3 - 1, t2 = s2 + k % 3 - 1;
-        if (t1 < 0 || t1 >= g.L || t2 < 0 || t2 >= g.L) continue;
-        const int t = t1 * g.L + t2;
+      const int s1 = (g.p == 2) ? s / g.L : s, s2 = (g.p == 2) ? s % g.L : 0;
+      for (int k = 0; k < nn; ++k) {
+        const int t1 = s1 + (g.p == 2 ? k / 3 : k) - 1, t2 = (g.p == 2) ? s2 + k % 3 - 1 : 0;
+        if (t1 < 0 || t1 >= ((g.p == 2) ? g.L : N) || t2 < 0 || (g.p == 2 && t2 >= g.L)) continue;
+        const int t = (g.p == 2) ? t1 * g.L + t2 : t1;
         if (t < s) continue;
-        hcb[(size_t)s * (b + 1) + (t - s)] = nb[(size_t)s * 9 + k];
+        hcb[(size_t)s * (b + 1) + (t - s)] = nb[(size_t)s * nn + k];
       }
     }
     DD_CUDA(cudaMemcpyAsync(CB, hcb.data(), cb, cudaMemcpyHostToDevice, c->stream));
     launch_band_factor(c, CB, RB, inv, 1, N, b, flag);
-    c->A0inv = (double*)dev_alloc(c, sizeof(double) * (size_t)N * N);
+    if (!c->A0inv) c->A0inv = (double*)dev_alloc(c, sizeof(double) * (size_t)N * N);
     launch_band_inverse_rows(N, b, CB, RB, inv, c->A0inv, c->stream);
   }
   int fl = 0;
@@ -388,7 +394,7 @@ void launch_coarse_restrict(dd_ctx* c, const double* r, cudaStream_t s) {
 
 void launch_coarse_solve(dd_ctx* c, cudaStream_t s) {
   const Geo& g = c->g;
-  if (g.p == 1) {
+  if (!c->coarse_dense) {
     const size_t W = (size_t)c->cr_np + 2;
     const size_t full = sizeof(double) * (2 * (size_t)c->cr_np + 4 * W);   // f + coefficients
     const int staged = full <= 210 * 1024 ? 1 : 0;

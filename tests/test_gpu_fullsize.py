@@ -83,3 +83,20 @@ def test_fullsize_ground_state(oracle, gpu):
     eta = np.linalg.norm(P.A @ xh - lam * Mx) / (abs(lam) * np.linalg.norm(Mx))
     assert eta <= 1.5e-8
     assert xh @ Mx == pytest.approx(1.0, rel=1e-12)
+
+
+def test_fullsize_coarse_solve_by_dense_inverse(oracle):
+    """The other coarse-solve form at full size (the default for p = 1 is cyclic reduction)."""
+    P, _ = oracle
+    es = make_solver(W, precision="fp64")
+    try:
+        dd.dd_set_option(es.ctx, dd.DD_OPT_COARSE_SOLVE, 2)
+        es.prepare()
+        r = np.random.default_rng(24).standard_normal(W.dofs)
+        z = gpu_vec(np.zeros(W.dofs))
+        dd.dd_apply_preconditioner(es.ctx, gpu_vec(r), z)
+        ev = np.linalg.eigvalsh(P.prec.A0)
+        tol = max(1e-10, 50 * np.finfo(float).eps * ev[-1] / ev[0])
+        assert rel_err(host(z), P.prec(r)) < tol
+    finally:
+        es.close()

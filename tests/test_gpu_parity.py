@@ -235,3 +235,22 @@ def test_local_rhs_per_warp_bit_exact(built, name):
     assert rel_err(out[0], P.prec(host(r))) < 1e-10
     with pytest.raises(dd.DDError):
         dd.dd_set_option(es.ctx, dd.DD_OPT_LOCAL_RHS, 3)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("name", ["cfg1", "cfg2_small", "ragged", "L2", "L1"])
+def test_coarse_solve_forms(name, mode):
+    """Both forms of the p = 1 coarse solve (cyclic reduction, dense inverse) give the oracle's
+    preconditioner."""
+    w = CASES[name]
+    P = oracle_problem(w)
+    es = make_solver(w)
+    try:
+        dd.dd_set_option(es.ctx, dd.DD_OPT_COARSE_SOLVE, mode)
+        es.prepare()
+        r = np.random.default_rng(23).standard_normal(w.dofs)
+        z = gpu_vec(np.zeros(w.dofs))
+        dd.dd_apply_preconditioner(es.ctx, gpu_vec(r), z)
+        assert rel_err(host(z), P.prec(r)) < 1e-10
+    finally:
+        es.close()
