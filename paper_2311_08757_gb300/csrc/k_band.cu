@@ -25,6 +25,7 @@ namespace dd {
 // bandwidths whose window does not fit.
 // ----------------------------------------------------------------------------------------
 constexpr int kBandWinMax = 160;
+constexpr int kMaxPairs = 16;   // triangle pairs per thread: b (b + 1) / 2 <= 16 x threads for b <= 160
 
 template <int P>
 __global__ void __launch_bounds__(1024) k_band_factor_win(double* CB, double* inv, const int* __restrict__ nvec,
@@ -38,9 +39,29 @@ __global__ void __launch_bounds__(1024) k_band_factor_win(double* CB, double* in
   double* colk = fsm + W * bs;     // L(k+d, k), d = 0..b
   double* A = CB + (size_t)m * nmax * bs;
   double* iv = inv + (size_t)m * nmax;
-  // this thread's first pair (1-based d1, d2 over the b x b square) and the stride in pairs
-  const int t0_d1 = t / b + 1, t0_d2 = t % b + 1;
-  const int st_d1 = (int)blockDim.x / b, st_d2 = (int)blockDim.x % b;
+  // this thread's pairs (d1, d2), 1 <= d2 <= d1 <= b, of the lower triangle of the window
+  // update: linear index e = d1 (d1 - 1) / 2 + d2 - 1 taken as e = t, t + T, ...; in that order
+  // d1 never decreases, so the pairs beyond the last column's reach form a suffix
+  unsigned pr[kMaxPairs / 2];   // two pairs per word: (d1 << 8 | d2) in each half (b <= 160 < 256)
+  int npr = 0;
+  {
+    const int T = (int)blockDim.x, tot = b * (b + 1) / 2;
+#pragma unroll
+    for (int j = 0; j < kMaxPairs; ++j) {
+      const int e = t + j * T;
+      int d1 = 0, d2 = 0;
+      if (e < tot) {
+        d1 = (int)((sqrtf(8.0f * (float)e + 1.0f) + 1.0f) * 0.5f);   // first guess, then exact
+        while (d1 * (d1 - 1) / 2 > e) --d1;
+        while ((d1 + 1) * d1 / 2 <= e) ++d1;
+        d2 = e - d1 * (d1 - 1) / 2 + 1;
+        ++npr;
+      }
+      const unsigned half = ((unsigned)d1 << 8) | (unsigned)d2;
+      if (j & 1) pr[j >> 1] |= half << 16;
+      else pr[j >> 1] = half;
+    }
+  }
   const int first = min(W, n);
   for (int e = t; e < first * bs; e += blockDim.x) win[e] = A[e];
   // entering columns are loaded P steps before they are needed
@@ -80,19 +101,16 @@ __global__ void __launch_bounds__(1024) k_band_factor_win(double* CB, double* in
           colk[d] = v;
         }
         __syncthreads();
-        // pairs (d1, d2) of the b x b square, walked with the step's fixed stride (no division)
-        for (int e = 0, d1 = t0_d1, d2 = t0_d2; d1 <= b; e += blockDim.x) {
-          if (d2 <= d1 && d1 <= dmax) {
+        // A(k+d1, k+d2) -= L(k+d1, k) L(k+d2, k) over this thread's pairs with d1 <= dmax
+#pragma unroll
+        for (int j = 0; j < kMaxPairs; ++j) {
+          const unsigned half = (j & 1) ? (pr[j >> 1] >> 16) : (pr[j >> 1] & 0xFFFFu);
+          const int d1 = (int)(half >> 8), d2 = (int)(half & 0xFFu);
+          if (j < npr && d1 <= dmax) {
             int slot = sk + d2;                  // ring slot of column k + d2
             if (slot >= W) slot -= W;
             double* a = win + slot * bs + (d1 - d2);
             *a = fma(-colk[d1], colk[d2], *a);
-          }
-          d2 += st_d2;
-          d1 += st_d1;
-          if (d2 > b) {
-            d2 -= b;
-            d1 += 1;
           }
         }
         __syncthreads();
@@ -189,13 +207,14 @@ static void factor_launch(const Geo&, double* CB, double* RB, double* inv, const
                           int* flag, cudaStream_t s) {
   if (b <= kBandWinMax) {
     const size_t smem = sizeof(double) * ((size_t)(b + 1) * (b + 1) + (b + 1));
-    const int threads = (b * b > 2048) ? 512 : 256;
+    const int tot = b * (b + 1) / 2;   // triangle pairs: at most kMaxPairs per thread
+    const int threads = (b * b > 2048) ? (tot > kMaxPairs * 512 ? 1024 : 512) : 256;
     static std::atomic<bool> attr{false};   // set once per process (idempotent if two threads race)
     if (!attr) {
-      DD_CUDA(cudaFuncSetAttribute(k_band_factor_win<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+      DD_CUDA(cudaFuncSetAttribute(k_band_factor_win<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
       attr = true;
     }
-    (k_band_factor_win<8><<<nmat, threads, smem, s>>>(CB, inv, nvec, nmax, b, flag), dd::note_launch());
+    (k_band_factor_win<4><<<nmat, threads, smem, s>>>(CB, inv, nvec, nmax, b, flag), dd::note_launch());
   } else {
     (k_band_factor<<<nmat, 1024, sizeof(double) * (b + 1), s>>>(CB, inv, nvec, nmax, b, flag), dd::note_launch());
   }
