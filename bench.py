@@ -230,10 +230,6 @@ def roofline_entry(name, model, ms_total, nlaunch, peaks, peak_src, precision):
 # from one ncu capture of this workload (profiles/top_kernels_cfg2_bench.md,
 # profiles/local_solve_fp64_cfg2.md); a kernel changed since its capture is left out.
 TRAFFIC = {
-    "stencil_Asigma": (33.65 + 0.52) * 1e6,
-    "prolong_sum": (44.66 + 0.13) * 1e6,
-    "xr_update": (67.13 + 0.64) * 1e6,
-    "pack_restrict": (16.88 + 0.00) * 1e6,
     "local_solve_fp64": (18.77 + 0.00) * 1e6,
 }
 

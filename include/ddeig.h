@@ -353,6 +353,16 @@ long long dd_kernel_launch_count(void);
  * frees its own device buffers.  DD_ETIMEOUT if a bounded device wait expired. */
 int dd_tc_gemm_test(int precision, int M, int N, int K, const float* A_host, const float* B_host, float* D_host);
 
+/* Self-test of the device precision conversions of the mixed form (no paper counterpart;
+ * they round the restrictions R_i r to the GEMM's operand type and widen its FP32 results
+ * with integer operations, off GB300's narrow FP64 pipe).  n host values in, n host values out:
+ *   kind 0: double -> BF16 bits (uint16), IEEE round to nearest even;
+ *   kind 1: double -> TF32 (float whose low 13 mantissa bits are zero), nearest, ties away;
+ *   kind 2: float -> double (exact).
+ * Allocates and frees its own device buffers.  DD_EINVAL for a bad kind, n < 1 or a null
+ * pointer. */
+int dd_convert_test(int kind, long long n, const void* in_host, void* out_host);
+
 /* Allocation-free form of the same tensor-core contraction (the paper has no counterpart: it
  * exists for callers that cannot allocate device memory where they need the product, such as
  * a server whose device memory is reserved up front by its own arena, or a latency-critical

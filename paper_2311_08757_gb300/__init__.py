@@ -82,6 +82,7 @@ _SIGS = {
                                   POINTER(c_double)]),
     "dd_reset_timings": (c_int, [c_void_p]),
     "dd_tc_gemm_test": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
+    "dd_convert_test": (c_int, [c_int, c_longlong, c_void_p, c_void_p]),
     "dd_set_potential": (c_int, [c_void_p, c_void_p, c_size_t]),
     "dd_kernel_launch_count": (c_longlong, []),
     "dd_tc_gemm_noalloc": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -283,6 +284,16 @@ def dd_tc_gemm_test(precision: int, A, B, D) -> int:
     M, K = A.shape
     N = B.shape[0]
     return _check(lib().dd_tc_gemm_test(precision, M, N, K, _ptr(A), _ptr(B), _ptr(D)))
+
+
+def dd_convert_test(kind: int, x):
+    """Device precision conversions on a host array: kind 0 float64 -> BF16 bits (uint16),
+    1 float64 -> TF32 (float32), 2 float32 -> float64."""
+    import numpy as np
+    x = np.ascontiguousarray(x, dtype=np.float32 if kind == 2 else np.float64)
+    out = np.zeros(x.size, dtype={0: np.uint16, 1: np.float32, 2: np.float64}[kind])
+    _check(lib().dd_convert_test(kind, x.size, _ptr(x), _ptr(out)))
+    return out
 
 
 def dd_tc_gemm_noalloc(precision: int, A_dev, B_dev, D_dev, stream=None) -> int:

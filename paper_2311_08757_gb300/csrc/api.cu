@@ -617,8 +617,11 @@ int dd_setup(const dd_grid* gr, const double* V, size_t nV, void* stream, dd_ctx
     c->psi_cell = (double*)dev_alloc(c, sizeof(double) * c->ncell);
     c->wT = (double*)dev_alloc(c, sizeof(double) * (size_t)c->ntypes * c->kpad);
     c->puT = (double*)dev_alloc(c, sizeof(double) * (size_t)c->ntypes * c->kpad);
+    c->wT32 = (float*)dev_alloc(c, sizeof(float) * (size_t)c->ntypes * c->kpad);
+    c->puT32 = (float*)dev_alloc(c, sizeof(float) * (size_t)c->ntypes * c->kpad);
     c->c0 = (double*)dev_alloc(c, sizeof(double) * g.nsub);
     c->u0 = (double*)dev_alloc(c, sizeof(double) * g.nsub);
+    c->u0f = (float*)dev_alloc(c, sizeof(float) * g.nsub);
     c->A0band = (double*)dev_alloc(c, sizeof(double) * (size_t)g.nsub * (G.p == 1 ? 3 : 9));
     DD_CUDA(cudaStreamSynchronize(c->stream));
     c->stage = 1;
@@ -696,13 +699,26 @@ int dd_coarse_build(dd_ctx* c) {
     int* flag = c->dev_err + 3;
     DD_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), c->stream));
     const size_t bsz = (size_t)c->ntypes * c->nloc_max * (c->band + 1);
-    if (!c->bandCB) {
-      c->bandCB = (double*)dev_alloc(c, sizeof(double) * bsz);
-      c->bandRB = (double*)dev_alloc(c, sizeof(double) * bsz);
-      c->bandInv = (double*)dev_alloc(c, sizeof(double) * (size_t)c->ntypes * c->nloc_max);
+    if (use_gemm(c)) {
+      // the mixed form only forms A_T^{-1} from the factor and rounds it to BF16/TF32/E4M3:
+      // an FP32 factor and FP32 solves are far more accurate than that rounding
+      if (!c->bandCB32) {
+        c->bandCB32 = (float*)dev_alloc(c, sizeof(float) * bsz);
+        c->bandRB32 = (float*)dev_alloc(c, sizeof(float) * bsz);
+        c->bandInv32 = (float*)dev_alloc(c, sizeof(float) * (size_t)c->ntypes * c->nloc_max);
+      }
+      launch_local_assemble(c, c->bandCB32);
+      launch_band_factor(c, c->bandCB32, c->bandRB32, c->bandInv32, c->ntypes, c->nloc_max, c->band, flag,
+                         c->type_nloc);
+    } else {
+      if (!c->bandCB) {
+        c->bandCB = (double*)dev_alloc(c, sizeof(double) * bsz);
+        c->bandRB = (double*)dev_alloc(c, sizeof(double) * bsz);
+        c->bandInv = (double*)dev_alloc(c, sizeof(double) * (size_t)c->ntypes * c->nloc_max);
+      }
+      launch_local_assemble(c, c->bandCB);
+      launch_band_factor(c, c->bandCB, c->bandRB, c->bandInv, c->ntypes, c->nloc_max, c->band, flag, c->type_nloc);
     }
-    launch_local_assemble(c);
-    launch_band_factor(c, c->bandCB, c->bandRB, c->bandInv, c->ntypes, c->nloc_max, c->band, flag);
     int fl = 0;
     DD_CUDA(cudaMemcpyAsync(&fl, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     DD_CUDA(cudaStreamSynchronize(c->stream));

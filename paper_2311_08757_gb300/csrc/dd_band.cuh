@@ -14,28 +14,32 @@
 
 namespace dd {
 
+__device__ __forceinline__ double fma_el(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_el(float a, float b, float c) { return fmaf(a, b, c); }
+
 // Solves (L L^T) x = r in place in xs[0..n).  Caller: all 32 lanes of a warp, xs visible to
-// the warp (shared memory).
-__device__ __forceinline__ void warp_band_solve(double* xs, int n, int b, const double* __restrict__ CB,
-                                                const double* __restrict__ RB,
-                                                const double* __restrict__ inv) {
+// the warp (shared memory).  T is double (the plain method, the coarse factor) or float (the
+// factors whose inverses are rounded to a tensor-core type, and the cell preconditioner).
+template <typename T>
+__device__ __forceinline__ void warp_band_solve(T* xs, int n, int b, const T* __restrict__ CB,
+                                                const T* __restrict__ RB, const T* __restrict__ inv) {
   const int lane = threadIdx.x & 31;
   const int bs = b + 1;
   __syncwarp();
   for (int i = 0; i < n; ++i) {
-    const double wi = xs[i];
-    const double* col = CB + (size_t)i * bs;
+    const T wi = xs[i];
+    const T* col = CB + (size_t)i * bs;
     const int dmax = min(b, n - 1 - i);
-    for (int d = 1 + lane; d <= dmax; d += 32) xs[i + d] = fma(-__ldg(col + d), wi, xs[i + d]);
+    for (int d = 1 + lane; d <= dmax; d += 32) xs[i + d] = fma_el(-__ldg(col + d), wi, xs[i + d]);
     __syncwarp();
   }
   for (int i = lane; i < n; i += 32) xs[i] *= __ldg(inv + i);
   __syncwarp();
   for (int i = n - 1; i >= 0; --i) {
-    const double xi = xs[i];
-    const double* row = RB + (size_t)i * bs;
+    const T xi = xs[i];
+    const T* row = RB + (size_t)i * bs;
     const int dmax = min(b, i);
-    for (int d = 1 + lane; d <= dmax; d += 32) xs[i - d] = fma(-__ldg(row + d), xi, xs[i - d]);
+    for (int d = 1 + lane; d <= dmax; d += 32) xs[i - d] = fma_el(-__ldg(row + d), xi, xs[i - d]);
     __syncwarp();
   }
 }
@@ -60,18 +64,23 @@ namespace dd {
 
 namespace dd {
 
-// Asynchronous 8-byte global -> shared copies (cp.async), committed one group per band row.
-__device__ __forceinline__ void cp_async8(double* dst_smem, const double* src) {
+// Asynchronous 8- or 4-byte global -> shared copies (cp.async), committed one group per band row.
+__device__ __forceinline__ void cp_async_el(double* dst_smem, const double* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_el(float* dst_smem, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // shared-memory ring of the band-coefficient prefetch: PF rows x NV values x 32 lanes
+// (elements of the factor's type)
 template <int NV, int PF>
-__host__ __device__ constexpr int band_ring_doubles() { return NV > 0 ? PF * NV * 32 : 0; }
+__host__ __device__ constexpr int band_ring_elems() { return NV > 0 ? PF * NV * 32 : 0; }
 
 // Lane-owned solve of K right-hand sides sharing one factor (vector k at xs + k * ldx).
 // Element j of every vector belongs to lane j & 31 for the whole solve: each lane keeps its
@@ -92,14 +101,13 @@ __host__ __device__ constexpr int band_ring_doubles() { return NV > 0 ? PF * NV 
 // is tracked by a handful of scoreboards, so a use waits on recent loads too).  Each lane
 // reads back only the slots it copied itself.  Per vector the floating-point operations are
 // those of warp_band_solve, in the same order, so the results are identical.
-template <int NV, int PF, int K>
-__device__ __forceinline__ void warp_band_solve_k(double* xs, int ldx, int n, int b, const double* __restrict__ CB,
-                                                  const double* __restrict__ RB, const double* __restrict__ inv,
-                                                  double* ring) {
+template <int NV, int PF, int K, typename T>
+__device__ __forceinline__ void warp_band_solve_k(T* xs, int ldx, int n, int b, const T* __restrict__ CB,
+                                                  const T* __restrict__ RB, const T* __restrict__ inv, T* ring) {
   const int lane = threadIdx.x & 31;
   const int bs = b + 1;
-  double e[K][NV], nx[K];
-  double* rl = ring + lane;   // this lane's column of the ring: slot (u, t) at rl[(u * NV + t) * 32]
+  T e[K][NV], nx[K];
+  T* rl = ring + lane;   // this lane's column of the ring: slot (u, t) at rl[(u * NV + t) * 32]
   // ---- forward sweep
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -112,7 +120,7 @@ __device__ __forceinline__ void warp_band_solve_k(double* xs, int ldx, int n, in
 #pragma unroll
     for (int t = 0; t < NV; ++t) {
       const int d = ((lane - u - 1) & 31) + 1 + 32 * t;
-      cp_async8(rl + (u * NV + t) * 32, CB + (size_t)min(u, n - 1) * bs + min(d, b));
+      cp_async_el(rl + (u * NV + t) * 32, CB + (size_t)min(u, n - 1) * bs + min(d, b));
     }
     cp_async_commit();
   }
@@ -122,11 +130,11 @@ __device__ __forceinline__ void warp_band_solve_k(double* xs, int ldx, int n, in
       const int i = i0 + u;
       if (i < n) {
         cp_async_wait<PF - 1>();
-        double rb[NV];
+        T rb[NV];
 #pragma unroll
         for (int t = 0; t < NV; ++t) rb[t] = rl[(u * NV + t) * 32];
         const int piv = i & 31;
-        double w[K];
+        T w[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) w[k] = __shfl_sync(kFull, e[k][0], piv);
         if (lane == piv) {
@@ -144,14 +152,14 @@ __device__ __forceinline__ void warp_band_solve_k(double* xs, int ldx, int n, in
           const int d = ((lane - i - 1) & 31) + 1 + 32 * t;
           if (d <= b && i + d < n) {
 #pragma unroll
-            for (int k = 0; k < K; ++k) e[k][t] = fma(-rb[t], w[k], e[k][t]);
+            for (int k = 0; k < K; ++k) e[k][t] = fma_el(-rb[t], w[k], e[k][t]);
           }
         }
         const int ni = i + PF;
 #pragma unroll
         for (int t = 0; t < NV; ++t) {
           const int d = ((lane - ni - 1) & 31) + 1 + 32 * t;
-          cp_async8(rl + (u * NV + t) * 32, CB + (size_t)min(ni, n - 1) * bs + min(d, b));
+          cp_async_el(rl + (u * NV + t) * 32, CB + (size_t)min(ni, n - 1) * bs + min(d, b));
         }
         cp_async_commit();
       }
@@ -160,7 +168,7 @@ __device__ __forceinline__ void warp_band_solve_k(double* xs, int ldx, int n, in
   cp_async_wait<0>();
   // ---- scale by 1 / L_jj^2 (own elements)
   for (int j = lane; j < n; j += 32) {
-    const double sc = __ldg(inv + j);
+    const T sc = __ldg(inv + j);
 #pragma unroll
     for (int k = 0; k < K; ++k) xs[k * ldx + j] *= sc;
   }
@@ -178,7 +186,7 @@ __device__ __forceinline__ void warp_band_solve_k(double* xs, int ldx, int n, in
 #pragma unroll
     for (int t = 0; t < NV; ++t) {
       const int d = ((i - lane - 1) & 31) + 1 + 32 * t;
-      cp_async8(rl + (u * NV + t) * 32, RB + (size_t)max(i, 0) * bs + min(d, b));
+      cp_async_el(rl + (u * NV + t) * 32, RB + (size_t)max(i, 0) * bs + min(d, b));
     }
     cp_async_commit();
   }
@@ -188,11 +196,11 @@ __device__ __forceinline__ void warp_band_solve_k(double* xs, int ldx, int n, in
       const int i = n - 1 - (i0 + u);
       if (i >= 0) {
         cp_async_wait<PF - 1>();
-        double rb[NV];
+        T rb[NV];
 #pragma unroll
         for (int t = 0; t < NV; ++t) rb[t] = rl[(u * NV + t) * 32];
         const int piv = i & 31;
-        double xv[K];
+        T xv[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) xv[k] = __shfl_sync(kFull, e[k][0], piv);
         if (lane == piv) {
@@ -210,14 +218,14 @@ __device__ __forceinline__ void warp_band_solve_k(double* xs, int ldx, int n, in
           const int d = ((i - lane - 1) & 31) + 1 + 32 * t;
           if (d <= b && i - d >= 0) {
 #pragma unroll
-            for (int k = 0; k < K; ++k) e[k][t] = fma(-rb[t], xv[k], e[k][t]);
+            for (int k = 0; k < K; ++k) e[k][t] = fma_el(-rb[t], xv[k], e[k][t]);
           }
         }
         const int ni = i - PF;
 #pragma unroll
         for (int t = 0; t < NV; ++t) {
           const int d = ((ni - lane - 1) & 31) + 1 + 32 * t;
-          cp_async8(rl + (u * NV + t) * 32, RB + (size_t)max(ni, 0) * bs + min(d, b));
+          cp_async_el(rl + (u * NV + t) * 32, RB + (size_t)max(ni, 0) * bs + min(d, b));
         }
         cp_async_commit();
       }
@@ -227,18 +235,17 @@ __device__ __forceinline__ void warp_band_solve_k(double* xs, int ldx, int n, in
 }
 
 // K-way solve for NV > 0; the plain single-vector solve otherwise (K = 1 then)
-template <int NV, int PF, int K>
-__device__ __forceinline__ void band_solve_k(double* xs, int ldx, int n, int b, const double* __restrict__ CB,
-                                             const double* __restrict__ RB, const double* __restrict__ inv,
-                                             double* ring) {
+template <int NV, int PF, int K, typename T>
+__device__ __forceinline__ void band_solve_k(T* xs, int ldx, int n, int b, const T* __restrict__ CB,
+                                             const T* __restrict__ RB, const T* __restrict__ inv, T* ring) {
   if constexpr (NV == 0) warp_band_solve(xs, n, b, CB, RB, inv);
   else warp_band_solve_k<NV, PF, K>(xs, ldx, n, b, CB, RB, inv, ring);
 }
 
-// bytes of the coefficient ring per warp for half bandwidth b (host side)
-inline size_t band_ring_bytes(int b) {
+// bytes of the coefficient ring per warp for half bandwidth b and element size es (host side)
+inline size_t band_ring_bytes(int b, size_t es = sizeof(double)) {
   size_t r = 0;
-  DD_BAND_DISPATCH(b, (r = sizeof(double) * (size_t)band_ring_doubles<NV, PF>()));
+  DD_BAND_DISPATCH(b, (r = es * (size_t)band_ring_elems<NV, PF>()));
   return r;
 }
 

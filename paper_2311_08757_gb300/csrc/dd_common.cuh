@@ -12,32 +12,46 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // Last-block counters (one per reduction site so that concurrent kernels never share one).
 enum CounterId {
-  CNT_PQ = 0, CNT_RR, CNT_RZ, CNT_INIT, CNT_DOT0, CNT_DOT1, CNT_OUTER0, CNT_OUTER1, CNT_OUTER2, CNT_LOP, CNT_GRAD,
+  CNT_PQ = 0, CNT_RR, CNT_RZ, CNT_INIT, CNT_DOT0, CNT_DOT1, CNT_OUTER0, CNT_OUTER1, CNT_OUTER2, CNT_LOP, CNT_GRAD, CNT_CELL,
   CNT_NUM = 16
 };
 constexpr int kMaxRedBlocks = 4096;   // partial slots per value
 
-// Tree sum over the warp (result in lane 0).  Only the lanes whose partial survives add:
-// FP64 instructions issue at 2 lanes per clock per SM on GB300, so the 31 adds of the
-// predicated tree cost a fifth of the 160 of a full butterfly.
+// Tree sum over the warp (result in lane 0).  GB300 issues FP64 at 2 lanes per clock per
+// SM and charges a whole warp instruction whatever its active mask (measured: predicated
+// adds execute on all 32 lanes), so every step costs a full warp's FP64 issue.
 __device__ __forceinline__ double warp_sum(double v) {
-  const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const double u = __shfl_down_sync(kFull, v, o);
-    // a predicated add (an if-converted select would issue the add on every lane)
-    asm("{\n .reg .pred q;\n setp.lt.s32 q, %2, %3;\n @q add.rn.f64 %0, %0, %1;\n}\n"
-        : "+d"(v)
-        : "d"(u), "r"(lane), "r"(o));
-  }
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
   return v;
 }
 
-// Sums NV values over the block; the result is valid in thread 0 only.
+// Sums NV values over the block; the result is valid in thread 0 only.  For up to four
+// values and blocks of at most 256 threads (a multiple of 32), the partials are staged in
+// shared memory and one warp adds them: (warps - 1) + 5 FP64 warp instructions per value
+// instead of 5 per warp plus 5 (12 against 45 for 256 threads).
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV]) {
-  __shared__ double sm[32][NV];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if constexpr (NV <= 4) {
+    if (blockDim.x <= 256 && (blockDim.x & 31) == 0) {
+      __shared__ double st[NV][256];
+#pragma unroll
+      for (int k = 0; k < NV; ++k) st[k][threadIdx.x] = v[k];
+      __syncthreads();
+      if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+          double a = st[k][lane];
+          for (int w = 1; w < nw; ++w) a += st[k][lane + 32 * w];
+          v[k] = warp_sum(a);
+        }
+      }
+      __syncthreads();
+      return;
+    }
+  }
+  __shared__ double sm[32][NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
   __syncthreads();
@@ -105,50 +119,44 @@ static __device__ __noinline__ float tf32_slow(double x) {
 }
 static __device__ __noinline__ double f64_slow(float f) { return (double)f; }
 
-// IEEE round-to-nearest-even of a double to bfloat16 (bits); non-normal results fall back to
-// the hardware conversion.
+// IEEE round-to-nearest-even of a double to bfloat16 (bits).  Only 32-bit integer
+// operations on the two words of x; zeros, results outside the normal range, infinities and
+// NaNs take the hardware conversion (one range check selects them).
 __device__ __forceinline__ unsigned short f64_to_bf16_bits(double x) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-  const unsigned sign = (unsigned)(u >> 63);
-  const int e = (int)((u >> 52) & 0x7FF);
-  const int eb = e - 1023 + 127;
-  if (e == 0 && (u << 1) == 0) return (unsigned short)(sign << 15);   // +-0
-  if (__builtin_expect(eb < 1 || eb > 254, 0)) return bf16_bits_slow(x);
-  const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
-  const unsigned long long keep = m >> 45, rem = m & ((1ull << 45) - 1), half = 1ull << 44;
-  unsigned r = ((unsigned)eb << 7) | (unsigned)keep;
-  if (rem > half || (rem == half && (keep & 1))) r += 1;   // a carry rounds into the exponent
-  return (unsigned short)((sign << 15) | r);
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const int eb = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
+  if (__builtin_expect((unsigned)(eb - 1) >= 254u, 0)) return bf16_bits_slow(x);
+  const unsigned keep = (hi >> 13) & 0x7Fu;   // top 7 of the 52 mantissa bits
+  const unsigned remh = hi & 0x1FFFu;         // the other 45 bits are remh:lo; half is 0x1000:0
+  unsigned r = ((unsigned)eb << 7) | keep;
+  const bool above = remh > 0x1000u || (remh == 0x1000u && lo != 0u);
+  const bool tie = remh == 0x1000u && lo == 0u;
+  if (above || (tie && (keep & 1u))) r += 1;   // a carry rounds into the exponent
+  return (unsigned short)(((hi >> 31) << 15) | r);
 }
 
 // Round-to-nearest, ties away from zero, of a double to TF32 (an FP32 bit pattern whose low
-// 13 mantissa bits are zero), as cvt.rna.tf32.f32 would round the exact value.
+// 13 mantissa bits are zero), as cvt.rna.tf32.f32 would round the exact value.  Integer
+// operations as above.
 __device__ __forceinline__ float f64_to_tf32(double x) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-  const unsigned sign = (unsigned)(u >> 63);
-  const int e = (int)((u >> 52) & 0x7FF);
-  const int ef = e - 1023 + 127;
-  if (e == 0 && (u << 1) == 0) return __uint_as_float(sign << 31);
-  if (__builtin_expect(ef < 1 || ef > 254, 0)) return tf32_slow(x);
-  const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
-  const unsigned long long keep = m >> 42, rem = m & ((1ull << 42) - 1), half = 1ull << 41;
-  unsigned r = ((unsigned)ef << 10) | (unsigned)keep;
-  if (rem >= half) r += 1;
-  return __uint_as_float((sign << 31) | (r << 13));
+  const unsigned hi = (unsigned)__double2hiint(x);
+  const int ef = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
+  if (__builtin_expect((unsigned)(ef - 1) >= 254u, 0)) return tf32_slow(x);
+  const unsigned keep = (hi >> 10) & 0x3FFu;   // top 10 mantissa bits
+  unsigned r = ((unsigned)ef << 10) | keep;
+  if ((hi & 0x3FFu) >= 0x200u) r += 1;         // the other 42 bits at or above half
+  return __uint_as_float(((hi >> 31) << 31) | (r << 13));
 }
 
-// Exact float -> double for normal floats and zeros.
+// Exact float -> double by integer operations for normal floats; zeros, subnormals,
+// infinities and NaNs take the hardware conversion.
 __device__ __forceinline__ double f32_to_f64(float f) {
   const unsigned u = __float_as_uint(f);
-  const unsigned e = (u >> 23) & 0xFF;
-  if (__builtin_expect(e == 0 || e == 255, 0)) {
-    if ((u << 1) == 0) return __longlong_as_double((long long)((unsigned long long)(u >> 31) << 63));
-    return f64_slow(f);
-  }
-  const unsigned long long bits = ((unsigned long long)(u >> 31) << 63) |
-                                  ((unsigned long long)(e + 896) << 52) |
-                                  ((unsigned long long)(u & 0x7FFFFF) << 29);
-  return __longlong_as_double((long long)bits);
+  const unsigned e = (u >> 23) & 0xFFu;
+  if (__builtin_expect(e - 1u >= 254u, 0)) return f64_slow(f);
+  const unsigned m = u & 0x7FFFFFu;
+  const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | (m >> 3);
+  return __hiloint2double((int)hi, (int)(m << 29));
 }
 
 // Interior-element enumeration of a padded vector: t in [0, nxi^p * Ypad).

@@ -187,6 +187,8 @@ struct dd_ctx {
   double* psi_cell = nullptr;      // natural cell order
   double* wT = nullptr;            // coarse weights per type [type][kpad]: D_i R_i psi
   double* puT = nullptr;           // partition of unity per type [type][kpad]: D_i
+  float* wT32 = nullptr;           // FP32 copies of wT and puT (the prolong-sum of the mixed form)
+  float* puT32 = nullptr;
   int ras = 0;                     // 1: restricted local prolongation (M_RAS2^{-1})
   int gemm_bn_opt = 0;             // local-solve GEMM N tile: 0 autotuned, 128 or 256
   float* ysc = nullptr;            // FP8: per packed row 1 / (s_i s_T) (undoes the operand scales)
@@ -205,6 +207,9 @@ struct dd_ctx {
   double* bandCB = nullptr;   // [type][nloc_max][band+1] column band of L
   double* bandRB = nullptr;   // [type][nloc_max][band+1] row band of L
   double* bandInv = nullptr;  // [type][nloc_max] 1/L_ii
+  float* bandCB32 = nullptr;  // the same in FP32: the mixed form, whose inverses are rounded
+  float* bandRB32 = nullptr;
+  float* bandInv32 = nullptr;
   double* Y64 = nullptr;      // [nsub][kpad] local solutions (FP64 path)
   float* Y32 = nullptr;       // [nsub][kpad] local solutions (GEMM path)
   void* Ainv = nullptr;       // [type][kpad][kpad] rounded local inverses
@@ -224,6 +229,7 @@ struct dd_ctx {
   int coarse_dense = 0;       // the form in use
   double* c0 = nullptr;       // coarse rhs [N]
   double* u0 = nullptr;       // coarse solution [N]
+  float* u0f = nullptr;       // the same rounded to FP32 (mixed form)
 
   // reductions
   double* red = nullptr;      // partials
@@ -267,12 +273,14 @@ void launch_prolong(dd_ctx* c, int init, cudaStream_t s, double* zout = nullptr)
 void launch_precond(dd_ctx* c, const double* r, double* z, int pcg_mode, cudaStream_t s);
 
 // local solves
-void launch_local_assemble(dd_ctx* c);
-int launch_band_factor(dd_ctx* c, double* CB, double* RB, double* inv, int nmat, int n, int b, int* flag);
+template <typename T>
+void launch_local_assemble(dd_ctx* c, T* CB);
+// banded Cholesky of nmat matrices (orders in sizes_host, or all n when null); T double or float
+template <typename T>
+int launch_band_factor(dd_ctx* c, T* CB, T* RB, T* inv, int nmat, int n, int b, int* flag, const int* sizes_host);
 void launch_band_solve_local(dd_ctx* c, const double* r, double* c0, cudaStream_t s);
-void launch_band_inverse(dd_ctx* c, double* out, int ld);
-void launch_band_inverse_rows(int n, int b, const double* CB, const double* RB, const double* inv, double* out,
-                              cudaStream_t s);
+template <typename T>
+void launch_band_inverse_rows(int n, int b, const T* CB, const T* RB, const T* inv, T* out, cudaStream_t s);
 
 // cell problem
 int cell_eigenpair(dd_ctx* c);

@@ -7,9 +7,11 @@
 // identical matrices, because the cells are translated copies and V is periodic (A1); the
 // factors are stored once per type.  Local order: (c1, c2, j) with j fastest, so the
 // half bandwidth is nyi + 1 (p = 1) or w2 nyi + nyi + 1 (p = 2).
+#include <algorithm>
 #include <atomic>
 
 #include "dd_band.cuh"
+#include "dd_ritz.cuh"
 
 namespace dd {
 
@@ -27,18 +29,24 @@ namespace dd {
 constexpr int kBandWinMax = 160;
 constexpr int kMaxPairs = 16;   // triangle pairs per thread: b (b + 1) / 2 <= 16 x threads for b <= 160
 
-template <int P>
-__global__ void __launch_bounds__(1024) k_band_factor_win(double* CB, double* inv, const int* __restrict__ nvec,
+__device__ __forceinline__ double rsqrt_el(double v) { return rsqrt(v); }
+__device__ __forceinline__ float rsqrt_el(float v) { return rsqrtf(v); }
+
+// T = double, or float for factors whose inverses are rounded to a tensor-core type and for
+// the cell preconditioner (GB300 issues FP32 at 64x the FP64 rate)
+template <typename T, int P>
+__global__ void __launch_bounds__(1024) k_band_factor_win(T* CB, T* inv, const int* __restrict__ nvec,
                                                           int nmax, int b, int* flag) {
-  extern __shared__ double fsm[];
+  extern __shared__ __align__(16) unsigned char fsm_raw[];
+  T* fsm = reinterpret_cast<T*>(fsm_raw);
   const int m = blockIdx.x;
   const int n = nvec[m];
   const int bs = b + 1, W = b + 1;
   const int t = threadIdx.x;   // owns entry d = t of the columns it stages (bs <= blockDim.x)
-  double* win = fsm;               // W columns x bs entries
-  double* colk = fsm + W * bs;     // L(k+d, k), d = 0..b
-  double* A = CB + (size_t)m * nmax * bs;
-  double* iv = inv + (size_t)m * nmax;
+  T* win = fsm;               // W columns x bs entries
+  T* colk = fsm + W * bs;     // L(k+d, k), d = 0..b
+  T* A = CB + (size_t)m * nmax * bs;
+  T* iv = inv + (size_t)m * nmax;
   // this thread's pairs (d1, d2), 1 <= d2 <= d1 <= b, of the lower triangle of the window
   // update: linear index e = d1 (d1 - 1) / 2 + d2 - 1 taken as e = t, t + T, ...; in that order
   // d1 never decreases, so the pairs beyond the last column's reach form a suffix
@@ -65,7 +73,7 @@ __global__ void __launch_bounds__(1024) k_band_factor_win(double* CB, double* in
   const int first = min(W, n);
   for (int e = t; e < first * bs; e += blockDim.x) win[e] = A[e];
   // entering columns are loaded P steps before they are needed
-  double ring[P];
+  T ring[P];
 #pragma unroll
   for (int u = 0; u < P; ++u) {
     const int j = W + u;
@@ -78,22 +86,39 @@ __global__ void __launch_bounds__(1024) k_band_factor_win(double* CB, double* in
       const int k = k0 + u;
       if (k < n) {
         const int sk = k % W;
-        if (t == 0) {
-          double piv = win[sk * bs];
-          if (!(piv > 0.0)) {
-            atomicOr(flag, 1);
-            piv = 1.0;
+        T il;
+        if constexpr (sizeof(T) == 4) {
+          // FP32: every thread forms the pivot's reciprocal square root itself (identical
+          // values), which saves the barrier that publishing it would take
+          T piv = win[sk * bs];
+          if (!(piv > (T)0)) {
+            if (t == 0) atomicOr(flag, 1);
+            piv = (T)1;
           }
-          const double il = rsqrt(piv);
-          A[(size_t)k * bs] = piv * il;
-          iv[k] = il * il;
-          colk[0] = il;
+          il = rsqrt_el(piv);
+          if (t == 0) {
+            A[(size_t)k * bs] = piv * il;
+            iv[k] = il * il;
+          }
+        } else {
+          // FP64: one thread (the FP64 pipe would pay for every redundant copy)
+          if (t == 0) {
+            T piv = win[sk * bs];
+            if (!(piv > (T)0)) {
+              atomicOr(flag, 1);
+              piv = (T)1;
+            }
+            const T l = rsqrt_el(piv);
+            A[(size_t)k * bs] = piv * l;
+            iv[k] = l * l;
+            colk[0] = l;
+          }
+          __syncthreads();
+          il = colk[0];
         }
-        __syncthreads();
-        const double il = colk[0];
         const int dmax = min(b, n - 1 - k);
         for (int d = 1 + t; d <= b; d += blockDim.x) {
-          double v = 0.0;
+          T v = (T)0;
           if (d <= dmax) {
             v = win[sk * bs + d] * il;           // L(k+d, k)
             A[(size_t)k * bs + d] = v * il;      // pre-scaled by 1/L(k,k)
@@ -101,7 +126,8 @@ __global__ void __launch_bounds__(1024) k_band_factor_win(double* CB, double* in
           colk[d] = v;
         }
         __syncthreads();
-        // A(k+d1, k+d2) -= L(k+d1, k) L(k+d2, k) over this thread's pairs with d1 <= dmax
+        // A(k+d1, k+d2) -= L(k+d1, k) L(k+d2, k) over this thread's pairs with d1 <= dmax;
+        // these touch the slots of columns k+1..k+b only
 #pragma unroll
         for (int j = 0; j < kMaxPairs; ++j) {
           const unsigned half = (j & 1) ? (pr[j >> 1] >> 16) : (pr[j >> 1] & 0xFFFFu);
@@ -109,45 +135,48 @@ __global__ void __launch_bounds__(1024) k_band_factor_win(double* CB, double* in
           if (j < npr && d1 <= dmax) {
             int slot = sk + d2;                  // ring slot of column k + d2
             if (slot >= W) slot -= W;
-            double* a = win + slot * bs + (d1 - d2);
-            *a = fma(-colk[d1], colk[d2], *a);
+            T* a = win + slot * bs + (d1 - d2);
+            *a = fma_el(-colk[d1], colk[d2], *a);
           }
         }
-        __syncthreads();
-        // the slot of column k is free: store column k + W (untouched so far), prefetch k + W + P
+        // the slot of column k is free (read before the barrier above): store column k + W
+        // (untouched so far) and prefetch k + W + P
         if (k + W < n && t < bs) win[sk * bs + t] = ring[u];
         const int j = k + W + P;
         ring[u] = A[(size_t)min(j, n - 1) * bs + min(t, b)];
+        __syncthreads();
       }
     }
   }
 }
 
-__global__ void __launch_bounds__(1024) k_band_factor(double* CB, double* inv, const int* __restrict__ nvec,
+template <typename T>
+__global__ void __launch_bounds__(1024) k_band_factor(T* CB, T* inv, const int* __restrict__ nvec,
                                                       int nmax, int b, int* flag) {
-  extern __shared__ double colk[];
+  extern __shared__ __align__(16) unsigned char colk_raw[];
+  T* colk = reinterpret_cast<T*>(colk_raw);
   const int m = blockIdx.x;
   const int n = nvec[m];
   const int bs = b + 1;
-  double* A = CB + (size_t)m * nmax * bs;
-  double* iv = inv + (size_t)m * nmax;
+  T* A = CB + (size_t)m * nmax * bs;
+  T* iv = inv + (size_t)m * nmax;
   for (int k = 0; k < n; ++k) {
     if (threadIdx.x == 0) {
-      double piv = A[(size_t)k * bs];
-      if (!(piv > 0.0)) {
+      T piv = A[(size_t)k * bs];
+      if (!(piv > (T)0)) {
         atomicOr(flag, 1);
-        piv = 1.0;
+        piv = (T)1;
       }
-      const double l = sqrt(piv);
+      const T l = sqrt(piv);
       A[(size_t)k * bs] = l;
-      iv[k] = 1.0 / piv;
-      colk[0] = 1.0 / l;
+      iv[k] = (T)1 / piv;
+      colk[0] = (T)1 / l;
     }
     __syncthreads();
-    const double il = colk[0];
+    const T il = colk[0];
     const int dmax = min(b, n - 1 - k);
     for (int d = 1 + threadIdx.x; d <= b; d += blockDim.x) {
-      double v = 0.0;
+      T v = (T)0;
       if (d <= dmax) v = A[(size_t)k * bs + d] * il;
       colk[d] = v;
     }
@@ -157,8 +186,8 @@ __global__ void __launch_bounds__(1024) k_band_factor(double* CB, double* inv, c
     for (int t = threadIdx.x; t < tot; t += blockDim.x) {
       const int d1 = t / dmax + 1, d2 = t % dmax + 1;
       if (d2 <= d1) {
-        double* a = A + (size_t)(k + d2) * bs + (d1 - d2);
-        *a = fma(-colk[d1], colk[d2], *a);
+        T* a = A + (size_t)(k + d2) * bs + (d1 - d2);
+        *a = fma_el(-colk[d1], colk[d2], *a);
       }
     }
     for (int d = 1 + threadIdx.x; d <= dmax; d += blockDim.x) A[(size_t)k * bs + d] = colk[d] * il;
@@ -167,11 +196,13 @@ __global__ void __launch_bounds__(1024) k_band_factor(double* CB, double* inv, c
 }
 
 // launch the factorisation of nmat band matrices (sizes in nvec) and build the row band
-static void factor_launch(const Geo&, double* CB, double* RB, double* inv, const int* nvec, int nmat, int nmax, int b,
-                          int* flag, cudaStream_t s);
+template <typename T>
+static void factor_launch(T* CB, T* RB, T* inv, const int* nvec, int nmat, int nmax, int b, int* flag,
+                          cudaStream_t s);
 
 // RB[i][d] = L(i, i-d) = CB[i-d][d]
-__global__ void k_band_rows(const double* __restrict__ CB, double* RB, const int* __restrict__ nvec,
+template <typename T>
+__global__ void k_band_rows(const T* __restrict__ CB, T* RB, const int* __restrict__ nvec,
                             int nmat, int nmax, int b) {
   const int bs = b + 1;
   const long long total = (long long)nmat * nmax * bs;
@@ -181,54 +212,56 @@ __global__ void k_band_rows(const double* __restrict__ CB, double* RB, const int
     const long long rem = t - (long long)m * nmax * bs;
     const int i = (int)(rem / bs), d = (int)(rem % bs);
     const int n = nvec[m];
-    double v = 0.0;
+    T v = (T)0;
     if (i < n && i - d >= 0) v = CB[((size_t)m * nmax + (i - d)) * bs + d];
     RB[t] = v;
   }
 }
 
-int launch_band_factor(dd_ctx* c, double* CB, double* RB, double* inv, int nmat, int nmax, int b, int* flag) {
-  // nvec: sizes of the matrices, taken from ctx scratch (c->dev_err + 16 ...) -> use a temp
+template <typename T>
+int launch_band_factor(dd_ctx* c, T* CB, T* RB, T* inv, int nmat, int nmax, int b, int* flag,
+                       const int* sizes_host) {
   int* nvec = nullptr;
   DD_CUDA(cudaMallocAsync(&nvec, sizeof(int) * nmat, c->stream));
-  std::vector<int> nh(nmat);
-  if (CB == c->bandCB) {
-    for (int t = 0; t < nmat; ++t) nh[t] = c->type_nloc[t];
-  } else {
-    for (int t = 0; t < nmat; ++t) nh[t] = nmax;
-  }
+  std::vector<int> nh(nmat, nmax);
+  if (sizes_host != nullptr)
+    for (int t = 0; t < nmat; ++t) nh[t] = sizes_host[t];
   DD_CUDA(cudaMemcpyAsync(nvec, nh.data(), sizeof(int) * nmat, cudaMemcpyHostToDevice, c->stream));
-  factor_launch(c->g, CB, RB, inv, nvec, nmat, nmax, b, flag, c->stream);
+  factor_launch(CB, RB, inv, nvec, nmat, nmax, b, flag, c->stream);
   DD_CUDA(cudaFreeAsync(nvec, c->stream));
   return DD_OK;
 }
+template int launch_band_factor<double>(dd_ctx*, double*, double*, double*, int, int, int, int*, const int*);
+template int launch_band_factor<float>(dd_ctx*, float*, float*, float*, int, int, int, int*, const int*);
 
-static void factor_launch(const Geo&, double* CB, double* RB, double* inv, const int* nvec, int nmat, int nmax, int b,
-                          int* flag, cudaStream_t s) {
+template <typename T>
+static void factor_launch(T* CB, T* RB, T* inv, const int* nvec, int nmat, int nmax, int b, int* flag,
+                          cudaStream_t s) {
   if (b <= kBandWinMax) {
-    const size_t smem = sizeof(double) * ((size_t)(b + 1) * (b + 1) + (b + 1));
+    const size_t smem = sizeof(T) * ((size_t)(b + 1) * (b + 1) + (b + 1));
     const int tot = b * (b + 1) / 2;   // triangle pairs: at most kMaxPairs per thread
     const int threads = (b * b > 2048) ? (tot > kMaxPairs * 512 ? 1024 : 512) : 256;
-    static std::atomic<bool> attr{false};   // set once per process (idempotent if two threads race)
+    static std::atomic<bool> attr{false};   // set once per process and type (idempotent if two threads race)
     if (!attr) {
-      DD_CUDA(cudaFuncSetAttribute(k_band_factor_win<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+      DD_CUDA(cudaFuncSetAttribute(k_band_factor_win<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
       attr = true;
     }
-    (k_band_factor_win<4><<<nmat, threads, smem, s>>>(CB, inv, nvec, nmax, b, flag), dd::note_launch());
+    (k_band_factor_win<T, 4><<<nmat, threads, smem, s>>>(CB, inv, nvec, nmax, b, flag), dd::note_launch());
   } else {
-    (k_band_factor<<<nmat, 1024, sizeof(double) * (b + 1), s>>>(CB, inv, nvec, nmax, b, flag), dd::note_launch());
+    (k_band_factor<T><<<nmat, 1024, sizeof(T) * (b + 1), s>>>(CB, inv, nvec, nmax, b, flag), dd::note_launch());
   }
   DD_CUDA(cudaGetLastError());
   const long long total = (long long)nmat * nmax * (b + 1);
-  (k_band_rows<<<grid_blocks(total, kThreads), kThreads, 0, s>>>(CB, RB, nvec, nmat, nmax, b), dd::note_launch());
+  (k_band_rows<T><<<grid_blocks(total, kThreads), kThreads, 0, s>>>(CB, RB, nvec, nmat, nmax, b), dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 
 // ----------------------------------------------------------------------------------------
 // Local matrix assembly from the A_sigma stencil table: CB[t][k][k'-k] = A_sigma(k', k), k' >= k.
 // ----------------------------------------------------------------------------------------
+template <typename T>
 __global__ void k_local_assemble(Geo g, const double* __restrict__ tabS, const Sub* __restrict__ rep,
-                                 int ntypes, int nmax, int b, double* CB) {
+                                 int ntypes, int nmax, int b, T* CB) {
   const int bs = b + 1;
   const long long total = (long long)ntypes * nmax;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
@@ -244,7 +277,7 @@ __global__ void k_local_assemble(Geo g, const double* __restrict__ tabS, const S
     int cls;
     if (g.p == 1) cls = (a1 % g.n) * g.Ypad + sj;
     else cls = ((a1 % g.n) * g.n + (a2 % g.n)) * g.Ypad + sj;
-    double* row = CB + ((size_t)ty * nmax + k) * bs;
+    T* row = CB + ((size_t)ty * nmax + k) * bs;
     for (int tap = 0; tap < g.ntap; ++tap) {
       int d1, d2 = 0, dy;
       if (g.p == 1) { d1 = tap / 3 - 1; dy = tap % 3 - 1; }
@@ -253,12 +286,13 @@ __global__ void k_local_assemble(Geo g, const double* __restrict__ tabS, const S
       if (n1 < 0 || n1 >= s.w1 || n2 < 0 || n2 >= s.w2 || nj < 0 || nj >= g.nyi) continue;
       const int kk = (n1 * s.w2 + n2) * g.nyi + nj;
       if (kk < k) continue;
-      row[kk - k] = tabS[(size_t)tap * g.ncls + cls];
+      row[kk - k] = (T)tabS[(size_t)tap * g.ncls + cls];
     }
   }
 }
 
-void launch_local_assemble(dd_ctx* c) {
+template <typename T>
+void launch_local_assemble(dd_ctx* c, T* CB) {
   // representative subdomain of every type
   std::vector<Sub> rep(c->ntypes);
   for (int t = 0; t < c->ntypes; ++t) {
@@ -268,14 +302,16 @@ void launch_local_assemble(dd_ctx* c) {
   Sub* drep = nullptr;
   DD_CUDA(cudaMallocAsync(&drep, sizeof(Sub) * c->ntypes, c->stream));
   DD_CUDA(cudaMemcpyAsync(drep, rep.data(), sizeof(Sub) * c->ntypes, cudaMemcpyHostToDevice, c->stream));
-  const size_t nbytes = sizeof(double) * (size_t)c->ntypes * c->nloc_max * (c->band + 1);
-  DD_CUDA(cudaMemsetAsync(c->bandCB, 0, nbytes, c->stream));
+  const size_t nbytes = sizeof(T) * (size_t)c->ntypes * c->nloc_max * (c->band + 1);
+  DD_CUDA(cudaMemsetAsync(CB, 0, nbytes, c->stream));
   const long long total = (long long)c->ntypes * c->nloc_max;
-  (k_local_assemble<<<grid_blocks(total, 128), 128, 0, c->stream>>>(c->g, c->tabS, drep, c->ntypes,
-                                                                   c->nloc_max, c->band, c->bandCB), dd::note_launch());
+  (k_local_assemble<T><<<grid_blocks(total, 128), 128, 0, c->stream>>>(c->g, c->tabS, drep, c->ntypes,
+                                                                      c->nloc_max, c->band, CB), dd::note_launch());
   DD_CUDA(cudaGetLastError());
   DD_CUDA(cudaFreeAsync(drep, c->stream));
 }
+template void launch_local_assemble<double>(dd_ctx*, double*);
+template void launch_local_assemble<float>(dd_ctx*, float*);
 
 // ----------------------------------------------------------------------------------------
 // FP64 local solves y_i = A_{sigma,i}^{-1} R_i r for every subdomain (one warp each); the
@@ -294,7 +330,7 @@ __global__ void k_local_solve(Geo g, const Sub* __restrict__ subs, const int2* _
   const int gi = blockIdx.x * wpb + wid;
   if (gi >= ngroups) return;
   const int2 grp = groups[gi];   // K (or fewer) consecutive slots of one type
-  constexpr int RING = band_ring_doubles<NV, PF>();
+  constexpr int RING = band_ring_elems<NV, PF>();
   double* xs = xs_all + (size_t)wid * (K * nmax + RING);
   double* ring = xs + (size_t)K * nmax;
   const int type = subs[sub_of_slot[grp.x]].type;
@@ -362,11 +398,9 @@ void launch_band_solve_local(dd_ctx* c, const double* r, double* c0, cudaStream_
 
 // ----------------------------------------------------------------------------------------
 // Cell eigenpair (cell problem of Sec. 1 / weak cell problem of Sec. 2): lowest eigenpair of
-// A_# psi = sigma M_# psi with x-periodic, y-Dirichlet conditions, by shifted inverse
-// iteration with shift s = min V - 1 (A_# - s M_# is SPD because M_V >= min(V) M for a
-// quadrature with positive weights).  The factor uses an interleaved x order
-// (0, n-1, 1, n-2, ...) that keeps periodic neighbours within two positions, so the
-// periodic operator is banded.
+// A_# psi = sigma M_# psi with x-periodic, y-Dirichlet conditions.  The factor of the shifted
+// cell matrix uses an interleaved x order (0, n-1, 1, n-2, ...) that keeps periodic
+// neighbours within two positions, so the periodic operator is banded.
 // ----------------------------------------------------------------------------------------
 __host__ __device__ inline int ipos(int a, int n) { return (2 * a < n) ? 2 * a : 2 * (n - 1 - a) + 1; }
 
@@ -385,8 +419,9 @@ __global__ void __launch_bounds__(1024) k_cell_shift(const double* __restrict__ 
 }
 
 // cell DOF (natural) k = (a1 [n + a2]) nyi + sj; interleaved row ri = (ipos(a1) [n + ipos(a2)]) nyi + sj
+template <typename T>
 __global__ void k_cell_assemble(Geo g, const double* __restrict__ tabA, const double* __restrict__ tabM,
-                                const double* __restrict__ shift, int b, double* CB) {
+                                const double* __restrict__ shift, int b, T* CB) {
   const int bs = b + 1;
   const int ncol = (g.p == 1) ? g.n : g.n * g.n;
   const long long ncell = (long long)ncol * g.nyi;
@@ -421,65 +456,62 @@ __global__ void k_cell_assemble(Geo g, const double* __restrict__ tabA, const do
       }
       if (col < row) continue;
       const size_t ti = (size_t)tap * g.ncls + cls;
-      CB[(size_t)row * bs + (col - row)] += tabA[ti] - s * tabM[ti];
+      CB[(size_t)row * bs + (col - row)] += (T)(tabA[ti] - s * tabM[ti]);
     }
   }
 }
 
-// periodic cell stencil y = T x (natural cell order), CTA-wide
-__device__ void cell_stencil(const Geo& g, const double* __restrict__ tab, const double* x, double* y, int ncell) {
-  for (int k = threadIdx.x; k < ncell; k += blockDim.x) {
-    const int sj = k % g.nyi, cc = k / g.nyi;
-    int a1, a2 = 0, cls;
-    if (g.p == 1) { a1 = cc; cls = a1 * g.Ypad + sj; }
-    else { a1 = cc / g.n; a2 = cc % g.n; cls = (a1 * g.n + a2) * g.Ypad + sj; }
-    double acc = 0.0;
-    for (int tap = 0; tap < g.ntap; ++tap) {
-      int d1, d2 = 0, dy;
-      if (g.p == 1) { d1 = tap / 3 - 1; dy = tap % 3 - 1; }
-      else { d1 = tap / 9 - 1; d2 = (tap / 3) % 3 - 1; dy = tap % 3 - 1; }
-      const int nj = sj + dy;
-      if (nj < 0 || nj >= g.nyi) continue;
-      const int b1 = (a1 + d1 + g.n) % g.n;
-      int kk;
-      if (g.p == 1) kk = b1 * g.nyi + nj;
-      else kk = (b1 * g.n + (a2 + d2 + g.n) % g.n) * g.nyi + nj;
-      acc = fma(__ldg(tab + (size_t)tap * g.ncls + cls), x[kk], acc);
+// value at natural cell index k of the periodic cell stencil T x; the taps are unrolled so
+// that all their loads are in flight at once (x-periodic wrap by compare and add)
+template <int P>
+__device__ __forceinline__ double cell_at(const Geo& g, const double* __restrict__ tab, const double* __restrict__ x,
+                                          int k) {
+  const int sj = k % g.nyi, cc = k / g.nyi;
+  const int a1 = (P == 1) ? cc : cc / g.n, a2 = (P == 1) ? 0 : cc % g.n;
+  const int cls = ((P == 1) ? a1 : a1 * g.n + a2) * g.Ypad + sj;
+  double acc = 0.0;
+#pragma unroll
+  for (int tap = 0; tap < (P == 1 ? 9 : 27); ++tap) {
+    const int d1 = (P == 1) ? tap / 3 - 1 : tap / 9 - 1;
+    const int d2 = (P == 1) ? 0 : (tap / 3) % 3 - 1;
+    const int dy = tap % 3 - 1;
+    const int nj = sj + dy;
+    int b1 = a1 + d1;
+    b1 += (b1 < 0) ? g.n : 0;
+    b1 -= (b1 >= g.n) ? g.n : 0;
+    int b2 = a2 + d2;
+    if (P == 2) {
+      b2 += (b2 < 0) ? g.n : 0;
+      b2 -= (b2 >= g.n) ? g.n : 0;
     }
-    y[k] = acc;
+    const bool ok = nj >= 0 && nj < g.nyi;
+    const int kk = ((P == 1) ? b1 : b1 * g.n + b2) * g.nyi + (ok ? nj : sj);   // in range either way
+    const double tv = __ldg(tab + (size_t)tap * g.ncls + cls), xv = x[kk];
+    if (ok) acc = fma(tv, xv, acc);
   }
+  return acc;
 }
 
-template <int NV>
-__device__ void cta_sum(double (&v)[NV]) {   // result broadcast to every thread
-  __shared__ double res[NV];
-  block_sum<NV>(v);
-  if (threadIdx.x == 0)
-    for (int k = 0; k < NV; ++k) res[k] = v[k];
-  __syncthreads();
-  for (int k = 0; k < NV; ++k) v[k] = res[k];
-  __syncthreads();
-}
-
-struct CellOut {
-  double sigma, eta, drho, shift;
-  int iters, status;
-};
-
-constexpr int kCellThreads = 512;
-
-// ---- cell inverse iteration on a dense inverse -------------------------------------------
-// G = (A_# - s M_#)^{-1} is formed once per shift from the band factor (every column an
-// independent band solve, one warp each, all in parallel) and permuted to the natural cell
-// order; each inverse-iteration step is then y = M_# x (stencil), w = G y (a GEMV across the
-// GPU) and one CTA that normalises, forms rho and eta and applies the stop rule.  The state
-// lives on the device; the host reads it every few steps.
-struct CellState {
-  double rho, rho_prev, eta, eta_prev, drho;
+// ---- cell eigen-solve: LOPCG preconditioned by an FP32 shift-and-invert ------------------
+// The lowest eigenpair of A_# psi = sigma M_# psi by locally optimal preconditioned
+// iterations on S = [x_k, w_k, x_{k-1}] with w_k = T (A_# x_k - rho_k M_# x_k) (the same
+// Rayleigh-Ritz step as Algorithm 1), where T is the dense inverse of A_# - s M_#,
+// s = min V - 1 (SPD because M_V >= min(V) M for a quadrature with positive weights), formed
+// in FP32 from an FP32 banded Cholesky.  T only steers the search direction: every residual,
+// Gram matrix and Rayleigh quotient is formed in FP64 from the FP64 stencils, so the pair is
+// accurate to FP64 whatever T's rounding.  One factorisation and one inverse replace the
+// two FP64 factorisations of a two-shift inverse iteration; the FP32 factor runs at GB300's
+// FP32 rate (64 lanes per FP64 lane).
+struct CellLop {
+  LopState ls;   // Gram matrices, Ritz coefficients and value (theta) of the last step
+  double rho, rho_prev, eta, eta_prev, drho, xmx;
   int iters, stable, done, status;
 };
 
-__global__ void k_cell_perm_dense(Geo g, int ncell, const double* __restrict__ Gi, double* __restrict__ Gn) {
+constexpr int kCellBlock = 64;   // small blocks: the cell vectors are short, spread them over SMs
+
+template <typename T>
+__global__ void k_cell_perm_dense(Geo g, int ncell, const T* __restrict__ Gi, T* __restrict__ Gn) {
   // Gn[i][j] = Gi[pos(i)][pos(j)], natural index k = (a1 [n + a2]) nyi + sj
   const long long total = (long long)ncell * ncell;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
@@ -498,247 +530,253 @@ __global__ void k_cell_perm_dense(Geo g, int ncell, const double* __restrict__ G
   }
 }
 
-// y = M_# x over the cell, grid-wide
-__global__ void k_cell_mass(Geo g, int ncell, const double* __restrict__ tabM, const double* __restrict__ x,
-                            double* __restrict__ y, const CellState* cs) {
-  if (cs->done) return;
+// theta_0 = x^T A_# x / x^T M_# x of the start vector
+template <int P>
+__global__ void __launch_bounds__(kCellBlock) k_cl_init(Geo g, int ncell, const double* __restrict__ tabA,
+                                                        const double* __restrict__ tabM, const double* __restrict__ x,
+                                                        CellLop* cl, double* partials, unsigned* counter) {
+  double acc[2] = {0.0, 0.0};
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ncell; k += gridDim.x * blockDim.x) {
-    const int sj = k % g.nyi, cc = k / g.nyi;
-    int a1, a2 = 0, cls;
-    if (g.p == 1) { a1 = cc; cls = a1 * g.Ypad + sj; }
-    else { a1 = cc / g.n; a2 = cc % g.n; cls = (a1 * g.n + a2) * g.Ypad + sj; }
-    double acc = 0.0;
-    for (int tap = 0; tap < g.ntap; ++tap) {
-      int d1, d2 = 0, dy;
-      if (g.p == 1) { d1 = tap / 3 - 1; dy = tap % 3 - 1; }
-      else { d1 = tap / 9 - 1; d2 = (tap / 3) % 3 - 1; dy = tap % 3 - 1; }
-      const int nj = sj + dy;
-      if (nj < 0 || nj >= g.nyi) continue;
-      const int b1 = (a1 + d1 + g.n) % g.n;
-      const int kk = (g.p == 1) ? b1 * g.nyi + nj : (b1 * g.n + (a2 + d2 + g.n) % g.n) * g.nyi + nj;
-      acc = fma(__ldg(tabM + (size_t)tap * g.ncls + cls), x[kk], acc);
+    acc[0] = fma(x[k], cell_at<P>(g, tabA, x, k), acc[0]);
+    acc[1] = fma(x[k], cell_at<P>(g, tabM, x, k), acc[1]);
+  }
+  double tot[2];
+  if (grid_sum_last<2>(acc, partials, counter, tot) && threadIdx.x == 0) {
+    cl->ls.theta = tot[0] / tot[1];
+    if (!(tot[1] > 0.0) || !isfinite(cl->ls.theta)) {
+      cl->status = DD_ENAN;
+      cl->done = 1;
     }
-    y[k] = acc;
   }
 }
 
-// w = G y, warp per row
-__global__ void k_cell_gemv(int n, const double* __restrict__ G, const double* __restrict__ y, double* __restrict__ w,
-                            const CellState* cs) {
-  if (cs->done) return;
+// r = A_# x - theta M_# x (to FP32 for the preconditioner), rho = Rayleigh quotient of x,
+// eta = ||A x - rho M x|| / (|rho| ||M x||) (with theta, the Ritz value, equal to rho up to
+// rounding), and the stop rule
+template <int P>
+__global__ void __launch_bounds__(kCellBlock) k_cl_resid(Geo g, int ncell, const double* __restrict__ tabA,
+                                                         const double* __restrict__ tabM, const double* __restrict__ x,
+                                                         float* __restrict__ rf, double tol_eta,
+                                                         int maxit, CellLop* cl, double* partials, unsigned* counter) {
+  if (cl->done) return;
+  const double th = cl->ls.theta;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ncell; k += gridDim.x * blockDim.x) {
+    const double ax = cell_at<P>(g, tabA, x, k), mx = cell_at<P>(g, tabM, x, k);
+    const double r = fma(-th, mx, ax);
+    rf[k] = __double2float_rn(r);
+    acc[0] = fma(r, r, acc[0]);
+    acc[1] = fma(mx, mx, acc[1]);
+    acc[2] = fma(x[k], ax, acc[2]);
+    acc[3] = fma(x[k], mx, acc[3]);
+  }
+  double tot[4];
+  if (grid_sum_last<4>(acc, partials, counter, tot) && threadIdx.x == 0) {
+    const double rho = tot[2] / tot[3];
+    const double eta = sqrt(tot[0] / tot[1]) / fabs(rho);
+    const double drho = fabs(rho - cl->rho_prev);
+    cl->iters += 1;
+    cl->rho = rho;
+    cl->eta = eta;
+    cl->drho = drho;
+    cl->xmx = tot[3];
+    if (!isfinite(rho) || !isfinite(eta)) {
+      cl->status = DD_ENAN;
+      cl->done = 1;
+    } else {
+      // past the residual target, go on while the residual still halves: psi enters the
+      // coarse space twice (A_0 = Z^T A_sigma Z), so it is driven to its rounding floor, which
+      // the cheap steps reach a few steps later; the Rayleigh quotient (error ~ eta^2) has long
+      // been stationary by then
+      if (eta <= tol_eta && eta >= 0.5 * cl->eta_prev) cl->stable += 1;
+      else cl->stable = 0;
+      if (cl->stable >= 2) cl->done = 1;
+      else if (cl->iters >= maxit) {
+        cl->status = DD_EMAXIT;
+        cl->done = 1;
+      }
+    }
+    cl->eta_prev = eta;
+    cl->rho_prev = rho;
+  }
+}
+
+// w = T r, warp per row, FP32 (T steers the search direction only)
+__global__ void k_cl_gemv(int n, const float* __restrict__ G, const float* __restrict__ r, double* __restrict__ w,
+                          const CellLop* cl) {
+  if (cl->done) return;
   const int lane = threadIdx.x & 31;
   const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (row >= n) return;
-  const double* gr = G + (size_t)row * n;
-  double acc = 0.0;
-  for (int k = lane; k < n; k += 32) acc = fma(gr[k], y[k], acc);
-  acc = warp_sum(acc);
-  if (lane == 0) w[row] = acc;
+  const float* gr = G + (size_t)row * n;
+  float acc = 0.0f;
+  for (int k = lane; k < n; k += 32) acc = fmaf(__ldg(gr + k), __ldg(r + k), acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+  if (lane == 0) w[row] = f32_to_f64(acc);
 }
 
-// x = w / ||w||_M (sign: sum > 0), rho = x^T A_# x, eta = ||A x - rho M x|| / (|rho| ||M x||), stop rule
-__global__ void __launch_bounds__(kCellThreads) k_cell_update(Geo g, int ncell, const double* __restrict__ tabA,
-                                                             const double* __restrict__ tabM, const double* w,
-                                                             double* x, double tol_drho, double tol_eta, int maxit,
-                                                             CellState* cs) {
-  if (cs->done) return;
-  extern __shared__ double sm[];
-  double* xs = sm;            // w, then x
-  double* ys = sm + ncell;    // M x
-  double* zs = sm + 2 * ncell;
-  for (int k = threadIdx.x; k < ncell; k += blockDim.x) xs[k] = w[k];
-  __syncthreads();
-  cell_stencil(g, tabM, xs, ys, ncell);
-  __syncthreads();
-  double d2[2] = {0.0, 0.0};
-  for (int k = threadIdx.x; k < ncell; k += blockDim.x) {
-    d2[0] = fma(xs[k], ys[k], d2[0]);
-    d2[1] += xs[k];
-  }
-  cta_sum<2>(d2);
-  if (!(d2[0] > 0.0)) {
-    if (threadIdx.x == 0) { cs->status = DD_ENAN; cs->done = 1; }
-    return;
-  }
-  const double sc = (d2[1] < 0.0 ? -1.0 : 1.0) / sqrt(d2[0]);
-  for (int k = threadIdx.x; k < ncell; k += blockDim.x) {
-    xs[k] *= sc;
-    ys[k] *= sc;
-  }
-  __syncthreads();
-  cell_stencil(g, tabA, xs, zs, ncell);
-  __syncthreads();
-  double d1[1] = {0.0};
-  for (int k = threadIdx.x; k < ncell; k += blockDim.x) d1[0] = fma(xs[k], zs[k], d1[0]);
-  cta_sum<1>(d1);
-  const double rho = d1[0];
-  double d3[2] = {0.0, 0.0};
-  for (int k = threadIdx.x; k < ncell; k += blockDim.x) {
-    const double e = fma(-rho, ys[k], zs[k]);
-    d3[0] = fma(e, e, d3[0]);
-    d3[1] = fma(ys[k], ys[k], d3[1]);
-  }
-  cta_sum<2>(d3);
-  for (int k = threadIdx.x; k < ncell; k += blockDim.x) x[k] = xs[k];
-  if (threadIdx.x == 0) {
-    const double eta = sqrt(d3[0] / d3[1]) / fabs(rho);
-    const double drho = fabs(rho - cs->rho_prev);
-    cs->iters += 1;
-    cs->rho = rho;
-    cs->eta = eta;
-    cs->drho = drho;
-    if (!isfinite(rho)) {
-      cs->status = DD_ENAN;
-      cs->done = 1;
-    } else {
-      // at the residual target, stop once the Rayleigh quotient is stationary or the residual
-      // no longer improves (its rounding floor grows as the shift nears sigma_1)
-      if (eta <= tol_eta && (drho <= tol_drho * fabs(rho) || eta >= 0.5 * cs->eta_prev)) cs->stable += 1;
-      else cs->stable = 0;
-      if (cs->stable >= 2) cs->done = 1;
-      else if (cs->iters >= maxit) {
-        cs->status = DD_EMAXIT;
-        cs->done = 1;
+// Gram matrices of S = [x, w, xp] under A_# and M_# (images formed on the fly: the cell
+// vectors are short) and the Rayleigh-Ritz step in the last block
+template <int P>
+__global__ void __launch_bounds__(kCellBlock) k_cl_gram(Geo g, int ncell, const double* __restrict__ tabA,
+                                                        const double* __restrict__ tabM, const double* __restrict__ x,
+                                                        const double* __restrict__ w, const double* __restrict__ xp,
+                                                        CellLop* cl, double* partials, unsigned* counter,
+                                                        double drop) {
+  if (cl->done) return;
+  double acc[15];
+#pragma unroll
+  for (int k = 0; k < 15; ++k) acc[k] = 0.0;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ncell; k += gridDim.x * blockDim.x) {
+    const double v[3] = {x[k], w[k], xp[k]};
+    const double a[3] = {cell_at<P>(g, tabA, x, k), cell_at<P>(g, tabA, w, k), cell_at<P>(g, tabA, xp, k)};
+    const double m[3] = {cell_at<P>(g, tabM, x, k), cell_at<P>(g, tabM, w, k), cell_at<P>(g, tabM, xp, k)};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = i; j < 3; ++j) {
+        acc[sym3(i, j)] = fma(v[i], a[j], acc[sym3(i, j)]);
+        acc[6 + sym3(i, j)] = fma(v[i], m[j], acc[6 + sym3(i, j)]);
       }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) acc[12 + i] += v[i];
+  }
+  double tot[15];
+  if (grid_sum_last<15>(acc, partials, counter, tot) && threadIdx.x == 0) {
+    LopState* ls = &cl->ls;
+    for (int k = 0; k < 6; ++k) {
+      ls->GA[k] = tot[k];
+      ls->GB[k] = tot[6 + k];
     }
-    cs->eta_prev = eta;
-    cs->rho_prev = rho;
+    for (int k = 0; k < 3; ++k) ls->sums[k] = tot[12 + k];
+    ls->status = 0;
+    rayleigh_ritz3(ls, drop);
+    if (ls->status != 0) {
+      cl->status = ls->status;
+      cl->done = 1;
+    }
   }
 }
 
-// one phase of the cell solve: assemble A_# - s M_#, factor, invert, iterate; returns false
-// if the factorisation met a non-positive pivot (s not below sigma_1)
-static bool cell_phase(dd_ctx* c, double* shift, bool from_minV, double margin_frac, int warm, double tol_drho,
-                       double tol_eta, int maxit, CellOut* out_h) {
-  const Geo& g = c->g;
-  const int ncell = (int)c->ncell;
-  const int b = c->cell_band;
-  const size_t cbsz = sizeof(double) * (size_t)ncell * (b + 1);
-  const size_t gsz = sizeof(double) * (size_t)ncell * ncell;
-  double *CB = nullptr, *RB = nullptr, *inv = nullptr, *Gi = nullptr, *Gn = nullptr, *y = nullptr, *w = nullptr;
-  CellState* cs = nullptr;
-  int* flag = c->dev_err + 1;
-  int* nvec = nullptr;
-  DD_CUDA(cudaMallocAsync(&CB, cbsz, c->stream));
-  DD_CUDA(cudaMallocAsync(&RB, cbsz, c->stream));
-  DD_CUDA(cudaMallocAsync(&inv, sizeof(double) * ncell, c->stream));
-  DD_CUDA(cudaMallocAsync(&nvec, sizeof(int), c->stream));
-  DD_CUDA(cudaMemsetAsync(CB, 0, cbsz, c->stream));
-  DD_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), c->stream));
-  DD_CUDA(cudaMemcpyAsync(nvec, &ncell, sizeof(int), cudaMemcpyHostToDevice, c->stream));
-  if (from_minV) {
-    long long nV = (long long)((g.p == 1) ? g.n : g.n * g.n) * g.ny;
-    for (int k = 0; k <= g.p; ++k) nV *= g.Q;
-    (k_cell_shift<<<1, 1024, 0, c->stream>>>(c->Vqp, nV, shift), dd::note_launch());
-  } else {
-    // shift = rho - margin_frac (rho - s_previous), from the previous phase's result
-    const double s_new = out_h->sigma - margin_frac * (out_h->sigma - out_h->shift);
-    DD_CUDA(cudaMemcpyAsync(shift, &s_new, sizeof(double), cudaMemcpyHostToDevice, c->stream));
-  }
-  (k_cell_assemble<<<grid_blocks(ncell, 128), 128, 0, c->stream>>>(g, c->tabA, c->tabM, shift, b, CB), dd::note_launch());
-  factor_launch(g, CB, RB, inv, nvec, 1, ncell, b, flag, c->stream);
-  int fl = 0;
-  DD_CUDA(cudaMemcpyAsync(&fl, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  DD_CUDA(cudaStreamSynchronize(c->stream));
-  bool ok = (fl == 0);
-  if (ok) {
-    DD_CUDA(cudaMallocAsync(&Gi, gsz, c->stream));
-    DD_CUDA(cudaMallocAsync(&Gn, gsz, c->stream));
-    DD_CUDA(cudaMallocAsync(&y, sizeof(double) * ncell, c->stream));
-    DD_CUDA(cudaMallocAsync(&w, sizeof(double) * ncell, c->stream));
-    DD_CUDA(cudaMallocAsync(&cs, sizeof(CellState), c->stream));
-    launch_band_inverse_rows(ncell, b, CB, RB, inv, Gi, c->stream);
-    (k_cell_perm_dense<<<grid_blocks((long long)ncell * ncell, kThreads), kThreads, 0, c->stream>>>(g, ncell, Gi, Gn),
-     dd::note_launch());
-    CellState init{};
-    init.rho_prev = 1e300;
-    init.eta_prev = 1e300;
-    DD_CUDA(cudaMemcpyAsync(cs, &init, sizeof(init), cudaMemcpyHostToDevice, c->stream));
-    if (!warm) {
-      std::vector<double> ones((size_t)ncell, 1.0);
-      DD_CUDA(cudaMemcpyAsync(c->psi_cell, ones.data(), sizeof(double) * ncell, cudaMemcpyHostToDevice, c->stream));
-      DD_CUDA(cudaStreamSynchronize(c->stream));
-    }
-    const size_t smem = sizeof(double) * 3 * (size_t)ncell;
-    DD_CUDA(cudaFuncSetAttribute(k_cell_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int gemv_blocks = (ncell + 7) / 8;
-    CellState h{};
-    for (int it = 0; it < maxit; it += 4) {
-      for (int k = 0; k < 4; ++k) {
-        (k_cell_mass<<<grid_blocks(ncell, 256), 256, 0, c->stream>>>(g, ncell, c->tabM, c->psi_cell, y, cs),
-         dd::note_launch());
-        (k_cell_gemv<<<gemv_blocks, 256, 0, c->stream>>>(ncell, Gn, y, w, cs), dd::note_launch());
-        (k_cell_update<<<1, kCellThreads, smem, c->stream>>>(g, ncell, c->tabA, c->tabM, w, c->psi_cell, tol_drho,
-                                                           tol_eta, maxit, cs), dd::note_launch());
-      }
-      DD_CUDA(cudaGetLastError());
-      DD_CUDA(cudaMemcpyAsync(&h, cs, sizeof(CellState), cudaMemcpyDeviceToHost, c->stream));
-      DD_CUDA(cudaStreamSynchronize(c->stream));
-      if (h.done) break;
-    }
-    double sh = 0.0;
-    DD_CUDA(cudaMemcpyAsync(&sh, shift, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    DD_CUDA(cudaStreamSynchronize(c->stream));
-    out_h->sigma = h.rho;
-    out_h->eta = h.eta;
-    out_h->drho = h.drho;
-    out_h->iters = h.iters;
-    out_h->status = h.done ? h.status : DD_EMAXIT;
-    out_h->shift = sh;
-    DD_CUDA(cudaFreeAsync(Gi, c->stream));
-    DD_CUDA(cudaFreeAsync(Gn, c->stream));
-    DD_CUDA(cudaFreeAsync(y, c->stream));
-    DD_CUDA(cudaFreeAsync(w, c->stream));
-    DD_CUDA(cudaFreeAsync(cs, c->stream));
-  }
-  DD_CUDA(cudaFreeAsync(CB, c->stream));
-  DD_CUDA(cudaFreeAsync(RB, c->stream));
-  DD_CUDA(cudaFreeAsync(inv, c->stream));
-  DD_CUDA(cudaFreeAsync(nvec, c->stream));
-  DD_CUDA(cudaStreamSynchronize(c->stream));
-  return ok;
+// x_{k+1} = c0 x_k + c1 w_k + c2 x_{k-1}
+__global__ void k_cl_update(int ncell, const double* __restrict__ x, const double* __restrict__ w,
+                            const double* __restrict__ xp, double* __restrict__ xn, const CellLop* cl) {
+  if (cl->done) return;
+  const double c0 = cl->ls.c[0], c1 = cl->ls.c[1], c2 = cl->ls.c[2];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ncell; k += gridDim.x * blockDim.x)
+    xn[k] = fma(c0, x[k], fma(c1, w[k], c2 * xp[k]));
 }
 
-// Two phases: shift s0 = min V - 1 (safe) until the Rayleigh quotient has settled to 1e-6,
-// then s1 = rho - 0.02 (rho - s0), warm-started, to full accuracy.  The refined shift is
-// below sigma_1 whenever the eigenvalue error is under 2% of rho - s0; if it is not, the
-// factorisation meets a non-positive pivot and the solve continues with the safe shift
-// (a larger margin is tried first).
+// psi = x / ||x||_M
+__global__ void k_cl_final(int ncell, const double* __restrict__ x, double* __restrict__ psi, const CellLop* cl) {
+  const double sc = 1.0 / sqrt(cl->xmx);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ncell; k += gridDim.x * blockDim.x) psi[k] = sc * x[k];
+}
+
 int cell_eigenpair(dd_ctx* c) {
   const Geo& g = c->g;
   const int ncol = (g.p == 1) ? g.n : g.n * g.n;
-  c->ncell = (long long)ncol * g.nyi;
-  c->cell_band = (g.p == 1) ? 2 * g.nyi + 1 : 2 * g.n * g.nyi + 2 * g.nyi + 1;
-  double* shift = nullptr;
-  DD_CUDA(cudaMallocAsync(&shift, sizeof(double), c->stream));
-  CellOut h{};
-  if (!cell_phase(c, shift, true, 0.0, 0, 1e-6, 1e-3, 20000, &h)) {
-    DD_CUDA(cudaFreeAsync(shift, c->stream));
-    throw Error(DD_ENOTSPD, "cell matrix A_# - s M_# not positive definite");
+  const int ncell = ncol * g.nyi;
+  c->ncell = ncell;
+  const int b = (g.p == 1) ? 2 * g.nyi + 1 : 2 * g.n * g.nyi + 2 * g.nyi + 1;
+  c->cell_band = b;
+  cudaStream_t s = c->stream;
+  // ---- T = (A_# - s M_#)^{-1} in FP32, natural cell order
+  const size_t cbsz = sizeof(float) * (size_t)ncell * (b + 1);
+  const size_t gsz = sizeof(float) * (size_t)ncell * ncell;
+  float *CB = nullptr, *RB = nullptr, *inv = nullptr, *Gi = nullptr, *Gn = nullptr, *rf = nullptr;
+  double *shift = nullptr, *vec = nullptr, *part = nullptr;
+  CellLop* cl = nullptr;
+  int* flag = c->dev_err + 1;
+  DD_CUDA(cudaMallocAsync(&shift, sizeof(double), s));
+  DD_CUDA(cudaMallocAsync(&CB, cbsz, s));
+  DD_CUDA(cudaMallocAsync(&RB, cbsz, s));
+  DD_CUDA(cudaMallocAsync(&inv, sizeof(float) * ncell, s));
+  DD_CUDA(cudaMallocAsync(&Gi, gsz, s));
+  DD_CUDA(cudaMallocAsync(&Gn, gsz, s));
+  DD_CUDA(cudaMallocAsync(&rf, sizeof(float) * ncell, s));
+  DD_CUDA(cudaMallocAsync(&vec, sizeof(double) * 4 * (size_t)ncell, s));   // three iterates and w
+  DD_CUDA(cudaMallocAsync(&cl, sizeof(CellLop), s));
+  DD_CUDA(cudaMallocAsync(&part, sizeof(double) * 15 * kMaxRedBlocks, s));   // block partials of the sums
+  DD_CUDA(cudaMemsetAsync(CB, 0, cbsz, s));
+  DD_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), s));
+  {
+    long long nV = (long long)((g.p == 1) ? g.n : g.n * g.n) * g.ny;
+    for (int k = 0; k <= g.p; ++k) nV *= g.Q;
+    (k_cell_shift<<<1, 1024, 0, s>>>(c->Vqp, nV, shift), dd::note_launch());
   }
-  if (h.status != 0 && h.status != DD_EMAXIT) throw Error(h.status, "cell inverse iteration failed");
-  int iters = h.iters;
-  CellOut h1 = h;
-  bool refined = false;
-  for (double frac : {0.02, 0.2}) {
-    CellOut h2 = h1;
-    if (cell_phase(c, shift, false, frac, 1, 1e-14, 1e-10, 2000, &h2)) {
-      h = h2;
-      iters += h2.iters;
-      refined = true;
-      break;
+  (k_cell_assemble<float><<<grid_blocks(ncell, 128), 128, 0, s>>>(g, c->tabA, c->tabM, shift, b, CB),
+   dd::note_launch());
+  launch_band_factor(c, CB, RB, inv, 1, ncell, b, flag, nullptr);
+  launch_band_inverse_rows(ncell, b, CB, RB, inv, Gi, s);
+  (k_cell_perm_dense<float><<<grid_blocks((long long)ncell * ncell, kThreads), kThreads, 0, s>>>(g, ncell, Gi, Gn),
+   dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+  // ---- LOPCG from x_0 = 1
+  double* bufs[3] = {vec, vec + ncell, vec + 2 * (size_t)ncell};
+  double* w = vec + 3 * (size_t)ncell;
+  {
+    std::vector<double> ones((size_t)ncell, 1.0);
+    DD_CUDA(cudaMemcpyAsync(bufs[0], ones.data(), sizeof(double) * ncell, cudaMemcpyHostToDevice, s));
+    DD_CUDA(cudaMemsetAsync(bufs[2], 0, sizeof(double) * ncell, s));   // x_{-1} = 0: dropped by the first step
+    CellLop init{};
+    init.rho_prev = 1e300;
+    init.eta_prev = 1e300;
+    DD_CUDA(cudaMemcpyAsync(cl, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+    DD_CUDA(cudaStreamSynchronize(s));   // the host vectors above are temporaries
+  }
+  const int nbv = std::min((ncell + kCellBlock - 1) / kCellBlock, 152 * 4);
+  const int gemv_blocks = (ncell + 7) / 8;
+  unsigned* cnt = c->cnt + CNT_CELL;
+  const int maxit = 400;
+  const double drop = 1e-10;
+  const bool p1 = g.p == 1;
+  if (p1) (k_cl_init<1><<<nbv, kCellBlock, 0, s>>>(g, ncell, c->tabA, c->tabM, bufs[0], cl, part, cnt), dd::note_launch());
+  else (k_cl_init<2><<<nbv, kCellBlock, 0, s>>>(g, ncell, c->tabA, c->tabM, bufs[0], cl, part, cnt), dd::note_launch());
+  CellLop h{};
+  for (int it = 0; it < maxit; it += 4) {
+    for (int k = 0; k < 4; ++k) {
+      const int j = it + k;
+      double *x = bufs[j % 3], *xn = bufs[(j + 1) % 3], *xp = bufs[(j + 2) % 3];
+      if (p1)
+        (k_cl_resid<1><<<nbv, kCellBlock, 0, s>>>(g, ncell, c->tabA, c->tabM, x, rf, 1e-10, maxit, cl, part, cnt),
+         dd::note_launch());
+      else
+        (k_cl_resid<2><<<nbv, kCellBlock, 0, s>>>(g, ncell, c->tabA, c->tabM, x, rf, 1e-10, maxit, cl, part, cnt),
+         dd::note_launch());
+      (k_cl_gemv<<<gemv_blocks, 256, 0, s>>>(ncell, Gn, rf, w, cl), dd::note_launch());
+      if (p1)
+        (k_cl_gram<1><<<nbv, kCellBlock, 0, s>>>(g, ncell, c->tabA, c->tabM, x, w, xp, cl, part, cnt, drop),
+         dd::note_launch());
+      else
+        (k_cl_gram<2><<<nbv, kCellBlock, 0, s>>>(g, ncell, c->tabA, c->tabM, x, w, xp, cl, part, cnt, drop),
+         dd::note_launch());
+      (k_cl_update<<<nbv, kCellBlock, 0, s>>>(ncell, x, w, xp, xn, cl), dd::note_launch());
     }
+    DD_CUDA(cudaGetLastError());
+    DD_CUDA(cudaMemcpyAsync(&h, cl, sizeof(CellLop), cudaMemcpyDeviceToHost, s));
+    DD_CUDA(cudaStreamSynchronize(s));
+    if (h.done) break;
   }
-  if (!refined) {
-    if (!cell_phase(c, shift, true, 0.0, 1, 1e-14, 1e-10, 20000, &h)) throw Error(DD_ENOTSPD, "cell factorisation");
-    iters += h.iters;
+  int fl = 0;
+  DD_CUDA(cudaMemcpyAsync(&fl, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DD_CUDA(cudaStreamSynchronize(s));
+  int status = h.done ? h.status : DD_EMAXIT;
+  if (h.iters >= 1 && (status == DD_OK || status == DD_EMAXIT)) {
+    // the iterate whose residual passed the test: x_j of the step j = iters - 1
+    (k_cl_final<<<nbv, kCellBlock, 0, s>>>(ncell, bufs[(h.iters - 1) % 3], c->psi_cell, cl), dd::note_launch());
+    DD_CUDA(cudaGetLastError());
   }
-  DD_CUDA(cudaFreeAsync(shift, c->stream));
-  DD_CUDA(cudaStreamSynchronize(c->stream));
-  if (h.status != 0 && h.status != DD_EMAXIT) throw Error(h.status, "cell inverse iteration failed");
-  c->sigma = h.sigma;
-  c->cell_iters = iters;
-  return h.status;
+  for (void* p : {(void*)shift, (void*)CB, (void*)RB, (void*)inv, (void*)Gi, (void*)Gn, (void*)rf, (void*)vec,
+                  (void*)cl, (void*)part})
+    DD_CUDA(cudaFreeAsync(p, s));
+  DD_CUDA(cudaStreamSynchronize(s));
+  if (fl) throw Error(DD_ENOTSPD, "cell matrix A_# - s M_# not positive definite");
+  if (status != DD_OK && status != DD_EMAXIT) throw Error(status, "cell eigen-solve failed");
+  c->sigma = h.rho;
+  c->cell_iters = h.iters;
+  return status;
 }
 
 }  // namespace dd

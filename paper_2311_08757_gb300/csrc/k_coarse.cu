@@ -47,7 +47,8 @@ __device__ double pu_weight(const Geo& g, int pu, int i1, int i2, int a1, int a2
 }
 
 __global__ void k_coarse_weights(Geo g, int pu, const Sub* __restrict__ rep, int ntypes, int kpad,
-                                 const double* __restrict__ psi, double* wT, double* puT) {
+                                 const double* __restrict__ psi, double* wT, double* puT,
+                                 float* wT32, float* puT32) {
   const long long total = (long long)ntypes * kpad;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
@@ -68,6 +69,8 @@ __global__ void k_coarse_weights(Geo g, int pu, const Sub* __restrict__ rep, int
     }
     wT[t] = v;     // D_i R_i psi: the coarse basis function of the type
     puT[t] = d;    // D_i: the partition-of-unity weights (restricted local prolongation)
+    wT32[t] = __double2float_rn(v);
+    puT32[t] = __double2float_rn(d);
   }
 }
 
@@ -86,7 +89,8 @@ void launch_coarse_weights(dd_ctx* c) {
   Sub* rep = upload_reps(c);
   const long long total = (long long)c->ntypes * c->kpad;
   (k_coarse_weights<<<grid_blocks(total, 128), 128, 0, c->stream>>>(c->g, c->grid.pu_kind, rep, c->ntypes,
-                                                                   c->kpad, c->psi_cell, c->wT, c->puT), dd::note_launch());
+                                                                   c->kpad, c->psi_cell, c->wT, c->puT, c->wT32,
+                                                                   c->puT32), dd::note_launch());
   DD_CUDA(cudaGetLastError());
   DD_CUDA(cudaFreeAsync(rep, c->stream));
 }
@@ -221,8 +225,9 @@ __global__ void __launch_bounds__(1024) k_cr_setup(const double* __restrict__ A0
   }
 }
 
-__global__ void __launch_bounds__(1024) k_cr_solve(const double* __restrict__ cr, int N, int m, int Np, const double* __restrict__ rhs,
-                           double* __restrict__ x, const PcgState* st, int staged) {
+__global__ void __launch_bounds__(1024) k_cr_solve(const double* __restrict__ cr, int N, int m, int Np,
+                                                   const double* __restrict__ rhs, double* __restrict__ x,
+                                                   float* __restrict__ xf, const PcgState* st, int staged) {
   if (st != nullptr && st->done) return;
   extern __shared__ double sm_cr[];
   const int W = Np + 2;
@@ -266,50 +271,58 @@ __global__ void __launch_bounds__(1024) k_cr_solve(const double* __restrict__ cr
     }
     __syncthreads();
   }
-  for (int j = threadIdx.x; j < N; j += blockDim.x) x[j] = f[j + 1];
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    x[j] = f[j + 1];
+    xf[j] = __double2float_rn(f[j + 1]);
+  }
 }
 
 // dense inverse rows from the banded factor (identity right-hand sides, K per warp)
-template <int NV, int PF, int K>
-__global__ void k_band_inverse_rows(int n, int b, const double* __restrict__ CB, const double* __restrict__ RB,
-                                    const double* __restrict__ inv, double* out) {
-  extern __shared__ double xs_all[];
+template <typename T, int NV, int PF, int K>
+__global__ void k_band_inverse_rows(int n, int b, const T* __restrict__ CB, const T* __restrict__ RB,
+                                    const T* __restrict__ inv, T* out) {
+  extern __shared__ __align__(16) unsigned char xs_raw[];
+  T* xs_all = reinterpret_cast<T*>(xs_raw);
   const int wpb = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int col0 = (blockIdx.x * wpb + wid) * K;
   if (col0 >= n) return;
-  constexpr int RING = band_ring_doubles<NV, PF>();
-  double* xs = xs_all + (size_t)wid * (K * n + RING);
-  double* ring = xs + (size_t)K * n;
+  constexpr int RING = band_ring_elems<NV, PF>();
+  T* xs = xs_all + (size_t)wid * (K * n + RING);
+  T* ring = xs + (size_t)K * n;
 #pragma unroll
   for (int j = 0; j < K; ++j)
-    for (int k = lane; k < n; k += 32) xs[(size_t)j * n + k] = (k == col0 + j) ? 1.0 : 0.0;
+    for (int k = lane; k < n; k += 32) xs[(size_t)j * n + k] = (k == col0 + j) ? (T)1 : (T)0;
   band_solve_k<NV, PF, K>(xs, n, n, b, CB, RB, inv, ring);
   __syncwarp();
   for (int j = 0; j < K && col0 + j < n; ++j)
     for (int k = lane; k < n; k += 32) out[(size_t)(col0 + j) * n + k] = xs[(size_t)j * n + k];
 }
 
-void launch_band_inverse_rows(int n, int b, const double* CB, const double* RB, const double* inv, double* out,
-                              cudaStream_t s) {
+template <typename T>
+void launch_band_inverse_rows(int n, int b, const T* CB, const T* RB, const T* inv, T* out, cudaStream_t s) {
   const int K = 1;
-  const size_t per = sizeof(double) * (size_t)K * n + band_ring_bytes(b);
+  const size_t per = sizeof(T) * (size_t)K * n + band_ring_bytes(b, sizeof(T));
   const int wpb = per <= 48 * 1024 ? 2 : 1;
   const size_t smem = per * wpb;
   const int ncolgroups = (n + K - 1) / K;
   DD_BAND_DISPATCH(b, {
     {
       constexpr int KK = 1;
-      DD_CUDA(cudaFuncSetAttribute(k_band_inverse_rows<NV, PF, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      DD_CUDA(cudaFuncSetAttribute(k_band_inverse_rows<T, NV, PF, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    220 * 1024));
-      (k_band_inverse_rows<NV, PF, KK><<<(ncolgroups + wpb - 1) / wpb, 32 * wpb, smem, s>>>(n, b, CB, RB, inv, out),
+      (k_band_inverse_rows<T, NV, PF, KK><<<(ncolgroups + wpb - 1) / wpb, 32 * wpb, smem, s>>>(n, b, CB, RB, inv, out),
        dd::note_launch());
     }
   });
   DD_CUDA(cudaGetLastError());
 }
+template void launch_band_inverse_rows<double>(int, int, const double*, const double*, const double*, double*,
+                                               cudaStream_t);
+template void launch_band_inverse_rows<float>(int, int, const float*, const float*, const float*, float*,
+                                              cudaStream_t);
 
 __global__ void k_gemv_rows(int n, const double* __restrict__ A, const double* __restrict__ xin,
-                            double* __restrict__ y, const PcgState* st) {
+                            double* __restrict__ y, float* __restrict__ yf, const PcgState* st) {
   if (st != nullptr && st->done) return;
   const int wpb = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = blockIdx.x * wpb + wid;
@@ -318,7 +331,10 @@ __global__ void k_gemv_rows(int n, const double* __restrict__ A, const double* _
   double acc = 0.0;
   for (int k = lane; k < n; k += 32) acc = fma(ar[k], __ldg(xin + k), acc);
   acc = warp_sum(acc);
-  if (lane == 0) y[row] = acc;
+  if (lane == 0) {
+    y[row] = acc;
+    if (yf != nullptr) yf[row] = __double2float_rn(acc);
+  }
 }
 
 int coarse_factor(dd_ctx* c) {
@@ -363,7 +379,7 @@ int coarse_factor(dd_ctx* c) {
       }
     }
     DD_CUDA(cudaMemcpyAsync(CB, hcb.data(), cb, cudaMemcpyHostToDevice, c->stream));
-    launch_band_factor(c, CB, RB, inv, 1, N, b, flag);
+    launch_band_factor(c, CB, RB, inv, 1, N, b, flag, nullptr);
     if (!c->A0inv) c->A0inv = (double*)dev_alloc(c, sizeof(double) * (size_t)N * N);
     launch_band_inverse_rows(N, b, CB, RB, inv, c->A0inv, c->stream);
   }
@@ -404,11 +420,11 @@ void launch_coarse_solve(dd_ctx* c, cudaStream_t s) {
       DD_CUDA(cudaFuncSetAttribute(k_cr_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
       attr = true;
     }
-    (k_cr_solve<<<1, 1024, smem, s>>>(c->cr, g.nsub, c->cr_m, c->cr_np, c->c0, c->u0, c->st, staged),
+    (k_cr_solve<<<1, 1024, smem, s>>>(c->cr, g.nsub, c->cr_m, c->cr_np, c->c0, c->u0, c->u0f, c->st, staged),
      dd::note_launch());
   } else {
     const int N = g.nsub;
-    (k_gemv_rows<<<(N + 7) / 8, 256, 0, s>>>(N, c->A0inv, c->c0, c->u0, c->st), dd::note_launch());
+    (k_gemv_rows<<<(N + 7) / 8, 256, 0, s>>>(N, c->A0inv, c->c0, c->u0, c->u0f, c->st), dd::note_launch());
   }
   DD_CUDA(cudaGetLastError());
 }

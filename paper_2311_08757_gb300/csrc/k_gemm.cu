@@ -336,11 +336,28 @@ __device__ __forceinline__ __nv_fp8_e4m3 to_e4m3(double v) {
 }
 constexpr double kE4M3Max = 448.0;   // largest finite E4M3 value
 
+// rounding of an FP32 solve result to the operand type (FP64: exact widening, for the FP8
+// path's scaling pass)
+template <typename T>
+__device__ __forceinline__ T round_f32(float v);
+template <>
+__device__ __forceinline__ __nv_bfloat16 round_f32<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <>
+__device__ __forceinline__ float round_f32<float>(float v) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return __uint_as_float(r);
+}
+template <>
+__device__ __forceinline__ double round_f32<double>(float v) { return f32_to_f64(v); }
+
+// Columns of A_T^{-1} by band solves of identity columns with the FP32 factor (the mixed
+// form: the result is rounded to the GEMM's operand type right away), one warp per column.
 template <typename T, int NV, int PF, int K>
-__global__ void k_local_inverse(const int* __restrict__ nloc, int nmax, int b, const double* __restrict__ CB,
-                                const double* __restrict__ RB, const double* __restrict__ inv, int ntypes, int kpad,
+__global__ void k_local_inverse(const int* __restrict__ nloc, int nmax, int b, const float* __restrict__ CB,
+                                const float* __restrict__ RB, const float* __restrict__ inv, int ntypes, int kpad,
                                 T* __restrict__ out) {
-  extern __shared__ double xs_all[];
+  extern __shared__ float xs_all[];
   const int wpb = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int groups_per_type = (nmax + K - 1) / K;
   const long long job = (long long)blockIdx.x * wpb + wid;
@@ -349,18 +366,18 @@ __global__ void k_local_inverse(const int* __restrict__ nloc, int nmax, int b, c
   const int col0 = (int)(job % groups_per_type) * K;
   const int n = nloc[ty];
   if (col0 >= n) return;
-  constexpr int RING = band_ring_doubles<NV, PF>();
-  double* xs = xs_all + (size_t)wid * (K * nmax + RING);
-  double* ring = xs + (size_t)K * nmax;
+  constexpr int RING = band_ring_elems<NV, PF>();
+  float* xs = xs_all + (size_t)wid * (K * nmax + RING);
+  float* ring = xs + (size_t)K * nmax;
 #pragma unroll
   for (int j = 0; j < K; ++j)
-    for (int k = lane; k < n; k += 32) xs[(size_t)j * nmax + k] = (k == col0 + j) ? 1.0 : 0.0;
+    for (int k = lane; k < n; k += 32) xs[(size_t)j * nmax + k] = (k == col0 + j) ? 1.0f : 0.0f;
   const size_t off = (size_t)ty * nmax;
   band_solve_k<NV, PF, K>(xs, nmax, n, b, CB + off * (b + 1), RB + off * (b + 1), inv + off, ring);
   __syncwarp();
   for (int j = 0; j < K && col0 + j < n; ++j) {
     T* row = out + ((size_t)ty * kpad + col0 + j) * kpad;
-    for (int k = lane; k < n; k += 32) row[k] = round_fast<T>(xs[(size_t)j * nmax + k]);
+    for (int k = lane; k < n; k += 32) row[k] = round_f32<T>(xs[(size_t)j * nmax + k]);
   }
 }
 
@@ -536,7 +553,7 @@ template <typename T>
 static void launch_local_inverse_t(dd_ctx* c, const int* nloc, T* out) {
   const int kpad = c->kpad;
   const int K = 1;
-  const size_t per = sizeof(double) * (size_t)K * c->nloc_max + band_ring_bytes(c->band);
+  const size_t per = sizeof(float) * (size_t)K * c->nloc_max + band_ring_bytes(c->band, sizeof(float));
   const int wpb = per <= 48 * 1024 ? 2 : 1;
   const size_t smem = per * wpb;
   const long long jobs = (long long)c->ntypes * ((c->nloc_max + K - 1) / K);
@@ -545,8 +562,8 @@ static void launch_local_inverse_t(dd_ctx* c, const int* nloc, T* out) {
     constexpr int KK = 1;
     DD_CUDA(cudaFuncSetAttribute(k_local_inverse<T, NV, PF, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  220 * 1024));
-    (k_local_inverse<T, NV, PF, KK><<<nb, 32 * wpb, smem, c->stream>>>(nloc, c->nloc_max, c->band, c->bandCB,
-                                                                       c->bandRB, c->bandInv, c->ntypes, kpad, out),
+    (k_local_inverse<T, NV, PF, KK><<<nb, 32 * wpb, smem, c->stream>>>(nloc, c->nloc_max, c->band, c->bandCB32,
+                                                                       c->bandRB32, c->bandInv32, c->ntypes, kpad, out),
      dd::note_launch());
   });
   DD_CUDA(cudaGetLastError());

@@ -531,19 +531,23 @@ void launch_xr_update(dd_ctx* c, cudaStream_t s) {
 //   z = sum_i R_i^T y_i + sum_i (D_i R_i psi) u0_i
 // gathered per node from its (at most 2^p) owning subdomains in a fixed order, with the
 // owners read from per-column tables; fused with (r, z) (and (q, z) for the flexible
-// variant) and the beta update.  With rounded local inverses y is FP32 and the owners'
-// contributions are summed in FP32 before the FP64 coarse term is added.
+// variant) and the beta update.  With rounded local inverses y is FP32, and the whole node
+// value (owners' contributions and the coarse term, from FP32 copies of the weights and of
+// u0) is formed in FP32 and widened exactly: the FP64 pipe then carries only the dot
+// products.
 //   mode 0: preconditioner only (no scalars); 1: PCG start (rho = (r,z), beta = 0);
 //   2: PCG iteration (beta standard or flexible).
 // ----------------------------------------------------------------------------------------
 __device__ __forceinline__ double to_f64(float f) { return f32_to_f64(f); }
 __device__ __forceinline__ double to_f64(double d) { return d; }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
 
 template <int P, typename TY, bool RAS>
 __global__ void __launch_bounds__(kThreads) k_prolong(Geo g, const int4* __restrict__ axown,
                                                       const int4* __restrict__ subrow, const TY* __restrict__ Y,
-                                                      const double* __restrict__ wT, const double* __restrict__ puT,
-                                                      const double* __restrict__ u0, int coarse,
+                                                      const TY* __restrict__ wT, const TY* __restrict__ puT,
+                                                      const TY* __restrict__ u0, int coarse,
                                                       const double* __restrict__ r, const double* __restrict__ q,
                                                       double* __restrict__ z, int mode, PcgState* st,
                                                       double* partials, unsigned* counter) {
@@ -558,8 +562,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong(Geo g, const int4* __restr
     if (nd.slot < g.nyi) {
       const int4 A1 = __ldg(axown + nd.a1);
       const int4 A2 = (P == 2) ? __ldg(axown + nd.a2) : make_int4(0, 0, -1, 0);
-      TY ys = (TY)0;
-      double cz = 0.0;
+      TY ys = (TY)0, cz = (TY)0;
 #pragma unroll
       for (int i = 0; i < 2; ++i) {
         const int o1 = i ? A1.z : A1.x;
@@ -573,12 +576,12 @@ __global__ void __launch_bounds__(kThreads) k_prolong(Geo g, const int4* __restr
           const int s = (P == 1) ? o1 : o1 * g.L + o2;
           const int4 sr = __ldg(subrow + s);
           const int loc = ((P == 1) ? l1 : l1 * sr.z + l2) * g.nyi + nd.slot;
-          if (RAS) ys += (TY)__ldg(puT + (size_t)sr.y + loc) * Y[(size_t)sr.x + loc];   // R_i^T D_i y_i
+          if (RAS) ys += __ldg(puT + (size_t)sr.y + loc) * Y[(size_t)sr.x + loc];   // R_i^T D_i y_i
           else ys += Y[(size_t)sr.x + loc];
-          if (coarse) cz = fma(__ldg(wT + (size_t)sr.y + loc), __ldg(u0 + s), cz);
+          if (coarse) cz = fma_t(__ldg(wT + (size_t)sr.y + loc), __ldg(u0 + s), cz);
         }
       }
-      v = to_f64(ys) + cz;
+      v = to_f64(ys + cz);
     }
     z[nd.idx] = v;
     if (mode != 0) {
@@ -613,23 +616,23 @@ void launch_prolong(dd_ctx* c, int mode, cudaStream_t s, double* zout) {
   const int coarse = c->grid.coarse;
   const bool f32 = (c->grid.precision != DD_PREC_FP64);
   double* z = zout != nullptr ? zout : c->z;
-#define DD_PROLONG(PP, TY, YP, RS)                                                                          \
-  (k_prolong<PP, TY, RS><<<nb, kThreads, 0, s>>>(g, c->axown, c->subrow, YP, c->wT, c->puT, c->u0, coarse, \
-                                                 c->r, c->q, z, mode, c->st, c->red, c->cnt + CNT_RZ),    \
+#define DD_PROLONG(PP, TY, YP, W, PU, U0, RS)                                                                   \
+  (k_prolong<PP, TY, RS><<<nb, kThreads, 0, s>>>(g, c->axown, c->subrow, YP, W, PU, U0, coarse, c->r, c->q, z, mode, \
+                                                 c->st, c->red, c->cnt + CNT_RZ),                                     \
    dd::note_launch())
+#define DD_PROLONG_T(PP, RS)                                                          \
+  do {                                                                                \
+    if (f32) DD_PROLONG(PP, float, c->Y32, c->wT32, c->puT32, c->u0f, RS);           \
+    else DD_PROLONG(PP, double, c->Y64, c->wT, c->puT, c->u0, RS);                    \
+  } while (0)
   if (c->ras) {
-    if (g.p == 1) {
-      if (f32) DD_PROLONG(1, float, c->Y32, true); else DD_PROLONG(1, double, c->Y64, true);
-    } else {
-      if (f32) DD_PROLONG(2, float, c->Y32, true); else DD_PROLONG(2, double, c->Y64, true);
-    }
+    if (g.p == 1) DD_PROLONG_T(1, true);
+    else DD_PROLONG_T(2, true);
   } else {
-    if (g.p == 1) {
-      if (f32) DD_PROLONG(1, float, c->Y32, false); else DD_PROLONG(1, double, c->Y64, false);
-    } else {
-      if (f32) DD_PROLONG(2, float, c->Y32, false); else DD_PROLONG(2, double, c->Y64, false);
-    }
+    if (g.p == 1) DD_PROLONG_T(1, false);
+    else DD_PROLONG_T(2, false);
   }
+#undef DD_PROLONG_T
 #undef DD_PROLONG
   DD_CUDA(cudaGetLastError());
 }
@@ -872,3 +875,38 @@ void launch_tab_shift(dd_ctx* c, double shift, double* dst) {
 }
 
 }  // namespace dd
+
+// ------------------------------------------------------------------------------------------
+// Self-test of the integer-pipe precision conversions used by the mixed form (no paper
+// counterpart): kind 0 rounds doubles to BF16 bits, kind 1 to TF32, kind 2 widens floats.
+// ------------------------------------------------------------------------------------------
+namespace dd {
+__global__ void k_convert_test(int kind, long long n, const void* __restrict__ in, void* __restrict__ out) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    if (kind == 0) static_cast<unsigned short*>(out)[t] = f64_to_bf16_bits(static_cast<const double*>(in)[t]);
+    else if (kind == 1) static_cast<float*>(out)[t] = f64_to_tf32(static_cast<const double*>(in)[t]);
+    else static_cast<double*>(out)[t] = f32_to_f64(static_cast<const float*>(in)[t]);
+  }
+}
+}  // namespace dd
+
+extern "C" int dd_convert_test(int kind, long long n, const void* in_host, void* out_host) {
+  using namespace dd;
+  if (kind < 0 || kind > 2 || n < 1 || !in_host || !out_host) return DD_EINVAL;
+  const size_t in_b = (size_t)n * (kind == 2 ? 4 : 8), out_b = (size_t)n * (kind == 0 ? 2 : (kind == 1 ? 4 : 8));
+  void *din = nullptr, *dout = nullptr;
+  int rc = DD_OK;
+  try {
+    DD_CUDA(cudaMalloc(&din, in_b));
+    DD_CUDA(cudaMalloc(&dout, out_b));
+    DD_CUDA(cudaMemcpy(din, in_host, in_b, cudaMemcpyHostToDevice));
+    (k_convert_test<<<grid_blocks(n, kThreads), kThreads>>>(kind, n, din, dout), dd::note_launch());
+    DD_CUDA(cudaGetLastError());
+    DD_CUDA(cudaMemcpy(out_host, dout, out_b, cudaMemcpyDeviceToHost));
+  } catch (const Error& e) {
+    rc = e.code;
+  }
+  if (din) cudaFree(din);
+  if (dout) cudaFree(dout);
+  return rc;
+}
