@@ -36,7 +36,19 @@ int fail(dd_ctx* c, int code, const std::string& msg) {
 template <typename F>
 int guarded(dd_ctx* c, F&& f) {
   try {
-    return f();
+    const int rc = f();
+    // a bounded device wait that expired (tensor-core GEMM pipeline, coarse-solve copy) left
+    // its bit in the error word; the results of that call cannot be trusted
+    if (rc == DD_OK && c != nullptr && c->dev_err != nullptr) {
+      int e = 0;
+      DD_CUDA(cudaMemcpyAsync(&e, c->dev_err + 8, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+      DD_CUDA(cudaStreamSynchronize(c->stream));
+      if (e != 0) {
+        DD_CUDA(cudaMemsetAsync(c->dev_err + 8, 0, sizeof(int), c->stream));
+        return fail(c, DD_ETIMEOUT, "a bounded device wait expired (code " + std::to_string(e) + ")");
+      }
+    }
+    return rc;
   } catch (const Error& e) {
     return fail(c, e.code, e.msg);
   } catch (const std::bad_alloc&) {

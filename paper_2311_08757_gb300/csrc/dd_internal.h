@@ -222,7 +222,7 @@ struct dd_ctx {
   // coarse
   double* A0band = nullptr;   // p=1: [3][N] (sub, diag, super); p=2: [N][9]
   double* cr = nullptr;       // p=1 cyclic-reduction coefficients
-  int cr_m = 0, cr_np = 0;
+  int cr_m = 0, cr_c2 = 0, cr_w2 = 0;   // cyclic reduction: levels + 1, packed multipliers, row arrays
   double* A0inv = nullptr;    // dense inverse [N][N] (p = 2; p = 1 on request)
   int coarse_mode = 0;        // 0 automatic, 1 cyclic reduction (p = 1), 2 dense inverse
   double *cf_CB = nullptr, *cf_RB = nullptr, *cf_inv = nullptr;   // banded factor of A_0

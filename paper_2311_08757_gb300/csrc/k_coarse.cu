@@ -13,6 +13,7 @@
 //          from a banded Cholesky factor and applied as an FP64 matrix-vector product.
 #include <atomic>
 
+#include "dd_async.cuh"
 #include "dd_band.cuh"
 
 namespace dd {
@@ -174,23 +175,27 @@ int coarse_assemble(dd_ctx* c) {
 
 // ----------------------------------------------------------------------------------------
 // p = 1: cyclic reduction for the tridiagonal A_0 (symmetric positive definite, so the
-// odd-even elimination needs no pivoting).  Equations j = 1..N' (N' = 2^m - 1 >= N,
-// padded with identity rows): a_j x_{j-1} + b_j x_j + c_j x_{j+1} = f_j.
-// Level l (stride s = 2^l) eliminates x_{j-s}, x_{j+s} from the equations j = 2s, 4s, ...
-// with multipliers alpha, gamma, stored packed per level (count floor(N'/2s) each).
-// Layout of c->cr: alpha[N'], gamma[N'], a[W], binv[W], cc[W], b[W] (W = N' + 2).
+// odd-even elimination needs no pivoting).  Equations j = 1..N:
+// a_j x_{j-1} + b_j x_j + c_j x_{j+1} = f_j, x_0 = x_{N+1} = 0.  Level l (stride s = 2^l)
+// eliminates x_{j-s}, x_{j+s} from the equations j = 2s, 4s, ... <= N with multipliers
+// alpha, gamma, stored packed per level (N >> (l+1) each); the levels run up to the root
+// 2^(m-1) <= N (2^m - 1 >= N).  Indices beyond N stand for identity rows (b = 1, a = c = 0,
+// f = 0), the usual padding to 2^m - 1 equations, which is never stored or computed.
+// Layout of c->cr (each array a multiple of two doubles, so every array starts 16-byte
+// aligned): alpha[C2], gamma[C2], a[W2], binv[W2], cc[W2], then b[W2] (set-up work),
+// C2 >= sum of the per-level counts, W2 >= N + 2.
 // ----------------------------------------------------------------------------------------
-__device__ __forceinline__ int cr_count(int Np, int l) { return Np >> (l + 1); }
+__device__ __forceinline__ int cr_count(int N, int l) { return N >> (l + 1); }
 
-__global__ void __launch_bounds__(1024) k_cr_setup(const double* __restrict__ A0nb, int N, int m, int Np, double* cr, int* flag) {
-  const int W = Np + 2;
+__global__ void __launch_bounds__(1024) k_cr_setup(const double* __restrict__ A0nb, int N, int m, int C2, int W2,
+                                                   double* cr, int* flag) {
   double* alpha = cr;
-  double* gamma = cr + Np;
-  double* a = cr + 2 * (size_t)Np;
-  double* binv = a + W;
-  double* cc = binv + W;
-  double* b = cc + W;   // work: b values
-  for (int j = threadIdx.x; j < W; j += blockDim.x) {
+  double* gamma = cr + C2;
+  double* a = cr + 2 * (size_t)C2;
+  double* binv = a + W2;
+  double* cc = binv + W2;
+  double* b = cc + W2;   // work: b values
+  for (int j = threadIdx.x; j < W2; j += blockDim.x) {
     double aj = 0.0, bj = 1.0, cj = 0.0;
     if (j >= 1 && j <= N) {
       bj = A0nb[(size_t)(j - 1) * 3 + 1];
@@ -205,56 +210,81 @@ __global__ void __launch_bounds__(1024) k_cr_setup(const double* __restrict__ A0
   int off = 0;
   for (int l = 0; l < m - 1; ++l) {
     const int s = 1 << l;
-    const int cnt = cr_count(Np, l);
+    const int cnt = cr_count(N, l);
     for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
       const int j = 2 * s * (t + 1);
+      const bool in = j + s <= N;   // otherwise x_{j+s} is a padding unknown
+      const double bp = in ? b[j + s] : 1.0, ap = in ? a[j + s] : 0.0, cp = in ? cc[j + s] : 0.0;
       const double al = -a[j] / b[j - s];
-      const double ga = -cc[j] / b[j + s];
+      const double ga = -cc[j] / bp;
       alpha[off + t] = al;
       gamma[off + t] = ga;
-      b[j] = b[j] + al * cc[j - s] + ga * a[j + s];
+      b[j] = b[j] + al * cc[j - s] + ga * ap;
       a[j] = al * a[j - s];
-      cc[j] = ga * cc[j + s];
+      cc[j] = ga * cp;
     }
     off += cnt;
     __syncthreads();
   }
-  for (int j = threadIdx.x; j < W; j += blockDim.x) {
+  for (int j = threadIdx.x; j < W2; j += blockDim.x) {
     if (!(b[j] > 0.0)) atomicOr(flag, 1);
     binv[j] = 1.0 / b[j];
   }
 }
 
-__global__ void __launch_bounds__(1024) k_cr_solve(const double* __restrict__ cr, int N, int m, int Np,
-                                                   const double* __restrict__ rhs, double* __restrict__ x,
-                                                   float* __restrict__ xf, const PcgState* st, int staged) {
+constexpr int kCrThreads = 512;
+constexpr int ERR_CR_WAIT = 1 << 7;   // error-word bit: the coefficient copy did not arrive in time
+
+// The coefficients are brought into shared memory by bulk copies (the TMA engine, one
+// thread issues them) while the threads load the right-hand side; every level then waits on
+// shared memory only.  When they do not fit (very long chains), they are read from global.
+__global__ void __launch_bounds__(kCrThreads) k_cr_solve(const double* __restrict__ cr, int N, int m, int C2,
+                                                         int W2, const double* __restrict__ rhs,
+                                                         double* __restrict__ x, float* __restrict__ xf,
+                                                         const PcgState* st, int staged, int* err) {
   if (st != nullptr && st->done) return;
-  extern __shared__ double sm_cr[];
-  const int W = Np + 2;
+  extern __shared__ __align__(16) double sm_cr[];
+  __shared__ __align__(8) unsigned long long cr_bar;
+  __shared__ int cr_ok;
   double* f = sm_cr;
-  // the coefficients (2 N' + 3 W doubles) are staged into shared memory in one coalesced
-  // sweep when they fit, so that every level waits on shared memory only
+  const size_t ncoef = 2 * (size_t)C2 + 3 * (size_t)W2;
   const double* src = cr;
   if (staged) {
-    double* dst = sm_cr + W;
-    const int tot = 2 * Np + 3 * W;
-    for (int t = threadIdx.x; t < tot; t += blockDim.x) dst[t] = __ldg(cr + t);
-    src = dst;
+    const uint32_t bar = smem_u32(&cr_bar);
+    if (threadIdx.x == 0) {
+      mbar_init(bar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      const uint32_t total = (uint32_t)(ncoef * sizeof(double));
+      mbar_expect_tx(bar, total);
+      const uint32_t dst = smem_u32(sm_cr + W2);
+      constexpr uint32_t kChunk = 32768;
+      for (uint32_t o = 0; o < total; o += kChunk)
+        bulk_g2s(dst + o, reinterpret_cast<const char*>(cr) + o, min(kChunk, total - o), bar);
+    }
+    src = sm_cr + W2;
   }
-  const double* alpha = src;
-  const double* gamma = src + Np;
-  const double* a = src + 2 * (size_t)Np;
-  const double* binv = a + W;
-  const double* cc = binv + W;
-  for (int j = threadIdx.x; j < W; j += blockDim.x) f[j] = (j >= 1 && j <= N) ? rhs[j - 1] : 0.0;
+  for (int j = threadIdx.x; j < W2; j += blockDim.x) f[j] = (j >= 1 && j <= N) ? rhs[j - 1] : 0.0;
+  if (staged) {
+    if (threadIdx.x == 0) cr_ok = mbar_wait(smem_u32(&cr_bar), 0, err, ERR_CR_WAIT) ? 1 : 0;
+  } else if (threadIdx.x == 0) {
+    cr_ok = 1;
+  }
   __syncthreads();
+  if (!cr_ok) return;   // the error word tells the host
+  const double* alpha = src;
+  const double* gamma = src + C2;
+  const double* a = src + 2 * (size_t)C2;
+  const double* binv = a + W2;
+  const double* cc = binv + W2;
   int off = 0;
   for (int l = 0; l < m - 1; ++l) {
     const int s = 1 << l;
-    const int cnt = cr_count(Np, l);
+    const int cnt = cr_count(N, l);
     for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
       const int j = 2 * s * (t + 1);
-      f[j] = fma(alpha[off + t], f[j - s], fma(gamma[off + t], f[j + s], f[j]));
+      const double fp = (j + s <= N) ? f[j + s] : 0.0;
+      f[j] = fma(alpha[off + t], f[j - s], fma(gamma[off + t], fp, f[j]));
     }
     off += cnt;
     __syncthreads();
@@ -264,9 +294,9 @@ __global__ void __launch_bounds__(1024) k_cr_solve(const double* __restrict__ cr
   __syncthreads();
   for (int l = m - 2; l >= 0; --l) {
     const int s = 1 << l;
-    for (int j = s + 2 * s * threadIdx.x; j <= Np; j += 2 * s * blockDim.x) {
+    for (int j = s + 2 * s * threadIdx.x; j <= N; j += 2 * s * blockDim.x) {
       const double left = f[j - s];
-      const double right = (j + s <= Np) ? f[j + s] : 0.0;
+      const double right = (j + s <= N) ? f[j + s] : 0.0;
       f[j] = (f[j] - a[j] * left - cc[j] * right) * binv[j];
     }
     __syncthreads();
@@ -346,12 +376,14 @@ int coarse_factor(dd_ctx* c) {
   if (!c->coarse_dense) {
     int m = 1;
     while ((1 << m) - 1 < N) ++m;
-    const int Np = (1 << m) - 1;
+    int C = 0;
+    for (int l = 0; l < m - 1; ++l) C += N >> (l + 1);
+    const int C2 = (C + 1) & ~1, W2 = (N + 3) & ~1;
     c->cr_m = m;
-    c->cr_np = Np;
-    const size_t W = (size_t)Np + 2;
-    if (!c->cr) c->cr = (double*)dev_alloc(c, sizeof(double) * (2 * (size_t)Np + 4 * W));   // kept across builds
-    (k_cr_setup<<<1, 1024, 0, c->stream>>>(c->A0band, N, m, Np, c->cr, flag), dd::note_launch());
+    c->cr_c2 = C2;
+    c->cr_w2 = W2;
+    if (!c->cr) c->cr = (double*)dev_alloc(c, sizeof(double) * (2 * (size_t)C2 + 4 * (size_t)W2));   // kept across builds
+    (k_cr_setup<<<1, 1024, 0, c->stream>>>(c->A0band, N, m, C2, W2, c->cr, flag), dd::note_launch());
     DD_CUDA(cudaGetLastError());
   } else {
     // dense A_0^{-1} (rows from the banded Cholesky factor), applied as a GEMV in the solve
@@ -411,16 +443,18 @@ void launch_coarse_restrict(dd_ctx* c, const double* r, cudaStream_t s) {
 void launch_coarse_solve(dd_ctx* c, cudaStream_t s) {
   const Geo& g = c->g;
   if (!c->coarse_dense) {
-    const size_t W = (size_t)c->cr_np + 2;
-    const size_t full = sizeof(double) * (2 * (size_t)c->cr_np + 4 * W);   // f + coefficients
-    const int staged = full <= 210 * 1024 ? 1 : 0;
-    const size_t smem = staged ? full : sizeof(double) * W;
+    const size_t W2 = (size_t)c->cr_w2, ncoef = 2 * (size_t)c->cr_c2 + 3 * W2;
+    const size_t full = sizeof(double) * (W2 + ncoef);   // f + coefficients
+    const int staged = full <= 200 * 1024 ? 1 : 0;
+    const size_t smem = staged ? full : sizeof(double) * W2;
+    if (smem > 220 * 1024) throw Error(DD_EINVAL, "coarse chain too long for the shared-memory cyclic reduction");
     static std::atomic<bool> attr{false};   // set once per process (idempotent if two threads race)
     if (!attr) {
       DD_CUDA(cudaFuncSetAttribute(k_cr_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
       attr = true;
     }
-    (k_cr_solve<<<1, 1024, smem, s>>>(c->cr, g.nsub, c->cr_m, c->cr_np, c->c0, c->u0, c->u0f, c->st, staged),
+    (k_cr_solve<<<1, kCrThreads, smem, s>>>(c->cr, g.nsub, c->cr_m, c->cr_c2, c->cr_w2, c->c0, c->u0, c->u0f, c->st,
+                                             staged, c->dev_err + 8),
      dd::note_launch());
   } else {
     const int N = g.nsub;
