@@ -32,10 +32,23 @@ __device__ inline void jacobi_lowest(double H[3][3], int m, double* theta, doubl
     if (off <= 1e-34 * dia) break;
     for (int p = 0; p < m; ++p)
       for (int q = p + 1; q < m; ++q) {
-        if (H[p][q] == 0.0) continue;
-        const double tau = (H[q][q] - H[p][p]) / (2.0 * H[p][q]);
-        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-        const double cs = 1.0 / sqrt(1.0 + t * t), sn = t * cs;
+        const double hpq = H[p][q];
+        if (hpq == 0.0) continue;
+        const double dq = H[q][q] - H[p][p];
+        // rotation angle: t = tan(phi) with tau = cot(2 phi).  It is formed in FP32 (GB300's
+        // FP64 divide and square root are long dependent chains on one thread); normalising
+        // (cs, sn) in FP64 keeps the rotation orthogonal to FP64 rounding, and an angle good
+        // to FP32 still cuts H[p][q] by about 1e-7, so the sweeps above end as before
+        double t;
+        const float fp = (float)hpq, fd = (float)dq;
+        if (fabsf(fp) > 1e-30f && fabsf(fp) < 1e30f && fabsf(fd) < 1e30f) {
+          const float tau = fd / (2.0f * fp);
+          t = (double)(copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f))));
+        } else {
+          const double tau = dq / (2.0 * hpq);
+          t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        }
+        const double cs = rsqrt(fma(t, t, 1.0)), sn = t * cs;
         for (int k = 0; k < m; ++k) {   // H <- H J
           const double hp = H[k][p], hq = H[k][q];
           H[k][p] = cs * hp - sn * hq;
@@ -89,7 +102,7 @@ __device__ inline void rayleigh_ritz3(LopState* ls, double drop) {
     for (int a = 0; a < 3; ++a) gv[a] = GB[a][0] * v[0] + GB[a][1] * v[1] + GB[a][2] * v[2];
     const double nrm2 = v[0] * gv[0] + v[1] * gv[1] + v[2] * gv[2];
     if (n0 > 0.0 && nrm2 > drop * drop * n0) {
-      const double s = 1.0 / sqrt(nrm2);
+      const double s = rsqrt(nrm2);
       for (int a = 0; a < 3; ++a) T[a][m] = v[a] * s;
       ++m;
     }
