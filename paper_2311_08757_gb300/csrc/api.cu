@@ -181,15 +181,16 @@ void build_subdomains(dd_ctx* c) {
   std::vector<int> next = c->type_first, slot(g.nsub);
   for (int s = 0; s < g.nsub; ++s) slot[s] = next[c->subs_h[s].type]++;
   c->nloc_max = 0;
-  int w2max = 1;
+  int w2max = 1, nlp_max = 0;
   for (int t = 0; t < c->ntypes; ++t) {
     c->nloc_max = std::max(c->nloc_max, c->type_nloc[t]);
     w2max = std::max(w2max, c->type_w2[t]);
+    nlp_max = std::max(nlp_max, c->type_nloc[t] / g.nyi * g.Ypad);   // columns x Ypad slots
   }
   // K of the local contraction: whole 128-byte swizzle rows of the operand type (64 BF16,
-  // 32 TF32, 128 E4M3 values)
+  // 32 TF32, 128 E4M3 values), over the column-padded local length
   const int kq = c->grid.precision == DD_PREC_FP8 ? 128 : 64;
-  c->kpad = (c->nloc_max + kq - 1) / kq * kq;
+  c->kpad = (nlp_max + kq - 1) / kq * kq;
   c->band = (g.p == 1) ? g.nyi + 1 : w2max * g.nyi + g.nyi + 1;
   c->subs = (Sub*)dev_alloc(c, sizeof(Sub) * g.nsub);
   c->slot_of_sub = (int*)dev_alloc(c, sizeof(int) * g.nsub);

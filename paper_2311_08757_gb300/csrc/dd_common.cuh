@@ -159,6 +159,13 @@ __device__ __forceinline__ double f32_to_f64(float f) {
   return __hiloint2double((int)hi, (int)(m << 29));
 }
 
+// Subdomain-local vectors stored in the kpad-strided arrays (rounded local inverses,
+// restrictions, local results, coarse and partition-of-unity weights) keep the column
+// padding of the global vectors: local column cc, slot sj sits at cc * Ypad + sj, so a
+// subdomain's restriction is a contiguous run of the padded global vector (p = 1) or w1 such
+// runs (p = 2).  The banded factors and the FP64 solves use the compact order cc * nyi + sj.
+__device__ __forceinline__ int loc_pad(const Geo& g, int k) { return (k / g.nyi) * g.Ypad + k % g.nyi; }
+
 // Interior-element enumeration of a padded vector: t in [0, nxi^p * Ypad).
 struct Node {
   long long idx;   // padded index

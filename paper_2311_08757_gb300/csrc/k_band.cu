@@ -353,7 +353,7 @@ __global__ void k_local_solve(Geo g, const Sub* __restrict__ subs, const int2* _
         else idx = ((long long)(sb.lo1 + c1) * g.ncx + (sb.lo2 + c2)) * g.Ypad + sj;
         const double v = r[idx];
         xj[k] = v;
-        if (c0 != nullptr) cr = fma(wt[k], v, cr);
+        if (c0 != nullptr) cr = fma(wt[loc_pad(g, k)], v, cr);
       }
       if (c0 != nullptr) {
         cr = warp_sum(cr);
@@ -368,7 +368,7 @@ __global__ void k_local_solve(Geo g, const Sub* __restrict__ subs, const int2* _
   __syncwarp();
   for (int j = 0; j < grp.y; ++j) {
     double* y = Y + (size_t)(grp.x + j) * kpad;
-    for (int k = lane; k < n; k += 32) y[k] = xs[(size_t)j * nmax + k];
+    for (int k = lane; k < n; k += 32) y[loc_pad(g, k)] = xs[(size_t)j * nmax + k];
   }
 }
 

@@ -53,11 +53,11 @@ __global__ void k_coarse_weights(Geo g, int pu, const Sub* __restrict__ rep, int
   const long long total = (long long)ntypes * kpad;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
-    const int ty = (int)(t / kpad), k = (int)(t % kpad);
+    const int ty = (int)(t / kpad), kp = (int)(t % kpad);   // column-padded local index
     const Sub s = rep[ty];
     double v = 0.0, d = 0.0;
-    if (k < s.nloc) {
-      const int sj = k % g.nyi, cc = k / g.nyi;
+    const int sj = kp & (g.Ypad - 1), cc = kp >> g.ylog;
+    if (sj < g.nyi && cc < s.w1 * s.w2) {
       const int c1 = cc / s.w2, c2 = cc % s.w2;
       const int a1 = s.lo1 + c1, a2 = s.lo2 + c2;
       // subdomain index of the representative along each axis: from its first column
@@ -122,7 +122,7 @@ __global__ void k_colour_vector(Geo g, const Sub* __restrict__ subs, const doubl
           if (g.p == 2 && o2[k] % 3 != col2) continue;
           const int s = (g.p == 1) ? o1[i] : o1[i] * g.L + o2[k];
           const Sub sb = subs[s];
-          const int loc = ((g.p == 1) ? l1[i] : l1[i] * sb.w2 + l2[k]) * g.nyi + nd.slot;
+          const int loc = ((g.p == 1) ? l1[i] : l1[i] * sb.w2 + l2[k]) * g.Ypad + nd.slot;
           val += wT[(size_t)sb.type * kpad + loc];
         }
     }
@@ -148,7 +148,7 @@ __global__ void k_coarse_entries(Geo g, const Sub* __restrict__ subs, const doub
   const Sub sb = subs[s];
   double acc[1] = {0.0};
   for (int k = threadIdx.x; k < sb.nloc; k += blockDim.x)
-    acc[0] = fma(wT[(size_t)sb.type * kpad + k], w[sub_global(g, sb, k)], acc[0]);
+    acc[0] = fma(wT[(size_t)sb.type * kpad + loc_pad(g, k)], w[sub_global(g, sb, k)], acc[0]);
   block_sum<1>(acc);
   if (threadIdx.x == 0) {
     const int nbk = (g.p == 1) ? (t1 - s1 + 1) : ((t1 - s1 + 1) * 3 + (t2 - s2 + 1));
@@ -430,7 +430,7 @@ __global__ void k_coarse_restrict(Geo g, const Sub* __restrict__ subs, const dou
   const Sub sb = subs[s];
   double acc[1] = {0.0};
   for (int k = threadIdx.x; k < sb.nloc; k += blockDim.x)
-    acc[0] = fma(wT[(size_t)sb.type * kpad + k], r[sub_global(g, sb, k)], acc[0]);
+    acc[0] = fma(wT[(size_t)sb.type * kpad + loc_pad(g, k)], r[sub_global(g, sb, k)], acc[0]);
   block_sum<1>(acc);
   if (threadIdx.x == 0) c0[s] = acc[0];
 }

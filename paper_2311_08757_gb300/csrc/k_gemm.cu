@@ -325,7 +325,7 @@ __device__ __forceinline__ double round_f32<double>(float v) { return f32_to_f64
 template <typename T, int NV, int PF, int K>
 __global__ void k_local_inverse(const int* __restrict__ nloc, int nmax, int b, const float* __restrict__ CB,
                                 const float* __restrict__ RB, const float* __restrict__ inv, int ntypes, int kpad,
-                                T* __restrict__ out) {
+                                int nyi, int ylog, T* __restrict__ out) {
   extern __shared__ float xs_all[];
   const int wpb = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int groups_per_type = (nmax + K - 1) / K;
@@ -344,17 +344,38 @@ __global__ void k_local_inverse(const int* __restrict__ nloc, int nmax, int b, c
   const size_t off = (size_t)ty * nmax;
   band_solve_k<NV, PF, K>(xs, nmax, n, b, CB + off * (b + 1), RB + off * (b + 1), inv + off, ring);
   __syncwarp();
+  // rows and columns at their column-padded local positions (the pad rows and columns stay 0)
+  auto lp = [&](int k) { return ((k / nyi) << ylog) + k % nyi; };
   for (int j = 0; j < K && col0 + j < n; ++j) {
-    T* row = out + ((size_t)ty * kpad + col0 + j) * kpad;
-    for (int k = lane; k < n; k += 32) row[k] = round_f32<T>(xs[(size_t)j * nmax + k]);
+    T* row = out + ((size_t)ty * kpad + lp(col0 + j)) * kpad;
+    for (int k = lane; k < n; k += 32) row[lp(k)] = round_f32<T>(xs[(size_t)j * nmax + k]);
   }
 }
 
 // R_i r rounded, subdomain rows in type-sorted order, zero tail up to kpad; the coarse
 // right-hand side c_i = (D_i R_i psi)^T r (Def. 2.1) is formed in FP64 in the same pass.
-// Block per subdomain, warp per local column (the y nodes of a column are contiguous in r).
+// In the column-padded local layout a subdomain is w1 contiguous runs of w2 * Ypad values of
+// r (one run for p = 1), so the block streams them two values per thread and step (pad slots
+// of r are zero, and so are the weights there).  Block per subdomain.
 // FP8: the row is scaled by s_i = 448 / max|R_i r| before rounding, and 1 / (s_i s_T) (with
 // s_T the scale of the type's inverse) is recorded for the GEMM's epilogue.
+template <typename T>
+__device__ __forceinline__ void store2(T* row, int k, double a, double b, double scale);
+template <>
+__device__ __forceinline__ void store2<__nv_bfloat16>(__nv_bfloat16* row, int k, double a, double b, double) {
+  const unsigned w = (unsigned)f64_to_bf16_bits(a) | ((unsigned)f64_to_bf16_bits(b) << 16);
+  *reinterpret_cast<unsigned*>(row + k) = w;
+}
+template <>
+__device__ __forceinline__ void store2<float>(float* row, int k, double a, double b, double) {
+  *reinterpret_cast<float2*>(row + k) = make_float2(f64_to_tf32(a), f64_to_tf32(b));
+}
+template <>
+__device__ __forceinline__ void store2<__nv_fp8_e4m3>(__nv_fp8_e4m3* row, int k, double a, double b, double scale) {
+  row[k] = to_e4m3(a * scale);
+  row[k + 1] = to_e4m3(b * scale);
+}
+
 template <typename T>
 __global__ void k_pack(Geo g, const Sub* __restrict__ subs, const int* __restrict__ slot_of,
                        const double* __restrict__ r, int kpad, T* __restrict__ out, const double* __restrict__ wT,
@@ -366,18 +387,21 @@ __global__ void k_pack(Geo g, const Sub* __restrict__ subs, const int* __restric
   const int slot = slot_of[s];
   T* row = out + (size_t)slot * kpad;
   const double* wt = wT + (size_t)sb.type * kpad;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int ncols = sb.w1 * sb.w2;
+  const int run = sb.w2 * g.Ypad, npair = sb.w1 * run / 2;   // run length is even (Ypad >= 4)
+  auto src = [&](int kp) -> long long {   // padded global index of local kp
+    const int c1 = kp / run, j = kp - c1 * run;
+    return (g.p == 1) ? (long long)(sb.lo1 + c1) * g.Ypad + j
+                      : ((long long)(sb.lo1 + c1) * g.ncx + sb.lo2) * g.Ypad + j;
+  };
   double scale = 1.0;
   if (FP8) {
     double mx[1] = {0.0};
-    for (int cc = warp; cc < ncols; cc += nw) {
-      const int c1 = cc / sb.w2, c2 = cc - c1 * sb.w2;
-      const long long base = (g.p == 1) ? (long long)(sb.lo1 + c1) * g.Ypad
-                                        : ((long long)(sb.lo1 + c1) * g.ncx + (sb.lo2 + c2)) * g.Ypad;
-      for (int sj = lane; sj < g.nyi; sj += 32) mx[0] = fmax(mx[0], fabs(r[base + sj]));
+    for (int e = threadIdx.x; e < npair; e += blockDim.x) {
+      const double2 v = *reinterpret_cast<const double2*>(r + src(2 * e));
+      mx[0] = fmax(mx[0], fmax(fabs(v.x), fabs(v.y)));
     }
     __shared__ double s_mx[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int o = 16; o > 0; o >>= 1) mx[0] = fmax(mx[0], __shfl_xor_sync(kFull, mx[0], o));
     if (lane == 0) s_mx[warp] = mx[0];
     __syncthreads();
@@ -387,22 +411,15 @@ __global__ void k_pack(Geo g, const Sub* __restrict__ subs, const int* __restric
     if (threadIdx.x == 0) ysc[slot] = (float)(ascale[sb.type] / scale);
   }
   double acc[1] = {0.0};
-  for (int cc = warp; cc < ncols; cc += nw) {
-    const int c1 = cc / sb.w2, c2 = cc - c1 * sb.w2;
-    const long long base = (g.p == 1) ? (long long)(sb.lo1 + c1) * g.Ypad
-                                      : ((long long)(sb.lo1 + c1) * g.ncx + (sb.lo2 + c2)) * g.Ypad;
-    for (int sj = lane; sj < g.nyi; sj += 32) {
-      const int k = cc * g.nyi + sj;
-      const double v = r[base + sj];
-      acc[0] = fma(wt[k], v, acc[0]);
-      if constexpr (FP8) row[k] = to_e4m3(v * scale);
-      else row[k] = round_fast<T>(v);
-    }
+  for (int e = threadIdx.x; e < npair; e += blockDim.x) {
+    const int kp = 2 * e;
+    const double2 v = *reinterpret_cast<const double2*>(r + src(kp));
+    const double2 w = *reinterpret_cast<const double2*>(wt + kp);
+    acc[0] = fma(w.x, v.x, acc[0]);
+    acc[0] = fma(w.y, v.y, acc[0]);
+    store2<T>(row, kp, v.x, v.y, scale);
   }
-  for (int k = sb.nloc + threadIdx.x; k < kpad; k += blockDim.x) {
-    if constexpr (FP8) row[k] = to_e4m3(0.0);
-    else row[k] = round_fast<T>(0.0);
-  }
+  for (int kp = 2 * npair + 2 * threadIdx.x; kp < kpad; kp += 2 * blockDim.x) store2<T>(row, kp, 0.0, 0.0, 1.0);
   if (c0 != nullptr) {
     block_sum<1>(acc);
     if (threadIdx.x == 0) c0[s] = acc[0];
@@ -532,7 +549,8 @@ static void launch_local_inverse_t(dd_ctx* c, const int* nloc, T* out) {
     DD_CUDA(cudaFuncSetAttribute(k_local_inverse<T, NV, PF, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  220 * 1024));
     (k_local_inverse<T, NV, PF, KK><<<nb, 32 * wpb, smem, c->stream>>>(nloc, c->nloc_max, c->band, c->bandCB32,
-                                                                       c->bandRB32, c->bandInv32, c->ntypes, kpad, out),
+                                                                       c->bandRB32, c->bandInv32, c->ntypes, kpad,
+                                                                       c->g.nyi, c->g.ylog, out),
      dd::note_launch());
   });
   DD_CUDA(cudaGetLastError());

@@ -584,7 +584,7 @@ __global__ void __launch_bounds__(kThreads, 8 / U) k_prolong(Geo g, const int4* 
         ok[u][e] = o1 >= 0 && (P == 1 || o2 >= 0);
         sub[u][e] = ok[u][e] ? ((P == 1) ? o1 : o1 * g.L + o2) : 0;
         sr[u][e] = __ldg(subrow + sub[u][e]);
-        loc[u][e] = ok[u][e] ? (((P == 1) ? l1 : l1 * sr[u][e].z + l2) * g.nyi + nd[u].slot) : 0;
+        loc[u][e] = ok[u][e] ? (((P == 1) ? l1 : l1 * sr[u][e].z + l2) * g.Ypad + nd[u].slot) : 0;
       }
     double rv[U], qv[U];
 #pragma unroll
