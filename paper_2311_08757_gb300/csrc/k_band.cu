@@ -132,12 +132,11 @@ __global__ void __launch_bounds__(1024) k_band_factor_win(T* CB, T* inv, const i
         for (int j = 0; j < kMaxPairs; ++j) {
           const unsigned half = (j & 1) ? (pr[j >> 1] >> 16) : (pr[j >> 1] & 0xFFFFu);
           const int d1 = (int)(half >> 8), d2 = (int)(half & 0xFFu);
-          if (j < npr && d1 <= dmax) {
-            int slot = sk + d2;                  // ring slot of column k + d2
-            if (slot >= W) slot -= W;
-            T* a = win + slot * bs + (d1 - d2);
-            *a = fma_el(-colk[d1], colk[d2], *a);
-          }
+          if (j >= npr || d1 > dmax) break;   // d1 does not decrease along the list
+          int slot = sk + d2;                  // ring slot of column k + d2
+          if (slot >= W) slot -= W;
+          T* a = win + slot * bs + (d1 - d2);
+          *a = fma_el(-colk[d1], colk[d2], *a);
         }
         // the slot of column k is free (read before the barrier above): store column k + W
         // (untouched so far) and prefetch k + W + P
@@ -239,8 +238,13 @@ static void factor_launch(T* CB, T* RB, T* inv, const int* nvec, int nmat, int n
                           cudaStream_t s) {
   if (b <= kBandWinMax) {
     const size_t smem = sizeof(T) * ((size_t)(b + 1) * (b + 1) + (b + 1));
-    const int tot = b * (b + 1) / 2;   // triangle pairs: at most kMaxPairs per thread
-    const int threads = (b * b > 2048) ? (tot > kMaxPairs * 512 ? 1024 : 512) : 256;
+    // about 8 triangle pairs per thread (at most kMaxPairs), and at least one thread per
+    // entry of a column (the window's entering columns are staged one entry per thread)
+    const int tot = b * (b + 1) / 2;
+    int threads = ((tot + 7) / 8 + 31) / 32 * 32;
+    threads = std::max(threads, (b + 1 + 31) / 32 * 32);
+    threads = std::max(threads, (tot + kMaxPairs - 1) / kMaxPairs);
+    threads = std::min(threads, 1024);
     static std::atomic<bool> attr{false};   // set once per process and type (idempotent if two threads race)
     if (!attr) {
       DD_CUDA(cudaFuncSetAttribute(k_band_factor_win<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
