@@ -38,7 +38,9 @@ struct TcCfg {
   static constexpr int BM = 128, BN = BN_;
   static constexpr int BK = 128 / (int)sizeof(T);   // one 128-byte swizzle row
   static constexpr int UK = 32 / (int)sizeof(T);    // K of one tcgen05.mma (32 bytes)
-  static constexpr int STAGES = 4;
+  // 128 x 256 tiles: 4 stages (193 KB, one CTA per SM); 128 x 128 tiles: 3 stages (97 KB),
+  // so that two CTAs share an SM and one's epilogue overlaps the other's MMAs
+  static constexpr int STAGES = (BN_ == 128) ? 3 : 4;
   static constexpr int A_BYTES = BM * 128;
   static constexpr int B_BYTES = BN * 128;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
