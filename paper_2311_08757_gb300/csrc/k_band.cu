@@ -590,10 +590,15 @@ __global__ void __launch_bounds__(kCellBlock) k_cl_resid(Geo g, int ncell, const
     } else {
       // past the residual target, go on while the residual still halves: psi enters the
       // coarse space twice (A_0 = Z^T A_sigma Z), so it is driven to its rounding floor, which
-      // the cheap steps reach a few steps later; the Rayleigh quotient (error ~ eta^2) has long
-      // been stationary by then
-      if (eta <= tol_eta && eta >= 0.5 * cl->eta_prev) cl->stable += 1;
-      else cl->stable = 0;
+      // the cheap steps reach a few steps later (the Rayleigh quotient, error ~ eta^2, has long
+      // been stationary by then).  Near the floor the residual alternates between halving and
+      // not, so every non-halving step below the target counts, and a residual 1e-3 below the
+      // target counts at once.
+      if (eta <= tol_eta) {
+        if (eta >= 0.5 * cl->eta_prev || eta <= 1e-3 * tol_eta) cl->stable += 1;
+      } else {
+        cl->stable = 0;
+      }
       if (cl->stable >= 2) cl->done = 1;
       else if (cl->iters >= maxit) {
         cl->status = DD_EMAXIT;
