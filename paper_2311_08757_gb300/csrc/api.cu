@@ -712,6 +712,15 @@ int dd_coarse_build(dd_ctx* c) {
     int* flag = c->dev_err + 3;
     DD_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), c->stream));
     const size_t bsz = (size_t)c->ntypes * c->nloc_max * (c->band + 1);
+    // the coarse matrix A_0 = Z^T A_sigma Z does not depend on the local factors: it is
+    // assembled on the side stream while the local matrices are factored and inverted (those
+    // run on a few SMs and leave the GPU mostly idle)
+    if (c->grid.coarse) {
+      DD_CUDA(cudaEventRecord(c->ev_fork, c->stream));
+      DD_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+      coarse_assemble(c, c->side);
+      DD_CUDA(cudaEventRecord(c->ev_join, c->side));
+    }
     if (use_gemm(c)) {
       // the mixed form only forms A_T^{-1} from the factor and rounds it to BF16/TF32/E4M3:
       // an FP32 factor and FP32 solves are far more accurate than that rounding
@@ -743,14 +752,8 @@ int dd_coarse_build(dd_ctx* c) {
       c->Y64 = (double*)dev_alloc(c, sizeof(double) * (size_t)g.nsub * c->kpad);
     }
     if (c->grid.coarse) {
-      coarse_assemble(c);
-      if (!c->cr && !c->A0inv) coarse_factor(c);
-      else {
-        // rebuild after a new cell eigenpair
-        c->cr = nullptr;
-        c->A0inv = nullptr;
-        coarse_factor(c);
-      }
+      DD_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+      coarse_factor(c);   // its storage is allocated on the first build and reused
     }
     DD_CUDA(cudaStreamSynchronize(c->stream));
     c->stage = 3;

@@ -287,7 +287,7 @@ int cell_eigenpair(dd_ctx* c);
 
 // coarse
 void launch_coarse_weights(dd_ctx* c);
-int coarse_assemble(dd_ctx* c);
+int coarse_assemble(dd_ctx* c, cudaStream_t s);
 int coarse_factor(dd_ctx* c);
 void launch_coarse_restrict(dd_ctx* c, const double* r, cudaStream_t s);
 void launch_coarse_solve(dd_ctx* c, cudaStream_t s);

@@ -27,14 +27,13 @@ namespace dd {
 // bandwidths whose window does not fit.
 // ----------------------------------------------------------------------------------------
 constexpr int kBandWinMax = 160;
-constexpr int kMaxPairs = 16;   // triangle pairs per thread: b (b + 1) / 2 <= 16 x threads for b <= 160
 
 __device__ __forceinline__ double rsqrt_el(double v) { return rsqrt(v); }
 __device__ __forceinline__ float rsqrt_el(float v) { return rsqrtf(v); }
 
 // T = double, or float for factors whose inverses are rounded to a tensor-core type and for
 // the cell preconditioner (GB300 issues FP32 at 64x the FP64 rate)
-template <typename T, int P>
+template <typename T, int P, int PPT>
 __global__ void __launch_bounds__(1024) k_band_factor_win(T* CB, T* inv, const int* __restrict__ nvec,
                                                           int nmax, int b, int* flag) {
   extern __shared__ __align__(16) unsigned char fsm_raw[];
@@ -42,28 +41,33 @@ __global__ void __launch_bounds__(1024) k_band_factor_win(T* CB, T* inv, const i
   const int m = blockIdx.x;
   const int n = nvec[m];
   const int bs = b + 1, W = b + 1;
+  // window column stride: even, so that the update's address step between consecutive
+  // threads (stride - 1 words per d2) is odd and their shared-memory banks differ (a stride of
+  // b + 1 = 33 for b = 32 put a whole warp on one bank)
+  const int S = (bs + 1) & ~1;
   const int t = threadIdx.x;   // owns entry d = t of the columns it stages (bs <= blockDim.x)
-  T* win = fsm;               // W columns x bs entries
-  T* colk = fsm + W * bs;     // L(k+d, k), d = 0..b
+  T* win = fsm;               // W columns x S entries
+  T* colk = fsm + W * S;      // L(k+d, k), d = 0..b
+  T* rq = colk + bs;          // P entering columns in flight (cp.async), P x bs
   T* A = CB + (size_t)m * nmax * bs;
   T* iv = inv + (size_t)m * nmax;
   // this thread's pairs (d1, d2), 1 <= d2 <= d1 <= b, of the lower triangle of the window
   // update: linear index e = d1 (d1 - 1) / 2 + d2 - 1 taken as e = t, t + T, ...; in that order
   // d1 never decreases, so the pairs beyond the last column's reach form a suffix
-  unsigned pr[kMaxPairs / 2];   // two pairs per word: (d1 << 8 | d2) in each half (b <= 160 < 256)
-  int npr = 0;
+  // exactly PPT pair slots per thread (the block is sized for it), unrolled so that their
+  // shared-memory loads issue together; an absent pair is (d1, d2) = (255, 0), beyond reach
+  unsigned pr[(PPT + 1) / 2];   // two pairs per word: (d1 << 8 | d2) in each half (b <= 160 < 255)
   {
     const int T = (int)blockDim.x, tot = b * (b + 1) / 2;
 #pragma unroll
-    for (int j = 0; j < kMaxPairs; ++j) {
+    for (int j = 0; j < PPT; ++j) {
       const int e = t + j * T;
-      int d1 = 0, d2 = 0;
+      int d1 = 255, d2 = 0;
       if (e < tot) {
         d1 = (int)((sqrtf(8.0f * (float)e + 1.0f) + 1.0f) * 0.5f);   // first guess, then exact
         while (d1 * (d1 - 1) / 2 > e) --d1;
         while ((d1 + 1) * d1 / 2 <= e) ++d1;
         d2 = e - d1 * (d1 - 1) / 2 + 1;
-        ++npr;
       }
       const unsigned half = ((unsigned)d1 << 8) | (unsigned)d2;
       if (j & 1) pr[j >> 1] |= half << 16;
@@ -71,26 +75,27 @@ __global__ void __launch_bounds__(1024) k_band_factor_win(T* CB, T* inv, const i
     }
   }
   const int first = min(W, n);
-  for (int e = t; e < first * bs; e += blockDim.x) win[e] = A[e];
-  // entering columns are loaded P steps before they are needed
-  T ring[P];
+  for (int e = t; e < first * bs; e += blockDim.x) win[(e / bs) * S + e % bs] = A[e];
+  // entering columns are copied P steps before they are needed, asynchronously into a
+  // shared ring (cp.async: a block barrier waits for a thread's outstanding loads, not for its
+  // asynchronous copies), one commit group per step; each thread reads back only what it copied
 #pragma unroll
   for (int u = 0; u < P; ++u) {
-    const int j = W + u;
-    ring[u] = A[(size_t)min(j, n - 1) * bs + min(t, b)];   // clamped: no select on the load
+    if (t < bs) cp_async_el(rq + u * bs + t, A + (size_t)min(W + u, n - 1) * bs + t);
+    cp_async_commit();
   }
   __syncthreads();
+  int sk = 0;   // ring slot of column k: k mod W, kept incrementally
   for (int k0 = 0; k0 < n; k0 += P) {
 #pragma unroll
     for (int u = 0; u < P; ++u) {
       const int k = k0 + u;
       if (k < n) {
-        const int sk = k % W;
         T il;
         if constexpr (sizeof(T) == 4) {
           // FP32: every thread forms the pivot's reciprocal square root itself (identical
           // values), which saves the barrier that publishing it would take
-          T piv = win[sk * bs];
+          T piv = win[sk * S];
           if (!(piv > (T)0)) {
             if (t == 0) atomicOr(flag, 1);
             piv = (T)1;
@@ -103,7 +108,7 @@ __global__ void __launch_bounds__(1024) k_band_factor_win(T* CB, T* inv, const i
         } else {
           // FP64: one thread (the FP64 pipe would pay for every redundant copy)
           if (t == 0) {
-            T piv = win[sk * bs];
+            T piv = win[sk * S];
             if (!(piv > (T)0)) {
               atomicOr(flag, 1);
               piv = (T)1;
@@ -120,7 +125,7 @@ __global__ void __launch_bounds__(1024) k_band_factor_win(T* CB, T* inv, const i
         for (int d = 1 + t; d <= b; d += blockDim.x) {
           T v = (T)0;
           if (d <= dmax) {
-            v = win[sk * bs + d] * il;           // L(k+d, k)
+            v = win[sk * S + d] * il;            // L(k+d, k)
             A[(size_t)k * bs + d] = v * il;      // pre-scaled by 1/L(k,k)
           }
           colk[d] = v;
@@ -129,24 +134,28 @@ __global__ void __launch_bounds__(1024) k_band_factor_win(T* CB, T* inv, const i
         // A(k+d1, k+d2) -= L(k+d1, k) L(k+d2, k) over this thread's pairs with d1 <= dmax;
         // these touch the slots of columns k+1..k+b only
 #pragma unroll
-        for (int j = 0; j < kMaxPairs; ++j) {
+        for (int j = 0; j < PPT; ++j) {
           const unsigned half = (j & 1) ? (pr[j >> 1] >> 16) : (pr[j >> 1] & 0xFFFFu);
           const int d1 = (int)(half >> 8), d2 = (int)(half & 0xFFu);
-          if (j >= npr || d1 > dmax) break;   // d1 does not decrease along the list
-          int slot = sk + d2;                  // ring slot of column k + d2
-          if (slot >= W) slot -= W;
-          T* a = win + slot * bs + (d1 - d2);
-          *a = fma_el(-colk[d1], colk[d2], *a);
+          if (d1 <= dmax) {
+            int slot = sk + d2;                  // ring slot of column k + d2
+            if (slot >= W) slot -= W;
+            T* a = win + slot * S + (d1 - d2);
+            *a = fma_el(-colk[d1], colk[d2], *a);
+          }
         }
         // the slot of column k is free (read before the barrier above): store column k + W
-        // (untouched so far) and prefetch k + W + P
-        if (k + W < n && t < bs) win[sk * bs + t] = ring[u];
-        const int j = k + W + P;
-        ring[u] = A[(size_t)min(j, n - 1) * bs + min(t, b)];
+        // (untouched so far, copied P steps ago) and start the copy of k + W + P
+        cp_async_wait<P - 1>();
+        if (k + W < n && t < bs) win[sk * S + t] = rq[u * bs + t];
+        if (t < bs) cp_async_el(rq + u * bs + t, A + (size_t)min(k + W + P, n - 1) * bs + t);
+        cp_async_commit();
         __syncthreads();
+        sk = (sk + 1 == W) ? 0 : sk + 1;
       }
     }
   }
+  cp_async_wait<0>();   // no copy into this block's shared memory outlives it
 }
 
 template <typename T>
@@ -237,20 +246,30 @@ template <typename T>
 static void factor_launch(T* CB, T* RB, T* inv, const int* nvec, int nmat, int nmax, int b, int* flag,
                           cudaStream_t s) {
   if (b <= kBandWinMax) {
-    const size_t smem = sizeof(T) * ((size_t)(b + 1) * (b + 1) + (b + 1));
-    // about 8 triangle pairs per thread (at most kMaxPairs), and at least one thread per
-    // entry of a column (the window's entering columns are staged one entry per thread)
+    const size_t smem = sizeof(T) * ((size_t)(b + 1) * (((b + 1) + 1) & ~1) + (size_t)(b + 1) * (1 + 4));
+    // PPT triangle pairs per thread, the block at least one thread per entry of a column (the
+    // window's entering columns are staged one entry per thread) and at most 1024 threads
     const int tot = b * (b + 1) / 2;
-    int threads = ((tot + 7) / 8 + 31) / 32 * 32;
+    // four pairs per thread where the block stays within 1024 threads (measured at b = 63:
+    // 4 pairs x 16 warps 0.53 ms, 16 pairs x 4 warps 0.90 ms: the wider block hides latency)
+    const int ppt = tot <= 2048 ? 4 : (tot <= 4096 ? 8 : 16);
+    int threads = ((tot + ppt - 1) / ppt + 31) / 32 * 32;
     threads = std::max(threads, (b + 1 + 31) / 32 * 32);
-    threads = std::max(threads, (tot + kMaxPairs - 1) / kMaxPairs);
     threads = std::min(threads, 1024);
-    static std::atomic<bool> attr{false};   // set once per process and type (idempotent if two threads race)
-    if (!attr) {
-      DD_CUDA(cudaFuncSetAttribute(k_band_factor_win<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-      attr = true;
-    }
-    (k_band_factor_win<T, 4><<<nmat, threads, smem, s>>>(CB, inv, nvec, nmax, b, flag), dd::note_launch());
+#define DD_FWIN(PPT_)                                                                                         \
+  do {                                                                                                      \
+    static std::atomic<bool> attr{false};   /* once per process and instance (idempotent if threads race) */ \
+    if (!attr) {                                                                                            \
+      DD_CUDA(cudaFuncSetAttribute(k_band_factor_win<T, 4, PPT_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                   220 * 1024));                                                            \
+      attr = true;                                                                                          \
+    }                                                                                                       \
+    (k_band_factor_win<T, 4, PPT_><<<nmat, threads, smem, s>>>(CB, inv, nvec, nmax, b, flag), dd::note_launch()); \
+  } while (0)
+    if (ppt == 4) DD_FWIN(4);
+    else if (ppt == 8) DD_FWIN(8);
+    else DD_FWIN(16);
+#undef DD_FWIN
   } else {
     (k_band_factor<T><<<nmat, 1024, sizeof(T) * (b + 1), s>>>(CB, inv, nvec, nmax, b, flag), dd::note_launch());
   }

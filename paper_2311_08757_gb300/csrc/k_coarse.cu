@@ -156,18 +156,19 @@ __global__ void k_coarse_entries(Geo g, const Sub* __restrict__ subs, const doub
   }
 }
 
-int coarse_assemble(dd_ctx* c) {
+int coarse_assemble(dd_ctx* c, cudaStream_t s) {
   const Geo& g = c->g;
   const int nnb = (g.p == 1) ? 3 : 9;
-  DD_CUDA(cudaMemsetAsync(c->A0band, 0, sizeof(double) * (size_t)g.nsub * nnb, c->stream));
+  DD_CUDA(cudaMemsetAsync(c->A0band, 0, sizeof(double) * (size_t)g.nsub * nnb, s));
   const long long work = (long long)g.nxi * (g.p == 2 ? g.nxi : 1) * g.Ypad;
   const int ncol2 = (g.p == 2) ? 3 : 1;
   for (int c1 = 0; c1 < 3; ++c1)
     for (int c2 = 0; c2 < ncol2; ++c2) {
-      (k_colour_vector<<<grid_blocks(work, kThreads), kThreads, 0, c->stream>>>(g, c->subs, c->wT, c->kpad, c1, c2,
-                                                                               c->w1), dd::note_launch());
-      launch_stencil(c, c->tabS, c->w1, c->w2, c->stream);
-      (k_coarse_entries<<<g.nsub, 256, 0, c->stream>>>(g, c->subs, c->wT, c->kpad, c1, c2, c->w2, c->A0band), dd::note_launch());
+      (k_colour_vector<<<grid_blocks(work, kThreads), kThreads, 0, s>>>(g, c->subs, c->wT, c->kpad, c1, c2, c->w1),
+       dd::note_launch());
+      launch_stencil(c, c->tabS, c->w1, c->w2, s);
+      (k_coarse_entries<<<g.nsub, 256, 0, s>>>(g, c->subs, c->wT, c->kpad, c1, c2, c->w2, c->A0band),
+       dd::note_launch());
       DD_CUDA(cudaGetLastError());
     }
   return DD_OK;
@@ -330,19 +331,18 @@ __global__ void k_band_inverse_rows(int n, int b, const T* __restrict__ CB, cons
 
 template <typename T>
 void launch_band_inverse_rows(int n, int b, const T* CB, const T* RB, const T* inv, T* out, cudaStream_t s) {
-  const int K = 1;
-  const size_t per = sizeof(T) * (size_t)K * n + band_ring_bytes(b, sizeof(T));
-  const int wpb = per <= 48 * 1024 ? 2 : 1;
-  const size_t smem = per * wpb;
-  const int ncolgroups = (n + K - 1) / K;
   DD_BAND_DISPATCH(b, {
-    {
-      constexpr int KK = 1;
-      DD_CUDA(cudaFuncSetAttribute(k_band_inverse_rows<T, NV, PF, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   220 * 1024));
-      (k_band_inverse_rows<T, NV, PF, KK><<<(ncolgroups + wpb - 1) / wpb, 32 * wpb, smem, s>>>(n, b, CB, RB, inv, out),
-       dd::note_launch());
-    }
+    // one identity column per warp: the warps, not the columns per warp, hide the latency of
+    // the sequential steps here (992 columns; four per warp measured 262 against 176 us)
+    constexpr int KK = 1;
+    const size_t per = sizeof(T) * (size_t)KK * n + band_ring_bytes(b, sizeof(T));
+    const int wpb = per <= 48 * 1024 ? 2 : 1;
+    const size_t smem = per * wpb;
+    const int ncolgroups = (n + KK - 1) / KK;
+    DD_CUDA(cudaFuncSetAttribute(k_band_inverse_rows<T, NV, PF, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 220 * 1024));
+    (k_band_inverse_rows<T, NV, PF, KK><<<(ncolgroups + wpb - 1) / wpb, 32 * wpb, smem, s>>>(n, b, CB, RB, inv, out),
+     dd::note_launch());
   });
   DD_CUDA(cudaGetLastError());
 }

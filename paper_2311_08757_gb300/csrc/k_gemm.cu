@@ -540,14 +540,15 @@ static int prec_bytes(int precision) {
 template <typename T>
 static void launch_local_inverse_t(dd_ctx* c, const int* nloc, T* out) {
   const int kpad = c->kpad;
-  const int K = 1;
-  const size_t per = sizeof(float) * (size_t)K * c->nloc_max + band_ring_bytes(c->band, sizeof(float));
-  const int wpb = per <= 48 * 1024 ? 2 : 1;
-  const size_t smem = per * wpb;
-  const long long jobs = (long long)c->ntypes * ((c->nloc_max + K - 1) / K);
-  const int nb = (int)((jobs + wpb - 1) / wpb);
   DD_BAND_DISPATCH(c->band, {
-    constexpr int KK = 1;
+    // identity columns solved four to a warp where the lane-owned solve allows it (its
+    // sequential steps are latency-bound; the columns share them)
+    constexpr int KK = (NV == 0 || NV > 4) ? 1 : 4;
+    const size_t per = sizeof(float) * (size_t)KK * c->nloc_max + band_ring_bytes(c->band, sizeof(float));
+    const int wpb = per <= 48 * 1024 ? 2 : 1;
+    const size_t smem = per * wpb;
+    const long long jobs = (long long)c->ntypes * ((c->nloc_max + KK - 1) / KK);
+    const int nb = (int)((jobs + wpb - 1) / wpb);
     DD_CUDA(cudaFuncSetAttribute(k_local_inverse<T, NV, PF, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  220 * 1024));
     (k_local_inverse<T, NV, PF, KK><<<nb, 32 * wpb, smem, c->stream>>>(nloc, c->nloc_max, c->band, c->bandCB32,
