@@ -230,11 +230,11 @@ def roofline_entry(name, model, ms_total, nlaunch, peaks, peak_src, precision):
 # from one ncu capture of this workload (profiles/top_kernels_cfg2_bench.md,
 # profiles/local_solve_fp64_cfg2.md); a kernel changed since its capture is left out.
 TRAFFIC = {
-    "stencil_Asigma": (33.654 + 0.537) * 1e6,
-    "prolong_sum": (44.658 + 0.120) * 1e6,
-    "xr_update": (67.132 + 0.681) * 1e6,
-    "pack_restrict": (16.881 + 0.000) * 1e6,
-    "local_solve_fp64": (18.77 + 0.00) * 1e6,
+    "stencil_Asigma": (33.651 + 0.522) * 1e6,
+    "prolong_sum": (44.915 + 0.108) * 1e6,
+    "xr_update": (67.132 + 0.627) * 1e6,
+    "pack_restrict": (16.874 + 0.000) * 1e6,
+    "local_solve_fp64": (18.789 + 0.022) * 1e6,
 }
 
 
