@@ -158,48 +158,92 @@ __global__ void __launch_bounds__(1024) k_band_factor_win(T* CB, T* inv, const i
   cp_async_wait<0>();   // no copy into this block's shared memory outlives it
 }
 
+// Wide bands (b > 160, the window does not fit in shared memory): blocked right-looking band
+// Cholesky.  Panels of kPanel columns: one CTA per matrix factors the panel in shared memory
+// (its columns have received every earlier update; within the panel the updates are rank 1),
+// writes the factor in the band storage the solves expect and the panel's unscaled L to a
+// scratch; then the rank-kPanel update of the trailing window, A(i, j) -= sum_c L(i, c) L(j, c)
+// for k1 <= j <= i <= k1 - 1 + b, is spread over many CTAs, each holding the panel in shared
+// memory.  The host steps through the panels (two launches each; no device-side waits).
+// Panel width np <= 32, as many columns as shared memory holds.
+constexpr int kPanel = 32;
+
 template <typename T>
-__global__ void __launch_bounds__(1024) k_band_factor(T* CB, T* inv, const int* __restrict__ nvec,
-                                                      int nmax, int b, int* flag) {
-  extern __shared__ __align__(16) unsigned char colk_raw[];
-  T* colk = reinterpret_cast<T*>(colk_raw);
-  const int m = blockIdx.x;
-  const int n = nvec[m];
-  const int bs = b + 1;
+__global__ void __launch_bounds__(1024) k_bpanel_factor(T* CB, T* inv, T* Lp, const int* __restrict__ nvec, int nmax,
+                                                       int b, int np, int k0, int* flag) {
+  extern __shared__ __align__(16) unsigned char bp_raw[];
+  T* P = reinterpret_cast<T*>(bp_raw);   // panel columns: P[c * bs + d] = A(k0 + c + d, k0 + c)
+  const int m = blockIdx.x, n = nvec[m];
+  if (k0 >= n) return;
+  const int bs = b + 1, nb = min(np, n - k0);
   T* A = CB + (size_t)m * nmax * bs;
   T* iv = inv + (size_t)m * nmax;
-  for (int k = 0; k < n; ++k) {
-    if (threadIdx.x == 0) {
-      T piv = A[(size_t)k * bs];
-      if (!(piv > (T)0)) {
-        atomicOr(flag, 1);
-        piv = (T)1;
-      }
-      const T l = sqrt(piv);
-      A[(size_t)k * bs] = l;
-      iv[k] = (T)1 / piv;
-      colk[0] = (T)1 / l;
+  T* L = Lp + (size_t)m * np * bs;
+  for (int e = threadIdx.x; e < nb * bs; e += blockDim.x) P[e] = A[(size_t)k0 * bs + e];
+  __syncthreads();
+  for (int c = 0; c < nb; ++c) {
+    const int k = k0 + c;
+    T piv = P[c * bs];
+    if (!(piv > (T)0)) {
+      if (threadIdx.x == 0) atomicOr(flag, 1);
+      piv = (T)1;
     }
-    __syncthreads();
-    const T il = colk[0];
+    const T il = rsqrt_el(piv);   // every thread
     const int dmax = min(b, n - 1 - k);
-    for (int d = 1 + threadIdx.x; d <= b; d += blockDim.x) {
-      T v = (T)0;
-      if (d <= dmax) v = A[(size_t)k * bs + d] * il;
-      colk[d] = v;
-    }
-    __syncthreads();
-    // A(k+d1, k+d2) -= L(k+d1,k) L(k+d2,k), 1 <= d2 <= d1 <= dmax; stored at CB[k+d2][d1-d2]
-    const int tot = dmax * dmax;
-    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-      const int d1 = t / dmax + 1, d2 = t % dmax + 1;
-      if (d2 <= d1) {
-        T* a = A + (size_t)(k + d2) * bs + (d1 - d2);
-        *a = fma_el(-colk[d1], colk[d2], *a);
+    for (int d = threadIdx.x; d <= b; d += blockDim.x) {
+      if (d == 0) {   // P[c * bs] stays the pivot: every thread reads it above, none after
+        A[(size_t)k * bs] = piv * il;   // L(k, k)
+        iv[k] = il * il;
+        L[c * bs] = piv * il;
+      } else {
+        const T l = (d <= dmax) ? P[c * bs + d] * il : (T)0;   // L(k + d, k)
+        A[(size_t)k * bs + d] = l * il;   // pre-scaled by 1 / L(k, k) (0 past the end)
+        P[c * bs + d] = l;
+        L[c * bs + d] = l;
       }
     }
-    for (int d = 1 + threadIdx.x; d <= dmax; d += blockDim.x) A[(size_t)k * bs + d] = colk[d] * il;
     __syncthreads();
+    // the later panel columns c2 > c: A(j + d2, j) -= L(j + d2, k) L(j, k), j = k0 + c2
+    const int rem = nb - 1 - c;
+    for (int e = threadIdx.x; e < rem * bs; e += blockDim.x) {
+      const int c2 = c + 1 + e / bs, d2 = e % bs;
+      const int ei = c2 - c + d2;   // row offset from k
+      if (ei <= b) P[c2 * bs + d2] = fma_el(-P[c * bs + ei], P[c * bs + (c2 - c)], P[c2 * bs + d2]);
+    }
+    __syncthreads();
+  }
+}
+
+// tile (blockIdx.x) of 32 trailing columns of matrix blockIdx.y
+template <typename T>
+__global__ void __launch_bounds__(1024) k_bpanel_update(T* CB, const T* __restrict__ Lp,
+                                                       const int* __restrict__ nvec, int nmax, int b, int np,
+                                                       int k0) {
+  extern __shared__ __align__(16) unsigned char bu_raw[];
+  T* Ls = reinterpret_cast<T*>(bu_raw);   // the panel's L: Ls[c * bs + e] = L(k0 + c + e, k0 + c)
+  const int m = blockIdx.y, n = nvec[m];
+  const int nb = min(np, n - k0);
+  if (nb <= 0) return;
+  const int k1 = k0 + nb, last = min(k1 - 1 + b, n - 1);   // rows and columns the panel reaches
+  const int j0 = k1 + 32 * blockIdx.x;
+  if (j0 > last) return;
+  const int bs = b + 1;
+  const T* L = Lp + (size_t)m * np * bs;
+  for (int e = threadIdx.x; e < nb * bs; e += blockDim.x) Ls[e] = L[e];
+  __syncthreads();
+  T* A = CB + (size_t)m * nmax * bs;
+  const int ncol = min(32, last - j0 + 1);
+  for (int e = threadIdx.x; e < ncol * bs; e += blockDim.x) {
+    const int jj = e / bs, r = e % bs;   // entry (i, j) = (j + r, j), stored at CB[j][r]
+    const int j = j0 + jj, i = j + r;
+    if (i > last) continue;
+    T acc = (T)0;
+#pragma unroll 8
+    for (int c = 0; c < nb; ++c) {
+      const int ei = i - k0 - c, ej = j - k0 - c;   // ej >= 1; both past the band give 0
+      if (ei <= b) acc = fma_el(Ls[c * bs + ei], Ls[c * bs + ej], acc);
+    }
+    A[(size_t)j * bs + r] -= acc;
   }
 }
 
@@ -271,7 +315,23 @@ static void factor_launch(T* CB, T* RB, T* inv, const int* nvec, int nmat, int n
     else DD_FWIN(16);
 #undef DD_FWIN
   } else {
-    (k_band_factor<T><<<nmat, 1024, sizeof(T) * (b + 1), s>>>(CB, inv, nvec, nmax, b, flag), dd::note_launch());
+    const int np = std::min<int>(kPanel, (int)((200 * 1024) / (sizeof(T) * (size_t)(b + 1))));
+    if (np < 1) throw Error(DD_EINVAL, "band too wide for the shared-memory panel factorisation");
+    T* Lp = nullptr;
+    DD_CUDA(cudaMallocAsync(&Lp, sizeof(T) * (size_t)nmat * np * (b + 1), s));
+    const size_t psm = sizeof(T) * (size_t)np * (b + 1);
+    static std::atomic<bool> attr{false};   // once per process and type (idempotent if threads race)
+    if (!attr) {
+      DD_CUDA(cudaFuncSetAttribute(k_bpanel_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+      DD_CUDA(cudaFuncSetAttribute(k_bpanel_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+      attr = true;
+    }
+    const dim3 ug((b + 31) / 32, nmat);
+    for (int k0 = 0; k0 < nmax; k0 += np) {
+      (k_bpanel_factor<T><<<nmat, 1024, psm, s>>>(CB, inv, Lp, nvec, nmax, b, np, k0, flag), dd::note_launch());
+      (k_bpanel_update<T><<<ug, 1024, psm, s>>>(CB, Lp, nvec, nmax, b, np, k0), dd::note_launch());
+    }
+    DD_CUDA(cudaFreeAsync(Lp, s));
   }
   DD_CUDA(cudaGetLastError());
   const long long total = (long long)nmat * nmax * (b + 1);
