@@ -541,9 +541,9 @@ template <typename T>
 static void launch_local_inverse_t(dd_ctx* c, const int* nloc, T* out) {
   const int kpad = c->kpad;
   DD_BAND_DISPATCH(c->band, {
-    // identity columns solved four to a warp where the lane-owned solve allows it (its
-    // sequential steps are latency-bound; the columns share them)
-    constexpr int KK = (NV == 0 || NV > 4) ? 1 : 4;
+    // identity columns solved four (two for wide bands) to a warp where the lane-owned solve
+    // allows it: its sequential steps are latency-bound, and the columns share them
+    constexpr int KK = (NV == 0) ? 1 : (NV <= 4 ? 4 : 2);
     const size_t per = sizeof(float) * (size_t)KK * c->nloc_max + band_ring_bytes(c->band, sizeof(float));
     const int wpb = per <= 48 * 1024 ? 2 : 1;
     const size_t smem = per * wpb;
