@@ -171,7 +171,7 @@ def kernel_model(w, info, ntype_counts, nloc_by_type, band, precision):
 
     Bytes count one pass over each vector the kernel must read or write (DOF = interior
     unknown, f = sum |N_i| / ndof); FP64 flops count 2 per FMA of the arithmetic the
-    kernel must do.  See the design doc, section 4.
+    kernel must do.
     """
     ndof = info["ndof"]
     nloc_sum = sum(c * n for c, n in zip(ntype_counts, nloc_by_type))
@@ -210,7 +210,8 @@ def roofline_entry(name, model, ms_total, nlaunch, peaks, peak_src, precision):
     bound = max((t_alu, "alu"), (t_ten, "tensor"), (t_hbm, "hbm"))[1]
     if bound == "alu":
         ent = {"bound": "alu", "achieved": fp64 / avg_s / 1e12, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
-               "peak_source": "FP64 FMA microbenchmark on this GB300 (DESIGN.md section 4)"}
+               "peak_source": "FP64 FMA microbenchmark on this GB300: 8 independent FMA chains per thread, "
+                              "152 x 8 blocks of 256 threads"}
     elif bound == "tensor":
         ent = {"bound": "tensor", "achieved": tens / avg_s / 1e12, "peak": tpeak, "unit": "TFLOP/s",
                "peak_source": peak_src + (" (bf16 x 1/2 for tf32)" if precision == "tf32" else "")}
