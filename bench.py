@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--coarse-solve", default="auto", choices=["auto", "cr", "dense"])
     ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--setup-only", default=None, choices=["cfg2", "cfg3"],
+                    help="time only the set-up stages (cell eigenpair, coarse build) of one workload")
     return ap.parse_args()
 
 
@@ -282,6 +284,35 @@ REF_INNER_ITERS = {"cfg2": 330, "cfg1": 106, "cfg2_small": 250}
 # ----------------------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------------------
+def setup_only(args, dd, dev, reps=3):
+    """Times the two set-up stages of one ground state on their own: the cell eigen-solve
+    (shift and cell eigenfunction) and the coarse build (local factors or inverses and the
+    coarse matrix).  One untimed pass, then `reps` timed ones with CUDA events."""
+    import torch
+    from ddinputs import WORKLOADS, sample_cell_qp
+    w = WORKLOADS[args.setup_only]
+    V = torch.from_numpy(sample_cell_qp(w)).to(dev)
+    es = dd.Eigensolver(dd.grid_from_workload(w, precision=dd.PRECISIONS[args.precision]), V)
+    stream = torch.cuda.current_stream(dev)
+    t_cell, t_coarse = [], []
+    for i in range(reps + 1):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize()
+        e[0].record(stream)
+        dd.dd_set_potential(es.ctx, V)
+        sigma = dd.dd_cell_eigenpair(es.ctx)
+        e[1].record(stream)
+        dd.dd_coarse_build(es.ctx)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        if i:
+            t_cell.append(e[0].elapsed_time(e[1]))
+            t_coarse.append(e[1].elapsed_time(e[2]))
+    es.close()
+    return {"mode": "setup_only", "workload": args.setup_only, "dofs": w.dofs, "precision": args.precision,
+            "sigma": sigma, "ms_cell_eigenpair": t_cell, "ms_coarse_build": t_coarse}
+
+
 def main():
     args = parse()
     if args.cpu_sample:
@@ -311,6 +342,10 @@ def main():
 
     if not os.path.exists(dd.lib_path()):
         raise RuntimeError("libddeig.so is not built (run __graft_entry__.build())")
+    if args.setup_only:
+        if rank == 0:
+            print(json.dumps(setup_only(args, dd, dev)))
+        return
 
     w = WORKLOADS[args.workload]
     V_host = sample_cell_qp(w)
