@@ -44,7 +44,7 @@ FP64_TFLOPS = 1.19
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cfg2")
@@ -116,42 +116,44 @@ def load_peaks() -> tuple[dict, str]:
 
 
 class ClockSampler:
-    """nvidia-smi sampling (200 ms) of SM clocks and throttle reasons while active."""
+    """nvidia-smi sampling (every 50 ms) of SM clocks and throttle reasons.  `start` returns
+    once the first sample has arrived, so the sampler is running before the timed region
+    opens; `stop(t0, t1)` keeps the samples taken between two `time.perf_counter` marks (the
+    first one after t0 when the region is shorter than the interval)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 50
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.lines = []
+        self.lines = []   # (perf_counter at arrival, csv line)
 
-    def start(self):
+    def start(self, wait_s: float = 5.0):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.th = threading.Thread(target=self._read, daemon=True)
-            self.th.start()
         except FileNotFoundError:
             self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+        t_end = time.perf_counter() + wait_s
+        while not self.lines and time.perf_counter() < t_end and self.proc.poll() is None:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
-    def stop(self) -> dict:
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
+    @staticmethod
+    def summarise(lines) -> dict:
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -166,6 +168,27 @@ class ClockSampler:
         sm.sort()
         return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+    def stop(self, t0: float = None, t1: float = None) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        if t1 is not None:   # one more interval so that a sample taken inside the region arrives
+            time.sleep(2 * self.INTERVAL_MS / 1e3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=5)
+        rows = list(self.lines)
+        if t0 is not None and t1 is not None:
+            inside = [ln for ts, ln in rows if t0 <= ts <= t1]
+            if not inside:
+                inside = [ln for ts, ln in rows if ts >= t0][:1]
+            rows = inside
+        else:
+            rows = [ln for _, ln in rows]
+        return self.summarise(rows)
 
 
 def kernel_model(w, info, ntype_counts, nloc_by_type, band, precision):
@@ -406,8 +429,9 @@ def main():
     per, res, launches = timed(mixed, args.steps)
     torch.cuda.synchronize()
     barrier()
-    t_wall = time.perf_counter() - t_wall0
-    clk = clocks.stop()
+    t_wall1 = time.perf_counter()
+    t_wall = t_wall1 - t_wall0
+    clk = clocks.stop(t_wall0, t_wall1)
     lam, sigma, outer, inner_tot = res
     step_ms = sum(per) / len(per)
     # max over ranks
