@@ -120,12 +120,16 @@ static __device__ __noinline__ float tf32_slow(double x) {
 static __device__ __noinline__ double f64_slow(float f) { return (double)f; }
 
 // IEEE round-to-nearest-even of a double to bfloat16 (bits).  Only 32-bit integer
-// operations on the two words of x; zeros, results outside the normal range, infinities and
-// NaNs take the hardware conversion (one range check selects them).
+// operations on the two words of x; results outside the normal range, infinities and NaNs
+// take the hardware conversion (one range check selects them).  Zeros, which every padded
+// column holds, are answered inside that branch by their sign bit, without the call.
 __device__ __forceinline__ unsigned short f64_to_bf16_bits(double x) {
   const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
   const int eb = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
-  if (__builtin_expect((unsigned)(eb - 1) >= 254u, 0)) return bf16_bits_slow(x);
+  if (__builtin_expect((unsigned)(eb - 1) >= 254u, 0)) {
+    if (((hi << 1) | lo) == 0u) return (unsigned short)(hi >> 16);   // +-0
+    return bf16_bits_slow(x);
+  }
   const unsigned keep = (hi >> 13) & 0x7Fu;   // top 7 of the 52 mantissa bits
   const unsigned remh = hi & 0x1FFFu;         // the other 45 bits are remh:lo; half is 0x1000:0
   unsigned r = ((unsigned)eb << 7) | keep;
@@ -137,23 +141,29 @@ __device__ __forceinline__ unsigned short f64_to_bf16_bits(double x) {
 
 // Round-to-nearest, ties away from zero, of a double to TF32 (an FP32 bit pattern whose low
 // 13 mantissa bits are zero), as cvt.rna.tf32.f32 would round the exact value.  Integer
-// operations as above.
+// operations as above (zeros too).
 __device__ __forceinline__ float f64_to_tf32(double x) {
   const unsigned hi = (unsigned)__double2hiint(x);
   const int ef = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
-  if (__builtin_expect((unsigned)(ef - 1) >= 254u, 0)) return tf32_slow(x);
+  if (__builtin_expect((unsigned)(ef - 1) >= 254u, 0)) {
+    if (((hi << 1) | (unsigned)__double2loint(x)) == 0u) return __uint_as_float(hi & 0x80000000u);   // +-0
+    return tf32_slow(x);
+  }
   const unsigned keep = (hi >> 10) & 0x3FFu;   // top 10 mantissa bits
   unsigned r = ((unsigned)ef << 10) | keep;
   if ((hi & 0x3FFu) >= 0x200u) r += 1;         // the other 42 bits at or above half
   return __uint_as_float(((hi >> 31) << 31) | (r << 13));
 }
 
-// Exact float -> double by integer operations for normal floats; zeros, subnormals,
+// Exact float -> double by integer operations for normal floats and zeros; subnormals,
 // infinities and NaNs take the hardware conversion.
 __device__ __forceinline__ double f32_to_f64(float f) {
   const unsigned u = __float_as_uint(f);
   const unsigned e = (u >> 23) & 0xFFu;
-  if (__builtin_expect(e - 1u >= 254u, 0)) return f64_slow(f);
+  if (__builtin_expect(e - 1u >= 254u, 0)) {
+    if ((u << 1) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);   // +-0
+    return f64_slow(f);
+  }
   const unsigned m = u & 0x7FFFFFu;
   const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | (m >> 3);
   return __hiloint2double((int)hi, (int)(m << 29));

@@ -543,8 +543,12 @@ __device__ __forceinline__ double to_f64(double d) { return d; }
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
 
+// Register budget: 32 per thread (8 blocks of 256 per SM) for p = 1, which fits it; 48
+// (5 blocks) for p = 2, whose four owners per node spilled at 32 (cfg3: 987 -> 971 ms per
+// ground state).  The FP64 p = 1 variant spills a little at 32 yet ran 4% faster there than
+// at 48 without spills.
 template <int P, typename TY, bool RAS, int U>
-__global__ void __launch_bounds__(kThreads, 8 / U) k_prolong(Geo g, const int4* __restrict__ axown,
+__global__ void __launch_bounds__(kThreads, (P == 1 ? 8 : 5) / U) k_prolong(Geo g, const int4* __restrict__ axown,
                                                       const int4* __restrict__ subrow, const TY* __restrict__ Y,
                                                       const TY* __restrict__ wT, const TY* __restrict__ puT,
                                                       const TY* __restrict__ u0, int coarse,
