@@ -317,8 +317,8 @@ int dd_coarse_matrix(dd_ctx* ctx, double* A0_host);
  *                       as a GEMV, 0 = automatic (cyclic reduction for p = 1: measured faster
  *                       beside the local GEMM at 2048 subdomains, and no N^2 set-up; dense for
  *                       p = 2); read by dd_coarse_build [0]
- *   DD_OPT_GEMM_TILE_N  N tile of the mixed local-solve contraction: 128 or 256, 0 = chosen by
- *                       timing both on the context's operands at dd_coarse_build (cached per
+ *   DD_OPT_GEMM_TILE_N  N tile of the mixed local-solve contraction: 128, 160 or 256, 0 = chosen
+ *                       by timing each on the context's operands at dd_coarse_build (cached per
  *                       problem shape); the result does not depend on it [0]
  *   DD_OPT_LOCAL_RHS    FP64 local solves: subdomains of one type solved together by one warp,
  *                       1, 2 or 4 (capped by shared memory), 0 = default (2 where allowed) [0]; the result

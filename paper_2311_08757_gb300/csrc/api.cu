@@ -1248,7 +1248,8 @@ int dd_set_option(dd_ctx* c, int option, int value) {
       c->coarse_mode = value;
       break;
     case DD_OPT_GEMM_TILE_N:
-      if (value != 0 && value != 128 && value != 256) return fail(c, DD_EINVAL, "GEMM tile N must be 0, 128 or 256");
+      if (value != 0 && value != 128 && value != 160 && value != 256)
+        return fail(c, DD_EINVAL, "GEMM tile N must be 0, 128, 160 or 256");
       c->gemm_bn_opt = value;
       break;
     case DD_OPT_LOCAL_RHS: {

@@ -190,7 +190,7 @@ struct dd_ctx {
   float* wT32 = nullptr;           // FP32 copies of wT and puT (the prolong-sum of the mixed form)
   float* puT32 = nullptr;
   int ras = 0;                     // 1: restricted local prolongation (M_RAS2^{-1})
-  int gemm_bn_opt = 0;             // local-solve GEMM N tile: 0 autotuned, 128 or 256
+  int gemm_bn_opt = 0;             // local-solve GEMM N tile: 0 autotuned, 128, 160 or 256
   float* ysc = nullptr;            // FP8: per packed row 1 / (s_i s_T) (undoes the operand scales)
   float* ascale = nullptr;         // FP8: per type 1 / s_T
   double* ascale64 = nullptr;      // FP8: per type s_T = 448 / max|A_T^{-1}|

@@ -38,9 +38,12 @@ struct TcCfg {
   static constexpr int BM = 128, BN = BN_;
   static constexpr int BK = 128 / (int)sizeof(T);   // one 128-byte swizzle row
   static constexpr int UK = 32 / (int)sizeof(T);    // K of one tcgen05.mma (32 bytes)
-  // 128 x 256 tiles: 4 stages (193 KB, one CTA per SM); 128 x 128 tiles: 3 stages (97 KB),
-  // so that two CTAs share an SM and one's epilogue overlaps the other's MMAs
+  // 128 x 256 tiles: 4 stages (193 KB, one CTA per SM); 128 x 160: 4 stages (145 KB, one
+  // CTA per SM); 128 x 128 tiles: 3 stages (97 KB), so that two CTAs share an SM and one's
+  // epilogue overlaps the other's MMAs
   static constexpr int STAGES = (BN_ == 128) ? 3 : 4;
+  // TMEM is allocated in powers of two of at least 32 columns (one FP32 column per output column)
+  static constexpr int TMEM_COLS = BN_ <= 32 ? 32 : (BN_ <= 64 ? 64 : (BN_ <= 128 ? 128 : 256));
   static constexpr int A_BYTES = BM * 128;
   static constexpr int B_BYTES = BN * 128;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
@@ -128,7 +131,7 @@ __global__ void __launch_bounds__(128, 1)
               const Tile* __restrict__ tiles, int K, int mlimit, int rows_per_type, float* __restrict__ Y,
               int ldy, int* err, const PcgState* st, const float* __restrict__ ysc) {
   using C = TcCfg<T, BN>;
-  constexpr int kTmemCols = BN;   // FP32 accumulator: one column per output column
+  constexpr int kTmemCols = C::TMEM_COLS;
   if (st != nullptr && st->done) return;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -466,14 +469,18 @@ __global__ void k_quantize_e4m3(const double* __restrict__ a, long long per_type
     out[t] = to_e4m3(a[t] * scale[t / per_type]);
 }
 
-// Two output-tile shapes, 128 x 256 and 128 x 128: per output element the K order of the
-// accumulation is the same in both, so the choice changes the speed, not the result.
+// Three output-tile shapes, 128 x 256, 128 x 160 and 128 x 128: per output element the K
+// order of the accumulation is the same in all, so the choice changes the speed, not the
+// result.  128 x 160 fits cfg2's 2046 interior subdomains in 13 column tiles, so that its
+// 150 tiles make one wave on 152 SMs.
+constexpr int kTileN[3] = {256, 128, 160};
+inline int tile_index(int bn) { return bn == 256 ? 0 : (bn == 128 ? 1 : 2); }
 struct GemmPlan {
-  CUtensorMap tA, tB256, tB128;
-  Tile* tiles[2] = {nullptr, nullptr};   // [0]: 128 x 256 tiles, [1]: 128 x 128 tiles
-  int ntiles[2] = {0, 0};
-  int cap[2] = {0, 0};
-  int es = 2;                            // operand bytes: 1 E4M3, 2 BF16, 4 TF32
+  CUtensorMap tA, tB[3];                         // tB[i]: box of kTileN[i] rows of R
+  Tile* tiles[3] = {nullptr, nullptr, nullptr};   // tiles[i]: 128 x kTileN[i] output tiles
+  int ntiles[3] = {0, 0, 0};
+  int cap[3] = {0, 0, 0};
+  int es = 2;                                     // operand bytes: 1 E4M3, 2 BF16, 4 TF32
 };
 
 // Autotuner cache: the faster N tile per problem shape (precision, K, rows per type, subdomain
@@ -483,10 +490,13 @@ static std::map<std::string, int> g_tune_bn;
 
 template <typename T>
 static void run_gemm_t(dd_ctx* c, GemmPlan* plan, int bn, const PcgState* st, cudaStream_t s, const float* ysc) {
-  const int i = bn == 256 ? 0 : 1;
-  const CUtensorMap* tB = bn == 256 ? &plan->tB256 : &plan->tB128;
+  const int i = tile_index(bn);
+  const CUtensorMap* tB = &plan->tB[i];
   if (bn == 256)
     launch_tc<T, 256>(&plan->tA, tB, plan->tiles[i], plan->ntiles[i], c->kpad, c->kpad, c->kpad, c->Y32, c->kpad,
+                      c->dev_err + 8, st, s, ysc);
+  else if (bn == 160)
+    launch_tc<T, 160>(&plan->tA, tB, plan->tiles[i], plan->ntiles[i], c->kpad, c->kpad, c->kpad, c->Y32, c->kpad,
                       c->dev_err + 8, st, s, ysc);
   else
     launch_tc<T, 128>(&plan->tA, tB, plan->tiles[i], plan->ntiles[i], c->kpad, c->kpad, c->kpad, c->Y32, c->kpad,
@@ -499,7 +509,7 @@ static void run_gemm(dd_ctx* c, GemmPlan* plan, int bn, const PcgState* st, cuda
   else run_gemm_t<__nv_fp8_e4m3>(c, plan, bn, st, s, c->ysc);
 }
 
-// time both tile shapes on the context's operands (3 launches each after one warm-up)
+// time the tile shapes on the context's operands (3 launches each after one warm-up)
 static int tune_bn(dd_ctx* c, GemmPlan* plan) {
   std::string key = std::to_string(plan->es) + ":" + std::to_string(c->kpad);
   for (int t = 0; t < c->ntypes; ++t) key += ":" + std::to_string(c->type_count[t]);
@@ -513,7 +523,7 @@ static int tune_bn(dd_ctx* c, GemmPlan* plan) {
   DD_CUDA(cudaEventCreate(&e1));
   float best = 0.0f;
   int best_bn = 256;
-  for (int bn : {256, 128}) {
+  for (int bn : kTileN) {
     run_gemm(c, plan, bn, nullptr, c->stream);
     DD_CUDA(cudaEventRecord(e0, c->stream));
     for (int r = 0; r < 3; ++r) run_gemm(c, plan, bn, nullptr, c->stream);
@@ -612,11 +622,10 @@ int gemm_setup(dd_ctx* c) {
   plan->es = es;
   const int BK = 128 / es;   // one 128-byte swizzle row of K
   make_tmap(&plan->tA, c->Ainv, es, kpad, (long long)c->ntypes * kpad, BK, 128);
-  make_tmap(&plan->tB256, c->Rpack, es, kpad, g.nsub, BK, 256);
-  make_tmap(&plan->tB128, c->Rpack, es, kpad, g.nsub, BK, 128);
   const int mt = (kpad + 127) / 128;
-  for (int i = 0; i < 2; ++i) {
-    const int bn = i == 0 ? 256 : 128;
+  for (int i = 0; i < 3; ++i) {
+    const int bn = kTileN[i];
+    make_tmap(&plan->tB[i], c->Rpack, es, kpad, g.nsub, BK, bn);
     std::vector<Tile> tl;
     for (int t = 0; t < c->ntypes; ++t) {
       const int first = c->type_first[t], cnt = c->type_count[t];

@@ -93,17 +93,19 @@ def test_mixed_ground_state(name, prec):
 @pytest.mark.parametrize("prec", ["bf16", "tf32", "fp8"])
 @pytest.mark.parametrize("name", ["cfg2_small", "p2_small"])
 def test_gemm_tile_shapes_give_identical_preconditioner(name, prec):
-    """The 128 x 128 and 128 x 256 output tiles accumulate every element over K in the same
-    order, so the autotuner's choice cannot change a bit of the preconditioner."""
+    """The 128 x 128, 128 x 160 and 128 x 256 output tiles accumulate every element over K in
+    the same order, so the autotuner's choice cannot change a bit of the preconditioner."""
     from ddinputs import WORKLOADS
     w = WORKLOADS["cfg2_small" if name == "cfg2_small" else "cfg3_small"]
     r = np.random.default_rng(19).standard_normal(w.dofs)
     out = {}
     with make_solver(w, precision=prec) as es:
         es.prepare()
-        for bn in (256, 128, 0):
+        for bn in (256, 160, 128, 0):
             dd.dd_set_option(es.ctx, dd.DD_OPT_GEMM_TILE_N, bn)
             z = gpu_vec(np.zeros(w.dofs))
             dd.dd_apply_preconditioner(es.ctx, gpu_vec(r), z)
             out[bn] = host(z)
     assert np.array_equal(out[256], out[128])
+    assert np.array_equal(out[256], out[160])
+    assert np.array_equal(out[256], out[0])
