@@ -645,16 +645,20 @@ int gemm_setup(dd_ctx* c) {
   return DD_OK;
 }
 
+// 128 threads (16 blocks of 31 registers per SM): all 2048 subdomain blocks of cfg2 are
+// resident at once instead of 1216 + 832 blocks of 256 (14.3 against 15.6 us)
+constexpr int kPackThreads = 128;
+
 void launch_pack(dd_ctx* c, const double* r, double* c0, cudaStream_t s) {
   const Geo& g = c->g;
   if (c->grid.precision == DD_PREC_BF16)
-    (k_pack<__nv_bfloat16><<<g.nsub, 256, 0, s>>>(g, c->subs, c->slot_of_sub, r, c->kpad, (__nv_bfloat16*)c->Rpack,
+    (k_pack<__nv_bfloat16><<<g.nsub, kPackThreads, 0, s>>>(g, c->subs, c->slot_of_sub, r, c->kpad, (__nv_bfloat16*)c->Rpack,
                                                  c->wT, c0, c->st, nullptr, nullptr), dd::note_launch());
   else if (c->grid.precision == DD_PREC_TF32)
-    (k_pack<float><<<g.nsub, 256, 0, s>>>(g, c->subs, c->slot_of_sub, r, c->kpad, (float*)c->Rpack, c->wT, c0,
+    (k_pack<float><<<g.nsub, kPackThreads, 0, s>>>(g, c->subs, c->slot_of_sub, r, c->kpad, (float*)c->Rpack, c->wT, c0,
                                          c->st, nullptr, nullptr), dd::note_launch());
   else
-    (k_pack<__nv_fp8_e4m3><<<g.nsub, 256, 0, s>>>(g, c->subs, c->slot_of_sub, r, c->kpad, (__nv_fp8_e4m3*)c->Rpack,
+    (k_pack<__nv_fp8_e4m3><<<g.nsub, kPackThreads, 0, s>>>(g, c->subs, c->slot_of_sub, r, c->kpad, (__nv_fp8_e4m3*)c->Rpack,
                                                  c->wT, c0, c->st, c->ascale, c->ysc), dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
