@@ -256,10 +256,11 @@ def roofline_entry(name, model, ms_total, nlaunch, peaks, peak_src, precision):
 # from one ncu capture of this workload (profiles/top_kernels_cfg2_bench.md,
 # profiles/local_solve_fp64_cfg2.md); a kernel changed since its capture is left out.
 TRAFFIC = {
-    "stencil_Asigma": (33.651 + 0.522) * 1e6,
-    "prolong_sum": (44.915 + 0.108) * 1e6,
-    "xr_update": (67.132 + 0.627) * 1e6,
+    "stencil_Asigma": (33.651 + 0.615) * 1e6,
+    "prolong_sum": (44.916 + 0.131) * 1e6,
+    "xr_update": (67.133 + 0.625) * 1e6,
     "pack_restrict": (16.874 + 0.000) * 1e6,
+    "local_gemm_tc": (15.096 + 0.000) * 1e6,
     "local_solve_fp64": (18.789 + 0.022) * 1e6,
 }
 
@@ -682,6 +683,7 @@ def main():
             "config": {"workload": f"{args.workload}: p=1, L={w.L}, ell=1, h=1/{w.n}, delta={w.overlap}, "
                                    f"dofs={w.dofs}, {w.L ** w.p} subdomains, V=4-term cosine (seed {w.seed})",
                        "precision": args.precision, "l2": "flushed between steps (256 MB write)",
+                       "local_gemm_tile": f"128x{dd.dd_query(mixed.ctx)['gemm_tile_n']}",
                        "parallelism": f"replicas x{world}"},
             "time_to_ground_state_ms": {"mixed": step_ms, "fp64_plain": fp64_ms,
                                         "speedup_mixed_vs_fp64": fp64_ms / step_ms},

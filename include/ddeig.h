@@ -101,6 +101,9 @@ typedef struct {
     int       cell_iters;    /* inverse iterations used by the cell solve                   */
     int       stage;         /* 1 set up, 2 cell eigenpair done, 3 coarse built             */
     long long device_bytes;  /* device memory held by the context                           */
+    int       gemm_tile_n;   /* N tile of the mixed local-solve contraction chosen at
+                                dd_coarse_build (128, 160 or 256; 0 before it and in FP64)   */
+    int       reserved_;     /* zero                                                         */
 } dd_info;
 
 /*

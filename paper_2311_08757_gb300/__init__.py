@@ -39,7 +39,8 @@ class dd_grid(ctypes.Structure):
 class dd_info(ctypes.Structure):
     _fields_ = [("ndof", c_longlong), ("ncell", c_longlong), ("nsub", c_int), ("ntypes", c_int),
                 ("nloc_max", c_int), ("kpad", c_int), ("band_local", c_int), ("sigma", c_double),
-                ("cell_iters", c_int), ("stage", c_int), ("device_bytes", c_longlong)]
+                ("cell_iters", c_int), ("stage", c_int), ("device_bytes", c_longlong), ("gemm_tile_n", c_int),
+                ("reserved_", c_int)]
 
 
 class DDError(RuntimeError):

@@ -1213,6 +1213,8 @@ int dd_query(const dd_ctx* c, dd_info* info) {
   info->cell_iters = c->cell_iters;
   info->stage = c->stage;
   info->device_bytes = c->bytes;
+  info->gemm_tile_n = c->gemm_ok ? (c->gemm_bn_opt != 0 ? c->gemm_bn_opt : c->gemm_bn) : 0;
+  info->reserved_ = 0;
   return DD_OK;
 }
 

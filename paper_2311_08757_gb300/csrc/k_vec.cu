@@ -6,8 +6,9 @@
 // only on (a mod n, j).  tab[tap][cls] holds the coupling of class cls to its neighbour at
 // offset tap in {-1,0,1}^d; A_sigma = A - sigma M (Sec. 1.1) is a third table.
 #include <algorithm>
-
 #include <atomic>
+#include <map>
+#include <mutex>
 
 #include "dd_common.cuh"
 
@@ -23,6 +24,28 @@ int grid_blocks(long long work, int threads, int max_per_sm) {
   if (b > kMaxRedBlocks) b = kMaxRedBlocks;
   if (b < 1) b = 1;
   return (int)b;
+}
+
+// Grid of a grid-stride kernel capped at the blocks the SMs keep resident at once (from the
+// kernel's registers and shared memory, queried once per kernel), so that it runs as one
+// wave: a second, partial wave of blocks leaves most SMs idle at its end.
+template <typename K>
+static int resident_grid(K* kernel, long long work, int threads) {
+  static std::mutex mu;
+  static std::map<const void*, int> per_sm;
+  int occ = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = per_sm.find((const void*)kernel);
+    if (it != per_sm.end()) occ = it->second;
+  }
+  if (occ == 0) {
+    DD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, 0));
+    occ = std::max(1, std::min(occ, 8));
+    std::lock_guard<std::mutex> lk(mu);
+    per_sm[(const void*)kernel] = occ;
+  }
+  return grid_blocks(work, threads, occ);
 }
 
 // ----------------------------------------------------------------------------------------
@@ -209,27 +232,43 @@ static long long interior_work(const Geo& g) {
 
 void launch_stencil(dd_ctx* c, const double* tab, const double* x, double* y, cudaStream_t s) {
   const Geo& g = c->g;
-  const int nb = grid_blocks(interior_work(g), kThreads);
-  if (g.p == 1) (k_stencil<1, false><<<nb, kThreads, 0, s>>>(g, tab, x, y, nullptr, nullptr, nullptr), dd::note_launch());
-  else (k_stencil<2, false><<<nb, kThreads, 0, s>>>(g, tab, x, y, nullptr, nullptr, nullptr), dd::note_launch());
+  const long long w = interior_work(g);
+  if (g.p == 1)
+    (k_stencil<1, false><<<resident_grid(k_stencil<1, false>, w, kThreads), kThreads, 0, s>>>(g, tab, x, y, nullptr,
+                                                                                              nullptr, nullptr),
+     dd::note_launch());
+  else
+    (k_stencil<2, false><<<resident_grid(k_stencil<2, false>, w, kThreads), kThreads, 0, s>>>(g, tab, x, y, nullptr,
+                                                                                              nullptr, nullptr),
+     dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 
 void launch_stencil2(dd_ctx* c, const double* tab1, const double* tab2, const double* x, double* y1, double* y2,
                      cudaStream_t s) {
   const Geo& g = c->g;
-  const int nb = grid_blocks(interior_work(g), kThreads);
-  if (g.p == 1) (k_stencil2<1><<<nb, kThreads, 0, s>>>(g, tab1, tab2, x, y1, y2), dd::note_launch());
-  else (k_stencil2<2><<<nb, kThreads, 0, s>>>(g, tab1, tab2, x, y1, y2), dd::note_launch());
+  const long long w = interior_work(g);
+  if (g.p == 1)
+    (k_stencil2<1><<<resident_grid(k_stencil2<1>, w, kThreads), kThreads, 0, s>>>(g, tab1, tab2, x, y1, y2),
+     dd::note_launch());
+  else
+    (k_stencil2<2><<<resident_grid(k_stencil2<2>, w, kThreads), kThreads, 0, s>>>(g, tab1, tab2, x, y1, y2),
+     dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 
 void launch_stencil_dot(dd_ctx* c, const double* tab, const double* x, double* y, double* out,
                         unsigned* counter, cudaStream_t s) {
   const Geo& g = c->g;
-  const int nb = grid_blocks(interior_work(g), kThreads);
-  if (g.p == 1) (k_stencil<1, true><<<nb, kThreads, 0, s>>>(g, tab, x, y, c->red, counter, out), dd::note_launch());
-  else (k_stencil<2, true><<<nb, kThreads, 0, s>>>(g, tab, x, y, c->red, counter, out), dd::note_launch());
+  const long long w = interior_work(g);
+  if (g.p == 1)
+    (k_stencil<1, true><<<resident_grid(k_stencil<1, true>, w, kThreads), kThreads, 0, s>>>(g, tab, x, y, c->red,
+                                                                                            counter, out),
+     dd::note_launch());
+  else
+    (k_stencil<2, true><<<resident_grid(k_stencil<2, true>, w, kThreads), kThreads, 0, s>>>(g, tab, x, y, c->red,
+                                                                                            counter, out),
+     dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 
@@ -650,12 +689,12 @@ constexpr int kProlongU = 1;
 
 void launch_prolong(dd_ctx* c, int mode, cudaStream_t s, double* zout) {
   const Geo& g = c->g;
-  const int nb = grid_blocks(interior_work(g), kThreads);
+  const long long work = interior_work(g);
   const int coarse = c->grid.coarse;
   const bool f32 = (c->grid.precision != DD_PREC_FP64);
   double* z = zout != nullptr ? zout : c->z;
 #define DD_PROLONG(PP, TY, YP, W, PU, U0, RS)                                                                   \
-  (k_prolong<PP, TY, RS, kProlongU><<<nb, kThreads, 0, s>>>(g, c->axown, c->subrow, YP, W, PU, U0, coarse, c->r, c->q, z, mode, \
+  (k_prolong<PP, TY, RS, kProlongU><<<resident_grid(k_prolong<PP, TY, RS, kProlongU>, work, kThreads), kThreads, 0, s>>>(g, c->axown, c->subrow, YP, W, PU, U0, coarse, c->r, c->q, z, mode, \
                                                  c->st, c->red, c->cnt + CNT_RZ),                                     \
    dd::note_launch())
 #define DD_PROLONG_T(PP, RS)                                                          \

@@ -54,3 +54,25 @@ def test_status_strings_without_gpu(libpath):
 def test_binding_signatures_cover_header():
     import paper_2311_08757_gb300 as dd
     assert set(declared_symbols()) <= set(dd._SIGS)
+
+
+@pytest.mark.parametrize("struct", ["dd_grid", "dd_info"])
+def test_binding_structs_match_the_header(struct, tmp_path):
+    """The ctypes structures of the binding have the header's size and field offsets (read
+    from a C program compiled against include/ddeig.h)."""
+    import shutil
+    import subprocess
+    import paper_2311_08757_gb300 as pkg
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not found")
+    cls = getattr(pkg, struct)
+    lines = [f'printf("%zu\\n", sizeof({struct}));']
+    lines += [f'printf("%zu\\n", offsetof({struct}, {name}));' for name, _ in cls._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"ddeig.h\"\nint main(void) {\n  "
+                   + "\n  ".join(lines) + "\n  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    want = [ctypes.sizeof(cls)] + [getattr(cls, name).offset for name, _ in cls._fields_]
+    assert got == want
