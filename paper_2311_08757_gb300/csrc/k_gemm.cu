@@ -471,8 +471,8 @@ __global__ void k_quantize_e4m3(const double* __restrict__ a, long long per_type
 
 // Three output-tile shapes, 128 x 256, 128 x 160 and 128 x 128: per output element the K
 // order of the accumulation is the same in all, so the choice changes the speed, not the
-// result.  128 x 160 fits cfg2's 2046 interior subdomains in 13 column tiles, so that its
-// 150 tiles make one wave on 152 SMs.
+// result.  128 x 160 fits the 2046 interior subdomains of the L = 2048, h = 1/32, delta = 4
+// box in 13 column tiles, so that its 150 tiles make one wave on 152 SMs.
 constexpr int kTileN[3] = {256, 128, 160};
 inline int tile_index(int bn) { return bn == 256 ? 0 : (bn == 128 ? 1 : 2); }
 struct GemmPlan {
@@ -645,8 +645,9 @@ int gemm_setup(dd_ctx* c) {
   return DD_OK;
 }
 
-// 128 threads (16 blocks of 31 registers per SM): all 2048 subdomain blocks of cfg2 are
-// resident at once instead of 1216 + 832 blocks of 256 (14.3 against 15.6 us)
+// 128 threads (16 blocks of 31 registers per SM): all 2048 subdomain blocks of the
+// L = 2048, h = 1/32 box are resident at once instead of 1216 + 832 blocks of 256 (14.3
+// against 15.6 us)
 constexpr int kPackThreads = 128;
 
 void launch_pack(dd_ctx* c, const double* r, double* c0, cudaStream_t s) {

@@ -560,7 +560,8 @@ __global__ void __launch_bounds__(kThreads) k_xr_update(long long n, double* pb0
 
 void launch_xr_update(dd_ctx* c, cudaStream_t s) {
   // the kernel takes 64 registers, so 4 blocks of 256 per SM are resident: one wave of
-  // 608 blocks (22.5 us at cfg2) instead of two of the default 1216 (25.5 us)
+  // 608 blocks (22.5 us on the 2.03M-unknown L = 2048 box) instead of two of the default
+  // 1216 (25.5 us)
   const long long n = c->g.plen;
   (k_xr_update<<<grid_blocks(n / 2, kThreads, 4), kThreads, 0, s>>>(n, c->pb[0], c->pb[1], c->q, c->x, c->r, c->st,
                                                                  c->red, c->cnt + CNT_RR), dd::note_launch());
@@ -585,9 +586,9 @@ __device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
 
 // Register budget: 32 per thread (8 blocks of 256 per SM) for p = 1, which fits it; 48
-// (5 blocks) for p = 2, whose four owners per node spilled at 32 (cfg3: 987 -> 971 ms per
-// ground state).  The FP64 p = 1 variant spills a little at 32 yet ran 4% faster there than
-// at 48 without spills.
+// (5 blocks) for p = 2, whose four owners per node spilled at 32 (on the L = 64, h = 1/16
+// three-dimensional box: 987 -> 971 ms per ground state).  The FP64 p = 1 variant spills a
+// little at 32 yet ran 4% faster there than at 48 without spills.
 template <int P, typename TY, bool RAS, int U>
 __global__ void __launch_bounds__(kThreads, (P == 1 ? 8 : 5) / U) k_prolong(Geo g, const int4* __restrict__ axown,
                                                       const int4* __restrict__ subrow, const TY* __restrict__ Y,
@@ -683,7 +684,7 @@ __global__ void __launch_bounds__(kThreads, (P == 1 ? 8 : 5) / U) k_prolong(Geo 
 }
 
 // nodes per thread and pass (each node's loads go out together, absent owners masked):
-// measured at cfg2, 24.7 / 31.5 / 42.4 us per launch for 1 / 2 / 4 (the register cost of
+// measured on the L = 2048, h = 1/32 box, 24.7 / 31.5 / 42.4 us per launch for 1 / 2 / 4 (the register cost of
 // more nodes takes away more resident warps than it adds loads in flight)
 constexpr int kProlongU = 1;
 
