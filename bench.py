@@ -115,6 +115,23 @@ def load_peaks() -> tuple[dict, str]:
     return dict(FALLBACK_PEAKS), "fallback"
 
 
+def max_over_ranks(value: float, device) -> float:
+    """The largest `value` over the ranks of the default process group (the value itself
+    without one): every rank's timed region must end before the job's does."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Units per second of the whole job: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 class ClockSampler:
     """nvidia-smi sampling (every 50 ms) of SM clocks and throttle reasons.  `start` returns
     once the first sample has arrived, so the sampler is running before the timed region
@@ -435,12 +452,8 @@ def main():
     clk = clocks.stop(t_wall0, t_wall1)
     lam, sigma, outer, inner_tot = res
     step_ms = sum(per) / len(per)
-    # max over ranks
-    if world > 1:
-        t = torch.tensor([step_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        step_ms = float(t.item())
-    value = world * 1e3 / step_ms
+    step_ms = max_over_ranks(step_ms, dev)
+    value = whole_job_rate(1.0, world, step_ms / 1e3)
 
     # plain FP64 method, same workload
     fp64_steps = args.fp64_steps if args.fp64_steps is not None else max(1, args.steps // 2)
@@ -650,11 +663,8 @@ def main():
         t0 = time.perf_counter()
         dd.dd_eigenpair(g, Vp, phi_out=phi)
         t_cold = time.perf_counter() - t0
-        if world > 1:
-            tt = torch.tensor([te], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            te = float(tt.item())
-        e2e = {"value": world / te, "unit": UNIT, "h2d_bytes_per_step": int(Vp.numel() * 8 + x0.numel() * 8),
+        te = max_over_ranks(te, dev)
+        e2e = {"value": whole_job_rate(1.0, world, te), "unit": UNIT, "h2d_bytes_per_step": int(Vp.numel() * 8 + x0.numel() * 8),
                "d2h_bytes_per_step": int(phi.numel() * 8), "ms_per_step": te * 1e3,
                "path": "dd_set_potential + dd_cell_eigenpair + dd_coarse_build + dd_inverse_iterate, host buffers",
                "lambda": lam_h,
