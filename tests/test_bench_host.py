@@ -1,5 +1,6 @@
 """Host logic of bench.py that needs no GPU: the clock sampler, driven by a stand-in
-`nvidia-smi` on PATH that prints rows in the query's CSV format."""
+`nvidia-smi` on PATH that prints rows in the query's CSV format, and the reference arm (the
+oracle on the host cores) on a small workload."""
 import importlib.util
 import os
 import stat
@@ -77,3 +78,36 @@ def test_sampler_without_nvidia_smi(tmp_path, monkeypatch):
     cs.start()
     out = cs.stop(0.0, 1.0)
     assert out["reasons"] == ["nvidia-smi unavailable"]
+
+
+def _run_reference(env_extra=None):
+    import json
+    import subprocess
+    env = dict(os.environ)
+    env.update(env_extra or {})
+    cmd = [sys.executable, str(ROOT / "bench.py"), "--impl", "reference", "--workload", "cfg2_small",
+           "--steps", "1", "--warmup", "3"]
+    p = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [ln for ln in p.stdout.splitlines() if ln.strip()]
+    return [json.loads(ln) for ln in lines]
+
+
+def test_reference_arm_line():
+    """The reference arm (the oracle on the host cores) prints one JSON line with the
+    contract's keys; its e2e moves no bytes between host and device."""
+    out = _run_reference()
+    assert len(out) == 1
+    d = out[0]
+    assert d["impl"] == "reference" and d["n_gpus"] == 1 and d["steps"] == 1 and d["warmup"] == 3
+    assert d["unit"] == "ground states/s" and d["higher_is_better"] is True and d["value"] > 0
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    e2e = d["e2e"]
+    assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+    assert d["config"]["workload"].startswith("cfg2_small")
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    assert _run_reference({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
