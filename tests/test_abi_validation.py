@@ -1,6 +1,6 @@
 """Argument checking at the C ABI, which needs no GPU: every entry point below rejects a bad
 argument with DD_EINVAL (and, for dd_setup, a message) before it touches the device, as
-include/ddeig.h states."""
+include/ddeig.h states.  A valid problem on a machine without a GPU fails with DD_ECUDA."""
 import ctypes
 import os
 
@@ -105,3 +105,19 @@ def test_self_test_entry_points_check_arguments_first():
     assert L.dd_tc_gemm_noalloc(dd.DD_PREC_BF16, 128, 128, 65, p, p, f, None) == dd.DD_EINVAL
     assert L.dd_tc_gemm_noalloc(dd.DD_PREC_BF16, 128, 128, 128, None, p, f, None) == dd.DD_EINVAL
     assert L.dd_tc_gemm_noalloc(dd.DD_PREC_BF16, 1 << 20, 1 << 20, 128, p, p, f, None) == dd.DD_EINVAL
+
+
+def test_no_cpu_fallback_without_a_gpu():
+    """A valid problem on a machine without a GPU fails with DD_ECUDA: the library has no
+    host path to fall back on."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from ddinputs import WORKLOADS, sample_cell_qp
+    w = WORKLOADS["cfg1"]
+    with pytest.raises(dd.DDError) as e:
+        dd.dd_setup(dd.grid_from_workload(w), sample_cell_qp(w))
+    assert e.value.code == dd.DD_ECUDA
+    with pytest.raises(dd.DDError) as e:
+        dd.dd_eigenpair(dd.grid_from_workload(w), sample_cell_qp(w))
+    assert e.value.code == dd.DD_ECUDA
