@@ -378,10 +378,12 @@ int dd_convert_test(int kind, long long n, const void* in_host, void* out_host);
  * Allocates nothing: the kernel's scratch (tile list, error word of its bounded waits) is a
  * fixed 64 KB array in the library's static device memory, present on every GPU that loads
  * the library until the process exits.  The first call on a device looks up that array's
- * device address (cudaGetSymbolAddress) and caches it; make that first call before any
- * stream capture.  All calls share the array and it keeps the last call's contents, so
- * calls that overlap on the GPU (concurrent streams, threads or graphs) race and must be
- * serialised by the caller.  DD_ETIMEOUT if a bounded device wait expired. */
+ * device address (cudaGetSymbolAddress) and caches it.  No call may be made while its
+ * stream is being captured into a CUDA graph: every call copies its tile list from host
+ * memory and synchronises the stream before it returns.  All calls share the array and it
+ * keeps the last call's contents, so calls that overlap on the GPU (concurrent streams or
+ * threads) race and must be serialised by the caller.  DD_ETIMEOUT if a bounded device
+ * wait expired. */
 int dd_tc_gemm_noalloc(int precision, int M, int N, int K, const void* A_dev, const void* B_dev, float* D_dev,
                        void* stream);
 

@@ -280,10 +280,21 @@ def dd_reset_timings(ctx) -> None:
     _check(lib().dd_reset_timings(ctx), ctx)
 
 
+def _require(cond: bool, msg: str) -> None:
+    if not cond:
+        raise ValueError(msg)
+
+
 def dd_tc_gemm_test(precision: int, A, B, D) -> int:
     """D[n][m] = sum_k A[m][k] B[n][k] (host float32 arrays) through the tensor-core kernel."""
+    import numpy as np
+    for name, a in (("A", A), ("B", B), ("D", D)):
+        _require(isinstance(a, np.ndarray) and a.dtype == np.float32 and a.ndim == 2 and a.flags["C_CONTIGUOUS"],
+                 f"{name} must be a C-contiguous 2-D float32 numpy array")
     M, K = A.shape
     N = B.shape[0]
+    _require(B.shape == (N, K), f"B must be N x K = {N} x {K}, got {B.shape}")
+    _require(D.shape == (N, M), f"D must be N x M = {N} x {M}, got {D.shape}")
     return _check(lib().dd_tc_gemm_test(precision, M, N, K, _ptr(A), _ptr(B), _ptr(D)))
 
 
@@ -301,9 +312,22 @@ def dd_tc_gemm_noalloc(precision: int, A_dev, B_dev, D_dev, stream=None) -> int:
     """Allocation-free tensor-core product D[n][m] = sum_k A[m][k] B[n][k] on device tensors
     (A: M x K, B: N x K, BF16 or FP32/TF32, K a multiple of 64; D: N x M float32).  For callers
     that must not allocate device memory; its scratch is fixed static device memory shared by
-    all calls, so overlapping calls race."""
+    all calls, so overlapping calls race.  Not to be called while its stream is being captured
+    into a CUDA graph: every call synchronises the stream and copies its tile list from host
+    memory.  Shapes, types and devices are checked here before the library is called."""
+    import torch
+    _require(precision in (DD_PREC_BF16, DD_PREC_TF32), "precision must be DD_PREC_BF16 or DD_PREC_TF32")
+    want = torch.bfloat16 if precision == DD_PREC_BF16 else torch.float32
+    for name, a, dt in (("A", A_dev, want), ("B", B_dev, want), ("D", D_dev, torch.float32)):
+        _require(isinstance(a, torch.Tensor) and a.dim() == 2 and a.is_contiguous(),
+                 f"{name} must be a contiguous 2-D torch tensor")
+        _require(a.dtype == dt, f"{name} must be {dt}, got {a.dtype}")
+        _require(a.is_cuda, f"{name} must be in device memory")
+        _require(a.device.index == torch.cuda.current_device(), f"{name} must be on the current device")
     M, K = A_dev.shape
     N = B_dev.shape[0]
+    _require(tuple(B_dev.shape) == (N, K), f"B must be N x K = {N} x {K}, got {tuple(B_dev.shape)}")
+    _require(tuple(D_dev.shape) == (N, M), f"D must be N x M = {N} x {M}, got {tuple(D_dev.shape)}")
     return _check(lib().dd_tc_gemm_noalloc(precision, M, N, K, _ptr(A_dev), _ptr(B_dev), _ptr(D_dev),
                                            _stream_ptr(stream)))
 

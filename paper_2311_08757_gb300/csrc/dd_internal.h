@@ -358,3 +358,27 @@ struct Error {
   Error(int c, std::string m) : code(c), msg(std::move(m)) {}
 };
 }  // namespace dd
+
+#include <atomic>
+
+namespace dd {
+// cudaFuncSetAttribute (dynamic shared-memory opt-in) applies to the current device only, so
+// a "set once" flag must remember every device ordinal it has been set on.  Ordinals up to 63
+// are remembered in one word; higher ordinals set the attribute on every call.
+struct PerDeviceOnce {
+  std::atomic<unsigned long long> done{0};
+};
+template <typename F>
+inline void once_per_device(PerDeviceOnce& o, F&& f) {
+  int dev = 0;
+  DD_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    f();
+    return;
+  }
+  const unsigned long long bit = 1ull << dev;
+  if (o.done.load(std::memory_order_acquire) & bit) return;
+  f();   // idempotent: two threads racing here both set the same attribute
+  o.done.fetch_or(bit, std::memory_order_release);
+}
+}  // namespace dd

@@ -302,12 +302,11 @@ static void factor_launch(T* CB, T* RB, T* inv, const int* nvec, int nmat, int n
     threads = std::min(threads, 1024);
 #define DD_FWIN(PPT_)                                                                                         \
   do {                                                                                                      \
-    static std::atomic<bool> attr{false};   /* once per process and instance (idempotent if threads race) */ \
-    if (!attr) {                                                                                            \
+    static dd::PerDeviceOnce attr;   /* once per device and instance */                                     \
+    dd::once_per_device(attr, [] {                                                                          \
       DD_CUDA(cudaFuncSetAttribute(k_band_factor_win<T, 4, PPT_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                    220 * 1024));                                                            \
-      attr = true;                                                                                          \
-    }                                                                                                       \
+    });                                                                                                     \
     (k_band_factor_win<T, 4, PPT_><<<nmat, threads, smem, s>>>(CB, inv, nvec, nmax, b, flag), dd::note_launch()); \
   } while (0)
     if (ppt == 4) DD_FWIN(4);
@@ -320,12 +319,11 @@ static void factor_launch(T* CB, T* RB, T* inv, const int* nvec, int nmat, int n
     T* Lp = nullptr;
     DD_CUDA(cudaMallocAsync(&Lp, sizeof(T) * (size_t)nmat * np * (b + 1), s));
     const size_t psm = sizeof(T) * (size_t)np * (b + 1);
-    static std::atomic<bool> attr{false};   // once per process and type (idempotent if threads race)
-    if (!attr) {
+    static PerDeviceOnce attr;   // once per device and type
+    once_per_device(attr, [] {
       DD_CUDA(cudaFuncSetAttribute(k_bpanel_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
       DD_CUDA(cudaFuncSetAttribute(k_bpanel_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-      attr = true;
-    }
+    });
     const dim3 ug((b + 31) / 32, nmat);
     for (int k0 = 0; k0 < nmax; k0 += np) {
       (k_bpanel_factor<T><<<nmat, 1024, psm, s>>>(CB, inv, Lp, nvec, nmax, b, np, k0, flag), dd::note_launch());
@@ -464,12 +462,11 @@ void launch_band_solve_local(dd_ctx* c, const double* r, double* c0, cudaStream_
     DD_K_DISPATCH(K, {
       constexpr int KK = (NV == 0 || NV > 4) ? 1 : KR;
       if (K > KK) throw Error(DD_EINVAL, "local right-hand sides per warp exceed the kernel's");
-      static std::atomic<bool> attr_set{false};
-      if (!attr_set) {
+      static PerDeviceOnce attr_set;   // once per device and instance
+      once_per_device(attr_set, [] {
         DD_CUDA(cudaFuncSetAttribute(k_local_solve<NV, PF, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      220 * 1024));
-        attr_set = true;
-      }
+      });
       (k_local_solve<NV, PF, KK><<<nb, wpb * 32, smem, s>>>(c->g, c->subs, c->groups, c->ngroups, c->sub_of_slot,
                                                            r, c->bandCB, c->bandRB, c->bandInv, c->nloc_max,
                                                            c->band, c->Y64, c->kpad, c->wT, c0, c->st),

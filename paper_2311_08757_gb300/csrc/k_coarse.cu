@@ -448,11 +448,10 @@ void launch_coarse_solve(dd_ctx* c, cudaStream_t s) {
     const int staged = full <= 200 * 1024 ? 1 : 0;
     const size_t smem = staged ? full : sizeof(double) * W2;
     if (smem > 220 * 1024) throw Error(DD_EINVAL, "coarse chain too long for the shared-memory cyclic reduction");
-    static std::atomic<bool> attr{false};   // set once per process (idempotent if two threads race)
-    if (!attr) {
+    static PerDeviceOnce attr;   // once per device
+    once_per_device(attr, [] {
       DD_CUDA(cudaFuncSetAttribute(k_cr_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-      attr = true;
-    }
+    });
     (k_cr_solve<<<1, kCrThreads, smem, s>>>(c->cr, g.nsub, c->cr_m, c->cr_c2, c->cr_w2, c->c0, c->u0, c->u0f, c->st,
                                              staged, c->dev_err + 8),
      dd::note_launch());

@@ -19,6 +19,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <new>
 #include <mutex>
 #include <string>
 
@@ -269,12 +270,11 @@ template <typename T, int BN = 256>
 static void launch_tc(const CUtensorMap* tA, const CUtensorMap* tB, const Tile* tiles, int ntiles, int K,
                       int mlimit, int rows_per_type, float* Y, int ldy, int* err, const PcgState* st,
                       cudaStream_t s, const float* ysc = nullptr) {
-  static std::atomic<bool> attr{false};   // set once per process (idempotent if two threads race)
-  if (!attr) {
+  static PerDeviceOnce attr;   // once per device and instance
+  once_per_device(attr, [] {
     DD_CUDA(cudaFuncSetAttribute(k_tc_gemm<T, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  TcCfg<T, BN>::SMEM));
-    attr = true;
-  }
+  });
   (k_tc_gemm<T, BN><<<ntiles, 128, TcCfg<T, BN>::SMEM, s>>>(*tA, *tB, tiles, K, mlimit, rows_per_type, Y, ldy, err,
                                                              st, ysc),
    dd::note_launch());
@@ -711,11 +711,17 @@ static uint8_t host_e4m3(float f) {
 
 }  // namespace dd
 
+namespace dd {
+constexpr int kTestMaxDim = 1 << 16;   // largest M, N or K accepted by dd_tc_gemm_test
+}
+
 extern "C" int dd_tc_gemm_test(int precision, int M, int N, int K, const float* A_host, const float* B_host,
                                float* D_host) {
   using namespace dd;
   if (precision != DD_PREC_BF16 && precision != DD_PREC_TF32 && precision != DD_PREC_FP8) return DD_EINVAL;
   if (M < 1 || N < 1 || K < 1 || !A_host || !B_host || !D_host) return DD_EINVAL;
+  // a self-test stages whole host copies of its operands: sizes stay far below int overflow
+  if (M > kTestMaxDim || N > kTestMaxDim || K > kTestMaxDim) return DD_EINVAL;
   const int es = precision == DD_PREC_BF16 ? 2 : (precision == DD_PREC_TF32 ? 4 : 1);
   const int kpad = (K + 127) / 128 * 128;
   const int mpad = (M + 127) / 128 * 128;
@@ -796,6 +802,8 @@ extern "C" int dd_tc_gemm_test(int precision, int M, int N, int K, const float* 
     if (herr) rc = DD_ETIMEOUT;
   } catch (const Error& e) {
     rc = e.code;
+  } catch (const std::bad_alloc&) {
+    rc = DD_ENOMEM;
   }
   if (dA) cudaFree(dA);
   if (dB) cudaFree(dB);
@@ -857,7 +865,8 @@ extern "C" int dd_tc_gemm_noalloc(int precision, int M, int N, int K, const void
   using namespace dd;
   if (precision != DD_PREC_BF16 && precision != DD_PREC_TF32) return DD_EINVAL;
   if (M < 1 || N < 1 || K < 64 || (K % 64) != 0 || !A_dev || !B_dev || !D_dev) return DD_EINVAL;
-  const long long ntiles = (long long)((M + 127) / 128) * ((N + 255) / 256);
+  // tile count in 64-bit arithmetic: M + 127 or N + 255 would overflow int near INT_MAX
+  const long long ntiles = (((long long)M + 127) / 128) * (((long long)N + 255) / 256);
   if (ntiles > kNoAllocMaxTiles) return DD_EINVAL;   // output larger than the fixed scratch allows
   void* scratch = nullptr;
   int rc = noalloc_scratch(&scratch);

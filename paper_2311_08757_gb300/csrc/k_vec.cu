@@ -464,11 +464,10 @@ void launch_fused_pq(dd_ctx* c, cudaStream_t s) {
   const int ntiles = (g.nxi + kFusedCols - 1) / kFusedCols;
   const int nb = ntiles < 152 * 6 ? ntiles : 152 * 6;
   const size_t smem = sizeof(double) * ((size_t)(kFusedCols + 2) * g.Ypad + 2);
-  static std::atomic<bool> attr{false};   // set once per process (idempotent if two threads race)
-  if (!attr) {
+  static PerDeviceOnce attr;   // once per device
+  once_per_device(attr, [] {
     DD_CUDA(cudaFuncSetAttribute(k_fused_pq, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr = true;
-  }
+  });
   (k_fused_pq<<<nb, kThreads, smem, s>>>(g, c->tabS, c->z, c->pb[0], c->pb[1], c->q, c->st, c->red,
                                          c->cnt + CNT_PQ), dd::note_launch());
   DD_CUDA(cudaGetLastError());

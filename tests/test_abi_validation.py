@@ -105,6 +105,34 @@ def test_self_test_entry_points_check_arguments_first():
     assert L.dd_tc_gemm_noalloc(dd.DD_PREC_BF16, 128, 128, 65, p, p, f, None) == dd.DD_EINVAL
     assert L.dd_tc_gemm_noalloc(dd.DD_PREC_BF16, 128, 128, 128, None, p, f, None) == dd.DD_EINVAL
     assert L.dd_tc_gemm_noalloc(dd.DD_PREC_BF16, 1 << 20, 1 << 20, 128, p, p, f, None) == dd.DD_EINVAL
+    # sizes near INT_MAX: the tile count must not wrap around to a small or negative number
+    imax = 2 ** 31 - 1
+    assert L.dd_tc_gemm_noalloc(dd.DD_PREC_BF16, imax, imax, 128, p, p, f, None) == dd.DD_EINVAL
+    assert L.dd_tc_gemm_noalloc(dd.DD_PREC_BF16, imax, 1, 128, p, p, f, None) == dd.DD_EINVAL
+    assert L.dd_tc_gemm_noalloc(dd.DD_PREC_TF32, 1, imax, 128, p, p, f, None) == dd.DD_EINVAL
+    assert L.dd_tc_gemm_test(dd.DD_PREC_BF16, imax, 8, 64, p, p, p) == dd.DD_EINVAL
+    assert L.dd_tc_gemm_test(dd.DD_PREC_BF16, 8, 8, imax, p, p, p) == dd.DD_EINVAL
+
+
+def test_gemm_wrappers_check_shapes_and_types_first():
+    """The binding's tensor-core wrappers reject mismatched operands before the library is
+    called: a wrong shape, type or device would make the kernel read or write out of bounds."""
+    import numpy as np
+    import torch
+    A = np.zeros((128, 64), np.float32)
+    with pytest.raises(ValueError):
+        dd.dd_tc_gemm_test(dd.DD_PREC_BF16, A, np.zeros((8, 32), np.float32), np.zeros((8, 128), np.float32))
+    with pytest.raises(ValueError):
+        dd.dd_tc_gemm_test(dd.DD_PREC_BF16, A, np.zeros((8, 64), np.float32), np.zeros((8, 64), np.float32))
+    with pytest.raises(ValueError):
+        dd.dd_tc_gemm_test(dd.DD_PREC_BF16, A, np.zeros((8, 64), np.float64), np.zeros((8, 128), np.float32))
+    At = torch.zeros(128, 64, dtype=torch.bfloat16)
+    Bt = torch.zeros(8, 64, dtype=torch.bfloat16)
+    Dt = torch.zeros(8, 128, dtype=torch.float32)
+    with pytest.raises(ValueError):          # host tensors: the entry point takes device memory
+        dd.dd_tc_gemm_noalloc(dd.DD_PREC_BF16, At, Bt, Dt)
+    with pytest.raises(ValueError):          # precision without an allocation-free form
+        dd.dd_tc_gemm_noalloc(dd.DD_PREC_FP8, At, Bt, Dt)
 
 
 def test_no_cpu_fallback_without_a_gpu():

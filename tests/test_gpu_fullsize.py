@@ -81,7 +81,7 @@ def test_fullsize_ground_state(oracle, gpu):
     xh = host(x)
     Mx = P.M @ xh
     eta = np.linalg.norm(P.A @ xh - lam * Mx) / (abs(lam) * np.linalg.norm(Mx))
-    assert eta <= 1.5e-8
+    assert eta <= 1e-8 + 1e-12   # the stop rule's 1e-8, plus the rounding of recomputing eta
     assert xh @ Mx == pytest.approx(1.0, rel=1e-12)
 
 

@@ -196,7 +196,7 @@ def test_fullsize3d_ground_state():
     assert abs(lam64 - lam16) <= 1e-10 * abs(lam64)
     for prec in ("fp64", "bf16"):
         lam, outer, mx, eta, xMx, sigma = out[prec]
-        assert eta <= 1.5e-8
+        assert eta <= 1e-8 + 1e-12   # the stop rule's 1e-8, plus the rounding of recomputing eta
         assert xMx == pytest.approx(1.0, rel=1e-12)
         assert sigma < lam < sigma + 1.0
         assert mx <= 1.25 * out[prec + "_l16"]

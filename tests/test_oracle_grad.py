@@ -86,8 +86,8 @@ def _solve_theta(w, theta):
 
 def test_gradients_match_central_differences():
     """d lambda / d theta and d l / d theta for l = ||phi - phi_target||_M^2 (the
-    differentiable workload's loss) against central differences, step 1e-4, of exact dense
-    eigen-solves."""
+    differentiable workload's loss) against Richardson-extrapolated central differences
+    (steps 2e-4 and 1e-4) of exact dense eigen-solves, to 1e-6 relative (gradient-vector norm)."""
     w = Workload("t", p=1, L=3, n=8, overlap=2, kind="theta8", seed=5)
     th, tt = theta_seed(5)
     Bq = theta8_qp_basis(w)
@@ -102,11 +102,17 @@ def test_gradients_match_central_differences():
         e = ph - phi_t
         return lm, float(e @ (Mm @ e))
 
-    eps = 1e-4
-    for j in range(8):
+    def central(j, eps):
         tp, tm = th.copy(), th.copy()
         tp[j] += eps
         tm[j] -= eps
         (lp, fp), (lm_, fm) = loss(tp), loss(tm)
-        assert (lp - lm_) / (2 * eps) == pytest.approx(dlam[j], rel=1e-6, abs=1e-9)
-        assert (fp - fm) / (2 * eps) == pytest.approx(dl[j], rel=1e-5, abs=1e-9 * max(1.0, np.abs(dl).max()))
+        return (lp - lm_) / (2 * eps), (fp - fm) / (2 * eps)
+
+    # Richardson extrapolation of two central differences (steps 2e-4 and 1e-4) cancels the
+    # O(eps^2) truncation term, leaving O(eps^4) plus rounding noise of ~1e-16 / 1e-4.  The
+    # agreement is measured on the gradient vector, max_j |fd_j - g_j| / max_j |g_j|: a
+    # component near zero carries only that noise, which no step can remove
+    fd = np.array([[(4 * a1 - a2) / 3 for a1, a2 in zip(central(j, 1e-4), central(j, 2e-4))] for j in range(8)])
+    assert np.abs(fd[:, 0] - dlam).max() <= 1e-6 * np.abs(dlam).max()
+    assert np.abs(fd[:, 1] - dl).max() <= 1e-6 * np.abs(dl).max()

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 import scipy.linalg as sla
 
-from ddinputs import Workload, potential
+from ddinputs import WORKLOADS, Workload, potential
 from oracle import q1, solvers
 from oracle.dd import Decomposition, TwoLevelAS
 
@@ -237,6 +237,124 @@ def test_subdomains_are_open_overlapping_boxes():
         assert (x > lo).all() and (x < hi).all()
         allx = np.arange(1, g.L * g.n) * g.h
         assert len(a) == ((allx > lo + 1e-12) & (allx < hi - 1e-12)).sum()
+
+
+def _weights_by_node(dec, nyi):
+    """{subdomain: {node column: weight}} from the decomposition's D_i, checking that every
+    y node of a column carries the same weight (the partition of unity is a function of the
+    expanding coordinates only)."""
+    out = []
+    for ids, w in zip(dec.idx, dec.weights):
+        col = {}
+        for k, c in enumerate(ids // nyi):
+            if c in col:
+                assert w[k] == col[c]
+            col[c] = w[k]
+        out.append(col)
+    return out
+
+
+def test_distance_pu_p1_linear_ramp():
+    """Distance partition of unity (Sec. 4.1.2), p = 1: across the overlap zone of the
+    interface x = t the weights of the two neighbouring subdomains fall and rise linearly,
+    chi = d_i / (d_i + d_j) with d measured to the artificial faces x = t -/+ delta h only
+    (faces on the box boundary, the ends and y = 0, ell, do not count).  delta = 3: the
+    left subdomain's weight at x = t + k h, k = -2..2, is 5/6, 2/3, 1/2, 1/3, 1/6; every
+    node outside an overlap zone belongs to one subdomain with weight 1."""
+    L, n, delta = 4, 8, 3
+    g = grid(1, L, n, 4, delta=delta)
+    dec = Decomposition(g, "distance")
+    W = _weights_by_node(dec, g.ny - 1)
+    left = {-2: 5 / 6, -1: 2 / 3, 0: 1 / 2, 1: 1 / 3, 2: 1 / 6}
+    for t in range(1, L):
+        for k, wl in left.items():
+            col = t * n + k - 1          # 0-based interior column of node a = t n + k
+            assert W[t - 1][col] == pytest.approx(wl, abs=1e-14)
+            assert W[t][col] == pytest.approx(1.0 - wl, abs=1e-14)
+    for i in range(L):
+        for col, wv in W[i].items():
+            a = col + 1
+            if all(abs(a - t * n) >= delta for t in range(1, L)):
+                assert wv == 1.0
+
+
+def test_distance_pu_p2_corner_zone_and_physical_boundary():
+    """Distance partition of unity (Sec. 4.1.2), p = 2, delta = 3, h = 1/8.  d_i is the
+    distance to the artificial part of the subdomain's boundary (the faces not on the box
+    boundary), so near the interior vertex (1, 1) four subdomains share a node with weights
+    fixed by the distances to their inner faces (worked by hand below), while along the
+    overlap zone of x_1 = 1 next to the box face x_2 = 0 the two covering subdomains keep
+    the 1-D ramp: the physical face x_2 = 0 is not a face to measure to, and the subdomains
+    are clipped at the box (no face at x_2 = -delta h either)."""
+    L, n, delta = 3, 8, 3
+    g = grid(2, L, n, 3, delta=delta)
+    dec = Decomposition(g, "distance")
+    nx, nyi = g.nx, g.ny - 1
+    W = _weights_by_node(dec, nyi)
+    sub = {(i1, i2): i1 * L + i2 for i1 in range(L) for i2 in range(L)}
+    # node (8 + u, 8 + v): weights of subdomains (0,0), (1,0), (0,1), (1,1)
+    corner = {(0, 0): (1 / 4, 1 / 4, 1 / 4, 1 / 4),
+              (-1, 0): (3 / 10, 1 / 5, 3 / 10, 1 / 5),
+              (-2, -2): (5 / 8, 1 / 8, 1 / 8, 1 / 8),
+              (2, -1): (1 / 8, 1 / 2, 1 / 8, 1 / 4),
+              (-1, 2): (1 / 8, 1 / 8, 1 / 2, 1 / 4)}
+    for (u, v), ws in corner.items():
+        col = (n + u - 1) * nx + (n + v - 1)
+        for key, wv in zip(((0, 0), (1, 0), (0, 1), (1, 1)), ws):
+            assert W[sub[key]][col] == pytest.approx(wv, abs=1e-14)
+    # next to the face x_2 = 0 (a_2 = 1): the ramp of the x_1 = 1 overlap zone
+    for u, wl in {-2: 5 / 6, -1: 2 / 3, 0: 1 / 2, 1: 1 / 3, 2: 1 / 6}.items():
+        col = (n + u - 1) * nx + 0
+        assert W[sub[(0, 0)]][col] == pytest.approx(wl, abs=1e-14)
+        assert W[sub[(1, 0)]][col] == pytest.approx(1.0 - wl, abs=1e-14)
+
+
+@pytest.mark.parametrize("pu", ["equal", "distance"])
+@pytest.mark.parametrize("p", [1, 2])
+def test_coarse_basis_sums_to_periodic_cell_function(p, pu):
+    """Definition 2.1 with the partition of unity of Sec. 2.2: the columns D_i R_i psi of
+    R_0^T extended by zero add up to the periodic extension E^# psi itself
+    (sum_i R_i^T D_i R_i = I), and A_sigma annihilates that sum on every row whose stencil
+    stays away from the x-ends of the box (those rows are translated rows of the periodic
+    cell problem whose eigenpair is (sigma, psi))."""
+    if p == 1:
+        w = Workload("t", p=1, L=5, n=8, overlap=2, kind="cos1")
+    else:
+        w = Workload("t", p=2, L=3, n=6, overlap=2, kind="asym3")
+    g = q1.Grid.from_workload(w)
+    P = solvers.Problem(g, potential(w), pu=pu, build_prec=False)
+    Z = P.dec.coarse_basis(P.psi)
+    assert Z.shape == (g.ndof, g.L ** g.p)
+    s = Z @ np.ones(Z.shape[1])
+    assert np.abs(s - P.psi).max() <= 1e-14 * np.abs(P.psi).max()
+    res = P.Asig @ s
+    nyi = g.ny - 1
+    if p == 1:
+        inner = res.reshape(g.nx, nyi)[1:-1]
+    else:
+        inner = res.reshape(g.nx, g.nx, nyi)[1:-1, 1:-1]
+    assert np.abs(inner).max() <= 1e-10 * P.sigma * np.abs(P.psi).max()
+    assert np.abs(res).max() > 1e-6 * P.sigma * np.abs(P.psi).max()   # the x-end rows do not vanish
+
+
+def test_cfg1_independent_probe_values():
+    """The smallest workload (p = 1, L = 8, h = 1/16, V = 10(1 + cos 2 pi x)(1 + sin(pi y)/2)):
+    the oracle's cell shift sigma and exact ground state lambda_1, lambda_2 against an
+    independent dense generalised eigensolve recorded in tests/golden/cfg1_probe.json
+    (12 digits), and the same for V = 0."""
+    with open(os.path.join(GOLDEN, "cfg1_probe.json")) as f:
+        ref = json.load(f)
+    w = WORKLOADS["cfg1"]
+    g = q1.Grid.from_workload(w)
+    for V, r in ((potential(w), ref), (zeroV(1), ref["v0"])):
+        P = solvers.Problem(g, V, build_prec=False)
+        assert P.sigma == pytest.approx(r["sigma"], rel=1e-11, abs=0)
+        lam, _ = solvers.exact_ground_state(P.A, P.M)
+        assert lam == pytest.approx(r["lambda1"], rel=1e-11, abs=0)
+    import scipy.linalg as sla2
+    P = solvers.Problem(g, potential(w), build_prec=False)
+    ev = sla2.eigh(P.A.toarray(), P.M.toarray(), eigvals_only=True, subset_by_index=[0, 1])
+    assert ev[1] == pytest.approx(ref["lambda2"], rel=1e-11, abs=0)
 
 
 @pytest.mark.parametrize("coarse", [False, True])
