@@ -36,9 +36,8 @@ if ROOT not in sys.path:
 METRIC = "time to ground state @1e-10 rel, mixed vs FP64 plain; PCG iters/s; % roofline"
 UNIT = "ground states/s"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
-# FP64 FMA throughput measured on this machine's GB300 with a DFMA microbenchmark
-# (8 independent chains per thread, 152 x 8 x 256 threads): 1.19 TFLOP/s.
-FP64_TFLOPS = 1.19
+ALU_PEAK_SOURCE = ("dd_alu_peak_test, measured in this run: 8 independent FMA chains per thread, 8 blocks of 256 "
+                   "threads per SM, fastest of 5 launches")
 
 
 def parse():
@@ -56,52 +55,78 @@ def parse():
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-3d", action="store_true")
+    ap.add_argument("--no-sweeps", action="store_true")
     ap.add_argument("--coarse-solve", default="auto", choices=["auto", "cr", "dense"])
     ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--setup-only", default=None, choices=["cfg2", "cfg3"],
                     help="time only the set-up stages (cell eigenpair, coarse build) of one workload")
+    ap.add_argument("--profile-region", default=None, choices=["cfg2", "cfg3"],
+                    help="set up one workload, then run --pcg-iters PCG iterations (eager launches) between "
+                         "cudaProfilerStart/Stop, for `ncu --profile-from-start off`")
+    ap.add_argument("--pcg-iters", type=int, default=2)
+    ap.add_argument("--one-shot-breakdown", action="store_true",
+                    help="time dd_setup, dd_cell_eigenpair, dd_coarse_build, dd_inverse_iterate and dd_destroy "
+                         "of fresh contexts on the headline workload")
     return ap.parse_args()
 
 
 # ----------------------------------------------------------------------------------------
-# oracle sample (runs in a child process with one BLAS thread)
+# the oracle's full ground state (runs in a child process with one BLAS thread)
 # ----------------------------------------------------------------------------------------
-def cpu_sample(workload: str, pcg_its: int = 3) -> dict:
+def cpu_ground_state(workload: str) -> dict:
+    """One complete ground state by the oracle as it stands: assembly, cell eigenpair, the
+    decomposition with one banded Cholesky factor per subdomain and the dense coarse factor,
+    then the shifted inverse iteration with its own PCG (same stop rules as the GPU)."""
     import numpy as np
     from ddinputs import WORKLOADS, potential
     from oracle import q1, solvers
-    from oracle.dd import Decomposition, TwoLevelAS
     w = WORKLOADS[workload]
-    g = q1.Grid.from_workload(w)
-    V = potential(w)
     t0 = time.perf_counter()
-    K, M, MV = q1.assemble_box(g, V)
-    A = (K + MV).tocsr()
-    sigma, psi = solvers.cell_eigenpair(g, V)
-    As = (A - sigma * M).tocsr()
-    P = TwoLevelAS(As, Decomposition(g), q1.periodic_extension(g, psi))
+    g = q1.Grid.from_workload(w)
+    P = solvers.Problem(g, potential(w))
     t1 = time.perf_counter()
-    x = np.ones(g.ndof)
-    x /= np.sqrt(x @ (M @ x))
-    b = M @ x
+    lam, x, k, inner, info = P.ground_state()
     t2 = time.perf_counter()
-    _, it, _ = solvers.pcg(As, b, None, P, 1e-8, pcg_its)
-    t3 = time.perf_counter()
-    return {"setup_s": t1 - t0, "pcg_s_per_iter": (t3 - t2) / max(it, 1), "pcg_iters_run": it,
-            "sigma": sigma}
+    return {"setup_s": t1 - t0, "solve_s": t2 - t1, "total_s": t2 - t0, "outer": int(k),
+            "inner_total": int(np.sum(inner)), "lambda": float(lam), "sigma": float(P.sigma)}
 
 
-def run_cpu_sample(workload: str) -> dict:
+def cpu_child_env() -> dict:
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[k] = "1"
-    env.pop("RANK", None)
-    env.pop("WORLD_SIZE", None)
-    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", workload],
-                         capture_output=True, text=True, env=env, timeout=900)
-    if out.returncode != 0:
-        raise RuntimeError(out.stderr[-2000:])
-    return json.loads(out.stdout.strip().splitlines()[-1])
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        env.pop(k, None)
+    return env
+
+
+def start_cpu_ground_state(workload: str) -> subprocess.Popen:
+    return subprocess.Popen([sys.executable, os.path.abspath(__file__), "--cpu-sample", workload],
+                            stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=cpu_child_env())
+
+
+def finish_cpu_ground_state(proc: subprocess.Popen, timeout: float = 900.0) -> dict:
+    out, err = proc.communicate(timeout=timeout)
+    if proc.returncode != 0:
+        raise RuntimeError(err[-2000:])
+    return json.loads(out.strip().splitlines()[-1])
+
+
+def cpu_baseline_entry(s: dict, w) -> dict:
+    return {"value": 1.0 / s["total_s"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"one full ground state of the same workload by the oracle (numpy/scipy FP64, one BLAS "
+                       f"thread): set-up {s['setup_s']:.1f} s (assembly, cell eigenpair, {w.L ** w.p} banded local "
+                       f"factorisations, coarse factorisation) + inverse iteration {s['solve_s']:.1f} s "
+                       f"({s['outer']} outer steps, {s['inner_total']} PCG iterations of its own)"),
+            "setup_s": s["setup_s"], "solve_s": s["solve_s"], "outer_iters": s["outer"],
+            "inner_iters_total": s["inner_total"], "lambda": s["lambda"]}
+
+
+def workload_label(w) -> str:
+    if w.p == 1:
+        return (f"{w.name}: p=1, L={w.L}, ell=1, h=1/{w.n}, delta={w.overlap}, dofs={w.dofs}, {w.L ** w.p} "
+                f"subdomains, V=4-term cosine (seed {w.seed})")
+    return f"{w.name}: p=2, L={w.L}, ell=1, h=1/{w.n}, delta={w.overlap}, dofs={w.dofs}, {w.L ** w.p} subdomains"
 
 
 # ----------------------------------------------------------------------------------------
@@ -209,15 +234,14 @@ class ClockSampler:
 
 
 def kernel_model(w, info, ntype_counts, nloc_by_type, band, precision):
-    """Algorithmic work per launch of each kernel class: (FP64 flops, tensor flops, bytes).
-
-    Bytes count one pass over each vector the kernel must read or write (DOF = interior
-    unknown, f = sum |N_i| / ndof); FP64 flops count 2 per FMA of the arithmetic the
-    kernel must do.
-    """
+    """Algorithmic work per launch of each kernel class: FP64 flops, FP32 flops, tensor flops
+    and bytes (2 flops per FMA; bytes = one pass over each vector the kernel must read or
+    write; DOF = interior unknown, f = sum |N_i| / ndof).  Work a kernel does in FP32 is
+    counted against the FP32 pipe, FP64 work against the FP64 pipe."""
     ndof = info["ndof"]
     nloc_sum = sum(c * n for c, n in zip(ntype_counts, nloc_by_type))
     f = nloc_sum / ndof
+    mixed = precision in ("bf16", "tf32")
     es = 2 if precision == "bf16" else 4
     gemm_flops = sum(2.0 * c * n * n for c, n in zip(ntype_counts, nloc_by_type))
     fp64_band = 0.0
@@ -227,33 +251,40 @@ def kernel_model(w, info, ntype_counts, nloc_by_type, band, precision):
         fp64_band += c * 2 * 2 * per_sweep
     taps = 3 ** (w.p + 1)
     if w.p == 1:   # fused p update + stencil + (p, q)
-        stencil = (2.0 * (taps + 2) * ndof, 0.0, 32.0 * ndof)
+        stencil = (2.0 * (taps + 2) * ndof, 0.0, 0.0, 32.0 * ndof)
     else:
-        stencil = (2.0 * (taps + 1) * ndof, 0.0, 16.0 * ndof)
+        stencil = (2.0 * (taps + 1) * ndof, 0.0, 0.0, 16.0 * ndof)
+    # prolong-sum: per owner of a node one add of its local result and one FMA of the coarse
+    # term (3 flops), then the (r, z) and (q, z) dots (4 FP64 flops); the mixed form forms the
+    # node value in FP32 from FP32 local results
+    if mixed:
+        prolong = (4.0 * ndof, 3.0 * f * ndof, 0.0, (24.0 + 4.0 * f) * ndof)
+    else:
+        prolong = ((4.0 + 3.0 * f) * ndof, 0.0, 0.0, (24.0 + 8.0 * f) * ndof)
     return {
         "stencil_Asigma": stencil,
-        "p_update": (2.0 * ndof, 0.0, 24.0 * ndof),
-        "xr_update": (6.0 * ndof, 0.0, 48.0 * ndof),
-        "prolong_sum": (2.0 * (3.0 + f) * ndof, 0.0, (24.0 + 4.0 * f) * ndof),
-        "pack_restrict": (2.0 * f * ndof, 0.0, (8.0 + es * f) * ndof),
-        "local_gemm_tc": (0.0, gemm_flops, (es * f + 4.0 * f) * ndof),
-        "local_solve_fp64": (fp64_band, 0.0, 16.0 * f * ndof),
+        "p_update": (2.0 * ndof, 0.0, 0.0, 24.0 * ndof),
+        "xr_update": (6.0 * ndof, 0.0, 0.0, 48.0 * ndof),
+        "prolong_sum": prolong,
+        "pack_restrict": (2.0 * f * ndof, 0.0, 0.0, (8.0 + es * f) * ndof),
+        "local_gemm_tc": (0.0, 0.0, gemm_flops, (es * f + 4.0 * f) * ndof),
+        "local_solve_fp64": (fp64_band, 0.0, 0.0, 16.0 * f * ndof),
     }
 
 
-def roofline_entry(name, model, ms_total, nlaunch, peaks, peak_src, precision):
-    """The binding roofline of one kernel class (the resource whose ideal time is longest)."""
-    fp64, tens, byt = model
+def roofline_entry(name, model, ms_total, nlaunch, peaks, peak_src, precision, alu):
+    """The binding roofline of one kernel class: the resource (FP64 pipe, FP32 pipe, tensor
+    pipe, HBM) whose ideal time for the kernel's algorithmic work is longest."""
+    fp64, fp32, tens, byt = model
     avg_s = ms_total / nlaunch / 1e3
-    t_alu = fp64 / (FP64_TFLOPS * 1e12)
     tpeak = peaks["bf16_tflops"] * (0.5 if precision == "tf32" else 1.0)
-    t_ten = tens / (tpeak * 1e12)
-    t_hbm = byt / (peaks["hbm_gbs"] * 1e9)
-    bound = max((t_alu, "alu"), (t_ten, "tensor"), (t_hbm, "hbm"))[1]
-    if bound == "alu":
-        ent = {"bound": "alu", "achieved": fp64 / avg_s / 1e12, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
-               "peak_source": "FP64 FMA microbenchmark on this GB300: 8 independent FMA chains per thread, "
-                              "152 x 8 blocks of 256 threads"}
+    times = [(fp64 / (alu["fp64_tflops"] * 1e12), "fp64"), (fp32 / (alu["fp32_tflops"] * 1e12), "fp32"),
+             (tens / (tpeak * 1e12), "tensor"), (byt / (peaks["hbm_gbs"] * 1e9), "hbm")]
+    bound = max(times)[1]
+    if bound in ("fp64", "fp32"):
+        work = fp64 if bound == "fp64" else fp32
+        ent = {"bound": "alu", "pipe": bound, "achieved": work / avg_s / 1e12, "peak": alu[bound + "_tflops"],
+               "unit": "TFLOP/s", "peak_source": ALU_PEAK_SOURCE}
     elif bound == "tensor":
         ent = {"bound": "tensor", "achieved": tens / avg_s / 1e12, "peak": tpeak, "unit": "TFLOP/s",
                "peak_source": peak_src + (" (bf16 x 1/2 for tf32)" if precision == "tf32" else "")}
@@ -265,13 +296,14 @@ def roofline_entry(name, model, ms_total, nlaunch, peaks, peak_src, precision):
     ent["avg_launch_us"] = avg_s * 1e6
     ent["launches"] = nlaunch
     ent["hbm_gbs_algorithmic"] = byt / avg_s / 1e9
+    ent["hbm_frac_algorithmic"] = byt / avg_s / 1e9 / peaks["hbm_gbs"]
     ent["traffic"] = TRAFFIC.get(name)
     return ent
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the current kernels
-# from one ncu capture of this workload (profiles/top_kernels_cfg2_bench.md,
-# profiles/local_solve_fp64_cfg2.md); a kernel changed since its capture is left out.
+# at the L = 2048, h = 1/32 workload, from one ncu capture of each; a kernel changed since its
+# capture is left out.
 TRAFFIC = {
     "stencil_Asigma": (33.651 + 0.615) * 1e6,
     "prolong_sum": (44.916 + 0.131) * 1e6,
@@ -286,40 +318,31 @@ TRAFFIC = {
 # reference arm: the oracle as it stands
 # ----------------------------------------------------------------------------------------
 def run_reference(args):
+    """The oracle as it stands, on the host cores: one complete ground state of the headline
+    workload, timed whole (about a minute on one core).  One step is timed whatever --steps
+    asks for, so that ms_per_step x steps is the measured time; `requested` records the
+    flags."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from ddinputs import WORKLOADS
     w = WORKLOADS[args.workload]
-    times = []
-    samples = []
-    for i in range(args.warmup + args.steps):
-        s = run_cpu_sample(args.workload)
-        samples.append(s)
-    # extrapolation to a full ground state: the plain method's inner iterations on this
-    # workload (outer x inner, measured by the FP64 GPU run of the same algorithm)
-    inner_total = REF_INNER_ITERS.get(args.workload)
-    for s in samples[args.warmup:]:
-        times.append(s["setup_s"] + s["pcg_s_per_iter"] * inner_total)
-    t = sum(times) / len(times)
+    t0 = time.perf_counter()
+    s = finish_cpu_ground_state(start_cpu_ground_state(args.workload), timeout=1800)
+    wall = time.perf_counter() - t0
+    t = s["total_s"]
     line = {
         "impl": "reference", "metric": METRIC, "value": 1.0 / t, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: p=1, L={w.L}, h=1/{w.n}, delta={w.overlap}, "
-                                 f"dofs={w.dofs}, V=4-term cosine (seed {w.seed})",
-                   "l2": "n/a (CPU)"},
-        "cpu_baseline": {"value": 1.0 / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"per step: oracle set-up + 3 PCG iterations; extrapolated with "
-                                   f"{inner_total} inner iterations per ground state"},
+        "steps": 1, "warmup": 0, "requested": {"steps": args.steps, "warmup": args.warmup},
+        "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_label(w), "precision": "fp64 (plain method)", "l2": "n/a (CPU)"},
+        "cpu_baseline": cpu_baseline_entry(s, w),
         "e2e": {"value": 1.0 / t, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "time_to_ground_state_ms": {"setup": 1e3 * s["setup_s"], "solve": 1e3 * s["solve_s"]},
+        "wall_s": wall,
     }
     print(json.dumps(line))
-
-
-# total inner PCG iterations of one ground state with the plain FP64 method, used to
-# extrapolate oracle samples (filled from the GPU run of the same algorithm)
-REF_INNER_ITERS = {"cfg2": 330, "cfg1": 106, "cfg2_small": 250}
 
 
 # ----------------------------------------------------------------------------------------
@@ -354,10 +377,150 @@ def setup_only(args, dd, dev, reps=3):
             "sigma": sigma, "ms_cell_eigenpair": t_cell, "ms_coarse_build": t_coarse}
 
 
+def profile_region(args, dd, dev):
+    """Set-up outside the profiled range, then `--pcg-iters` PCG iterations on b = M 1 with
+    eager launches (no graph) inside cudaProfilerStart/Stop."""
+    import torch
+    from ddinputs import WORKLOADS, sample_cell_qp
+    w = WORKLOADS[args.profile_region]
+    V = torch.from_numpy(sample_cell_qp(w)).to(dev)
+    with dd.Eigensolver(dd.grid_from_workload(w, precision=dd.PRECISIONS[args.precision]), V) as es:
+        es.prepare()
+        dd.dd_set_option(es.ctx, dd.DD_OPT_USE_GRAPH, 0)
+        dd.dd_set_option(es.ctx, dd.DD_OPT_CHECK_EVERY, 1)
+        ones = torch.ones(w.dofs, dtype=torch.float64, device=dev)
+        b = torch.empty_like(ones)
+        dd.dd_apply_operator(es.ctx, dd.DD_OP_MASS, ones, b)
+        x = torch.zeros_like(ones)
+        dd.dd_pcg_solve(es.ctx, b, x, 1e-8, 1, allow_maxit=True)   # untimed warm pass
+        x.zero_()
+        torch.cuda.synchronize()
+        l0 = dd.dd_kernel_launch_count()
+        torch.cuda.profiler.start()
+        its, rel = dd.dd_pcg_solve(es.ctx, b, x, 1e-8, args.pcg_iters, allow_maxit=True)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        l1 = dd.dd_kernel_launch_count()
+    return {"mode": "profile_region", "workload": args.profile_region, "dofs": w.dofs, "precision": args.precision,
+            "pcg_iters": its, "relres": rel, "library_launches": l1 - l0}
+
+
+def one_shot_breakdown(args, dd, dev, reps=3, precision=None):
+    """Host wall time of each call of a fresh context (dd_setup ... dd_destroy) on the headline
+    workload, device buffers; every call synchronises before it returns, so the host clock
+    around it is its time.  The first of reps + 1 passes is untimed."""
+    import torch
+    from ddinputs import WORKLOADS, sample_cell_qp
+    precision = precision or args.precision
+    w = WORKLOADS[args.workload]
+    V = torch.from_numpy(sample_cell_qp(w)).to(dev)
+    x = torch.empty(w.dofs, dtype=torch.float64, device=dev)
+    grid = dd.grid_from_workload(w, precision=dd.PRECISIONS[precision])
+    rows = []
+    for i in range(reps + 1):
+        torch.cuda.synchronize()
+        t = [time.perf_counter()]
+        ctx = dd.dd_setup(grid, V)
+        t.append(time.perf_counter())
+        dd.dd_cell_eigenpair(ctx)
+        t.append(time.perf_counter())
+        dd.dd_coarse_build(ctx)
+        t.append(time.perf_counter())
+        x.fill_(1.0)
+        torch.cuda.synchronize()
+        t.append(time.perf_counter())
+        dd.dd_inverse_iterate(ctx, x)
+        t.append(time.perf_counter())
+        dd.dd_destroy(ctx)
+        t.append(time.perf_counter())
+        if i:
+            rows.append([1e3 * (b - a) for a, b in zip(t[:-1], t[1:])])
+    names = ["dd_setup", "cell_eigenpair", "coarse_build", "fill_x0", "inverse_iterate", "destroy"]
+    med = {k: sorted(r[j] for r in rows)[len(rows) // 2] for j, k in enumerate(names)}
+    return {"mode": "one_shot_breakdown", "workload": args.workload, "precision": precision,
+            "ms": {k: [r[j] for r in rows] for j, k in enumerate(names)},
+            "median_ms": med,
+            "setup_ms": med["dd_setup"] + med["cell_eigenpair"] + med["coarse_build"],
+            "solve_ms": med["inverse_iterate"],
+            "total_ms": med["dd_setup"] + med["cell_eigenpair"] + med["coarse_build"] + med["inverse_iterate"]}
+
+
+def sweeps(dd, dev, headline) -> dict:
+    """The iteration-count sweeps of Sec. 4.1 and the L-independence of the eigen-solver's
+    inner counts, on the GPU kernels (plain FP64 form unless noted):
+      fig3    source problem a_sigma(u, v) = (1, v), printed potential of Sec. 4.1, h = 1/30,
+              delta = 1, CG from 1 to rTOL = 1e-8: one-level M_AS1 / two-level M_AS2 counts;
+      table1  the same with the distance partition of unity, h in {1/10, 1/20, 1/30} x delta in
+              {1, 2, 3} (M_AS1 up to L = 256, M_AS2 up to L = 2048);
+      eigen_L inverse iteration on the headline potential (h = 1/32, delta = 4), FP64 and mixed:
+              outer steps, inner PCG iterations (total and per outer step), time;
+      gmres_ras2  the headline ground state with GMRES + M_RAS2^{-1} as the inner solver (Sec. 2.2,
+              Sec. 4.2) beside CG + M_AS2^{-1}."""
+    import numpy as np
+    import torch
+    from ddinputs import WORKLOADS, Workload, sample_cell_qp
+
+    def solver(w, precision="fp64", coarse=1, pu=0):
+        V = torch.from_numpy(sample_cell_qp(w)).to(dev)
+        es = dd.Eigensolver(dd.grid_from_workload(w, precision=dd.PRECISIONS[precision], coarse=coarse,
+                                                  pu_kind=pu), V)
+        es.prepare()
+        return es
+
+    def count(L, n, delta, coarse, pu):
+        w = Workload("e1", p=1, L=L, n=n, overlap=delta, kind="sin4")
+        with solver(w, coarse=coarse, pu=pu) as es:
+            b = torch.full((w.dofs,), (1.0 / n) ** 2, dtype=torch.float64, device=dev)
+            x = torch.ones(w.dofs, dtype=torch.float64, device=dev)
+            its, rel = dd.dd_pcg_solve(es.ctx, b, x, 1e-8, 20000)
+        return its
+
+    Ls = [2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048]
+    fig3 = {"h": "1/30", "delta": 1, "pu": "equal", "L": Ls,
+            "as1": [count(L, 30, 1, 0, 0) for L in Ls], "as2": [count(L, 30, 1, 1, 0) for L in Ls]}
+    t1L = [16, 256, 2048]
+    table1 = {"pu": "distance", "L": t1L, "cases": []}
+    for n in (10, 20, 30):
+        for delta in (1, 2, 3):
+            table1["cases"].append({"h": f"1/{n}", "delta": delta,
+                                    "as1": [count(L, n, delta, 0, 1) if L <= 256 else None for L in t1L],
+                                    "as2": [count(L, n, delta, 1, 1) for L in t1L]})
+    eigen = {"h": "1/32", "delta": 4, "potential": "4-term cosine (seed 2311)", "L": [2, 8, 32, 128, 512, 2048],
+             "fp64": [], "mixed": []}
+    for L in eigen["L"]:
+        w = WORKLOADS["cfg2"].with_(name=f"cfg2_l{L}", L=L)
+        for label, prec in (("fp64", "fp64"), ("mixed", "bf16")):
+            with solver(w, prec) as es:
+                x = torch.ones(w.dofs, dtype=torch.float64, device=dev)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                lam, outer, tot, mx = dd.dd_inverse_iterate(es.ctx, x)
+                ms = 1e3 * (time.perf_counter() - t0)
+            eigen[label].append({"outer": outer, "inner_total": tot, "inner_max": mx,
+                                 "inner_per_outer": tot / max(outer, 1), "ms": ms})
+    w = WORKLOADS["cfg2"]
+    gm = {}
+    for label, prec in (("fp64", "fp64"), ("mixed", "bf16")):
+        with solver(w, prec) as es:
+            dd.dd_set_option(es.ctx, dd.DD_OPT_KRYLOV, 1)
+            dd.dd_set_option(es.ctx, dd.DD_OPT_PRECOND, 1)
+            x = torch.ones(w.dofs, dtype=torch.float64, device=dev)
+            dd.dd_inverse_iterate(es.ctx, x)          # warm-up (GMRES workspace)
+            x.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lam, outer, tot, mx = dd.dd_inverse_iterate(es.ctx, x)
+            ms = 1e3 * (time.perf_counter() - t0)
+        gm[label] = {"lambda": lam, "outer": outer, "inner_total": tot, "inner_max": mx,
+                     "inverse_iterate_ms": ms}
+    gm["cg_as2_inverse_iterate_ms"] = headline
+    return {"fig3": fig3, "table1": table1, "eigen_L": eigen, "gmres_ras2": gm}
+
+
 def main():
     args = parse()
     if args.cpu_sample:
-        print(json.dumps(cpu_sample(args.cpu_sample)))
+        print(json.dumps(cpu_ground_state(args.cpu_sample)))
         return
     if args.impl == "reference":
         run_reference(args)
@@ -386,6 +549,14 @@ def main():
     if args.setup_only:
         if rank == 0:
             print(json.dumps(setup_only(args, dd, dev)))
+        return
+    if args.profile_region:
+        if rank == 0:
+            print(json.dumps(profile_region(args, dd, dev)))
+        return
+    if args.one_shot_breakdown:
+        if rank == 0:
+            print(json.dumps(one_shot_breakdown(args, dd, dev)))
         return
 
     w = WORKLOADS[args.workload]
@@ -454,6 +625,60 @@ def main():
     step_ms = sum(per) / len(per)
     step_ms = max_over_ranks(step_ms, dev)
     value = whole_job_rate(1.0, world, step_ms / 1e3)
+
+    # end to end through the public C-ABI with HOST buffers: one context serves the stream of
+    # potentials (dd_setup once); every step uploads V and x_0 from pinned host memory and
+    # returns phi to host memory.  The one-shot dd_eigenpair (context set-up and teardown
+    # inside) is reported beside it.
+    e2e = None
+    if not args.no_e2e:
+        Vp = torch.from_numpy(V_host).pin_memory()
+        x0 = torch.ones(w.dofs, dtype=torch.float64).pin_memory()
+        phi = torch.empty(w.dofs, dtype=torch.float64).pin_memory()
+        es_h = make(args.precision)
+
+        def host_step():
+            dd.dd_set_potential(es_h.ctx, Vp)
+            dd.dd_cell_eigenpair(es_h.ctx)
+            dd.dd_coarse_build(es_h.ctx)
+            phi.copy_(x0)
+            return dd.dd_inverse_iterate(es_h.ctx, phi)
+
+        for _ in range(2):
+            host_step()
+        ts = []
+        for _ in range(max(1, args.steps)):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lam_h = host_step()[0]
+            ts.append(time.perf_counter() - t0)
+        te = sum(ts) / len(ts)
+        es_h.close()
+        g = dd.grid_from_workload(w, precision=dd.PRECISIONS[args.precision])
+        dd.dd_eigenpair(g, Vp, phi_out=phi)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dd.dd_eigenpair(g, Vp, phi_out=phi)
+        t_cold = time.perf_counter() - t0
+        te = max_over_ranks(te, dev)
+        e2e = {"value": whole_job_rate(1.0, world, te), "unit": UNIT, "h2d_bytes_per_step": int(Vp.numel() * 8 + x0.numel() * 8),
+               "d2h_bytes_per_step": int(phi.numel() * 8), "ms_per_step": te * 1e3,
+               "path": "dd_set_potential + dd_cell_eigenpair + dd_coarse_build + dd_inverse_iterate, host buffers",
+               "lambda": lam_h,
+               "one_shot_dd_eigenpair_ms": t_cold * 1e3}
+
+    # the oracle's full ground state on one host core, in a child process beside the GPU work
+    # that follows (started after the headline and end-to-end regions, so that neither shares
+    # the host with it)
+    cpu_proc = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_proc = start_cpu_ground_state(args.workload)
+
+    # measured FP64 / FP32 FMA throughput: the roofline denominators of the ALU-bound kernels
+    alu = {"fp64_tflops": dd.dd_alu_peak_test(0, 5), "fp32_tflops": dd.dd_alu_peak_test(1, 5),
+           "source": ALU_PEAK_SOURCE}
+    peaks, peak_src = load_peaks()
 
     # plain FP64 method, same workload
     fp64_steps = args.fp64_steps if args.fp64_steps is not None else max(1, args.steps // 2)
@@ -578,6 +803,25 @@ def main():
         d3_line = {"workload": f"cfg3: p=2, L=64, h=1/16, delta=2, dofs={w3.dofs}, 4096 subdomains, Gaussian-well "
                                "lattice", "precision": args.precision, "ms_per_ground_state": sum(ts3) / len(ts3),
                    "lambda": r3[0], "outer_iters": r3[1], "inner_iters_total": r3[2]}
+        # per-kernel device times of one profiled ground state (CUDA events around every
+        # launch) and each kernel class against its binding roofline
+        dd.dd_set_option(es3.ctx, dd.DD_OPT_TIMING, 1)
+        dd.dd_reset_timings(es3.ctx)
+        step3()
+        kt3 = {k: v for k, v in dd.dd_kernel_timings(es3.ctx).items() if v[0] > 0}
+        dd.dd_set_option(es3.ctx, dd.DD_OPT_TIMING, 0)
+        i3 = es3.info
+        wi, we = w3.n + 2 * w3.overlap - 1, w3.n + w3.overlap - 1
+        cnt3 = [(w3.L - 2) ** 2, 4 * (w3.L - 2), 4]
+        nl3 = [wi * wi * (w3.ny - 1), wi * we * (w3.ny - 1), we * we * (w3.ny - 1)]
+        m3 = kernel_model(w3, i3, cnt3, nl3, i3["band_local"], args.precision)
+        d3_line["kernels"] = {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in kt3.items()}
+        d3_line["roofline"] = {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv)
+                                   for kk, vv in roofline_entry(k, m3[k], v[1], v[0], peaks, peak_src, args.precision,
+                                                                alu).items()
+                                   if kk in ("bound", "pipe", "achieved", "peak", "unit", "frac", "avg_launch_us",
+                                             "launches", "hbm_frac_algorithmic")}
+                               for k, v in kt3.items() if k in m3}
         es3.close()
 
     # phase breakdown of one step (host timer around each synchronous call)
@@ -601,6 +845,20 @@ def main():
 
     breakdown = {"mixed": phases(mixed), "fp64_plain": phases(plain)}
 
+    sweep_line = None
+    if not args.no_sweeps:
+        sweep_line = sweeps(dd, dev, {"fp64": breakdown["fp64_plain"]["inverse_iterate"],
+                                      "mixed": breakdown["mixed"]["inverse_iterate"]})
+
+    # time to the ground state from dd_setup (a fresh context each time), split into set-up
+    # (dd_setup, cell eigenpair, coarse build) and solve (inverse iteration)
+    from_setup = {}
+    for label, prec in (("mixed", args.precision), ("fp64_plain", "fp64")):
+        ob = one_shot_breakdown(args, dd, dev, reps=3, precision=prec)
+        from_setup[label] = {"setup_ms": ob["setup_ms"], "solve_ms": ob["solve_ms"], "total_ms": ob["total_ms"],
+                             "destroy_ms": ob["median_ms"]["destroy"],
+                             "phases_ms": {k: round(v, 3) for k, v in ob["median_ms"].items()}}
+
     # per-kernel device times (CUDA events around every launch, one profiled step)
     dd.dd_set_option(mixed.ctx, dd.DD_OPT_TIMING, 1)
     dd.dd_reset_timings(mixed.ctx)
@@ -614,7 +872,6 @@ def main():
     dd.dd_set_option(plain.ctx, dd.DD_OPT_TIMING, 0)
 
     info = mixed.info
-    peaks, peak_src = load_peaks()
     subs = []
     nloc_interior = (w.n + 2 * w.overlap - 1) * (w.ny - 1)
     nloc_edge = (w.n + w.overlap - 1) * (w.ny - 1)
@@ -622,66 +879,16 @@ def main():
     model = kernel_model(w, info, counts, nlocs, info["band_local"], args.precision)
     busy = {k: v for k, v in kt.items() if v[0] > 0}
     dom = max((k for k in busy if k in model), key=lambda k: busy[k][1])
-    roofline = roofline_entry(dom, model[dom], busy[dom][1], busy[dom][0], peaks, peak_src, args.precision)
-    others = {k: roofline_entry(k, model[k], v[1], v[0], peaks, peak_src, args.precision)
+    roofline = roofline_entry(dom, model[dom], busy[dom][1], busy[dom][0], peaks, peak_src, args.precision, alu)
+    others = {k: roofline_entry(k, model[k], v[1], v[0], peaks, peak_src, args.precision, alu)
               for k, v in busy.items() if k in model and k != dom}
     kernel_table = {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in busy.items()}
     kernel_table64 = {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in kt64.items() if v[0] > 0}
 
-    # end to end through the public C-ABI with HOST buffers: one context serves the stream of
-    # potentials (dd_setup once); every step uploads V and x_0 from pinned host memory and
-    # returns phi to host memory.  The one-shot dd_eigenpair (context set-up and teardown
-    # inside) is reported beside it.
-    e2e = None
-    if not args.no_e2e:
-        Vp = torch.from_numpy(V_host).pin_memory()
-        x0 = torch.ones(w.dofs, dtype=torch.float64).pin_memory()
-        phi = torch.empty(w.dofs, dtype=torch.float64).pin_memory()
-        es_h = make(args.precision)
-
-        def host_step():
-            dd.dd_set_potential(es_h.ctx, Vp)
-            dd.dd_cell_eigenpair(es_h.ctx)
-            dd.dd_coarse_build(es_h.ctx)
-            phi.copy_(x0)
-            return dd.dd_inverse_iterate(es_h.ctx, phi)
-
-        for _ in range(2):
-            host_step()
-        ts = []
-        for _ in range(max(1, args.steps)):
-            flush.zero_()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            lam_h = host_step()[0]
-            ts.append(time.perf_counter() - t0)
-        te = sum(ts) / len(ts)
-        es_h.close()
-        g = dd.grid_from_workload(w, precision=dd.PRECISIONS[args.precision])
-        dd.dd_eigenpair(g, Vp, phi_out=phi)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        dd.dd_eigenpair(g, Vp, phi_out=phi)
-        t_cold = time.perf_counter() - t0
-        te = max_over_ranks(te, dev)
-        e2e = {"value": whole_job_rate(1.0, world, te), "unit": UNIT, "h2d_bytes_per_step": int(Vp.numel() * 8 + x0.numel() * 8),
-               "d2h_bytes_per_step": int(phi.numel() * 8), "ms_per_step": te * 1e3,
-               "path": "dd_set_potential + dd_cell_eigenpair + dd_coarse_build + dd_inverse_iterate, host buffers",
-               "lambda": lam_h,
-               "one_shot_dd_eigenpair_ms": t_cold * 1e3}
-
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if cpu_proc is not None:
         try:
-            s = run_cpu_sample(args.workload)
-            t_cpu = s["setup_s"] + s["pcg_s_per_iter"] * res64[3]
-            cpu = {"value": 1.0 / t_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": (f"oracle set-up of the same workload ({s['setup_s']:.1f} s: assembly, cell "
-                              f"eigenpair, {w.L ** w.p} local factorisations, coarse factorisation) + "
-                              f"{s['pcg_iters_run']} PCG iterations ({s['pcg_s_per_iter']:.3f} s each); "
-                              f"time to ground state extrapolated with the {res64[3]} inner iterations "
-                              f"the plain FP64 method needs"),
-                   "est_time_to_ground_state_s": t_cpu}
+            cpu = cpu_baseline_entry(finish_cpu_ground_state(cpu_proc), w)
         except Exception as e:  # noqa: BLE001
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
 
@@ -690,13 +897,14 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64 (local inverses %s)" % args.precision, "data": "synthetic",
-            "config": {"workload": f"{args.workload}: p=1, L={w.L}, ell=1, h=1/{w.n}, delta={w.overlap}, "
-                                   f"dofs={w.dofs}, {w.L ** w.p} subdomains, V=4-term cosine (seed {w.seed})",
+            "config": {"workload": workload_label(w),
                        "precision": args.precision, "l2": "flushed between steps (256 MB write)",
                        "local_gemm_tile": f"128x{dd.dd_query(mixed.ctx)['gemm_tile_n']}",
                        "parallelism": f"replicas x{world}"},
             "time_to_ground_state_ms": {"mixed": step_ms, "fp64_plain": fp64_ms,
-                                        "speedup_mixed_vs_fp64": fp64_ms / step_ms},
+                                        "speedup_mixed_vs_fp64": fp64_ms / step_ms,
+                                        "from_dd_setup": from_setup},
+            "alu_peaks": alu,
             "lambda": lam, "sigma": sigma, "outer_iters": outer, "inner_iters_total": inner_tot,
             "fp64_plain": {"lambda": res64[0], "outer_iters": res64[2], "inner_iters_total": res64[3]},
             "pcg_iters_per_s": inner_tot / (step_ms / 1e3),
@@ -704,6 +912,7 @@ def main():
             "differentiable": grad_line,
             "batched": batch_line,
             "d3": d3_line,
+            "sweeps": sweep_line,
             "roofline": roofline,
             "roofline_other_kernels": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv)
                                            for kk, vv in v.items() if kk in ("bound", "achieved", "peak", "unit",

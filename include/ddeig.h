@@ -366,6 +366,15 @@ int dd_tc_gemm_test(int precision, int M, int N, int K, const float* A_host, con
  * pointer. */
 int dd_convert_test(int kind, long long n, const void* in_host, void* out_host);
 
+/* Self-test of the arithmetic pipes that bound the FP64 vector kernels (no paper counterpart;
+ * it measures their roofline denominators on the GPU at hand): kind 0 the FP64 fused
+ * multiply-add (DFMA) pipe, kind 1 the FP32 one (FFMA).  Every thread of 8 blocks of 256 per
+ * SM runs 8 independent FMA chains; *tflops_out receives 2 flops per FMA over the CUDA-event
+ * time of the fastest of `reps` launches (1..100, after one untimed launch), in TFLOP/s.
+ * Allocates and frees its own device buffers.  DD_EINVAL for a bad kind or reps or a null
+ * pointer. */
+int dd_alu_peak_test(int kind, int reps, double* tflops_out);
+
 /* Allocation-free form of the same tensor-core contraction (the paper has no counterpart: it
  * exists for callers that cannot allocate device memory where they need the product, such as
  * a server whose device memory is reserved up front by its own arena, or a latency-critical

@@ -87,6 +87,7 @@ _SIGS = {
     "dd_set_potential": (c_int, [c_void_p, c_void_p, c_size_t]),
     "dd_kernel_launch_count": (c_longlong, []),
     "dd_tc_gemm_noalloc": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "dd_alu_peak_test": (c_int, [c_int, c_int, POINTER(c_double)]),
 }
 
 
@@ -306,6 +307,13 @@ def dd_convert_test(kind: int, x):
     out = np.zeros(x.size, dtype={0: np.uint16, 1: np.float32, 2: np.float64}[kind])
     _check(lib().dd_convert_test(kind, x.size, _ptr(x), _ptr(out)))
     return out
+
+
+def dd_alu_peak_test(kind: int, reps: int = 5) -> float:
+    """Measured FMA throughput of the GPU (TFLOP/s): kind 0 FP64, kind 1 FP32."""
+    t = c_double()
+    _check(lib().dd_alu_peak_test(kind, reps, byref(t)))
+    return t.value
 
 
 def dd_tc_gemm_noalloc(precision: int, A_dev, B_dev, D_dev, stream=None) -> int:

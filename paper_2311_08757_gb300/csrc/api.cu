@@ -199,7 +199,11 @@ void build_subdomains(dd_ctx* c) {
   for (int a = 0; a < g.ncx; ++a) {
     int4 v = make_int4(-1, 0, -1, 0);
     int k = 0;
-    for (int i = 0; i < g.L && k < 2; ++i)
+    // subdomain i spans columns i n - delta + 1 .. (i + 1) n + delta - 1 (clipped), so only
+    // i = floor(a / n) - 1 .. floor(a / n) + 1 can hold column a (2 delta < n); scanned in
+    // increasing i, the order the owners are listed in
+    const int i0 = std::max(0, a / g.n - 1), i1 = std::min(g.L - 1, a / g.n + 1);
+    for (int i = i0; i <= i1 && k < 2; ++i)
       if (a >= ax_lo(g, i) && a <= ax_hi(g, i)) {
         if (k == 0) { v.x = i; v.y = a - ax_lo(g, i); }
         else { v.z = i; v.w = a - ax_lo(g, i); }
@@ -1173,9 +1177,7 @@ int dd_eigenpair(const dd_grid* g, const double* V, size_t nV, void* stream, dou
   if (rc == DD_OK) {
     rc = guarded(c, [&]() -> int {
       // x_0 = 1 in the context's staging buffer (device), phi written to phi_out
-      const long long n = c->g.ndof;
-      std::vector<double> ones((size_t)n, 1.0);
-      DD_CUDA(cudaMemcpyAsync(c->stage_b, ones.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+      launch_fill(c->stage_b, c->g.ndof, 1.0, c->stream);
       DD_CUDA(cudaStreamSynchronize(c->stream));
       return DD_OK;
     });

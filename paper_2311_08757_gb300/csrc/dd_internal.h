@@ -335,6 +335,7 @@ void timer_end(dd_ctx* c, int kc, cudaStream_t s, cudaEvent_t e0);
 void timer_collect(dd_ctx* c);
 
 void* dev_alloc(dd_ctx* c, size_t bytes);
+void launch_fill(double* x, long long n, double v, cudaStream_t s);
 
 // process-wide count of kernel launches issued by this library (graph replays included)
 void note_launch();

@@ -473,6 +473,17 @@ void launch_fused_pq(dd_ctx* c, cudaStream_t s) {
   DD_CUDA(cudaGetLastError());
 }
 
+// x[0..n) = v (start vectors of the convenience entry points)
+__global__ void __launch_bounds__(kThreads) k_fill_value(long long n, double v, double* __restrict__ x) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    x[t] = v;
+}
+
+void launch_fill(double* x, long long n, double v, cudaStream_t s) {
+  (k_fill_value<<<grid_blocks(n, kThreads), kThreads, 0, s>>>(n, v, x), dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+}
+
 // q = A_sigma p, pq = (p, q), alpha = rho / pq.
 template <int P>
 __global__ void __launch_bounds__(kThreads) k_matvec_pq(Geo g, const double* __restrict__ tab, double* pb0,

@@ -99,6 +99,10 @@ def test_self_test_entry_points_check_arguments_first():
     assert L.dd_convert_test(3, 4, buf, out) == dd.DD_EINVAL     # no such conversion
     assert L.dd_convert_test(0, 0, buf, out) == dd.DD_EINVAL     # empty
     assert L.dd_convert_test(0, 4, None, out) == dd.DD_EINVAL
+    t = ctypes.c_double()
+    assert L.dd_alu_peak_test(2, 3, ctypes.byref(t)) == dd.DD_EINVAL     # no such pipe
+    assert L.dd_alu_peak_test(0, 0, ctypes.byref(t)) == dd.DD_EINVAL     # no timed launch
+    assert L.dd_alu_peak_test(1, 3, None) == dd.DD_EINVAL
     p = ctypes.c_void_p(16)   # never dereferenced: the checks come first
     f = ctypes.cast(p, ctypes.POINTER(ctypes.c_float))
     assert L.dd_tc_gemm_noalloc(dd.DD_PREC_FP64, 128, 128, 128, p, p, f, None) == dd.DD_EINVAL

@@ -1,0 +1,96 @@
+"""The sweeps of Sec. 4.1 on the GPU kernels, and the L-independence of the inner iteration
+counts of the eigen-solver.
+
+* Fig. 3 (Sec. 4.1.1): the source problem a_sigma(u, v) = (1, v) with the printed potential,
+  h = 1/30, delta = 1, CG from the initial guess 1 to rTOL = 1e-8, one-level M_AS1 against
+  two-level M_AS2.  The plain FP64 form runs the same CG as the oracle, so its counts must
+  equal the oracle's (tests/golden/source_sweeps.json) within one iteration for L <= 256;
+  beyond, up to L = 2048, the two-level counts stay bounded while the one-level ones grow.
+* Table 1 (Sec. 4.1.2): the same with the distance partition of unity, h in {1/10, 1/20,
+  1/30} x delta in {1, 2, 3}, against the oracle's counts.
+* Inverse iteration (Sec. 2) on the headline potential (h = 1/32, delta = 4): outer steps and
+  inner PCG counts equal the oracle's for L <= 32, and the inner counts stay flat up to
+  L = 2048 in both the FP64 and the mixed (BF16) form (the theorem of Sec. 3: the condition
+  number of the preconditioned operator is bounded independently of L)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import paper_2311_08757_gb300 as dd
+from ddinputs import WORKLOADS, Workload
+from tests.gpu_util import gpu_vec, make_solver
+
+pytestmark = pytest.mark.gpu
+
+with open(os.path.join(os.path.dirname(__file__), "golden", "source_sweeps.json")) as _f:
+    GOLD = json.load(_f)
+
+
+def source_count(L, n, delta, coarse, pu, precision="fp64"):
+    w = Workload("e1", p=1, L=L, n=n, overlap=delta, kind="sin4")
+    with make_solver(w, precision=precision, coarse=1 if coarse else 0, pu=pu) as es:
+        es.prepare()
+        b = gpu_vec(np.full(w.dofs, (1.0 / n) ** 2))   # (f, v_h) for f = 1
+        x = gpu_vec(np.ones(w.dofs))
+        its, rel = dd.dd_pcg_solve(es.ctx, b, x, 1e-8, 20000)
+        assert rel <= 1e-8
+        return its
+
+
+def test_fig3_counts_match_oracle():
+    f = GOLD["fig3"]
+    for L, a1, a2 in zip(f["L"], f["as1"], f["as2"]):
+        g1 = source_count(L, f["n"], f["delta"], False, f["pu"])
+        g2 = source_count(L, f["n"], f["delta"], True, f["pu"])
+        assert abs(g1 - a1) <= 1, (L, g1, a1)
+        assert abs(g2 - a2) <= 1, (L, g2, a2)
+
+
+def test_fig3_extended_to_large_L():
+    """L = 512 ... 2048 (61,439 x 29 unknowns at the end): M_AS2 stays within a few
+    iterations of its L = 256 count, M_AS1 keeps growing roughly linearly in L."""
+    f = GOLD["fig3"]
+    as2_256 = f["as2"][f["L"].index(256)]
+    as1_256 = f["as1"][f["L"].index(256)]
+    for L in (512, 1024, 2048):
+        g2 = source_count(L, f["n"], f["delta"], True, f["pu"])
+        assert g2 <= as2_256 + 5, (L, g2)
+    g1 = source_count(2048, f["n"], f["delta"], False, f["pu"])
+    assert g1 > 4 * as1_256 and g1 > 20 * as2_256
+
+
+def test_table1_counts_match_oracle():
+    t = GOLD["table1"]
+    for row in t["cases"]:
+        for L, a1, a2 in zip(t["L"], row["as1"], row["as2"]):
+            g1 = source_count(L, row["n"], row["delta"], False, t["pu"])
+            g2 = source_count(L, row["n"], row["delta"], True, t["pu"])
+            assert abs(g1 - a1) <= 1, (row["n"], row["delta"], L, g1, a1)
+            assert abs(g2 - a2) <= 1, (row["n"], row["delta"], L, g2, a2)
+
+
+def _eigen(L, precision):
+    w = WORKLOADS["cfg2"].with_(name=f"cfg2_l{L}", L=L)
+    with make_solver(w, precision=precision) as es:
+        es.prepare()
+        x = gpu_vec(np.ones(w.dofs))
+        lam, outer, tot, mx = dd.dd_inverse_iterate(es.ctx, x)
+    return outer, tot, mx
+
+
+def test_eigen_inner_counts_match_oracle_and_stay_flat():
+    e = GOLD["eigen"]
+    for L, k, tot, mx in zip(e["L"], e["outer"], e["inner_total"], e["inner_max"]):
+        go, gt, gm = _eigen(L, "fp64")
+        assert abs(go - k) <= 1, (L, go, k)
+        assert abs(gm - mx) <= 1, (L, gm, mx)
+        assert abs(gt - tot) <= go, (L, gt, tot)
+    for prec in ("fp64", "bf16"):
+        ref = max(_eigen(L, prec)[2] for L in (8, 32))
+        for L in (128, 512, 2048):
+            outer, tot, mx = _eigen(L, prec)
+            print(f"{prec} L={L}: outer {outer}, inner total {tot}, inner max {mx} (L <= 32: {ref})")
+            assert mx <= 1.25 * ref, (prec, L, mx, ref)
+            assert outer <= 10

@@ -544,3 +544,22 @@ def test_inner_tolerance_strategies_order():
     assert tot["fused"] < tot["adaptive"]
     assert lams["adaptive"] == pytest.approx(lams["fixed"], rel=1e-10)
     assert lams["fused"] == pytest.approx(lams["fixed"], rel=1e-10)
+
+
+def test_source_sweep_goldens_are_the_oracles():
+    """The stored iteration counts of tests/golden/source_sweeps.json (the reference of the
+    GPU sweeps of Sec. 4.1) are what the oracle computes now: a few entries recomputed."""
+    with open(os.path.join(GOLDEN, "source_sweeps.json")) as f:
+        gold = json.load(f)
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("mk", os.path.join(GOLDEN, "make_source_sweeps.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    f3 = gold["fig3"]
+    for L in (4, 8):
+        i = f3["L"].index(L)
+        assert mk.source_count(L, 30, 1, False, "equal") == f3["as1"][i]
+        assert mk.source_count(L, 30, 1, True, "equal") == f3["as2"][i]
+    row = [r for r in gold["table1"]["cases"] if r["n"] == 10 and r["delta"] == 2][0]
+    assert mk.source_count(4, 10, 2, True, "distance") == row["as2"][0]
+    assert mk.source_count(4, 10, 2, False, "distance") == row["as1"][0]
