@@ -248,28 +248,49 @@ int dd_eigenpair(const dd_grid* g, const double* V_cell_qp, size_t nV, void* str
  * Batched ground states (many independent instances: uneven L, own potential and shift).
  * dd_batch_create sets up one context per instance (grids[i], V[i] of nV[i] doubles, host or
  * device, as for dd_setup; all on the caller's stream).  dd_batch_ground_states runs every
- * instance's whole pipeline -- dd_cell_eigenpair, dd_coarse_build and, from x_0 = 1,
- *   DD_BATCH_IPM             dd_inverse_iterate (tol_res 1e-8, tol_lam 1e-10, rtol_inner 1e-8)
- *   DD_BATCH_LOPCG_FUSED     dd_lopcg with DD_INNER_FUSED
- *   DD_BATCH_LOPCG_ADAPTIVE  dd_lopcg with DD_INNER_ADAPTIVE
- * -- on a pool of `threads` host threads (<= 0: min(count, 16)), largest instance first, each
- * instance on its own context stream, so that the instances' kernels overlap on the GPU.
+ * instance's whole pipeline -- dd_cell_eigenpair and dd_coarse_build on a pool of `threads`
+ * host threads (<= 0: min(count, 16)), largest instance first, each on its own context
+ * stream, then from x_0 = 1:
+ *   DD_BATCH_IPM             the shifted inverse iteration (tol_res 1e-8, tol_lam 1e-10,
+ *                            rtol_inner 1e-8, as dd_inverse_iterate).  When the instances share
+ *                            p = 1, the precision (BF16 or TF32), h, delta, ell, quadrature and
+ *                            partition of unity, it runs BATCHED: every kernel of a PCG iteration
+ *                            is one launch over all instances (the blocks of each instance's own
+ *                            launch side by side; the local solves one grouped tensor-core
+ *                            contraction over all instances' tiles), a block of iterations of
+ *                            all instances is one CUDA graph, each instance keeps its own device
+ *                            scalars, kernels of an instance whose solve is done return at once,
+ *                            and an instance whose eigen-iteration has stopped drops out; the
+ *                            outer steps run in lockstep.  Otherwise as DD_BATCH_IPM_CONCURRENT.
+ *   DD_BATCH_LOPCG_FUSED     dd_lopcg with DD_INNER_FUSED, per instance, concurrently
+ *   DD_BATCH_LOPCG_ADAPTIVE  dd_lopcg with DD_INNER_ADAPTIVE, per instance, concurrently
+ *   DD_BATCH_IPM_CONCURRENT  dd_inverse_iterate per instance on the thread pool (the instances'
+ *                            own launches overlap on the GPU)
  * Outputs per instance (arrays of count entries, each may be NULL): lambda, outer and inner
- * iteration counts, wall seconds from the start of its cell eigenpair to its eigenpair;
+ * iteration counts, wall seconds from the start of the call to the instance's eigenpair;
  * phi_out[i] (host or device, ndof_i doubles; phi_out or an entry may be NULL).
  * Returns the first failing instance's status (the others still run).  Results equal those
- * of the single-instance calls bit for bit (same kernels, deterministic reductions).
- * dd_batch_context gives instance i's context (owned by the batch) for options and queries.
+ * of the single-instance calls bit for bit (same arithmetic per instance, deterministic
+ * reductions), batched or not.
+ * dd_batch_context gives instance i's context (owned by the batch) for options and queries;
+ * a context with timing, GMRES, the restricted preconditioner or the dense coarse solve
+ * selected makes DD_BATCH_IPM run per instance.  dd_batch_info reports whether the batch
+ * qualifies for the batched kernels, whether the last call ran them, the N tile of the
+ * grouped contraction chosen by timing the three shapes on the batch's own operands at the
+ * first batched call (0 before), and the PCG iterations per graph replay (each may be NULL).
  */
 typedef struct dd_batch dd_batch;
 #define DD_BATCH_IPM            0
 #define DD_BATCH_LOPCG_FUSED    1
 #define DD_BATCH_LOPCG_ADAPTIVE 2
+#define DD_BATCH_IPM_CONCURRENT 3
 int dd_batch_create(const dd_grid* grids, const double* const* V, const size_t* nV, int count, void* stream,
                     dd_batch** out);
 int dd_batch_ground_states(dd_batch* b, int method, int threads, double* lambda_out, double* const* phi_out,
                            int* outer_out, int* inner_out, double* seconds_out);
 int dd_batch_size(const dd_batch* b);
+int dd_batch_info(const dd_batch* b, int* batchable_out, int* last_batched_out, int* gemm_tile_n_out,
+                  int* check_every_out);
 dd_ctx* dd_batch_context(dd_batch* b, int i);
 void dd_batch_destroy(dd_batch* b);
 

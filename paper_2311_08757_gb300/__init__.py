@@ -65,6 +65,7 @@ _SIGS = {
                                 POINTER(c_void_p)]),
     "dd_batch_ground_states": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "dd_batch_size": (c_int, [c_void_p]),
+    "dd_batch_info": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
     "dd_batch_context": (c_void_p, [c_void_p, c_int]),
     "dd_batch_destroy": (None, [c_void_p]),
     "dd_lopcg": (c_int, [c_void_p, c_void_p, c_int, c_double, c_double, c_int, c_double, POINTER(c_double),
@@ -381,8 +382,9 @@ class Eigensolver:
         return dd_lopcg(self.ctx, x, inner, **kw)
 
 
-DD_BATCH_IPM, DD_BATCH_LOPCG_FUSED, DD_BATCH_LOPCG_ADAPTIVE = 0, 1, 2
-BATCH_METHODS = {"ipm": DD_BATCH_IPM, "lopcg_fused": DD_BATCH_LOPCG_FUSED, "lopcg_adaptive": DD_BATCH_LOPCG_ADAPTIVE}
+DD_BATCH_IPM, DD_BATCH_LOPCG_FUSED, DD_BATCH_LOPCG_ADAPTIVE, DD_BATCH_IPM_CONCURRENT = 0, 1, 2, 3
+BATCH_METHODS = {"ipm": DD_BATCH_IPM, "lopcg_fused": DD_BATCH_LOPCG_FUSED, "lopcg_adaptive": DD_BATCH_LOPCG_ADAPTIVE,
+                 "ipm_concurrent": DD_BATCH_IPM_CONCURRENT}
 
 
 class Batch:
@@ -423,6 +425,12 @@ class Batch:
         if code != DD_OK:
             raise DDError(code, "batched ground states failed")
         return {"lambda": lam, "outer": outer, "inner": inner, "seconds": sec}
+
+    def info(self) -> dict:
+        """dd_batch_info: batchable, last_batched, gemm_tile_n, check_every."""
+        v = [c_int() for _ in range(4)]
+        _check(lib().dd_batch_info(self.handle, *[byref(x) for x in v]))
+        return dict(zip(("batchable", "last_batched", "gemm_tile_n", "check_every"), (x.value for x in v)))
 
     def close(self):
         if getattr(self, "handle", None):

@@ -69,19 +69,29 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
   __syncthreads();
 }
 
+// A block's place in the launch of one problem: block b of nb.  A plain launch is one
+// problem (b = blockIdx.x, nb = gridDim.x); a batched launch runs the blocks of several
+// problems' launches side by side, each block with the index and count it would have had
+// in its own problem's launch, so every problem's arithmetic (and the order of its
+// reductions) is that of its plain launch.
+struct VBlk {
+  int b, nb;
+};
+__device__ __forceinline__ VBlk vblk_self() { return VBlk{(int)blockIdx.x, (int)gridDim.x}; }
+
 // Deterministic grid-wide sum: every block stores its partial; the last block to finish
 // adds the partials in block order and returns true (result in tot[] of thread 0).
 template <int NV>
 __device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* partials, unsigned* counter,
-                                              double (&tot)[NV]) {
+                                              double (&tot)[NV], VBlk vb) {
   __shared__ int s_last;
   block_sum<NV>(v);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) partials[(size_t)k * kMaxRedBlocks + blockIdx.x] = v[k];
+    for (int k = 0; k < NV; ++k) partials[(size_t)k * kMaxRedBlocks + vb.b] = v[k];
     __threadfence();
     unsigned t = atomicAdd(counter, 1u);
-    s_last = (t == gridDim.x - 1);
+    s_last = (t == (unsigned)vb.nb - 1);
   }
   __syncthreads();
   if (!s_last) return false;
@@ -90,7 +100,7 @@ __device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* partials,
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
     s[k] = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+    for (int b = threadIdx.x; b < vb.nb; b += blockDim.x)
       s[k] += __ldcg(partials + (size_t)k * kMaxRedBlocks + b);
   }
   block_sum<NV>(s);
@@ -100,6 +110,11 @@ __device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* partials,
     *counter = 0u;
   }
   return true;
+}
+template <int NV>
+__device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* partials, unsigned* counter,
+                                              double (&tot)[NV]) {
+  return grid_sum_last<NV>(v, partials, counter, tot, vblk_self());
 }
 
 // ---- precision conversions on the integer pipe ------------------------------------------

@@ -251,6 +251,48 @@ struct dd_ctx {
 
 namespace dd {
 
+// One problem of a batched launch: its geometry, the device buffers of its context, and the
+// block counts of its own plain launches (each batched kernel gives every block of problem i
+// the index and count it has in problem i's plain launch, so that the arithmetic, and the
+// order of every reduction, is that of the plain launch).
+struct BInst {
+  Geo g;
+  double *x, *r, *z, *pb0, *pb1, *q, *w1, *w2, *w3, *xe;   // padded vectors
+  const double *tabS, *tabM;
+  PcgState* st;
+  OuterState* ost;
+  double* red;
+  unsigned* cnt;
+  const Sub* subs;
+  const int* slot_of_sub;
+  void* Rpack;            // this problem's rows of the batch's packed restrictions
+  const double* wT;
+  double* c0;
+  double* u0;
+  float* u0f;
+  const float* Y32;       // this problem's rows of the batch's local solutions
+  const float* wT32;
+  const float* puT32;
+  const int4* axown;
+  const int4* subrow;
+  const double* cr;       // cyclic-reduction coefficients of A_0 (p = 1)
+  int cr_m, cr_c2, cr_w2, cr_staged;
+  int kpad, coarse, nsub, flexible;
+  int nb_init, nb_fused, nb_xr, nb_prolong, nb_sdot, nb_st, nb_vec;
+  int active;             // 0 once the problem's eigen-iteration has stopped
+  int* err;               // the context's error word of bounded waits
+};
+
+// Vector roles in BInst (the batched outer-step kernels take roles, not pointers).
+enum BVec { BV_X = 0, BV_R, BV_Z, BV_Q, BV_W1, BV_W2, BV_W3, BV_XE };
+
+// Per-problem scalars copied to the host after a batched step.
+struct BStat {
+  int pcg_done, pcg_status, pcg_iter, active;
+  double xAx, rr, mm;
+  int outer_status, pad_;
+};
+
 // ----- launchers (kernels in k_*.cu) -----
 int grid_blocks(long long work, int threads, int max_per_sm = 8);
 
@@ -327,6 +369,33 @@ void launch_givens(dd_ctx* c, int j, cudaStream_t s);
 void launch_backsolve(dd_ctx* c, int m, cudaStream_t s);
 void launch_gmres_start(dd_ctx* c, const double* nrm2, cudaStream_t s);
 void launch_add_inplace(dd_ctx* c, int n, double* a, const double* b, cudaStream_t s);
+
+// ----- batched launchers (vmap[k] = {problem, block within the problem's launch}) -----
+void batch_grid_sizes(const dd_ctx* c, BInst* I);   // the nb_* of the plain launchers
+void launch_b_pcg_reset(const BInst* B, int n, double rtol2, int maxit, cudaStream_t s);
+void launch_b_zero_pcg(const BInst* B, const int2* vmap, int nvb, cudaStream_t s);
+void launch_b_pcg_init(const BInst* B, const int2* vmap, int nvb, int b_role, cudaStream_t s);
+void launch_b_fused_pq(const BInst* B, const int2* vmap, int nvb, int ypad, cudaStream_t s);
+void launch_b_xr_update(const BInst* B, const int2* vmap, int nvb, cudaStream_t s);
+void launch_b_prolong(const BInst* B, const int2* vmap, int nvb, int mode, cudaStream_t s);
+void launch_b_stencil(const BInst* B, const int2* vmap, int nvb, int mass, int x_role, int y_role, cudaStream_t s);
+void launch_b_stencil_dot(const BInst* B, const int2* vmap, int nvb, int x_role, int y_role, cudaStream_t s);
+void launch_b_outer_normalize(const BInst* B, const int2* vmap, int nvb, int w_role, int mw_role, int x_role,
+                              cudaStream_t s);
+void launch_b_outer_res(const BInst* B, const int2* vmap, int nvb, int ax_role, int mx_role, cudaStream_t s);
+void launch_b_gather(const BInst* B, int n, BStat* out, cudaStream_t s);
+void launch_b_pack(const BInst* B, const int2* vmap, int nvb, int precision, cudaStream_t s);
+void launch_b_cr_solve(const BInst* B, int n, size_t smem, cudaStream_t s);
+void cr_launch_shape(const dd_ctx* c, size_t* smem, int* staged);
+struct BGemm;   // grouped local-solve contraction of a batch (k_gemm.cu)
+BGemm* bgemm_create(const std::vector<dd_ctx*>& cs, const std::vector<int>& type_base,
+                    const std::vector<int>& slot_base, void* Ainv_all, void* Rpack_all, float* Y_all, int* err,
+                    cudaStream_t s);
+void bgemm_run(BGemm* b, int bn, cudaStream_t s);
+int bgemm_tune(BGemm* b, cudaStream_t s);
+void bgemm_destroy(BGemm* b);
+void launch_b_unpad(const BInst* B, const int2* vmap, int nvb, int src_role, double* const* dst, cudaStream_t s);
+void launch_b_pad(const BInst* B, const int2* vmap, int nvb, const double* const* src, int dst_role, cudaStream_t s);
 
 
 // timing helpers

@@ -239,10 +239,9 @@ constexpr int ERR_CR_WAIT = 1 << 7;   // error-word bit: the coefficient copy di
 // The coefficients are brought into shared memory by bulk copies (the TMA engine, one
 // thread issues them) while the threads load the right-hand side; every level then waits on
 // shared memory only.  When they do not fit (very long chains), they are read from global.
-__global__ void __launch_bounds__(kCrThreads) k_cr_solve(const double* __restrict__ cr, int N, int m, int C2,
-                                                         int W2, const double* __restrict__ rhs,
-                                                         double* __restrict__ x, float* __restrict__ xf,
-                                                         const PcgState* st, int staged, int* err) {
+__device__ __forceinline__ void cr_solve_body(const double* __restrict__ cr, int N, int m, int C2, int W2,
+                                              const double* __restrict__ rhs, double* __restrict__ x,
+                                              float* __restrict__ xf, const PcgState* st, int staged, int* err) {
   if (st != nullptr && st->done) return;
   extern __shared__ __align__(16) double sm_cr[];
   __shared__ __align__(8) unsigned long long cr_bar;
@@ -306,6 +305,20 @@ __global__ void __launch_bounds__(kCrThreads) k_cr_solve(const double* __restric
     x[j] = f[j + 1];
     xf[j] = __double2float_rn(f[j + 1]);
   }
+}
+
+__global__ void __launch_bounds__(kCrThreads) k_cr_solve(const double* __restrict__ cr, int N, int m, int C2,
+                                                         int W2, const double* __restrict__ rhs,
+                                                         double* __restrict__ x, float* __restrict__ xf,
+                                                         const PcgState* st, int staged, int* err) {
+  cr_solve_body(cr, N, m, C2, W2, rhs, x, xf, st, staged, err);
+}
+
+// batched: one CTA per problem
+__global__ void __launch_bounds__(kCrThreads) kb_cr_solve(const BInst* __restrict__ B) {
+  const BInst& I = B[blockIdx.x];
+  if (!I.active) return;
+  cr_solve_body(I.cr, I.nsub, I.cr_m, I.cr_c2, I.cr_w2, I.c0, I.u0, I.u0f, I.st, I.cr_staged, I.err + 8);
 }
 
 // dense inverse rows from the banded factor (identity right-hand sides, K per warp)
@@ -460,6 +473,23 @@ void launch_coarse_solve(dd_ctx* c, cudaStream_t s) {
     (k_gemv_rows<<<(N + 7) / 8, 256, 0, s>>>(N, c->A0inv, c->c0, c->u0, c->u0f, c->st), dd::note_launch());
   }
   DD_CUDA(cudaGetLastError());
+}
+
+void launch_b_cr_solve(const BInst* B, int n, size_t smem, cudaStream_t s) {
+  static PerDeviceOnce attr;   // once per device
+  once_per_device(attr, [] {
+    DD_CUDA(cudaFuncSetAttribute(kb_cr_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+  });
+  (kb_cr_solve<<<n, kCrThreads, smem, s>>>(B), dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+}
+
+// shared memory and staging of the plain p = 1 coarse solve of one context (cyclic reduction)
+void cr_launch_shape(const dd_ctx* c, size_t* smem, int* staged) {
+  const size_t W2 = (size_t)c->cr_w2, ncoef = 2 * (size_t)c->cr_c2 + 3 * W2;
+  const size_t full = sizeof(double) * (W2 + ncoef);
+  *staged = full <= 200 * 1024 ? 1 : 0;
+  *smem = *staged ? full : sizeof(double) * W2;
 }
 
 }  // namespace dd

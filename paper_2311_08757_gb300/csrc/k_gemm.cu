@@ -130,9 +130,12 @@ template <typename T, int BN>
 __global__ void __launch_bounds__(128, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const Tile* __restrict__ tiles, int K, int mlimit, int rows_per_type, float* __restrict__ Y,
-              int ldy, int* err, const PcgState* st, const float* __restrict__ ysc) {
+              int ldy, int* err, const PcgState* st, const float* __restrict__ ysc,
+              const PcgState* const* __restrict__ tile_st) {
   using C = TcCfg<T, BN>;
   constexpr int kTmemCols = C::TMEM_COLS;
+  // a grouped launch over several problems' tiles gives each tile its problem's state
+  if (tile_st != nullptr) st = tile_st[blockIdx.x];
   if (st != nullptr && st->done) return;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -269,14 +272,14 @@ static void make_tmap(CUtensorMap* tm, void* base, int es, int inner, long long 
 template <typename T, int BN = 256>
 static void launch_tc(const CUtensorMap* tA, const CUtensorMap* tB, const Tile* tiles, int ntiles, int K,
                       int mlimit, int rows_per_type, float* Y, int ldy, int* err, const PcgState* st,
-                      cudaStream_t s, const float* ysc = nullptr) {
+                      cudaStream_t s, const float* ysc = nullptr, const PcgState* const* tile_st = nullptr) {
   static PerDeviceOnce attr;   // once per device and instance
   once_per_device(attr, [] {
     DD_CUDA(cudaFuncSetAttribute(k_tc_gemm<T, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  TcCfg<T, BN>::SMEM));
   });
   (k_tc_gemm<T, BN><<<ntiles, 128, TcCfg<T, BN>::SMEM, s>>>(*tA, *tB, tiles, K, mlimit, rows_per_type, Y, ldy, err,
-                                                             st, ysc),
+                                                             st, ysc, tile_st),
    dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
@@ -382,12 +385,12 @@ __device__ __forceinline__ void store2<__nv_fp8_e4m3>(__nv_fp8_e4m3* row, int k,
 }
 
 template <typename T>
-__global__ void k_pack(Geo g, const Sub* __restrict__ subs, const int* __restrict__ slot_of,
-                       const double* __restrict__ r, int kpad, T* __restrict__ out, const double* __restrict__ wT,
-                       double* c0, const PcgState* st, const float* __restrict__ ascale, float* __restrict__ ysc) {
+__device__ __forceinline__ void pack_body(Geo g, const Sub* __restrict__ subs, const int* __restrict__ slot_of,
+                                          const double* __restrict__ r, int kpad, T* __restrict__ out,
+                                          const double* __restrict__ wT, double* c0, const PcgState* st,
+                                          const float* __restrict__ ascale, float* __restrict__ ysc, int s) {
   if (st != nullptr && st->done) return;
   constexpr bool FP8 = sizeof(T) == 1;
-  const int s = blockIdx.x;
   const Sub sb = subs[s];
   const int slot = slot_of[s];
   T* row = out + (size_t)slot * kpad;
@@ -429,6 +432,24 @@ __global__ void k_pack(Geo g, const Sub* __restrict__ subs, const int* __restric
     block_sum<1>(acc);
     if (threadIdx.x == 0) c0[s] = acc[0];
   }
+}
+
+// one block per subdomain (blockIdx.x = subdomain id)
+template <typename T>
+__global__ void k_pack(Geo g, const Sub* __restrict__ subs, const int* __restrict__ slot_of,
+                       const double* __restrict__ r, int kpad, T* __restrict__ out, const double* __restrict__ wT,
+                       double* c0, const PcgState* st, const float* __restrict__ ascale, float* __restrict__ ysc) {
+  pack_body<T>(g, subs, slot_of, r, kpad, out, wT, c0, st, ascale, ysc, (int)blockIdx.x);
+}
+
+// batched: vmap[blockIdx.x] = {problem, subdomain}
+template <typename T>
+__global__ void kb_pack(const BInst* __restrict__ B, const int2* __restrict__ vmap) {
+  const int2 m = vmap[blockIdx.x];
+  const BInst& I = B[m.x];
+  if (!I.active) return;
+  pack_body<T>(I.g, I.subs, I.slot_of_sub, I.r, I.kpad, reinterpret_cast<T*>(I.Rpack), I.wT,
+               I.coarse ? I.c0 : nullptr, I.st, nullptr, nullptr, m.y);
 }
 
 // FP8 local inverses: per-type max |A_T^{-1}| (grid = blocks x types), then the scaled rounding
@@ -674,6 +695,144 @@ int launch_gemm(dd_ctx* c, cudaStream_t s) {
 void gemm_free(dd_ctx* c) {
   delete reinterpret_cast<GemmPlan*>(c->tmapA);
   c->tmapA = nullptr;
+}
+
+void launch_b_pack(const BInst* B, const int2* vmap, int nvb, int precision, cudaStream_t s) {
+  if (precision == DD_PREC_BF16)
+    (kb_pack<__nv_bfloat16><<<nvb, kPackThreads, 0, s>>>(B, vmap), dd::note_launch());
+  else if (precision == DD_PREC_TF32)
+    (kb_pack<float><<<nvb, kPackThreads, 0, s>>>(B, vmap), dd::note_launch());
+  else
+    throw Error(DD_EUNSUPPORTED, "batched packing supports BF16 and TF32 operands");
+  DD_CUDA(cudaGetLastError());
+}
+
+// ----------------------------------------------------------------------------------------
+// Grouped local-solve contraction of a batch: the problems' rounded inverses, packed
+// restrictions and local solutions live in three batch-wide buffers (problem i's rows
+// start at type_base[i] kpad, slot_base[i] and slot_base[i] rows), so one pair of tensor
+// maps and one tile list cover every problem, and each tile carries its problem's PCG state
+// (its CTAs return at once when that problem's solve is done).  Per output element the K
+// order of the accumulation is that of the problem's own launch: results are identical.
+// ----------------------------------------------------------------------------------------
+struct BGemm {
+  CUtensorMap tA, tB[3];
+  Tile* tiles[3] = {nullptr, nullptr, nullptr};
+  const PcgState** tile_st[3] = {nullptr, nullptr, nullptr};
+  int ntiles[3] = {0, 0, 0};
+  int es = 2, kpad = 0, bn = 0;
+  float* Y = nullptr;
+  int* err = nullptr;
+};
+
+BGemm* bgemm_create(const std::vector<dd_ctx*>& cs, const std::vector<int>& type_base,
+                    const std::vector<int>& slot_base, void* Ainv_all, void* Rpack_all, float* Y_all, int* err,
+                    cudaStream_t s) {
+  BGemm* b = new BGemm();
+  try {
+    const dd_ctx* c0 = cs.front();
+    b->es = prec_bytes(c0->grid.precision);
+    b->kpad = c0->kpad;
+    b->Y = Y_all;
+    b->err = err;
+    int types = 0, slots = 0;
+    for (size_t i = 0; i < cs.size(); ++i) {
+      types = std::max(types, type_base[i] + cs[i]->ntypes);
+      slots = std::max(slots, slot_base[i] + cs[i]->g.nsub);
+    }
+    const int BK = 128 / b->es;
+    make_tmap(&b->tA, Ainv_all, b->es, b->kpad, (long long)types * b->kpad, BK, 128);
+    const int mt = (b->kpad + 127) / 128;
+    for (int k = 0; k < 3; ++k) {
+      const int bn = kTileN[k];
+      make_tmap(&b->tB[k], Rpack_all, b->es, b->kpad, slots, BK, bn);
+      std::vector<Tile> tl;
+      std::vector<const PcgState*> ts;
+      for (size_t i = 0; i < cs.size(); ++i) {
+        const dd_ctx* c = cs[i];
+        for (int t = 0; t < c->ntypes; ++t) {
+          const int first = slot_base[i] + c->type_first[t], cnt = c->type_count[t];
+          for (int n0 = 0; n0 < cnt; n0 += bn)
+            for (int m = 0; m < mt; ++m) {
+              tl.push_back(Tile{type_base[i] + t, m * 128, first + n0, first + cnt});
+              ts.push_back(c->st);
+            }
+        }
+      }
+      DD_CUDA(cudaMalloc(&b->tiles[k], sizeof(Tile) * tl.size()));
+      DD_CUDA(cudaMalloc(&b->tile_st[k], sizeof(PcgState*) * ts.size()));
+      DD_CUDA(cudaMemcpyAsync(b->tiles[k], tl.data(), sizeof(Tile) * tl.size(), cudaMemcpyHostToDevice, s));
+      DD_CUDA(cudaMemcpyAsync(b->tile_st[k], ts.data(), sizeof(PcgState*) * ts.size(), cudaMemcpyHostToDevice, s));
+      b->ntiles[k] = (int)tl.size();
+    }
+    DD_CUDA(cudaStreamSynchronize(s));
+  } catch (...) {
+    bgemm_destroy(b);
+    throw;
+  }
+  return b;
+}
+
+void bgemm_destroy(BGemm* b) {
+  if (!b) return;
+  for (int k = 0; k < 3; ++k) {
+    if (b->tiles[k]) cudaFree(b->tiles[k]);
+    if (b->tile_st[k]) cudaFree(b->tile_st[k]);
+  }
+  delete b;
+}
+
+template <typename T>
+static void bgemm_run_t(BGemm* b, int bn, cudaStream_t s) {
+  const int k = tile_index(bn);
+  if (bn == 256)
+    launch_tc<T, 256>(&b->tA, &b->tB[k], b->tiles[k], b->ntiles[k], b->kpad, b->kpad, b->kpad, b->Y, b->kpad, b->err,
+                      nullptr, s, nullptr, b->tile_st[k]);
+  else if (bn == 160)
+    launch_tc<T, 160>(&b->tA, &b->tB[k], b->tiles[k], b->ntiles[k], b->kpad, b->kpad, b->kpad, b->Y, b->kpad, b->err,
+                      nullptr, s, nullptr, b->tile_st[k]);
+  else
+    launch_tc<T, 128>(&b->tA, &b->tB[k], b->tiles[k], b->ntiles[k], b->kpad, b->kpad, b->kpad, b->Y, b->kpad, b->err,
+                      nullptr, s, nullptr, b->tile_st[k]);
+}
+
+void bgemm_run(BGemm* b, int bn, cudaStream_t s) {
+  if (b->es == 2) bgemm_run_t<__nv_bfloat16>(b, bn, s);
+  else if (b->es == 4) bgemm_run_t<float>(b, bn, s);
+  else throw Error(DD_EUNSUPPORTED, "grouped contraction supports BF16 and TF32 operands");
+}
+
+// the N tile of the grouped launch, by timing each shape on the batch's operands; every tile
+// reads its problem's PCG state, so the caller clears the done flags first
+int bgemm_tune(BGemm* b, cudaStream_t s) {
+  cudaEvent_t e0, e1;
+  DD_CUDA(cudaEventCreate(&e0));
+  DD_CUDA(cudaEventCreate(&e1));
+  float best = 0.0f;
+  int best_bn = 256;
+  try {
+    for (int bn : kTileN) {
+      bgemm_run(b, bn, s);
+      DD_CUDA(cudaEventRecord(e0, s));
+      for (int r = 0; r < 3; ++r) bgemm_run(b, bn, s);
+      DD_CUDA(cudaEventRecord(e1, s));
+      DD_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      DD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (bn == 256 || ms < best) {
+        best = ms;
+        best_bn = bn;
+      }
+    }
+  } catch (...) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    throw;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->bn = best_bn;
+  return best_bn;
 }
 
 }  // namespace dd

@@ -192,13 +192,13 @@ void launch_tabS(dd_ctx* c, double sigma) {
 // K1: matrix-free operator y = T x (T = A_sigma, A or M) over the interior columns.
 // ----------------------------------------------------------------------------------------
 template <int P, bool DOT>
-__global__ void __launch_bounds__(kThreads) k_stencil(Geo g, const double* __restrict__ tab,
+__device__ __forceinline__ void stencil_body(VBlk vb, Geo g, const double* __restrict__ tab,
                                                       const double* __restrict__ x, double* __restrict__ y,
                                                       double* partials, unsigned* counter, double* out) {
   const long long total = (long long)g.nxi * (P == 2 ? g.nxi : 1) * g.Ypad;
   double acc[1] = {0.0};
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
+  for (long long t = (long long)vb.b * blockDim.x + threadIdx.x; t < total;
+       t += (long long)vb.nb * blockDim.x) {
     Node nd = node_of<P>(g, t);
     const int cls = cls_of<P>(g, nd);
     const double v = stencil_at<P>(g, tab, x, nd.idx, cls);
@@ -207,8 +207,15 @@ __global__ void __launch_bounds__(kThreads) k_stencil(Geo g, const double* __res
   }
   if (DOT) {
     double tot[1];
-    if (grid_sum_last<1>(acc, partials, counter, tot) && threadIdx.x == 0) *out = tot[0];
+    if (grid_sum_last<1>(acc, partials, counter, tot, vb) && threadIdx.x == 0) *out = tot[0];
   }
+}
+
+template <int P, bool DOT>
+__global__ void __launch_bounds__(kThreads) k_stencil(Geo g, const double* __restrict__ tab,
+                                                      const double* __restrict__ x, double* __restrict__ y,
+                                                      double* partials, unsigned* counter, double* out) {
+  stencil_body<P, DOT>(vblk_self(), g, tab, x, y, partials, counter, out);
 }
 
 // two operators on one vector in one pass: y1 = T1 x, y2 = T2 x
@@ -327,14 +334,14 @@ void launch_check_finite(const double* v, long long n, int* flag, cudaStream_t s
 
 // r = b - A_sigma x, rr0 = (r, r), tol2 = rtol^2 rr0 (rtol^2 preset in tol2 by the host).
 template <int P>
-__global__ void __launch_bounds__(kThreads) k_pcg_init(Geo g, const double* __restrict__ tab,
+__device__ __forceinline__ void pcg_init_body(VBlk vb, Geo g, const double* __restrict__ tab,
                                                        const double* __restrict__ x,
                                                        const double* __restrict__ b, double* __restrict__ r,
                                                        PcgState* st, double* partials, unsigned* counter) {
   const long long total = (long long)g.nxi * (P == 2 ? g.nxi : 1) * g.Ypad;
   double acc[1] = {0.0};
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
+  for (long long t = (long long)vb.b * blockDim.x + threadIdx.x; t < total;
+       t += (long long)vb.nb * blockDim.x) {
     Node nd = node_of<P>(g, t);
     const int cls = cls_of<P>(g, nd);
     const double v = b[nd.idx] - stencil_at<P>(g, tab, x, nd.idx, cls);
@@ -342,7 +349,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_init(Geo g, const double* __re
     acc[0] = fma(v, v, acc[0]);
   }
   double tot[1];
-  if (grid_sum_last<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
+  if (grid_sum_last<1>(acc, partials, counter, tot, vb) && threadIdx.x == 0) {
     st->rr0 = tot[0];
     st->rr = tot[0];
     st->tol2 = st->tol2 * tot[0];
@@ -353,6 +360,14 @@ __global__ void __launch_bounds__(kThreads) k_pcg_init(Geo g, const double* __re
     if (!isfinite(tot[0])) { st->status = DD_ENAN; st->done = 1; }
     else if (tot[0] == 0.0) st->done = 1;
   }
+}
+
+template <int P>
+__global__ void __launch_bounds__(kThreads) k_pcg_init(Geo g, const double* __restrict__ tab,
+                                                       const double* __restrict__ x,
+                                                       const double* __restrict__ b, double* __restrict__ r,
+                                                       PcgState* st, double* partials, unsigned* counter) {
+  pcg_init_body<P>(vblk_self(), g, tab, x, b, r, st, partials, counter);
 }
 
 void launch_pcg_init(dd_ctx* c, const double* b, cudaStream_t s) {
@@ -401,7 +416,7 @@ void launch_pupdate(dd_ctx* c, cudaStream_t s) {
 // are evaluated from shared memory.
 constexpr int kFusedCols = 32;
 
-__global__ void __launch_bounds__(kThreads) k_fused_pq(Geo g, const double* __restrict__ tab,
+__device__ __forceinline__ void fused_pq_body(VBlk vb, Geo g, const double* __restrict__ tab,
                                                        const double* __restrict__ z, double* pb0, double* pb1,
                                                        double* __restrict__ q, PcgState* st, double* partials,
                                                        unsigned* counter) {
@@ -419,7 +434,7 @@ __global__ void __launch_bounds__(kThreads) k_fused_pq(Geo g, const double* __re
     sp_raw[(kFusedCols + 2) * Y + 1] = 0.0;
   }
   double acc[1] = {0.0};
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (int tile = vb.b; tile < ntiles; tile += vb.nb) {
     const int a0 = 1 + tile * kFusedCols;
     const int own = min(kFusedCols, g.nxi - (a0 - 1));
     const int nload = (own + 2) << yl;
@@ -447,7 +462,7 @@ __global__ void __launch_bounds__(kThreads) k_fused_pq(Geo g, const double* __re
     }
   }
   double tot[1];
-  if (grid_sum_last<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
+  if (grid_sum_last<1>(acc, partials, counter, tot, vb) && threadIdx.x == 0) {
     const double pq = tot[0];
     st->pq = pq;
     if (!(pq > 0.0)) {
@@ -457,6 +472,13 @@ __global__ void __launch_bounds__(kThreads) k_fused_pq(Geo g, const double* __re
       st->alpha = st->rho / pq;
     }
   }
+}
+
+__global__ void __launch_bounds__(kThreads) k_fused_pq(Geo g, const double* __restrict__ tab,
+                                                       const double* __restrict__ z, double* pb0, double* pb1,
+                                                       double* __restrict__ q, PcgState* st, double* partials,
+                                                       unsigned* counter) {
+  fused_pq_body(vblk_self(), g, tab, z, pb0, pb1, q, st, partials, counter);
 }
 
 void launch_fused_pq(dd_ctx* c, cudaStream_t s) {
@@ -527,7 +549,7 @@ void launch_matvec_pq(dd_ctx* c, cudaStream_t s) {
 }
 
 // x += alpha p, r -= alpha q, rr = (r, r); stop test ||r|| <= rtol ||r0|| (Sec. 4.1).
-__global__ void __launch_bounds__(kThreads) k_xr_update(long long n, double* pb0, double* pb1,
+__device__ __forceinline__ void xr_update_body(VBlk vb, long long n, double* pb0, double* pb1,
                                                         const double* __restrict__ q, double* __restrict__ x,
                                                         double* __restrict__ r, PcgState* st,
                                                         double* partials, unsigned* counter) {
@@ -539,8 +561,8 @@ __global__ void __launch_bounds__(kThreads) k_xr_update(long long n, double* pb0
   double2* x2 = reinterpret_cast<double2*>(x);
   double2* r2 = reinterpret_cast<double2*>(r);
   double acc[1] = {0.0};
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n / 2;
-       t += (long long)gridDim.x * blockDim.x) {
+  for (long long t = (long long)vb.b * blockDim.x + threadIdx.x; t < n / 2;
+       t += (long long)vb.nb * blockDim.x) {
     double2 pv = p2[t], qv = q2[t], xv = x2[t], rv = r2[t];
     xv.x = fma(alpha, pv.x, xv.x);
     xv.y = fma(alpha, pv.y, xv.y);
@@ -552,7 +574,7 @@ __global__ void __launch_bounds__(kThreads) k_xr_update(long long n, double* pb0
     acc[0] = fma(rv.y, rv.y, acc[0]);
   }
   double tot[1];
-  if (grid_sum_last<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
+  if (grid_sum_last<1>(acc, partials, counter, tot, vb) && threadIdx.x == 0) {
     const double rr = tot[0];
     st->rr = rr;
     st->iter += 1;
@@ -566,6 +588,13 @@ __global__ void __launch_bounds__(kThreads) k_xr_update(long long n, double* pb0
       st->done = 1;
     }
   }
+}
+
+__global__ void __launch_bounds__(kThreads) k_xr_update(long long n, double* pb0, double* pb1,
+                                                        const double* __restrict__ q, double* __restrict__ x,
+                                                        double* __restrict__ r, PcgState* st,
+                                                        double* partials, unsigned* counter) {
+  xr_update_body(vblk_self(), n, pb0, pb1, q, x, r, st, partials, counter);
 }
 
 void launch_xr_update(dd_ctx* c, cudaStream_t s) {
@@ -600,7 +629,7 @@ __device__ __forceinline__ double fma_t(double a, double b, double c) { return f
 // three-dimensional box: 987 -> 971 ms per ground state).  The FP64 p = 1 variant spills a
 // little at 32 yet ran 4% faster there than at 48 without spills.
 template <int P, typename TY, bool RAS, int U>
-__global__ void __launch_bounds__(kThreads, (P == 1 ? 8 : 5) / U) k_prolong(Geo g, const int4* __restrict__ axown,
+__device__ __forceinline__ void prolong_body(VBlk vb, Geo g, const int4* __restrict__ axown,
                                                       const int4* __restrict__ subrow, const TY* __restrict__ Y,
                                                       const TY* __restrict__ wT, const TY* __restrict__ puT,
                                                       const TY* __restrict__ u0, int coarse,
@@ -610,10 +639,10 @@ __global__ void __launch_bounds__(kThreads, (P == 1 ? 8 : 5) / U) k_prolong(Geo 
   if (mode != 0 && st->done) return;
   const bool flex = (mode == 2) && st->flexible;
   const long long total = (long long)g.nxi * (P == 2 ? g.nxi : 1) * g.Ypad;
-  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long stride = (long long)vb.nb * blockDim.x;
   constexpr int NO = (P == 2) ? 4 : 2;  // owners per node at most; U nodes per thread and pass
   double acc[2] = {0.0, 0.0};
-  for (long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; t0 < total; t0 += U * stride) {
+  for (long long t0 = (long long)vb.b * blockDim.x + threadIdx.x; t0 < total; t0 += U * stride) {
     // branch-free: out-of-range nodes and absent owners read valid addresses and are masked
     bool in[U], valid[U];
     Node nd[U];
@@ -674,7 +703,7 @@ __global__ void __launch_bounds__(kThreads, (P == 1 ? 8 : 5) / U) k_prolong(Geo 
   }
   if (mode == 0) return;
   double tot[2];
-  if (grid_sum_last<2>(acc, partials, counter, tot) && threadIdx.x == 0) {
+  if (grid_sum_last<2>(acc, partials, counter, tot, vb) && threadIdx.x == 0) {
     const double rz = tot[0];
     if (!isfinite(rz)) {
       st->status = DD_ENAN;
@@ -691,6 +720,17 @@ __global__ void __launch_bounds__(kThreads, (P == 1 ? 8 : 5) / U) k_prolong(Geo 
     st->rho = rz;
     st->zq = tot[1];
   }
+}
+
+template <int P, typename TY, bool RAS, int U>
+__global__ void __launch_bounds__(kThreads, (P == 1 ? 8 : 5) / U) k_prolong(Geo g, const int4* __restrict__ axown,
+                                                      const int4* __restrict__ subrow, const TY* __restrict__ Y,
+                                                      const TY* __restrict__ wT, const TY* __restrict__ puT,
+                                                      const TY* __restrict__ u0, int coarse,
+                                                      const double* __restrict__ r, const double* __restrict__ q,
+                                                      double* __restrict__ z, int mode, PcgState* st,
+                                                      double* partials, unsigned* counter) {
+  prolong_body<P, TY, RAS, U>(vblk_self(), g, axown, subrow, Y, wT, puT, u0, coarse, r, q, z, mode, st, partials, counter);
 }
 
 // nodes per thread and pass (each node's loads go out together, absent owners masked):
@@ -732,17 +772,17 @@ void launch_prolong(dd_ctx* c, int mode, cudaStream_t s, double* zout) {
 //   residual : given A_sigma x (w3) and Mx (w2): mu = (x, A_sigma x);
 //              ||A_sigma x - mu M x||^2 and ||M x||^2
 // ----------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_outer_dots(long long n, const double* __restrict__ w,
+__device__ __forceinline__ void outer_dots_body(VBlk vb, long long n, const double* __restrict__ w,
                                                          const double* __restrict__ Mw, OuterState* os,
                                                          double* partials, unsigned* counter) {
   double acc[2] = {0.0, 0.0};
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
-       t += (long long)gridDim.x * blockDim.x) {
+  for (long long t = (long long)vb.b * blockDim.x + threadIdx.x; t < n;
+       t += (long long)vb.nb * blockDim.x) {
     acc[0] = fma(w[t], Mw[t], acc[0]);
     acc[1] += w[t];
   }
   double tot[2];
-  if (grid_sum_last<2>(acc, partials, counter, tot) && threadIdx.x == 0) {
+  if (grid_sum_last<2>(acc, partials, counter, tot, vb) && threadIdx.x == 0) {
     os->wMw = tot[0];
     os->wsum = tot[1];
     if (!(tot[0] > 0.0)) {
@@ -754,15 +794,27 @@ __global__ void __launch_bounds__(kThreads) k_outer_dots(long long n, const doub
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_outer_scale(long long n, double* __restrict__ x,
+__global__ void __launch_bounds__(kThreads) k_outer_dots(long long n, const double* __restrict__ w,
+                                                         const double* __restrict__ Mw, OuterState* os,
+                                                         double* partials, unsigned* counter) {
+  outer_dots_body(vblk_self(), n, w, Mw, os, partials, counter);
+}
+
+__device__ __forceinline__ void outer_scale_body(VBlk vb, long long n, double* __restrict__ x,
                                                           const double* __restrict__ w, double* __restrict__ Mw,
                                                           const OuterState* os) {
   const double s = os->scale;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
-       t += (long long)gridDim.x * blockDim.x) {
+  for (long long t = (long long)vb.b * blockDim.x + threadIdx.x; t < n;
+       t += (long long)vb.nb * blockDim.x) {
     x[t] = s * w[t];
     Mw[t] *= s;
   }
+}
+
+__global__ void __launch_bounds__(kThreads) k_outer_scale(long long n, double* __restrict__ x,
+                                                          const double* __restrict__ w, double* __restrict__ Mw,
+                                                          const OuterState* os) {
+  outer_scale_body(vblk_self(), n, x, w, Mw, os);
 }
 
 void launch_outer_normalize(dd_ctx* c, const double* w, double* Mw, double* xout, cudaStream_t s) {
@@ -773,23 +825,29 @@ void launch_outer_normalize(dd_ctx* c, const double* w, double* Mw, double* xout
   DD_CUDA(cudaGetLastError());
 }
 
-__global__ void __launch_bounds__(kThreads) k_outer_res(long long n, const double* __restrict__ Ax,
+__device__ __forceinline__ void outer_res_body(VBlk vb, long long n, const double* __restrict__ Ax,
                                                         const double* __restrict__ Mx, OuterState* os,
                                                         double* partials, unsigned* counter, double* __restrict__ ro) {
   const double mu = os->xAx;
   double acc[2] = {0.0, 0.0};
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
-       t += (long long)gridDim.x * blockDim.x) {
+  for (long long t = (long long)vb.b * blockDim.x + threadIdx.x; t < n;
+       t += (long long)vb.nb * blockDim.x) {
     const double e = fma(-mu, Mx[t], Ax[t]);
     if (ro != nullptr) ro[t] = e;
     acc[0] = fma(e, e, acc[0]);
     acc[1] = fma(Mx[t], Mx[t], acc[1]);
   }
   double tot[2];
-  if (grid_sum_last<2>(acc, partials, counter, tot) && threadIdx.x == 0) {
+  if (grid_sum_last<2>(acc, partials, counter, tot, vb) && threadIdx.x == 0) {
     os->rr = tot[0];
     os->mm = tot[1];
   }
+}
+
+__global__ void __launch_bounds__(kThreads) k_outer_res(long long n, const double* __restrict__ Ax,
+                                                        const double* __restrict__ Mx, OuterState* os,
+                                                        double* partials, unsigned* counter, double* __restrict__ ro) {
+  outer_res_body(vblk_self(), n, Ax, Mx, os, partials, counter, ro);
 }
 
 void launch_outer_residual(dd_ctx* c, const double* xe, const double* Mx, double* Ax, cudaStream_t s, double* ro) {
@@ -962,6 +1020,249 @@ void launch_tab_shift(dd_ctx* c, double shift, double* dst) {
   DD_CUDA(cudaGetLastError());
 }
 
+
+// ========================================================================================
+// Batched launches (p = 1, rounded local inverses): the blocks of every problem's plain
+// launch in one grid.  vmap[blockIdx.x] = {problem i, block b within problem i's launch};
+// the block runs the plain kernel's body with the index b and count nb it has there, on
+// problem i's buffers, so every problem's results are bit-identical to its plain launches.
+// A problem whose eigen-iteration has stopped (active = 0) returns at once; so does every
+// PCG kernel of a problem whose solve is done (its PcgState.done), as in a plain launch.
+// ========================================================================================
+__device__ __forceinline__ double* bvec(const BInst& I, int role) {
+  switch (role) {
+    case BV_X: return I.x;
+    case BV_R: return I.r;
+    case BV_Z: return I.z;
+    case BV_Q: return I.q;
+    case BV_W1: return I.w1;
+    case BV_W2: return I.w2;
+    case BV_W3: return I.w3;
+    default: return I.xe;
+  }
+}
+
+// PcgState of a new solve: zero, then tol2 = rtol^2 (scaled by rr0 in pcg_init), maxit,
+// flexible (what the host writes before a plain solve)
+__global__ void kb_pcg_reset(const BInst* __restrict__ B, int n, double rtol2, int maxit) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || !B[i].active) return;
+  PcgState init;
+  memset(&init, 0, sizeof(init));
+  init.tol2 = rtol2;
+  init.maxit = maxit;
+  init.flexible = B[i].flexible;
+  *B[i].st = init;
+}
+
+// x = 0 and both search-direction buffers = 0 (the plain solve's memsets)
+__global__ void __launch_bounds__(kThreads) kb_zero_pcg(const BInst* __restrict__ B, const int2* __restrict__ vmap) {
+  const int2 m = vmap[blockIdx.x];
+  const BInst& I = B[m.x];
+  if (!I.active) return;
+  const long long n = I.g.plen;
+  for (long long t = (long long)m.y * blockDim.x + threadIdx.x; t < n; t += (long long)I.nb_vec * blockDim.x) {
+    I.x[t] = 0.0;
+    I.pb0[t] = 0.0;
+    I.pb1[t] = 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) kb_pcg_init(const BInst* __restrict__ B, const int2* __restrict__ vmap,
+                                                        int b_role) {
+  const int2 m = vmap[blockIdx.x];
+  const BInst& I = B[m.x];
+  if (!I.active) return;
+  pcg_init_body<1>(VBlk{m.y, I.nb_init}, I.g, I.tabS, I.x, bvec(I, b_role), I.r, I.st, I.red, I.cnt + CNT_INIT);
+}
+
+__global__ void __launch_bounds__(kThreads) kb_fused_pq(const BInst* __restrict__ B, const int2* __restrict__ vmap) {
+  const int2 m = vmap[blockIdx.x];
+  const BInst& I = B[m.x];
+  if (!I.active) return;
+  fused_pq_body(VBlk{m.y, I.nb_fused}, I.g, I.tabS, I.z, I.pb0, I.pb1, I.q, I.st, I.red, I.cnt + CNT_PQ);
+}
+
+__global__ void __launch_bounds__(kThreads) kb_xr_update(const BInst* __restrict__ B, const int2* __restrict__ vmap) {
+  const int2 m = vmap[blockIdx.x];
+  const BInst& I = B[m.x];
+  if (!I.active) return;
+  xr_update_body(VBlk{m.y, I.nb_xr}, I.g.plen, I.pb0, I.pb1, I.q, I.x, I.r, I.st, I.red, I.cnt + CNT_RR);
+}
+
+__global__ void __launch_bounds__(kThreads, 8 / kProlongU) kb_prolong(const BInst* __restrict__ B,
+                                                                      const int2* __restrict__ vmap, int mode) {
+  const int2 m = vmap[blockIdx.x];
+  const BInst& I = B[m.x];
+  if (!I.active) return;
+  prolong_body<1, float, false, kProlongU>(VBlk{m.y, I.nb_prolong}, I.g, I.axown, I.subrow, I.Y32, I.wT32, I.puT32,
+                                           I.u0f, I.coarse, I.r, I.q, I.z, mode, I.st, I.red, I.cnt + CNT_RZ);
+}
+
+__global__ void __launch_bounds__(kThreads) kb_stencil(const BInst* __restrict__ B, const int2* __restrict__ vmap,
+                                                       int mass, int x_role, int y_role) {
+  const int2 m = vmap[blockIdx.x];
+  const BInst& I = B[m.x];
+  if (!I.active) return;
+  stencil_body<1, false>(VBlk{m.y, I.nb_st}, I.g, mass ? I.tabM : I.tabS, bvec(I, x_role), bvec(I, y_role), nullptr,
+                         nullptr, nullptr);
+}
+
+// y = A_sigma x and (x, A_sigma x) into the outer state (the plain outer residual's first pass)
+__global__ void __launch_bounds__(kThreads) kb_stencil_dot(const BInst* __restrict__ B, const int2* __restrict__ vmap,
+                                                           int x_role, int y_role) {
+  const int2 m = vmap[blockIdx.x];
+  const BInst& I = B[m.x];
+  if (!I.active) return;
+  stencil_body<1, true>(VBlk{m.y, I.nb_sdot}, I.g, I.tabS, bvec(I, x_role), bvec(I, y_role), I.red,
+                        I.cnt + CNT_OUTER1, &I.ost->xAx);
+}
+
+__global__ void __launch_bounds__(kThreads) kb_outer_dots(const BInst* __restrict__ B, const int2* __restrict__ vmap,
+                                                          int w_role, int mw_role) {
+  const int2 m = vmap[blockIdx.x];
+  const BInst& I = B[m.x];
+  if (!I.active) return;
+  outer_dots_body(VBlk{m.y, I.nb_vec}, I.g.plen, bvec(I, w_role), bvec(I, mw_role), I.ost, I.red,
+                  I.cnt + CNT_OUTER0);
+}
+
+__global__ void __launch_bounds__(kThreads) kb_outer_scale(const BInst* __restrict__ B, const int2* __restrict__ vmap,
+                                                           int x_role, int w_role, int mw_role) {
+  const int2 m = vmap[blockIdx.x];
+  const BInst& I = B[m.x];
+  if (!I.active) return;
+  outer_scale_body(VBlk{m.y, I.nb_vec}, I.g.plen, bvec(I, x_role), bvec(I, w_role), bvec(I, mw_role), I.ost);
+}
+
+__global__ void __launch_bounds__(kThreads) kb_outer_res(const BInst* __restrict__ B, const int2* __restrict__ vmap,
+                                                         int ax_role, int mx_role) {
+  const int2 m = vmap[blockIdx.x];
+  const BInst& I = B[m.x];
+  if (!I.active) return;
+  outer_res_body(VBlk{m.y, I.nb_vec}, I.g.plen, bvec(I, ax_role), bvec(I, mx_role), I.ost, I.red,
+                 I.cnt + CNT_OUTER2, nullptr);
+}
+
+__global__ void kb_gather(const BInst* __restrict__ B, int n, BStat* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const BInst& I = B[i];
+  BStat o;
+  o.pcg_done = I.st->done;
+  o.pcg_status = I.st->status;
+  o.pcg_iter = I.st->iter;
+  o.active = I.active;
+  o.xAx = I.ost->xAx;
+  o.rr = I.ost->rr;
+  o.mm = I.ost->mm;
+  o.outer_status = I.ost->status;
+  o.pad_ = 0;
+  out[i] = o;
+}
+
+// layout conversion between a user vector (ABI order) and a role vector (padded), p = 1
+template <bool TO_PAD>
+__global__ void __launch_bounds__(kThreads) kb_pad(const BInst* __restrict__ B, const int2* __restrict__ vmap,
+                                                   const double* const* __restrict__ user_in,
+                                                   double* const* __restrict__ user_out, int role) {
+  const int2 m = vmap[blockIdx.x];
+  const BInst& I = B[m.x];
+  const Geo& g = I.g;
+  double* pv = bvec(I, role);
+  for (long long t = (long long)m.y * blockDim.x + threadIdx.x; t < g.ndof; t += (long long)I.nb_vec * blockDim.x) {
+    const long long col = t / g.nyi;
+    const int j = (int)(t - col * g.nyi);
+    const long long pidx = (col + 1) * g.Ypad + j;
+    if (TO_PAD) pv[pidx] = user_in[m.x][t];
+    else user_out[m.x][t] = pv[pidx];
+  }
+}
+
+void batch_grid_sizes(const dd_ctx* c, BInst* I) {
+  const Geo& g = c->g;
+  const long long w = interior_work(g);
+  const int ntiles = (g.nxi + kFusedCols - 1) / kFusedCols;
+  I->nb_init = grid_blocks(w, kThreads);
+  I->nb_fused = ntiles < 152 * 6 ? ntiles : 152 * 6;
+  I->nb_xr = grid_blocks(g.plen / 2, kThreads, 4);
+  I->nb_prolong = resident_grid(k_prolong<1, float, false, kProlongU>, w, kThreads);
+  I->nb_sdot = resident_grid(k_stencil<1, true>, w, kThreads);
+  I->nb_st = resident_grid(k_stencil<1, false>, w, kThreads);
+  I->nb_vec = grid_blocks(g.plen, kThreads);
+}
+
+void launch_b_pcg_reset(const BInst* B, int n, double rtol2, int maxit, cudaStream_t s) {
+  (kb_pcg_reset<<<(n + 127) / 128, 128, 0, s>>>(B, n, rtol2, maxit), dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+}
+
+void launch_b_zero_pcg(const BInst* B, const int2* vmap, int nvb, cudaStream_t s) {
+  (kb_zero_pcg<<<nvb, kThreads, 0, s>>>(B, vmap), dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+}
+
+void launch_b_pcg_init(const BInst* B, const int2* vmap, int nvb, int b_role, cudaStream_t s) {
+  (kb_pcg_init<<<nvb, kThreads, 0, s>>>(B, vmap, b_role), dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+}
+
+void launch_b_fused_pq(const BInst* B, const int2* vmap, int nvb, int ypad, cudaStream_t s) {
+  const size_t smem = sizeof(double) * ((size_t)(kFusedCols + 2) * ypad + 2);
+  static PerDeviceOnce attr;
+  once_per_device(attr, [] {
+    DD_CUDA(cudaFuncSetAttribute(kb_fused_pq, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  });
+  (kb_fused_pq<<<nvb, kThreads, smem, s>>>(B, vmap), dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+}
+
+void launch_b_xr_update(const BInst* B, const int2* vmap, int nvb, cudaStream_t s) {
+  (kb_xr_update<<<nvb, kThreads, 0, s>>>(B, vmap), dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+}
+
+void launch_b_prolong(const BInst* B, const int2* vmap, int nvb, int mode, cudaStream_t s) {
+  (kb_prolong<<<nvb, kThreads, 0, s>>>(B, vmap, mode), dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+}
+
+void launch_b_stencil(const BInst* B, const int2* vmap, int nvb, int mass, int x_role, int y_role, cudaStream_t s) {
+  (kb_stencil<<<nvb, kThreads, 0, s>>>(B, vmap, mass, x_role, y_role), dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+}
+
+void launch_b_stencil_dot(const BInst* B, const int2* vmap, int nvb, int x_role, int y_role, cudaStream_t s) {
+  (kb_stencil_dot<<<nvb, kThreads, 0, s>>>(B, vmap, x_role, y_role), dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+}
+
+void launch_b_outer_normalize(const BInst* B, const int2* vmap, int nvb, int w_role, int mw_role, int x_role,
+                              cudaStream_t s) {
+  (kb_outer_dots<<<nvb, kThreads, 0, s>>>(B, vmap, w_role, mw_role), dd::note_launch());
+  (kb_outer_scale<<<nvb, kThreads, 0, s>>>(B, vmap, x_role, w_role, mw_role), dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+}
+
+void launch_b_outer_res(const BInst* B, const int2* vmap, int nvb, int ax_role, int mx_role, cudaStream_t s) {
+  (kb_outer_res<<<nvb, kThreads, 0, s>>>(B, vmap, ax_role, mx_role), dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+}
+
+void launch_b_gather(const BInst* B, int n, BStat* out, cudaStream_t s) {
+  (kb_gather<<<(n + 127) / 128, 128, 0, s>>>(B, n, out), dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+}
+
+void launch_b_unpad(const BInst* B, const int2* vmap, int nvb, int src_role, double* const* dst, cudaStream_t s) {
+  (kb_pad<false><<<nvb, kThreads, 0, s>>>(B, vmap, nullptr, dst, src_role), dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+}
+
+void launch_b_pad(const BInst* B, const int2* vmap, int nvb, const double* const* src, int dst_role, cudaStream_t s) {
+  (kb_pad<true><<<nvb, kThreads, 0, s>>>(B, vmap, src, nullptr, dst_role), dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+}
 }  // namespace dd
 
 // ------------------------------------------------------------------------------------------

@@ -26,13 +26,17 @@ def test_small_batch_matches_oracle_and_single_calls(method, precision):
     phis = [gpu_vec(np.zeros(w.dofs)) for w in ws]
     with _batch(ws, precision) as b:
         res = b.ground_states(method, threads=4, phi=phis)
+        info = b.info()
+    # the inverse iteration of the mixed form runs as batched kernels over all instances
+    assert info["batchable"] == (precision == "bf16")
+    assert info["last_batched"] == (precision == "bf16" and method == "ipm")
     for i, w in enumerate(ws):
         P = oracle_problem(w, build_prec=False)
         lam_ex, _ = solvers.exact_ground_state(P.A, P.M, sigma=P.sigma, dense_limit=3000 if w.dofs <= 3000 else 0)
         assert abs(res["lambda"][i] - lam_ex) <= 1e-10 * abs(lam_ex), (i, w.L)
         xh = host(phis[i])
         Mx = P.M @ xh
-        assert np.linalg.norm(P.A @ xh - res["lambda"][i] * Mx) / (abs(lam_ex) * np.linalg.norm(Mx)) <= 1.5e-8
+        assert np.linalg.norm(P.A @ xh - res["lambda"][i] * Mx) / (abs(lam_ex) * np.linalg.norm(Mx)) <= 1e-8 + 1e-12
         # the single-instance path gives the same bits
         with make_solver(w, precision=precision) as es:
             es.prepare()
@@ -54,6 +58,7 @@ def test_full_batched_workload():
     order = np.argsort([w.L for w in ws])
     with _batch(ws) as b:
         res = b.ground_states("ipm")
+        assert b.info()["last_batched"] == 1 and b.info()["gemm_tile_n"] in (128, 160, 256)
         for i, w in enumerate(ws):
             ctx = b.context(i)
             x = torch.ones(w.dofs, dtype=torch.float64, device="cuda")
@@ -65,7 +70,7 @@ def test_full_batched_workload():
             dd.dd_apply_operator(ctx, dd.DD_OP_A, x, Ax)
             dd.dd_apply_operator(ctx, dd.DD_OP_MASS, x, Mx)
             eta = float(torch.linalg.norm(Ax - lam * Mx) / (abs(lam) * torch.linalg.norm(Mx)))
-            assert eta <= 1.5e-8, (i, w.L)
+            assert eta <= 1e-8 + 1e-12, (i, w.L)
     for i in order[:3]:
         w = ws[i]
         P = oracle_problem(w, build_prec=False)
@@ -78,3 +83,27 @@ def test_full_batched_workload():
             x = gpu_vec(np.ones(w.dofs))
             lam, outer, tot, mx = dd.dd_inverse_iterate(es.ctx, x)
         assert lam == res["lambda"][i] and tot == res["inner"][i]
+
+
+def test_batched_kernels_equal_concurrent_pipelines():
+    """The batched inverse iteration (one launch per kernel over all instances, one graph per
+    block of iterations, lockstep outer steps) and the concurrent per-instance pipelines give
+    the same bits, instance by instance, and the phi they return are M-normalised ground
+    states; the batched one launches far fewer kernels."""
+    ws = batch_workloads(seed=7, count=12, L_min=3, L_max=300, n=32, overlap=4)
+    out = {}
+    for method in ("ipm", "ipm_concurrent"):
+        phis = [gpu_vec(np.zeros(w.dofs)) for w in ws]
+        with _batch(ws) as b:
+            b.ground_states(method, phi=phis)              # warm-up (graphs, tuning)
+            l0 = dd.dd_kernel_launch_count()
+            res = b.ground_states(method, phi=phis)
+            launches = dd.dd_kernel_launch_count() - l0
+            assert b.info()["last_batched"] == (method == "ipm")
+        out[method] = (res, [host(p) for p in phis], launches)
+    (ra, pa, la), (rc, pc, lc) = out["ipm"], out["ipm_concurrent"]
+    assert np.array_equal(ra["lambda"], rc["lambda"])
+    assert np.array_equal(ra["outer"], rc["outer"]) and np.array_equal(ra["inner"], rc["inner"])
+    for a, c in zip(pa, pc):
+        assert np.array_equal(a, c)
+    assert la < lc
