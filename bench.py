@@ -499,11 +499,14 @@ def sweeps(dd, dev, headline) -> dict:
             eigen[label].append({"outer": outer, "inner_total": tot, "inner_max": mx,
                                  "inner_per_outer": tot / max(outer, 1), "ms": ms})
     w = WORKLOADS["cfg2"]
-    gm = {}
+    gm = {"restart": 120}
     for label, prec in (("fp64", "fp64"), ("mixed", "bf16")):
         with solver(w, prec) as es:
             dd.dd_set_option(es.ctx, dd.DD_OPT_KRYLOV, 1)
             dd.dd_set_option(es.ctx, dd.DD_OPT_PRECOND, 1)
+            # restarted GMRES(30) stagnates on this 2048-cell box (every inner solve hit
+            # the 10000-iteration cap); a basis longer than the iterations it needs does not
+            dd.dd_set_option(es.ctx, dd.DD_OPT_RESTART, gm["restart"])
             x = torch.ones(w.dofs, dtype=torch.float64, device=dev)
             dd.dd_inverse_iterate(es.ctx, x)          # warm-up (GMRES workspace)
             x.fill_(1.0)
@@ -754,10 +757,12 @@ def main():
         Vb = [torch.from_numpy(sample_cell_qp(wi)).to(dev) for wi in wb]
         with dd.Batch(grids_b, Vb) as bt:
             runs = {}
-            for label, method, threads in (("concurrent_ipm", "ipm", 0), ("concurrent_lopcg_fused", "lopcg_fused", 0),
-                                           ("one_thread_ipm", "ipm", 1)):
-                bt.ground_states(method, threads=threads)          # warm-up (graphs, workspaces)
+            for label, method, threads in (("batched_ipm", "ipm", 0), ("concurrent_ipm", "ipm_concurrent", 0),
+                                           ("concurrent_lopcg_fused", "lopcg_fused", 0),
+                                           ("one_thread_ipm", "ipm_concurrent", 1)):
+                bt.ground_states(method, threads=threads)          # warm-up (graphs, workspaces, tuning)
                 torch.cuda.synchronize()
+                l0 = dd.dd_kernel_launch_count()
                 t0 = time.perf_counter()
                 rb = bt.ground_states(method, threads=threads)
                 torch.cuda.synchronize()
@@ -766,10 +771,14 @@ def main():
                                "instance_seconds_min_median_max": [float(rb["seconds"].min()),
                                                                    float(np.median(rb["seconds"])),
                                                                    float(rb["seconds"].max())],
-                               "inner_iters_total": int(rb["inner"].sum())}
+                               "inner_iters_total": int(rb["inner"].sum()),
+                               "kernel_launches": dd.dd_kernel_launch_count() - l0,
+                               "batched_kernels": bool(bt.info()["last_batched"])}
+            runs["grouped_gemm_tile"] = f"128x{bt.info()['gemm_tile_n']}"
+            runs["pcg_iterations_per_graph"] = bt.info()["check_every"]
         batch_line = {"workload": f"cfg4: {len(wb)} instances, p=1, h=1/32, delta=4, L log-uniform in [16, 2048] "
                                   f"(sum of unknowns {sum(wi.dofs for wi in wb)}), own 4-term cosine potentials "
-                                  "(seed 4242)", **runs}
+                                  "(seed 4242), mixed (bf16 local inverses)", **runs}
 
     # the d = 3 workload (p = 2, L = 64, h = 1/16, delta = 2, Gaussian wells; 15.7M unknowns,
     # 4096 subdomains of 9 types): mixed form, same step as the headline

@@ -346,7 +346,10 @@ int dd_coarse_matrix(dd_ctx* ctx, double* A0_host);
  *                       problem shape); the result does not depend on it [0]
  *   DD_OPT_LOCAL_RHS    FP64 local solves: subdomains of one type solved together by one warp,
  *                       1, 2 or 4 (capped by shared memory), 0 = default (2 where allowed) [0]; the result
- *                       does not depend on it (same operations per vector) */
+ *                       does not depend on it (same operations per vector)
+ *   DD_OPT_FUSED_PQ     p = 1: -1 automatic / 1 one kernel stages p = z + beta p in shared memory
+ *                       and applies the stencil from there, 0 a vector update then the stencil
+ *                       from global memory (the p = 2 form); the arithmetic is the same [-1] */
 #define DD_OPT_CHECK_EVERY 0
 #define DD_OPT_USE_GRAPH   1
 #define DD_OPT_FLEXIBLE    2
@@ -357,6 +360,7 @@ int dd_coarse_matrix(dd_ctx* ctx, double* A0_host);
 #define DD_OPT_RESTART     7
 #define DD_OPT_GEMM_TILE_N 8
 #define DD_OPT_COARSE_SOLVE 9
+#define DD_OPT_FUSED_PQ    10
 int dd_set_option(dd_ctx* ctx, int option, int value);
 
 /* Per-kernel-class timing collected while DD_OPT_TIMING = 1: for class k (0 <= k < count),

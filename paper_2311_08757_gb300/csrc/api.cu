@@ -301,7 +301,7 @@ void precond(dd_ctx* c, const double* r, int mode, double* zout = nullptr) {
 
 void pcg_iteration(dd_ctx* c) {
   cudaStream_t s = c->stream;
-  if (c->g.p == 1) {
+  if (c->g.p == 1 && c->fused_pq_opt != 0) {
     TIMED(KC_STENCIL, s, launch_fused_pq(c, s));
   } else {
     TIMED(KC_PUPDATE, s, launch_pupdate(c, s));
@@ -1250,6 +1250,11 @@ int dd_set_option(dd_ctx* c, int option, int value) {
       if (value < 0 || value > 2) return fail(c, DD_EINVAL, "coarse solve must be 0, 1 or 2");
       if (value == 1 && c->g.p == 2) return fail(c, DD_EINVAL, "cyclic reduction needs p = 1");
       c->coarse_mode = value;
+      break;
+    case DD_OPT_FUSED_PQ:
+      if (value < -1 || value > 1) return fail(c, DD_EINVAL, "fused p update must be -1, 0 or 1");
+      if (value == 1 && c->g.p == 2) return fail(c, DD_EINVAL, "the fused p update and stencil needs p = 1");
+      c->fused_pq_opt = value;
       break;
     case DD_OPT_GEMM_TILE_N:
       if (value != 0 && value != 128 && value != 160 && value != 256)

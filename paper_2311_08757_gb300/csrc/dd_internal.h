@@ -138,6 +138,7 @@ struct dd_ctx {
   int use_graph = 1;
   int flexible_opt = -1;
   int timing = 0;
+  int fused_pq_opt = -1;            // p = 1: one kernel for p = z + beta p and q = A_sigma p (-1, 1) or two (0)
   dd::Timer timer;
 
   // types and subdomains

@@ -4,7 +4,7 @@ counts of the eigen-solver.
 * Fig. 3 (Sec. 4.1.1): the source problem a_sigma(u, v) = (1, v) with the printed potential,
   h = 1/30, delta = 1, CG from the initial guess 1 to rTOL = 1e-8, one-level M_AS1 against
   two-level M_AS2.  The plain FP64 form runs the same CG as the oracle, so its counts must
-  equal the oracle's (tests/golden/source_sweeps.json) within two iterations for L <= 256;
+  equal the oracle's (tests/golden/source_sweeps.json) up to where rounding moves the stop (see COUNT_TOL) for L <= 256;
   beyond, up to L = 2048, the two-level counts stay bounded while the one-level ones grow.
 * Table 1 (Sec. 4.1.2): the same with the distance partition of unity, h in {1/10, 1/20,
   1/30} x delta in {1, 2, 3}, against the oracle's counts.
@@ -40,20 +40,27 @@ def source_count(L, n, delta, coarse, pu, precision="fp64"):
 
 
 # Iteration counts of the same CG in FP64 with different summation orders (and a cyclic
-# reduction against a Cholesky coarse solve) agree to within two: near the stop the residual
-# norms of this problem oscillate by factors of about 3 from one iteration to the next
-# (oracle, L = 32, two-level: 2.7e-8, 9.5e-8, 4.8e-8, 1.9e-8, 6.6e-9 at iterations 54-58), so
-# rounding can move the first crossing of 1e-8 by an oscillation.
+# reduction against a Cholesky coarse solve): near the stop the residual norms of these
+# problems oscillate or hover within a factor of 3 of the threshold for several iterations
+# (oracle, L = 32, two-level: 2.7e-8, 9.5e-8, 4.8e-8, 1.9e-8, 6.6e-9 at iterations 54-58;
+# h = 1/20, delta = 2, L = 64: 1.7e-8, 1.4e-8, 1.1e-8, 1.3e-8 at iterations 44-47, where the
+# oracle alone stops at 44 or 48 depending on its BLAS thread count), so rounding moves the
+# first crossing of 1e-8 within that window.  The GPU count must lie between the oracle's first
+# iteration within 3e-8 (minus one) and the oracle's count (plus two).
 COUNT_TOL = 2
+
+
+def in_window(gpu, count, near):
+    return near - 1 <= gpu <= count + COUNT_TOL
 
 
 def test_fig3_counts_match_oracle():
     f = GOLD["fig3"]
-    for L, a1, a2 in zip(f["L"], f["as1"], f["as2"]):
+    for L, a1, a2, n1, n2 in zip(f["L"], f["as1"], f["as2"], f["as1_near"], f["as2_near"]):
         g1 = source_count(L, f["n"], f["delta"], False, f["pu"])
         g2 = source_count(L, f["n"], f["delta"], True, f["pu"])
-        assert abs(g1 - a1) <= COUNT_TOL, (L, g1, a1)
-        assert abs(g2 - a2) <= COUNT_TOL, (L, g2, a2)
+        assert in_window(g1, a1, n1), (L, g1, a1, n1)
+        assert in_window(g2, a2, n2), (L, g2, a2, n2)
 
 
 def test_fig3_extended_to_large_L():
@@ -72,11 +79,11 @@ def test_fig3_extended_to_large_L():
 def test_table1_counts_match_oracle():
     t = GOLD["table1"]
     for row in t["cases"]:
-        for L, a1, a2 in zip(t["L"], row["as1"], row["as2"]):
+        for L, a1, a2, n1, n2 in zip(t["L"], row["as1"], row["as2"], row["as1_near"], row["as2_near"]):
             g1 = source_count(L, row["n"], row["delta"], False, t["pu"])
             g2 = source_count(L, row["n"], row["delta"], True, t["pu"])
-            assert abs(g1 - a1) <= COUNT_TOL, (row["n"], row["delta"], L, g1, a1)
-            assert abs(g2 - a2) <= COUNT_TOL, (row["n"], row["delta"], L, g2, a2)
+            assert in_window(g1, a1, n1), (row["n"], row["delta"], L, g1, a1, n1)
+            assert in_window(g2, a2, n2), (row["n"], row["delta"], L, g2, a2, n2)
 
 
 def _eigen(L, precision):
