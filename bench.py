@@ -499,13 +499,11 @@ def sweeps(dd, dev, headline) -> dict:
             eigen[label].append({"outer": outer, "inner_total": tot, "inner_max": mx,
                                  "inner_per_outer": tot / max(outer, 1), "ms": ms})
     w = WORKLOADS["cfg2"]
-    gm = {"restart": 120}
+    gm = {"restart": 30}
     for label, prec in (("fp64", "fp64"), ("mixed", "bf16")):
         with solver(w, prec) as es:
             dd.dd_set_option(es.ctx, dd.DD_OPT_KRYLOV, 1)
             dd.dd_set_option(es.ctx, dd.DD_OPT_PRECOND, 1)
-            # restarted GMRES(30) stagnates on this 2048-cell box (every inner solve hit
-            # the 10000-iteration cap); a basis longer than the iterations it needs does not
             dd.dd_set_option(es.ctx, dd.DD_OPT_RESTART, gm["restart"])
             x = torch.ones(w.dofs, dtype=torch.float64, device=dev)
             dd.dd_inverse_iterate(es.ctx, x)          # warm-up (GMRES workspace)

@@ -162,7 +162,9 @@ int dd_pcg_solve(dd_ctx* ctx, const double* b, double* x, double rtol, int maxit
  * restart length DD_OPT_RESTART.  Arnoldi by classical Gram-Schmidt applied twice.
  *   b        host or device, ndof doubles
  *   x        host or device, ndof doubles; in: initial guess, out: solution
- *   stops when ||b - A_sigma x||_2 <= rtol ||b - A_sigma x_0||_2 (true residual)
+ *   stops when the method's own residual (the least-squares residual of the Arnoldi relation,
+ *   as PCG stops on its recursive residual) is <= rtol ||b - A_sigma x_0||_2; each restart
+ *   begins from the true residual.  relres_out is that residual over ||b - A_sigma x_0||_2.
  * DD_EMAXIT after maxit iterations (x holds the last iterate).  dd_pcg_solve returns
  * DD_EINVAL while the restricted preconditioner is selected.
  */

@@ -11,7 +11,9 @@
   |rho_k - rho_{k-1}| <= tol_lam |rho_k|.
 * ``gmres``: right-preconditioned restarted GMRES (Arnoldi with modified Gram-Schmidt,
   Givens rotations), the Krylov method for the unsymmetric M_RAS2^{-1} (Sec. 2.2); stopped
-  on the true residual ||r_k||_2 <= rtol ||r_0||_2 like ``pcg``.
+  when its own residual (the least-squares residual of the Arnoldi relation, |g_{j+1}|)
+  satisfies ||r_k||_2 <= rtol ||r_0||_2, as ``pcg`` stops on its recursive residual; restarts
+  begin from the true residual.
 * ``si_lopcg``: the inexact shift-and-invert preconditioned LOPCG of Algorithm 1:
   outer residual r_o = A x_k - R(x_k) B x_k, inner solve A_sigma w_k = r_o by PCG
   (relative tolerance fixed, or min{0.1, ||r_o||_2} as in Sec. 4.3), or w_k = M^{-1} r_o
@@ -118,9 +120,11 @@ def gmres(A, b, x0=None, prec=None, rtol=1e-8, restart=30, maxit=10000):
         y = sla.solve_triangular(H[:j_done, :j_done], g[:j_done])
         for i in range(j_done):
             x = x + y[i] * Z[i]
-        r = b - A @ x
-        if np.sqrt(dot(r, r)) <= rtol * r0:
+        # stop on the method's own residual |g_{j+1}| (the minimised least-squares residual),
+        # as PCG stops on its recursive residual; the cycle restarts from the true residual
+        if abs(g[j_done]) <= rtol * r0:
             return x, its, hist
+        r = b - A @ x
     return x, its, hist
 
 

@@ -62,6 +62,15 @@ int guarded(dd_ctx* c, F&& f) {
 
 namespace dd {
 
+// Padded box vector with a zeroed guard band of kVecGuard doubles on each side: the
+// 3^d-point stencil of the first (last) interior node reaches one element before (after)
+// the padded range, where the homogeneous Dirichlet value 0 must be read.
+constexpr long long kVecGuard = 64;   // 512 bytes, keeps the 256-byte alignment
+double* alloc_vec(dd_ctx* c) {
+  double* base = (double*)dev_alloc(c, sizeof(double) * (size_t)(c->g.plen + 2 * kVecGuard));
+  return base + kVecGuard;
+}
+
 static std::atomic<long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void note_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
@@ -228,14 +237,6 @@ void build_subdomains(dd_ctx* c) {
   DD_CUDA(cudaStreamSynchronize(c->stream));
 }
 
-// Padded box vector with a zeroed guard band of kVecGuard doubles on each side: the
-// 3^d-point stencil of the first (last) interior node reaches one element before (after)
-// the padded range, where the homogeneous Dirichlet value 0 must be read.
-constexpr long long kVecGuard = 64;   // 512 bytes, keeps the 256-byte alignment
-double* alloc_vec(dd_ctx* c) {
-  double* base = (double*)dev_alloc(c, sizeof(double) * (size_t)(c->g.plen + 2 * kVecGuard));
-  return base + kVecGuard;
-}
 
 // user vector (ABI order, host or device) -> padded device vector
 void load_vec(dd_ctx* c, const double* u, double* padded) {
@@ -452,8 +453,13 @@ int gmres_run(dd_ctx* c, const double* b, double rtol, int maxit, int* iters, do
       const double est = read_scalar(c->gm_res);
       ++its;
       if (!std::isfinite(est)) return fail(c, DD_ENAN, "non-finite GMRES residual");
-      if (est <= rtol * r0 || its >= maxit) {
+      rel = est / r0;
+      if (est <= rtol * r0) {
         done = 1;
+        ++j;
+        break;
+      }
+      if (its >= maxit) {
         ++j;
         break;
       }
@@ -461,18 +467,18 @@ int gmres_run(dd_ctx* c, const double* b, double rtol, int maxit, int* iters, do
     const int mm = std::min(j, m);
     TIMED(KC_MISC, s, launch_backsolve(c, mm, s));
     TIMED(KC_XRUPDATE, s, launch_multiaxpy(c, mm, c->gm_Zptr, c->gm_y, 1.0, c->x, s));
-    // true residual
-    TIMED(KC_STENCIL, s, launch_stencil(c, c->tabS, c->x, W, s));
-    TIMED(KC_XRUPDATE, s, launch_axpby(c, -1.0, W, 1.0, nullptr, b, W, s));
-    TIMED(KC_XRUPDATE, s, launch_dot(c, W, W, nrm2, s));
-    rel = std::sqrt(read_scalar(nrm2)) / r0;
-    if (rel <= rtol) break;
+    // stop on the method's own residual |g_{j+1}| (as PCG stops on its recursive residual);
+    // otherwise restart from the true residual
+    if (done) break;
     if (its >= maxit) {
       if (iters) *iters = its;
       if (relres) *relres = rel;
       return fail(c, DD_EMAXIT, "GMRES reached maxit");
     }
-    (void)done;
+    TIMED(KC_STENCIL, s, launch_stencil(c, c->tabS, c->x, W, s));
+    TIMED(KC_XRUPDATE, s, launch_axpby(c, -1.0, W, 1.0, nullptr, b, W, s));
+    TIMED(KC_XRUPDATE, s, launch_dot(c, W, W, nrm2, s));
+    if (!std::isfinite(read_scalar(nrm2))) return fail(c, DD_ENAN, "non-finite GMRES residual");
   }
   if (iters) *iters = its;
   if (relres) *relres = rel;

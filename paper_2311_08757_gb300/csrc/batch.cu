@@ -20,6 +20,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <limits>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -43,8 +44,8 @@ struct dd_batch {
   std::vector<dd::BInst> Bh;
   dd::BInst* B = nullptr;
   int2 *vm_init = nullptr, *vm_fused = nullptr, *vm_xr = nullptr, *vm_prolong = nullptr, *vm_sdot = nullptr,
-       *vm_st = nullptr, *vm_vec = nullptr, *vm_pack = nullptr;
-  int n_init = 0, n_fused = 0, n_xr = 0, n_prolong = 0, n_sdot = 0, n_st = 0, n_vec = 0, n_pack = 0;
+       *vm_st = nullptr, *vm_vec = nullptr, *vm_pack = nullptr, *vm_st2 = nullptr;
+  int n_init = 0, n_fused = 0, n_xr = 0, n_prolong = 0, n_sdot = 0, n_st = 0, n_vec = 0, n_pack = 0, n_st2 = 0;
   size_t cr_smem = 0;
   int ypad = 0;
   dd::BGemm* gemm = nullptr;
@@ -80,10 +81,11 @@ void free_engine(dd_batch* b) {
   b->gemm = nullptr;
   for (void* p : {(void*)b->B, (void*)b->vm_init, (void*)b->vm_fused, (void*)b->vm_xr, (void*)b->vm_prolong,
                   (void*)b->vm_sdot, (void*)b->vm_st, (void*)b->vm_vec, (void*)b->vm_pack, (void*)b->stat_d,
-                  (void*)b->xptr_d, (void*)b->err_d})
+                  (void*)b->xptr_d, (void*)b->err_d, (void*)b->vm_st2})
     if (p) cudaFree(p);
   b->B = nullptr;
   b->vm_init = b->vm_fused = b->vm_xr = b->vm_prolong = b->vm_sdot = b->vm_st = b->vm_vec = b->vm_pack = nullptr;
+  b->vm_st2 = nullptr;
   b->stat_d = nullptr;
   b->xptr_d = nullptr;
   b->err_d = nullptr;
@@ -142,7 +144,7 @@ void build_engine(dd_batch* b) {
   DD_CUDA(cudaMalloc(&b->err_d, sizeof(int) * 16));
   DD_CUDA(cudaMemset(b->err_d, 0, sizeof(int) * 16));
   b->Bh.assign(n, BInst());
-  std::vector<int2> vinit, vfused, vxr, vprol, vsdot, vst, vvec, vpack;
+  std::vector<int2> vinit, vfused, vxr, vprol, vsdot, vst, vst2, vvec, vpack;
   b->cr_smem = 0;
   for (int i = 0; i < n; ++i) {
     dd_ctx* c = b->ctx[i];
@@ -173,6 +175,7 @@ void build_engine(dd_batch* b) {
     for (int k = 0; k < I.nb_prolong; ++k) vprol.push_back(make_int2(i, k));
     for (int k = 0; k < I.nb_sdot; ++k) vsdot.push_back(make_int2(i, k));
     for (int k = 0; k < I.nb_st; ++k) vst.push_back(make_int2(i, k));
+    for (int k = 0; k < I.nb_st2; ++k) vst2.push_back(make_int2(i, k));
     for (int k = 0; k < I.nb_vec; ++k) vvec.push_back(make_int2(i, k));
     for (int k = 0; k < c->g.nsub; ++k) vpack.push_back(make_int2(i, k));
   }
@@ -184,6 +187,7 @@ void build_engine(dd_batch* b) {
   b->vm_prolong = upload_vmap(vprol); b->n_prolong = (int)vprol.size();
   b->vm_sdot = upload_vmap(vsdot); b->n_sdot = (int)vsdot.size();
   b->vm_st = upload_vmap(vst); b->n_st = (int)vst.size();
+  b->vm_st2 = upload_vmap(vst2); b->n_st2 = (int)vst2.size();
   b->vm_vec = upload_vmap(vvec); b->n_vec = (int)vvec.size();
   b->vm_pack = upload_vmap(vpack); b->n_pack = (int)vpack.size();
   DD_CUDA(cudaMalloc(&b->B, sizeof(BInst) * n));
@@ -370,6 +374,204 @@ int batched_ipm(dd_batch* b, double* lambda_out, int* outer_out, int* inner_out,
   return first;
 }
 
+// the SI-LOPCG work space of every instance (what dd_lopcg allocates on its first call)
+void ensure_lopcg(dd_batch* b) {
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    dd_ctx* c = b->ctx[i];
+    if (!c->lst) {
+      c->lst = (dd::LopState*)dd::dev_alloc(c, sizeof(dd::LopState));
+      DD_CUDA(cudaMallocHost(&c->lst_h, sizeof(dd::LopState)));
+      c->lop_red = (double*)dd::dev_alloc(c, sizeof(double) * dd::kMaxRedBlocksHost * 15);
+      for (double*& v : c->lop) v = dd::alloc_vec(c);
+      DD_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    BInst& I = b->Bh[i];
+    for (int k = 0; k < 12; ++k) I.lop[k] = c->lop[k];
+    I.lst = c->lst;
+    I.lop_red = c->lop_red;
+  }
+}
+
+// Batched SI-LOPCG with the fused inner step (Algorithm 1 with w_k = M_AS2^{-1} r_o, Sec. 4.3),
+// the steps of dd_lopcg for every active instance at once.  The twelve work vectors play the
+// same roles in every instance (the roles rotate in lockstep), so each launch names roles.
+int batched_lopcg_fused(dd_batch* b, double* lambda_out, int* outer_out, int* inner_out, double* seconds_out,
+                        const std::vector<double>& setup_s, std::chrono::steady_clock::time_point t_start) {
+  using namespace dd;
+  const int n = (int)b->ctx.size();
+  const double tol_res = 1e-8, tol_lam = 1e-10;
+  const int maxit_outer = 1000;
+  if (!b->built) build_engine(b);
+  ensure_lopcg(b);
+  for (int i = 0; i < n; ++i) {
+    b->Bh[i].active = 1;
+    b->Bh[i].r = b->ctx[i]->lop[9];   // the preconditioner is applied to the outer residual r_o
+  }
+  upload_active(b);
+  // roles: X XP T AX AXP MX MXP AW MW RO AT MT = lop[0..11] at the start
+  int X = 0, XP = 1, T = 2, AX = 3, AXP = 4, MX = 5, MXP = 6;
+  const int AW = 7, MW = 8, RO = 9;
+  int AT = 10, MT = 11;
+  auto R = [](int k) { return BV_LOP + k; };
+  cudaStream_t s = b->s;
+  launch_b_zero_roles(b->B, b->vm_vec, b->n_vec, BV_LOP, 12, s);
+  launch_b_lop_reset(b->B, n, s);
+  const long long first = (long long)b->ctx.front()->g.Ypad;   // first interior node (p = 1)
+  launch_b_set_entry(b->B, n, R(XP), first, 1.0, s);
+  launch_b_stencil_role(b->B, b->vm_st, b->n_st, 1, R(XP), R(MXP), s);
+  launch_b_lop_normalize(b->B, b->vm_vec, b->n_vec, R(XP), R(MXP), s);
+  launch_b_stencil_role(b->B, b->vm_st, b->n_st, 0, R(XP), R(AXP), s);
+  auto explicit_images = [&]() {
+    launch_b_stencil_role(b->B, b->vm_st, b->n_st, 1, R(X), R(MX), s);
+    launch_b_lop_normalize(b->B, b->vm_vec, b->n_vec, R(X), R(MX), s);
+    launch_b_stencil_dot(b->B, b->vm_sdot, b->n_sdot, R(X), R(AX), s);
+    launch_b_outer_res_ro(b->B, b->vm_vec, b->n_vec, R(AX), R(MX), R(RO), s);
+    gather(b);
+  };
+  launch_b_pad(b->B, b->vm_vec, b->n_vec, b->xptr_d, R(X), s);
+  explicit_images();
+  std::vector<double> lam(n), rr(n), mm(n), rho(n), rho_prev(n, std::numeric_limits<double>::infinity());
+  std::vector<int> exact(n, 1), outer(n, 0), inner(n, 0), status(n, DD_OK), xrole(n, X);
+  for (int i = 0; i < n; ++i) {
+    if (b->stat_h[i].outer_status != 0) {
+      status[i] = b->stat_h[i].outer_status;
+      b->Bh[i].active = 0;
+      continue;
+    }
+    lam[i] = b->stat_h[i].xAx;
+    rr[i] = b->stat_h[i].rr;
+    mm[i] = b->stat_h[i].mm;
+  }
+  upload_active(b);
+  auto stops = [&](double rh, double r2, double m2, double prev) {
+    const double eta = std::sqrt(r2 / m2) / std::fabs(rh);
+    return eta <= tol_res && std::fabs(rh - prev) <= tol_lam * std::fabs(rh);
+  };
+  for (int k = 0; k <= maxit_outer; ++k) {
+    // stop test; instances whose images are carried combinations confirm on recomputed ones
+    std::vector<int> confirm;
+    int active = 0;
+    for (int i = 0; i < n; ++i) {
+      if (!b->Bh[i].active) continue;
+      rho[i] = b->ctx[i]->sigma + lam[i];
+      if (!std::isfinite(rho[i])) {
+        status[i] = DD_ENAN;
+        b->Bh[i].active = 0;
+        continue;
+      }
+      if (stops(rho[i], rr[i], mm[i], rho_prev[i])) {
+        if (exact[i]) {
+          b->Bh[i].active = 0;
+          outer[i] = k;
+          xrole[i] = X;
+          if (seconds_out)
+            seconds_out[i] = setup_s[i] + std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+          continue;
+        }
+        confirm.push_back(i);
+      }
+      ++active;
+    }
+    if (!confirm.empty()) {
+      std::vector<int> keep(n);
+      for (int i = 0; i < n; ++i) {
+        keep[i] = b->Bh[i].active;
+        b->Bh[i].active = 0;
+      }
+      for (int i : confirm) b->Bh[i].active = 1;
+      upload_active(b);
+      explicit_images();
+      for (int i = 0; i < n; ++i) b->Bh[i].active = keep[i];
+      for (int i : confirm) {
+        exact[i] = 1;
+        lam[i] = b->stat_h[i].xAx;
+        rr[i] = b->stat_h[i].rr;
+        mm[i] = b->stat_h[i].mm;
+        const double rho_e = b->ctx[i]->sigma + lam[i];
+        if (stops(rho_e, rr[i], mm[i], rho_prev[i])) {
+          rho[i] = rho_e;
+          b->Bh[i].active = 0;
+          outer[i] = k;
+          xrole[i] = X;
+          --active;
+          if (seconds_out)
+            seconds_out[i] = setup_s[i] + std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+        }
+      }
+      upload_active(b);
+    }
+    if (active == 0) break;
+    if (k == maxit_outer) {
+      for (int i = 0; i < n; ++i)
+        if (b->Bh[i].active) {
+          status[i] = DD_EMAXIT;
+          outer[i] = k;
+          xrole[i] = X;
+        }
+      break;
+    }
+    // w = M_AS2^{-1} r_o; images of w; Rayleigh-Ritz on span{x_k, w, x_{k-1}}; update
+    launch_b_pcg_reset(b->B, n, 0.0, 0, s);
+    precond(b, 0);
+    launch_b_stencil2(b->B, b->vm_st2, b->n_st2, BV_Z, R(AW), R(MW), s);
+    const int S[3] = {R(X), BV_Z, R(XP)}, AS[3] = {R(AX), R(AW), R(AXP)}, MS[3] = {R(MX), R(MW), R(MXP)};
+    launch_b_lop_gram(b->B, b->vm_vec, b->n_vec, S, AS, MS, 1e-10, s);
+    launch_b_lop_update3(b->B, b->vm_vec, b->n_vec, S, AS, MS, R(T), R(AT), R(MT), R(RO), s);
+    int t0 = XP;
+    XP = X; X = T; T = t0;
+    t0 = AXP; AXP = AX; AX = AT; AT = t0;
+    t0 = MXP; MXP = MX; MX = MT; MT = t0;
+    gather(b);
+    for (int i = 0; i < n; ++i) {
+      if (!b->Bh[i].active) continue;
+      inner[i] += 1;
+      if (b->stat_h[i].lop_status != 0) {
+        status[i] = b->stat_h[i].lop_status;
+        b->Bh[i].active = 0;
+        outer[i] = k + 1;
+        xrole[i] = X;
+        continue;
+      }
+      rho_prev[i] = rho[i];
+      lam[i] = b->stat_h[i].theta;
+      rr[i] = b->stat_h[i].lop_rr;
+      mm[i] = b->stat_h[i].lop_mm;
+      exact[i] = 0;
+    }
+    upload_active(b);
+  }
+  // phi back to the instances' vectors: each from the role its iterate had when it stopped
+  for (int role = 0; role < 12; ++role) {
+    bool any = false;
+    for (int i = 0; i < n; ++i) {
+      b->Bh[i].active = (xrole[i] == role) ? 1 : 0;
+      any = any || xrole[i] == role;
+    }
+    if (!any) continue;
+    upload_active(b);
+    launch_b_unpad_active(b->B, b->vm_vec, b->n_vec, R(role), b->xptr_d, s);
+  }
+  for (int i = 0; i < n; ++i) b->Bh[i].r = b->ctx[i]->r;
+  upload_active(b);
+  int herr = 0;
+  DD_CUDA(cudaMemcpyAsync(&herr, b->err_d + 8, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DD_CUDA(cudaStreamSynchronize(s));
+  const double end = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  int first_err = DD_OK;
+  for (int i = 0; i < n; ++i) {
+    if (lambda_out) lambda_out[i] = rho[i];
+    if (outer_out) outer_out[i] = std::min(outer[i], maxit_outer);
+    if (inner_out) inner_out[i] = inner[i];
+    if (seconds_out && status[i] != DD_OK) seconds_out[i] = setup_s[i] + end;
+    if (status[i] != DD_OK && first_err == DD_OK) first_err = status[i];
+  }
+  if (herr != 0) {
+    DD_CUDA(cudaMemsetAsync(b->err_d + 8, 0, sizeof(int), s));
+    return DD_ETIMEOUT;
+  }
+  return first_err;
+}
+
 }  // namespace
 
 extern "C" {
@@ -461,7 +663,7 @@ int dd_batch_ground_states(dd_batch* b, int method, int threads, double* lambda_
   threads = std::min(threads, n);
   // the batched engine needs the options it was built for (the grouped contraction and
   // the cyclic-reduction coarse solve, PCG inner solves)
-  bool engine = b->eligible && method == DD_BATCH_IPM;
+  bool engine = b->eligible && (method == DD_BATCH_IPM || method == DD_BATCH_LOPCG_FUSED);
   for (dd_ctx* c : b->ctx)
     if (c->krylov != 0 || c->ras != 0 || c->coarse_mode == 2 || c->timing) engine = false;
   std::vector<int> order(n);
@@ -523,7 +725,9 @@ int dd_batch_ground_states(dd_batch* b, int method, int threads, double* lambda_
     // every instance's set-up is complete (each call synchronised its context's stream)
     try {
       DD_CUDA(cudaSetDevice(b->device));
-      rc = batched_ipm(b, lambda_out, outer_out, inner_out, seconds_out, setup_s, t_start);
+      rc = method == DD_BATCH_IPM
+               ? batched_ipm(b, lambda_out, outer_out, inner_out, seconds_out, setup_s, t_start)
+               : batched_lopcg_fused(b, lambda_out, outer_out, inner_out, seconds_out, setup_s, t_start);
       b->last_batched = 1;
       // bounded waits of the instances' coarse solves
       for (dd_ctx* c : b->ctx) {

@@ -279,19 +279,24 @@ struct BInst {
   const double* cr;       // cyclic-reduction coefficients of A_0 (p = 1)
   int cr_m, cr_c2, cr_w2, cr_staged;
   int kpad, coarse, nsub, flexible;
-  int nb_init, nb_fused, nb_xr, nb_prolong, nb_sdot, nb_st, nb_vec;
+  int nb_init, nb_fused, nb_xr, nb_prolong, nb_sdot, nb_st, nb_vec, nb_st2;
   int active;             // 0 once the problem's eigen-iteration has stopped
   int* err;               // the context's error word of bounded waits
+  double* lop[12];        // SI-LOPCG work vectors (padded)
+  LopState* lst;
+  double* lop_red;
 };
 
-// Vector roles in BInst (the batched outer-step kernels take roles, not pointers).
-enum BVec { BV_X = 0, BV_R, BV_Z, BV_Q, BV_W1, BV_W2, BV_W3, BV_XE };
+// Vector roles in BInst (the batched outer-step kernels take roles, not pointers);
+// BV_LOP + k is the SI-LOPCG work vector lop[k].
+enum BVec { BV_X = 0, BV_R, BV_Z, BV_Q, BV_W1, BV_W2, BV_W3, BV_XE, BV_NONE = 15, BV_LOP = 16 };
 
 // Per-problem scalars copied to the host after a batched step.
 struct BStat {
   int pcg_done, pcg_status, pcg_iter, active;
   double xAx, rr, mm;
-  int outer_status, pad_;
+  int outer_status, lop_status;
+  double theta, lop_rr, lop_mm;
 };
 
 // ----- launchers (kernels in k_*.cu) -----
@@ -397,6 +402,25 @@ int bgemm_tune(BGemm* b, cudaStream_t s);
 void bgemm_destroy(BGemm* b);
 void launch_b_unpad(const BInst* B, const int2* vmap, int nvb, int src_role, double* const* dst, cudaStream_t s);
 void launch_b_pad(const BInst* B, const int2* vmap, int nvb, const double* const* src, int dst_role, cudaStream_t s);
+void launch_b_zero_roles(const BInst* B, const int2* vmap, int nvb, int first_role, int nroles, cudaStream_t s);
+void launch_b_set_entry(const BInst* B, int n, int role, long long idx, double val, cudaStream_t s);
+void launch_b_stencil_role(const BInst* B, const int2* vmap, int nvb, int mass, int x_role, int y_role,
+                           cudaStream_t s);
+void launch_b_stencil2(const BInst* B, const int2* vmap_st2, int nvb, int x_role, int ys_role, int ym_role,
+                       cudaStream_t s);
+void launch_b_lop_normalize(const BInst* B, const int2* vmap, int nvb, int x_role, int mx_role, cudaStream_t s);
+void launch_b_outer_res_ro(const BInst* B, const int2* vmap, int nvb, int ax_role, int mx_role, int ro_role,
+                           cudaStream_t s);
+void launch_b_lop_gram(const BInst* B, const int2* vmap, int nvb, const int* S, const int* AS, const int* MS,
+                       double drop, cudaStream_t s);
+void launch_b_lop_update3(const BInst* B, const int2* vmap, int nvb, const int* S, const int* AS, const int* MS,
+                          int x_role, int ax_role, int mx_role, int ro_role, cudaStream_t s);
+void launch_b_lop_reset(const BInst* B, int n, cudaStream_t s);
+void launch_b_unpad_active(const BInst* B, const int2* vmap, int nvb, int src_role, double* const* dst,
+                           cudaStream_t s);
+constexpr int kMaxRedBlocksHost = 4096;   // partial slots per reduced value (kMaxRedBlocks)
+void launch_b_outer_dots_roles(const BInst* B, const int2* vmap, int nvb, int w_role, int mw_role, cudaStream_t s);
+double* alloc_vec(dd_ctx* c);
 
 
 // timing helpers

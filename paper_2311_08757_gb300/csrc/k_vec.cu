@@ -220,17 +220,24 @@ __global__ void __launch_bounds__(kThreads) k_stencil(Geo g, const double* __res
 
 // two operators on one vector in one pass: y1 = T1 x, y2 = T2 x
 template <int P>
-__global__ void __launch_bounds__(kThreads) k_stencil2(Geo g, const double* __restrict__ tab1,
+__device__ __forceinline__ void stencil2_body(VBlk vb, Geo g, const double* __restrict__ tab1,
                                                        const double* __restrict__ tab2, const double* __restrict__ x,
                                                        double* __restrict__ y1, double* __restrict__ y2) {
   const long long total = (long long)g.nxi * (P == 2 ? g.nxi : 1) * g.Ypad;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
+  for (long long t = (long long)vb.b * blockDim.x + threadIdx.x; t < total;
+       t += (long long)vb.nb * blockDim.x) {
     Node nd = node_of<P>(g, t);
     const int cls = cls_of<P>(g, nd);
     y1[nd.idx] = stencil_at<P>(g, tab1, x, nd.idx, cls);
     y2[nd.idx] = stencil_at<P>(g, tab2, x, nd.idx, cls);
   }
+}
+
+template <int P>
+__global__ void __launch_bounds__(kThreads) k_stencil2(Geo g, const double* __restrict__ tab1,
+                                                       const double* __restrict__ tab2, const double* __restrict__ x,
+                                                       double* __restrict__ y1, double* __restrict__ y2) {
+  stencil2_body<P>(vblk_self(), g, tab1, tab2, x, y1, y2);
 }
 
 static long long interior_work(const Geo& g) {
@@ -1029,7 +1036,10 @@ void launch_tab_shift(dd_ctx* c, double shift, double* dst) {
 // A problem whose eigen-iteration has stopped (active = 0) returns at once; so does every
 // PCG kernel of a problem whose solve is done (its PcgState.done), as in a plain launch.
 // ========================================================================================
+static_assert(kMaxRedBlocksHost == kMaxRedBlocks, "host and device partial-slot counts differ");
+
 __device__ __forceinline__ double* bvec(const BInst& I, int role) {
+  if (role >= BV_LOP) return I.lop[role - BV_LOP];
   switch (role) {
     case BV_X: return I.x;
     case BV_R: return I.r;
@@ -1157,17 +1167,21 @@ __global__ void kb_gather(const BInst* __restrict__ B, int n, BStat* __restrict_
   o.rr = I.ost->rr;
   o.mm = I.ost->mm;
   o.outer_status = I.ost->status;
-  o.pad_ = 0;
+  o.lop_status = I.lst != nullptr ? I.lst->status : 0;
+  o.theta = I.lst != nullptr ? I.lst->theta : 0.0;
+  o.lop_rr = I.lst != nullptr ? I.lst->rr : 0.0;
+  o.lop_mm = I.lst != nullptr ? I.lst->mm : 0.0;
   out[i] = o;
 }
 
 // layout conversion between a user vector (ABI order) and a role vector (padded), p = 1
-template <bool TO_PAD>
+template <bool TO_PAD, bool ACTIVE_ONLY = false>
 __global__ void __launch_bounds__(kThreads) kb_pad(const BInst* __restrict__ B, const int2* __restrict__ vmap,
                                                    const double* const* __restrict__ user_in,
                                                    double* const* __restrict__ user_out, int role) {
   const int2 m = vmap[blockIdx.x];
   const BInst& I = B[m.x];
+  if (ACTIVE_ONLY && !I.active) return;
   const Geo& g = I.g;
   double* pv = bvec(I, role);
   for (long long t = (long long)m.y * blockDim.x + threadIdx.x; t < g.ndof; t += (long long)I.nb_vec * blockDim.x) {
@@ -1177,6 +1191,41 @@ __global__ void __launch_bounds__(kThreads) kb_pad(const BInst* __restrict__ B, 
     if (TO_PAD) pv[pidx] = user_in[m.x][t];
     else user_out[m.x][t] = pv[pidx];
   }
+}
+
+__global__ void __launch_bounds__(kThreads) kb_zero_roles(const BInst* __restrict__ B, const int2* __restrict__ vmap,
+                                                          int first_role, int nroles) {
+  const int2 m = vmap[blockIdx.x];
+  const BInst& I = B[m.x];
+  if (!I.active) return;
+  const long long n = I.g.plen;
+  for (int k = 0; k < nroles; ++k) {
+    double* v = bvec(I, first_role + k);
+    for (long long t = (long long)m.y * blockDim.x + threadIdx.x; t < n; t += (long long)I.nb_vec * blockDim.x)
+      v[t] = 0.0;
+  }
+}
+
+__global__ void kb_set_entry(const BInst* __restrict__ B, int n, int role, long long idx, double val) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && B[i].active) bvec(B[i], role)[idx] = val;
+}
+
+__global__ void __launch_bounds__(kThreads) kb_stencil2(const BInst* __restrict__ B, const int2* __restrict__ vmap,
+                                                        int x_role, int ys_role, int ym_role) {
+  const int2 m = vmap[blockIdx.x];
+  const BInst& I = B[m.x];
+  if (!I.active) return;
+  stencil2_body<1>(VBlk{m.y, I.nb_st2}, I.g, I.tabS, I.tabM, bvec(I, x_role), bvec(I, ys_role), bvec(I, ym_role));
+}
+
+__global__ void __launch_bounds__(kThreads) kb_outer_res_ro(const BInst* __restrict__ B, const int2* __restrict__ vmap,
+                                                            int ax_role, int mx_role, int ro_role) {
+  const int2 m = vmap[blockIdx.x];
+  const BInst& I = B[m.x];
+  if (!I.active) return;
+  outer_res_body(VBlk{m.y, I.nb_vec}, I.g.plen, bvec(I, ax_role), bvec(I, mx_role), I.ost, I.red,
+                 I.cnt + CNT_OUTER2, ro_role == BV_NONE ? nullptr : bvec(I, ro_role));
 }
 
 void batch_grid_sizes(const dd_ctx* c, BInst* I) {
@@ -1190,6 +1239,34 @@ void batch_grid_sizes(const dd_ctx* c, BInst* I) {
   I->nb_sdot = resident_grid(k_stencil<1, true>, w, kThreads);
   I->nb_st = resident_grid(k_stencil<1, false>, w, kThreads);
   I->nb_vec = grid_blocks(g.plen, kThreads);
+  I->nb_st2 = resident_grid(k_stencil2<1>, w, kThreads);
+}
+
+void launch_b_zero_roles(const BInst* B, const int2* vmap, int nvb, int first_role, int nroles, cudaStream_t s) {
+  (kb_zero_roles<<<nvb, kThreads, 0, s>>>(B, vmap, first_role, nroles), dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+}
+
+void launch_b_set_entry(const BInst* B, int n, int role, long long idx, double val, cudaStream_t s) {
+  (kb_set_entry<<<(n + 127) / 128, 128, 0, s>>>(B, n, role, idx, val), dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+}
+
+void launch_b_stencil_role(const BInst* B, const int2* vmap, int nvb, int mass, int x_role, int y_role,
+                           cudaStream_t s) {
+  launch_b_stencil(B, vmap, nvb, mass, x_role, y_role, s);
+}
+
+void launch_b_stencil2(const BInst* B, const int2* vmap_st2, int nvb, int x_role, int ys_role, int ym_role,
+                       cudaStream_t s) {
+  (kb_stencil2<<<nvb, kThreads, 0, s>>>(B, vmap_st2, x_role, ys_role, ym_role), dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+}
+
+void launch_b_outer_res_ro(const BInst* B, const int2* vmap, int nvb, int ax_role, int mx_role, int ro_role,
+                           cudaStream_t s) {
+  (kb_outer_res_ro<<<nvb, kThreads, 0, s>>>(B, vmap, ax_role, mx_role, ro_role), dd::note_launch());
+  DD_CUDA(cudaGetLastError());
 }
 
 void launch_b_pcg_reset(const BInst* B, int n, double rtol2, int maxit, cudaStream_t s) {
@@ -1244,6 +1321,11 @@ void launch_b_outer_normalize(const BInst* B, const int2* vmap, int nvb, int w_r
   DD_CUDA(cudaGetLastError());
 }
 
+void launch_b_outer_dots_roles(const BInst* B, const int2* vmap, int nvb, int w_role, int mw_role, cudaStream_t s) {
+  (kb_outer_dots<<<nvb, kThreads, 0, s>>>(B, vmap, w_role, mw_role), dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+}
+
 void launch_b_outer_res(const BInst* B, const int2* vmap, int nvb, int ax_role, int mx_role, cudaStream_t s) {
   (kb_outer_res<<<nvb, kThreads, 0, s>>>(B, vmap, ax_role, mx_role), dd::note_launch());
   DD_CUDA(cudaGetLastError());
@@ -1256,6 +1338,12 @@ void launch_b_gather(const BInst* B, int n, BStat* out, cudaStream_t s) {
 
 void launch_b_unpad(const BInst* B, const int2* vmap, int nvb, int src_role, double* const* dst, cudaStream_t s) {
   (kb_pad<false><<<nvb, kThreads, 0, s>>>(B, vmap, nullptr, dst, src_role), dd::note_launch());
+  DD_CUDA(cudaGetLastError());
+}
+
+void launch_b_unpad_active(const BInst* B, const int2* vmap, int nvb, int src_role, double* const* dst,
+                           cudaStream_t s) {
+  (kb_pad<false, true><<<nvb, kThreads, 0, s>>>(B, vmap, nullptr, dst, src_role), dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 

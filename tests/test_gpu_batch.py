@@ -29,7 +29,7 @@ def test_small_batch_matches_oracle_and_single_calls(method, precision):
         info = b.info()
     # the inverse iteration of the mixed form runs as batched kernels over all instances
     assert info["batchable"] == (precision == "bf16")
-    assert info["last_batched"] == (precision == "bf16" and method == "ipm")
+    assert info["last_batched"] == (precision == "bf16" and method in ("ipm", "lopcg_fused"))
     for i, w in enumerate(ws):
         P = oracle_problem(w, build_prec=False)
         lam_ex, _ = solvers.exact_ground_state(P.A, P.M, sigma=P.sigma, dense_limit=3000 if w.dofs <= 3000 else 0)
@@ -83,6 +83,26 @@ def test_full_batched_workload():
             x = gpu_vec(np.ones(w.dofs))
             lam, outer, tot, mx = dd.dd_inverse_iterate(es.ctx, x)
         assert lam == res["lambda"][i] and tot == res["inner"][i]
+
+
+def test_batched_lopcg_equals_single_calls_on_the_full_workload():
+    """Fused SI-LOPCG batched over the 64-instance workload: every instance's eigenvalue, step
+    count and iterate equal those of its own dd_lopcg call (checked on the four largest and
+    the four smallest instances), and the batched kernels ran."""
+    ws = batch_workloads()
+    order = np.argsort([w.L for w in ws])
+    phis = [gpu_vec(np.zeros(w.dofs)) for w in ws]
+    with _batch(ws) as b:
+        res = b.ground_states("lopcg_fused", phi=phis)
+        assert b.info()["last_batched"] == 1
+    for i in list(order[:4]) + list(order[-4:]):
+        w = ws[i]
+        with make_solver(w, precision="bf16") as es:
+            es.prepare()
+            x = gpu_vec(np.ones(w.dofs))
+            lam, outer, tot, mx = dd.dd_lopcg(es.ctx, x, "fused")
+        assert lam == res["lambda"][i] and outer == res["outer"][i] and tot == res["inner"][i]
+        assert np.array_equal(host(x), host(phis[i]))
 
 
 def test_batched_kernels_equal_concurrent_pipelines():
