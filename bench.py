@@ -755,25 +755,45 @@ def main():
         Vb = [torch.from_numpy(sample_cell_qp(wi)).to(dev) for wi in wb]
         with dd.Batch(grids_b, Vb) as bt:
             runs = {}
-            for label, method, threads in (("batched_ipm", "ipm", 0), ("concurrent_ipm", "ipm_concurrent", 0),
-                                           ("concurrent_lopcg_fused", "lopcg_fused", 0),
-                                           ("one_thread_ipm", "ipm_concurrent", 1)):
-                bt.ground_states(method, threads=threads)          # warm-up (graphs, workspaces, tuning)
+
+            def timed_call(label, method, groups, threads=0, warm=1):
+                bt.set_groups(groups)
+                for _ in range(warm):
+                    bt.ground_states(method, threads=threads)          # warm-up (graphs, workspaces)
                 torch.cuda.synchronize()
                 l0 = dd.dd_kernel_launch_count()
                 t0 = time.perf_counter()
                 rb = bt.ground_states(method, threads=threads)
                 torch.cuda.synchronize()
                 tb = time.perf_counter() - t0
+                info = bt.info()
                 runs[label] = {"seconds": tb, "eigenpairs_per_s": len(wb) / tb,
                                "instance_seconds_min_median_max": [float(rb["seconds"].min()),
                                                                    float(np.median(rb["seconds"])),
                                                                    float(rb["seconds"].max())],
                                "inner_iters_total": int(rb["inner"].sum()),
                                "kernel_launches": dd.dd_kernel_launch_count() - l0,
-                               "batched_kernels": bool(bt.info()["last_batched"])}
-            runs["grouped_gemm_tile"] = f"128x{bt.info()['gemm_tile_n']}"
-            runs["pcg_iterations_per_graph"] = bt.info()["check_every"]
+                               "batched_kernels": bool(info["last_batched"]),
+                               "groups": info["groups"] if info["last_batched"] else None,
+                               "grouped_gemm_tile": f"128x{info['gemm_tile_n']}" if info["last_batched"] else None,
+                               "setup_phase_s": info["setup_seconds"]}
+                return runs[label]
+
+            # batched kernels: every group count timed, then the library's own choice (it tries
+            # each count on successive calls and keeps the fastest)
+            runs["batched_ipm_by_groups"] = {str(G): timed_call("tmp", "ipm", G)["seconds"] for G in (1, 2, 4, 8)}
+            bt.set_groups(0)
+            for _ in range(8):
+                bt.ground_states("ipm")
+            timed_call("batched_ipm", "ipm", 0, warm=0)
+            for _ in range(8):
+                bt.ground_states("lopcg_fused")
+            timed_call("batched_lopcg_fused", "lopcg_fused", 0, warm=0)
+            # the same methods as concurrent per-instance pipelines, and one thread
+            timed_call("concurrent_ipm", "ipm", -1)
+            timed_call("concurrent_lopcg_fused", "lopcg_fused", -1)
+            timed_call("one_thread_ipm", "ipm", -1, threads=1)
+            runs.pop("tmp", None)
         batch_line = {"workload": f"cfg4: {len(wb)} instances, p=1, h=1/32, delta=4, L log-uniform in [16, 2048] "
                                   f"(sum of unknowns {sum(wi.dofs for wi in wb)}), own 4-term cosine potentials "
                                   "(seed 4242), mixed (bf16 local inverses)", **runs}

@@ -254,32 +254,36 @@ int dd_eigenpair(const dd_grid* g, const double* V_cell_qp, size_t nV, void* str
  * host threads (<= 0: min(count, 16)), largest instance first, each on its own context
  * stream, then from x_0 = 1:
  *   DD_BATCH_IPM             the shifted inverse iteration (tol_res 1e-8, tol_lam 1e-10,
- *                            rtol_inner 1e-8, as dd_inverse_iterate).  When the instances share
- *                            p = 1, the precision (BF16 or TF32), h, delta, ell, quadrature and
- *                            partition of unity, it runs BATCHED: every kernel of a PCG iteration
- *                            is one launch over all instances (the blocks of each instance's own
- *                            launch side by side; the local solves one grouped tensor-core
- *                            contraction over all instances' tiles), a block of iterations of
- *                            all instances is one CUDA graph, each instance keeps its own device
- *                            scalars, kernels of an instance whose solve is done return at once,
- *                            and an instance whose eigen-iteration has stopped drops out; the
- *                            outer steps run in lockstep.  Otherwise as DD_BATCH_IPM_CONCURRENT.
- *   DD_BATCH_LOPCG_FUSED     dd_lopcg with DD_INNER_FUSED, per instance, concurrently
+ *                            rtol_inner 1e-8, as dd_inverse_iterate)
+ *   DD_BATCH_LOPCG_FUSED     SI-LOPCG with the fused inner step (dd_lopcg, DD_INNER_FUSED)
  *   DD_BATCH_LOPCG_ADAPTIVE  dd_lopcg with DD_INNER_ADAPTIVE, per instance, concurrently
  *   DD_BATCH_IPM_CONCURRENT  dd_inverse_iterate per instance on the thread pool (the instances'
  *                            own launches overlap on the GPU)
+ * DD_BATCH_IPM and DD_BATCH_LOPCG_FUSED run BATCHED when the instances share p = 1, the
+ * precision (BF16 or TF32), h, delta, ell, quadrature and partition of unity: the instances
+ * are split into G groups of about equal total size, each driven by one host thread on its own
+ * streams; within a group every kernel of an iteration is one launch over all the group's
+ * instances (the blocks of each instance's own launch side by side; the local solves one
+ * grouped tensor-core contraction over the instances' tiles), a block of PCG iterations is one
+ * CUDA graph, each instance keeps its own device scalars, kernels of an instance whose solve is
+ * done return at once, an instance joins its group's iteration as soon as its own set-up is
+ * done and drops out when its eigen-iteration stops.  G (1, 2, 4 or 8) is set by
+ * dd_batch_set_groups, or, with 0 (the default), chosen by timing: each count is tried on
+ * successive calls (its first use builds it) and the fastest is kept; -1 runs every method per
+ * instance.  Otherwise these two methods run per instance, concurrently.
  * Outputs per instance (arrays of count entries, each may be NULL): lambda, outer and inner
  * iteration counts, wall seconds from the start of the call to the instance's eigenpair;
  * phi_out[i] (host or device, ndof_i doubles; phi_out or an entry may be NULL).
  * Returns the first failing instance's status (the others still run).  Results equal those
  * of the single-instance calls bit for bit (same arithmetic per instance, deterministic
- * reductions), batched or not.
+ * reductions), batched or not, for every G.
  * dd_batch_context gives instance i's context (owned by the batch) for options and queries;
- * a context with timing, GMRES, the restricted preconditioner or the dense coarse solve
- * selected makes DD_BATCH_IPM run per instance.  dd_batch_info reports whether the batch
- * qualifies for the batched kernels, whether the last call ran them, the N tile of the
- * grouped contraction chosen by timing the three shapes on the batch's own operands at the
- * first batched call (0 before), and the PCG iterations per graph replay (each may be NULL).
+ * a context with timing, GMRES, the restricted preconditioner, the dense coarse solve or the
+ * two-kernel p update selected makes these methods run per instance.  dd_batch_info reports
+ * whether the batch qualifies for the batched kernels, whether the last call ran them, the N
+ * tile of the grouped contraction of its first group (timed on the group's operands when the
+ * group was built), the number of groups, and the wall seconds of the last call's set-up phase
+ * (until every instance's coarse build is done) and of the whole last call (each may be NULL).
  */
 typedef struct dd_batch dd_batch;
 #define DD_BATCH_IPM            0
@@ -291,8 +295,9 @@ int dd_batch_create(const dd_grid* grids, const double* const* V, const size_t* 
 int dd_batch_ground_states(dd_batch* b, int method, int threads, double* lambda_out, double* const* phi_out,
                            int* outer_out, int* inner_out, double* seconds_out);
 int dd_batch_size(const dd_batch* b);
+int dd_batch_set_groups(dd_batch* b, int groups);
 int dd_batch_info(const dd_batch* b, int* batchable_out, int* last_batched_out, int* gemm_tile_n_out,
-                  int* check_every_out);
+                  int* groups_out, double* setup_seconds_out, double* total_seconds_out);
 dd_ctx* dd_batch_context(dd_batch* b, int i);
 void dd_batch_destroy(dd_batch* b);
 
@@ -350,8 +355,10 @@ int dd_coarse_matrix(dd_ctx* ctx, double* A0_host);
  *                       1, 2 or 4 (capped by shared memory), 0 = default (2 where allowed) [0]; the result
  *                       does not depend on it (same operations per vector)
  *   DD_OPT_FUSED_PQ     p = 1: -1 automatic / 1 one kernel stages p = z + beta p in shared memory
- *                       and applies the stencil from there, 0 a vector update then the stencil
- *                       from global memory (the p = 2 form); the arithmetic is the same [-1] */
+ *                       and applies the stencil from there (one node per thread and pass), 2 the
+ *                       same with two nodes per thread and pass (their tap chains interleaved),
+ *                       0 a vector update then the stencil from global memory (the p = 2 form);
+ *                       the result is the same bits for 1 and 2; automatic = 2 [-1] */
 #define DD_OPT_CHECK_EVERY 0
 #define DD_OPT_USE_GRAPH   1
 #define DD_OPT_FLEXIBLE    2

@@ -66,7 +66,9 @@ _SIGS = {
                                 POINTER(c_void_p)]),
     "dd_batch_ground_states": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "dd_batch_size": (c_int, [c_void_p]),
-    "dd_batch_info": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
+    "dd_batch_info": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int),
+                              POINTER(c_double), POINTER(c_double)]),
+    "dd_batch_set_groups": (c_int, [c_void_p, c_int]),
     "dd_batch_context": (c_void_p, [c_void_p, c_int]),
     "dd_batch_destroy": (None, [c_void_p]),
     "dd_lopcg": (c_int, [c_void_p, c_void_p, c_int, c_double, c_double, c_int, c_double, POINTER(c_double),
@@ -428,10 +430,15 @@ class Batch:
         return {"lambda": lam, "outer": outer, "inner": inner, "seconds": sec}
 
     def info(self) -> dict:
-        """dd_batch_info: batchable, last_batched, gemm_tile_n, check_every."""
-        v = [c_int() for _ in range(4)]
+        """dd_batch_info: batchable, last_batched, gemm_tile_n, groups, setup_seconds, total_seconds."""
+        v = [c_int() for _ in range(4)] + [c_double(), c_double()]
         _check(lib().dd_batch_info(self.handle, *[byref(x) for x in v]))
-        return dict(zip(("batchable", "last_batched", "gemm_tile_n", "check_every"), (x.value for x in v)))
+        return dict(zip(("batchable", "last_batched", "gemm_tile_n", "groups", "setup_seconds",
+                         "total_seconds"), (x.value for x in v)))
+
+    def set_groups(self, groups: int) -> None:
+        """dd_batch_set_groups: instances split into this many batched groups (0: chosen by timing)."""
+        _check(lib().dd_batch_set_groups(self.handle, groups))
 
     def close(self):
         if getattr(self, "handle", None):

@@ -72,9 +72,28 @@ double* alloc_vec(dd_ctx* c) {
 }
 
 static std::atomic<long long> g_launches{0};
-void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+// launches issued while this thread captures a stream into a graph do not run: the graph's
+// kernel nodes are counted when the graph is launched
+static thread_local int t_capturing = 0;
+void note_launch() {
+  if (!t_capturing) g_launches.fetch_add(1, std::memory_order_relaxed);
+}
 void note_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+void set_capturing(bool on) { t_capturing = on ? 1 : 0; }
+long long graph_kernel_nodes(cudaGraph_t gr) {
+  size_t n = 0;
+  DD_CUDA(cudaGraphGetNodes(gr, nullptr, &n));
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (n) DD_CUDA(cudaGraphGetNodes(gr, nodes.data(), &n));
+  long long k = 0;
+  for (size_t i = 0; i < n; ++i) {
+    cudaGraphNodeType t;
+    DD_CUDA(cudaGraphNodeGetType(nodes[i], &t));
+    if (t == cudaGraphNodeTypeKernel) ++k;
+  }
+  return k;
+}
 
 void* dev_alloc(dd_ctx* c, size_t bytes) {
   void* p = nullptr;
@@ -302,7 +321,7 @@ void precond(dd_ctx* c, const double* r, int mode, double* zout = nullptr) {
 
 void pcg_iteration(dd_ctx* c) {
   cudaStream_t s = c->stream;
-  if (c->g.p == 1 && c->fused_pq_opt != 0) {
+  if (c->g.p == 1 && c->fused_pq_opt != 0) {   // fused, two nodes per thread unless option 1
     TIMED(KC_STENCIL, s, launch_fused_pq(c, s));
   } else {
     TIMED(KC_PUPDATE, s, launch_pupdate(c, s));
@@ -323,20 +342,20 @@ void reset_graph(dd_ctx* c) {
 void build_graph(dd_ctx* c) {
   reset_graph(c);
   cudaGraph_t gr;
-  const long long before = launch_count();
   DD_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  set_capturing(true);
   try {
     for (int i = 0; i < c->check_every; ++i) pcg_iteration(c);
   } catch (...) {
+    set_capturing(false);
     cudaStreamEndCapture(c->stream, &gr);
     cudaGetLastError();
-    note_launches(before - launch_count());
     throw;
   }
+  set_capturing(false);
   DD_CUDA(cudaStreamEndCapture(c->stream, &gr));
   // captured launches do not run; replays are counted when the graph is launched
-  c->graph_kernels = launch_count() - before;
-  note_launches(-c->graph_kernels);
+  c->graph_kernels = graph_kernel_nodes(gr);
   DD_CUDA(cudaGraphInstantiate(&c->graph, gr, 0));
   DD_CUDA(cudaGraphDestroy(gr));
   c->graph_iters = c->check_every;
@@ -1258,8 +1277,8 @@ int dd_set_option(dd_ctx* c, int option, int value) {
       c->coarse_mode = value;
       break;
     case DD_OPT_FUSED_PQ:
-      if (value < -1 || value > 1) return fail(c, DD_EINVAL, "fused p update must be -1, 0 or 1");
-      if (value == 1 && c->g.p == 2) return fail(c, DD_EINVAL, "the fused p update and stencil needs p = 1");
+      if (value < -1 || value > 2) return fail(c, DD_EINVAL, "fused p update must be -1, 0, 1 or 2");
+      if (value >= 1 && c->g.p == 2) return fail(c, DD_EINVAL, "the fused p update and stencil needs p = 1");
       c->fused_pq_opt = value;
       break;
     case DD_OPT_GEMM_TILE_N:

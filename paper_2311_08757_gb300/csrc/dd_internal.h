@@ -390,6 +390,7 @@ void launch_b_outer_normalize(const BInst* B, const int2* vmap, int nvb, int w_r
                               cudaStream_t s);
 void launch_b_outer_res(const BInst* B, const int2* vmap, int nvb, int ax_role, int mx_role, cudaStream_t s);
 void launch_b_gather(const BInst* B, int n, BStat* out, cudaStream_t s);
+void launch_b_mark_done(const BInst* B, int n, cudaStream_t s);
 void launch_b_pack(const BInst* B, const int2* vmap, int nvb, int precision, cudaStream_t s);
 void launch_b_cr_solve(const BInst* B, int n, size_t smem, cudaStream_t s);
 void cr_launch_shape(const dd_ctx* c, size_t* smem, int* staged);
@@ -401,6 +402,7 @@ void bgemm_run(BGemm* b, int bn, cudaStream_t s);
 int bgemm_tune(BGemm* b, cudaStream_t s);
 void bgemm_destroy(BGemm* b);
 void launch_b_unpad(const BInst* B, const int2* vmap, int nvb, int src_role, double* const* dst, cudaStream_t s);
+// (active problems only)
 void launch_b_pad(const BInst* B, const int2* vmap, int nvb, const double* const* src, int dst_role, cudaStream_t s);
 void launch_b_zero_roles(const BInst* B, const int2* vmap, int nvb, int first_role, int nroles, cudaStream_t s);
 void launch_b_set_entry(const BInst* B, int n, int role, long long idx, double val, cudaStream_t s);
@@ -435,6 +437,8 @@ void launch_fill(double* x, long long n, double v, cudaStream_t s);
 void note_launch();
 void note_launches(long long k);
 long long launch_count();
+void set_capturing(bool on);                  // this thread is capturing a graph
+long long graph_kernel_nodes(cudaGraph_t gr);
 
 }  // namespace dd
 

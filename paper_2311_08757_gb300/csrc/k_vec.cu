@@ -423,10 +423,14 @@ void launch_pupdate(dd_ctx* c, cudaStream_t s) {
 // are evaluated from shared memory.
 constexpr int kFusedCols = 32;
 
+// U2 = 2: each thread evaluates two nodes (e, e + blockDim) per pass, their 9-tap chains
+// interleaved; the (p, q) partial is accumulated in the same node order as with U2 = 1, so the
+// result is bit-identical.
+template <int U2>
 __device__ __forceinline__ void fused_pq_body(VBlk vb, Geo g, const double* __restrict__ tab,
-                                                       const double* __restrict__ z, double* pb0, double* pb1,
-                                                       double* __restrict__ q, PcgState* st, double* partials,
-                                                       unsigned* counter) {
+                                              const double* __restrict__ z, double* pb0, double* pb1,
+                                              double* __restrict__ q, PcgState* st, double* partials,
+                                              unsigned* counter) {
   if (st->done) return;
   extern __shared__ double sp_raw[];
   double* sp = sp_raw + 1;   // one zero guard element on each side
@@ -451,21 +455,50 @@ __device__ __forceinline__ void fused_pq_body(VBlk vb, Geo g, const double* __re
     if (threadIdx.x == 0) sp[nload] = 0.0;   // corner tap of the last (pad) slot of a partial tile
     __syncthreads();
     const int nown = own << yl;
-    for (int e = threadIdx.x; e < nown; e += blockDim.x) {
-      const int se = e + Y;
-      const long long gi = gbase + se;
-      const double pv = sp[se];
-      pc[gi] = pv;
-      const int col = a0 + (e >> yl), slot = e & (Y - 1);
-      const int cls = (col % g.n) * Y + slot;
-      double qv = 0.0;
+    if (U2 == 1) {
+      for (int e = threadIdx.x; e < nown; e += blockDim.x) {
+        const int se = e + Y;
+        const long long gi = gbase + se;
+        const double pv = sp[se];
+        pc[gi] = pv;
+        const int col = a0 + (e >> yl), slot = e & (Y - 1);
+        const int cls = (col % g.n) * Y + slot;
+        double qv = 0.0;
 #pragma unroll
-      for (int dx = -1; dx <= 1; ++dx)
+        for (int dx = -1; dx <= 1; ++dx)
 #pragma unroll
-        for (int dy = -1; dy <= 1; ++dy)
-          qv = fma(__ldg(tab + (size_t)((dx + 1) * 3 + (dy + 1)) * g.ncls + cls), sp[se + dx * Y + dy], qv);
-      q[gi] = qv;
-      acc[0] = fma(pv, qv, acc[0]);
+          for (int dy = -1; dy <= 1; ++dy)
+            qv = fma(__ldg(tab + (size_t)((dx + 1) * 3 + (dy + 1)) * g.ncls + cls), sp[se + dx * Y + dy], qv);
+        q[gi] = qv;
+        acc[0] = fma(pv, qv, acc[0]);
+      }
+    } else {
+      for (int e = threadIdx.x; e < nown; e += 2 * blockDim.x) {
+        const int e1 = e + blockDim.x;
+        const bool two = e1 < nown;
+        const int f = two ? e1 : e;   // a valid node for the masked second chain
+        const int se0 = e + Y, se1 = f + Y;
+        const double pv0 = sp[se0], pv1 = sp[se1];
+        const int cls0 = ((a0 + (e >> yl)) % g.n) * Y + (e & (Y - 1));
+        const int cls1 = ((a0 + (f >> yl)) % g.n) * Y + (f & (Y - 1));
+        double q0 = 0.0, q1 = 0.0;
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx)
+#pragma unroll
+          for (int dy = -1; dy <= 1; ++dy) {
+            const double* tt = tab + (size_t)((dx + 1) * 3 + (dy + 1)) * g.ncls;
+            q0 = fma(__ldg(tt + cls0), sp[se0 + dx * Y + dy], q0);
+            q1 = fma(__ldg(tt + cls1), sp[se1 + dx * Y + dy], q1);
+          }
+        pc[gbase + se0] = pv0;
+        q[gbase + se0] = q0;
+        acc[0] = fma(pv0, q0, acc[0]);
+        if (two) {
+          pc[gbase + se1] = pv1;
+          q[gbase + se1] = q1;
+          acc[0] = fma(pv1, q1, acc[0]);
+        }
+      }
     }
   }
   double tot[1];
@@ -481,11 +514,12 @@ __device__ __forceinline__ void fused_pq_body(VBlk vb, Geo g, const double* __re
   }
 }
 
+template <int U2>
 __global__ void __launch_bounds__(kThreads) k_fused_pq(Geo g, const double* __restrict__ tab,
                                                        const double* __restrict__ z, double* pb0, double* pb1,
                                                        double* __restrict__ q, PcgState* st, double* partials,
                                                        unsigned* counter) {
-  fused_pq_body(vblk_self(), g, tab, z, pb0, pb1, q, st, partials, counter);
+  fused_pq_body<U2>(vblk_self(), g, tab, z, pb0, pb1, q, st, partials, counter);
 }
 
 void launch_fused_pq(dd_ctx* c, cudaStream_t s) {
@@ -495,10 +529,17 @@ void launch_fused_pq(dd_ctx* c, cudaStream_t s) {
   const size_t smem = sizeof(double) * ((size_t)(kFusedCols + 2) * g.Ypad + 2);
   static PerDeviceOnce attr;   // once per device
   once_per_device(attr, [] {
-    DD_CUDA(cudaFuncSetAttribute(k_fused_pq, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    DD_CUDA(cudaFuncSetAttribute(k_fused_pq<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    DD_CUDA(cudaFuncSetAttribute(k_fused_pq<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   });
-  (k_fused_pq<<<nb, kThreads, smem, s>>>(g, c->tabS, c->z, c->pb[0], c->pb[1], c->q, c->st, c->red,
-                                         c->cnt + CNT_PQ), dd::note_launch());
+  // two nodes per thread and pass by default: 53.0 against 53.8 us per launch on the
+  // L = 2048, h = 1/32 box, the same bits
+  if (c->fused_pq_opt != 1)
+    (k_fused_pq<2><<<nb, kThreads, smem, s>>>(g, c->tabS, c->z, c->pb[0], c->pb[1], c->q, c->st, c->red,
+                                              c->cnt + CNT_PQ), dd::note_launch());
+  else
+    (k_fused_pq<1><<<nb, kThreads, smem, s>>>(g, c->tabS, c->z, c->pb[0], c->pb[1], c->q, c->st, c->red,
+                                              c->cnt + CNT_PQ), dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 
@@ -1090,7 +1131,7 @@ __global__ void __launch_bounds__(kThreads) kb_fused_pq(const BInst* __restrict_
   const int2 m = vmap[blockIdx.x];
   const BInst& I = B[m.x];
   if (!I.active) return;
-  fused_pq_body(VBlk{m.y, I.nb_fused}, I.g, I.tabS, I.z, I.pb0, I.pb1, I.q, I.st, I.red, I.cnt + CNT_PQ);
+  fused_pq_body<2>(VBlk{m.y, I.nb_fused}, I.g, I.tabS, I.z, I.pb0, I.pb1, I.q, I.st, I.red, I.cnt + CNT_PQ);
 }
 
 __global__ void __launch_bounds__(kThreads) kb_xr_update(const BInst* __restrict__ B, const int2* __restrict__ vmap) {
@@ -1152,6 +1193,18 @@ __global__ void __launch_bounds__(kThreads) kb_outer_res(const BInst* __restrict
   if (!I.active) return;
   outer_res_body(VBlk{m.y, I.nb_vec}, I.g.plen, bvec(I, ax_role), bvec(I, mx_role), I.ost, I.red,
                  I.cnt + CNT_OUTER2, nullptr);
+}
+
+// every problem's PCG state marked done, whatever its active flag: the tiles of the grouped
+// contraction (which read only that flag) then skip problems that have not joined yet
+__global__ void kb_mark_done(const BInst* __restrict__ B, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) B[i].st->done = 1;
+}
+
+void launch_b_mark_done(const BInst* B, int n, cudaStream_t s) {
+  (kb_mark_done<<<(n + 127) / 128, 128, 0, s>>>(B, n), dd::note_launch());
+  DD_CUDA(cudaGetLastError());
 }
 
 __global__ void kb_gather(const BInst* __restrict__ B, int n, BStat* __restrict__ out) {
@@ -1348,7 +1401,7 @@ void launch_b_unpad_active(const BInst* B, const int2* vmap, int nvb, int src_ro
 }
 
 void launch_b_pad(const BInst* B, const int2* vmap, int nvb, const double* const* src, int dst_role, cudaStream_t s) {
-  (kb_pad<true><<<nvb, kThreads, 0, s>>>(B, vmap, src, nullptr, dst_role), dd::note_launch());
+  (kb_pad<true, true><<<nvb, kThreads, 0, s>>>(B, vmap, src, nullptr, dst_role), dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 }  // namespace dd

@@ -106,24 +106,36 @@ def test_batched_lopcg_equals_single_calls_on_the_full_workload():
 
 
 def test_batched_kernels_equal_concurrent_pipelines():
-    """The batched inverse iteration (one launch per kernel over all instances, one graph per
-    block of iterations, lockstep outer steps) and the concurrent per-instance pipelines give
-    the same bits, instance by instance, and the phi they return are M-normalised ground
-    states; the batched one launches far fewer kernels."""
+    """The batched inverse iteration and fused SI-LOPCG (one launch per kernel over a group's
+    instances, one graph per block of PCG iterations, instances joining as their set-up ends)
+    give the same bits as the concurrent per-instance pipelines, instance by instance, for
+    1, 2 and 4 groups, on a group's first call (built after every set-up) and on later calls
+    (set-up and solves overlapping); the batched path launches fewer kernels."""
     ws = batch_workloads(seed=7, count=12, L_min=3, L_max=300, n=32, overlap=4)
-    out = {}
-    for method in ("ipm", "ipm_concurrent"):
-        phis = [gpu_vec(np.zeros(w.dofs)) for w in ws]
-        with _batch(ws) as b:
-            b.ground_states(method, phi=phis)              # warm-up (graphs, tuning)
+    with _batch(ws) as b:
+        ref = {}
+        b.set_groups(-1)                       # every method per instance, concurrently
+        for method in ("ipm", "lopcg_fused"):
+            phis_c = [gpu_vec(np.zeros(w.dofs)) for w in ws]
+            b.ground_states(method, phi=phis_c)   # warm-up (graphs, workspaces)
             l0 = dd.dd_kernel_launch_count()
-            res = b.ground_states(method, phi=phis)
-            launches = dd.dd_kernel_launch_count() - l0
-            assert b.info()["last_batched"] == (method == "ipm")
-        out[method] = (res, [host(p) for p in phis], launches)
-    (ra, pa, la), (rc, pc, lc) = out["ipm"], out["ipm_concurrent"]
-    assert np.array_equal(ra["lambda"], rc["lambda"])
-    assert np.array_equal(ra["outer"], rc["outer"]) and np.array_equal(ra["inner"], rc["inner"])
-    for a, c in zip(pa, pc):
-        assert np.array_equal(a, c)
-    assert la < lc
+            rc = b.ground_states(method, phi=phis_c)
+            lc = dd.dd_kernel_launch_count() - l0
+            assert b.info()["last_batched"] == 0
+            ref[method] = (rc, [host(p) for p in phis_c], lc)
+        for groups in (1, 2, 4):
+            b.set_groups(groups)
+            for method in ("ipm", "lopcg_fused"):
+                rc, pc, lc = ref[method]
+                for call in range(2):
+                    phis = [gpu_vec(np.zeros(w.dofs)) for w in ws]
+                    l0 = dd.dd_kernel_launch_count()
+                    res = b.ground_states(method, phi=phis)
+                    la = dd.dd_kernel_launch_count() - l0
+                    info = b.info()
+                    assert info["last_batched"] == 1 and info["groups"] == groups
+                    assert np.array_equal(res["lambda"], rc["lambda"]), (groups, method, call)
+                    assert np.array_equal(res["outer"], rc["outer"]) and np.array_equal(res["inner"], rc["inner"])
+                    for a, c in zip(phis, pc):
+                        assert np.array_equal(host(a), c)
+                    assert la < lc
