@@ -358,7 +358,12 @@ int dd_coarse_matrix(dd_ctx* ctx, double* A0_host);
  *                       and applies the stencil from there (one node per thread and pass), 2 the
  *                       same with two nodes per thread and pass (their tap chains interleaved),
  *                       0 a vector update then the stencil from global memory (the p = 2 form);
- *                       the result is the same bits for 1 and 2; automatic = 2 [-1] */
+ *                       the result is the same bits for 1 and 2; automatic = 2 [-1]
+ *   DD_OPT_PROLONG_TABLES p = 1: 1 reads the owners of every node and their packed rows from
+ *                       index tables in the prolong-sum; 0 computes them in closed form where
+ *                       set-up found the formula equal to the tables (same values, two dependent
+ *                       loads fewer per node, but more integer work: 28.1 against 24.5 us per
+ *                       launch on the L = 2048, h = 1/32 box) [1] */
 #define DD_OPT_CHECK_EVERY 0
 #define DD_OPT_USE_GRAPH   1
 #define DD_OPT_FLEXIBLE    2
@@ -370,6 +375,7 @@ int dd_coarse_matrix(dd_ctx* ctx, double* A0_host);
 #define DD_OPT_GEMM_TILE_N 8
 #define DD_OPT_COARSE_SOLVE 9
 #define DD_OPT_FUSED_PQ    10
+#define DD_OPT_PROLONG_TABLES 11
 int dd_set_option(dd_ctx* ctx, int option, int value);
 
 /* Per-kernel-class timing collected while DD_OPT_TIMING = 1: for class k (0 <= k < count),

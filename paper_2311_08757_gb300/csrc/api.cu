@@ -247,6 +247,23 @@ void build_subdomains(dd_ctx* c) {
   c->groups = (int2*)dev_alloc(c, sizeof(int2) * g.nsub);
   DD_CUDA(cudaMemcpyAsync(c->sub_of_slot, sos.data(), sizeof(int) * g.nsub, cudaMemcpyHostToDevice, c->stream));
   set_local_groups(c, std::min(2, rhs_per_warp(c->nloc_max, c->band)));
+  // p = 1: the prolong-sum computes owners and packed rows in closed form where the formula
+  // reproduces these tables exactly (every column, packed row i = subdomain i)
+  bool closed = g.p == 1;
+  for (int a = 1; closed && a <= g.nxi; ++a) {
+    const int4 v = p1_owners(g, a), t = ax[a];
+    closed = v.x == t.x && v.y == t.y && v.z == t.z && (t.z < 0 || v.w == t.w);
+  }
+  for (int s2 = 0; closed && s2 < g.nsub; ++s2) closed = slot[s2] == s2;
+  if (g.p == 1) {
+    c->ptypes = make_int4(c->subs_h[0].type, g.L >= 3 ? c->subs_h[1].type : 0, c->subs_h[g.L - 1].type, 0);
+    for (int s2 = 0; closed && s2 < g.nsub; ++s2) {
+      const int want = s2 == 0 ? c->ptypes.x : (s2 == g.L - 1 ? c->ptypes.z : c->ptypes.y);
+      closed = c->subs_h[s2].type == want;
+    }
+  }
+  c->prolong_closed = closed ? 1 : 0;
+  c->prolong_arith = (closed && !c->prolong_tables_opt) ? 1 : 0;
   c->axown = (int4*)dev_alloc(c, sizeof(int4) * g.ncx);
   c->subrow = (int4*)dev_alloc(c, sizeof(int4) * g.nsub);
   DD_CUDA(cudaMemcpyAsync(c->axown, ax.data(), sizeof(int4) * g.ncx, cudaMemcpyHostToDevice, c->stream));
@@ -1280,6 +1297,11 @@ int dd_set_option(dd_ctx* c, int option, int value) {
       if (value < -1 || value > 2) return fail(c, DD_EINVAL, "fused p update must be -1, 0, 1 or 2");
       if (value >= 1 && c->g.p == 2) return fail(c, DD_EINVAL, "the fused p update and stencil needs p = 1");
       c->fused_pq_opt = value;
+      break;
+    case DD_OPT_PROLONG_TABLES:
+      if (value != 0 && value != 1) return fail(c, DD_EINVAL, "prolong tables must be 0 or 1");
+      c->prolong_tables_opt = value;
+      c->prolong_arith = (c->prolong_closed && !value) ? 1 : 0;
       break;
     case DD_OPT_GEMM_TILE_N:
       if (value != 0 && value != 128 && value != 160 && value != 256)

@@ -49,6 +49,7 @@ struct BGroup {
   int n_init = 0, n_fused = 0, n_xr = 0, n_prolong = 0, n_sdot = 0, n_st = 0, n_st2 = 0, n_vec = 0, n_pack = 0;
   size_t cr_smem = 0;
   int ypad = 0, precision = 0, check_every = 8;
+  bool arith = true;               // every instance's prolong-sum owners in closed form
   dd::BGemm* gemm = nullptr;
   int bn = 0;                      // N tile of the grouped contraction (timed at build)
   cudaStream_t s = nullptr, side = nullptr;
@@ -160,7 +161,7 @@ void precond(BGroup* g, int mode) {
   DD_CUDA(cudaEventRecord(g->ev_join, g->side));
   dd::bgemm_run(g->gemm, g->bn, g->s);
   DD_CUDA(cudaStreamWaitEvent(g->s, g->ev_join, 0));
-  dd::launch_b_prolong(g->B, g->vm_prolong, g->n_prolong, mode, g->s);
+  dd::launch_b_prolong(g->B, g->vm_prolong, g->n_prolong, mode, g->arith, g->s);
 }
 
 void pcg_iteration(BGroup* g) {
@@ -248,6 +249,9 @@ BGroup* build_group(dd_batch* b, const std::vector<int>& idx) {
       I.flexible = (c->flexible_opt < 0) ? 1 : c->flexible_opt;
       I.err = c->dev_err;
       I.active = 1;
+      I.ptypes = c->ptypes;
+      I.prolong_arith = c->prolong_arith;
+      g->arith = g->arith && c->prolong_arith;
       dd::batch_grid_sizes(c, &I);
       for (int k = 0; k < I.nb_init; ++k) vinit.push_back(make_int2(j, k));
       for (int k = 0; k < I.nb_fused; ++k) vfused.push_back(make_int2(j, k));

@@ -62,6 +62,21 @@ __host__ __device__ inline int ax_type(const Geo& g, int i) {
   return 1;
 }
 
+// Owners of node column a (1 <= a <= Ln - 1) along a p = 1 box: subdomain i spans columns
+// max(1, i n - delta + 1) .. min(Ln - 1, (i + 1) n + delta - 1), so the owners are
+// i = ceil((a - delta + 1)/n) - 1 .. floor((a + delta - 1)/n) (clipped to 0 .. L - 1), one or two
+// of them as 2 delta < n; returned as the owner table holds them: {first owner, its local
+// column, second owner or -1, 0}.
+__host__ __device__ inline int4 p1_owners(const Geo& g, int a) {
+  const int u = a - g.delta + 1;
+  const int ilo = u <= 0 ? 0 : (u + g.n - 1) / g.n - 1;
+  const int hi = (a + g.delta - 1) / g.n;
+  const int ihi = hi < g.L - 1 ? hi : g.L - 1;
+  const int lo0 = ilo * g.n - g.delta + 1, lo1 = ihi * g.n - g.delta + 1;
+  const int l0 = a - (lo0 > 1 ? lo0 : 1);
+  return ihi > ilo ? make_int4(ilo, l0, ihi, a - (lo1 > 1 ? lo1 : 1)) : make_int4(ilo, l0, -1, 0);
+}
+
 // Subdomain descriptor on the device.
 struct Sub {
   int type;     // compact type id
@@ -139,6 +154,10 @@ struct dd_ctx {
   int flexible_opt = -1;
   int timing = 0;
   int fused_pq_opt = -1;            // p = 1: one kernel for p = z + beta p and q = A_sigma p (-1, 1) or two (0)
+  int prolong_arith = 0;            // p = 1: prolong-sum owners in closed form (checked against the tables)
+  int prolong_closed = 0;           // the closed form reproduces the tables
+  int prolong_tables_opt = 1;       // 0: owners in closed form where it holds (slower: 28.1 against 24.5 us at L = 2048)
+  int4 ptypes = {0, 0, 0, 0};       // p = 1: type ids of the left end, interior and right end subdomains
   dd::Timer timer;
 
   // types and subdomains
@@ -285,6 +304,8 @@ struct BInst {
   double* lop[12];        // SI-LOPCG work vectors (padded)
   LopState* lst;
   double* lop_red;
+  int4 ptypes;            // p = 1: type ids of the left end, interior and right end subdomains
+  int prolong_arith;      // the prolong-sum's owners computed in closed form (p = 1)
 };
 
 // Vector roles in BInst (the batched outer-step kernels take roles, not pointers);
@@ -383,7 +404,7 @@ void launch_b_zero_pcg(const BInst* B, const int2* vmap, int nvb, cudaStream_t s
 void launch_b_pcg_init(const BInst* B, const int2* vmap, int nvb, int b_role, cudaStream_t s);
 void launch_b_fused_pq(const BInst* B, const int2* vmap, int nvb, int ypad, cudaStream_t s);
 void launch_b_xr_update(const BInst* B, const int2* vmap, int nvb, cudaStream_t s);
-void launch_b_prolong(const BInst* B, const int2* vmap, int nvb, int mode, cudaStream_t s);
+void launch_b_prolong(const BInst* B, const int2* vmap, int nvb, int mode, bool arith, cudaStream_t s);
 void launch_b_stencil(const BInst* B, const int2* vmap, int nvb, int mass, int x_role, int y_role, cudaStream_t s);
 void launch_b_stencil_dot(const BInst* B, const int2* vmap, int nvb, int x_role, int y_role, cudaStream_t s);
 void launch_b_outer_normalize(const BInst* B, const int2* vmap, int nvb, int w_role, int mw_role, int x_role,

@@ -40,8 +40,8 @@ struct TcCfg {
   static constexpr int BK = 128 / (int)sizeof(T);   // one 128-byte swizzle row
   static constexpr int UK = 32 / (int)sizeof(T);    // K of one tcgen05.mma (32 bytes)
   // 128 x 256 tiles: 4 stages (193 KB, one CTA per SM); 128 x 160: 4 stages (145 KB, one
-  // CTA per SM); 128 x 128 tiles: 3 stages (97 KB), so that two CTAs share an SM and one's
-  // epilogue overlaps the other's MMAs
+  // CTA per SM; 6 stages measured the same); 128 x 128 tiles: 3 stages (97 KB), so that two
+  // CTAs share an SM and one's epilogue overlaps the other's MMAs
   static constexpr int STAGES = (BN_ == 128) ? 3 : 4;
   // TMEM is allocated in powers of two of at least 32 columns (one FP32 column per output column)
   static constexpr int TMEM_COLS = BN_ <= 32 ? 32 : (BN_ <= 64 ? 64 : (BN_ <= 128 ? 128 : 256));
@@ -444,7 +444,7 @@ __global__ void k_pack(Geo g, const Sub* __restrict__ subs, const int* __restric
 
 // batched: vmap[blockIdx.x] = {problem, subdomain}
 template <typename T>
-__global__ void kb_pack(const BInst* __restrict__ B, const int2* __restrict__ vmap) {
+__global__ void __launch_bounds__(128, 16) kb_pack(const BInst* __restrict__ B, const int2* __restrict__ vmap) {
   const int2 m = vmap[blockIdx.x];
   const BInst& I = B[m.x];
   if (!I.active) return;

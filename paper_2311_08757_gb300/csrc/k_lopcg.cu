@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(kThreads) kb_lop_gram(const BInst* __restrict_
                 I.lop_red, I.cnt + CNT_LOP, drop);
 }
 
-__global__ void __launch_bounds__(kThreads) kb_lop_update3(const BInst* __restrict__ B, const int2* __restrict__ vmap,
+__global__ void __launch_bounds__(kThreads, 4) kb_lop_update3(const BInst* __restrict__ B, const int2* __restrict__ vmap,
                                                            Roles3 R, int x_role, int ax_role, int mx_role,
                                                            int ro_role) {
   const int2 m = vmap[blockIdx.x];

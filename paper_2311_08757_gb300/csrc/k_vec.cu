@@ -676,14 +676,20 @@ __device__ __forceinline__ double fma_t(double a, double b, double c) { return f
 // (5 blocks) for p = 2, whose four owners per node spilled at 32 (on the L = 64, h = 1/16
 // three-dimensional box: 987 -> 971 ms per ground state).  The FP64 p = 1 variant spills a
 // little at 32 yet ran 4% faster there than at 48 without spills.
-template <int P, typename TY, bool RAS, int U>
+// ARITH (p = 1): the owners from p1_owners and their packed rows from the subdomain index
+// (subdomain i is packed row i; its type is pt.x, pt.y or pt.z for the left end, the interior
+// and the right end) instead of the two index tables -- the same values, without two levels of
+// dependent loads per node (the host checks the formula against the tables at set-up).
+template <int P, typename TY, bool RAS, int U, bool ARITH = false>
 __device__ __forceinline__ void prolong_body(VBlk vb, Geo g, const int4* __restrict__ axown,
                                                       const int4* __restrict__ subrow, const TY* __restrict__ Y,
                                                       const TY* __restrict__ wT, const TY* __restrict__ puT,
                                                       const TY* __restrict__ u0, int coarse,
                                                       const double* __restrict__ r, const double* __restrict__ q,
                                                       double* __restrict__ z, int mode, PcgState* st,
-                                                      double* partials, unsigned* counter) {
+                                                      double* partials, unsigned* counter, int kpad = 0,
+                                                      int4 pt = make_int4(0, 0, 0, 0)) {
+  static_assert(!ARITH || P == 1, "closed-form owners are those of a p = 1 box");
   if (mode != 0 && st->done) return;
   const bool flex = (mode == 2) && st->flexible;
   const long long total = (long long)g.nxi * (P == 2 ? g.nxi : 1) * g.Ypad;
@@ -701,7 +707,7 @@ __device__ __forceinline__ void prolong_body(VBlk vb, Geo g, const int4* __restr
       in[u] = t < total;
       nd[u] = node_of<P>(g, in[u] ? t : 0);
       valid[u] = in[u] && nd[u].slot < g.nyi;
-      A1[u] = __ldg(axown + nd[u].a1);
+      A1[u] = ARITH ? p1_owners(g, nd[u].a1) : __ldg(axown + nd[u].a1);
       A2[u] = (P == 2) ? __ldg(axown + nd[u].a2) : make_int4(0, 0, -1, 0);
     }
     bool ok[U][NO];
@@ -716,7 +722,13 @@ __device__ __forceinline__ void prolong_body(VBlk vb, Geo g, const int4* __restr
         const int o2 = k ? A2[u].z : A2[u].x, l2 = k ? A2[u].w : A2[u].y;
         ok[u][e] = o1 >= 0 && (P == 1 || o2 >= 0);
         sub[u][e] = ok[u][e] ? ((P == 1) ? o1 : o1 * g.L + o2) : 0;
-        sr[u][e] = __ldg(subrow + sub[u][e]);
+        if (ARITH) {
+          const int sb = sub[u][e];
+          const int ty = sb == 0 ? pt.x : (sb == g.L - 1 ? pt.z : pt.y);
+          sr[u][e] = make_int4(sb * kpad, ty * kpad, 1, 0);
+        } else {
+          sr[u][e] = __ldg(subrow + sub[u][e]);
+        }
         loc[u][e] = ok[u][e] ? (((P == 1) ? l1 : l1 * sr[u][e].z + l2) * g.Ypad + nd[u].slot) : 0;
       }
     double rv[U], qv[U];
@@ -770,15 +782,16 @@ __device__ __forceinline__ void prolong_body(VBlk vb, Geo g, const int4* __restr
   }
 }
 
-template <int P, typename TY, bool RAS, int U>
+template <int P, typename TY, bool RAS, int U, bool ARITH = false>
 __global__ void __launch_bounds__(kThreads, (P == 1 ? 8 : 5) / U) k_prolong(Geo g, const int4* __restrict__ axown,
                                                       const int4* __restrict__ subrow, const TY* __restrict__ Y,
                                                       const TY* __restrict__ wT, const TY* __restrict__ puT,
                                                       const TY* __restrict__ u0, int coarse,
                                                       const double* __restrict__ r, const double* __restrict__ q,
                                                       double* __restrict__ z, int mode, PcgState* st,
-                                                      double* partials, unsigned* counter) {
-  prolong_body<P, TY, RAS, U>(vblk_self(), g, axown, subrow, Y, wT, puT, u0, coarse, r, q, z, mode, st, partials, counter);
+                                                      double* partials, unsigned* counter, int kpad, int4 pt) {
+  prolong_body<P, TY, RAS, U, ARITH>(vblk_self(), g, axown, subrow, Y, wT, puT, u0, coarse, r, q, z, mode, st,
+                                     partials, counter, kpad, pt);
 }
 
 // nodes per thread and pass (each node's loads go out together, absent owners masked):
@@ -792,10 +805,15 @@ void launch_prolong(dd_ctx* c, int mode, cudaStream_t s, double* zout) {
   const int coarse = c->grid.coarse;
   const bool f32 = (c->grid.precision != DD_PREC_FP64);
   double* z = zout != nullptr ? zout : c->z;
-#define DD_PROLONG(PP, TY, YP, W, PU, U0, RS)                                                                   \
-  (k_prolong<PP, TY, RS, kProlongU><<<resident_grid(k_prolong<PP, TY, RS, kProlongU>, work, kThreads), kThreads, 0, s>>>(g, c->axown, c->subrow, YP, W, PU, U0, coarse, c->r, c->q, z, mode, \
-                                                 c->st, c->red, c->cnt + CNT_RZ),                                     \
+#define DD_PROLONG_A(PP, TY, YP, W, PU, U0, RS, AR)                                                                   \
+  (k_prolong<PP, TY, RS, kProlongU, AR><<<resident_grid(k_prolong<PP, TY, RS, kProlongU, AR>, work, kThreads), kThreads, 0, s>>>(g, c->axown, c->subrow, YP, W, PU, U0, coarse, c->r, c->q, z, mode, \
+                                                 c->st, c->red, c->cnt + CNT_RZ, c->kpad, c->ptypes),                 \
    dd::note_launch())
+#define DD_PROLONG(PP, TY, YP, W, PU, U0, RS)                                    \
+  do {                                                                           \
+    if (PP == 1 && c->prolong_arith) DD_PROLONG_A(1, TY, YP, W, PU, U0, RS, true); \
+    else DD_PROLONG_A(PP, TY, YP, W, PU, U0, RS, false);                         \
+  } while (0)
 #define DD_PROLONG_T(PP, RS)                                                          \
   do {                                                                                \
     if (f32) DD_PROLONG(PP, float, c->Y32, c->wT32, c->puT32, c->u0f, RS);           \
@@ -810,6 +828,7 @@ void launch_prolong(dd_ctx* c, int mode, cudaStream_t s, double* zout) {
   }
 #undef DD_PROLONG_T
 #undef DD_PROLONG
+#undef DD_PROLONG_A
   DD_CUDA(cudaGetLastError());
 }
 
@@ -1119,7 +1138,7 @@ __global__ void __launch_bounds__(kThreads) kb_zero_pcg(const BInst* __restrict_
   }
 }
 
-__global__ void __launch_bounds__(kThreads) kb_pcg_init(const BInst* __restrict__ B, const int2* __restrict__ vmap,
+__global__ void __launch_bounds__(kThreads, 8) kb_pcg_init(const BInst* __restrict__ B, const int2* __restrict__ vmap,
                                                         int b_role) {
   const int2 m = vmap[blockIdx.x];
   const BInst& I = B[m.x];
@@ -1127,7 +1146,7 @@ __global__ void __launch_bounds__(kThreads) kb_pcg_init(const BInst* __restrict_
   pcg_init_body<1>(VBlk{m.y, I.nb_init}, I.g, I.tabS, I.x, bvec(I, b_role), I.r, I.st, I.red, I.cnt + CNT_INIT);
 }
 
-__global__ void __launch_bounds__(kThreads) kb_fused_pq(const BInst* __restrict__ B, const int2* __restrict__ vmap) {
+__global__ void __launch_bounds__(kThreads, 6) kb_fused_pq(const BInst* __restrict__ B, const int2* __restrict__ vmap) {
   const int2 m = vmap[blockIdx.x];
   const BInst& I = B[m.x];
   if (!I.active) return;
@@ -1141,13 +1160,15 @@ __global__ void __launch_bounds__(kThreads) kb_xr_update(const BInst* __restrict
   xr_update_body(VBlk{m.y, I.nb_xr}, I.g.plen, I.pb0, I.pb1, I.q, I.x, I.r, I.st, I.red, I.cnt + CNT_RR);
 }
 
+template <bool ARITH>
 __global__ void __launch_bounds__(kThreads, 8 / kProlongU) kb_prolong(const BInst* __restrict__ B,
                                                                       const int2* __restrict__ vmap, int mode) {
   const int2 m = vmap[blockIdx.x];
   const BInst& I = B[m.x];
   if (!I.active) return;
-  prolong_body<1, float, false, kProlongU>(VBlk{m.y, I.nb_prolong}, I.g, I.axown, I.subrow, I.Y32, I.wT32, I.puT32,
-                                           I.u0f, I.coarse, I.r, I.q, I.z, mode, I.st, I.red, I.cnt + CNT_RZ);
+  prolong_body<1, float, false, kProlongU, ARITH>(VBlk{m.y, I.nb_prolong}, I.g, I.axown, I.subrow, I.Y32, I.wT32,
+                                                  I.puT32, I.u0f, I.coarse, I.r, I.q, I.z, mode, I.st, I.red,
+                                                  I.cnt + CNT_RZ, I.kpad, I.ptypes);
 }
 
 __global__ void __launch_bounds__(kThreads) kb_stencil(const BInst* __restrict__ B, const int2* __restrict__ vmap,
@@ -1160,7 +1181,7 @@ __global__ void __launch_bounds__(kThreads) kb_stencil(const BInst* __restrict__
 }
 
 // y = A_sigma x and (x, A_sigma x) into the outer state (the plain outer residual's first pass)
-__global__ void __launch_bounds__(kThreads) kb_stencil_dot(const BInst* __restrict__ B, const int2* __restrict__ vmap,
+__global__ void __launch_bounds__(kThreads, 6) kb_stencil_dot(const BInst* __restrict__ B, const int2* __restrict__ vmap,
                                                            int x_role, int y_role) {
   const int2 m = vmap[blockIdx.x];
   const BInst& I = B[m.x];
@@ -1169,7 +1190,7 @@ __global__ void __launch_bounds__(kThreads) kb_stencil_dot(const BInst* __restri
                         I.cnt + CNT_OUTER1, &I.ost->xAx);
 }
 
-__global__ void __launch_bounds__(kThreads) kb_outer_dots(const BInst* __restrict__ B, const int2* __restrict__ vmap,
+__global__ void __launch_bounds__(kThreads, 8) kb_outer_dots(const BInst* __restrict__ B, const int2* __restrict__ vmap,
                                                           int w_role, int mw_role) {
   const int2 m = vmap[blockIdx.x];
   const BInst& I = B[m.x];
@@ -1186,7 +1207,7 @@ __global__ void __launch_bounds__(kThreads) kb_outer_scale(const BInst* __restri
   outer_scale_body(VBlk{m.y, I.nb_vec}, I.g.plen, bvec(I, x_role), bvec(I, w_role), bvec(I, mw_role), I.ost);
 }
 
-__global__ void __launch_bounds__(kThreads) kb_outer_res(const BInst* __restrict__ B, const int2* __restrict__ vmap,
+__global__ void __launch_bounds__(kThreads, 8) kb_outer_res(const BInst* __restrict__ B, const int2* __restrict__ vmap,
                                                          int ax_role, int mx_role) {
   const int2 m = vmap[blockIdx.x];
   const BInst& I = B[m.x];
@@ -1272,7 +1293,7 @@ __global__ void __launch_bounds__(kThreads) kb_stencil2(const BInst* __restrict_
   stencil2_body<1>(VBlk{m.y, I.nb_st2}, I.g, I.tabS, I.tabM, bvec(I, x_role), bvec(I, ys_role), bvec(I, ym_role));
 }
 
-__global__ void __launch_bounds__(kThreads) kb_outer_res_ro(const BInst* __restrict__ B, const int2* __restrict__ vmap,
+__global__ void __launch_bounds__(kThreads, 8) kb_outer_res_ro(const BInst* __restrict__ B, const int2* __restrict__ vmap,
                                                             int ax_role, int mx_role, int ro_role) {
   const int2 m = vmap[blockIdx.x];
   const BInst& I = B[m.x];
@@ -1288,7 +1309,8 @@ void batch_grid_sizes(const dd_ctx* c, BInst* I) {
   I->nb_init = grid_blocks(w, kThreads);
   I->nb_fused = ntiles < 152 * 6 ? ntiles : 152 * 6;
   I->nb_xr = grid_blocks(g.plen / 2, kThreads, 4);
-  I->nb_prolong = resident_grid(k_prolong<1, float, false, kProlongU>, w, kThreads);
+  I->nb_prolong = c->prolong_arith ? resident_grid(k_prolong<1, float, false, kProlongU, true>, w, kThreads)
+                                    : resident_grid(k_prolong<1, float, false, kProlongU, false>, w, kThreads);
   I->nb_sdot = resident_grid(k_stencil<1, true>, w, kThreads);
   I->nb_st = resident_grid(k_stencil<1, false>, w, kThreads);
   I->nb_vec = grid_blocks(g.plen, kThreads);
@@ -1352,8 +1374,9 @@ void launch_b_xr_update(const BInst* B, const int2* vmap, int nvb, cudaStream_t 
   DD_CUDA(cudaGetLastError());
 }
 
-void launch_b_prolong(const BInst* B, const int2* vmap, int nvb, int mode, cudaStream_t s) {
-  (kb_prolong<<<nvb, kThreads, 0, s>>>(B, vmap, mode), dd::note_launch());
+void launch_b_prolong(const BInst* B, const int2* vmap, int nvb, int mode, bool arith, cudaStream_t s) {
+  if (arith) (kb_prolong<true><<<nvb, kThreads, 0, s>>>(B, vmap, mode), dd::note_launch());
+  else (kb_prolong<false><<<nvb, kThreads, 0, s>>>(B, vmap, mode), dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 

@@ -87,7 +87,29 @@ def test_mixed_ground_state(name, prec):
     xh = host(x)
     Mx = P.M @ xh
     eta = np.linalg.norm(P.A @ xh - lam * Mx) / (abs(lam) * np.linalg.norm(Mx))
-    assert eta <= 1.5e-8
+    assert eta <= 1e-8 + 1e-12   # the stop rule's 1e-8, plus the rounding of recomputing eta
+
+
+@pytest.mark.parametrize("name", ["cfg1", "cfg2_small"])
+def test_fp8_local_inverses_do_not_allow_a_solve(name):
+    """E4M3 local inverses (3 mantissa bits): the preconditioner is within about 10% of
+    M_AS2^{-1}, but no longer close enough to SPD for the flexible CG -- on the shifted system
+    A_sigma w = M 1 it does not reach rTOL = 1e-8 in 800 iterations, where the BF16 form
+    converges in a few dozen."""
+    w = MIXED[name]
+    b = None
+    out = {}
+    for prec in ("bf16", "fp8"):
+        with make_solver(w, precision=prec) as es:
+            es.prepare()
+            ones = gpu_vec(np.ones(w.dofs))
+            b = gpu_vec(np.zeros(w.dofs))
+            dd.dd_apply_operator(es.ctx, dd.DD_OP_MASS, ones, b)
+            x = gpu_vec(np.zeros(w.dofs))
+            out[prec] = dd.dd_pcg_solve(es.ctx, b, x, 1e-8, 800, allow_maxit=True)
+    print(f"{name}: bf16 {out['bf16']}, fp8 {out['fp8']}")
+    assert out["bf16"][0] < 200 and out["bf16"][1] <= 1e-8
+    assert out["fp8"][0] == 800 and out["fp8"][1] > 1e-6
 
 
 @pytest.mark.parametrize("prec", ["bf16", "tf32", "fp8"])
