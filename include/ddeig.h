@@ -363,7 +363,15 @@ int dd_coarse_matrix(dd_ctx* ctx, double* A0_host);
  *                       index tables in the prolong-sum; 0 computes them in closed form where
  *                       set-up found the formula equal to the tables (same values, two dependent
  *                       loads fewer per node, but more integer work: 28.1 against 24.5 us per
- *                       launch on the L = 2048, h = 1/32 box) [1] */
+ *                       launch on the L = 2048, h = 1/32 box) [1]
+ *   DD_OPT_PQ_ARITH     p = 1, fused p update: the arithmetic of q = A_sigma p inside the PCG
+ *                       iteration.  0 FP64; 1 float pairs on the FP32 pipe (each coefficient and
+ *                       p value split into hi + lo, error-free products and sums; q, p and every
+ *                       reduction stay FP64; q agrees with the FP64 stencil to about 2^-47 times
+ *                       the sum of the taps' magnitudes).  Only the inner solve's operator
+ *                       changes: residuals and Rayleigh quotients of the outer iteration, the
+ *                       stop rules and dd_apply_operator stay FP64.  -1: 1 when the local
+ *                       inverses are rounded (precision other than FP64), else 0 [-1] */
 #define DD_OPT_CHECK_EVERY 0
 #define DD_OPT_USE_GRAPH   1
 #define DD_OPT_FLEXIBLE    2
@@ -376,6 +384,7 @@ int dd_coarse_matrix(dd_ctx* ctx, double* A0_host);
 #define DD_OPT_COARSE_SOLVE 9
 #define DD_OPT_FUSED_PQ    10
 #define DD_OPT_PROLONG_TABLES 11
+#define DD_OPT_PQ_ARITH    12
 int dd_set_option(dd_ctx* ctx, int option, int value);
 
 /* Per-kernel-class timing collected while DD_OPT_TIMING = 1: for class k (0 <= k < count),

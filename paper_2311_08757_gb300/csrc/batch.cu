@@ -50,6 +50,7 @@ struct BGroup {
   size_t cr_smem = 0;
   int ypad = 0, precision = 0, check_every = 8;
   bool arith = true;               // every instance's prolong-sum owners in closed form
+  bool pairs = false;              // q = A_sigma p in float pairs (the same choice for every instance)
   dd::BGemm* gemm = nullptr;
   int bn = 0;                      // N tile of the grouped contraction (timed at build)
   cudaStream_t s = nullptr, side = nullptr;
@@ -79,6 +80,7 @@ struct dd_batch {
   std::map<int, std::vector<BGroup*>> engines;   // built groups, per group count
   std::map<long long, double> timed;              // (method, groups) -> best call seconds
   int groups_opt = 0;          // 0: chosen by timing; > 0: fixed
+  long long opt_sig = -1;      // the instances' options the built groups were made for
   int last_batched = 0, last_groups = 0, last_bn = 0;
   double last_setup_s = 0.0, last_total_s = 0.0;
 };
@@ -105,6 +107,23 @@ void free_group(BGroup* g) {
   if (g->ev_fork) cudaEventDestroy(g->ev_fork);
   if (g->ev_join) cudaEventDestroy(g->ev_join);
   delete g;
+}
+
+// The per-instance options a built group bakes in; a change on any instance's context
+// (dd_batch_context + dd_set_option) drops the built groups and their timings.
+long long option_signature(const dd_batch* b) {
+  long long h = 1469598103934665603LL;
+  for (const dd_ctx* c : b->ctx)
+    for (int v : {c->prolong_arith, c->pq_pairs, c->flexible_opt, c->check_every, c->gemm_bn_opt})
+      h = (h ^ (long long)(v + 7)) * 1099511628211LL;
+  return h;
+}
+
+void drop_engines(dd_batch* b) {
+  for (auto& kv : b->engines)
+    for (BGroup* g : kv.second) free_group(g);
+  b->engines.clear();
+  b->timed.clear();
 }
 
 void destroy_all(dd_batch* b) {
@@ -165,7 +184,7 @@ void precond(BGroup* g, int mode) {
 }
 
 void pcg_iteration(BGroup* g) {
-  dd::launch_b_fused_pq(g->B, g->vm_fused, g->n_fused, g->ypad, g->s);
+  dd::launch_b_fused_pq(g->B, g->vm_fused, g->n_fused, g->ypad, g->pairs, g->s);
   dd::launch_b_xr_update(g->B, g->vm_xr, g->n_xr, g->s);
   precond(g, 2);
 }
@@ -235,6 +254,9 @@ BGroup* build_group(dd_batch* b, const std::vector<int>& idx) {
       I.x = c->x; I.r = c->r; I.z = c->z; I.pb0 = c->pb[0]; I.pb1 = c->pb[1]; I.q = c->q;
       I.w1 = c->w1; I.w2 = c->w2; I.w3 = c->w3; I.xe = c->xe;
       I.tabS = c->tabS; I.tabM = c->tabM;
+      I.tabS2 = c->tabS2;
+      I.pq_pairs = c->pq_pairs;
+      g->pairs = c->pq_pairs != 0;
       I.st = c->st; I.ost = c->ost; I.red = c->red; I.cnt = c->cnt;
       I.subs = c->subs; I.slot_of_sub = c->slot_of_sub; I.Rpack = c->Rpack; I.wT = c->wT; I.c0 = c->c0;
       I.u0 = c->u0; I.u0f = c->u0f; I.Y32 = c->Y32; I.wT32 = c->wT32; I.puT32 = c->puT32;
@@ -768,7 +790,9 @@ int dd_batch_ground_states(dd_batch* b, int method, int threads, double* lambda_
   // contraction and the cyclic-reduction coarse solve, PCG inner solves)
   bool engine = b->eligible && b->groups_opt >= 0 && (method == DD_BATCH_IPM || method == DD_BATCH_LOPCG_FUSED);
   for (dd_ctx* c : b->ctx)
-    if (c->krylov != 0 || c->ras != 0 || c->coarse_mode == 2 || c->timing || c->fused_pq_opt == 0) engine = false;
+    if (c->krylov != 0 || c->ras != 0 || c->coarse_mode == 2 || c->timing || c->fused_pq_opt == 0 ||
+        c->pq_pairs != b->ctx.front()->pq_pairs)
+      engine = false;
   const auto t_start = std::chrono::steady_clock::now();
   std::vector<double> setup_s(n, 0.0);
   Ready ready(n);
@@ -781,6 +805,11 @@ int dd_batch_ground_states(dd_batch* b, int method, int threads, double* lambda_
       if (method == DD_BATCH_LOPCG_FUSED) ensure_lopcg(b);   // before any worker touches a context
     } catch (const dd::Error& e) {
       return e.code;
+    }
+    const long long sig = option_signature(b);
+    if (sig != b->opt_sig) {
+      drop_engines(b);
+      b->opt_sig = sig;
     }
     G = choose_groups(b, method);
     fresh_engine = b->engines.find(G) == b->engines.end();

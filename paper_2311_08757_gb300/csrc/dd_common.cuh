@@ -184,6 +184,53 @@ __device__ __forceinline__ double f32_to_f64(float f) {
   return __hiloint2double((int)hi, (int)(m << 29));
 }
 
+// ---- float pairs: FP64 values carried as hi + lo on the FP32 pipe ---------------------
+// A pair (hi, lo) of floats stands for hi + lo (48 significand bits).  Products of pairs are
+// formed with the FMA error-free product (Dekker's two-product: a*b = p + fma(a, b, -p)
+// exactly), sums of the leading parts with Knuth's two-sum (s = a + b exactly as s + err);
+// the error terms and the cross products hi*lo' + lo*hi' are carried in the low word.  The
+// explicit _rn intrinsics keep the compiler from contracting the error-free steps.
+
+static __device__ __noinline__ float2 f64_split_slow(double d) {
+  const float hi = __double2float_rz(d);
+  return make_float2(hi, __double2float_rz(d - (double)hi));
+}
+
+// d = hi + lo + e with |e| < 2^-47 |d|: hi is d's first 24 significand bits, lo the next 24
+// (both truncated toward zero).  Integer operations on the two words of d for
+// 2^-74 <= |d| < 2^127 (so that lo stays a normal float) and zeros; other values (tiny,
+// huge, infinities, NaNs) take the hardware conversions.
+__device__ __forceinline__ float2 f64_split(double d) {
+  const unsigned H = (unsigned)__double2hiint(d), Lw = (unsigned)__double2loint(d);
+  const unsigned E = (H >> 20) & 0x7FFu;
+  if (__builtin_expect(E - 949u > 1150u - 949u, 0)) {
+    if (((H << 1) | Lw) == 0u) return make_float2(0.0f, 0.0f);
+    return f64_split_slow(d);
+  }
+  const unsigned sgn = H & 0x80000000u;
+  // exponent rebias 1023 -> 127 (896 << 20) and the 20 + 3 leading significand bits
+  const float hi = __uint_as_float(sgn | ((H - 0x38000000u) << 3) | (Lw >> 29));
+  // the remaining 29 bits: normalise to bit 31, keep 24 (the leading one lands on the
+  // exponent field's lowest bit, hence E - 918 - lz rather than E - 917 - lz)
+  const unsigned m29 = Lw & 0x1FFFFFFFu;
+  const unsigned lz = __clz((int)m29);
+  const unsigned lo_bits = sgn | (((E - 918u - lz) << 23) + ((m29 << lz) >> 8));
+  return make_float2(hi, __uint_as_float(m29 ? lo_bits : 0u));
+}
+
+// (s, c) += (th + tl) * (xh + xl): s the running leading sum, c the low-order accumulator
+__device__ __forceinline__ void pair_fma(float th, float tl, float xh, float xl, float& s, float& c) {
+  const float p = __fmul_rn(th, xh);
+  const float e = __fmaf_rn(th, xh, -p);                   // th * xh = p + e exactly
+  const float u = __fadd_rn(s, p);
+  const float bv = __fsub_rn(u, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(u, bv)), __fsub_rn(p, bv));   // s + p = u + err
+  s = u;
+  c = __fadd_rn(c, __fadd_rn(e, err));
+  c = __fmaf_rn(th, xl, c);
+  c = __fmaf_rn(tl, xh, c);
+}
+
 // Subdomain-local vectors stored in the kpad-strided arrays (rounded local inverses,
 // restrictions, local results, coarse and partition-of-unity weights) keep the column
 // padding of the global vectors: local column cc, slot sj sits at cc * Ypad + sj, so a

@@ -158,6 +158,8 @@ struct dd_ctx {
   int prolong_closed = 0;           // the closed form reproduces the tables
   int prolong_tables_opt = 1;       // 0: owners in closed form where it holds (slower: 28.1 against 24.5 us at L = 2048)
   int4 ptypes = {0, 0, 0, 0};       // p = 1: type ids of the left end, interior and right end subdomains
+  int pq_pairs_opt = -1;            // q = A_sigma p of the fused p = 1 kernel: -1 automatic, 0 FP64, 1 float pairs
+  int pq_pairs = 0;                 // the resolved choice
   dd::Timer timer;
 
   // types and subdomains
@@ -183,6 +185,7 @@ struct dd_ctx {
   double* tabA = nullptr;   // K + M_V
   double* tabM = nullptr;   // M
   double* tabS = nullptr;   // K + M_V - sigma M
+  float2* tabS2 = nullptr;  // tabS as float pairs (hi, lo)
   double* tabL = nullptr;   // K + M_V - lambda M (adjoint of the eigenvector)
   double* qp_part = nullptr;      // quadrature-point reduction partials
   long long qp_part_len = 0;
@@ -279,6 +282,8 @@ struct BInst {
   Geo g;
   double *x, *r, *z, *pb0, *pb1, *q, *w1, *w2, *w3, *xe;   // padded vectors
   const double *tabS, *tabM;
+  const float2* tabS2;
+  int pq_pairs;
   PcgState* st;
   OuterState* ost;
   double* red;
@@ -402,7 +407,7 @@ void batch_grid_sizes(const dd_ctx* c, BInst* I);   // the nb_* of the plain lau
 void launch_b_pcg_reset(const BInst* B, int n, double rtol2, int maxit, cudaStream_t s);
 void launch_b_zero_pcg(const BInst* B, const int2* vmap, int nvb, cudaStream_t s);
 void launch_b_pcg_init(const BInst* B, const int2* vmap, int nvb, int b_role, cudaStream_t s);
-void launch_b_fused_pq(const BInst* B, const int2* vmap, int nvb, int ypad, cudaStream_t s);
+void launch_b_fused_pq(const BInst* B, const int2* vmap, int nvb, int ypad, bool pairs, cudaStream_t s);
 void launch_b_xr_update(const BInst* B, const int2* vmap, int nvb, cudaStream_t s);
 void launch_b_prolong(const BInst* B, const int2* vmap, int nvb, int mode, bool arith, cudaStream_t s);
 void launch_b_stencil(const BInst* B, const int2* vmap, int nvb, int mass, int x_role, int y_role, cudaStream_t s);

@@ -182,10 +182,20 @@ __global__ void k_tabS(long long n, const double* __restrict__ A, const double* 
     S[t] = A[t] - sigma * M[t];
 }
 
+__global__ void k_tab_split(long long n, const double* __restrict__ S, float2* __restrict__ S2) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    S2[t] = f64_split(S[t]);
+}
+
 void launch_tabS(dd_ctx* c, double sigma) {
   const long long n = (long long)c->g.ncls * c->g.ntap;
   (k_tabS<<<grid_blocks(n, kThreads), kThreads, 0, c->stream>>>(n, c->tabA, c->tabM, sigma, c->tabS), dd::note_launch());
   DD_CUDA(cudaGetLastError());
+  if (c->tabS2) {
+    (k_tab_split<<<grid_blocks(n, kThreads), kThreads, 0, c->stream>>>(n, c->tabS, c->tabS2), dd::note_launch());
+    DD_CUDA(cudaGetLastError());
+  }
 }
 
 // ----------------------------------------------------------------------------------------
@@ -514,6 +524,97 @@ __device__ __forceinline__ void fused_pq_body(VBlk vb, Geo g, const double* __re
   }
 }
 
+// The same pass with q = A_sigma p evaluated in float pairs on the FP32 pipe: each staged p
+// value is also split into (hi, lo) (integer operations), the 9 taps accumulate with the
+// error-free product and sum (pair_fma) against the split table, and q = hi + lo in FP64.
+// p_k, the (p, q) partial and everything else stay FP64; q differs from the FP64 stencil by
+// about 2^-47 times the sum of the taps' magnitudes.  Three FP64 instructions per node (p
+// update, q = hi + lo, the partial) instead of eleven.
+__device__ __forceinline__ void fused_pq_pairs_body(VBlk vb, Geo g, const float2* __restrict__ tab2,
+                                                    const double* __restrict__ z, double* pb0, double* pb1,
+                                                    double* __restrict__ q, PcgState* st, double* partials,
+                                                    unsigned* counter) {
+  if (st->done) return;
+  extern __shared__ double sp_raw[];
+  const int Y = g.Ypad, yl = g.ylog;
+  const int nstage = (kFusedCols + 2) * Y + 2;
+  double* sp = sp_raw + 1;   // one zero guard element on each side
+  float2* sp2_raw = reinterpret_cast<float2*>(sp_raw + nstage);
+  float2* sp2 = sp2_raw + 1;
+  const int k = st->iter;
+  const double beta = st->beta;
+  const double* __restrict__ pp = p_prev(pb0, pb1, k);
+  double* __restrict__ pc = p_cur(pb0, pb1, k);
+  const int ntiles = (g.nxi + kFusedCols - 1) / kFusedCols;
+  if (threadIdx.x == 0) {
+    sp_raw[0] = 0.0;
+    sp_raw[nstage - 1] = 0.0;
+    sp2_raw[0] = make_float2(0.0f, 0.0f);
+    sp2_raw[nstage - 1] = make_float2(0.0f, 0.0f);
+  }
+  double acc[1] = {0.0};
+  for (int tile = vb.b; tile < ntiles; tile += vb.nb) {
+    const int a0 = 1 + tile * kFusedCols;
+    const int own = min(kFusedCols, g.nxi - (a0 - 1));
+    const int nload = (own + 2) << yl;
+    const long long gbase = (long long)(a0 - 1) << yl;
+    __syncthreads();
+    for (int e = threadIdx.x; e < nload; e += blockDim.x) {
+      const double pv = fma(beta, pp[gbase + e], z[gbase + e]);
+      sp[e] = pv;
+      sp2[e] = f64_split(pv);
+    }
+    if (threadIdx.x == 0) {   // corner tap of the last (pad) slot of a partial tile
+      sp[nload] = 0.0;
+      sp2[nload] = make_float2(0.0f, 0.0f);
+    }
+    __syncthreads();
+    const int nown = own << yl;
+    for (int e = threadIdx.x; e < nown; e += blockDim.x) {
+      const int se = e + Y;
+      const long long gi = gbase + se;
+      const double pv = sp[se];
+      pc[gi] = pv;
+      const int cls = ((a0 + (e >> yl)) % g.n) * Y + (e & (Y - 1));
+      float hs = 0.0f, ls = 0.0f;
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx)
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+          const float2 t = __ldg(tab2 + (size_t)((dx + 1) * 3 + (dy + 1)) * g.ncls + cls);
+          const float2 x = sp2[se + dx * Y + dy];
+          pair_fma(t.x, t.y, x.x, x.y, hs, ls);
+        }
+      const double qv = f32_to_f64(hs) + f32_to_f64(ls);
+      q[gi] = qv;
+      acc[0] = fma(pv, qv, acc[0]);
+    }
+  }
+  double tot[1];
+  if (grid_sum_last<1>(acc, partials, counter, tot, vb) && threadIdx.x == 0) {
+    const double pq = tot[0];
+    st->pq = pq;
+    if (!(pq > 0.0)) {
+      st->status = isfinite(pq) ? DD_ENOTSPD : DD_ENAN;
+      st->done = 1;
+    } else {
+      st->alpha = st->rho / pq;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_fused_pq_pairs(Geo g, const float2* __restrict__ tab2,
+                                                             const double* __restrict__ z, double* pb0, double* pb1,
+                                                             double* __restrict__ q, PcgState* st, double* partials,
+                                                             unsigned* counter) {
+  fused_pq_pairs_body(vblk_self(), g, tab2, z, pb0, pb1, q, st, partials, counter);
+}
+
+static size_t fused_pq_smem(int ypad, bool pairs) {
+  const size_t n = (size_t)(kFusedCols + 2) * ypad + 2;
+  return n * (sizeof(double) + (pairs ? sizeof(float2) : 0));
+}
+
 template <int U2>
 __global__ void __launch_bounds__(kThreads) k_fused_pq(Geo g, const double* __restrict__ tab,
                                                        const double* __restrict__ z, double* pb0, double* pb1,
@@ -526,12 +627,19 @@ void launch_fused_pq(dd_ctx* c, cudaStream_t s) {
   const Geo& g = c->g;
   const int ntiles = (g.nxi + kFusedCols - 1) / kFusedCols;
   const int nb = ntiles < 152 * 6 ? ntiles : 152 * 6;
-  const size_t smem = sizeof(double) * ((size_t)(kFusedCols + 2) * g.Ypad + 2);
+  const size_t smem = fused_pq_smem(g.Ypad, c->pq_pairs != 0);
   static PerDeviceOnce attr;   // once per device
   once_per_device(attr, [] {
     DD_CUDA(cudaFuncSetAttribute(k_fused_pq<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     DD_CUDA(cudaFuncSetAttribute(k_fused_pq<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    DD_CUDA(cudaFuncSetAttribute(k_fused_pq_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   });
+  if (c->pq_pairs) {
+    (k_fused_pq_pairs<<<nb, kThreads, smem, s>>>(g, c->tabS2, c->z, c->pb[0], c->pb[1], c->q, c->st, c->red,
+                                                c->cnt + CNT_PQ), dd::note_launch());
+    DD_CUDA(cudaGetLastError());
+    return;
+  }
   // two nodes per thread and pass by default: 53.0 against 53.8 us per launch on the
   // L = 2048, h = 1/32 box, the same bits
   if (c->fused_pq_opt != 1)
@@ -1146,11 +1254,15 @@ __global__ void __launch_bounds__(kThreads, 8) kb_pcg_init(const BInst* __restri
   pcg_init_body<1>(VBlk{m.y, I.nb_init}, I.g, I.tabS, I.x, bvec(I, b_role), I.r, I.st, I.red, I.cnt + CNT_INIT);
 }
 
+template <bool PAIRS>
 __global__ void __launch_bounds__(kThreads, 6) kb_fused_pq(const BInst* __restrict__ B, const int2* __restrict__ vmap) {
   const int2 m = vmap[blockIdx.x];
   const BInst& I = B[m.x];
   if (!I.active) return;
-  fused_pq_body<2>(VBlk{m.y, I.nb_fused}, I.g, I.tabS, I.z, I.pb0, I.pb1, I.q, I.st, I.red, I.cnt + CNT_PQ);
+  if (PAIRS)
+    fused_pq_pairs_body(VBlk{m.y, I.nb_fused}, I.g, I.tabS2, I.z, I.pb0, I.pb1, I.q, I.st, I.red, I.cnt + CNT_PQ);
+  else
+    fused_pq_body<2>(VBlk{m.y, I.nb_fused}, I.g, I.tabS, I.z, I.pb0, I.pb1, I.q, I.st, I.red, I.cnt + CNT_PQ);
 }
 
 __global__ void __launch_bounds__(kThreads) kb_xr_update(const BInst* __restrict__ B, const int2* __restrict__ vmap) {
@@ -1359,13 +1471,15 @@ void launch_b_pcg_init(const BInst* B, const int2* vmap, int nvb, int b_role, cu
   DD_CUDA(cudaGetLastError());
 }
 
-void launch_b_fused_pq(const BInst* B, const int2* vmap, int nvb, int ypad, cudaStream_t s) {
-  const size_t smem = sizeof(double) * ((size_t)(kFusedCols + 2) * ypad + 2);
+void launch_b_fused_pq(const BInst* B, const int2* vmap, int nvb, int ypad, bool pairs, cudaStream_t s) {
+  const size_t smem = fused_pq_smem(ypad, pairs);
   static PerDeviceOnce attr;
   once_per_device(attr, [] {
-    DD_CUDA(cudaFuncSetAttribute(kb_fused_pq, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    DD_CUDA(cudaFuncSetAttribute(kb_fused_pq<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    DD_CUDA(cudaFuncSetAttribute(kb_fused_pq<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   });
-  (kb_fused_pq<<<nvb, kThreads, smem, s>>>(B, vmap), dd::note_launch());
+  if (pairs) (kb_fused_pq<true><<<nvb, kThreads, smem, s>>>(B, vmap), dd::note_launch());
+  else (kb_fused_pq<false><<<nvb, kThreads, smem, s>>>(B, vmap), dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 
