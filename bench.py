@@ -250,7 +250,12 @@ def kernel_model(w, info, ntype_counts, nloc_by_type, band, precision):
         per_sweep = n * b - b * (b + 1) / 2
         fp64_band += c * 2 * 2 * per_sweep
     taps = 3 ** (w.p + 1)
-    if w.p == 1:   # fused p update + stencil + (p, q)
+    if w.p == 1 and mixed:
+        # fused p update + stencil + (p, q) with q = A_sigma p in float pairs (the default with
+        # rounded local inverses): FP64 p update, q = hi + lo and the (p, q) FMA (5 flops); per
+        # tap one error-free product and sum with the cross terms (15 FP32 flops)
+        stencil = (5.0 * ndof, 15.0 * taps * ndof, 0.0, 32.0 * ndof)
+    elif w.p == 1:   # fused p update + stencil + (p, q)
         stencil = (2.0 * (taps + 2) * ndof, 0.0, 0.0, 32.0 * ndof)
     else:
         stencil = (2.0 * (taps + 1) * ndof, 0.0, 0.0, 16.0 * ndof)
@@ -305,7 +310,6 @@ def roofline_entry(name, model, ms_total, nlaunch, peaks, peak_src, precision, a
 # at the L = 2048, h = 1/32 workload, from one ncu capture of each; a kernel changed since its
 # capture is left out.
 TRAFFIC = {
-    "stencil_Asigma": (33.651 + 0.615) * 1e6,
     "prolong_sum": (44.916 + 0.131) * 1e6,
     "xr_update": (67.133 + 0.625) * 1e6,
     "pack_restrict": (16.874 + 0.000) * 1e6,
@@ -923,7 +927,9 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64 (local inverses %s)" % args.precision, "data": "synthetic",
+            "vs_baseline": None, "data": "synthetic",
+            "dtype": "f64 (local inverses %s%s)" % (args.precision, "; inner-solve A_sigma p in float pairs"
+                                                    if args.precision in ("bf16", "tf32") and w.p == 1 else ""),
             "config": {"workload": workload_label(w),
                        "precision": args.precision, "l2": "flushed between steps (256 MB write)",
                        "local_gemm_tile": f"128x{dd.dd_query(mixed.ctx)['gemm_tile_n']}",

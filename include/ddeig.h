@@ -364,14 +364,25 @@ int dd_coarse_matrix(dd_ctx* ctx, double* A0_host);
  *                       set-up found the formula equal to the tables (same values, two dependent
  *                       loads fewer per node, but more integer work: 28.1 against 24.5 us per
  *                       launch on the L = 2048, h = 1/32 box) [1]
- *   DD_OPT_PQ_ARITH     p = 1, fused p update: the arithmetic of q = A_sigma p inside the PCG
- *                       iteration.  0 FP64; 1 float pairs on the FP32 pipe (each coefficient and
- *                       p value split into hi + lo, error-free products and sums; q, p and every
- *                       reduction stay FP64; q agrees with the FP64 stencil to about 2^-47 times
- *                       the sum of the taps' magnitudes).  Only the inner solve's operator
- *                       changes: residuals and Rayleigh quotients of the outer iteration, the
- *                       stop rules and dd_apply_operator stay FP64.  -1: 1 when the local
- *                       inverses are rounded (precision other than FP64), else 0 [-1] */
+ *   DD_OPT_PAIRS        p = 1: the FP64 arithmetic of the PCG iteration that the
+ *                       FP32 pipe can carry, done in float pairs (a value split into hi + lo,
+ *                       48 significand bits; error-free products and sums).  1: q = A_sigma p
+ *                       (each coefficient and p value split; q agrees with the FP64 stencil to
+ *                       about 2^-47 times the sum of the taps' magnitudes) and the partial sums
+ *                       of (r, r) (r scaled by a power of two from the previous (r, r), error
+ *                       about 2^-46 of each thread's sum; the sum across threads stays FP64).
+ *                       p, q, x, r, z and their updates, (p, q), (r, z), (q, z), the
+ *                       outer iteration's residuals and Rayleigh quotients, the stop rules and
+ *                       dd_apply_operator stay FP64.  0: all FP64.  Needs at most 256 padded
+ *                       rows (Ypad).  -1: 1 when the local inverses are rounded (precision
+ *                       other than FP64) and Ypad <= 256, else 0 [-1]
+ *   DD_OPT_PDL          1: the kernels of the PCG iteration's chain (fused p update, x/r update,
+ *                       restriction packing, local contraction, prolong-sum) are launched with
+ *                       programmatic dependent launch, so that each one's blocks are scheduled
+ *                       while its predecessor drains (each waits for the predecessor's results
+ *                       before reading anything); 0: plain launches.  The same results; on the
+ *                       L = 2048, h = 1/32 box the ground state took 24.0 ms with it against
+ *                       23.3 ms without, hence off by default [0] */
 #define DD_OPT_CHECK_EVERY 0
 #define DD_OPT_USE_GRAPH   1
 #define DD_OPT_FLEXIBLE    2
@@ -384,7 +395,8 @@ int dd_coarse_matrix(dd_ctx* ctx, double* A0_host);
 #define DD_OPT_COARSE_SOLVE 9
 #define DD_OPT_FUSED_PQ    10
 #define DD_OPT_PROLONG_TABLES 11
-#define DD_OPT_PQ_ARITH    12
+#define DD_OPT_PAIRS       12
+#define DD_OPT_PDL         13
 int dd_set_option(dd_ctx* ctx, int option, int value);
 
 /* Per-kernel-class timing collected while DD_OPT_TIMING = 1: for class k (0 <= k < count),

@@ -658,8 +658,8 @@ int dd_setup(const dd_grid* gr, const double* V, size_t nV, void* stream, dd_ctx
     c->tabA = (double*)dev_alloc(c, sizeof(double) * ntab);
     c->tabM = (double*)dev_alloc(c, sizeof(double) * ntab);
     c->tabS = (double*)dev_alloc(c, sizeof(double) * ntab);
-    if (g.p == 1) c->tabS2 = (float2*)dev_alloc(c, sizeof(float2) * ntab);
-    c->pq_pairs = (g.p == 1 && G.precision != DD_PREC_FP64) ? 1 : 0;
+    if (g.p == 1) c->tabS2 = (float2*)dev_alloc(c, sizeof(float2) * kPairTapStride * g.ncls);
+    c->pq_pairs = (g.p == 1 && g.Ypad <= 256 && G.precision != DD_PREC_FP64) ? 1 : 0;
     launch_build_tables(c);
     build_subdomains(c);
     c->x = alloc_vec(c);
@@ -1300,11 +1300,17 @@ int dd_set_option(dd_ctx* c, int option, int value) {
       if (value >= 1 && c->g.p == 2) return fail(c, DD_EINVAL, "the fused p update and stencil needs p = 1");
       c->fused_pq_opt = value;
       break;
-    case DD_OPT_PQ_ARITH:
-      if (value < -1 || value > 1) return fail(c, DD_EINVAL, "p q arithmetic must be -1, 0 or 1");
-      if (value == 1 && c->g.p == 2) return fail(c, DD_EINVAL, "float-pair q = A_sigma p needs p = 1");
+    case DD_OPT_PDL:
+      if (value != 0 && value != 1) return fail(c, DD_EINVAL, "programmatic dependent launch must be 0 or 1");
+      c->pdl = value;
+      break;
+    case DD_OPT_PAIRS:
+      if (value < -1 || value > 1) return fail(c, DD_EINVAL, "float pairs must be -1, 0 or 1");
+      if (value == 1 && (c->g.p == 2 || c->g.Ypad > 256))
+        return fail(c, DD_EINVAL, "float pairs need p = 1 and at most 256 padded rows");
       c->pq_pairs_opt = value;
-      c->pq_pairs = value >= 0 ? value : ((c->g.p == 1 && c->grid.precision != DD_PREC_FP64) ? 1 : 0);
+      c->pq_pairs = value >= 0 ? value
+                               : ((c->g.p == 1 && c->g.Ypad <= 256 && c->grid.precision != DD_PREC_FP64) ? 1 : 0);
       break;
     case DD_OPT_PROLONG_TABLES:
       if (value != 0 && value != 1) return fail(c, DD_EINVAL, "prolong tables must be 0 or 1");

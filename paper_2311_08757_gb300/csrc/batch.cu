@@ -185,7 +185,7 @@ void precond(BGroup* g, int mode) {
 
 void pcg_iteration(BGroup* g) {
   dd::launch_b_fused_pq(g->B, g->vm_fused, g->n_fused, g->ypad, g->pairs, g->s);
-  dd::launch_b_xr_update(g->B, g->vm_xr, g->n_xr, g->s);
+  dd::launch_b_xr_update(g->B, g->vm_xr, g->n_xr, g->pairs, g->s);
   precond(g, 2);
 }
 

@@ -77,6 +77,10 @@ __host__ __device__ inline int4 p1_owners(const Geo& g, int a) {
   return ihi > ilo ? make_int4(ilo, l0, ihi, a - (lo1 > 1 ? lo1 : 1)) : make_int4(ilo, l0, -1, 0);
 }
 
+// The float-pair stencil table of a p = 1 box holds each class's 9 taps and one zero pad, so
+// that a class's row is five aligned 16-byte loads.
+constexpr int kPairTapStride = 10;
+
 // Subdomain descriptor on the device.
 struct Sub {
   int type;     // compact type id
@@ -158,6 +162,7 @@ struct dd_ctx {
   int prolong_closed = 0;           // the closed form reproduces the tables
   int prolong_tables_opt = 1;       // 0: owners in closed form where it holds (slower: 28.1 against 24.5 us at L = 2048)
   int4 ptypes = {0, 0, 0, 0};       // p = 1: type ids of the left end, interior and right end subdomains
+  int pdl = 0;                      // PCG chain kernels launched with programmatic dependent launch
   int pq_pairs_opt = -1;            // q = A_sigma p of the fused p = 1 kernel: -1 automatic, 0 FP64, 1 float pairs
   int pq_pairs = 0;                 // the resolved choice
   dd::Timer timer;
@@ -185,7 +190,7 @@ struct dd_ctx {
   double* tabA = nullptr;   // K + M_V
   double* tabM = nullptr;   // M
   double* tabS = nullptr;   // K + M_V - sigma M
-  float2* tabS2 = nullptr;  // tabS as float pairs (hi, lo)
+  float2* tabS2 = nullptr;  // p = 1: tabS as float pairs (hi, lo), class-major [cls][kPairTapStride]
   double* tabL = nullptr;   // K + M_V - lambda M (adjoint of the eigenvector)
   double* qp_part = nullptr;      // quadrature-point reduction partials
   long long qp_part_len = 0;
@@ -408,7 +413,7 @@ void launch_b_pcg_reset(const BInst* B, int n, double rtol2, int maxit, cudaStre
 void launch_b_zero_pcg(const BInst* B, const int2* vmap, int nvb, cudaStream_t s);
 void launch_b_pcg_init(const BInst* B, const int2* vmap, int nvb, int b_role, cudaStream_t s);
 void launch_b_fused_pq(const BInst* B, const int2* vmap, int nvb, int ypad, bool pairs, cudaStream_t s);
-void launch_b_xr_update(const BInst* B, const int2* vmap, int nvb, cudaStream_t s);
+void launch_b_xr_update(const BInst* B, const int2* vmap, int nvb, bool pairs, cudaStream_t s);
 void launch_b_prolong(const BInst* B, const int2* vmap, int nvb, int mode, bool arith, cudaStream_t s);
 void launch_b_stencil(const BInst* B, const int2* vmap, int nvb, int mass, int x_role, int y_role, cudaStream_t s);
 void launch_b_stencil_dot(const BInst* B, const int2* vmap, int nvb, int x_role, int y_role, cudaStream_t s);
@@ -485,6 +490,30 @@ struct Error {
 }  // namespace dd
 
 #include <atomic>
+#include <utility>
+
+namespace dd {
+// Launch of a kernel of the PCG iteration's chain.  With pdl set, the launch carries the
+// programmatic-serialization attribute: the kernel's blocks may be scheduled while its
+// predecessor on the stream drains, and wait in griddepcontrol.wait (pdl_wait) until the
+// predecessor has completed and its writes are visible.  Without it, a plain launch.
+template <typename... KArgs, typename... Args>
+void launch_chain(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
+                  Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = pdl ? at : nullptr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  DD_CUDA(cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...));
+  note_launch();
+}
+}  // namespace dd
 
 namespace dd {
 // cudaFuncSetAttribute (dynamic shared-memory opt-in) applies to the current device only, so

@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(128, 1)
               const PcgState* const* __restrict__ tile_st) {
   using C = TcCfg<T, BN>;
   constexpr int kTmemCols = C::TMEM_COLS;
+  pdl_enter();
   // a grouped launch over several problems' tiles gives each tile its problem's state
   if (tile_st != nullptr) st = tile_st[blockIdx.x];
   if (st != nullptr && st->done) return;
@@ -272,16 +273,15 @@ static void make_tmap(CUtensorMap* tm, void* base, int es, int inner, long long 
 template <typename T, int BN = 256>
 static void launch_tc(const CUtensorMap* tA, const CUtensorMap* tB, const Tile* tiles, int ntiles, int K,
                       int mlimit, int rows_per_type, float* Y, int ldy, int* err, const PcgState* st,
-                      cudaStream_t s, const float* ysc = nullptr, const PcgState* const* tile_st = nullptr) {
+                      cudaStream_t s, const float* ysc = nullptr, const PcgState* const* tile_st = nullptr,
+                      bool pdl = false) {
   static PerDeviceOnce attr;   // once per device and instance
   once_per_device(attr, [] {
     DD_CUDA(cudaFuncSetAttribute(k_tc_gemm<T, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  TcCfg<T, BN>::SMEM));
   });
-  (k_tc_gemm<T, BN><<<ntiles, 128, TcCfg<T, BN>::SMEM, s>>>(*tA, *tB, tiles, K, mlimit, rows_per_type, Y, ldy, err,
-                                                             st, ysc, tile_st),
-   dd::note_launch());
-  DD_CUDA(cudaGetLastError());
+  launch_chain(k_tc_gemm<T, BN>, dim3(ntiles), dim3(128), TcCfg<T, BN>::SMEM, s, pdl, *tA, *tB, tiles, K, mlimit,
+               rows_per_type, Y, ldy, err, st, ysc, tile_st);
 }
 
 // ----------------------------------------------------------------------------------------
@@ -439,6 +439,7 @@ template <typename T>
 __global__ void k_pack(Geo g, const Sub* __restrict__ subs, const int* __restrict__ slot_of,
                        const double* __restrict__ r, int kpad, T* __restrict__ out, const double* __restrict__ wT,
                        double* c0, const PcgState* st, const float* __restrict__ ascale, float* __restrict__ ysc) {
+  pdl_enter();
   pack_body<T>(g, subs, slot_of, r, kpad, out, wT, c0, st, ascale, ysc, (int)blockIdx.x);
 }
 
@@ -512,16 +513,17 @@ static std::map<std::string, int> g_tune_bn;
 template <typename T>
 static void run_gemm_t(dd_ctx* c, GemmPlan* plan, int bn, const PcgState* st, cudaStream_t s, const float* ysc) {
   const int i = tile_index(bn);
+  const bool pdl = c->pdl != 0 && st != nullptr;   // inside the PCG chain
   const CUtensorMap* tB = &plan->tB[i];
   if (bn == 256)
     launch_tc<T, 256>(&plan->tA, tB, plan->tiles[i], plan->ntiles[i], c->kpad, c->kpad, c->kpad, c->Y32, c->kpad,
-                      c->dev_err + 8, st, s, ysc);
+                      c->dev_err + 8, st, s, ysc, nullptr, pdl);
   else if (bn == 160)
     launch_tc<T, 160>(&plan->tA, tB, plan->tiles[i], plan->ntiles[i], c->kpad, c->kpad, c->kpad, c->Y32, c->kpad,
-                      c->dev_err + 8, st, s, ysc);
+                      c->dev_err + 8, st, s, ysc, nullptr, pdl);
   else
     launch_tc<T, 128>(&plan->tA, tB, plan->tiles[i], plan->ntiles[i], c->kpad, c->kpad, c->kpad, c->Y32, c->kpad,
-                      c->dev_err + 8, st, s, ysc);
+                      c->dev_err + 8, st, s, ysc, nullptr, pdl);
 }
 
 static void run_gemm(dd_ctx* c, GemmPlan* plan, int bn, const PcgState* st, cudaStream_t s) {
@@ -673,16 +675,20 @@ constexpr int kPackThreads = 128;
 
 void launch_pack(dd_ctx* c, const double* r, double* c0, cudaStream_t s) {
   const Geo& g = c->g;
+  const bool pdl = c->pdl != 0;
+  const PcgState* st = c->st;
   if (c->grid.precision == DD_PREC_BF16)
-    (k_pack<__nv_bfloat16><<<g.nsub, kPackThreads, 0, s>>>(g, c->subs, c->slot_of_sub, r, c->kpad, (__nv_bfloat16*)c->Rpack,
-                                                 c->wT, c0, c->st, nullptr, nullptr), dd::note_launch());
+    launch_chain(k_pack<__nv_bfloat16>, dim3(g.nsub), dim3(kPackThreads), 0, s, pdl, g, (const Sub*)c->subs,
+                 (const int*)c->slot_of_sub, r, c->kpad, (__nv_bfloat16*)c->Rpack, (const double*)c->wT, c0, st,
+                 (const float*)nullptr, (float*)nullptr);
   else if (c->grid.precision == DD_PREC_TF32)
-    (k_pack<float><<<g.nsub, kPackThreads, 0, s>>>(g, c->subs, c->slot_of_sub, r, c->kpad, (float*)c->Rpack, c->wT, c0,
-                                         c->st, nullptr, nullptr), dd::note_launch());
+    launch_chain(k_pack<float>, dim3(g.nsub), dim3(kPackThreads), 0, s, pdl, g, (const Sub*)c->subs,
+                 (const int*)c->slot_of_sub, r, c->kpad, (float*)c->Rpack, (const double*)c->wT, c0, st,
+                 (const float*)nullptr, (float*)nullptr);
   else
-    (k_pack<__nv_fp8_e4m3><<<g.nsub, kPackThreads, 0, s>>>(g, c->subs, c->slot_of_sub, r, c->kpad, (__nv_fp8_e4m3*)c->Rpack,
-                                                 c->wT, c0, c->st, c->ascale, c->ysc), dd::note_launch());
-  DD_CUDA(cudaGetLastError());
+    launch_chain(k_pack<__nv_fp8_e4m3>, dim3(g.nsub), dim3(kPackThreads), 0, s, pdl, g, (const Sub*)c->subs,
+                 (const int*)c->slot_of_sub, r, c->kpad, (__nv_fp8_e4m3*)c->Rpack, (const double*)c->wT, c0, st,
+                 (const float*)c->ascale, (float*)c->ysc);
 }
 
 int launch_gemm(dd_ctx* c, cudaStream_t s) {

@@ -182,10 +182,14 @@ __global__ void k_tabS(long long n, const double* __restrict__ A, const double* 
     S[t] = A[t] - sigma * M[t];
 }
 
-__global__ void k_tab_split(long long n, const double* __restrict__ S, float2* __restrict__ S2) {
+// S2[cls][tap] = split(S[tap][cls]) for the 9 taps of a p = 1 class, zero pad in slot 9
+__global__ void k_tab_split(int ncls, const double* __restrict__ S, float2* __restrict__ S2) {
+  const long long n = (long long)ncls * kPairTapStride;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
-       t += (long long)gridDim.x * blockDim.x)
-    S2[t] = f64_split(S[t]);
+       t += (long long)gridDim.x * blockDim.x) {
+    const int cls = (int)(t / kPairTapStride), tap = (int)(t % kPairTapStride);
+    S2[t] = tap < 9 ? f64_split(S[(size_t)tap * ncls + cls]) : make_float2(0.0f, 0.0f);
+  }
 }
 
 void launch_tabS(dd_ctx* c, double sigma) {
@@ -193,7 +197,9 @@ void launch_tabS(dd_ctx* c, double sigma) {
   (k_tabS<<<grid_blocks(n, kThreads), kThreads, 0, c->stream>>>(n, c->tabA, c->tabM, sigma, c->tabS), dd::note_launch());
   DD_CUDA(cudaGetLastError());
   if (c->tabS2) {
-    (k_tab_split<<<grid_blocks(n, kThreads), kThreads, 0, c->stream>>>(n, c->tabS, c->tabS2), dd::note_launch());
+    const long long n2 = (long long)c->g.ncls * kPairTapStride;
+    (k_tab_split<<<grid_blocks(n2, kThreads), kThreads, 0, c->stream>>>(c->g.ncls, c->tabS, c->tabS2),
+     dd::note_launch());
     DD_CUDA(cudaGetLastError());
   }
 }
@@ -529,7 +535,32 @@ __device__ __forceinline__ void fused_pq_body(VBlk vb, Geo g, const double* __re
 // error-free product and sum (pair_fma) against the split table, and q = hi + lo in FP64.
 // p_k, the (p, q) partial and everything else stay FP64; q differs from the FP64 stencil by
 // about 2^-47 times the sum of the taps' magnitudes.  Three FP64 instructions per node (p
-// update, q = hi + lo, the partial) instead of eleven.
+// update, q = hi + lo, the partial) instead of eleven.  The split table is class-major (a
+// class's taps are five 16-byte loads), p_k is written back from the staging loop, and each
+// thread evaluates two nodes (e, e + blockDim) per pass with their chains interleaved.
+__device__ __forceinline__ void pair_taps(const float2* __restrict__ tab2, int cls, const float2* x, int Y,
+                                          float& hs, float& ls) {
+  const float4* tr = reinterpret_cast<const float4*>(tab2 + (size_t)cls * kPairTapStride);
+  float t[18];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float4 v = __ldg(tr + k);
+    t[4 * k] = v.x; t[4 * k + 1] = v.y; t[4 * k + 2] = v.z; t[4 * k + 3] = v.w;
+  }
+  {
+    const float4 v = __ldg(tr + 4);
+    t[16] = v.x; t[17] = v.y;
+  }
+#pragma unroll
+  for (int dx = -1; dx <= 1; ++dx)
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int k = (dx + 1) * 3 + (dy + 1);
+      const float2 xv = x[dx * Y + dy];
+      pair_fma(t[2 * k], t[2 * k + 1], xv.x, xv.y, hs, ls);
+    }
+}
+
 __device__ __forceinline__ void fused_pq_pairs_body(VBlk vb, Geo g, const float2* __restrict__ tab2,
                                                     const double* __restrict__ z, double* pb0, double* pb1,
                                                     double* __restrict__ q, PcgState* st, double* partials,
@@ -538,56 +569,61 @@ __device__ __forceinline__ void fused_pq_pairs_body(VBlk vb, Geo g, const float2
   extern __shared__ double sp_raw[];
   const int Y = g.Ypad, yl = g.ylog;
   const int nstage = (kFusedCols + 2) * Y + 2;
-  double* sp = sp_raw + 1;   // one zero guard element on each side
-  float2* sp2_raw = reinterpret_cast<float2*>(sp_raw + nstage);
-  float2* sp2 = sp2_raw + 1;
+  float2* sp2_raw = reinterpret_cast<float2*>(sp_raw);
+  float2* sp2 = sp2_raw + 1;   // one zero guard element on each side
+  double* spd = sp_raw + nstage;   // the tile's own p values (FP64), for the partial
   const int k = st->iter;
   const double beta = st->beta;
   const double* __restrict__ pp = p_prev(pb0, pb1, k);
   double* __restrict__ pc = p_cur(pb0, pb1, k);
   const int ntiles = (g.nxi + kFusedCols - 1) / kFusedCols;
   if (threadIdx.x == 0) {
-    sp_raw[0] = 0.0;
-    sp_raw[nstage - 1] = 0.0;
     sp2_raw[0] = make_float2(0.0f, 0.0f);
     sp2_raw[nstage - 1] = make_float2(0.0f, 0.0f);
   }
+  const int cstep = blockDim.x >> yl;   // node columns per pass of the block (blockDim >= Y)
   double acc[1] = {0.0};
   for (int tile = vb.b; tile < ntiles; tile += vb.nb) {
     const int a0 = 1 + tile * kFusedCols;
     const int own = min(kFusedCols, g.nxi - (a0 - 1));
     const int nload = (own + 2) << yl;
+    const int nown = own << yl;
     const long long gbase = (long long)(a0 - 1) << yl;
     __syncthreads();
     for (int e = threadIdx.x; e < nload; e += blockDim.x) {
       const double pv = fma(beta, pp[gbase + e], z[gbase + e]);
-      sp[e] = pv;
       sp2[e] = f64_split(pv);
+      if (e >= Y && e < Y + nown) {
+        pc[gbase + e] = pv;
+        spd[e - Y] = pv;
+      }
     }
-    if (threadIdx.x == 0) {   // corner tap of the last (pad) slot of a partial tile
-      sp[nload] = 0.0;
-      sp2[nload] = make_float2(0.0f, 0.0f);
-    }
+    if (threadIdx.x == 0) sp2[nload] = make_float2(0.0f, 0.0f);   // corner tap of the last pad slot
     __syncthreads();
-    const int nown = own << yl;
-    for (int e = threadIdx.x; e < nown; e += blockDim.x) {
-      const int se = e + Y;
-      const long long gi = gbase + se;
-      const double pv = sp[se];
-      pc[gi] = pv;
-      const int cls = ((a0 + (e >> yl)) % g.n) * Y + (e & (Y - 1));
-      float hs = 0.0f, ls = 0.0f;
-#pragma unroll
-      for (int dx = -1; dx <= 1; ++dx)
-#pragma unroll
-        for (int dy = -1; dy <= 1; ++dy) {
-          const float2 t = __ldg(tab2 + (size_t)((dx + 1) * 3 + (dy + 1)) * g.ncls + cls);
-          const float2 x = sp2[se + dx * Y + dy];
-          pair_fma(t.x, t.y, x.x, x.y, hs, ls);
-        }
-      const double qv = f32_to_f64(hs) + f32_to_f64(ls);
-      q[gi] = qv;
-      acc[0] = fma(pv, qv, acc[0]);
+    // class column (a0 + e / Y) mod n, advanced by cstep columns per pass
+    int cm = (a0 + (threadIdx.x >> yl)) % g.n;
+    int cm1 = cm + cstep;
+    while (cm1 >= g.n) cm1 -= g.n;
+    for (int e = threadIdx.x; e < nown; e += 2 * blockDim.x) {
+      const int e1 = e + blockDim.x;
+      const bool two = e1 < nown;
+      const int f = two ? e1 : e;   // a valid node for the masked second chain
+      const int slot = e & (Y - 1);
+      float h0 = 0.0f, l0 = 0.0f, h1 = 0.0f, l1 = 0.0f;
+      pair_taps(tab2, cm * Y + slot, sp2 + e + Y, Y, h0, l0);
+      pair_taps(tab2, cm1 * Y + slot, sp2 + f + Y, Y, h1, l1);
+      const double q0 = f32_to_f64(h0) + f32_to_f64(l0);
+      q[gbase + Y + e] = q0;
+      acc[0] = fma(spd[e], q0, acc[0]);
+      if (two) {
+        const double q1 = f32_to_f64(h1) + f32_to_f64(l1);
+        q[gbase + Y + e1] = q1;
+        acc[0] = fma(spd[e1], q1, acc[0]);
+      }
+      cm += 2 * cstep;
+      while (cm >= g.n) cm -= g.n;
+      cm1 += 2 * cstep;
+      while (cm1 >= g.n) cm1 -= g.n;
     }
   }
   double tot[1];
@@ -607,12 +643,13 @@ __global__ void __launch_bounds__(kThreads) k_fused_pq_pairs(Geo g, const float2
                                                              const double* __restrict__ z, double* pb0, double* pb1,
                                                              double* __restrict__ q, PcgState* st, double* partials,
                                                              unsigned* counter) {
+  pdl_enter();
   fused_pq_pairs_body(vblk_self(), g, tab2, z, pb0, pb1, q, st, partials, counter);
 }
 
 static size_t fused_pq_smem(int ypad, bool pairs) {
   const size_t n = (size_t)(kFusedCols + 2) * ypad + 2;
-  return n * (sizeof(double) + (pairs ? sizeof(float2) : 0));
+  return pairs ? n * sizeof(float2) + (size_t)kFusedCols * ypad * sizeof(double) : n * sizeof(double);
 }
 
 template <int U2>
@@ -620,6 +657,7 @@ __global__ void __launch_bounds__(kThreads) k_fused_pq(Geo g, const double* __re
                                                        const double* __restrict__ z, double* pb0, double* pb1,
                                                        double* __restrict__ q, PcgState* st, double* partials,
                                                        unsigned* counter) {
+  pdl_enter();
   fused_pq_body<U2>(vblk_self(), g, tab, z, pb0, pb1, q, st, partials, counter);
 }
 
@@ -634,21 +672,17 @@ void launch_fused_pq(dd_ctx* c, cudaStream_t s) {
     DD_CUDA(cudaFuncSetAttribute(k_fused_pq<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     DD_CUDA(cudaFuncSetAttribute(k_fused_pq_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   });
+  const bool pdl = c->pdl != 0;
   if (c->pq_pairs) {
-    (k_fused_pq_pairs<<<nb, kThreads, smem, s>>>(g, c->tabS2, c->z, c->pb[0], c->pb[1], c->q, c->st, c->red,
-                                                c->cnt + CNT_PQ), dd::note_launch());
-    DD_CUDA(cudaGetLastError());
+    launch_chain(k_fused_pq_pairs, dim3(nb), dim3(kThreads), smem, s, pdl, g, (const float2*)c->tabS2,
+                 (const double*)c->z, c->pb[0], c->pb[1], c->q, c->st, c->red, c->cnt + CNT_PQ);
     return;
   }
   // two nodes per thread and pass by default: 53.0 against 53.8 us per launch on the
   // L = 2048, h = 1/32 box, the same bits
-  if (c->fused_pq_opt != 1)
-    (k_fused_pq<2><<<nb, kThreads, smem, s>>>(g, c->tabS, c->z, c->pb[0], c->pb[1], c->q, c->st, c->red,
-                                              c->cnt + CNT_PQ), dd::note_launch());
-  else
-    (k_fused_pq<1><<<nb, kThreads, smem, s>>>(g, c->tabS, c->z, c->pb[0], c->pb[1], c->q, c->st, c->red,
-                                              c->cnt + CNT_PQ), dd::note_launch());
-  DD_CUDA(cudaGetLastError());
+  launch_chain(c->fused_pq_opt != 1 ? k_fused_pq<2> : k_fused_pq<1>, dim3(nb), dim3(kThreads), smem, s, pdl, g,
+               (const double*)c->tabS, (const double*)c->z, c->pb[0], c->pb[1], c->q, c->st, c->red,
+               c->cnt + CNT_PQ);
 }
 
 // x[0..n) = v (start vectors of the convenience entry points)
@@ -705,6 +739,7 @@ void launch_matvec_pq(dd_ctx* c, cudaStream_t s) {
 }
 
 // x += alpha p, r -= alpha q, rr = (r, r); stop test ||r|| <= rtol ||r0|| (Sec. 4.1).
+template <bool PAIRS>
 __device__ __forceinline__ void xr_update_body(VBlk vb, long long n, double* pb0, double* pb1,
                                                         const double* __restrict__ q, double* __restrict__ x,
                                                         double* __restrict__ r, PcgState* st,
@@ -717,17 +752,38 @@ __device__ __forceinline__ void xr_update_body(VBlk vb, long long n, double* pb0
   double2* x2 = reinterpret_cast<double2*>(x);
   double2* r2 = reinterpret_cast<double2*>(r);
   double acc[1] = {0.0};
-  for (long long t = (long long)vb.b * blockDim.x + threadIdx.x; t < n / 2;
-       t += (long long)vb.nb * blockDim.x) {
-    double2 pv = p2[t], qv = q2[t], xv = x2[t], rv = r2[t];
-    xv.x = fma(alpha, pv.x, xv.x);
-    xv.y = fma(alpha, pv.y, xv.y);
-    rv.x = fma(-alpha, qv.x, rv.x);
-    rv.y = fma(-alpha, qv.y, rv.y);
-    x2[t] = xv;
-    r2[t] = rv;
-    acc[0] = fma(rv.x, rv.x, acc[0]);
-    acc[0] = fma(rv.y, rv.y, acc[0]);
+  if (PAIRS) {
+    // (r, r) in float pairs on r 2^-k, 2^k ~ sqrt of the previous (r, r): each thread's sum
+    // hi + lo (error ~2^-46 of it) is scaled back by 2^2k and enters the FP64 reduction
+    const int k = half_exponent(st->rr);
+    float hs = 0.0f, ls = 0.0f;
+    for (long long t = (long long)vb.b * blockDim.x + threadIdx.x; t < n / 2;
+         t += (long long)vb.nb * blockDim.x) {
+      double2 pv = p2[t], qv = q2[t], xv = x2[t], rv = r2[t];
+      xv.x = fma(alpha, pv.x, xv.x);
+      xv.y = fma(alpha, pv.y, xv.y);
+      rv.x = fma(-alpha, qv.x, rv.x);
+      rv.y = fma(-alpha, qv.y, rv.y);
+      x2[t] = xv;
+      r2[t] = rv;
+      const float2 a = f64_split_pow2(rv.x, k), b = f64_split_pow2(rv.y, k);
+      pair_fma(a.x, a.y, a.x, a.y, hs, ls);
+      pair_fma(b.x, b.y, b.x, b.y, hs, ls);
+    }
+    acc[0] = (f32_to_f64(hs) + f32_to_f64(ls)) * pow2_f64(2 * k);
+  } else {
+    for (long long t = (long long)vb.b * blockDim.x + threadIdx.x; t < n / 2;
+         t += (long long)vb.nb * blockDim.x) {
+      double2 pv = p2[t], qv = q2[t], xv = x2[t], rv = r2[t];
+      xv.x = fma(alpha, pv.x, xv.x);
+      xv.y = fma(alpha, pv.y, xv.y);
+      rv.x = fma(-alpha, qv.x, rv.x);
+      rv.y = fma(-alpha, qv.y, rv.y);
+      x2[t] = xv;
+      r2[t] = rv;
+      acc[0] = fma(rv.x, rv.x, acc[0]);
+      acc[0] = fma(rv.y, rv.y, acc[0]);
+    }
   }
   double tot[1];
   if (grid_sum_last<1>(acc, partials, counter, tot, vb) && threadIdx.x == 0) {
@@ -746,20 +802,24 @@ __device__ __forceinline__ void xr_update_body(VBlk vb, long long n, double* pb0
   }
 }
 
+template <bool PAIRS>
 __global__ void __launch_bounds__(kThreads) k_xr_update(long long n, double* pb0, double* pb1,
                                                         const double* __restrict__ q, double* __restrict__ x,
                                                         double* __restrict__ r, PcgState* st,
                                                         double* partials, unsigned* counter) {
-  xr_update_body(vblk_self(), n, pb0, pb1, q, x, r, st, partials, counter);
+  pdl_enter();
+  xr_update_body<PAIRS>(vblk_self(), n, pb0, pb1, q, x, r, st, partials, counter);
 }
 
+// The FP64 form takes 64 registers, so 4 blocks of 256 per SM are resident: one wave of
+// 608 blocks (22.5 us on the 2.03M-unknown L = 2048 box) instead of two of the default 1216
+// (25.5 us); the float-pair form takes 32, so 8 per SM.
+static int xr_blocks(const dd_ctx* c) { return grid_blocks(c->g.plen / 2, kThreads, c->pq_pairs ? 8 : 4); }
+
 void launch_xr_update(dd_ctx* c, cudaStream_t s) {
-  // the kernel takes 64 registers, so 4 blocks of 256 per SM are resident: one wave of
-  // 608 blocks (22.5 us on the 2.03M-unknown L = 2048 box) instead of two of the default
-  // 1216 (25.5 us)
   const long long n = c->g.plen;
-  (k_xr_update<<<grid_blocks(n / 2, kThreads, 4), kThreads, 0, s>>>(n, c->pb[0], c->pb[1], c->q, c->x, c->r, c->st,
-                                                                 c->red, c->cnt + CNT_RR), dd::note_launch());
+  launch_chain(c->pq_pairs ? k_xr_update<true> : k_xr_update<false>, dim3(xr_blocks(c)), dim3(kThreads), 0, s,
+               c->pdl != 0, n, c->pb[0], c->pb[1], (const double*)c->q, c->x, c->r, c->st, c->red, c->cnt + CNT_RR);
   DD_CUDA(cudaGetLastError());
 }
 
@@ -898,6 +958,7 @@ __global__ void __launch_bounds__(kThreads, (P == 1 ? 8 : 5) / U) k_prolong(Geo 
                                                       const double* __restrict__ r, const double* __restrict__ q,
                                                       double* __restrict__ z, int mode, PcgState* st,
                                                       double* partials, unsigned* counter, int kpad, int4 pt) {
+  pdl_enter();
   prolong_body<P, TY, RAS, U, ARITH>(vblk_self(), g, axown, subrow, Y, wT, puT, u0, coarse, r, q, z, mode, st,
                                      partials, counter, kpad, pt);
 }
@@ -913,10 +974,12 @@ void launch_prolong(dd_ctx* c, int mode, cudaStream_t s, double* zout) {
   const int coarse = c->grid.coarse;
   const bool f32 = (c->grid.precision != DD_PREC_FP64);
   double* z = zout != nullptr ? zout : c->z;
-#define DD_PROLONG_A(PP, TY, YP, W, PU, U0, RS, AR)                                                                   \
-  (k_prolong<PP, TY, RS, kProlongU, AR><<<resident_grid(k_prolong<PP, TY, RS, kProlongU, AR>, work, kThreads), kThreads, 0, s>>>(g, c->axown, c->subrow, YP, W, PU, U0, coarse, c->r, c->q, z, mode, \
-                                                 c->st, c->red, c->cnt + CNT_RZ, c->kpad, c->ptypes),                 \
-   dd::note_launch())
+#define DD_PROLONG_A(PP, TY, YP, W, PU, U0, RS, AR)                                                              \
+  launch_chain(k_prolong<PP, TY, RS, kProlongU, AR>,                                                              \
+               dim3(resident_grid(k_prolong<PP, TY, RS, kProlongU, AR>, work, kThreads)), dim3(kThreads), 0, s, \
+               c->pdl != 0, g, (const int4*)c->axown, (const int4*)c->subrow, (const TY*)(YP), (const TY*)(W),  \
+               (const TY*)(PU), (const TY*)(U0), coarse, (const double*)c->r, (const double*)c->q, z, mode, c->st, \
+               c->red, c->cnt + CNT_RZ, c->kpad, c->ptypes)
 #define DD_PROLONG(PP, TY, YP, W, PU, U0, RS)                                    \
   do {                                                                           \
     if (PP == 1 && c->prolong_arith) DD_PROLONG_A(1, TY, YP, W, PU, U0, RS, true); \
@@ -1265,11 +1328,12 @@ __global__ void __launch_bounds__(kThreads, 6) kb_fused_pq(const BInst* __restri
     fused_pq_body<2>(VBlk{m.y, I.nb_fused}, I.g, I.tabS, I.z, I.pb0, I.pb1, I.q, I.st, I.red, I.cnt + CNT_PQ);
 }
 
+template <bool PAIRS>
 __global__ void __launch_bounds__(kThreads) kb_xr_update(const BInst* __restrict__ B, const int2* __restrict__ vmap) {
   const int2 m = vmap[blockIdx.x];
   const BInst& I = B[m.x];
   if (!I.active) return;
-  xr_update_body(VBlk{m.y, I.nb_xr}, I.g.plen, I.pb0, I.pb1, I.q, I.x, I.r, I.st, I.red, I.cnt + CNT_RR);
+  xr_update_body<PAIRS>(VBlk{m.y, I.nb_xr}, I.g.plen, I.pb0, I.pb1, I.q, I.x, I.r, I.st, I.red, I.cnt + CNT_RR);
 }
 
 template <bool ARITH>
@@ -1420,7 +1484,7 @@ void batch_grid_sizes(const dd_ctx* c, BInst* I) {
   const int ntiles = (g.nxi + kFusedCols - 1) / kFusedCols;
   I->nb_init = grid_blocks(w, kThreads);
   I->nb_fused = ntiles < 152 * 6 ? ntiles : 152 * 6;
-  I->nb_xr = grid_blocks(g.plen / 2, kThreads, 4);
+  I->nb_xr = xr_blocks(c);
   I->nb_prolong = c->prolong_arith ? resident_grid(k_prolong<1, float, false, kProlongU, true>, w, kThreads)
                                     : resident_grid(k_prolong<1, float, false, kProlongU, false>, w, kThreads);
   I->nb_sdot = resident_grid(k_stencil<1, true>, w, kThreads);
@@ -1483,8 +1547,9 @@ void launch_b_fused_pq(const BInst* B, const int2* vmap, int nvb, int ypad, bool
   DD_CUDA(cudaGetLastError());
 }
 
-void launch_b_xr_update(const BInst* B, const int2* vmap, int nvb, cudaStream_t s) {
-  (kb_xr_update<<<nvb, kThreads, 0, s>>>(B, vmap), dd::note_launch());
+void launch_b_xr_update(const BInst* B, const int2* vmap, int nvb, bool pairs, cudaStream_t s) {
+  if (pairs) (kb_xr_update<true><<<nvb, kThreads, 0, s>>>(B, vmap), dd::note_launch());
+  else (kb_xr_update<false><<<nvb, kThreads, 0, s>>>(B, vmap), dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 

@@ -1,11 +1,16 @@
-"""q = A_sigma p of the fused PCG pass in float pairs (DD_OPT_PQ_ARITH = 1, the default with
-rounded local inverses) against the FP64 form of the same pass.
+"""Float pairs in the PCG iteration (DD_OPT_PAIRS = 1, the default with rounded local inverses):
+q = A_sigma p of the fused pass and the partial sums of (r, r) on the FP32 pipe, against the FP64
+form of the same iteration.
 
-The pair arithmetic changes only the inner solve's operator, by about 2^-47 times the sum of
-the taps' magnitudes; the outer iteration's residuals and Rayleigh quotients stay FP64.  So
-both forms must reach the stop rule's eta <= 1e-8 measured in FP64 by the oracle's matrices,
-the same eigenvalue (well inside the 1e-10 target), and the oracle's exact eigenvalue, with
-inner iteration counts that differ by at most a few."""
+The pair arithmetic changes only the inner solve (its operator by about 2^-47 times the sum of
+the taps' magnitudes, (r, r) by about 2^-46 of each thread's partial); the outer
+iteration's residuals and Rayleigh quotients stay FP64.  So both forms must reach the stop
+rule's eta <= 1e-8 measured in FP64 by the oracle's matrices, the same eigenvalue (well inside
+the 1e-10 target), and the oracle's exact eigenvalue, with inner iteration counts that differ
+by at most a few.  A right-hand side scaled by 2^-40 or 2^40 gives the same iteration count and
+the scaled solution, bit for bit (the operands of (r, r) are scaled by a power of two that
+follows (r, r); the BF16 local solves keep the float exponent range, which bounds the scales a
+mixed solve can take)."""
 import numpy as np
 import pytest
 
@@ -32,7 +37,7 @@ def _eta(P, x, lam):
 def _solve(w, prec, arith, method):
     with make_solver(w, precision=prec) as es:
         es.prepare()
-        dd.dd_set_option(es.ctx, dd.DD_OPT_PQ_ARITH, arith)
+        dd.dd_set_option(es.ctx, dd.DD_OPT_PAIRS, arith)
         x = gpu_vec(np.ones(w.dofs))
         if method == "ipm":
             lam, outer, tot, mx = dd.dd_inverse_iterate(es.ctx, x)
@@ -73,7 +78,7 @@ def test_pairs_pcg_solve(name):
     for arith in (0, 1):
         with make_solver(w, precision="bf16") as es:
             es.prepare()
-            dd.dd_set_option(es.ctx, dd.DD_OPT_PQ_ARITH, arith)
+            dd.dd_set_option(es.ctx, dd.DD_OPT_PAIRS, arith)
             b = gpu_vec(np.zeros(w.dofs))
             dd.dd_apply_operator(es.ctx, dd.DD_OP_MASS, gpu_vec(np.ones(w.dofs)), b)
             x = gpu_vec(np.zeros(w.dofs))
@@ -89,13 +94,30 @@ def test_pairs_pcg_solve(name):
     assert np.linalg.norm(d_perp) <= 1e-6 * np.linalg.norm(out[0][2])
 
 
+@pytest.mark.parametrize("e", [-40, 40])
+def test_pairs_scale_invariance(e):
+    w = CASES["cfg2_small"]
+    out = {}
+    for scale in (1.0, 2.0 ** e):
+        with make_solver(w, precision="bf16") as es:
+            es.prepare()
+            b = gpu_vec(np.zeros(w.dofs))
+            dd.dd_apply_operator(es.ctx, dd.DD_OP_MASS, gpu_vec(np.full(w.dofs, scale)), b)
+            x = gpu_vec(np.zeros(w.dofs))
+            it, rel = dd.dd_pcg_solve(es.ctx, b, x, 1e-8)
+            out[scale] = (it, rel, host(x) / scale)
+    (i0, r0, x0), (i1, r1, x1) = out.values()
+    assert i0 == i1 and r1 <= 1e-8
+    assert np.array_equal(x0, x1)
+
+
 def test_option_validation():
     w = CASES["cfg1"]
     with make_solver(w, precision="bf16") as es:
         for bad in (-2, 2):
             with pytest.raises(dd.DDError):
-                dd.dd_set_option(es.ctx, dd.DD_OPT_PQ_ARITH, bad)
+                dd.dd_set_option(es.ctx, dd.DD_OPT_PAIRS, bad)
     with make_solver(Workload("p2", p=2, L=2, n=6, overlap=2, kind="asym3"), precision="bf16") as es:
         with pytest.raises(dd.DDError):
-            dd.dd_set_option(es.ctx, dd.DD_OPT_PQ_ARITH, 1)
-        dd.dd_set_option(es.ctx, dd.DD_OPT_PQ_ARITH, 0)
+            dd.dd_set_option(es.ctx, dd.DD_OPT_PAIRS, 1)
+        dd.dd_set_option(es.ctx, dd.DD_OPT_PAIRS, 0)
