@@ -382,7 +382,18 @@ int dd_coarse_matrix(dd_ctx* ctx, double* A0_host);
  *                       while its predecessor drains (each waits for the predecessor's results
  *                       before reading anything); 0: plain launches.  The same results; on the
  *                       L = 2048, h = 1/32 box the ground state took 24.0 ms with it against
- *                       23.3 ms without, hence off by default [0] */
+ *                       23.3 ms without, hence off by default [0]
+ *   DD_OPT_FUSE_XR      p = 1, BF16/TF32 local inverses, fused p update, at most 4096
+ *                       subdomains: 1 runs the iteration's x, r update inside the restriction
+ *                       packing (each subdomain's block forms r - alpha q for its packed row and,
+ *                       on the node columns it owns, updates x and sums (r, r) and takes the stop
+ *                       test), and the prolong-sum stores r - alpha q; one pass over x, p, q, r
+ *                       fewer per iteration.  x and r take the same values as with 0; (r, r) is
+ *                       summed in another order.  On the L = 2048, h = 1/32 box the fused
+ *                       kernel took 32 us against 22 + 14 us for the two, but the ground state
+ *                       24.0 ms against 23.6 ms (the r store moves into the prolong-sum, which
+ *                       slows by 1.5 us, and the coarse solve forks later), so off by default;
+ *                       -1: off [0] */
 #define DD_OPT_CHECK_EVERY 0
 #define DD_OPT_USE_GRAPH   1
 #define DD_OPT_FLEXIBLE    2
@@ -397,6 +408,7 @@ int dd_coarse_matrix(dd_ctx* ctx, double* A0_host);
 #define DD_OPT_PROLONG_TABLES 11
 #define DD_OPT_PAIRS       12
 #define DD_OPT_PDL         13
+#define DD_OPT_FUSE_XR     14
 int dd_set_option(dd_ctx* ctx, int option, int value);
 
 /* Per-kernel-class timing collected while DD_OPT_TIMING = 1: for class k (0 <= k < count),

@@ -111,7 +111,7 @@ void* dev_alloc(dd_ctx* c, size_t bytes) {
 
 static const char* kClassNames[KC_COUNT] = {
     "stencil_Asigma", "p_update", "xr_update", "local_solve_fp64", "pack_restrict", "local_gemm_tc",
-    "prolong_sum", "coarse_restrict", "coarse_solve", "outer_step", "misc", "rayleigh_ritz"};
+    "prolong_sum", "coarse_restrict", "coarse_solve", "outer_step", "misc", "rayleigh_ritz", "pack_xr_update"};
 
 void timer_begin(dd_ctx* c, int, cudaStream_t s, cudaEvent_t* e0) {
   *e0 = nullptr;
@@ -313,12 +313,14 @@ bool use_gemm(const dd_ctx* c) { return c->grid.precision != DD_PREC_FP64; }
 // The coarse right-hand side is formed in the pass that gathers R_i r (local solve or pack);
 // with tensor-core local solves the coarse solve then runs on a second stream beside the
 // GEMM (the two-level operator is additive, so the branches are independent).
-void precond(dd_ctx* c, const double* r, int mode, double* zout = nullptr) {
+// packed: the restrictions were packed by launch_pack_xr (a fused iteration), whose r update
+// the prolong-sum then applies.
+void precond(dd_ctx* c, const double* r, int mode, double* zout = nullptr, bool packed = false) {
   cudaStream_t s = c->stream;
   const bool coarse = c->grid.coarse != 0;
   double* c0 = coarse ? c->c0 : nullptr;
   if (use_gemm(c)) {
-    TIMED(KC_PACK, s, launch_pack(c, r, c0, s));
+    if (!packed) TIMED(KC_PACK, s, launch_pack(c, r, c0, s));
     if (coarse) {
       DD_CUDA(cudaEventRecord(c->ev_fork, s));
       DD_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
@@ -333,7 +335,15 @@ void precond(dd_ctx* c, const double* r, int mode, double* zout = nullptr) {
     TIMED(KC_LOCAL_FP64, s, launch_band_solve_local(c, r, c0, s));
     if (coarse) TIMED(KC_CSOLVE, s, launch_coarse_solve(c, s));
   }
-  TIMED(KC_PROLONG, s, launch_prolong(c, mode, s, zout));
+  TIMED(KC_PROLONG, s, launch_prolong(c, mode, s, zout, packed));
+}
+
+// The x/r update runs inside the restriction packing (launch_pack_xr) for p = 1 boxes with
+// BF16/TF32 local inverses and the fused p update, when the partial sums of (r, r) fit the
+// reduction buffer (one per subdomain).
+bool fuse_xr_possible(const dd_ctx* c) {
+  return c->g.p == 1 && (c->grid.precision == DD_PREC_BF16 || c->grid.precision == DD_PREC_TF32) &&
+         c->fused_pq_opt != 0 && c->g.nsub <= kMaxRedBlocksHost;
 }
 
 void pcg_iteration(dd_ctx* c) {
@@ -344,8 +354,13 @@ void pcg_iteration(dd_ctx* c) {
     TIMED(KC_PUPDATE, s, launch_pupdate(c, s));
     TIMED(KC_STENCIL, s, launch_matvec_pq(c, s));
   }
-  TIMED(KC_XRUPDATE, s, launch_xr_update(c, s));
-  precond(c, c->r, 2);
+  if (c->fuse_xr) {
+    TIMED(KC_PACK_XR, s, launch_pack_xr(c, s));
+    precond(c, c->r, 2, nullptr, true);
+  } else {
+    TIMED(KC_XRUPDATE, s, launch_xr_update(c, s));
+    precond(c, c->r, 2);
+  }
 }
 
 void reset_graph(dd_ctx* c) {
@@ -1299,6 +1314,15 @@ int dd_set_option(dd_ctx* c, int option, int value) {
       if (value < -1 || value > 2) return fail(c, DD_EINVAL, "fused p update must be -1, 0, 1 or 2");
       if (value >= 1 && c->g.p == 2) return fail(c, DD_EINVAL, "the fused p update and stencil needs p = 1");
       c->fused_pq_opt = value;
+      if (!fuse_xr_possible(c)) c->fuse_xr = 0;
+      break;
+    case DD_OPT_FUSE_XR:
+      if (value < -1 || value > 1) return fail(c, DD_EINVAL, "fused x/r update must be -1, 0 or 1");
+      if (value == 1 && !fuse_xr_possible(c))
+        return fail(c, DD_EINVAL, "the fused x/r update needs p = 1, BF16 or TF32 local inverses, the fused p "
+                                  "update and at most 4096 subdomains");
+      c->fuse_xr_opt = value;
+      c->fuse_xr = value > 0 ? 1 : 0;
       break;
     case DD_OPT_PDL:
       if (value != 0 && value != 1) return fail(c, DD_EINVAL, "programmatic dependent launch must be 0 or 1");

@@ -51,6 +51,7 @@ struct BGroup {
   int ypad = 0, precision = 0, check_every = 8;
   bool arith = true;               // every instance's prolong-sum owners in closed form
   bool pairs = false;              // q = A_sigma p in float pairs (the same choice for every instance)
+  bool fuse = false;               // the x/r update inside the packing (the same for every instance)
   dd::BGemm* gemm = nullptr;
   int bn = 0;                      // N tile of the grouped contraction (timed at build)
   cudaStream_t s = nullptr, side = nullptr;
@@ -114,7 +115,7 @@ void free_group(BGroup* g) {
 long long option_signature(const dd_batch* b) {
   long long h = 1469598103934665603LL;
   for (const dd_ctx* c : b->ctx)
-    for (int v : {c->prolong_arith, c->pq_pairs, c->flexible_opt, c->check_every, c->gemm_bn_opt})
+    for (int v : {c->prolong_arith, c->pq_pairs, c->fuse_xr, c->flexible_opt, c->check_every, c->gemm_bn_opt})
       h = (h ^ (long long)(v + 7)) * 1099511628211LL;
   return h;
 }
@@ -172,21 +173,27 @@ void mask(BGroup* g, F&& on) {
 
 // z = M_AS2^{-1} r for every active instance (mode 0: alone, 1: PCG start, 2: iteration); the
 // coarse solves run on the side stream beside the grouped contraction (the operator is additive)
-void precond(BGroup* g, int mode) {
-  dd::launch_b_pack(g->B, g->vm_pack, g->n_pack, g->precision, g->s);
+// (packed: the restrictions came from the fused x/r update, whose r update the prolong-sum applies)
+void precond(BGroup* g, int mode, bool packed = false) {
+  if (!packed) dd::launch_b_pack(g->B, g->vm_pack, g->n_pack, g->precision, g->s);
   DD_CUDA(cudaEventRecord(g->ev_fork, g->s));
   DD_CUDA(cudaStreamWaitEvent(g->side, g->ev_fork, 0));
   dd::launch_b_cr_solve(g->B, (int)g->idx.size(), g->cr_smem, g->side);
   DD_CUDA(cudaEventRecord(g->ev_join, g->side));
   dd::bgemm_run(g->gemm, g->bn, g->s);
   DD_CUDA(cudaStreamWaitEvent(g->s, g->ev_join, 0));
-  dd::launch_b_prolong(g->B, g->vm_prolong, g->n_prolong, mode, g->arith, g->s);
+  dd::launch_b_prolong(g->B, g->vm_prolong, g->n_prolong, mode, g->arith, packed, g->s);
 }
 
 void pcg_iteration(BGroup* g) {
   dd::launch_b_fused_pq(g->B, g->vm_fused, g->n_fused, g->ypad, g->pairs, g->s);
-  dd::launch_b_xr_update(g->B, g->vm_xr, g->n_xr, g->pairs, g->s);
-  precond(g, 2);
+  if (g->fuse) {
+    dd::launch_b_pack_xr(g->B, g->vm_pack, g->n_pack, g->precision, g->pairs, g->s);
+    precond(g, 2, true);
+  } else {
+    dd::launch_b_xr_update(g->B, g->vm_xr, g->n_xr, g->pairs, g->s);
+    precond(g, 2);
+  }
 }
 
 void build_graph(BGroup* g) {
@@ -257,6 +264,7 @@ BGroup* build_group(dd_batch* b, const std::vector<int>& idx) {
       I.tabS2 = c->tabS2;
       I.pq_pairs = c->pq_pairs;
       g->pairs = c->pq_pairs != 0;
+      g->fuse = c->fuse_xr != 0;
       I.st = c->st; I.ost = c->ost; I.red = c->red; I.cnt = c->cnt;
       I.subs = c->subs; I.slot_of_sub = c->slot_of_sub; I.Rpack = c->Rpack; I.wT = c->wT; I.c0 = c->c0;
       I.u0 = c->u0; I.u0f = c->u0f; I.Y32 = c->Y32; I.wT32 = c->wT32; I.puT32 = c->puT32;
@@ -791,7 +799,7 @@ int dd_batch_ground_states(dd_batch* b, int method, int threads, double* lambda_
   bool engine = b->eligible && b->groups_opt >= 0 && (method == DD_BATCH_IPM || method == DD_BATCH_LOPCG_FUSED);
   for (dd_ctx* c : b->ctx)
     if (c->krylov != 0 || c->ras != 0 || c->coarse_mode == 2 || c->timing || c->fused_pq_opt == 0 ||
-        c->pq_pairs != b->ctx.front()->pq_pairs)
+        c->pq_pairs != b->ctx.front()->pq_pairs || c->fuse_xr != b->ctx.front()->fuse_xr)
       engine = false;
   const auto t_start = std::chrono::steady_clock::now();
   std::vector<double> setup_s(n, 0.0);

@@ -81,6 +81,13 @@ __device__ __forceinline__ void pdl_enter() {
   pdl_trigger();
 }
 
+// PCG direction double buffer: iteration k (k = completed iterations) reads p_{k-1} from
+// pb[k & 1] and writes p_k to pb[(k + 1) & 1].
+__device__ __forceinline__ const double* p_prev(const double* pb0, const double* pb1, int k) {
+  return (k & 1) ? pb1 : pb0;
+}
+__device__ __forceinline__ double* p_cur(double* pb0, double* pb1, int k) { return (k & 1) ? pb0 : pb1; }
+
 // A block's place in the launch of one problem: block b of nb.  A plain launch is one
 // problem (b = blockIdx.x, nb = gridDim.x); a batched launch runs the blocks of several
 // problems' launches side by side, each block with the index and count it would have had

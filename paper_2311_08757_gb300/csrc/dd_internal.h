@@ -126,7 +126,7 @@ struct OuterState {
 
 enum KernelClass {
   KC_STENCIL = 0, KC_PUPDATE, KC_XRUPDATE, KC_LOCAL_FP64, KC_PACK, KC_GEMM, KC_PROLONG,
-  KC_CRESTRICT, KC_CSOLVE, KC_OUTER, KC_MISC, KC_RR, KC_COUNT
+  KC_CRESTRICT, KC_CSOLVE, KC_OUTER, KC_MISC, KC_RR, KC_PACK_XR, KC_COUNT
 };
 
 struct Timer {
@@ -163,6 +163,8 @@ struct dd_ctx {
   int prolong_tables_opt = 1;       // 0: owners in closed form where it holds (slower: 28.1 against 24.5 us at L = 2048)
   int4 ptypes = {0, 0, 0, 0};       // p = 1: type ids of the left end, interior and right end subdomains
   int pdl = 0;                      // PCG chain kernels launched with programmatic dependent launch
+  int fuse_xr_opt = 0;              // x/r update fused into the packing: 1 on, 0 or -1 off
+  int fuse_xr = 0;                  // the resolved choice
   int pq_pairs_opt = -1;            // q = A_sigma p of the fused p = 1 kernel: -1 automatic, 0 FP64, 1 float pairs
   int pq_pairs = 0;                 // the resolved choice
   dd::Timer timer;
@@ -348,7 +350,8 @@ void launch_pupdate(dd_ctx* c, cudaStream_t s);                     // p = z + b
 void launch_matvec_pq(dd_ctx* c, cudaStream_t s);                   // q = A p, pq, alpha
 void launch_fused_pq(dd_ctx* c, cudaStream_t s);                    // p = z + beta p; q = A p; pq (p = 1)
 void launch_xr_update(dd_ctx* c, cudaStream_t s);                   // x, r, rr, done
-void launch_prolong(dd_ctx* c, int init, cudaStream_t s, double* zout = nullptr);   // z = ..., rz, beta
+// z = ..., rz, beta; upd (iterations): r -= alpha q first, the x update having run in launch_pack_xr
+void launch_prolong(dd_ctx* c, int init, cudaStream_t s, double* zout = nullptr, bool upd = false);
 void launch_precond(dd_ctx* c, const double* r, double* z, int pcg_mode, cudaStream_t s);
 
 // local solves
@@ -374,6 +377,7 @@ void launch_coarse_solve(dd_ctx* c, cudaStream_t s);
 // GEMM path
 int gemm_setup(dd_ctx* c);
 void launch_pack(dd_ctx* c, const double* r, double* c0, cudaStream_t s);
+void launch_pack_xr(dd_ctx* c, cudaStream_t s);   // p = 1 iteration: x update, (r, r), stop test and the packing
 int launch_gemm(dd_ctx* c, cudaStream_t s);
 void gemm_free(dd_ctx* c);
 
@@ -414,7 +418,8 @@ void launch_b_zero_pcg(const BInst* B, const int2* vmap, int nvb, cudaStream_t s
 void launch_b_pcg_init(const BInst* B, const int2* vmap, int nvb, int b_role, cudaStream_t s);
 void launch_b_fused_pq(const BInst* B, const int2* vmap, int nvb, int ypad, bool pairs, cudaStream_t s);
 void launch_b_xr_update(const BInst* B, const int2* vmap, int nvb, bool pairs, cudaStream_t s);
-void launch_b_prolong(const BInst* B, const int2* vmap, int nvb, int mode, bool arith, cudaStream_t s);
+void launch_b_prolong(const BInst* B, const int2* vmap, int nvb, int mode, bool arith, bool upd, cudaStream_t s);
+void launch_b_pack_xr(const BInst* B, const int2* vmap, int nvb, int precision, bool pairs, cudaStream_t s);
 void launch_b_stencil(const BInst* B, const int2* vmap, int nvb, int mass, int x_role, int y_role, cudaStream_t s);
 void launch_b_stencil_dot(const BInst* B, const int2* vmap, int nvb, int x_role, int y_role, cudaStream_t s);
 void launch_b_outer_normalize(const BInst* B, const int2* vmap, int nvb, int w_role, int mw_role, int x_role,

@@ -434,6 +434,106 @@ __device__ __forceinline__ void pack_body(Geo g, const Sub* __restrict__ subs, c
   }
 }
 
+// A p = 1 PCG iteration's x, r update fused into the restriction packing (BF16/TF32
+// operands).  Block s forms r_new = r - alpha q over its subdomain's run of the padded vector
+// (the FMA of the separate x/r update), rounds r_new into its packed row and the coarse
+// right-hand side, and on the node columns it owns -- a with min(a / n, L - 1) = s, so each
+// column once -- updates x += alpha p and adds r_new^2 to (r, r) (float pairs: as in the x/r
+// update).  r itself is written by the prolong-sum that follows (each node once, the same
+// FMA), because the neighbouring blocks still read the old r of the columns they share.  The
+// last block to finish takes the stop test.
+template <typename T, bool PAIRS>
+__device__ __forceinline__ void pack_xr_body(VBlk vb, Geo g, const Sub* __restrict__ subs,
+                                             const int* __restrict__ slot_of, const double* __restrict__ r,
+                                             const double* __restrict__ q, double* __restrict__ x, double* pb0,
+                                             double* pb1, int kpad, T* __restrict__ out,
+                                             const double* __restrict__ wT, double* c0, PcgState* st,
+                                             double* partials, unsigned* counter) {
+  if (st->done) return;
+  const int s = vb.b;
+  const double alpha = st->alpha;
+  const double* __restrict__ p = p_cur(pb0, pb1, st->iter);
+  const Sub sb = subs[s];
+  T* row = out + (size_t)slot_of[s] * kpad;
+  const double* wt = wT + (size_t)sb.type * kpad;
+  const int Y = g.Ypad;
+  const int npair = sb.w1 * Y / 2;   // p = 1: the restriction is one run of w1 columns
+  const long long g0 = (long long)sb.lo1 * Y;
+  const int own_lo = max(1, s * g.n), own_hi = (s == g.L - 1) ? g.nxi : (s + 1) * g.n - 1;
+  const int e_lo = (own_lo - sb.lo1) * Y / 2, e_hi = (own_hi + 1 - sb.lo1) * Y / 2;
+  const int k = PAIRS ? half_exponent(st->rr) : 0;
+  float hs = 0.0f, ls = 0.0f;
+  double rr[1] = {0.0}, acc[1] = {0.0};
+  for (int e = threadIdx.x; e < npair; e += blockDim.x) {
+    const int kp = 2 * e;
+    const long long gi = g0 + kp;
+    double2 rv = *reinterpret_cast<const double2*>(r + gi);
+    const double2 qv = *reinterpret_cast<const double2*>(q + gi);
+    rv.x = fma(-alpha, qv.x, rv.x);
+    rv.y = fma(-alpha, qv.y, rv.y);
+    if (e >= e_lo && e < e_hi) {
+      const double2 pv = *reinterpret_cast<const double2*>(p + gi);
+      double2 xv = *reinterpret_cast<const double2*>(x + gi);
+      xv.x = fma(alpha, pv.x, xv.x);
+      xv.y = fma(alpha, pv.y, xv.y);
+      *reinterpret_cast<double2*>(x + gi) = xv;
+      if (PAIRS) {
+        const float2 a = f64_split_pow2(rv.x, k), b = f64_split_pow2(rv.y, k);
+        pair_fma(a.x, a.y, a.x, a.y, hs, ls);
+        pair_fma(b.x, b.y, b.x, b.y, hs, ls);
+      } else {
+        rr[0] = fma(rv.x, rv.x, rr[0]);
+        rr[0] = fma(rv.y, rv.y, rr[0]);
+      }
+    }
+    const double2 w = *reinterpret_cast<const double2*>(wt + kp);
+    acc[0] = fma(w.x, rv.x, acc[0]);
+    acc[0] = fma(w.y, rv.y, acc[0]);
+    store2<T>(row, kp, rv.x, rv.y, 1.0);
+  }
+  for (int kp = 2 * npair + 2 * threadIdx.x; kp < kpad; kp += 2 * blockDim.x) store2<T>(row, kp, 0.0, 0.0, 1.0);
+  if (c0 != nullptr) {
+    block_sum<1>(acc);
+    if (threadIdx.x == 0) c0[s] = acc[0];
+  }
+  if (PAIRS) rr[0] = (f32_to_f64(hs) + f32_to_f64(ls)) * pow2_f64(2 * k);
+  double tot[1];
+  if (grid_sum_last<1>(rr, partials, counter, tot, vb) && threadIdx.x == 0) {
+    const double rrv = tot[0];
+    st->rr = rrv;
+    st->iter += 1;
+    if (!isfinite(rrv)) {
+      st->status = DD_ENAN;
+      st->done = 1;
+    } else if (rrv <= st->tol2) {
+      st->done = 1;
+    } else if (st->iter >= st->maxit) {
+      st->status = DD_EMAXIT;
+      st->done = 1;
+    }
+  }
+}
+
+template <typename T, bool PAIRS>
+__global__ void __launch_bounds__(128, 16) k_pack_xr(Geo g, const Sub* __restrict__ subs, const int* __restrict__ slot_of,
+                                                 const double* __restrict__ r, const double* __restrict__ q,
+                                                 double* __restrict__ x, double* pb0, double* pb1, int kpad,
+                                                 T* __restrict__ out, const double* __restrict__ wT, double* c0,
+                                                 PcgState* st, double* partials, unsigned* counter) {
+  pdl_enter();
+  pack_xr_body<T, PAIRS>(vblk_self(), g, subs, slot_of, r, q, x, pb0, pb1, kpad, out, wT, c0, st, partials, counter);
+}
+
+template <typename T, bool PAIRS>
+__global__ void __launch_bounds__(128, 16) kb_pack_xr(const BInst* __restrict__ B, const int2* __restrict__ vmap) {
+  const int2 m = vmap[blockIdx.x];
+  const BInst& I = B[m.x];
+  if (!I.active) return;
+  pack_xr_body<T, PAIRS>(VBlk{m.y, I.nsub}, I.g, I.subs, I.slot_of_sub, I.r, I.q, I.x, I.pb0, I.pb1, I.kpad,
+                         reinterpret_cast<T*>(I.Rpack), I.wT, I.coarse ? I.c0 : nullptr, I.st, I.red,
+                         I.cnt + CNT_RR);
+}
+
 // one block per subdomain (blockIdx.x = subdomain id)
 template <typename T>
 __global__ void k_pack(Geo g, const Sub* __restrict__ subs, const int* __restrict__ slot_of,
@@ -691,6 +791,26 @@ void launch_pack(dd_ctx* c, const double* r, double* c0, cudaStream_t s) {
                  (const float*)c->ascale, (float*)c->ysc);
 }
 
+void launch_pack_xr(dd_ctx* c, cudaStream_t s) {
+  const Geo& g = c->g;
+  const bool pdl = c->pdl != 0;
+  double* c0 = c->grid.coarse ? c->c0 : nullptr;
+#define DD_PACK_XR(T, PR)                                                                                       \
+  launch_chain(k_pack_xr<T, PR>, dim3(g.nsub), dim3(kPackThreads), 0, s, pdl, g, (const Sub*)c->subs,             \
+               (const int*)c->slot_of_sub, (const double*)c->r, (const double*)c->q, c->x, c->pb[0], c->pb[1],   \
+               c->kpad, (T*)c->Rpack, (const double*)c->wT, c0, c->st, c->red, c->cnt + CNT_RR)
+  if (c->grid.precision == DD_PREC_BF16) {
+    if (c->pq_pairs) DD_PACK_XR(__nv_bfloat16, true);
+    else DD_PACK_XR(__nv_bfloat16, false);
+  } else if (c->grid.precision == DD_PREC_TF32) {
+    if (c->pq_pairs) DD_PACK_XR(float, true);
+    else DD_PACK_XR(float, false);
+  } else {
+    throw Error(DD_EUNSUPPORTED, "the fused x/r update and packing takes BF16 or TF32 operands");
+  }
+#undef DD_PACK_XR
+}
+
 int launch_gemm(dd_ctx* c, cudaStream_t s) {
   GemmPlan* plan = reinterpret_cast<GemmPlan*>(c->tmapA);
   if (!c->gemm_ok || !plan) return DD_ESTATE;
@@ -701,6 +821,19 @@ int launch_gemm(dd_ctx* c, cudaStream_t s) {
 void gemm_free(dd_ctx* c) {
   delete reinterpret_cast<GemmPlan*>(c->tmapA);
   c->tmapA = nullptr;
+}
+
+void launch_b_pack_xr(const BInst* B, const int2* vmap, int nvb, int precision, bool pairs, cudaStream_t s) {
+  if (precision == DD_PREC_BF16) {
+    if (pairs) (kb_pack_xr<__nv_bfloat16, true><<<nvb, kPackThreads, 0, s>>>(B, vmap), dd::note_launch());
+    else (kb_pack_xr<__nv_bfloat16, false><<<nvb, kPackThreads, 0, s>>>(B, vmap), dd::note_launch());
+  } else if (precision == DD_PREC_TF32) {
+    if (pairs) (kb_pack_xr<float, true><<<nvb, kPackThreads, 0, s>>>(B, vmap), dd::note_launch());
+    else (kb_pack_xr<float, false><<<nvb, kPackThreads, 0, s>>>(B, vmap), dd::note_launch());
+  } else {
+    throw Error(DD_EUNSUPPORTED, "batched packing supports BF16 and TF32 operands");
+  }
+  DD_CUDA(cudaGetLastError());
 }
 
 void launch_b_pack(const BInst* B, const int2* vmap, int nvb, int precision, cudaStream_t s) {

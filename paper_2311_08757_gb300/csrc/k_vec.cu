@@ -403,12 +403,8 @@ void launch_pcg_init(dd_ctx* c, const double* b, cudaStream_t s) {
   DD_CUDA(cudaGetLastError());
 }
 
-// p_k = z + beta p_{k-1} (whole padded vector; boundary columns and pads stay zero).
-// Iteration k reads pb[k & 1] and writes pb[(k + 1) & 1] (k = completed iterations).
-__device__ __forceinline__ const double* p_prev(const double* pb0, const double* pb1, int k) {
-  return (k & 1) ? pb1 : pb0;
-}
-__device__ __forceinline__ double* p_cur(double* pb0, double* pb1, int k) { return (k & 1) ? pb0 : pb1; }
+// p_k = z + beta p_{k-1} (whole padded vector; boundary columns and pads stay zero); the
+// double buffer's index helpers p_prev / p_cur are in dd_common.cuh.
 
 __global__ void __launch_bounds__(kThreads) k_pupdate(long long n, const double* __restrict__ z, double* pb0,
                                                       double* pb1, const PcgState* st) {
@@ -848,7 +844,9 @@ __device__ __forceinline__ double fma_t(double a, double b, double c) { return f
 // (subdomain i is packed row i; its type is pt.x, pt.y or pt.z for the left end, the interior
 // and the right end) instead of the two index tables -- the same values, without two levels of
 // dependent loads per node (the host checks the formula against the tables at set-up).
-template <int P, typename TY, bool RAS, int U, bool ARITH = false>
+// UPD (p = 1 iterations whose x update ran in the packing, launch_pack_xr): r_out = r - alpha q
+// first (the same FMA as the separate x/r update, each node once), and the dots take that r.
+template <int P, typename TY, bool RAS, int U, bool ARITH = false, bool UPD = false>
 __device__ __forceinline__ void prolong_body(VBlk vb, Geo g, const int4* __restrict__ axown,
                                                       const int4* __restrict__ subrow, const TY* __restrict__ Y,
                                                       const TY* __restrict__ wT, const TY* __restrict__ puT,
@@ -856,10 +854,11 @@ __device__ __forceinline__ void prolong_body(VBlk vb, Geo g, const int4* __restr
                                                       const double* __restrict__ r, const double* __restrict__ q,
                                                       double* __restrict__ z, int mode, PcgState* st,
                                                       double* partials, unsigned* counter, int kpad = 0,
-                                                      int4 pt = make_int4(0, 0, 0, 0)) {
+                                                      int4 pt = make_int4(0, 0, 0, 0), double* r_out = nullptr) {
   static_assert(!ARITH || P == 1, "closed-form owners are those of a p = 1 box");
   if (mode != 0 && st->done) return;
   const bool flex = (mode == 2) && st->flexible;
+  const double alpha_r = UPD ? st->alpha : 0.0;
   const long long total = (long long)g.nxi * (P == 2 ? g.nxi : 1) * g.Ypad;
   const long long stride = (long long)vb.nb * blockDim.x;
   constexpr int NO = (P == 2) ? 4 : 2;  // owners per node at most; U nodes per thread and pass
@@ -903,7 +902,12 @@ __device__ __forceinline__ void prolong_body(VBlk vb, Geo g, const int4* __restr
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       rv[u] = (mode != 0) ? r[nd[u].idx] : 0.0;
-      qv[u] = flex ? q[nd[u].idx] : 0.0;
+      const double qq = (flex || UPD) ? q[nd[u].idx] : 0.0;
+      if (UPD) {
+        rv[u] = fma(-alpha_r, qq, rv[u]);
+        if (in[u]) r_out[nd[u].idx] = rv[u];
+      }
+      qv[u] = flex ? qq : 0.0;
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -950,17 +954,18 @@ __device__ __forceinline__ void prolong_body(VBlk vb, Geo g, const int4* __restr
   }
 }
 
-template <int P, typename TY, bool RAS, int U, bool ARITH = false>
+template <int P, typename TY, bool RAS, int U, bool ARITH = false, bool UPD = false>
 __global__ void __launch_bounds__(kThreads, (P == 1 ? 8 : 5) / U) k_prolong(Geo g, const int4* __restrict__ axown,
                                                       const int4* __restrict__ subrow, const TY* __restrict__ Y,
                                                       const TY* __restrict__ wT, const TY* __restrict__ puT,
                                                       const TY* __restrict__ u0, int coarse,
                                                       const double* __restrict__ r, const double* __restrict__ q,
                                                       double* __restrict__ z, int mode, PcgState* st,
-                                                      double* partials, unsigned* counter, int kpad, int4 pt) {
+                                                      double* partials, unsigned* counter, int kpad, int4 pt,
+                                                      double* r_out) {
   pdl_enter();
-  prolong_body<P, TY, RAS, U, ARITH>(vblk_self(), g, axown, subrow, Y, wT, puT, u0, coarse, r, q, z, mode, st,
-                                     partials, counter, kpad, pt);
+  prolong_body<P, TY, RAS, U, ARITH, UPD>(vblk_self(), g, axown, subrow, Y, wT, puT, u0, coarse, r, q, z, mode, st,
+                                          partials, counter, kpad, pt, r_out);
 }
 
 // nodes per thread and pass (each node's loads go out together, absent owners masked):
@@ -968,29 +973,35 @@ __global__ void __launch_bounds__(kThreads, (P == 1 ? 8 : 5) / U) k_prolong(Geo 
 // more nodes takes away more resident warps than it adds loads in flight)
 constexpr int kProlongU = 1;
 
-void launch_prolong(dd_ctx* c, int mode, cudaStream_t s, double* zout) {
+void launch_prolong(dd_ctx* c, int mode, cudaStream_t s, double* zout, bool upd) {
   const Geo& g = c->g;
   const long long work = interior_work(g);
   const int coarse = c->grid.coarse;
   const bool f32 = (c->grid.precision != DD_PREC_FP64);
   double* z = zout != nullptr ? zout : c->z;
-#define DD_PROLONG_A(PP, TY, YP, W, PU, U0, RS, AR)                                                              \
-  launch_chain(k_prolong<PP, TY, RS, kProlongU, AR>,                                                              \
-               dim3(resident_grid(k_prolong<PP, TY, RS, kProlongU, AR>, work, kThreads)), dim3(kThreads), 0, s, \
-               c->pdl != 0, g, (const int4*)c->axown, (const int4*)c->subrow, (const TY*)(YP), (const TY*)(W),  \
-               (const TY*)(PU), (const TY*)(U0), coarse, (const double*)c->r, (const double*)c->q, z, mode, c->st, \
-               c->red, c->cnt + CNT_RZ, c->kpad, c->ptypes)
+  const bool upd_r = upd && mode == 2;
+#define DD_PROLONG_A(PP, TY, YP, W, PU, U0, RS, AR, UP)                                                          \
+  launch_chain(k_prolong<PP, TY, RS, kProlongU, AR, UP>,                                                          \
+               dim3(resident_grid(k_prolong<PP, TY, RS, kProlongU, AR, false>, work, kThreads)), dim3(kThreads), 0, \
+               s, c->pdl != 0, g, (const int4*)c->axown, (const int4*)c->subrow, (const TY*)(YP),                \
+               (const TY*)(W), (const TY*)(PU), (const TY*)(U0), coarse, (const double*)c->r,                    \
+               (const double*)c->q, z, mode, c->st, c->red, c->cnt + CNT_RZ, c->kpad, c->ptypes,               \
+               UP ? c->r : (double*)nullptr)
 #define DD_PROLONG(PP, TY, YP, W, PU, U0, RS)                                    \
   do {                                                                           \
-    if (PP == 1 && c->prolong_arith) DD_PROLONG_A(1, TY, YP, W, PU, U0, RS, true); \
-    else DD_PROLONG_A(PP, TY, YP, W, PU, U0, RS, false);                         \
+    if (PP == 1 && c->prolong_arith) DD_PROLONG_A(1, TY, YP, W, PU, U0, RS, true, false); \
+    else DD_PROLONG_A(PP, TY, YP, W, PU, U0, RS, false, false);                 \
   } while (0)
 #define DD_PROLONG_T(PP, RS)                                                          \
   do {                                                                                \
     if (f32) DD_PROLONG(PP, float, c->Y32, c->wT32, c->puT32, c->u0f, RS);           \
     else DD_PROLONG(PP, double, c->Y64, c->wT, c->puT, c->u0, RS);                    \
   } while (0)
-  if (c->ras) {
+  if (upd_r) {   // p = 1, rounded local inverses, AS (launch_pack_xr ran before)
+    if (g.p != 1 || !f32 || c->ras) throw Error(DD_EINVAL, "the r update of the prolong-sum needs p = 1 and FP32 local results");
+    if (c->prolong_arith) DD_PROLONG_A(1, float, c->Y32, c->wT32, c->puT32, c->u0f, false, true, true);
+    else DD_PROLONG_A(1, float, c->Y32, c->wT32, c->puT32, c->u0f, false, false, true);
+  } else if (c->ras) {
     if (g.p == 1) DD_PROLONG_T(1, true);
     else DD_PROLONG_T(2, true);
   } else {
@@ -1336,15 +1347,15 @@ __global__ void __launch_bounds__(kThreads) kb_xr_update(const BInst* __restrict
   xr_update_body<PAIRS>(VBlk{m.y, I.nb_xr}, I.g.plen, I.pb0, I.pb1, I.q, I.x, I.r, I.st, I.red, I.cnt + CNT_RR);
 }
 
-template <bool ARITH>
+template <bool ARITH, bool UPD>
 __global__ void __launch_bounds__(kThreads, 8 / kProlongU) kb_prolong(const BInst* __restrict__ B,
                                                                       const int2* __restrict__ vmap, int mode) {
   const int2 m = vmap[blockIdx.x];
   const BInst& I = B[m.x];
   if (!I.active) return;
-  prolong_body<1, float, false, kProlongU, ARITH>(VBlk{m.y, I.nb_prolong}, I.g, I.axown, I.subrow, I.Y32, I.wT32,
-                                                  I.puT32, I.u0f, I.coarse, I.r, I.q, I.z, mode, I.st, I.red,
-                                                  I.cnt + CNT_RZ, I.kpad, I.ptypes);
+  prolong_body<1, float, false, kProlongU, ARITH, UPD>(VBlk{m.y, I.nb_prolong}, I.g, I.axown, I.subrow, I.Y32,
+                                                       I.wT32, I.puT32, I.u0f, I.coarse, I.r, I.q, I.z, mode, I.st,
+                                                       I.red, I.cnt + CNT_RZ, I.kpad, I.ptypes, UPD ? I.r : nullptr);
 }
 
 __global__ void __launch_bounds__(kThreads) kb_stencil(const BInst* __restrict__ B, const int2* __restrict__ vmap,
@@ -1553,9 +1564,14 @@ void launch_b_xr_update(const BInst* B, const int2* vmap, int nvb, bool pairs, c
   DD_CUDA(cudaGetLastError());
 }
 
-void launch_b_prolong(const BInst* B, const int2* vmap, int nvb, int mode, bool arith, cudaStream_t s) {
-  if (arith) (kb_prolong<true><<<nvb, kThreads, 0, s>>>(B, vmap, mode), dd::note_launch());
-  else (kb_prolong<false><<<nvb, kThreads, 0, s>>>(B, vmap, mode), dd::note_launch());
+void launch_b_prolong(const BInst* B, const int2* vmap, int nvb, int mode, bool arith, bool upd, cudaStream_t s) {
+  if (upd && mode == 2) {
+    if (arith) (kb_prolong<true, true><<<nvb, kThreads, 0, s>>>(B, vmap, mode), dd::note_launch());
+    else (kb_prolong<false, true><<<nvb, kThreads, 0, s>>>(B, vmap, mode), dd::note_launch());
+  } else {
+    if (arith) (kb_prolong<true, false><<<nvb, kThreads, 0, s>>>(B, vmap, mode), dd::note_launch());
+    else (kb_prolong<false, false><<<nvb, kThreads, 0, s>>>(B, vmap, mode), dd::note_launch());
+  }
   DD_CUDA(cudaGetLastError());
 }
 

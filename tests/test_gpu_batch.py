@@ -139,3 +139,27 @@ def test_batched_kernels_equal_concurrent_pipelines():
                     for a, c in zip(phis, pc):
                         assert np.array_equal(host(a), c)
                     assert la < lc
+
+
+@pytest.mark.parametrize("fuse,pairs", [(1, 1), (0, 0)])
+def test_batched_kernels_with_options_equal_single_calls(fuse, pairs):
+    """The batched kernels follow each instance's options (here the x/r update fused into the
+    packing, or the FP64 form of the fused pass): set on every instance's context, the
+    batched inverse iteration still gives each instance's single-call bits."""
+    ws = batch_workloads(seed=13, count=6, L_min=2, L_max=30, n=16, overlap=2)
+    phis = [gpu_vec(np.zeros(w.dofs)) for w in ws]
+    with _batch(ws) as b:
+        for i in range(len(ws)):
+            dd.dd_set_option(b.context(i), dd.DD_OPT_PAIRS, pairs)
+            dd.dd_set_option(b.context(i), dd.DD_OPT_FUSE_XR, fuse)
+        res = b.ground_states("ipm", threads=3, phi=phis)
+        assert b.info()["last_batched"] == 1
+    for i, w in enumerate(ws):
+        with make_solver(w, precision="bf16") as es:
+            es.prepare()
+            dd.dd_set_option(es.ctx, dd.DD_OPT_PAIRS, pairs)
+            dd.dd_set_option(es.ctx, dd.DD_OPT_FUSE_XR, fuse)
+            x = gpu_vec(np.ones(w.dofs))
+            lam, outer, tot, mx = dd.dd_inverse_iterate(es.ctx, x)
+        assert lam == res["lambda"][i] and outer == res["outer"][i] and tot == res["inner"][i]
+        assert np.array_equal(host(x), host(phis[i]))
