@@ -64,6 +64,9 @@ def parse():
                     help="set up one workload, then run --pcg-iters PCG iterations (eager launches) between "
                          "cudaProfilerStart/Stop, for `ncu --profile-from-start off`")
     ap.add_argument("--pcg-iters", type=int, default=2)
+    ap.add_argument("--gemm-tile", type=int, default=0, choices=[0, 128, 160, 256],
+                    help="--profile-region: the local GEMM's N tile (0: the set-up autotuner's choice, which "
+                         "under ncu sees serialised launches)")
     ap.add_argument("--one-shot-breakdown", action="store_true",
                     help="time dd_setup, dd_cell_eigenpair, dd_coarse_build, dd_inverse_iterate and dd_destroy "
                          "of fresh contexts on the headline workload")
@@ -257,6 +260,10 @@ def kernel_model(w, info, ntype_counts, nloc_by_type, band, precision):
         stencil = (5.0 * ndof, 15.0 * taps * ndof, 0.0, 32.0 * ndof)
     elif w.p == 1:   # fused p update + stencil + (p, q)
         stencil = (2.0 * (taps + 2) * ndof, 0.0, 0.0, 32.0 * ndof)
+    elif mixed:
+        # p = 2 in float pairs: the taps read the split p (8 B), the (p, q) FMA reads p (8 B),
+        # q written (8 B); FP64: q = hi + lo and the (p, q) FMA (3 flops)
+        stencil = (3.0 * ndof, 15.0 * taps * ndof, 0.0, 24.0 * ndof)
     else:
         stencil = (2.0 * (taps + 1) * ndof, 0.0, 0.0, 16.0 * ndof)
     # prolong-sum: per owner of a node one add of its local result and one FMA of the coarse
@@ -268,7 +275,8 @@ def kernel_model(w, info, ntype_counts, nloc_by_type, band, precision):
         prolong = ((4.0 + 3.0 * f) * ndof, 0.0, 0.0, (24.0 + 8.0 * f) * ndof)
     return {
         "stencil_Asigma": stencil,
-        "p_update": (2.0 * ndof, 0.0, 0.0, 24.0 * ndof),
+        # p = 2 in float pairs: the split p is written beside p
+        "p_update": (2.0 * ndof, 0.0, 0.0, (32.0 if (mixed and w.p == 2) else 24.0) * ndof),
         "xr_update": (6.0 * ndof, 0.0, 0.0, 48.0 * ndof),
         "prolong_sum": prolong,
         "pack_restrict": (2.0 * f * ndof, 0.0, 0.0, (8.0 + es * f) * ndof),
@@ -392,6 +400,8 @@ def profile_region(args, dd, dev):
         es.prepare()
         dd.dd_set_option(es.ctx, dd.DD_OPT_USE_GRAPH, 0)
         dd.dd_set_option(es.ctx, dd.DD_OPT_CHECK_EVERY, 1)
+        if args.gemm_tile:
+            dd.dd_set_option(es.ctx, dd.DD_OPT_GEMM_TILE_N, args.gemm_tile)
         ones = torch.ones(w.dofs, dtype=torch.float64, device=dev)
         b = torch.empty_like(ones)
         dd.dd_apply_operator(es.ctx, dd.DD_OP_MASS, ones, b)
@@ -406,7 +416,7 @@ def profile_region(args, dd, dev):
         torch.cuda.profiler.stop()
         l1 = dd.dd_kernel_launch_count()
     return {"mode": "profile_region", "workload": args.profile_region, "dofs": w.dofs, "precision": args.precision,
-            "pcg_iters": its, "relres": rel, "library_launches": l1 - l0}
+            "pcg_iters": its, "relres": rel, "library_launches": l1 - l0, "gemm_tile": args.gemm_tile}
 
 
 def one_shot_breakdown(args, dd, dev, reps=3, precision=None):

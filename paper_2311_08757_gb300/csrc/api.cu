@@ -341,6 +341,9 @@ void precond(dd_ctx* c, const double* r, int mode, double* zout = nullptr, bool 
 // The x/r update runs inside the restriction packing (launch_pack_xr) for p = 1 boxes with
 // BF16/TF32 local inverses and the fused p update, when the partial sums of (r, r) fit the
 // reduction buffer (one per subdomain).
+// The p = 1 float-pair pass stages whole node columns of at most blockDim rows.
+bool pairs_possible(const dd_ctx* c) { return c->g.p == 2 || c->g.Ypad <= 256; }
+
 bool fuse_xr_possible(const dd_ctx* c) {
   return c->g.p == 1 && (c->grid.precision == DD_PREC_BF16 || c->grid.precision == DD_PREC_TF32) &&
          c->fused_pq_opt != 0 && c->g.nsub <= kMaxRedBlocksHost;
@@ -350,6 +353,9 @@ void pcg_iteration(dd_ctx* c) {
   cudaStream_t s = c->stream;
   if (c->g.p == 1 && c->fused_pq_opt != 0) {   // fused, two nodes per thread unless option 1
     TIMED(KC_STENCIL, s, launch_fused_pq(c, s));
+  } else if (c->g.p == 2 && c->pq_pairs) {
+    TIMED(KC_PUPDATE, s, launch_pupdate_pairs(c, s));
+    TIMED(KC_STENCIL, s, launch_matvec_pq_pairs(c, s));
   } else {
     TIMED(KC_PUPDATE, s, launch_pupdate(c, s));
     TIMED(KC_STENCIL, s, launch_matvec_pq(c, s));
@@ -673,8 +679,8 @@ int dd_setup(const dd_grid* gr, const double* V, size_t nV, void* stream, dd_ctx
     c->tabA = (double*)dev_alloc(c, sizeof(double) * ntab);
     c->tabM = (double*)dev_alloc(c, sizeof(double) * ntab);
     c->tabS = (double*)dev_alloc(c, sizeof(double) * ntab);
-    if (g.p == 1) c->tabS2 = (float2*)dev_alloc(c, sizeof(float2) * kPairTapStride * g.ncls);
-    c->pq_pairs = (g.p == 1 && g.Ypad <= 256 && G.precision != DD_PREC_FP64) ? 1 : 0;
+    c->tabS2 = (float2*)dev_alloc(c, sizeof(float2) * pair_tap_stride(g.p) * g.ncls);
+    c->pq_pairs = (pairs_possible(c) && G.precision != DD_PREC_FP64) ? 1 : 0;
     launch_build_tables(c);
     build_subdomains(c);
     c->x = alloc_vec(c);
@@ -682,6 +688,7 @@ int dd_setup(const dd_grid* gr, const double* V, size_t nV, void* stream, dd_ctx
     c->z = alloc_vec(c);
     c->pb[0] = alloc_vec(c);
     c->pb[1] = alloc_vec(c);
+    if (g.p == 2) c->p2 = reinterpret_cast<float2*>(alloc_vec(c));   // 8-byte elements, the vectors' layout
     c->q = alloc_vec(c);
     c->w1 = alloc_vec(c);
     c->w2 = alloc_vec(c);
@@ -1330,11 +1337,10 @@ int dd_set_option(dd_ctx* c, int option, int value) {
       break;
     case DD_OPT_PAIRS:
       if (value < -1 || value > 1) return fail(c, DD_EINVAL, "float pairs must be -1, 0 or 1");
-      if (value == 1 && (c->g.p == 2 || c->g.Ypad > 256))
-        return fail(c, DD_EINVAL, "float pairs need p = 1 and at most 256 padded rows");
+      if (value == 1 && !pairs_possible(c))
+        return fail(c, DD_EINVAL, "float pairs need at most 256 padded rows for p = 1");
       c->pq_pairs_opt = value;
-      c->pq_pairs = value >= 0 ? value
-                               : ((c->g.p == 1 && c->g.Ypad <= 256 && c->grid.precision != DD_PREC_FP64) ? 1 : 0);
+      c->pq_pairs = value >= 0 ? value : ((pairs_possible(c) && c->grid.precision != DD_PREC_FP64) ? 1 : 0);
       break;
     case DD_OPT_PROLONG_TABLES:
       if (value != 0 && value != 1) return fail(c, DD_EINVAL, "prolong tables must be 0 or 1");

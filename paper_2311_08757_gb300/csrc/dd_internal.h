@@ -77,9 +77,12 @@ __host__ __device__ inline int4 p1_owners(const Geo& g, int a) {
   return ihi > ilo ? make_int4(ilo, l0, ihi, a - (lo1 > 1 ? lo1 : 1)) : make_int4(ilo, l0, -1, 0);
 }
 
-// The float-pair stencil table of a p = 1 box holds each class's 9 taps and one zero pad, so
-// that a class's row is five aligned 16-byte loads.
+// The float-pair stencil table holds each class's taps and one zero pad, so that a class's
+// row is a whole number of aligned 16-byte loads: 9 + 1 (p = 1, five loads), 27 + 1 (p = 2,
+// fourteen loads).
 constexpr int kPairTapStride = 10;
+constexpr int kPairTapStride3 = 28;
+inline int pair_tap_stride(int p) { return p == 1 ? kPairTapStride : kPairTapStride3; }
 
 // Subdomain descriptor on the device.
 struct Sub {
@@ -192,7 +195,8 @@ struct dd_ctx {
   double* tabA = nullptr;   // K + M_V
   double* tabM = nullptr;   // M
   double* tabS = nullptr;   // K + M_V - sigma M
-  float2* tabS2 = nullptr;  // p = 1: tabS as float pairs (hi, lo), class-major [cls][kPairTapStride]
+  float2* tabS2 = nullptr;  // tabS as float pairs (hi, lo), class-major [cls][pair_tap_stride(p)]
+  float2* p2 = nullptr;     // p = 2: the current PCG direction as float pairs (guard band as the vectors)
   double* tabL = nullptr;   // K + M_V - lambda M (adjoint of the eigenvector)
   double* qp_part = nullptr;      // quadrature-point reduction partials
   long long qp_part_len = 0;
@@ -348,6 +352,8 @@ void launch_check_finite(const double* v, long long n, int* flag, cudaStream_t s
 void launch_pcg_init(dd_ctx* c, const double* b, cudaStream_t s);   // r = b - A x, rr0
 void launch_pupdate(dd_ctx* c, cudaStream_t s);                     // p = z + beta p
 void launch_matvec_pq(dd_ctx* c, cudaStream_t s);                   // q = A p, pq, alpha
+void launch_pupdate_pairs(dd_ctx* c, cudaStream_t s);               // p = 2: p update, p also as float pairs
+void launch_matvec_pq_pairs(dd_ctx* c, cudaStream_t s);             // p = 2: q = A p in float pairs, pq, alpha
 void launch_fused_pq(dd_ctx* c, cudaStream_t s);                    // p = z + beta p; q = A p; pq (p = 1)
 void launch_xr_update(dd_ctx* c, cudaStream_t s);                   // x, r, rr, done
 // z = ..., rz, beta; upd (iterations): r -= alpha q first, the x update having run in launch_pack_xr

@@ -182,13 +182,13 @@ __global__ void k_tabS(long long n, const double* __restrict__ A, const double* 
     S[t] = A[t] - sigma * M[t];
 }
 
-// S2[cls][tap] = split(S[tap][cls]) for the 9 taps of a p = 1 class, zero pad in slot 9
-__global__ void k_tab_split(int ncls, const double* __restrict__ S, float2* __restrict__ S2) {
-  const long long n = (long long)ncls * kPairTapStride;
+// S2[cls][tap] = split(S[tap][cls]) for the ntap taps of a class, zero pads up to the stride
+__global__ void k_tab_split(int ncls, int ntap, int stride, const double* __restrict__ S, float2* __restrict__ S2) {
+  const long long n = (long long)ncls * stride;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x) {
-    const int cls = (int)(t / kPairTapStride), tap = (int)(t % kPairTapStride);
-    S2[t] = tap < 9 ? f64_split(S[(size_t)tap * ncls + cls]) : make_float2(0.0f, 0.0f);
+    const int cls = (int)(t / stride), tap = (int)(t % stride);
+    S2[t] = tap < ntap ? f64_split(S[(size_t)tap * ncls + cls]) : make_float2(0.0f, 0.0f);
   }
 }
 
@@ -197,8 +197,10 @@ void launch_tabS(dd_ctx* c, double sigma) {
   (k_tabS<<<grid_blocks(n, kThreads), kThreads, 0, c->stream>>>(n, c->tabA, c->tabM, sigma, c->tabS), dd::note_launch());
   DD_CUDA(cudaGetLastError());
   if (c->tabS2) {
-    const long long n2 = (long long)c->g.ncls * kPairTapStride;
-    (k_tab_split<<<grid_blocks(n2, kThreads), kThreads, 0, c->stream>>>(c->g.ncls, c->tabS, c->tabS2),
+    const int stride = pair_tap_stride(c->g.p);
+    const long long n2 = (long long)c->g.ncls * stride;
+    (k_tab_split<<<grid_blocks(n2, kThreads), kThreads, 0, c->stream>>>(c->g.ncls, c->g.ntap, stride, c->tabS,
+                                                                          c->tabS2),
      dd::note_launch());
     DD_CUDA(cudaGetLastError());
   }
@@ -732,6 +734,93 @@ void launch_matvec_pq(dd_ctx* c, cudaStream_t s) {
     (k_matvec_pq<2><<<nb, kThreads, 0, s>>>(g, c->tabS, c->pb[0], c->pb[1], c->q, c->st, c->red, c->cnt + CNT_PQ),
      dd::note_launch());
   DD_CUDA(cudaGetLastError());
+}
+
+// p = 2 with float pairs: the p update also stores p split into (hi, lo) floats (integer
+// operations, as f64_split), so that the 27 taps of every node read split values.
+__global__ void __launch_bounds__(kThreads) k_pupdate_pairs(long long n, const double* __restrict__ z, double* pb0,
+                                                            double* pb1, float2* __restrict__ p2, const PcgState* st) {
+  pdl_enter();
+  if (st->done) return;
+  const double beta = st->beta;
+  const int k = st->iter;
+  const double2* z2 = reinterpret_cast<const double2*>(z);
+  const double2* pp = reinterpret_cast<const double2*>(p_prev(pb0, pb1, k));
+  double2* pc = reinterpret_cast<double2*>(p_cur(pb0, pb1, k));
+  float4* ps = reinterpret_cast<float4*>(p2);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n / 2;
+       t += (long long)gridDim.x * blockDim.x) {
+    double2 a = z2[t], b = pp[t];
+    b.x = fma(beta, b.x, a.x);
+    b.y = fma(beta, b.y, a.y);
+    pc[t] = b;
+    const float2 u = f64_split(b.x), v = f64_split(b.y);
+    ps[t] = make_float4(u.x, u.y, v.x, v.y);
+  }
+}
+
+void launch_pupdate_pairs(dd_ctx* c, cudaStream_t s) {
+  const long long n = c->g.plen;
+  launch_chain(k_pupdate_pairs, dim3(grid_blocks(n / 2, kThreads)), dim3(kThreads), 0, s, c->pdl != 0, n,
+               (const double*)c->z, c->pb[0], c->pb[1], c->p2, (const PcgState*)c->st);
+}
+
+// p = 2: q = A_sigma p with the 27 taps in float pairs (split table, class-major, 14 aligned
+// 16-byte loads per class; split p from the p update; error-free products and sums as in the
+// p = 1 pass), q = hi + lo in FP64, pq = (p, q) and alpha in FP64.
+__global__ void __launch_bounds__(kThreads) k_matvec_pq_pairs(Geo g, const float2* __restrict__ tab2,
+                                                              const float2* __restrict__ p2, double* pb0,
+                                                              double* pb1, double* __restrict__ q, PcgState* st,
+                                                              double* partials, unsigned* counter) {
+  pdl_enter();
+  if (st->done) return;
+  const double* __restrict__ p = p_cur(pb0, pb1, st->iter);
+  const long long total = (long long)g.nxi * g.nxi * g.Ypad;
+  const long long c1 = (long long)g.ncx * g.Ypad, c2 = g.Ypad;
+  double acc[1] = {0.0};
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const Node nd = node_of<2>(g, t);
+    const int cls = cls_of<2>(g, nd);
+    const float4* tr = reinterpret_cast<const float4*>(tab2 + (size_t)cls * kPairTapStride3);
+    const float2* x = p2 + nd.idx;
+    float hs = 0.0f, ls = 0.0f;
+#pragma unroll
+    for (int k4 = 0; k4 < kPairTapStride3 / 2; ++k4) {
+      const float4 tv = __ldg(tr + k4);
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int tap = 2 * k4 + j;
+        if (tap < 27) {
+          const int d1 = tap / 9 - 1, d2 = (tap / 3) % 3 - 1, dy = tap % 3 - 1;
+          const float2 xv = __ldg(x + d1 * c1 + d2 * c2 + dy);
+          pair_fma(j ? tv.z : tv.x, j ? tv.w : tv.y, xv.x, xv.y, hs, ls);
+        }
+      }
+    }
+    const double qv = f32_to_f64(hs) + f32_to_f64(ls);
+    q[nd.idx] = qv;
+    acc[0] = fma(p[nd.idx], qv, acc[0]);
+  }
+  double tot[1];
+  if (grid_sum_last<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
+    const double pq = tot[0];
+    st->pq = pq;
+    if (!(pq > 0.0)) {
+      st->status = isfinite(pq) ? DD_ENOTSPD : DD_ENAN;
+      st->done = 1;
+    } else {
+      st->alpha = st->rho / pq;
+    }
+  }
+}
+
+void launch_matvec_pq_pairs(dd_ctx* c, cudaStream_t s) {
+  const Geo& g = c->g;
+  if (g.p != 2) throw Error(DD_EINVAL, "the float-pair matvec pass is the p = 2 form");
+  launch_chain(k_matvec_pq_pairs, dim3(resident_grid(k_matvec_pq_pairs, interior_work(g), kThreads)), dim3(kThreads),
+               0, s, c->pdl != 0, g, (const float2*)c->tabS2, (const float2*)c->p2, c->pb[0], c->pb[1], c->q, c->st,
+               c->red, c->cnt + CNT_PQ);
 }
 
 // x += alpha p, r -= alpha q, rr = (r, r); stop test ||r|| <= rtol ||r0|| (Sec. 4.1).

@@ -26,6 +26,8 @@ CASES = {
     "cfg2_small": WORKLOADS["cfg2_small"],
     "ragged": Workload("ragged", p=1, L=5, n=10, ell=1.2, overlap=3, kind="cos4", seed=7),
     "L256": Workload("L256", p=1, L=256, n=32, overlap=4, kind="cos4", seed=11),
+    "p2": Workload("p2", p=2, L=3, n=6, overlap=2, kind="asym3"),
+    "p2_wells": Workload("p2_wells", p=2, L=4, n=8, overlap=2, kind="wells"),
 }
 
 
@@ -117,7 +119,11 @@ def test_option_validation():
         for bad in (-2, 2):
             with pytest.raises(dd.DDError):
                 dd.dd_set_option(es.ctx, dd.DD_OPT_PAIRS, bad)
-    with make_solver(Workload("p2", p=2, L=2, n=6, overlap=2, kind="asym3"), precision="bf16") as es:
+    # p = 1 stages whole node columns in one block: at most 256 padded rows
+    with make_solver(Workload("tall", p=1, L=1, n=32, ell=9.0, overlap=2, kind="cos1"), precision="bf16") as es:
         with pytest.raises(dd.DDError):
             dd.dd_set_option(es.ctx, dd.DD_OPT_PAIRS, 1)
+        dd.dd_set_option(es.ctx, dd.DD_OPT_PAIRS, 0)
+    with make_solver(Workload("p2", p=2, L=2, n=6, overlap=2, kind="asym3"), precision="bf16") as es:
+        dd.dd_set_option(es.ctx, dd.DD_OPT_PAIRS, 1)
         dd.dd_set_option(es.ctx, dd.DD_OPT_PAIRS, 0)
