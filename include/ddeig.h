@@ -393,7 +393,12 @@ int dd_coarse_matrix(dd_ctx* ctx, double* A0_host);
  *                       kernel took 32 us against 22 + 14 us for the two, but the ground state
  *                       24.0 ms against 23.6 ms (the r store moves into the prolong-sum, which
  *                       slows by 1.5 us, and the coarse solve forks later), so off by default;
- *                       -1: off [0] */
+ *                       -1: off [0]
+ *   DD_OPT_TILED3       p = 2 with float pairs: 1 evaluates q = A_sigma p tile by tile from
+ *                       shared memory (each block takes the planes of one residue a1 mod n, so
+ *                       it stages the n Ypad classes of the split table once, and for every tile
+ *                       the split p of three planes), where n Ypad <= 448; 0 reads the table and
+ *                       p through the caches.  The same q; (p, q) summed in another order [1] */
 #define DD_OPT_CHECK_EVERY 0
 #define DD_OPT_USE_GRAPH   1
 #define DD_OPT_FLEXIBLE    2
@@ -409,6 +414,7 @@ int dd_coarse_matrix(dd_ctx* ctx, double* A0_host);
 #define DD_OPT_PAIRS       12
 #define DD_OPT_PDL         13
 #define DD_OPT_FUSE_XR     14
+#define DD_OPT_TILED3      15
 int dd_set_option(dd_ctx* ctx, int option, int value);
 
 /* Per-kernel-class timing collected while DD_OPT_TIMING = 1: for class k (0 <= k < count),

@@ -1331,6 +1331,10 @@ int dd_set_option(dd_ctx* c, int option, int value) {
       c->fuse_xr_opt = value;
       c->fuse_xr = value > 0 ? 1 : 0;
       break;
+    case DD_OPT_TILED3:
+      if (value != 0 && value != 1) return fail(c, DD_EINVAL, "tiled p = 2 matvec must be 0 or 1");
+      c->matvec_tiled = value;
+      break;
     case DD_OPT_PDL:
       if (value != 0 && value != 1) return fail(c, DD_EINVAL, "programmatic dependent launch must be 0 or 1");
       c->pdl = value;

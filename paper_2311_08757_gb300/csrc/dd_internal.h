@@ -167,6 +167,7 @@ struct dd_ctx {
   int4 ptypes = {0, 0, 0, 0};       // p = 1: type ids of the left end, interior and right end subdomains
   int pdl = 0;                      // PCG chain kernels launched with programmatic dependent launch
   int fuse_xr_opt = 0;              // x/r update fused into the packing: 1 on, 0 or -1 off
+  int matvec_tiled = 1;             // p = 2 float pairs: the shared-memory tiled matvec where it fits
   int fuse_xr = 0;                  // the resolved choice
   int pq_pairs_opt = -1;            // q = A_sigma p of the fused p = 1 kernel: -1 automatic, 0 FP64, 1 float pairs
   int pq_pairs = 0;                 // the resolved choice

@@ -815,9 +815,121 @@ __global__ void __launch_bounds__(kThreads) k_matvec_pq_pairs(Geo g, const float
   }
 }
 
+// The same pass tiled through shared memory.  The class of node (a1, a2, slot) is
+// ((a1 mod n) n + a2 mod n) Ypad + slot, so a block that takes only planes a1 = r (mod n)
+// needs n Ypad classes of the table: it stages that slice once (n Ypad rows of 28 float
+// pairs), then walks its share of the residue's (plane, a2 tile) pairs; each tile (one plane,
+// TA = blockDim / Ypad node columns, one node per thread) stages the split p of the planes
+// a1 - 1 .. a1 + 1 over columns a2 - 1 .. a2 + TA, so every tap reads shared memory.  Each
+// node's arithmetic is that of k_matvec_pq_pairs (the same q bits); the (p, q) partials are
+// summed in another order.
+constexpr int kTiledMaxClasses = 448;   // n Ypad <= 448: the table slice is at most 98 KB
+
+__global__ void __launch_bounds__(kThreads) k_matvec_pq_pairs_tiled(Geo g, const float2* __restrict__ tab2,
+                                                                    const float2* __restrict__ p2, double* pb0,
+                                                                    double* pb1, double* __restrict__ q,
+                                                                    PcgState* st, double* partials,
+                                                                    unsigned* counter) {
+  pdl_enter();
+  if (st->done) return;
+  extern __shared__ __align__(16) float4 smt[];
+  const int Y = g.Ypad, yl = g.ylog, n = g.n;
+  const int ncls_r = n * Y;                      // classes of one residue
+  const int TA = (int)blockDim.x >> yl;          // node columns per tile (blockDim multiple of Y)
+  float2* tabs = reinterpret_cast<float2*>(smt);                    // [ncls_r][28]
+  float2* tile_raw = tabs + (size_t)ncls_r * kPairTapStride3;       // guard, [3][TA + 2][Y], guard
+  float2* tile = tile_raw + 1;
+  const int row = (TA + 2) * Y;                  // one plane's staged run
+  const int nbr = (int)gridDim.x / n;            // blocks per residue
+  const int r = (int)blockIdx.x % n, kb = (int)blockIdx.x / n;
+  // the residue's table slice: classes (r n + m) Y + slot for m < n
+  {
+    const float4* src = reinterpret_cast<const float4*>(tab2 + (size_t)r * ncls_r * kPairTapStride3);
+    float4* dst = smt;
+    for (int e = threadIdx.x; e < ncls_r * (kPairTapStride3 / 2); e += blockDim.x) dst[e] = __ldg(src + e);
+  }
+  if (threadIdx.x == 0) {
+    tile_raw[0] = make_float2(0.0f, 0.0f);
+    tile_raw[3 * row + 1] = make_float2(0.0f, 0.0f);
+  }
+  const double* __restrict__ p = p_cur(pb0, pb1, st->iter);
+  const int a1_first = (r == 0) ? n : r;
+  const int nplanes = (a1_first <= g.nxi) ? (g.nxi - a1_first) / n + 1 : 0;
+  const int ntile2 = (g.nxi + TA - 1) / TA;
+  const long long ntiles = (long long)nplanes * ntile2;
+  const long long c1 = (long long)g.ncx * Y;
+  const int c = (int)threadIdx.x >> yl, slot = (int)threadIdx.x & (Y - 1);
+  double acc[1] = {0.0};
+  for (long long tt = kb; tt < ntiles; tt += nbr) {
+    const int a1 = a1_first + n * (int)(tt / ntile2);
+    const int a2_0 = 1 + TA * (int)(tt % ntile2);
+    __syncthreads();   // the previous tile's taps are read (and, the first time, the table staged)
+    for (int e = threadIdx.x; e < 3 * row; e += blockDim.x) {
+      const int pl = e / row, w = e - pl * row;
+      const int col = a2_0 - 1 + (w >> yl);
+      tile[e] = (col <= g.nxi + 1) ? p2[(long long)(a1 - 1 + pl) * c1 + (long long)col * Y + (w & (Y - 1))]
+                                   : make_float2(0.0f, 0.0f);
+    }
+    __syncthreads();
+    const int a2 = a2_0 + c;
+    if (a2 <= g.nxi) {
+      const float4* tr = reinterpret_cast<const float4*>(tabs + (size_t)((a2 % n) * Y + slot) * kPairTapStride3);
+      const float2* x = tile + row + (c + 1) * Y + slot;   // plane a1, column a2 (the centre of the taps)
+      float hs = 0.0f, ls = 0.0f;
+#pragma unroll
+      for (int k4 = 0; k4 < kPairTapStride3 / 2; ++k4) {
+        const float4 tv = tr[k4];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int tap = 2 * k4 + j;
+          if (tap < 27) {
+            const int d1 = tap / 9 - 1, d2 = (tap / 3) % 3 - 1, dy = tap % 3 - 1;
+            const float2 xv = x[d1 * row + d2 * Y + dy];
+            pair_fma(j ? tv.z : tv.x, j ? tv.w : tv.y, xv.x, xv.y, hs, ls);
+          }
+        }
+      }
+      const long long idx = ((long long)a1 * g.ncx + a2) * Y + slot;
+      const double qv = f32_to_f64(hs) + f32_to_f64(ls);
+      q[idx] = qv;
+      acc[0] = fma(p[idx], qv, acc[0]);
+    }
+  }
+  double tot[1];
+  if (grid_sum_last<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
+    const double pq = tot[0];
+    st->pq = pq;
+    if (!(pq > 0.0)) {
+      st->status = isfinite(pq) ? DD_ENOTSPD : DD_ENAN;
+      st->done = 1;
+    } else {
+      st->alpha = st->rho / pq;
+    }
+  }
+}
+
+bool matvec_tiled_fits(const Geo& g) {
+  return g.p == 2 && g.n * g.Ypad <= kTiledMaxClasses && g.Ypad <= kThreads && g.nxi >= g.n;
+}
+
 void launch_matvec_pq_pairs(dd_ctx* c, cudaStream_t s) {
   const Geo& g = c->g;
   if (g.p != 2) throw Error(DD_EINVAL, "the float-pair matvec pass is the p = 2 form");
+  if (c->matvec_tiled && matvec_tiled_fits(g)) {
+    const int TA = kThreads / g.Ypad;
+    const size_t smem = sizeof(float2) * ((size_t)g.n * g.Ypad * kPairTapStride3 + 3 * (size_t)(TA + 2) * g.Ypad + 2);
+    static PerDeviceOnce attr;
+    once_per_device(attr, [] {
+      DD_CUDA(cudaFuncSetAttribute(k_matvec_pq_pairs_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    });
+    int per_sm = 0;
+    DD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_matvec_pq_pairs_tiled, kThreads, smem));
+    const int nbr = std::max(1, 152 * std::max(per_sm, 1) / g.n);   // blocks per residue
+    launch_chain(k_matvec_pq_pairs_tiled, dim3(g.n * nbr), dim3(kThreads), smem, s, c->pdl != 0, g,
+                 (const float2*)c->tabS2, (const float2*)c->p2, c->pb[0], c->pb[1], c->q, c->st, c->red,
+                 c->cnt + CNT_PQ);
+    return;
+  }
   launch_chain(k_matvec_pq_pairs, dim3(resident_grid(k_matvec_pq_pairs, interior_work(g), kThreads)), dim3(kThreads),
                0, s, c->pdl != 0, g, (const float2*)c->tabS2, (const float2*)c->p2, c->pb[0], c->pb[1], c->q, c->st,
                c->red, c->cnt + CNT_PQ);

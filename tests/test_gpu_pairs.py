@@ -67,6 +67,29 @@ def test_pairs_reach_the_fp64_ground_state(name, prec, method):
     assert abs(t1 - t0) <= max(3, 0.05 * t0)
 
 
+@pytest.mark.parametrize("name", ["p2", "p2_wells"])
+def test_tiled_3d_pairs_matvec(name):
+    """The shared-memory tiled p = 2 pass (DD_OPT_TILED3) against the cached one: the same q
+    per node, (p, q) summed in another order, so the same ground state within the stop rule and
+    iteration counts within a few."""
+    w = CASES[name]
+    P = oracle_problem(w, build_prec=False)
+    lam_ex, _ = solvers.exact_ground_state(P.A, P.M, sigma=P.sigma, dense_limit=3000 if w.dofs <= 3000 else 0)
+    out = {}
+    for tiled in (0, 1):
+        with make_solver(w, precision="bf16") as es:
+            es.prepare()
+            dd.dd_set_option(es.ctx, dd.DD_OPT_TILED3, tiled)
+            x = gpu_vec(np.ones(w.dofs))
+            lam, outer, tot, mx = dd.dd_inverse_iterate(es.ctx, x)
+            out[tiled] = (lam, tot, host(x))
+    print(f"{name}: inner {out[0][1]} (cached) {out[1][1]} (tiled)")
+    for lam, tot, x in out.values():
+        assert abs(lam - lam_ex) <= 1e-10 * abs(lam_ex)
+        assert _eta(P, x, lam) <= 1e-8 + 1e-12
+    assert abs(out[0][1] - out[1][1]) <= 3
+
+
 @pytest.mark.parametrize("name", ["cfg1", "cfg2_small", "L256"])
 def test_pairs_pcg_solve(name):
     """The shifted solve A_sigma w = M 1 to rTOL = 1e-8: the same iteration count within one or
