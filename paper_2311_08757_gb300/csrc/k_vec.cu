@@ -952,20 +952,30 @@ __device__ __forceinline__ void xr_update_body(VBlk vb, long long n, double* pb0
   if (PAIRS) {
     // (r, r) in float pairs on r 2^-k, 2^k ~ sqrt of the previous (r, r): each thread's sum
     // hi + lo (error ~2^-46 of it) is scaled back by 2^2k and enters the FP64 reduction
+    // Two grid-stride steps per pass, their eight loads issued together (the elements, and
+    // the order of their partial sums, are those of one step per pass).
     const int k = half_exponent(st->rr);
     float hs = 0.0f, ls = 0.0f;
-    for (long long t = (long long)vb.b * blockDim.x + threadIdx.x; t < n / 2;
-         t += (long long)vb.nb * blockDim.x) {
-      double2 pv = p2[t], qv = q2[t], xv = x2[t], rv = r2[t];
-      xv.x = fma(alpha, pv.x, xv.x);
-      xv.y = fma(alpha, pv.y, xv.y);
-      rv.x = fma(-alpha, qv.x, rv.x);
-      rv.y = fma(-alpha, qv.y, rv.y);
-      x2[t] = xv;
-      r2[t] = rv;
-      const float2 a = f64_split_pow2(rv.x, k), b = f64_split_pow2(rv.y, k);
-      pair_fma(a.x, a.y, a.x, a.y, hs, ls);
-      pair_fma(b.x, b.y, b.x, b.y, hs, ls);
+    const long long stride = (long long)vb.nb * blockDim.x, n2 = n / 2;
+    for (long long t = (long long)vb.b * blockDim.x + threadIdx.x; t < n2; t += 2 * stride) {
+      const bool two = t + stride < n2;
+      const long long u = two ? t + stride : t;
+      double2 pv[2] = {__ldg(p2 + t), __ldg(p2 + u)}, qv[2] = {__ldg(q2 + t), __ldg(q2 + u)};
+      double2 xv[2] = {x2[t], x2[u]}, rv[2] = {r2[t], r2[u]};
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        if (j == 1 && !two) break;
+        const long long tj = j ? u : t;
+        xv[j].x = fma(alpha, pv[j].x, xv[j].x);
+        xv[j].y = fma(alpha, pv[j].y, xv[j].y);
+        rv[j].x = fma(-alpha, qv[j].x, rv[j].x);
+        rv[j].y = fma(-alpha, qv[j].y, rv[j].y);
+        x2[tj] = xv[j];
+        r2[tj] = rv[j];
+        const float2 a = f64_split_pow2(rv[j].x, k), b = f64_split_pow2(rv[j].y, k);
+        pair_fma(a.x, a.y, a.x, a.y, hs, ls);
+        pair_fma(b.x, b.y, b.x, b.y, hs, ls);
+      }
     }
     acc[0] = (f32_to_f64(hs) + f32_to_f64(ls)) * pow2_f64(2 * k);
   } else {
@@ -1010,8 +1020,11 @@ __global__ void __launch_bounds__(kThreads) k_xr_update(long long n, double* pb0
 
 // The FP64 form takes 64 registers, so 4 blocks of 256 per SM are resident: one wave of
 // 608 blocks (22.5 us on the 2.03M-unknown L = 2048 box) instead of two of the default 1216
-// (25.5 us); the float-pair form takes 32, so 8 per SM.
-static int xr_blocks(const dd_ctx* c) { return grid_blocks(c->g.plen / 2, kThreads, c->pq_pairs ? 8 : 4); }
+// (25.5 us); the float-pair form, one wave of what the occupancy calculator allows.
+static int xr_blocks(const dd_ctx* c) {
+  return c->pq_pairs ? resident_grid(k_xr_update<true>, c->g.plen / 2, kThreads)
+                     : grid_blocks(c->g.plen / 2, kThreads, 4);
+}
 
 void launch_xr_update(dd_ctx* c, cudaStream_t s) {
   const long long n = c->g.plen;
