@@ -268,6 +268,19 @@ void build_subdomains(dd_ctx* c) {
   c->subrow = (int4*)dev_alloc(c, sizeof(int4) * g.nsub);
   DD_CUDA(cudaMemcpyAsync(c->axown, ax.data(), sizeof(int4) * g.ncx, cudaMemcpyHostToDevice, c->stream));
   DD_CUDA(cudaMemcpyAsync(c->subrow, sr.data(), sizeof(int4) * g.nsub, cudaMemcpyHostToDevice, c->stream));
+  if (g.p == 1) {
+    // per node column a and owner: its packed row and type row advanced to the column's local
+    // position; an absent owner repeats subdomain 0's rows (a valid address, masked)
+    std::vector<int4> crw(g.ncx);
+    for (int a = 0; a < g.ncx; ++a) {
+      const int4 t = ax[a];
+      const int o0 = t.x >= 0 ? t.x : 0, o1 = t.z >= 0 ? t.z : 0;
+      const int l0 = t.x >= 0 ? t.y : 0, l1 = t.z >= 0 ? t.w : 0;
+      crw[a] = make_int4(sr[o0].x + l0 * g.Ypad, sr[o0].y + l0 * g.Ypad, sr[o1].x + l1 * g.Ypad, sr[o1].y + l1 * g.Ypad);
+    }
+    c->colrow = (int4*)dev_alloc(c, sizeof(int4) * g.ncx);
+    DD_CUDA(cudaMemcpyAsync(c->colrow, crw.data(), sizeof(int4) * g.ncx, cudaMemcpyHostToDevice, c->stream));
+  }
   DD_CUDA(cudaMemcpyAsync(c->subs, c->subs_h.data(), sizeof(Sub) * g.nsub, cudaMemcpyHostToDevice, c->stream));
   DD_CUDA(cudaMemcpyAsync(c->slot_of_sub, slot.data(), sizeof(int) * g.nsub, cudaMemcpyHostToDevice, c->stream));
   DD_CUDA(cudaStreamSynchronize(c->stream));

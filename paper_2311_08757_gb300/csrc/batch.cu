@@ -268,7 +268,7 @@ BGroup* build_group(dd_batch* b, const std::vector<int>& idx) {
       I.st = c->st; I.ost = c->ost; I.red = c->red; I.cnt = c->cnt;
       I.subs = c->subs; I.slot_of_sub = c->slot_of_sub; I.Rpack = c->Rpack; I.wT = c->wT; I.c0 = c->c0;
       I.u0 = c->u0; I.u0f = c->u0f; I.Y32 = c->Y32; I.wT32 = c->wT32; I.puT32 = c->puT32;
-      I.axown = c->axown; I.subrow = c->subrow; I.cr = c->cr;
+      I.axown = c->axown; I.subrow = c->subrow; I.colrow = c->colrow; I.cr = c->cr;
       I.cr_m = c->cr_m; I.cr_c2 = c->cr_c2; I.cr_w2 = c->cr_w2;
       size_t smem = 0;
       int staged = 0;

@@ -198,6 +198,7 @@ struct dd_ctx {
   double* tabS = nullptr;   // K + M_V - sigma M
   float2* tabS2 = nullptr;  // tabS as float pairs (hi, lo), class-major [cls][pair_tap_stride(p)]
   float2* p2 = nullptr;     // p = 2: the current PCG direction as float pairs (guard band as the vectors)
+  int4* colrow = nullptr;   // p = 1: per node column, each owner's packed-row and type-row offsets there
   double* tabL = nullptr;   // K + M_V - lambda M (adjoint of the eigenvector)
   double* qp_part = nullptr;      // quadrature-point reduction partials
   long long qp_part_len = 0;
@@ -312,6 +313,7 @@ struct BInst {
   const float* puT32;
   const int4* axown;
   const int4* subrow;
+  const int4* colrow;
   const double* cr;       // cyclic-reduction coefficients of A_0 (p = 1)
   int cr_m, cr_c2, cr_w2, cr_staged;
   int kpad, coarse, nsub, flexible;

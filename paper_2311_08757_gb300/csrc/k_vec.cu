@@ -1062,7 +1062,8 @@ __device__ __forceinline__ double fma_t(double a, double b, double c) { return f
 // first (the same FMA as the separate x/r update, each node once), and the dots take that r.
 template <int P, typename TY, bool RAS, int U, bool ARITH = false, bool UPD = false>
 __device__ __forceinline__ void prolong_body(VBlk vb, Geo g, const int4* __restrict__ axown,
-                                                      const int4* __restrict__ subrow, const TY* __restrict__ Y,
+                                                      const int4* __restrict__ subrow,
+                                                      const int4* __restrict__ colrow, const TY* __restrict__ Y,
                                                       const TY* __restrict__ wT, const TY* __restrict__ puT,
                                                       const TY* __restrict__ u0, int coarse,
                                                       const double* __restrict__ r, const double* __restrict__ q,
@@ -1070,6 +1071,10 @@ __device__ __forceinline__ void prolong_body(VBlk vb, Geo g, const int4* __restr
                                                       double* partials, unsigned* counter, int kpad = 0,
                                                       int4 pt = make_int4(0, 0, 0, 0), double* r_out = nullptr) {
   static_assert(!ARITH || P == 1, "closed-form owners are those of a p = 1 box");
+  // p = 1 with the tables: colrow[a] holds, per owner of node column a, the offsets of its
+  // packed row and type row at the column's local position (subrow[o] + local column * Ypad),
+  // so a node's loads of Y, wT and u0 wait on one table load instead of two
+  constexpr bool kColRow = (P == 1) && !ARITH;
   if (mode != 0 && st->done) return;
   const bool flex = (mode == 2) && st->flexible;
   const double alpha_r = UPD ? st->alpha : 0.0;
@@ -1081,7 +1086,7 @@ __device__ __forceinline__ void prolong_body(VBlk vb, Geo g, const int4* __restr
     // branch-free: out-of-range nodes and absent owners read valid addresses and are masked
     bool in[U], valid[U];
     Node nd[U];
-    int4 A1[U], A2[U];
+    int4 A1[U], A2[U], CR[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const long long t = t0 + u * stride;
@@ -1090,6 +1095,7 @@ __device__ __forceinline__ void prolong_body(VBlk vb, Geo g, const int4* __restr
       valid[u] = in[u] && nd[u].slot < g.nyi;
       A1[u] = ARITH ? p1_owners(g, nd[u].a1) : __ldg(axown + nd[u].a1);
       A2[u] = (P == 2) ? __ldg(axown + nd[u].a2) : make_int4(0, 0, -1, 0);
+      CR[u] = kColRow ? __ldg(colrow + nd[u].a1) : make_int4(0, 0, 0, 0);
     }
     bool ok[U][NO];
     int sub[U][NO], loc[U][NO];
@@ -1103,6 +1109,11 @@ __device__ __forceinline__ void prolong_body(VBlk vb, Geo g, const int4* __restr
         const int o2 = k ? A2[u].z : A2[u].x, l2 = k ? A2[u].w : A2[u].y;
         ok[u][e] = o1 >= 0 && (P == 1 || o2 >= 0);
         sub[u][e] = ok[u][e] ? ((P == 1) ? o1 : o1 * g.L + o2) : 0;
+        if (kColRow) {   // the owner's packed row and type row, its local column included
+          sr[u][e] = i ? make_int4(CR[u].z, CR[u].w, 1, 0) : make_int4(CR[u].x, CR[u].y, 1, 0);
+          loc[u][e] = ok[u][e] ? nd[u].slot : 0;
+          continue;
+        }
         if (ARITH) {
           const int sb = sub[u][e];
           const int ty = sb == 0 ? pt.x : (sb == g.L - 1 ? pt.z : pt.y);
@@ -1170,7 +1181,8 @@ __device__ __forceinline__ void prolong_body(VBlk vb, Geo g, const int4* __restr
 
 template <int P, typename TY, bool RAS, int U, bool ARITH = false, bool UPD = false>
 __global__ void __launch_bounds__(kThreads, (P == 1 ? 8 : 5) / U) k_prolong(Geo g, const int4* __restrict__ axown,
-                                                      const int4* __restrict__ subrow, const TY* __restrict__ Y,
+                                                      const int4* __restrict__ subrow,
+                                                      const int4* __restrict__ colrow, const TY* __restrict__ Y,
                                                       const TY* __restrict__ wT, const TY* __restrict__ puT,
                                                       const TY* __restrict__ u0, int coarse,
                                                       const double* __restrict__ r, const double* __restrict__ q,
@@ -1178,8 +1190,8 @@ __global__ void __launch_bounds__(kThreads, (P == 1 ? 8 : 5) / U) k_prolong(Geo 
                                                       double* partials, unsigned* counter, int kpad, int4 pt,
                                                       double* r_out) {
   pdl_enter();
-  prolong_body<P, TY, RAS, U, ARITH, UPD>(vblk_self(), g, axown, subrow, Y, wT, puT, u0, coarse, r, q, z, mode, st,
-                                          partials, counter, kpad, pt, r_out);
+  prolong_body<P, TY, RAS, U, ARITH, UPD>(vblk_self(), g, axown, subrow, colrow, Y, wT, puT, u0, coarse, r, q, z,
+                                          mode, st, partials, counter, kpad, pt, r_out);
 }
 
 // nodes per thread and pass (each node's loads go out together, absent owners masked):
@@ -1197,7 +1209,8 @@ void launch_prolong(dd_ctx* c, int mode, cudaStream_t s, double* zout, bool upd)
 #define DD_PROLONG_A(PP, TY, YP, W, PU, U0, RS, AR, UP)                                                          \
   launch_chain(k_prolong<PP, TY, RS, kProlongU, AR, UP>,                                                          \
                dim3(resident_grid(k_prolong<PP, TY, RS, kProlongU, AR, false>, work, kThreads)), dim3(kThreads), 0, \
-               s, c->pdl != 0, g, (const int4*)c->axown, (const int4*)c->subrow, (const TY*)(YP),                \
+               s, c->pdl != 0, g, (const int4*)c->axown, (const int4*)c->subrow, (const int4*)c->colrow,        \
+               (const TY*)(YP),                                                                               \
                (const TY*)(W), (const TY*)(PU), (const TY*)(U0), coarse, (const double*)c->r,                    \
                (const double*)c->q, z, mode, c->st, c->red, c->cnt + CNT_RZ, c->kpad, c->ptypes,               \
                UP ? c->r : (double*)nullptr)
@@ -1567,7 +1580,7 @@ __global__ void __launch_bounds__(kThreads, 8 / kProlongU) kb_prolong(const BIns
   const int2 m = vmap[blockIdx.x];
   const BInst& I = B[m.x];
   if (!I.active) return;
-  prolong_body<1, float, false, kProlongU, ARITH, UPD>(VBlk{m.y, I.nb_prolong}, I.g, I.axown, I.subrow, I.Y32,
+  prolong_body<1, float, false, kProlongU, ARITH, UPD>(VBlk{m.y, I.nb_prolong}, I.g, I.axown, I.subrow, I.colrow, I.Y32,
                                                        I.wT32, I.puT32, I.u0f, I.coarse, I.r, I.q, I.z, mode, I.st,
                                                        I.red, I.cnt + CNT_RZ, I.kpad, I.ptypes, UPD ? I.r : nullptr);
 }
