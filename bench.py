@@ -319,7 +319,6 @@ def roofline_entry(name, model, ms_total, nlaunch, peaks, peak_src, precision, a
 # capture is left out.
 TRAFFIC = {
     "stencil_Asigma": (33.67 + 0.586) * 1e6,
-    "xr_update": (67.13 + 0.660) * 1e6,
     "pack_restrict": (16.87 + 0.000) * 1e6,
     "local_gemm_tc": (15.10 + 0.000) * 1e6,
     "prolong_sum": (44.92 + 0.136) * 1e6,

@@ -364,18 +364,16 @@ int dd_coarse_matrix(dd_ctx* ctx, double* A0_host);
  *                       set-up found the formula equal to the tables (same values, two dependent
  *                       loads fewer per node, but more integer work: 28.1 against 24.5 us per
  *                       launch on the L = 2048, h = 1/32 box) [1]
- *   DD_OPT_PAIRS        p = 1: the FP64 arithmetic of the PCG iteration that the
- *                       FP32 pipe can carry, done in float pairs (a value split into hi + lo,
- *                       48 significand bits; error-free products and sums).  1: q = A_sigma p
- *                       (each coefficient and p value split; q agrees with the FP64 stencil to
- *                       about 2^-47 times the sum of the taps' magnitudes) and the partial sums
- *                       of (r, r) (r scaled by a power of two from the previous (r, r), error
- *                       about 2^-46 of each thread's sum; the sum across threads stays FP64).
- *                       p, q, x, r, z and their updates, (p, q), (r, z), (q, z), the
- *                       outer iteration's residuals and Rayleigh quotients, the stop rules and
- *                       dd_apply_operator stay FP64.  0: all FP64.  Needs at most 256 padded
- *                       rows (Ypad).  -1: 1 when the local inverses are rounded (precision
- *                       other than FP64) and Ypad <= 256, else 0 [-1]
+ *   DD_OPT_PAIRS        the matvec q = A_sigma p of the PCG iteration in float pairs on the FP32
+ *                       pipe: each coefficient and p value split into hi + lo (48 significand
+ *                       bits), error-free products and sums, q = hi + lo in FP64; q agrees with
+ *                       the FP64 stencil to about 2^-47 times the sum of the taps' magnitudes (the
+ *                       FP64 one: 2^-53).  p = 1: inside the fused p update pass; p = 2: the p
+ *                       update also stores p split.  p, q, x, r, z and their updates, every dot
+ *                       product, the coarse solve, the outer iteration's residuals and Rayleigh
+ *                       quotients, the stop rules and dd_apply_operator stay FP64.  0: the FP64
+ *                       matvec.  p = 1 needs at most 256 padded rows (Ypad).  -1: 1 when the
+ *                       local inverses are rounded (precision other than FP64), else 0 [-1]
  *   DD_OPT_PDL          1: the kernels of the PCG iteration's chain (fused p update, x/r update,
  *                       restriction packing, local contraction, prolong-sum) are launched with
  *                       programmatic dependent launch, so that each one's blocks are scheduled

@@ -188,10 +188,10 @@ void precond(BGroup* g, int mode, bool packed = false) {
 void pcg_iteration(BGroup* g) {
   dd::launch_b_fused_pq(g->B, g->vm_fused, g->n_fused, g->ypad, g->pairs, g->s);
   if (g->fuse) {
-    dd::launch_b_pack_xr(g->B, g->vm_pack, g->n_pack, g->precision, g->pairs, g->s);
+    dd::launch_b_pack_xr(g->B, g->vm_pack, g->n_pack, g->precision, g->s);
     precond(g, 2, true);
   } else {
-    dd::launch_b_xr_update(g->B, g->vm_xr, g->n_xr, g->pairs, g->s);
+    dd::launch_b_xr_update(g->B, g->vm_xr, g->n_xr, g->s);
     precond(g, 2);
   }
 }

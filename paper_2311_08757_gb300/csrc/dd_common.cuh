@@ -215,22 +215,17 @@ static __device__ __noinline__ float2 f64_split_slow(double d) {
   return make_float2(hi, __double2float_rz(d - (double)hi));
 }
 
-static __device__ __noinline__ float2 f64_split_pow2_slow(double d, int k) { return f64_split_slow(ldexp(d, -k)); }
-
-// d 2^-k = hi + lo + e with |e| < 2^-47 |d 2^-k|: hi is the first 24 significand bits, lo the
-// next 24 (both truncated toward zero).  Integer operations on the two words of d for
-// 2^-74 <= |d 2^-k| < 2^127 (so that lo stays a normal float) and zeros; other values (tiny,
-// huge, subnormal, infinities, NaNs) take the hardware operations.  k = 0: the plain split.
-__device__ __forceinline__ float2 f64_split_pow2(double d, int k) {
-  unsigned H = (unsigned)__double2hiint(d);
-  const unsigned Lw = (unsigned)__double2loint(d);
-  const unsigned E0 = (H >> 20) & 0x7FFu;
-  const unsigned E = E0 - (unsigned)k;
-  if (__builtin_expect(E - 949u > 1150u - 949u || E0 - 1u > 2045u, 0)) {
+// d = hi + lo + e with |e| < 2^-47 |d|: hi is d's first 24 significand bits, lo the next 24
+// (both truncated toward zero).  Integer operations on the two words of d for
+// 2^-74 <= |d| < 2^127 (so that lo stays a normal float) and zeros; other values (tiny,
+// huge, subnormal, infinities, NaNs) take the hardware conversions.
+__device__ __forceinline__ float2 f64_split(double d) {
+  const unsigned H = (unsigned)__double2hiint(d), Lw = (unsigned)__double2loint(d);
+  const unsigned E = (H >> 20) & 0x7FFu;
+  if (__builtin_expect(E - 949u > 1150u - 949u, 0)) {
     if (((H << 1) | Lw) == 0u) return make_float2(0.0f, 0.0f);
-    return k ? f64_split_pow2_slow(d, k) : f64_split_slow(d);
+    return f64_split_slow(d);
   }
-  H -= (unsigned)k << 20;   // the exponent field, E0 -> E (both normal)
   const unsigned sgn = H & 0x80000000u;
   // exponent rebias 1023 -> 127 (896 << 20) and the 20 + 3 leading significand bits
   const float hi = __uint_as_float(sgn | ((H - 0x38000000u) << 3) | (Lw >> 29));
@@ -240,17 +235,6 @@ __device__ __forceinline__ float2 f64_split_pow2(double d, int k) {
   const unsigned lz = __clz((int)m29);
   const unsigned lo_bits = sgn | (((E - 918u - lz) << 23) + ((m29 << lz) >> 8));
   return make_float2(hi, __uint_as_float(m29 ? lo_bits : 0u));
-}
-__device__ __forceinline__ float2 f64_split(double d) { return f64_split_pow2(d, 0); }
-
-// 2^e as a double, for -1022 <= e <= 1023
-__device__ __forceinline__ double pow2_f64(int e) { return __hiloint2double((e + 1023) << 20, 0); }
-
-// floor(log2(sqrt(v))) for a positive normal v, from its exponent field (0 for others): the
-// scale 2^k that brings the components of a vector with squared norm v near 1
-__device__ __forceinline__ int half_exponent(double v) {
-  const int E = (__double2hiint(v) >> 20) & 0x7FF;
-  return (E == 0 || E == 2047) ? 0 : (E - 1023) >> 1;
 }
 
 // (s, c) += (th + tl) * (xh + xl): s the running leading sum, c the low-order accumulator

@@ -426,9 +426,9 @@ void launch_b_pcg_reset(const BInst* B, int n, double rtol2, int maxit, cudaStre
 void launch_b_zero_pcg(const BInst* B, const int2* vmap, int nvb, cudaStream_t s);
 void launch_b_pcg_init(const BInst* B, const int2* vmap, int nvb, int b_role, cudaStream_t s);
 void launch_b_fused_pq(const BInst* B, const int2* vmap, int nvb, int ypad, bool pairs, cudaStream_t s);
-void launch_b_xr_update(const BInst* B, const int2* vmap, int nvb, bool pairs, cudaStream_t s);
+void launch_b_xr_update(const BInst* B, const int2* vmap, int nvb, cudaStream_t s);
 void launch_b_prolong(const BInst* B, const int2* vmap, int nvb, int mode, bool arith, bool upd, cudaStream_t s);
-void launch_b_pack_xr(const BInst* B, const int2* vmap, int nvb, int precision, bool pairs, cudaStream_t s);
+void launch_b_pack_xr(const BInst* B, const int2* vmap, int nvb, int precision, cudaStream_t s);
 void launch_b_stencil(const BInst* B, const int2* vmap, int nvb, int mass, int x_role, int y_role, cudaStream_t s);
 void launch_b_stencil_dot(const BInst* B, const int2* vmap, int nvb, int x_role, int y_role, cudaStream_t s);
 void launch_b_outer_normalize(const BInst* B, const int2* vmap, int nvb, int w_role, int mw_role, int x_role,

@@ -438,11 +438,10 @@ __device__ __forceinline__ void pack_body(Geo g, const Sub* __restrict__ subs, c
 // operands).  Block s forms r_new = r - alpha q over its subdomain's run of the padded vector
 // (the FMA of the separate x/r update), rounds r_new into its packed row and the coarse
 // right-hand side, and on the node columns it owns -- a with min(a / n, L - 1) = s, so each
-// column once -- updates x += alpha p and adds r_new^2 to (r, r) (float pairs: as in the x/r
-// update).  r itself is written by the prolong-sum that follows (each node once, the same
+// column once -- updates x += alpha p and adds r_new^2 to (r, r) (FP64).  r itself is written by the prolong-sum that follows (each node once, the same
 // FMA), because the neighbouring blocks still read the old r of the columns they share.  The
 // last block to finish takes the stop test.
-template <typename T, bool PAIRS>
+template <typename T>
 __device__ __forceinline__ void pack_xr_body(VBlk vb, Geo g, const Sub* __restrict__ subs,
                                              const int* __restrict__ slot_of, const double* __restrict__ r,
                                              const double* __restrict__ q, double* __restrict__ x, double* pb0,
@@ -461,8 +460,6 @@ __device__ __forceinline__ void pack_xr_body(VBlk vb, Geo g, const Sub* __restri
   const long long g0 = (long long)sb.lo1 * Y;
   const int own_lo = max(1, s * g.n), own_hi = (s == g.L - 1) ? g.nxi : (s + 1) * g.n - 1;
   const int e_lo = (own_lo - sb.lo1) * Y / 2, e_hi = (own_hi + 1 - sb.lo1) * Y / 2;
-  const int k = PAIRS ? half_exponent(st->rr) : 0;
-  float hs = 0.0f, ls = 0.0f;
   double rr[1] = {0.0}, acc[1] = {0.0};
   for (int e = threadIdx.x; e < npair; e += blockDim.x) {
     const int kp = 2 * e;
@@ -477,14 +474,8 @@ __device__ __forceinline__ void pack_xr_body(VBlk vb, Geo g, const Sub* __restri
       xv.x = fma(alpha, pv.x, xv.x);
       xv.y = fma(alpha, pv.y, xv.y);
       *reinterpret_cast<double2*>(x + gi) = xv;
-      if (PAIRS) {
-        const float2 a = f64_split_pow2(rv.x, k), b = f64_split_pow2(rv.y, k);
-        pair_fma(a.x, a.y, a.x, a.y, hs, ls);
-        pair_fma(b.x, b.y, b.x, b.y, hs, ls);
-      } else {
-        rr[0] = fma(rv.x, rv.x, rr[0]);
-        rr[0] = fma(rv.y, rv.y, rr[0]);
-      }
+      rr[0] = fma(rv.x, rv.x, rr[0]);
+      rr[0] = fma(rv.y, rv.y, rr[0]);
     }
     const double2 w = *reinterpret_cast<const double2*>(wt + kp);
     acc[0] = fma(w.x, rv.x, acc[0]);
@@ -496,7 +487,6 @@ __device__ __forceinline__ void pack_xr_body(VBlk vb, Geo g, const Sub* __restri
     block_sum<1>(acc);
     if (threadIdx.x == 0) c0[s] = acc[0];
   }
-  if (PAIRS) rr[0] = (f32_to_f64(hs) + f32_to_f64(ls)) * pow2_f64(2 * k);
   double tot[1];
   if (grid_sum_last<1>(rr, partials, counter, tot, vb) && threadIdx.x == 0) {
     const double rrv = tot[0];
@@ -514,22 +504,22 @@ __device__ __forceinline__ void pack_xr_body(VBlk vb, Geo g, const Sub* __restri
   }
 }
 
-template <typename T, bool PAIRS>
+template <typename T>
 __global__ void __launch_bounds__(128, 16) k_pack_xr(Geo g, const Sub* __restrict__ subs, const int* __restrict__ slot_of,
                                                  const double* __restrict__ r, const double* __restrict__ q,
                                                  double* __restrict__ x, double* pb0, double* pb1, int kpad,
                                                  T* __restrict__ out, const double* __restrict__ wT, double* c0,
                                                  PcgState* st, double* partials, unsigned* counter) {
   pdl_enter();
-  pack_xr_body<T, PAIRS>(vblk_self(), g, subs, slot_of, r, q, x, pb0, pb1, kpad, out, wT, c0, st, partials, counter);
+  pack_xr_body<T>(vblk_self(), g, subs, slot_of, r, q, x, pb0, pb1, kpad, out, wT, c0, st, partials, counter);
 }
 
-template <typename T, bool PAIRS>
+template <typename T>
 __global__ void __launch_bounds__(128, 16) kb_pack_xr(const BInst* __restrict__ B, const int2* __restrict__ vmap) {
   const int2 m = vmap[blockIdx.x];
   const BInst& I = B[m.x];
   if (!I.active) return;
-  pack_xr_body<T, PAIRS>(VBlk{m.y, I.nsub}, I.g, I.subs, I.slot_of_sub, I.r, I.q, I.x, I.pb0, I.pb1, I.kpad,
+  pack_xr_body<T>(VBlk{m.y, I.nsub}, I.g, I.subs, I.slot_of_sub, I.r, I.q, I.x, I.pb0, I.pb1, I.kpad,
                          reinterpret_cast<T*>(I.Rpack), I.wT, I.coarse ? I.c0 : nullptr, I.st, I.red,
                          I.cnt + CNT_RR);
 }
@@ -795,16 +785,14 @@ void launch_pack_xr(dd_ctx* c, cudaStream_t s) {
   const Geo& g = c->g;
   const bool pdl = c->pdl != 0;
   double* c0 = c->grid.coarse ? c->c0 : nullptr;
-#define DD_PACK_XR(T, PR)                                                                                       \
-  launch_chain(k_pack_xr<T, PR>, dim3(g.nsub), dim3(kPackThreads), 0, s, pdl, g, (const Sub*)c->subs,             \
+#define DD_PACK_XR(T)                                                                                           \
+  launch_chain(k_pack_xr<T>, dim3(g.nsub), dim3(kPackThreads), 0, s, pdl, g, (const Sub*)c->subs,             \
                (const int*)c->slot_of_sub, (const double*)c->r, (const double*)c->q, c->x, c->pb[0], c->pb[1],   \
                c->kpad, (T*)c->Rpack, (const double*)c->wT, c0, c->st, c->red, c->cnt + CNT_RR)
   if (c->grid.precision == DD_PREC_BF16) {
-    if (c->pq_pairs) DD_PACK_XR(__nv_bfloat16, true);
-    else DD_PACK_XR(__nv_bfloat16, false);
+    DD_PACK_XR(__nv_bfloat16);
   } else if (c->grid.precision == DD_PREC_TF32) {
-    if (c->pq_pairs) DD_PACK_XR(float, true);
-    else DD_PACK_XR(float, false);
+    DD_PACK_XR(float);
   } else {
     throw Error(DD_EUNSUPPORTED, "the fused x/r update and packing takes BF16 or TF32 operands");
   }
@@ -823,13 +811,11 @@ void gemm_free(dd_ctx* c) {
   c->tmapA = nullptr;
 }
 
-void launch_b_pack_xr(const BInst* B, const int2* vmap, int nvb, int precision, bool pairs, cudaStream_t s) {
+void launch_b_pack_xr(const BInst* B, const int2* vmap, int nvb, int precision, cudaStream_t s) {
   if (precision == DD_PREC_BF16) {
-    if (pairs) (kb_pack_xr<__nv_bfloat16, true><<<nvb, kPackThreads, 0, s>>>(B, vmap), dd::note_launch());
-    else (kb_pack_xr<__nv_bfloat16, false><<<nvb, kPackThreads, 0, s>>>(B, vmap), dd::note_launch());
+    (kb_pack_xr<__nv_bfloat16><<<nvb, kPackThreads, 0, s>>>(B, vmap), dd::note_launch());
   } else if (precision == DD_PREC_TF32) {
-    if (pairs) (kb_pack_xr<float, true><<<nvb, kPackThreads, 0, s>>>(B, vmap), dd::note_launch());
-    else (kb_pack_xr<float, false><<<nvb, kPackThreads, 0, s>>>(B, vmap), dd::note_launch());
+    (kb_pack_xr<float><<<nvb, kPackThreads, 0, s>>>(B, vmap), dd::note_launch());
   } else {
     throw Error(DD_EUNSUPPORTED, "batched packing supports BF16 and TF32 operands");
   }

@@ -936,7 +936,6 @@ void launch_matvec_pq_pairs(dd_ctx* c, cudaStream_t s) {
 }
 
 // x += alpha p, r -= alpha q, rr = (r, r); stop test ||r|| <= rtol ||r0|| (Sec. 4.1).
-template <bool PAIRS>
 __device__ __forceinline__ void xr_update_body(VBlk vb, long long n, double* pb0, double* pb1,
                                                         const double* __restrict__ q, double* __restrict__ x,
                                                         double* __restrict__ r, PcgState* st,
@@ -949,48 +948,17 @@ __device__ __forceinline__ void xr_update_body(VBlk vb, long long n, double* pb0
   double2* x2 = reinterpret_cast<double2*>(x);
   double2* r2 = reinterpret_cast<double2*>(r);
   double acc[1] = {0.0};
-  if (PAIRS) {
-    // (r, r) in float pairs on r 2^-k, 2^k ~ sqrt of the previous (r, r): each thread's sum
-    // hi + lo (error ~2^-46 of it) is scaled back by 2^2k and enters the FP64 reduction
-    // Two grid-stride steps per pass, their eight loads issued together (the elements, and
-    // the order of their partial sums, are those of one step per pass).
-    const int k = half_exponent(st->rr);
-    float hs = 0.0f, ls = 0.0f;
-    const long long stride = (long long)vb.nb * blockDim.x, n2 = n / 2;
-    for (long long t = (long long)vb.b * blockDim.x + threadIdx.x; t < n2; t += 2 * stride) {
-      const bool two = t + stride < n2;
-      const long long u = two ? t + stride : t;
-      double2 pv[2] = {__ldg(p2 + t), __ldg(p2 + u)}, qv[2] = {__ldg(q2 + t), __ldg(q2 + u)};
-      double2 xv[2] = {x2[t], x2[u]}, rv[2] = {r2[t], r2[u]};
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        if (j == 1 && !two) break;
-        const long long tj = j ? u : t;
-        xv[j].x = fma(alpha, pv[j].x, xv[j].x);
-        xv[j].y = fma(alpha, pv[j].y, xv[j].y);
-        rv[j].x = fma(-alpha, qv[j].x, rv[j].x);
-        rv[j].y = fma(-alpha, qv[j].y, rv[j].y);
-        x2[tj] = xv[j];
-        r2[tj] = rv[j];
-        const float2 a = f64_split_pow2(rv[j].x, k), b = f64_split_pow2(rv[j].y, k);
-        pair_fma(a.x, a.y, a.x, a.y, hs, ls);
-        pair_fma(b.x, b.y, b.x, b.y, hs, ls);
-      }
-    }
-    acc[0] = (f32_to_f64(hs) + f32_to_f64(ls)) * pow2_f64(2 * k);
-  } else {
-    for (long long t = (long long)vb.b * blockDim.x + threadIdx.x; t < n / 2;
-         t += (long long)vb.nb * blockDim.x) {
-      double2 pv = p2[t], qv = q2[t], xv = x2[t], rv = r2[t];
-      xv.x = fma(alpha, pv.x, xv.x);
-      xv.y = fma(alpha, pv.y, xv.y);
-      rv.x = fma(-alpha, qv.x, rv.x);
-      rv.y = fma(-alpha, qv.y, rv.y);
-      x2[t] = xv;
-      r2[t] = rv;
-      acc[0] = fma(rv.x, rv.x, acc[0]);
-      acc[0] = fma(rv.y, rv.y, acc[0]);
-    }
+  for (long long t = (long long)vb.b * blockDim.x + threadIdx.x; t < n / 2;
+       t += (long long)vb.nb * blockDim.x) {
+    double2 pv = p2[t], qv = q2[t], xv = x2[t], rv = r2[t];
+    xv.x = fma(alpha, pv.x, xv.x);
+    xv.y = fma(alpha, pv.y, xv.y);
+    rv.x = fma(-alpha, qv.x, rv.x);
+    rv.y = fma(-alpha, qv.y, rv.y);
+    x2[t] = xv;
+    r2[t] = rv;
+    acc[0] = fma(rv.x, rv.x, acc[0]);
+    acc[0] = fma(rv.y, rv.y, acc[0]);
   }
   double tot[1];
   if (grid_sum_last<1>(acc, partials, counter, tot, vb) && threadIdx.x == 0) {
@@ -1009,26 +977,22 @@ __device__ __forceinline__ void xr_update_body(VBlk vb, long long n, double* pb0
   }
 }
 
-template <bool PAIRS>
 __global__ void __launch_bounds__(kThreads) k_xr_update(long long n, double* pb0, double* pb1,
                                                         const double* __restrict__ q, double* __restrict__ x,
                                                         double* __restrict__ r, PcgState* st,
                                                         double* partials, unsigned* counter) {
   pdl_enter();
-  xr_update_body<PAIRS>(vblk_self(), n, pb0, pb1, q, x, r, st, partials, counter);
+  xr_update_body(vblk_self(), n, pb0, pb1, q, x, r, st, partials, counter);
 }
 
-// The FP64 form takes 64 registers, so 4 blocks of 256 per SM are resident: one wave of
-// 608 blocks (22.5 us on the 2.03M-unknown L = 2048 box) instead of two of the default 1216
-// (25.5 us); the float-pair form, one wave of what the occupancy calculator allows.
-static int xr_blocks(const dd_ctx* c) {
-  return c->pq_pairs ? resident_grid(k_xr_update<true>, c->g.plen / 2, kThreads)
-                     : grid_blocks(c->g.plen / 2, kThreads, 4);
-}
+// The kernel takes 64 registers, so 4 blocks of 256 per SM are resident: one wave of 608
+// blocks (22.5 us on the 2.03M-unknown L = 2048 box) instead of two of the default 1216
+// (25.5 us).  (Two grid-stride steps per pass with their loads issued together took 26 us.)
+static int xr_blocks(const dd_ctx* c) { return grid_blocks(c->g.plen / 2, kThreads, 4); }
 
 void launch_xr_update(dd_ctx* c, cudaStream_t s) {
   const long long n = c->g.plen;
-  launch_chain(c->pq_pairs ? k_xr_update<true> : k_xr_update<false>, dim3(xr_blocks(c)), dim3(kThreads), 0, s,
+  launch_chain(k_xr_update, dim3(xr_blocks(c)), dim3(kThreads), 0, s,
                c->pdl != 0, n, c->pb[0], c->pb[1], (const double*)c->q, c->x, c->r, c->st, c->red, c->cnt + CNT_RR);
   DD_CUDA(cudaGetLastError());
 }
@@ -1566,12 +1530,11 @@ __global__ void __launch_bounds__(kThreads, 6) kb_fused_pq(const BInst* __restri
     fused_pq_body<2>(VBlk{m.y, I.nb_fused}, I.g, I.tabS, I.z, I.pb0, I.pb1, I.q, I.st, I.red, I.cnt + CNT_PQ);
 }
 
-template <bool PAIRS>
 __global__ void __launch_bounds__(kThreads) kb_xr_update(const BInst* __restrict__ B, const int2* __restrict__ vmap) {
   const int2 m = vmap[blockIdx.x];
   const BInst& I = B[m.x];
   if (!I.active) return;
-  xr_update_body<PAIRS>(VBlk{m.y, I.nb_xr}, I.g.plen, I.pb0, I.pb1, I.q, I.x, I.r, I.st, I.red, I.cnt + CNT_RR);
+  xr_update_body(VBlk{m.y, I.nb_xr}, I.g.plen, I.pb0, I.pb1, I.q, I.x, I.r, I.st, I.red, I.cnt + CNT_RR);
 }
 
 template <bool ARITH, bool UPD>
@@ -1785,9 +1748,8 @@ void launch_b_fused_pq(const BInst* B, const int2* vmap, int nvb, int ypad, bool
   DD_CUDA(cudaGetLastError());
 }
 
-void launch_b_xr_update(const BInst* B, const int2* vmap, int nvb, bool pairs, cudaStream_t s) {
-  if (pairs) (kb_xr_update<true><<<nvb, kThreads, 0, s>>>(B, vmap), dd::note_launch());
-  else (kb_xr_update<false><<<nvb, kThreads, 0, s>>>(B, vmap), dd::note_launch());
+void launch_b_xr_update(const BInst* B, const int2* vmap, int nvb, cudaStream_t s) {
+  (kb_xr_update<<<nvb, kThreads, 0, s>>>(B, vmap), dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 

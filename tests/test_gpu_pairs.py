@@ -1,16 +1,16 @@
 """Float pairs in the PCG iteration (DD_OPT_PAIRS = 1, the default with rounded local inverses):
-q = A_sigma p of the fused pass and the partial sums of (r, r) on the FP32 pipe, against the FP64
-form of the same iteration.
+the matvec q = A_sigma p on the FP32 pipe (the fused p = 1 pass, the p = 2 pass), against the
+FP64 form of the same iteration; every dot product stays FP64.
 
-The pair arithmetic changes only the inner solve (its operator by about 2^-47 times the sum of
-the taps' magnitudes, (r, r) by about 2^-46 of each thread's partial); the outer
+The pair arithmetic changes only the inner solve's operator (by about 2^-47 times the sum of
+the taps' magnitudes); the outer
 iteration's residuals and Rayleigh quotients stay FP64.  So both forms must reach the stop
 rule's eta <= 1e-8 measured in FP64 by the oracle's matrices, the same eigenvalue (well inside
 the 1e-10 target), and the oracle's exact eigenvalue, with inner iteration counts that differ
 by at most a few.  A right-hand side scaled by 2^-40 or 2^40 gives the same iteration count and
-the scaled solution, bit for bit (the operands of (r, r) are scaled by a power of two that
-follows (r, r); the BF16 local solves keep the float exponent range, which bounds the scales a
-mixed solve can take)."""
+the scaled solution, bit for bit (the splits of the coefficients and of p are exact under a
+power-of-two scaling; the BF16 local solves keep the float exponent range, which bounds the
+scales a mixed solve can take)."""
 import numpy as np
 import pytest
 
