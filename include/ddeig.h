@@ -335,7 +335,8 @@ int dd_apply_preconditioner(dd_ctx* ctx, const double* r, double* z);
 int dd_coarse_matrix(dd_ctx* ctx, double* A0_host);
 
 /* Options of the iteration engine (defaults in brackets):
- *   DD_OPT_CHECK_EVERY  iterations between host convergence checks [8]
+ *   DD_OPT_CHECK_EVERY  iterations between host convergence checks (iterations after the stop
+ *                       return at once) [16]
  *   DD_OPT_USE_GRAPH    replay the PCG iteration as a CUDA graph [1]
  *   DD_OPT_FLEXIBLE     -1 automatic (flexible iff rounded local inverses) / 0 / 1 [-1]
  *   DD_OPT_TIMING       1: time every kernel class with CUDA events (eager launches) [0]

@@ -156,7 +156,7 @@ struct dd_ctx {
   std::vector<void*> allocs;
 
   // options
-  int check_every = 8;
+  int check_every = 16;             // PCG iterations per graph replay between host checks
   int use_graph = 1;
   int flexible_opt = -1;
   int timing = 0;
