@@ -739,11 +739,24 @@ int gemm_setup(dd_ctx* c) {
   for (int i = 0; i < 3; ++i) {
     const int bn = kTileN[i];
     make_tmap(&plan->tB[i], c->Rpack, es, kpad, g.nsub, BK, bn);
+    // Tiles in launch order.  Grids of several waves go band by band (per type, one 128-row
+    // band of A_T^{-1} with all its column tiles), so that the CTAs in flight share a few bands
+    // in L2 instead of each wave streaming the whole inverse again (L = 64, h = 1/16: 274 ->
+    // 264 us per launch); a single wave keeps the column tiles outermost (L = 2048, h = 1/32:
+    // 16.1 against 17.0 us band by band).
+    long long total = 0;
+    for (int t = 0; t < c->ntypes; ++t) total += (long long)mt * ((c->type_count[t] + bn - 1) / bn);
+    const bool bands = total > 2 * 152;
     std::vector<Tile> tl;
     for (int t = 0; t < c->ntypes; ++t) {
       const int first = c->type_first[t], cnt = c->type_count[t];
-      for (int n0 = 0; n0 < cnt; n0 += bn)
-        for (int m = 0; m < mt; ++m) tl.push_back(Tile{t, m * 128, first + n0, first + cnt});
+      if (bands) {
+        for (int m = 0; m < mt; ++m)
+          for (int n0 = 0; n0 < cnt; n0 += bn) tl.push_back(Tile{t, m * 128, first + n0, first + cnt});
+      } else {
+        for (int n0 = 0; n0 < cnt; n0 += bn)
+          for (int m = 0; m < mt; ++m) tl.push_back(Tile{t, m * 128, first + n0, first + cnt});
+      }
     }
     if (!plan->tiles[i] || plan->cap[i] < (int)tl.size()) {
       plan->tiles[i] = (Tile*)dev_alloc(c, sizeof(Tile) * tl.size());
