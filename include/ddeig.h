@@ -326,6 +326,19 @@ int dd_query(const dd_ctx* ctx, dd_info* info);
 /* y = op x over the box (x, y host or device, ndof doubles). */
 int dd_apply_operator(dd_ctx* ctx, int op, const double* x, double* y);
 
+/* y = A_sigma x evaluated by the float-pair pass of the PCG iteration (DD_OPT_PAIRS: each
+ * coefficient and x value split into two floats, error-free products and sums on the FP32
+ * pipe, y = hi + lo in FP64), whatever DD_OPT_PAIRS is set to: p = 1 the fused p-update pass
+ * with beta = 0, p = 2 the split p update and the (tiled, where DD_OPT_TILED3 and the box
+ * allow) pair matvec.  It exposes that arithmetic for checking against dd_apply_operator
+ * (DD_OP_ASIGMA).  Per node, |y_pairs - y| relative to the sum of |a_ij x_j| over the row: the
+ * splits and the dropped lo * lo product leave 2.5 * 2^-47 of each term; the FP32 roundings of
+ * the low-order accumulator add an amount that grows with the number of taps.  Largest ratios
+ * measured: 8.5 * 2^-47 with the 9 taps of p = 1, 13.4 * 2^-47 with the 27 of p = 2 (tested
+ * against 2^-42).  x, y host or device, ndof doubles; needs dd_cell_eigenpair; DD_EINVAL for
+ * null pointers or a p = 1 box with more than 256 padded rows (Ypad). */
+int dd_apply_asigma_pairs(dd_ctx* ctx, const double* x, double* y);
+
 /* z = M_AS2^{-1} r (or M_AS1^{-1} r), Sec. 3.1 (r, z host or device, ndof doubles);
  * needs dd_coarse_build. */
 int dd_apply_preconditioner(dd_ctx* ctx, const double* r, double* z);
@@ -368,8 +381,9 @@ int dd_coarse_matrix(dd_ctx* ctx, double* A0_host);
  *   DD_OPT_PAIRS        the matvec q = A_sigma p of the PCG iteration in float pairs on the FP32
  *                       pipe: each coefficient and p value split into hi + lo (48 significand
  *                       bits), error-free products and sums, q = hi + lo in FP64; q agrees with
- *                       the FP64 stencil to about 2^-47 times the sum of the taps' magnitudes (the
- *                       FP64 one: 2^-53).  p = 1: inside the fused p update pass; p = 2: the p
+ *                       the FP64 stencil to within 2^-42 times the sum of the taps' magnitudes
+ *                       (measured up to 13.4 * 2^-47; the FP64 one: about 2^-53; see
+ *                       dd_apply_asigma_pairs).  p = 1: inside the fused p update pass; p = 2: the p
  *                       update also stores p split.  p, q, x, r, z and their updates, every dot
  *                       product, the coarse solve, the outer iteration's residuals and Rayleigh
  *                       quotients, the stop rules and dd_apply_operator stay FP64.  0: the FP64

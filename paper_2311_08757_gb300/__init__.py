@@ -80,6 +80,7 @@ _SIGS = {
     "dd_last_error": (c_char_p, [c_void_p]),
     "dd_query": (c_int, [c_void_p, POINTER(dd_info)]),
     "dd_apply_operator": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    "dd_apply_asigma_pairs": (c_int, [c_void_p, c_void_p, c_void_p]),
     "dd_apply_preconditioner": (c_int, [c_void_p, c_void_p, c_void_p]),
     "dd_coarse_matrix": (c_int, [c_void_p, c_void_p]),
     "dd_set_option": (c_int, [c_void_p, c_int, c_int]),
@@ -256,6 +257,11 @@ def dd_query(ctx) -> dict:
 
 def dd_apply_operator(ctx, op: int, x, y) -> None:
     _check(lib().dd_apply_operator(ctx, op, _ptr(x), _ptr(y)), ctx)
+
+
+def dd_apply_asigma_pairs(ctx, x, y) -> None:
+    """y = A_sigma x by the float-pair pass of the PCG iteration (see the header)."""
+    _check(lib().dd_apply_asigma_pairs(ctx, _ptr(x), _ptr(y)), ctx)
 
 
 def dd_apply_preconditioner(ctx, r, z) -> None:

@@ -859,6 +859,41 @@ int dd_apply_operator(dd_ctx* c, int op, const double* x, double* y) {
   });
 }
 
+int dd_apply_asigma_pairs(dd_ctx* c, const double* x, double* y) {
+  if (!x || !y) return fail(c, DD_EINVAL, "null pointer");
+  int rc = stage_err(c, 2);
+  if (rc) return rc;
+  if (!pairs_possible(c)) return fail(c, DD_EINVAL, "float pairs need at most 256 padded rows for p = 1");
+  return guarded(c, [&]() -> int {
+    enter(c);
+    reset_graph(c);   // the iteration's scalars and vectors are reused here
+    // p = z + beta p_{-1} with beta = 0 and p_{-1} = 0: p = x
+    PcgState init;
+    std::memset(&init, 0, sizeof(init));
+    init.rho = 1.0;
+    DD_CUDA(cudaMemcpyAsync(c->st, &init, sizeof(init), cudaMemcpyHostToDevice, c->stream));
+    DD_CUDA(cudaMemsetAsync(c->pb[0], 0, sizeof(double) * c->g.plen, c->stream));
+    load_vec(c, x, c->z);
+    const int keep = c->pq_pairs;
+    c->pq_pairs = 1;
+    try {
+      if (c->g.p == 1) {
+        launch_fused_pq(c, c->stream);
+      } else {
+        launch_pupdate_pairs(c, c->stream);
+        launch_matvec_pq_pairs(c, c->stream);
+      }
+    } catch (...) {
+      c->pq_pairs = keep;
+      throw;
+    }
+    c->pq_pairs = keep;
+    store_vec(c, c->q, y);
+    DD_CUDA(cudaStreamSynchronize(c->stream));
+    return DD_OK;
+  });
+}
+
 int dd_apply_preconditioner(dd_ctx* c, const double* r, double* z) {
   if (!r || !z) return fail(c, DD_EINVAL, "null pointer");
   int rc = stage_err(c, 3);

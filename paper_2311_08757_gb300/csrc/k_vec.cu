@@ -532,8 +532,8 @@ __device__ __forceinline__ void fused_pq_body(VBlk vb, Geo g, const double* __re
 // value is also split into (hi, lo) (integer operations), the 9 taps accumulate with the
 // error-free product and sum (pair_fma) against the split table, and q = hi + lo in FP64.
 // p_k, the (p, q) partial and everything else stay FP64; q differs from the FP64 stencil by
-// about 2^-47 times the sum of the taps' magnitudes.  Three FP64 instructions per node (p
-// update, q = hi + lo, the partial) instead of eleven.  The split table is class-major (a
+// up to 8.5 * 2^-47 (measured) times the sum of the taps' magnitudes.  Three FP64
+// instructions per node (p update, q = hi + lo, the partial) instead of eleven.  The split table is class-major (a
 // class's taps are five 16-byte loads), p_k is written back from the staging loop, and each
 // thread evaluates two nodes (e, e + blockDim) per pass with their chains interleaved.
 __device__ __forceinline__ void pair_taps(const float2* __restrict__ tab2, int cls, const float2* x, int Y,

@@ -92,6 +92,15 @@ def test_options_need_a_context():
     assert dd.lib().dd_set_option(None, dd.DD_OPT_CHECK_EVERY, 8) == dd.DD_EINVAL
 
 
+def test_operator_entry_points_need_a_context_and_buffers():
+    L = dd.lib()
+    buf = (ctypes.c_double * 4)()
+    out = (ctypes.c_double * 4)()
+    assert L.dd_apply_asigma_pairs(None, buf, out) == dd.DD_EINVAL
+    assert L.dd_apply_asigma_pairs(None, None, out) == dd.DD_EINVAL
+    assert L.dd_apply_operator(None, dd.DD_OP_ASIGMA, buf, out) == dd.DD_EINVAL
+
+
 def test_self_test_entry_points_check_arguments_first():
     L = dd.lib()
     buf = (ctypes.c_double * 4)()

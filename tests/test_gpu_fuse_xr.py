@@ -1,5 +1,5 @@
 """The x, r update of a p = 1 PCG iteration fused into the restriction packing
-(DD_OPT_FUSE_XR, on by default with BF16/TF32 local inverses).
+(DD_OPT_FUSE_XR, opt-in, with BF16/TF32 local inverses).
 
 Each subdomain's block forms r - alpha q with the same FMA as the separate x/r update, the
 owner of each node column updates x and adds to (r, r), and the prolong-sum stores r - alpha q.
