@@ -321,7 +321,7 @@ TRAFFIC = {
     "stencil_Asigma": (33.67 + 0.463) * 1e6,
     "xr_update": (67.13 + 0.588) * 1e6,
     "pack_restrict": (16.87 + 0.000) * 1e6,
-    "local_gemm_tc": (15.10 + 0.000) * 1e6,
+    "local_gemm_tc": (15.103 + 0.000) * 1e6,
     "prolong_sum": (45.93 + 0.147) * 1e6,
     "local_solve_fp64": (18.789 + 0.022) * 1e6,
 }

@@ -242,7 +242,8 @@ constexpr int ERR_CR_WAIT = 1 << 7;   // error-word bit: the coefficient copy di
 __device__ __forceinline__ void cr_solve_body(const double* __restrict__ cr, int N, int m, int C2, int W2,
                                               const double* __restrict__ rhs, double* __restrict__ x,
                                               float* __restrict__ xf, const PcgState* st, int staged, int* err) {
-  if (st != nullptr && st->done) return;
+  // the converged flag is tested once the copies have landed, so that its load overlaps them
+  const int done = (st != nullptr) ? st->done : 0;
   extern __shared__ __align__(16) double sm_cr[];
   __shared__ __align__(8) unsigned long long cr_bar;
   __shared__ int cr_ok;
@@ -271,7 +272,7 @@ __device__ __forceinline__ void cr_solve_body(const double* __restrict__ cr, int
     cr_ok = 1;
   }
   __syncthreads();
-  if (!cr_ok) return;   // the error word tells the host
+  if (!cr_ok || done) return;   // the error word tells the host
   const double* alpha = src;
   const double* gamma = src + C2;
   const double* a = src + 2 * (size_t)C2;

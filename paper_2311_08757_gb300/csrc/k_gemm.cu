@@ -7,10 +7,10 @@
 // with Ainv_T rounded to BF16 or TF32 and FP32 accumulation.  The rounding makes the
 // preconditioner inexact; the outer Krylov method is then flexible CG.
 //
-// Kernel: one CTA per 128 x 256 output tile; warp 0 lane 0 issues TMA loads into a
-// 4-stage ring of 128B-swizzled shared-memory tiles, warp 1 lane 0 issues tcgen05.mma
-// with the accumulator in tensor memory, all four warps read it back with tcgen05.ld and
-// store Y (FP32).  Every mbarrier wait is bounded; on expiry the CTA records an error in a
+// Kernel: one CTA per 128 x BN output tile; warp 0 lane 0 issues TMA loads into a ring of
+// 128B-swizzled shared-memory stages (one or two 128-byte swizzle atoms of K each), warp 1
+// lane 0 issues tcgen05.mma with the accumulator in tensor memory, all four warps read it
+// back with tcgen05.ld and store Y (FP32).  Every mbarrier wait is bounded; on expiry the CTA records an error in a
 // device word, stops issuing work and returns after freeing its tensor memory.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -37,16 +37,23 @@ struct Tile {
 template <typename T, int BN_ = 256>
 struct TcCfg {
   static constexpr int BM = 128, BN = BN_;
-  static constexpr int BK = 128 / (int)sizeof(T);   // one 128-byte swizzle row
+  static constexpr int BK = 128 / (int)sizeof(T);   // K of one 128-byte swizzle atom
   static constexpr int UK = 32 / (int)sizeof(T);    // K of one tcgen05.mma (32 bytes)
-  // 128 x 256 tiles: 4 stages (193 KB, one CTA per SM); 128 x 160: 4 stages (145 KB, one
-  // CTA per SM; 6 stages measured the same); 128 x 128 tiles: 3 stages (97 KB), so that two
-  // CTAs share an SM and one's epilogue overlaps the other's MMAs
-  static constexpr int STAGES = (BN_ == 128) ? 3 : 4;
+  // Swizzle atoms per stage and stages.  A stage costs a fixed round trip (full barrier,
+  // MMA issue, commit, empty barrier, TMA issue) of about 600 cycles whatever its size, more
+  // than the tensor time of one atom (about 460 cycles for 128 x 160 x 64), so the 128 x 160
+  // tile moves two atoms per stage in 3 stages (217 KB): its K loop at L = 2048, h = 1/32
+  // went from 6.3 to 5.0 us, the tensor floor of the tile shape.  128 x 256 tiles: one atom,
+  // 4 stages (193 KB); 128 x 128 tiles: one atom, 3 stages (97 KB), so that two CTAs share
+  // an SM and one's epilogue overlaps the other's MMAs.
+  static constexpr int ATOMS = (BN_ == 160) ? 2 : 1;
+  static constexpr int STAGES = (BN_ == 128 || BN_ == 160) ? 3 : 4;
   // TMEM is allocated in powers of two of at least 32 columns (one FP32 column per output column)
   static constexpr int TMEM_COLS = BN_ <= 32 ? 32 : (BN_ <= 64 ? 64 : (BN_ <= 128 ? 128 : 256));
-  static constexpr int A_BYTES = BM * 128;
-  static constexpr int B_BYTES = BN * 128;
+  static constexpr int A_ATOM = BM * 128;
+  static constexpr int B_ATOM = BN * 128;
+  static constexpr int A_BYTES = A_ATOM * ATOMS;
+  static constexpr int B_BYTES = B_ATOM * ATOMS;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
 };
@@ -115,16 +122,27 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+// 16 consecutive FP32 columns of this warp's 32 TMEM lanes; complete after tmem_ld_wait
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
         "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 constexpr int ERR_TMA_WAIT = 1 << 4, ERR_MMA_WAIT = 1 << 5, ERR_ACC_WAIT = 1 << 6;
+
+// The CTA's tile (16-byte aligned), loaded by a volatile instruction so that it is issued
+// before the converged-flag test rather than after it: the two L2 round trips overlap.
+__device__ __forceinline__ Tile load_tile(const Tile* p) {
+  Tile t;
+  asm volatile("ld.global.nc.v4.s32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(t.type), "=r"(t.m0), "=r"(t.n0), "=r"(t.nend)
+               : "l"(p));
+  return t;
+}
 
 template <typename T, int BN>
 __global__ void __launch_bounds__(128, 1)
@@ -135,6 +153,7 @@ __global__ void __launch_bounds__(128, 1)
   using C = TcCfg<T, BN>;
   constexpr int kTmemCols = C::TMEM_COLS;
   pdl_enter();
+  const Tile tl = load_tile(tiles + blockIdx.x);
   // a grouped launch over several problems' tiles gives each tile its problem's state
   if (tile_st != nullptr) st = tile_st[blockIdx.x];
   if (st != nullptr && st->done) return;
@@ -149,7 +168,6 @@ __global__ void __launch_bounds__(128, 1)
   // barriers: full[s] at bar + 8 s, empty[s] at bar + 64 + 8 s, accum at bar + 128, tmem slot at bar + 192
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_ptr + 192);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const Tile tl = tiles[blockIdx.x];
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
@@ -170,7 +188,8 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  const int nk = K / C::BK;
+  const int natoms = K / C::BK;
+  const int nk = (natoms + C::ATOMS - 1) / C::ATOMS;   // stages; the last may hold fewer atoms
   const int rowA = tl.type * rows_per_type + tl.m0;
 
   if (warp == 0 && lane == 0) {
@@ -178,10 +197,14 @@ __global__ void __launch_bounds__(128, 1)
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % C::STAGES;
       const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
+      const int na = min(C::ATOMS, natoms - kb * C::ATOMS);
       if (!mbar_wait(bar + 64 + 8 * s, ph ^ 1u, err, ERR_TMA_WAIT)) break;
-      mbar_expect_tx(bar + 8 * s, C::STAGE_BYTES);
-      tma_load_2d(sA0 + s * C::A_BYTES, &tmA, kb * C::BK, rowA, bar + 8 * s);
-      tma_load_2d(sB0 + s * C::B_BYTES, &tmB, kb * C::BK, tl.n0, bar + 8 * s);
+      mbar_expect_tx(bar + 8 * s, (uint32_t)(na * (C::A_ATOM + C::B_ATOM)));
+      for (int a = 0; a < na; ++a) {
+        const int k0 = (kb * C::ATOMS + a) * C::BK;
+        tma_load_2d(sA0 + s * C::A_BYTES + a * C::A_ATOM, &tmA, k0, rowA, bar + 8 * s);
+        tma_load_2d(sB0 + s * C::B_BYTES + a * C::B_ATOM, &tmB, k0, tl.n0, bar + 8 * s);
+      }
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
@@ -196,11 +219,14 @@ __global__ void __launch_bounds__(128, 1)
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int na = min(C::ATOMS, natoms - kb * C::ATOMS);
+      for (int a = 0; a < na; ++a) {
 #pragma unroll
-      for (int kk = 0; kk < C::BK / C::UK; ++kk) {
-        const uint64_t ad = sw128_desc(sA0 + s * C::A_BYTES + kk * 32);
-        const uint64_t bd = sw128_desc(sB0 + s * C::B_BYTES + kk * 32);
-        mma_issue<T>(tmem, ad, bd, idesc, (kb | kk) != 0 ? 1u : 0u);
+        for (int kk = 0; kk < C::BK / C::UK; ++kk) {
+          const uint64_t ad = sw128_desc(sA0 + s * C::A_BYTES + a * C::A_ATOM + kk * 32);
+          const uint64_t bd = sw128_desc(sB0 + s * C::B_BYTES + a * C::B_ATOM + kk * 32);
+          mma_issue<T>(tmem, ad, bd, idesc, (kb | a | kk) != 0 ? 1u : 0u);
+        }
       }
       mma_commit(bar + 64 + 8 * s);
     }
@@ -211,17 +237,22 @@ __global__ void __launch_bounds__(128, 1)
   const bool ready = mbar_wait(bar + 128, 0, err, ERR_ACC_WAIT);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ready) {
+    // 32 columns per wait (two loads in flight): 1.9 -> 1.6 us for the 128 x 160 tile
     const int m = tl.m0 + warp * 32 + lane;
-    for (int c0 = 0; c0 < C::BN; c0 += 16) {
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int c0 = 0; c0 < C::BN; c0 += 32) {
       if (tl.n0 + c0 >= tl.nend) break;
-      uint32_t r[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+      uint32_t r[32];
+      tmem_ld16(trow + (uint32_t)c0, r);
+      if (c0 + 16 < C::BN) tmem_ld16(trow + (uint32_t)(c0 + 16), r + 16);
+      tmem_ld_wait();
       if (m < mlimit) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
+        for (int j = 0; j < 32; ++j) {
           const int n = tl.n0 + c0 + j;
           // scaled operands (FP8): undo the row scales of A and B
-          if (n < tl.nend) Y[(size_t)n * ldy + m] = ysc != nullptr ? __uint_as_float(r[j]) * ysc[n] : __uint_as_float(r[j]);
+          if (c0 + j < C::BN && n < tl.nend)
+            Y[(size_t)n * ldy + m] = ysc != nullptr ? __uint_as_float(r[j]) * ysc[n] : __uint_as_float(r[j]);
         }
       }
     }
