@@ -253,13 +253,15 @@ def kernel_model(w, info, ntype_counts, nloc_by_type, band, precision):
         per_sweep = n * b - b * (b + 1) / 2
         fp64_band += c * 2 * 2 * per_sweep
     taps = 3 ** (w.p + 1)
+    # the p update also makes the previous iteration's x += alpha p (DD_OPT_X_LAG, the default):
+    # x read and written, one FMA
     if w.p == 1 and mixed:
         # fused p update + stencil + (p, q) with q = A_sigma p in float pairs (the default with
-        # rounded local inverses): FP64 p update, q = hi + lo and the (p, q) FMA (5 flops); per
-        # tap one error-free product and sum with the cross terms (15 FP32 flops)
-        stencil = (5.0 * ndof, 15.0 * taps * ndof, 0.0, 32.0 * ndof)
-    elif w.p == 1:   # fused p update + stencil + (p, q)
-        stencil = (2.0 * (taps + 2) * ndof, 0.0, 0.0, 32.0 * ndof)
+        # rounded local inverses): FP64 p update, x update, q = hi + lo and the (p, q) FMA
+        # (7 flops); per tap one error-free product and sum with the cross terms (15 FP32 flops)
+        stencil = (7.0 * ndof, 15.0 * taps * ndof, 0.0, 48.0 * ndof)
+    elif w.p == 1:   # fused p update + x update + stencil + (p, q)
+        stencil = (2.0 * (taps + 3) * ndof, 0.0, 0.0, 48.0 * ndof)
     elif mixed:
         # p = 2 in float pairs: the taps read the split p (8 B), the (p, q) FMA reads p (8 B),
         # q written (8 B); FP64: q = hi + lo and the (p, q) FMA (3 flops)
@@ -276,8 +278,9 @@ def kernel_model(w, info, ntype_counts, nloc_by_type, band, precision):
     return {
         "stencil_Asigma": stencil,
         # p = 2 in float pairs: the split p is written beside p
-        "p_update": (2.0 * ndof, 0.0, 0.0, (32.0 if (mixed and w.p == 2) else 24.0) * ndof),
-        "xr_update": (6.0 * ndof, 0.0, 0.0, 48.0 * ndof),
+        "p_update": (4.0 * ndof, 0.0, 0.0, (48.0 if (mixed and w.p == 2) else 40.0) * ndof),
+        # r -= alpha q and (r, r); x is updated by the next p update
+        "xr_update": (4.0 * ndof, 0.0, 0.0, 24.0 * ndof),
         "prolong_sum": prolong,
         "pack_restrict": (2.0 * f * ndof, 0.0, 0.0, (8.0 + es * f) * ndof),
         "local_gemm_tc": (0.0, 0.0, gemm_flops, (es * f + 4.0 * f) * ndof),
@@ -318,8 +321,8 @@ def roofline_entry(name, model, ms_total, nlaunch, peaks, peak_src, precision, a
 # at the L = 2048, h = 1/32 workload, from one ncu capture of each; a kernel changed since its
 # capture is left out.
 TRAFFIC = {
-    "stencil_Asigma": (33.67 + 0.463) * 1e6,
-    "xr_update": (67.13 + 0.588) * 1e6,
+    "stencil_Asigma": (50.447 + 1.114) * 1e6,   # an iteration k >= 1 pass (it also updates x)
+    "xr_update": (33.576 + 0.000) * 1e6,
     "pack_restrict": (16.87 + 0.000) * 1e6,
     "local_gemm_tc": (15.103 + 0.000) * 1e6,
     "prolong_sum": (45.93 + 0.147) * 1e6,

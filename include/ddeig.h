@@ -411,7 +411,12 @@ int dd_coarse_matrix(dd_ctx* ctx, double* A0_host);
  *                       shared memory (each block takes the planes of one residue a1 mod n, so
  *                       it stages the n Ypad classes of the split table once, and for every tile
  *                       the split p of three planes), where n Ypad <= 448; 0 reads the table and
- *                       p through the caches.  The same q; (p, q) summed in another order [1] */
+ *                       p through the caches.  The same q; (p, q) summed in another order [1]
+ *   DD_OPT_X_LAG        1: the PCG update x_{k+1} = x_k + alpha_k p_k is made by iteration k + 1's
+ *                       p update (which reads p_k anyway), and once more after the last
+ *                       iteration, so the x/r update streams only r and q; the same FMA on the
+ *                       same operands, so x is bit-identical to 0 (x updated with r).  Not
+ *                       with DD_OPT_FUSE_XR, whose fused update keeps x [1] */
 #define DD_OPT_CHECK_EVERY 0
 #define DD_OPT_USE_GRAPH   1
 #define DD_OPT_FLEXIBLE    2
@@ -428,6 +433,7 @@ int dd_coarse_matrix(dd_ctx* ctx, double* A0_host);
 #define DD_OPT_PDL         13
 #define DD_OPT_FUSE_XR     14
 #define DD_OPT_TILED3      15
+#define DD_OPT_X_LAG       16
 int dd_set_option(dd_ctx* ctx, int option, int value);
 
 /* Per-kernel-class timing collected while DD_OPT_TIMING = 1: for class k (0 <= k < count),

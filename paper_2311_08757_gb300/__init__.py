@@ -26,6 +26,7 @@ DD_OP_ASIGMA, DD_OP_MASS, DD_OP_A = 0, 1, 2
 DD_OPT_CHECK_EVERY, DD_OPT_USE_GRAPH, DD_OPT_FLEXIBLE, DD_OPT_TIMING, DD_OPT_LOCAL_RHS = 0, 1, 2, 3, 4
 DD_OPT_KRYLOV, DD_OPT_PRECOND, DD_OPT_RESTART, DD_OPT_GEMM_TILE_N, DD_OPT_COARSE_SOLVE = 5, 6, 7, 8, 9
 DD_OPT_FUSED_PQ, DD_OPT_PROLONG_TABLES, DD_OPT_PAIRS, DD_OPT_PDL, DD_OPT_FUSE_XR, DD_OPT_TILED3 = 10, 11, 12, 13, 14, 15
+DD_OPT_X_LAG = 16
 PRECISIONS = {"fp64": DD_PREC_FP64, "tf32": DD_PREC_TF32, "bf16": DD_PREC_BF16, "fp8": DD_PREC_FP8}
 DD_INNER_FIXED, DD_INNER_ADAPTIVE, DD_INNER_FUSED = 0, 1, 2
 INNER_MODES = {"fixed": DD_INNER_FIXED, "adaptive": DD_INNER_ADAPTIVE, "fused": DD_INNER_FUSED}

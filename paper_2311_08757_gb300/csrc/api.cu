@@ -439,6 +439,7 @@ int pcg_run(dd_ctx* c, const double* b, double rtol, int maxit, int* iters, doub
     if (c->timing) timer_collect(c);
     if (c->st_h->done) break;
   }
+  if (x_lag_target(c) != nullptr) TIMED(KC_MISC, s, launch_x_final(c, s));
   const PcgState& h = *c->st_h;
   if (iters) *iters = h.iter;
   if (relres) *relres = (h.rr0 > 0.0) ? std::sqrt(h.rr / h.rr0) : 0.0;
@@ -1382,6 +1383,10 @@ int dd_set_option(dd_ctx* c, int option, int value) {
     case DD_OPT_TILED3:
       if (value != 0 && value != 1) return fail(c, DD_EINVAL, "tiled p = 2 matvec must be 0 or 1");
       c->matvec_tiled = value;
+      break;
+    case DD_OPT_X_LAG:
+      if (value != 0 && value != 1) return fail(c, DD_EINVAL, "deferred x update must be 0 or 1");
+      c->x_lag = value;
       break;
     case DD_OPT_PDL:
       if (value != 0 && value != 1) return fail(c, DD_EINVAL, "programmatic dependent launch must be 0 or 1");

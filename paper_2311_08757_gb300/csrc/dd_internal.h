@@ -168,6 +168,9 @@ struct dd_ctx {
   int pdl = 0;                      // PCG chain kernels launched with programmatic dependent launch
   int fuse_xr_opt = 0;              // x/r update fused into the packing: 1 on, 0 or -1 off
   int matvec_tiled = 1;             // p = 2 float pairs: the shared-memory tiled matvec where it fits
+  // x_{k+1} = x_k + alpha_k p_k deferred to iteration k + 1's p update, which reads p_k anyway,
+  // and one final update after the last iteration: the x/r update then streams r and q only
+  int x_lag = 1;
   int fuse_xr = 0;                  // the resolved choice
   int pq_pairs_opt = -1;            // q = A_sigma p of the fused p = 1 kernel: -1 automatic, 0 FP64, 1 float pairs
   int pq_pairs = 0;                 // the resolved choice
@@ -285,6 +288,9 @@ struct dd_ctx {
   long long graph_kernels = 0;   // kernel nodes in one replay of the graph
 };
 
+// the x that the PCG p update advances (x_lag), or null when the x/r update does it
+inline double* x_lag_target(dd_ctx* c) { return (c->x_lag && !c->fuse_xr) ? c->x : nullptr; }
+
 namespace dd {
 
 // One problem of a batched launch: its geometry, the device buffers of its context, and the
@@ -358,7 +364,8 @@ void launch_matvec_pq(dd_ctx* c, cudaStream_t s);                   // q = A p, 
 void launch_pupdate_pairs(dd_ctx* c, cudaStream_t s);               // p = 2: p update, p also as float pairs
 void launch_matvec_pq_pairs(dd_ctx* c, cudaStream_t s);             // p = 2: q = A p in float pairs, pq, alpha
 void launch_fused_pq(dd_ctx* c, cudaStream_t s);                    // p = z + beta p; q = A p; pq (p = 1)
-void launch_xr_update(dd_ctx* c, cudaStream_t s);                   // x, r, rr, done
+void launch_xr_update(dd_ctx* c, cudaStream_t s);                   // x (unless x_lag), r, rr, done
+void launch_x_final(dd_ctx* c, cudaStream_t s);                      // x_lag: the last x += alpha p
 // z = ..., rz, beta; upd (iterations): r -= alpha q first, the x update having run in launch_pack_xr
 void launch_prolong(dd_ctx* c, int init, cudaStream_t s, double* zout = nullptr, bool upd = false);
 void launch_precond(dd_ctx* c, const double* r, double* z, int pcg_mode, cudaStream_t s);

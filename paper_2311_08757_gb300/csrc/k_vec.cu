@@ -408,17 +408,28 @@ void launch_pcg_init(dd_ctx* c, const double* b, cudaStream_t s) {
 // p_k = z + beta p_{k-1} (whole padded vector; boundary columns and pads stay zero); the
 // double buffer's index helpers p_prev / p_cur are in dd_common.cuh.
 
+// x (when not null): the previous iteration's x += alpha_{k-1} p_{k-1}, deferred to this
+// pass, which reads p_{k-1} anyway (see x_lag in dd_internal.h).
 __global__ void __launch_bounds__(kThreads) k_pupdate(long long n, const double* __restrict__ z, double* pb0,
-                                                      double* pb1, const PcgState* st) {
+                                                      double* pb1, double* __restrict__ x, const PcgState* st) {
   if (st->done) return;
   const double beta = st->beta;
   const int k = st->iter;
+  const double alpha = st->alpha;
+  const bool upx = x != nullptr && k > 0;
   const double2* z2 = reinterpret_cast<const double2*>(z);
   const double2* pp = reinterpret_cast<const double2*>(p_prev(pb0, pb1, k));
   double2* pc = reinterpret_cast<double2*>(p_cur(pb0, pb1, k));
+  double2* x2 = reinterpret_cast<double2*>(x);
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n / 2;
        t += (long long)gridDim.x * blockDim.x) {
     double2 a = z2[t], b = pp[t];
+    if (upx) {
+      double2 xv = x2[t];
+      xv.x = fma(alpha, b.x, xv.x);
+      xv.y = fma(alpha, b.y, xv.y);
+      x2[t] = xv;
+    }
     b.x = fma(beta, b.x, a.x);
     b.y = fma(beta, b.y, a.y);
     pc[t] = b;
@@ -427,7 +438,8 @@ __global__ void __launch_bounds__(kThreads) k_pupdate(long long n, const double*
 
 void launch_pupdate(dd_ctx* c, cudaStream_t s) {
   const long long n = c->g.plen;
-  (k_pupdate<<<grid_blocks(n / 2, kThreads), kThreads, 0, s>>>(n, c->z, c->pb[0], c->pb[1], c->st), dd::note_launch());
+  (k_pupdate<<<grid_blocks(n / 2, kThreads), kThreads, 0, s>>>(n, c->z, c->pb[0], c->pb[1], x_lag_target(c), c->st),
+   dd::note_launch());
   DD_CUDA(cudaGetLastError());
 }
 
@@ -443,13 +455,15 @@ constexpr int kFusedCols = 32;
 template <int U2>
 __device__ __forceinline__ void fused_pq_body(VBlk vb, Geo g, const double* __restrict__ tab,
                                               const double* __restrict__ z, double* pb0, double* pb1,
-                                              double* __restrict__ q, PcgState* st, double* partials,
-                                              unsigned* counter) {
+                                              double* __restrict__ q, double* __restrict__ x, PcgState* st,
+                                              double* partials, unsigned* counter) {
   if (st->done) return;
   extern __shared__ double sp_raw[];
   double* sp = sp_raw + 1;   // one zero guard element on each side
   const int k = st->iter;
   const double beta = st->beta;
+  const double alpha = st->alpha;   // alpha_{k-1}: this pass's last block overwrites it after all have read it
+  const bool upx = x != nullptr && k > 0;
   const double* __restrict__ pp = p_prev(pb0, pb1, k);
   double* __restrict__ pc = p_cur(pb0, pb1, k);
   const int Y = g.Ypad, yl = g.ylog;
@@ -465,10 +479,17 @@ __device__ __forceinline__ void fused_pq_body(VBlk vb, Geo g, const double* __re
     const int nload = (own + 2) << yl;
     const long long gbase = (long long)(a0 - 1) << yl;
     __syncthreads();
-    for (int e = threadIdx.x; e < nload; e += blockDim.x) sp[e] = fma(beta, pp[gbase + e], z[gbase + e]);
+    const int nown = own << yl;
+    for (int e = threadIdx.x; e < nload; e += blockDim.x) {
+      // x is loaded beside p_{k-1} and z (one memory round trip per pass), stored for own nodes
+      const bool mine = upx && e >= Y && e < Y + nown;
+      const double pv = pp[gbase + e], zv = z[gbase + e];
+      const double xv = mine ? x[gbase + e] : 0.0;
+      sp[e] = fma(beta, pv, zv);
+      if (mine) x[gbase + e] = fma(alpha, pv, xv);
+    }
     if (threadIdx.x == 0) sp[nload] = 0.0;   // corner tap of the last (pad) slot of a partial tile
     __syncthreads();
-    const int nown = own << yl;
     if (U2 == 1) {
       for (int e = threadIdx.x; e < nown; e += blockDim.x) {
         const int se = e + Y;
@@ -561,17 +582,19 @@ __device__ __forceinline__ void pair_taps(const float2* __restrict__ tab2, int c
 
 __device__ __forceinline__ void fused_pq_pairs_body(VBlk vb, Geo g, const float2* __restrict__ tab2,
                                                     const double* __restrict__ z, double* pb0, double* pb1,
-                                                    double* __restrict__ q, PcgState* st, double* partials,
-                                                    unsigned* counter) {
+                                                    double* __restrict__ q, double* __restrict__ x, PcgState* st,
+                                                    double* partials, unsigned* counter) {
   if (st->done) return;
   extern __shared__ double sp_raw[];
   const int Y = g.Ypad, yl = g.ylog;
+  const double alpha = st->alpha;   // alpha_{k-1}, read before this pass's last block replaces it
   const int nstage = (kFusedCols + 2) * Y + 2;
   float2* sp2_raw = reinterpret_cast<float2*>(sp_raw);
   float2* sp2 = sp2_raw + 1;   // one zero guard element on each side
   double* spd = sp_raw + nstage;   // the tile's own p values (FP64), for the partial
   const int k = st->iter;
   const double beta = st->beta;
+  const bool upx = x != nullptr && k > 0;
   const double* __restrict__ pp = p_prev(pb0, pb1, k);
   double* __restrict__ pc = p_cur(pb0, pb1, k);
   const int ntiles = (g.nxi + kFusedCols - 1) / kFusedCols;
@@ -589,11 +612,16 @@ __device__ __forceinline__ void fused_pq_pairs_body(VBlk vb, Geo g, const float2
     const long long gbase = (long long)(a0 - 1) << yl;
     __syncthreads();
     for (int e = threadIdx.x; e < nload; e += blockDim.x) {
-      const double pv = fma(beta, pp[gbase + e], z[gbase + e]);
+      // x is loaded beside p_{k-1} and z (one memory round trip per pass), stored for own nodes
+      const bool own_e = e >= Y && e < Y + nown;
+      const double pprev = pp[gbase + e], zv = z[gbase + e];
+      const double xv = (upx && own_e) ? x[gbase + e] : 0.0;
+      const double pv = fma(beta, pprev, zv);
       sp2[e] = f64_split(pv);
-      if (e >= Y && e < Y + nown) {
+      if (own_e) {
         pc[gbase + e] = pv;
         spd[e - Y] = pv;
+        if (upx) x[gbase + e] = fma(alpha, pprev, xv);
       }
     }
     if (threadIdx.x == 0) sp2[nload] = make_float2(0.0f, 0.0f);   // corner tap of the last pad slot
@@ -639,10 +667,10 @@ __device__ __forceinline__ void fused_pq_pairs_body(VBlk vb, Geo g, const float2
 
 __global__ void __launch_bounds__(kThreads) k_fused_pq_pairs(Geo g, const float2* __restrict__ tab2,
                                                              const double* __restrict__ z, double* pb0, double* pb1,
-                                                             double* __restrict__ q, PcgState* st, double* partials,
-                                                             unsigned* counter) {
+                                                             double* __restrict__ q, double* __restrict__ x,
+                                                             PcgState* st, double* partials, unsigned* counter) {
   pdl_enter();
-  fused_pq_pairs_body(vblk_self(), g, tab2, z, pb0, pb1, q, st, partials, counter);
+  fused_pq_pairs_body(vblk_self(), g, tab2, z, pb0, pb1, q, x, st, partials, counter);
 }
 
 static size_t fused_pq_smem(int ypad, bool pairs) {
@@ -653,10 +681,10 @@ static size_t fused_pq_smem(int ypad, bool pairs) {
 template <int U2>
 __global__ void __launch_bounds__(kThreads) k_fused_pq(Geo g, const double* __restrict__ tab,
                                                        const double* __restrict__ z, double* pb0, double* pb1,
-                                                       double* __restrict__ q, PcgState* st, double* partials,
-                                                       unsigned* counter) {
+                                                       double* __restrict__ q, double* __restrict__ x, PcgState* st,
+                                                       double* partials, unsigned* counter) {
   pdl_enter();
-  fused_pq_body<U2>(vblk_self(), g, tab, z, pb0, pb1, q, st, partials, counter);
+  fused_pq_body<U2>(vblk_self(), g, tab, z, pb0, pb1, q, x, st, partials, counter);
 }
 
 void launch_fused_pq(dd_ctx* c, cudaStream_t s) {
@@ -673,14 +701,14 @@ void launch_fused_pq(dd_ctx* c, cudaStream_t s) {
   const bool pdl = c->pdl != 0;
   if (c->pq_pairs) {
     launch_chain(k_fused_pq_pairs, dim3(nb), dim3(kThreads), smem, s, pdl, g, (const float2*)c->tabS2,
-                 (const double*)c->z, c->pb[0], c->pb[1], c->q, c->st, c->red, c->cnt + CNT_PQ);
+                 (const double*)c->z, c->pb[0], c->pb[1], c->q, x_lag_target(c), c->st, c->red, c->cnt + CNT_PQ);
     return;
   }
   // two nodes per thread and pass by default: 53.0 against 53.8 us per launch on the
   // L = 2048, h = 1/32 box, the same bits
   launch_chain(c->fused_pq_opt != 1 ? k_fused_pq<2> : k_fused_pq<1>, dim3(nb), dim3(kThreads), smem, s, pdl, g,
-               (const double*)c->tabS, (const double*)c->z, c->pb[0], c->pb[1], c->q, c->st, c->red,
-               c->cnt + CNT_PQ);
+               (const double*)c->tabS, (const double*)c->z, c->pb[0], c->pb[1], c->q, x_lag_target(c), c->st,
+               c->red, c->cnt + CNT_PQ);
 }
 
 // x[0..n) = v (start vectors of the convenience entry points)
@@ -739,18 +767,28 @@ void launch_matvec_pq(dd_ctx* c, cudaStream_t s) {
 // p = 2 with float pairs: the p update also stores p split into (hi, lo) floats (integer
 // operations, as f64_split), so that the 27 taps of every node read split values.
 __global__ void __launch_bounds__(kThreads) k_pupdate_pairs(long long n, const double* __restrict__ z, double* pb0,
-                                                            double* pb1, float2* __restrict__ p2, const PcgState* st) {
+                                                            double* pb1, float2* __restrict__ p2,
+                                                            double* __restrict__ x, const PcgState* st) {
   pdl_enter();
   if (st->done) return;
   const double beta = st->beta;
   const int k = st->iter;
+  const double alpha = st->alpha;
+  const bool upx = x != nullptr && k > 0;
   const double2* z2 = reinterpret_cast<const double2*>(z);
   const double2* pp = reinterpret_cast<const double2*>(p_prev(pb0, pb1, k));
   double2* pc = reinterpret_cast<double2*>(p_cur(pb0, pb1, k));
+  double2* x2 = reinterpret_cast<double2*>(x);
   float4* ps = reinterpret_cast<float4*>(p2);
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n / 2;
        t += (long long)gridDim.x * blockDim.x) {
     double2 a = z2[t], b = pp[t];
+    if (upx) {
+      double2 xv = x2[t];
+      xv.x = fma(alpha, b.x, xv.x);
+      xv.y = fma(alpha, b.y, xv.y);
+      x2[t] = xv;
+    }
     b.x = fma(beta, b.x, a.x);
     b.y = fma(beta, b.y, a.y);
     pc[t] = b;
@@ -762,7 +800,7 @@ __global__ void __launch_bounds__(kThreads) k_pupdate_pairs(long long n, const d
 void launch_pupdate_pairs(dd_ctx* c, cudaStream_t s) {
   const long long n = c->g.plen;
   launch_chain(k_pupdate_pairs, dim3(grid_blocks(n / 2, kThreads)), dim3(kThreads), 0, s, c->pdl != 0, n,
-               (const double*)c->z, c->pb[0], c->pb[1], c->p2, (const PcgState*)c->st);
+               (const double*)c->z, c->pb[0], c->pb[1], c->p2, x_lag_target(c), (const PcgState*)c->st);
 }
 
 // p = 2: q = A_sigma p with the 27 taps in float pairs (split table, class-major, 14 aligned
@@ -935,7 +973,9 @@ void launch_matvec_pq_pairs(dd_ctx* c, cudaStream_t s) {
                c->red, c->cnt + CNT_PQ);
 }
 
-// x += alpha p, r -= alpha q, rr = (r, r); stop test ||r|| <= rtol ||r0|| (Sec. 4.1).
+// x += alpha p, r -= alpha q, rr = (r, r); stop test ||r|| <= rtol ||r0|| (Sec. 4.1).  UPX
+// false: x is left to the next iteration's p update (x_lag), so only r and q are read.
+template <bool UPX>
 __device__ __forceinline__ void xr_update_body(VBlk vb, long long n, double* pb0, double* pb1,
                                                         const double* __restrict__ q, double* __restrict__ x,
                                                         double* __restrict__ r, PcgState* st,
@@ -950,12 +990,15 @@ __device__ __forceinline__ void xr_update_body(VBlk vb, long long n, double* pb0
   double acc[1] = {0.0};
   for (long long t = (long long)vb.b * blockDim.x + threadIdx.x; t < n / 2;
        t += (long long)vb.nb * blockDim.x) {
-    double2 pv = p2[t], qv = q2[t], xv = x2[t], rv = r2[t];
-    xv.x = fma(alpha, pv.x, xv.x);
-    xv.y = fma(alpha, pv.y, xv.y);
+    double2 qv = q2[t], rv = r2[t];
+    if (UPX) {
+      double2 pv = p2[t], xv = x2[t];
+      xv.x = fma(alpha, pv.x, xv.x);
+      xv.y = fma(alpha, pv.y, xv.y);
+      x2[t] = xv;
+    }
     rv.x = fma(-alpha, qv.x, rv.x);
     rv.y = fma(-alpha, qv.y, rv.y);
-    x2[t] = xv;
     r2[t] = rv;
     acc[0] = fma(rv.x, rv.x, acc[0]);
     acc[0] = fma(rv.y, rv.y, acc[0]);
@@ -977,12 +1020,41 @@ __device__ __forceinline__ void xr_update_body(VBlk vb, long long n, double* pb0
   }
 }
 
+template <bool UPX>
 __global__ void __launch_bounds__(kThreads) k_xr_update(long long n, double* pb0, double* pb1,
                                                         const double* __restrict__ q, double* __restrict__ x,
                                                         double* __restrict__ r, PcgState* st,
                                                         double* partials, unsigned* counter) {
   pdl_enter();
-  xr_update_body(vblk_self(), n, pb0, pb1, q, x, r, st, partials, counter);
+  xr_update_body<UPX>(vblk_self(), n, pb0, pb1, q, x, r, st, partials, counter);
+}
+
+// After the last PCG iteration K: x += alpha_K p_K, the update the lagged scheme left for a
+// next p update that does not run.  Not after a failed (p, q) or a non-finite iterate.
+__global__ void __launch_bounds__(kThreads) k_x_final(long long n, const double* __restrict__ pb0,
+                                                      const double* __restrict__ pb1, double* __restrict__ x,
+                                                      const PcgState* st) {
+  if (st->status != 0 && st->status != DD_EMAXIT) return;
+  const double alpha = st->alpha;
+  // after iteration K the counter is K + 1, and p_K sits where iteration K + 1 would read p_{k-1}
+  const double2* p2 = reinterpret_cast<const double2*>(p_prev(const_cast<double*>(pb0), const_cast<double*>(pb1),
+                                                                st->iter));
+  double2* x2 = reinterpret_cast<double2*>(x);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n / 2;
+       t += (long long)gridDim.x * blockDim.x) {
+    const double2 pv = p2[t];
+    double2 xv = x2[t];
+    xv.x = fma(alpha, pv.x, xv.x);
+    xv.y = fma(alpha, pv.y, xv.y);
+    x2[t] = xv;
+  }
+}
+
+void launch_x_final(dd_ctx* c, cudaStream_t s) {
+  const long long n = c->g.plen;
+  (k_x_final<<<grid_blocks(n / 2, kThreads), kThreads, 0, s>>>(n, c->pb[0], c->pb[1], c->x, c->st),
+   dd::note_launch());
+  DD_CUDA(cudaGetLastError());
 }
 
 // The kernel takes 64 registers, so 4 blocks of 256 per SM are resident: one wave of 608
@@ -992,8 +1064,9 @@ static int xr_blocks(const dd_ctx* c) { return grid_blocks(c->g.plen / 2, kThrea
 
 void launch_xr_update(dd_ctx* c, cudaStream_t s) {
   const long long n = c->g.plen;
-  launch_chain(k_xr_update, dim3(xr_blocks(c)), dim3(kThreads), 0, s,
-               c->pdl != 0, n, c->pb[0], c->pb[1], (const double*)c->q, c->x, c->r, c->st, c->red, c->cnt + CNT_RR);
+  launch_chain(x_lag_target(c) != nullptr ? k_xr_update<false> : k_xr_update<true>, dim3(xr_blocks(c)), dim3(kThreads),
+               0, s, c->pdl != 0, n, c->pb[0], c->pb[1], (const double*)c->q, c->x, c->r, c->st, c->red,
+               c->cnt + CNT_RR);
   DD_CUDA(cudaGetLastError());
 }
 
@@ -1525,16 +1598,18 @@ __global__ void __launch_bounds__(kThreads, 6) kb_fused_pq(const BInst* __restri
   const BInst& I = B[m.x];
   if (!I.active) return;
   if (PAIRS)
-    fused_pq_pairs_body(VBlk{m.y, I.nb_fused}, I.g, I.tabS2, I.z, I.pb0, I.pb1, I.q, I.st, I.red, I.cnt + CNT_PQ);
+    fused_pq_pairs_body(VBlk{m.y, I.nb_fused}, I.g, I.tabS2, I.z, I.pb0, I.pb1, I.q, nullptr, I.st, I.red,
+                        I.cnt + CNT_PQ);
   else
-    fused_pq_body<2>(VBlk{m.y, I.nb_fused}, I.g, I.tabS, I.z, I.pb0, I.pb1, I.q, I.st, I.red, I.cnt + CNT_PQ);
+    fused_pq_body<2>(VBlk{m.y, I.nb_fused}, I.g, I.tabS, I.z, I.pb0, I.pb1, I.q, nullptr, I.st, I.red,
+                     I.cnt + CNT_PQ);
 }
 
 __global__ void __launch_bounds__(kThreads) kb_xr_update(const BInst* __restrict__ B, const int2* __restrict__ vmap) {
   const int2 m = vmap[blockIdx.x];
   const BInst& I = B[m.x];
   if (!I.active) return;
-  xr_update_body(VBlk{m.y, I.nb_xr}, I.g.plen, I.pb0, I.pb1, I.q, I.x, I.r, I.st, I.red, I.cnt + CNT_RR);
+  xr_update_body<true>(VBlk{m.y, I.nb_xr}, I.g.plen, I.pb0, I.pb1, I.q, I.x, I.r, I.st, I.red, I.cnt + CNT_RR);
 }
 
 template <bool ARITH, bool UPD>
