@@ -399,14 +399,14 @@ int dd_coarse_matrix(dd_ctx* ctx, double* A0_host);
  *   DD_OPT_FUSE_XR      p = 1, BF16/TF32 local inverses, fused p update, at most 4096
  *                       subdomains: 1 runs the iteration's x, r update inside the restriction
  *                       packing (each subdomain's block forms r - alpha q for its packed row and,
- *                       on the node columns it owns, updates x and sums (r, r) and takes the stop
- *                       test), and the prolong-sum stores r - alpha q; one pass over x, p, q, r
- *                       fewer per iteration.  x and r take the same values as with 0; (r, r) is
- *                       summed in another order.  On the L = 2048, h = 1/32 box the fused
- *                       kernel took 32 us against 22 + 14 us for the two, but the ground state
- *                       24.0 ms against 23.6 ms (the r store moves into the prolong-sum, which
- *                       slows by 1.5 us, and the coarse solve forks later), so off by default;
- *                       -1: off [0]
+ *                       on the node columns it owns, updates x (unless DD_OPT_X_LAG) and sums
+ *                       (r, r) and takes the stop test), and the prolong-sum stores r - alpha q;
+ *                       one kernel fewer per iteration.  x and r take the same values as with
+ *                       0; (r, r) is summed in another order.  On the L = 2048, h = 1/32 box a
+ *                       PCG iteration took 104.5 us against 99.3 us with 0 (106.0 us without
+ *                       DD_OPT_X_LAG): the packing blocks, one per overlapping subdomain, form
+ *                       r - alpha q and (r, r) slower than the separate update does, so off by
+ *                       default; -1: off [0]
  *   DD_OPT_TILED3       p = 2 with float pairs: 1 evaluates q = A_sigma p tile by tile from
  *                       shared memory (each block takes the planes of one residue a1 mod n, so
  *                       it stages the n Ypad classes of the split table once, and for every tile
@@ -415,8 +415,8 @@ int dd_coarse_matrix(dd_ctx* ctx, double* A0_host);
  *   DD_OPT_X_LAG        1: the PCG update x_{k+1} = x_k + alpha_k p_k is made by iteration k + 1's
  *                       p update (which reads p_k anyway), and once more after the last
  *                       iteration, so the x/r update streams only r and q; the same FMA on the
- *                       same operands, so x is bit-identical to 0 (x updated with r).  Not
- *                       with DD_OPT_FUSE_XR, whose fused update keeps x [1] */
+ *                       same operands, so x is bit-identical to 0 (x updated with r); with
+ *                       DD_OPT_FUSE_XR the fused packing then leaves x alone too [1] */
 #define DD_OPT_CHECK_EVERY 0
 #define DD_OPT_USE_GRAPH   1
 #define DD_OPT_FLEXIBLE    2

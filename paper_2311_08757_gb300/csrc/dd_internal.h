@@ -289,7 +289,7 @@ struct dd_ctx {
 };
 
 // the x that the PCG p update advances (x_lag), or null when the x/r update does it
-inline double* x_lag_target(dd_ctx* c) { return (c->x_lag && !c->fuse_xr) ? c->x : nullptr; }
+inline double* x_lag_target(dd_ctx* c) { return c->x_lag ? c->x : nullptr; }
 
 namespace dd {
 

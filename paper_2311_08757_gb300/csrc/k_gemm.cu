@@ -500,11 +500,13 @@ __device__ __forceinline__ void pack_xr_body(VBlk vb, Geo g, const Sub* __restri
     rv.x = fma(-alpha, qv.x, rv.x);
     rv.y = fma(-alpha, qv.y, rv.y);
     if (e >= e_lo && e < e_hi) {
-      const double2 pv = *reinterpret_cast<const double2*>(p + gi);
-      double2 xv = *reinterpret_cast<const double2*>(x + gi);
-      xv.x = fma(alpha, pv.x, xv.x);
-      xv.y = fma(alpha, pv.y, xv.y);
-      *reinterpret_cast<double2*>(x + gi) = xv;
+      if (x != nullptr) {   // null: the next p update makes it (x_lag)
+        const double2 pv = *reinterpret_cast<const double2*>(p + gi);
+        double2 xv = *reinterpret_cast<const double2*>(x + gi);
+        xv.x = fma(alpha, pv.x, xv.x);
+        xv.y = fma(alpha, pv.y, xv.y);
+        *reinterpret_cast<double2*>(x + gi) = xv;
+      }
       rr[0] = fma(rv.x, rv.x, rr[0]);
       rr[0] = fma(rv.y, rv.y, rr[0]);
     }
@@ -831,7 +833,8 @@ void launch_pack_xr(dd_ctx* c, cudaStream_t s) {
   double* c0 = c->grid.coarse ? c->c0 : nullptr;
 #define DD_PACK_XR(T)                                                                                           \
   launch_chain(k_pack_xr<T>, dim3(g.nsub), dim3(kPackThreads), 0, s, pdl, g, (const Sub*)c->subs,             \
-               (const int*)c->slot_of_sub, (const double*)c->r, (const double*)c->q, c->x, c->pb[0], c->pb[1],   \
+               (const int*)c->slot_of_sub, (const double*)c->r, (const double*)c->q,                              \
+               x_lag_target(c) != nullptr ? nullptr : c->x, c->pb[0], c->pb[1],                                 \
                c->kpad, (T*)c->Rpack, (const double*)c->wT, c0, c->st, c->red, c->cnt + CNT_RR)
   if (c->grid.precision == DD_PREC_BF16) {
     DD_PACK_XR(__nv_bfloat16);
