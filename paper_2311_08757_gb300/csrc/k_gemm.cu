@@ -16,6 +16,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -781,12 +782,27 @@ int gemm_setup(dd_ctx* c) {
     for (int t = 0; t < c->ntypes; ++t) total += (long long)mt * ((c->type_count[t] + bn - 1) / bn);
     const bool bands = total > 2 * 152;
     std::vector<Tile> tl;
-    for (int t = 0; t < c->ntypes; ++t) {
-      const int first = c->type_first[t], cnt = c->type_count[t];
-      if (bands) {
+    if (bands) {
+      // Each type band by band, and the types interleaved in proportion to their tile counts:
+      // a type with few subdomains (an edge or corner of the box) still reads its whole
+      // inverse for a few output columns (bound by DRAM), the many-subdomain interior type is
+      // bound by the tensor pipe, and spread through the launch order the two kinds of tiles
+      // run side by side instead of one phase after the other.
+      std::vector<std::pair<double, Tile>> keyed;
+      for (int t = 0; t < c->ntypes; ++t) {
+        const int first = c->type_first[t], cnt = c->type_count[t];
+        const int nt = mt * ((cnt + bn - 1) / bn);
+        int i = 0;
         for (int m = 0; m < mt; ++m)
-          for (int n0 = 0; n0 < cnt; n0 += bn) tl.push_back(Tile{t, m * 128, first + n0, first + cnt});
-      } else {
+          for (int n0 = 0; n0 < cnt; n0 += bn, ++i)
+            keyed.push_back({(i + 0.5) / nt, Tile{t, m * 128, first + n0, first + cnt}});
+      }
+      std::stable_sort(keyed.begin(), keyed.end(),
+                       [](const std::pair<double, Tile>& a, const std::pair<double, Tile>& b) { return a.first < b.first; });
+      for (const auto& k : keyed) tl.push_back(k.second);
+    } else {
+      for (int t = 0; t < c->ntypes; ++t) {
+        const int first = c->type_first[t], cnt = c->type_count[t];
         for (int n0 = 0; n0 < cnt; n0 += bn)
           for (int m = 0; m < mt; ++m) tl.push_back(Tile{t, m * 128, first + n0, first + cnt});
       }
