@@ -562,8 +562,17 @@ __global__ void __launch_bounds__(128, 16) kb_pack_xr(const BInst* __restrict__ 
 template <typename T>
 __global__ void k_pack(Geo g, const Sub* __restrict__ subs, const int* __restrict__ slot_of,
                        const double* __restrict__ r, int kpad, T* __restrict__ out, const double* __restrict__ wT,
-                       double* c0, const PcgState* st, const float* __restrict__ ascale, float* __restrict__ ysc) {
+                       double* c0, const PcgState* st, const float* __restrict__ ascale, float* __restrict__ ysc,
+                       const char* __restrict__ pf, unsigned pf_bytes) {
   pdl_enter();
+  // pf: the coarse cyclic reduction's coefficients, which the iteration's other vectors have
+  // pushed out of L2 since the last solve; prefetched into L2 here (a hint, nothing waits on
+  // it) so that the solve that follows this pass copies them from L2 rather than from DRAM
+  if (pf != nullptr && blockIdx.x == 0 && threadIdx.x == 0) {
+    for (unsigned o = 0; o < pf_bytes; o += 32768u)
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(pf + o), "r"(min(32768u, pf_bytes - o))
+                   : "memory");
+  }
   pack_body<T>(g, subs, slot_of, r, kpad, out, wT, c0, st, ascale, ysc, (int)blockIdx.x);
 }
 
@@ -829,18 +838,22 @@ void launch_pack(dd_ctx* c, const double* r, double* c0, cudaStream_t s) {
   const Geo& g = c->g;
   const bool pdl = c->pdl != 0;
   const PcgState* st = c->st;
+  // the staged part of the cyclic reduction's coefficients (a multiple of 16 bytes)
+  const bool pf_on = c0 != nullptr && !c->coarse_dense && c->cr != nullptr;
+  const char* pf = pf_on ? reinterpret_cast<const char*>(c->cr) : nullptr;
+  const unsigned pf_bytes = pf_on ? (unsigned)(sizeof(double) * (2 * (size_t)c->cr_c2 + 3 * (size_t)c->cr_w2)) : 0u;
   if (c->grid.precision == DD_PREC_BF16)
     launch_chain(k_pack<__nv_bfloat16>, dim3(g.nsub), dim3(kPackThreads), 0, s, pdl, g, (const Sub*)c->subs,
                  (const int*)c->slot_of_sub, r, c->kpad, (__nv_bfloat16*)c->Rpack, (const double*)c->wT, c0, st,
-                 (const float*)nullptr, (float*)nullptr);
+                 (const float*)nullptr, (float*)nullptr, pf, pf_bytes);
   else if (c->grid.precision == DD_PREC_TF32)
     launch_chain(k_pack<float>, dim3(g.nsub), dim3(kPackThreads), 0, s, pdl, g, (const Sub*)c->subs,
                  (const int*)c->slot_of_sub, r, c->kpad, (float*)c->Rpack, (const double*)c->wT, c0, st,
-                 (const float*)nullptr, (float*)nullptr);
+                 (const float*)nullptr, (float*)nullptr, pf, pf_bytes);
   else
     launch_chain(k_pack<__nv_fp8_e4m3>, dim3(g.nsub), dim3(kPackThreads), 0, s, pdl, g, (const Sub*)c->subs,
                  (const int*)c->slot_of_sub, r, c->kpad, (__nv_fp8_e4m3*)c->Rpack, (const double*)c->wT, c0, st,
-                 (const float*)c->ascale, (float*)c->ysc);
+                 (const float*)c->ascale, (float*)c->ysc, pf, pf_bytes);
 }
 
 void launch_pack_xr(dd_ctx* c, cudaStream_t s) {
